@@ -1,0 +1,54 @@
+"""Split-square periodic triangulations and the element lattice convention.
+
+Square (i, j) of an N x N grid on [x0, x0+L]^2 is cut along its SW-NE diagonal:
+lower triangle (i,j),(i+1,j),(i+1,j+1) and upper triangle (i,j),(i+1,j+1),(i,j+1),
+both counter-clockwise; element ids 2*(j*N+i) + {0, 1}. Periodic vertex id of
+grid point (i, j) is (i mod N) + N*(j mod N). Coordinates are unwrapped, so an
+element next to the periodic seam keeps its true shape.
+"""
+import numpy as np
+
+
+def split_square_mesh(N, L=2.0 * np.pi, origin=(0.0, 0.0)):
+    """Return (tri_vertex_ids [2N^2,3] int64, tri_coords [2N^2,3,2] float64)."""
+    N = int(N)
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    h = L / N
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")  # j rows, i columns
+    i = i.reshape(-1)
+    j = j.reshape(-1)
+    corners_lo = [(0, 0), (1, 0), (1, 1)]
+    corners_up = [(0, 0), (1, 1), (0, 1)]
+    n_tri = 2 * N * N
+    vid = np.empty((n_tri, 3), dtype=np.int64)
+    X = np.empty((n_tri, 3, 2), dtype=np.float64)
+    cell = j * N + i
+    for which, corners in enumerate((corners_lo, corners_up)):
+        t = 2 * cell + which
+        for c, (di, dj) in enumerate(corners):
+            vid[t, c] = ((i + di) % N) + N * ((j + dj) % N)
+            X[t, c, 0] = origin[0] + (i + di) * h
+            X[t, c, 1] = origin[1] + (j + dj) * h
+    return vid, X
+
+
+def n_lattice(m):
+    """Number of points of the degree-m element lattice (1 point, the centroid, for m = 0)."""
+    return (m + 1) * (m + 2) // 2
+
+
+def lattice_points(tri_coords, m):
+    """Equispaced lattice points v0 + (i/m)(v1-v0) + (j/m)(v2-v0), j = 0..m, i = 0..m-j.
+
+    For m = 0 the single point is the centroid. Returns [n_tri, n_lattice(m), 2].
+    """
+    X = np.asarray(tri_coords, dtype=np.float64)
+    v0, v1, v2 = X[:, 0, :], X[:, 1, :], X[:, 2, :]
+    if m == 0:
+        return ((v0 + v1 + v2) / 3.0)[:, None, :]
+    pts = []
+    for jj in range(m + 1):
+        for ii in range(m + 1 - jj):
+            pts.append(v0 + (ii / m) * (v1 - v0) + (jj / m) * (v2 - v0))
+    return np.stack(pts, axis=1)

@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test is chosen so that a plausible mistake in one part of the oracle
+(a dropped term, a wrong sign, a transposed operand, a wrong stage
+coefficient) fails it. None of them compares the oracle with itself.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import Discretization
+from oracle.quadrature import triangle_rule, facet_rule
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def disc(N, k, nu=0.0, L=2 * np.pi, alpha=2.0):
+    vid, X = synth.split_square_mesh(N, L=L)
+    return Discretization(vid, X, k, nu, alpha=alpha), X
+
+
+def projected(d, X, field):
+    return d.project(d.from_lattice(synth.sample_lattice(field, X, d.k)))
+
+
+def load_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("deg", [2, 5, 8, 11])
+def test_triangle_rule_exact_for_monomials(deg):
+    # closed form: int over the unit right triangle of x^a y^b = a! b! / (a + b + 2)!
+    xi, w = triangle_rule(deg)
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs((w * xi[:, 0] ** a * xi[:, 1] ** b).sum() - exact) < 1e-15
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_facet_rule_exact_to_degree_3k(k):
+    t, w = facet_rule(k)
+    assert len(t) == math.ceil((3 * k + 1) / 2)
+    for p in range(3 * k + 1):
+        assert abs((w * t ** p).sum() - 1.0 / (p + 1)) < 1e-15
+
+
+# ------------------------------------------------------------------------ mesh
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_periodic_split_square_topology(N):
+    d, _ = disc(N, 1)
+    T = d.topo
+    assert d.n_tri == 2 * N * N and d.n_facet == 3 * N * N
+    # every facet is shared by two triangles traversing it in opposite directions
+    assert np.all(T.facet_orient[:, 0] == -T.facet_orient[:, 1])
+    # both sides see the same edge length and opposite outward normals
+    l0 = T.edge_len[T.facet_tri[:, 0], T.facet_loc[:, 0]]
+    l1 = T.edge_len[T.facet_tri[:, 1], T.facet_loc[:, 1]]
+    n0 = T.normal[T.facet_tri[:, 0], T.facet_loc[:, 0]]
+    n1 = T.normal[T.facet_tri[:, 1], T.facet_loc[:, 1]]
+    assert np.allclose(l0, l1) and np.allclose(n0, -n1)
+    # the two copies of a facet point differ by a period (or coincide)
+    t = np.array([0.3])
+    f = np.arange(d.n_facet)
+    p0 = T.facet_points(f, np.zeros_like(f), t)[:, 0]
+    p1 = T.facet_points(f, np.ones_like(f), t)[:, 0]
+    shift = (p0 - p1) / (2 * np.pi)
+    assert np.allclose(shift, np.round(shift), atol=1e-12)
+
+
+def test_open_mesh_rejected():
+    vid, X = synth.split_square_mesh(3)
+    with pytest.raises(ValueError):
+        Discretization(vid[:-1], X[:-1], 1, 0.0)
+
+
+# ------------------------------------------------------------ space dimensions
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 1), (2, 2), (3, 2), (2, 3), (3, 3)])
+def test_divfree_dimension_on_torus(N, k):
+    # V_h^{k,-1} = curl of continuous P^{k+1} (Remark 1): N^2 (k+1)^2 - 1 curls plus 2 constant fields
+    d, _ = disc(N, k)
+    assert d.divfree_basis().shape[1] == N * N * (k + 1) ** 2 + 1
+    # the BDM space (normal continuity only) has N^2 (k+1)(2k+1) dimensions on the torus
+    B = d.constraint_matrix().toarray()
+    nf = d.n_facet * d.nl
+    jump_rows = B[d.n_tri * d.nw:]
+    assert jump_rows.shape[0] == nf
+    bdm = d.n_tri * d.nd - np.linalg.matrix_rank(jump_rows)
+    assert bdm == N * N * (k + 1) * (2 * k + 1)
+
+
+def test_table3_dof_counts():
+    # NGSolve variant of Remark 3: velocity with div in P^0 plus a constant pressure per element,
+    # multipliers P^k per facet; Table 3 totals over 488 triangles and 772 facets
+    import scipy.linalg as sla
+    for k, local, glob in load_golden("table3_dofs.txt"):
+        k = int(k)
+        d, _ = disc(2, k)
+        D = d.prepare()["D"][0]                               # (z_m, div phi_j) on triangle 0
+        P, W = d._vol(np.array([0]))
+        Z, _ = d._basis(d.wexps, np.array([0]), P)
+        mean = np.einsum("tq,tqm->m", W, Z)                   # (z_m, 1)
+        Q = sla.null_space(mean[None, :])                     # mean-free pressures
+        dim_vel = d.nd - np.linalg.matrix_rank(Q.T @ D)
+        assert 488 * (dim_vel + 1) == int(local)
+        assert 772 * d.nl == int(glob)
+
+
+# ------------------------------------------------------------------ the solve
+@pytest.mark.parametrize("N,k", [(2, 1), (2, 2), (3, 3)])
+def test_four_solve_routes_agree(N, k):
+    d, X = disc(N, k)
+    rng = np.random.default_rng(7)
+    F = rng.standard_normal((d.n_tri, d.nd))
+    u1, w1, l1 = d.solve_condensed(F)
+    u2 = d.project_nullspace(F)
+    u3, w3, l3 = d.solve_full(F)
+    u4, l4 = d.solve_fe4(F)
+    s = np.linalg.norm(u1)
+    assert np.linalg.norm(u1 - u2) / s < 1e-12
+    assert np.linalg.norm(u1 - u3) / s < 1e-12
+    assert np.linalg.norm(u1 - u4) / s < 1e-12
+    w1n, l1n = d.normalize_pressure(w1, l1)
+    w3n, l3n = d.normalize_pressure(w3, l3)
+    assert np.abs(w1n - w3n).max() < 1e-10 * max(1, np.abs(w1n).max())
+    # eq. (13) carries the multiplier with the opposite sign (defined up to the same constant)
+    _, l4n = d.normalize_pressure(w1, -l4)
+    assert np.abs(l4n - l1n).max() < 1e-10 * max(1, np.abs(l1n).max())
+
+
+def test_projection_is_divfree_idempotent_and_symmetric():
+    d, X = disc(3, 2)
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal((d.n_tri, d.nd))
+    P1 = d.project(U)
+    dg = d.diagnostics(P1)
+    assert dg["max_div"] < 1e-12 and dg["max_jump"] < 1e-12
+    P2 = d.project(P1)
+    assert np.abs(P2 - P1).max() < 1e-12 * np.abs(P1).max()
+    # the solve operator Q: F -> u is symmetric in the L2 pairing (the adjoint relies on it)
+    F1, F2 = rng.standard_normal((2, d.n_tri, d.nd))
+    a = (F1 * d.solve_condensed(F2)[0]).sum()
+    b = (F2 * d.solve_condensed(F1)[0]).sum()
+    assert abs(a - b) < 1e-12 * max(abs(a), 1)
+
+
+def test_projection_energy_never_grows():
+    d, X = disc(4, 2)
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((d.n_tri, d.nd))
+    assert d.energy(d.project(U)) <= d.energy(U)
+
+
+# ------------------------------------------------------------------- residual
+def test_constant_velocity_is_a_steady_state():
+    d, X = disc(3, 2, nu=0.1)
+    U = projected(d, X, synth.constant_field((0.3, -0.7)))
+    lat = d.to_lattice(U)
+    assert np.abs(lat - np.array([0.3, -0.7])).max() < 1e-13
+    assert np.abs(d.residual(U)).max() < 1e-12
+    U2 = d.rk3_step(U, 0.05, 3)
+    assert np.abs(U2 - U).max() < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_energy_identity_of_upwind_form(k):
+    # Sec. 2.2: C_h(u;u,u) = (1/2) sum_F int |u.n| |[u]|^2 >= 0 for u in V_h^{k,-1}
+    # (the paper omits the 1/2 and writes the normal jump; integrating by parts gives this).
+    d, X = disc(3, k)
+    rng = np.random.default_rng(11 + k)
+    U = d.project(rng.standard_normal((d.n_tri, d.nd)))
+    R = d.residual(U, nu=0.0)
+    lhs = -(R * U).sum()                   # C_h(u;u,u)
+    rhs = d.upwind_dissipation(U)
+    assert rhs > 0
+    assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_sipg_form_is_symmetric(k):
+    # eq. (18) is symmetric in (u, v) for any broken fields
+    d, X = disc(3, k)
+    rng = np.random.default_rng(21 + k)
+    U, V = rng.standard_normal((2, d.n_tri, d.nd))
+    BU = d.residual(U, nu=1.0) - d.residual(U, nu=0.0)
+    BV = d.residual(V, nu=1.0) - d.residual(V, nu=0.0)
+    a = (BU * V).sum()
+    b = (BV * U).sum()
+    assert abs(a - b) < 1e-12 * max(1.0, abs(a))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_sipg_coercive_on_divfree_space_at_alpha_2(k):
+    # B_h(u,u) >= 0 on V_h^{k,-1}; its kernel is the two constant fields
+    d, X = disc(3, k, L=1.0)
+    Z = d.divfree_basis()
+    B = np.stack([-(d.residual(Z[:, i].reshape(d.n_tri, d.nd), 1.0)
+                    - d.residual(Z[:, i].reshape(d.n_tri, d.nd), 0.0)).ravel()
+                  for i in range(Z.shape[1])], 1)
+    ev = np.linalg.eigvalsh(0.5 * (Z.T @ B + (Z.T @ B).T))
+    assert ev[0] > -1e-12 * ev[-1]
+    assert (ev < 1e-10 * ev[-1]).sum() == 2
+
+
+def test_sipg_not_coercive_for_k1_at_alpha_2_but_at_3():
+    # recorded reading: alpha k^2/h with h the element diameter is too weak for k = 1 on these meshes
+    def mineig(alpha):
+        d, X = disc(3, 1, L=1.0, alpha=alpha)
+        Z = d.divfree_basis()
+        B = np.stack([-(d.residual(Z[:, i].reshape(d.n_tri, d.nd), 1.0)
+                        - d.residual(Z[:, i].reshape(d.n_tri, d.nd), 0.0)).ravel()
+                      for i in range(Z.shape[1])], 1)
+        return np.linalg.eigvalsh(0.5 * (Z.T @ B + (Z.T @ B).T))[0]
+    assert mineig(2.0) < -0.1
+    assert mineig(3.0) > -1e-12
+
+
+# ------------------------------------------------------- closed-form solutions
+def _tgv_error(N, k, nu, T, field_exact, field0, L=2 * np.pi, steps_per=None):
+    d, X = disc(N, k, nu=nu, L=L)
+    U = projected(d, X, field0)
+    h = math.sqrt(2) * L / N
+    dt = 0.1 * h / (k * k * 2.0)
+    n = max(1, int(math.ceil(T / dt)))
+    U = d.rk3_step(U, T / n, n)
+    return d.l2_error(U, field_exact), d, U
+
+
+def test_taylor_green_velocity_order():
+    # Example 1a / Table 1: L2 velocity error of order k + 1
+    nu, T = 1e-2, 0.3
+    tg = synth.taylor_green()
+
+    def exact(x, y):
+        a, b = tg(x, y)
+        f = math.exp(-2 * nu * T)
+        return f * a, f * b
+    table = {int(r[0]): r[1] for r in load_golden("table1_eoc.txt")}
+    for k, Ns in ((1, (8, 16)), (2, (4, 8))):
+        e = [_tgv_error(N, k, nu, T, exact, tg)[0] for N in Ns]
+        eoc = math.log2(e[0] / e[1])
+        assert abs(eoc - table[k]) < 0.45, (k, eoc)
+
+
+def test_advected_taylor_green_moves_downstream():
+    # Galilean translate of the vortex (exact NS solution); pins the direction of convection
+    nu, T, U0 = 1e-2, 0.5, (1.0, 0.0)
+    f0 = synth.advected_taylor_green(U0, t=0.0, nu=nu)
+    fwd = synth.advected_taylor_green(U0, t=T, nu=nu)
+    bwd = synth.advected_taylor_green((-1.0, 0.0), t=T, nu=nu)
+
+    def back(x, y):
+        a, b = bwd(x, y)
+        return a + 2.0, b                      # mean flow (1, 0), pattern moved upstream
+    e_fwd, d, U = _tgv_error(8, 2, nu, T, fwd, f0)
+    e_bwd = d.l2_error(U, back)
+    assert e_fwd < 0.05 and e_bwd > 10 * e_fwd
+
+
+def test_taylor_green_pressure():
+    # p = (cos 2x + cos 2y)/4 for u = (sin x cos y, -cos x sin y) (steady Euler); w ~ p (Remark 2)
+    errs = []
+    for N in (4, 8):
+        d, X = disc(N, 3, nu=0.0)
+        U = projected(d, X, synth.taylor_green())
+        w, lam = d.pressure(U)
+        errs.append(d.pressure_l2_error(w, lambda x, y: 0.25 * (np.cos(2 * x) + np.cos(2 * y))))
+        pe, pf = d.pressure_lattice(w, lam)
+    assert errs[1] < 0.3 * errs[0] and errs[1] < 0.05
+    # facet multiplier approximates the same pressure on the skeleton (Theorem 2)
+    T = d.topo
+    f = np.arange(d.n_facet)
+    pts = T.facet_points(f, np.zeros_like(f), np.arange(4) / 3.0)
+    ex = 0.25 * (np.cos(2 * pts[..., 0]) + np.cos(2 * pts[..., 1]))
+    assert np.abs(pf - ex).max() < 0.01
+
+
+def test_rk3_is_third_order_in_time():
+    # Table 2 (TVD-RK3 eoc 3): Richardson errors against a fine-step solution on a fixed mesh
+    d, X = disc(4, 2, nu=1e-2)
+    U0 = projected(d, X, synth.advected_taylor_green((1.0, 0.5), nu=1e-2))
+    T = 0.4
+    ref = d.rk3_step(U0, T / 256, 256)
+    e = []
+    for n in (8, 16, 32):
+        e.append(np.sqrt(d.energy(d.rk3_step(U0, T / n, n) - ref)))
+    eoc = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    tab = [r[1] for r in load_golden("table2_eoc.txt")]
+    assert all(abs(a - 3.0) < 0.25 for a in eoc), eoc
+    assert all(abs(b - 3.0) < 0.05 for b in tab)
+
+
+def test_euler_energy_non_increasing():
+    # Sec. 2.2: with nu = 0 and upwinding the discrete energy does not grow
+    vid, X = synth.split_square_mesh(6, L=1.0)
+    d = Discretization(vid, X, 2, 0.0)
+    U = projected(d, X, synth.random_spectrum_velocity(5, kmax=4, L=1.0))
+    vmax = np.abs(d.to_lattice(U)).max()
+    dt = synth.cfl_dt(X, 2, vmax, 0.0)
+    E = [d.energy(U)]
+    for _ in range(15):
+        U = d.rk3_step(U, dt, 1)
+        E.append(d.energy(U))
+    dE = np.diff(E)
+    assert np.all(dE <= 1e-14 * E[0]), dE
+    assert E[-1] < E[0]
+
+
+def test_euler_energy_rate_matches_semidiscrete_identity():
+    # dE/dt = 2 L(u)(u) = -2 C_h(u;u,u) for the semi-discrete scheme eq. (6): a small step of RK3
+    # must reproduce it to O(dt^2)
+    d, X = disc(4, 2, nu=0.0, L=1.0)
+    U = projected(d, X, synth.random_spectrum_velocity(2, kmax=3, L=1.0))
+    rate = -2.0 * d.upwind_dissipation(U)
+    for dt in (1e-3, 5e-4):
+        est = (d.energy(d.rk3_step(U, dt, 1)) - d.energy(U)) / dt
+        assert abs(est - rate) < 50 * dt * abs(rate) + 1e-12
