@@ -1,0 +1,161 @@
+/*
+ * dgdf.h - C ABI of the GB300 explicit divergence-free DG library (libdgdf).
+ *
+ * The library advances the incompressible Euler / Navier-Stokes equations with
+ * the explicit divergence-free DG method of G. Fu, "An explicit divergence-free
+ * DG method for incompressible flow" (arXiv:1808.04669):
+ *   - velocity in the globally divergence-free subspace V_h^{k,-1} of the broken
+ *     space [P^k(T)]^2 on a triangulation (Sec. 2.1, eq. (4d));
+ *   - spatial operator L(u)(v) = -C_h(u;u,v) - B_h(u,v), the upwind convection
+ *     form (Sec. 2.2, eq. (7)) plus the symmetric interior-penalty viscous form
+ *     (Sec. 3, eq. (18));
+ *   - SSP-RK3 in time (Sec. 2.3, eq. (8)); every stage inverts the mass matrix
+ *     of V_h^{k,-1} as the hybrid-mixed Poisson solve of Sec. 2.4, eq. (12)
+ *     (Theorem 2): element static condensation, a preconditioned CG solve of
+ *     the SPD facet-multiplier system, element-local recovery.
+ *
+ * All compute runs in CUDA kernels on the current device (sm_103a). The host
+ * does set-up only (topology, reference tables, element operators, once per
+ * mesh, in FP64).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh: n_tri counter-clockwise triangles. tri_vertex_ids[t][c] (int64) is the
+ *   id of corner c after periodic identification; tri_coords[t][c][0..1]
+ *   (double) are the unwrapped corner coordinates, so every triangle keeps its
+ *   true shape next to a periodic seam. The mesh must be closed: every edge is
+ *   shared by exactly two triangles (periodic or interior facets, Sec. 2.1);
+ *   an edge with one triangle is a boundary facet, which this version rejects
+ *   with DG_ERR_UNSUPPORTED.
+ * Local facet e of a triangle is the edge opposite corner e. Two edges are the
+ *   same facet when they join the same identified vertices in the same
+ *   canonical order and have equal edge vectors; the canonical direction of a
+ *   facet is its edge vector d with d_x > 0, or d_x = 0 and d_y > 0. Facets
+ *   are numbered in order of first appearance over (triangle, local facet).
+ * Lattice values (the basis-free exchange format): a field of degree m on a
+ *   triangle is given by its values at v0 + (i/m)(v1-v0) + (j/m)(v2-v0),
+ *   j = 0..m, i = 0..m-j (j outer), n_lat(m) = (m+1)(m+2)/2 points; for m = 0
+ *   the point is the centroid. Velocity: double [n_tri][n_lat(k)][2];
+ *   element pressure: double [n_tri][n_lat(k-1)]; facet pressure: double
+ *   [n_facet][k+1] at the equispaced points t = i/k, i = 0..k, along the
+ *   canonical direction.
+ * Memory: the library owns every device buffer inside a dg_mesh. Inputs are
+ *   copied; outputs go to caller-allocated buffers. "on_device" = 1 means the
+ *   pointer is device memory on the mesh's device, 0 host memory.
+ * Streams: all work is enqueued on dg_params.cuda_stream (NULL = legacy
+ *   default stream). Every call returns a dg_status and has finished its
+ *   device work (the stream is synchronised) before returning, except where
+ *   stated.
+ * Errors: a negative dg_status; dg_last_error() gives a message (per thread).
+ *   After DG_ERR_CUDA the mesh should be destroyed.
+ */
+#ifndef DGDF_H
+#define DGDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh;
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_INVALID_ARG = -1,   /* bad pointer, size or parameter */
+  DG_ERR_MESH = -2,          /* degenerate / clockwise triangle, inconsistent facet */
+  DG_ERR_UNSUPPORTED = -3,   /* boundary facets, degree out of range */
+  DG_ERR_CUDA = -4,          /* a CUDA runtime call failed */
+  DG_ERR_NOT_CONVERGED = -5, /* a facet-system solve hit cg_maxit (state is still updated) */
+  DG_ERR_NONFINITE = -6,     /* NaN/Inf in an input or in a solver residual */
+  DG_ERR_OOM = -7            /* device allocation failed */
+} dg_status;
+
+enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
+
+typedef struct {
+  int k;              /* polynomial degree, 1 <= k <= 3 */
+  double nu;          /* kinematic viscosity >= 0 (nu = 0: Euler) */
+  double alpha;       /* SIPG penalty alpha of eq. (18); the paper uses 2 (Sec. 4) */
+  int precision;      /* DG_PRECISION_FP64 or DG_PRECISION_MIXED (FP32 PCG in FP64 refinement) */
+  double cg_rtol;     /* facet solve stops at ||g - S lam||_2 <= cg_rtol ||g||_2 (<= 0: 1e-13) */
+  int cg_maxit;       /* iteration cap per solve (<= 0: 20000) */
+  void* cuda_stream;  /* cudaStream_t to enqueue on (NULL: default stream) */
+} dg_params;
+
+/* Build a mesh: topology, reference tables and the per-element operators of
+ * eq. (12) on the host in FP64 (Remark 2: the matrix does not depend on dt, so
+ * it is set up once), then uploaded. State starts at zero.
+ * n_tri >= 1; tri_vertex_ids int64 [n_tri][3]; tri_coords double [n_tri][3][2]
+ * (both host memory). On success *out owns the mesh.
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED, DG_ERR_CUDA, DG_ERR_OOM. */
+int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords,
+                   const dg_params* params, dg_mesh** out);
+
+/* Release every device buffer of the mesh. NULL is allowed. */
+int dg_mesh_destroy(dg_mesh* mesh);
+
+/* Sizes: out[0] = n_tri, out[1] = n_facet, out[2] = k, out[3] = n_lat(k),
+ * out[4] = element geometry classes, out[5] = facet stencil classes,
+ * out[6] = broken velocity DOFs n_tri (k+1)(k+2), out[7] = multiplier DOFs n_facet (k+1). */
+int dg_mesh_info(const dg_mesh* mesh, int64_t out[8]);
+
+/* Set the state from lattice values vals [n_tri][n_lat(k)][2] (the broken P^k
+ * field interpolating them). No projection is applied: call
+ * dg_project_divfree to move it into V_h^{k,-1}.
+ * Errors: DG_ERR_INVALID_ARG (NULL), DG_ERR_NONFINITE (NaN/Inf in vals). */
+int dg_set_velocity(dg_mesh* mesh, const double* vals, int on_device);
+
+/* Read the state as lattice values [n_tri][n_lat(k)][2]. */
+int dg_get_velocity(dg_mesh* mesh, double* vals, int on_device);
+
+/* State <- L2 projection onto V_h^{k,-1}: the hybrid-mixed solve of eq. (12)
+ * with the functional F(v) = (u, v) (Theorem 2). */
+int dg_project_divfree(dg_mesh* mesh);
+
+/* nsteps >= 0 steps of SSP-RK3 (eq. (8)) with the fixed step dt > 0. Each stage
+ * forms F = a M u^n + b [M u' + dt L(u')] and solves eq. (12) for the next
+ * stage velocity. With DG_PRECISION_MIXED the stage increment b dt L(u') is
+ * evaluated and projected in FP32 (FP32 PCG inside FP64 iterative
+ * refinement) and added to a u^n + b u' in FP64.
+ * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
+ * a residual norm became NaN/Inf (the state is then undefined). */
+int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
+
+/* Pressure of the current state: the (w, lam) of eq. (12) with the functional
+ * L(u) alone, so w ~ p in the elements and lam ~ p on the skeleton (Theorem 2,
+ * Remark 2), shifted by one constant so that the integral of w is zero
+ * (L^2_0, eq. (4e)). p_elem [n_tri][n_lat(k-1)]; p_facet [n_facet][k+1] or NULL. */
+int dg_get_pressure(dg_mesh* mesh, double* p_elem, double* p_facet, int on_device);
+
+/* Riesz representer of L(u) for the current state u (no projection): the
+ * broken P^k field r with (r, v) = L(u)(v) for every broken v, as lattice
+ * values [n_tri][n_lat(k)][2]. Exposes the residual kernels on their own. */
+int dg_eval_residual(dg_mesh* mesh, double* vals, int on_device);
+
+/* Diagnostics of the current state, computed on the device in FP64:
+ * out[0] energy ||u||^2, out[1] enstrophy ||curl_h u||^2 (Example 2),
+ * out[2] max |div u| at volume quadrature points, out[3] max |[u.n]| at facet
+ * quadrature points, out[4] CG iterations of the last solve, out[5] CG
+ * iterations summed since creation, out[6] solves since creation,
+ * out[7] relative residual of the last solve. */
+int dg_get_diagnostics(dg_mesh* mesh, double out[8]);
+
+/* Per-kernel-class device timing. enable = 1 makes the library record a CUDA
+ * event pair on its stream around every kernel launch from then on and add the
+ * elapsed times up at the end of each call; enable = 0 stops recording,
+ * enable = 2 resets the totals. out_ms / out_launches (each n entries, or NULL)
+ * receive the totals per class in the order of dg_kernel_name(0..). */
+int dg_profile(dg_mesh* mesh, int enable, double* out_ms, int64_t* out_launches, int n);
+
+/* Name of kernel class i, or NULL past the last class. */
+const char* dg_kernel_name(int i);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGDF_H */

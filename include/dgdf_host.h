@@ -1,0 +1,43 @@
+/*
+ * dgdf_host.h - host-only introspection of libdgdf's set-up (no GPU needed).
+ *
+ * These calls expose the FP64 set-up that dg_mesh_create performs on the host
+ * before anything reaches the device, so that it can be checked on a machine
+ * without a GPU: the facet topology of Sec. 2.1 and the reference quadrature
+ * rules and orthonormal basis behind the element and facet kernels. They
+ * allocate host memory only and never touch CUDA.
+ */
+#ifndef DGDF_HOST_H
+#define DGDF_HOST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Facet topology with the conventions of dgdf.h. Inputs as dg_mesh_create.
+ * *n_facet receives the facet count. If tri_facet (int32 [n_tri][3]) is not
+ * NULL it receives the facet of each local facet; tri_orient (int8 [n_tri][3])
+ * +1 / -1 when the triangle traverses it along / against its canonical
+ * direction; facet_tri (int32 [n_facet][2]) its two triangles, first
+ * appearance first; all three must then hold the sizes above (call once with
+ * NULLs to get n_facet). Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED. */
+int dg_host_topology(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords,
+                     int64_t* n_facet, int32_t* tri_facet, int8_t* tri_orient, int32_t* facet_tri);
+
+/* Reference tables for degree k (1..3) on the triangle {xi1, xi2 >= 0, xi1 + xi2 <= 1}:
+ *   table 0: volume rule, [nq][3] = (xi1, xi2, weight), exact to degree 3k-1 (weights sum to 1/2)
+ *   table 1: facet rule on [0,1], [nqf][2] = (t, weight), nqf = ceil((3k+1)/2)
+ *   table 2: orthonormal basis at the volume points, [nq][ns]
+ *   table 3: reference gradients at the volume points, [nq][ns][2]
+ *   table 4: basis at the k-lattice points, [ns][ns] (row = point)
+ * ns = (k+1)(k+2)/2. *n_out receives the number of doubles; out (capacity cap
+ * doubles) may be NULL to query the size. */
+int dg_host_reference(int k, int table, double* out, int64_t cap, int64_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGDF_HOST_H */

@@ -166,6 +166,14 @@ class Discretization:
             out[tri] = np.einsum("tij,tcj->tci", self.scalar_mass(tri), U[tri])
         return out.reshape(self.n_tri, self.nd)
 
+    def riesz(self, R):
+        """Broken field r with (r, phi_i) = R[t, i] for every broken test phi_i (element mass solves)."""
+        R = np.asarray(R).reshape(self.n_tri, 2, self.ns)
+        out = np.empty_like(R)
+        for tri in self._chunks(self.n_tri):
+            out[tri] = np.transpose(np.linalg.solve(self.scalar_mass(tri), np.transpose(R[tri], (0, 2, 1))), (0, 2, 1))
+        return out.reshape(self.n_tri, self.nd)
+
     # ------------------------------------------------------- local operators
     def _local_ops(self, tri):
         """M_T, D_T = (z_m, div phi_j)_T, C_T = <mu_m, phi_j.n>_{F_e} of eq. (12) on triangles tri."""

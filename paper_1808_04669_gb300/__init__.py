@@ -1,0 +1,168 @@
+"""GB300-native explicit divergence-free DG (Fu, arXiv:1808.04669): Python binding of libdgdf.
+
+The library (C ABI in include/dgdf.h) holds the whole hot path: the SSP-RK3
+stage residual, the hybrid-mixed facet solve and the recovery run as CUDA
+kernels for sm_103a. This module only marshals arguments: numpy arrays are
+passed as host pointers, torch CUDA tensors as device pointers on their stream.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import DGError, DGParams, check, lib
+
+FP64 = 0
+MIXED = 1
+
+
+def _ptr(a):
+    """(pointer, on_device) of a C-contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("need a C-contiguous float64 array")
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("need a contiguous float64 tensor")
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class DGMesh:
+    """One mesh and its state, owned by libdgdf (dg_mesh_create ... dg_mesh_destroy)."""
+
+    def __init__(self, tri_vertex_ids, tri_coords, k, nu, alpha=2.0, precision=FP64, cg_rtol=1e-13,
+                 cg_maxit=20000, stream=None):
+        L = lib()
+        vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
+        X = np.ascontiguousarray(tri_coords, dtype=np.float64)
+        if vid.ndim != 2 or vid.shape[1] != 3 or X.shape != (vid.shape[0], 3, 2):
+            raise ValueError("tri_vertex_ids [n,3] and tri_coords [n,3,2] expected")
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        self.params = DGParams(int(k), float(nu), float(alpha), int(precision), float(cg_rtol), int(cg_maxit),
+                               ctypes.c_void_p(int(stream)))
+        h = ctypes.c_void_p()
+        check(L.dg_mesh_create(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(self.params), ctypes.byref(h)), "dg_mesh_create")
+        self._h = h
+        info = self.info()
+        self.n_tri, self.n_facet, self.k, self.n_lat = (int(v) for v in info[:4])
+        self.n_class, self.n_stencil = int(info[4]), int(info[5])
+        self.n_vel_dofs, self.n_lam_dofs = int(info[6]), int(info[7])
+        self.nw = self.k * (self.k + 1) // 2
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        out = (ctypes.c_int64 * 8)()
+        check(lib().dg_mesh_info(self._h, out), "dg_mesh_info")
+        return list(out)
+
+    def set_velocity(self, vals):
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        p, dev = _ptr(vals)
+        check(lib().dg_set_velocity(self._h, p, dev), "dg_set_velocity")
+
+    def get_velocity(self, out=None):
+        if out is None:
+            out = np.empty((self.n_tri, self.n_lat, 2))
+        p, dev = _ptr(out)
+        check(lib().dg_get_velocity(self._h, p, dev), "dg_get_velocity")
+        return out
+
+    def project_divfree(self):
+        check(lib().dg_project_divfree(self._h), "dg_project_divfree")
+
+    def rk3_step(self, dt, nsteps=1):
+        check(lib().dg_rk3_step(self._h, float(dt), int(nsteps)), "dg_rk3_step")
+
+    def get_pressure(self, with_facet=True, out=None):
+        if out is None:
+            pe = np.empty((self.n_tri, self.nw))
+            pf = np.empty((self.n_facet, self.k + 1)) if with_facet else None
+        else:
+            pe, pf = out
+        p1, dev = _ptr(pe)
+        p2 = _ptr(pf)[0] if pf is not None else None
+        check(lib().dg_get_pressure(self._h, p1, p2, dev), "dg_get_pressure")
+        return pe, pf
+
+    def eval_residual(self, out=None):
+        if out is None:
+            out = np.empty((self.n_tri, self.n_lat, 2))
+        p, dev = _ptr(out)
+        check(lib().dg_eval_residual(self._h, p, dev), "dg_eval_residual")
+        return out
+
+    def diagnostics(self):
+        out = (ctypes.c_double * 8)()
+        check(lib().dg_get_diagnostics(self._h, out), "dg_get_diagnostics")
+        keys = ("energy", "enstrophy", "max_div", "max_jump", "last_iters", "total_iters", "solves", "last_relres")
+        return dict(zip(keys, list(out)))
+
+    def profile(self, enable):
+        n = 16
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        check(lib().dg_profile(self._h, int(enable), ms, cnt, n), "dg_profile")
+        res = {}
+        for i in range(n):
+            name = lib().dg_kernel_name(i)
+            if name is None:
+                break
+            res[name.decode()] = (ms[i], int(cnt[i]))
+        return res
+
+
+def host_topology(tri_vertex_ids, tri_coords):
+    """Facet topology computed by the library's host set-up (no GPU): (tri_facet, tri_orient, facet_tri)."""
+    L = lib()
+    vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tri_coords, dtype=np.float64)
+    nf = ctypes.c_int64()
+    V = ctypes.c_void_p
+    check(L.dg_host_topology(vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), ctypes.byref(nf),
+                             None, None, None), "dg_host_topology")
+    tf = np.empty((vid.shape[0], 3), dtype=np.int32)
+    to = np.empty((vid.shape[0], 3), dtype=np.int8)
+    ft = np.empty((nf.value, 2), dtype=np.int32)
+    check(L.dg_host_topology(vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), ctypes.byref(nf),
+                             tf.ctypes.data_as(V), to.ctypes.data_as(V), ft.ctypes.data_as(V)), "dg_host_topology")
+    return tf, to, ft
+
+
+def host_reference(k, table):
+    """Reference tables of the library's host set-up (see include/dgdf_host.h)."""
+    L = lib()
+    n = ctypes.c_int64()
+    check(L.dg_host_reference(int(k), int(table), None, 0, ctypes.byref(n)), "dg_host_reference")
+    out = np.empty(n.value)
+    check(L.dg_host_reference(int(k), int(table), out.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
+          "dg_host_reference")
+    return out
+
+
+__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "lib"]

@@ -1,0 +1,485 @@
+// C ABI of libdgdf (declared in include/dgdf.h): mesh set-up, state I/O and
+// the stage pipeline. Host code here only orchestrates; every step of the
+// method runs in the kernels of k_element.cu and k_solver.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgdf.h"
+#include "device.cuh"
+#include "setup.hpp"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+enum KernelClass {
+  KC_STAGE = 0,
+  KC_INCREMENT,
+  KC_SOLVE64,
+  KC_SOLVE_MIXED,
+  KC_RECOVER,
+  KC_PROJECT_RHS,
+  KC_LATTICE,
+  KC_DIAG,
+  KC_PRESSURE,
+  KC_COUNT
+};
+const char* kKernelNames[KC_COUNT] = {"stage_residual_fp64", "stage_increment_fp32", "facet_pcg_fp64",
+                                      "facet_pcg_mixed",     "recover",              "project_rhs",
+                                      "lattice",             "diagnostics",          "pressure"};
+
+}  // namespace
+
+struct dg_mesh {
+  dgdf::HostMesh hm;
+  dgdf::DevMesh dm{};
+  dg_params p{};
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  int solver_blocks[2] = {1, 1};
+  double last_bdt = 0.0;
+  bool has_lam = false;
+  double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
+  double* wbuf = nullptr;        // [n_tri][nw] element pressure
+  double* pe = nullptr;          // [n_tri][nw] pressure lattice staging
+  double* pfac = nullptr;        // [n_facet][nl]
+  int* dflag = nullptr;          // finite check
+  dgdf::DevStats* host_stats = nullptr;
+  // profiling
+  bool prof = false;
+  struct Rec {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[KC_COUNT] = {};
+  long long prof_n[KC_COUNT] = {};
+};
+
+namespace {
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,                         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                \
+  } while (0)
+
+template <typename T>
+int dalloc(dg_mesh* M, T** out, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) return fail(DG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  M->allocs.push_back(p);
+  *out = static_cast<T*>(p);
+  return DG_OK;
+}
+
+template <typename T>
+int upload(dg_mesh* M, const T** out, const std::vector<T>& v) {
+  T* p = nullptr;
+  int rc = dalloc(M, &p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = p;
+  return DG_OK;
+}
+
+std::vector<float> to_float(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+cudaEvent_t get_event(dg_mesh* M) {
+  if (!M->pool.empty()) {
+    cudaEvent_t e = M->pool.back();
+    M->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch wrapper: records an event pair around the launch when profiling.
+template <typename F>
+int launch(dg_mesh* M, int kc, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (M->prof) {
+    a = get_event(M);
+    b = get_event(M);
+    cudaEventRecord(a, M->stream);
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("kernel launch (") + kKernelNames[kc] + "): " + cudaGetErrorString(e));
+  if (M->prof) {
+    cudaEventRecord(b, M->stream);
+    M->pending.push_back({kc, a, b});
+  }
+  return DG_OK;
+}
+
+void collect_profile(dg_mesh* M) {
+  for (auto& r : M->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      M->prof_ms[r.kc] += ms;
+      M->prof_n[r.kc] += 1;
+    }
+    M->pool.push_back(r.a);
+    M->pool.push_back(r.b);
+  }
+  M->pending.clear();
+}
+
+// Synchronise the stream, gather profiling, translate device flags to a status.
+int finish(dg_mesh* M, bool check_solver) {
+  CK(cudaStreamSynchronize(M->stream));
+  collect_profile(M);
+  if (!check_solver) return DG_OK;
+  CK(cudaMemcpy(M->host_stats, M->dm.stats, sizeof(dgdf::DevStats), cudaMemcpyDeviceToHost));
+  const int fl = M->host_stats->flags;
+  if (fl & dgdf::kFlagBarrierTimeout) return fail(DG_ERR_CUDA, "solver grid barrier timed out");
+  if (fl & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
+  if (fl & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached cg_maxit");
+  return DG_OK;
+}
+
+int reset_flags(dg_mesh* M) {
+  CK(cudaMemsetAsync(&M->dm.stats->flags, 0, sizeof(int), M->stream));
+  return DG_OK;
+}
+
+int solve(dg_mesh* M, double warm_scale, int from_float) {
+  dgdf::SolveArgs a{};
+  a.warm_scale = warm_scale;
+  a.rtol = M->p.cg_rtol;
+  a.maxit = M->p.cg_maxit;
+  a.mixed = M->p.precision == DG_PRECISION_MIXED;
+  a.inner_rtol = 1e-4;
+  a.max_sweeps = 12;
+  a.from_float = from_float;
+  const int nb = M->solver_blocks[a.mixed];
+  return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
+}
+
+int check_mesh(const dg_mesh* M) {
+  if (!M) return fail(DG_ERR_INVALID_ARG, "NULL mesh");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+const char* dg_kernel_name(int i) { return (i >= 0 && i < KC_COUNT) ? kKernelNames[i] : nullptr; }
+
+int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, const dg_params* params,
+                   dg_mesh** out) {
+  g_err.clear();
+  if (!out || !params || !tri_vertex_ids || !tri_coords) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  dg_params p = *params;
+  if (p.k < 1 || p.k > dgdf::kMaxDegree) return fail(DG_ERR_UNSUPPORTED, "k must be 1..3");
+  if (!(p.nu >= 0.0) || !std::isfinite(p.nu)) return fail(DG_ERR_INVALID_ARG, "nu must be finite and >= 0");
+  if (!(p.alpha > 0.0) || !std::isfinite(p.alpha)) return fail(DG_ERR_INVALID_ARG, "alpha must be > 0");
+  if (p.precision != DG_PRECISION_FP64 && p.precision != DG_PRECISION_MIXED)
+    return fail(DG_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+  if (!(p.cg_rtol > 0.0)) p.cg_rtol = 1e-13;
+  if (p.cg_maxit <= 0) p.cg_maxit = 20000;
+  dg_mesh* M = new dg_mesh();
+  M->p = p;
+  M->stream = static_cast<cudaStream_t>(p.cuda_stream);
+  std::string err;
+  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, p.k, p.alpha, M->hm, err);
+  if (rc) {
+    delete M;
+    return fail(rc, err);
+  }
+  auto cleanup = [&](int code) {
+    dg_mesh_destroy(M);
+    return code;
+  };
+  const dgdf::HostMesh& hm = M->hm;
+  const dgdf::RefTables& ref = hm.ref;
+  dgdf::DevMesh& d = M->dm;
+  d.k = hm.k;
+  d.ns = hm.ns;
+  d.nd = hm.nd;
+  d.nw = hm.nw;
+  d.nl = hm.nl;
+  d.nq = ref.nq;
+  d.nqf = ref.nqf;
+  d.n_tri = int(hm.topo.n_tri);
+  d.n_facet = int(hm.topo.n_facet);
+  d.n_class = int(hm.classes.size());
+  d.n_stencil = hm.n_stencil;
+  d.nu = p.nu;
+  d.area_total = hm.area_total;
+  const int nd = hm.nd, nw = hm.nw, nl = hm.nl, L3 = 3 * nl;
+  // class data
+  std::vector<double> geo(size_t(d.n_class) * dgdf::kGeo, 0.0), P, G, W, WC;
+  for (int c = 0; c < d.n_class; ++c) {
+    const dgdf::ClassOps& co = hm.classes[c];
+    double* g = &geo[size_t(c) * dgdf::kGeo];
+    for (int i = 0; i < 4; ++i) g[dgdf::G_JINV + i] = co.Jinv[i];
+    g[dgdf::G_DET] = co.det;
+    g[dgdf::G_S] = 1.0 / std::sqrt(co.det);
+    for (int e = 0; e < 3; ++e) {
+      g[dgdf::G_NRM + 2 * e] = co.normal[e][0];
+      g[dgdf::G_NRM + 2 * e + 1] = co.normal[e][1];
+      g[dgdf::G_FLEN + e] = co.flen[e];
+    }
+    // integral over T of the first (constant) basis function, and 1 / its value
+    double psi0 = ref.vphi[0];
+    double s = 1.0 / std::sqrt(co.det);
+    g[dgdf::G_ZINT0] = co.det * 0.5 * psi0 * s;   // psi0 constant; reference area 1/2
+    g[dgdf::G_CINV0] = 1.0 / (psi0 * s);
+    P.insert(P.end(), co.P.begin(), co.P.end());
+    G.insert(G.end(), co.G.begin(), co.G.end());
+    W.insert(W.end(), co.W.begin(), co.W.end());
+    WC.insert(WC.end(), co.WCt.begin(), co.WCt.end());
+  }
+  if ((rc = upload(M, &d.vw, ref.vw)) || (rc = upload(M, &d.vphi, ref.vphi)) || (rc = upload(M, &d.vdphi, ref.vdphi)) ||
+      (rc = upload(M, &d.fw, ref.fw)) || (rc = upload(M, &d.fphi, ref.fphi)) || (rc = upload(M, &d.fdphi, ref.fdphi)) ||
+      (rc = upload(M, &d.lat_inv, ref.lat_inv)) || (rc = upload(M, &d.lat_phi, ref.lat_phi)) ||
+      (rc = upload(M, &d.plat_phi, ref.plat_phi)) || (rc = upload(M, &d.mu_lat, ref.mu_lat)) ||
+      (rc = upload(M, &d.geo, geo)) || (rc = upload(M, &d.P, P)) || (rc = upload(M, &d.G, G)) ||
+      (rc = upload(M, &d.W, W)) || (rc = upload(M, &d.WCt, WC)) || (rc = upload(M, &d.Pf, to_float(P))) ||
+      (rc = upload(M, &d.Gf, to_float(G))) || (rc = upload(M, &d.tri_class, hm.tri_class)) ||
+      (rc = upload(M, &d.tri_nbr, hm.tri_nbr)) || (rc = upload(M, &d.tri_facet, hm.topo.tri_facet)) ||
+      (rc = upload(M, &d.tri_nbr_loc, hm.tri_nbr_loc)) || (rc = upload(M, &d.tri_orient, hm.topo.tri_orient)) ||
+      (rc = upload(M, &d.facet_sigma, hm.facet_sigma)) || (rc = upload(M, &d.facet_nbr, hm.facet_nbr)) ||
+      (rc = upload(M, &d.facet_stencil, hm.facet_stencil)) || (rc = upload(M, &d.facet_tri, hm.topo.facet_tri)) ||
+      (rc = upload(M, &d.facet_loc, hm.topo.facet_loc)) || (rc = upload(M, &d.st_blk, hm.stencil_blocks)) ||
+      (rc = upload(M, &d.st_binv, hm.stencil_binv)) || (rc = upload(M, &d.st_blk_f, to_float(hm.stencil_blocks))) ||
+      (rc = upload(M, &d.st_binv_f, to_float(hm.stencil_binv))))
+    return cleanup(rc);
+  const size_t nT = size_t(d.n_tri), nF = size_t(d.n_facet);
+  const size_t nred = std::max<size_t>(size_t(dgdf::kRedSlots) * dgdf::kMaxSolverBlocks, nT / 128 + 2);
+  if ((rc = dalloc(M, &d.u, nT * nd)) || (rc = dalloc(M, &d.ustage, nT * nd)) || (rc = dalloc(M, &d.h, nT * nd)) ||
+      (rc = dalloc(M, &d.gl, nT * L3)) || (rc = dalloc(M, &d.hf, nT * nd)) || (rc = dalloc(M, &d.glf, nT * L3)) ||
+      (rc = dalloc(M, &d.lam, nF * nl)) || (rc = dalloc(M, &d.g, nF * nl)) || (rc = dalloc(M, &d.r, nF * nl)) ||
+      (rc = dalloc(M, &d.z, nF * nl)) || (rc = dalloc(M, &d.pa, nF * nl)) || (rc = dalloc(M, &d.pb, nF * nl)) ||
+      (rc = dalloc(M, &d.q, nF * nl)) || (rc = dalloc(M, &d.rf, nF * nl)) || (rc = dalloc(M, &d.zf, nF * nl)) ||
+      (rc = dalloc(M, &d.paf, nF * nl)) || (rc = dalloc(M, &d.pbf, nF * nl)) || (rc = dalloc(M, &d.qf, nF * nl)) ||
+      (rc = dalloc(M, &d.xf, nF * nl)) || (rc = dalloc(M, &d.red, nred)) || (rc = dalloc(M, &d.bar, 1)) ||
+      (rc = dalloc(M, &d.stats, 1)) || (rc = dalloc(M, &d.diag, 8)) ||
+      (rc = dalloc(M, &M->lattice, nT * hm.ns * 2)) || (rc = dalloc(M, &M->wbuf, nT * nw)) ||
+      (rc = dalloc(M, &M->pe, nT * nw)) || (rc = dalloc(M, &M->pfac, nF * nl)) || (rc = dalloc(M, &M->dflag, 1)))
+    return cleanup(rc);
+  cudaError_t e = cudaMallocHost(&M->host_stats, sizeof(dgdf::DevStats));
+  if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e)));
+  e = cudaMemsetAsync(d.u, 0, nT * nd * sizeof(double), M->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.lam, 0, nF * nl * sizeof(double), M->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.stats, 0, sizeof(dgdf::DevStats), M->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+  if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
+  M->solver_blocks[0] = dgdf::solver_max_blocks(d, 0);
+  M->solver_blocks[1] = dgdf::solver_max_blocks(d, 1);
+  *out = M;
+  return DG_OK;
+}
+
+int dg_mesh_destroy(dg_mesh* M) {
+  if (!M) return DG_OK;
+  cudaStreamSynchronize(M->stream);
+  for (void* p : M->allocs) cudaFree(p);
+  for (auto& r : M->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : M->pool) cudaEventDestroy(e);
+  if (M->host_stats) cudaFreeHost(M->host_stats);
+  delete M;
+  return DG_OK;
+}
+
+int dg_mesh_info(const dg_mesh* M, int64_t out[8]) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!out) return fail(DG_ERR_INVALID_ARG, "NULL out");
+  out[0] = M->hm.topo.n_tri;
+  out[1] = M->hm.topo.n_facet;
+  out[2] = M->hm.k;
+  out[3] = M->hm.ns;
+  out[4] = int64_t(M->hm.classes.size());
+  out[5] = M->hm.n_stencil;
+  out[6] = M->hm.topo.n_tri * M->hm.nd;
+  out[7] = M->hm.topo.n_facet * M->hm.nl;
+  return DG_OK;
+}
+
+int dg_set_velocity(dg_mesh* M, const double* vals, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!vals) return fail(DG_ERR_INVALID_ARG, "NULL vals");
+  const size_t n = size_t(M->dm.n_tri) * M->hm.ns * 2;
+  CK(cudaMemcpyAsync(M->lattice, vals, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     M->stream));
+  CK(cudaMemsetAsync(M->dflag, 0, sizeof(int), M->stream));
+  int rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_check_finite(M->lattice, (long long)n, M->dflag, M->stream); });
+  if (rc) return rc;
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, M->dflag, sizeof(int), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  if (flag) return fail(DG_ERR_NONFINITE, "non-finite velocity value");
+  rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_lattice_to_coef(M->dm, M->lattice, M->dm.u, M->stream); });
+  if (rc) return rc;
+  M->has_lam = false;
+  return finish(M, false);
+}
+
+int dg_get_velocity(dg_mesh* M, double* vals, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!vals) return fail(DG_ERR_INVALID_ARG, "NULL vals");
+  const size_t n = size_t(M->dm.n_tri) * M->hm.ns * 2;
+  int rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_coef_to_lattice(M->dm, M->dm.u, M->lattice, M->stream); });
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(vals, M->lattice, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     M->stream));
+  return finish(M, false);
+}
+
+int dg_project_divfree(dg_mesh* M) {
+  if (int rc = check_mesh(M)) return rc;
+  int rc = reset_flags(M);
+  if (rc) return rc;
+  dgdf::StageArgs a{};
+  a.mode = dgdf::MODE_PROJECT;
+  a.up = M->dm.u;
+  a.un = M->dm.u;
+  if ((rc = launch(M, KC_PROJECT_RHS, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
+  if ((rc = solve(M, 0.0, 0))) return rc;
+  if ((rc = launch(M, KC_RECOVER,
+                   [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->dm.u, M->dm.u, 0.0, 0.0, 0, M->stream); })))
+    return rc;
+  M->has_lam = false;
+  return finish(M, true);
+}
+
+int dg_rk3_step(dg_mesh* M, double dt, int64_t nsteps) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  int rc = reset_flags(M);
+  if (rc) return rc;
+  static const double kA[3] = {0.0, 0.75, 1.0 / 3.0}, kB[3] = {1.0, 0.25, 2.0 / 3.0};
+  dgdf::DevMesh& d = M->dm;
+  const bool mixed = M->p.precision == DG_PRECISION_MIXED;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    for (int s = 0; s < 3; ++s) {
+      const double a = kA[s], b = kB[s];
+      const double* up = (s == 0) ? d.u : d.ustage;
+      double* out = (s == 2) ? d.u : d.ustage;
+      dgdf::StageArgs sa{};
+      sa.mode = mixed ? dgdf::MODE_INCREMENT : dgdf::MODE_STAGE;
+      sa.a = a;
+      sa.b = b;
+      sa.dt = dt;
+      sa.un = d.u;
+      sa.up = up;
+      if ((rc = launch(M, mixed ? KC_INCREMENT : KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); })))
+        return rc;
+      const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
+      if ((rc = solve(M, warm, mixed ? 1 : 0))) return rc;
+      if ((rc = launch(M, KC_RECOVER,
+                       [&] { return dgdf::launch_recover(d, out, d.u, up, a, b, mixed ? 1 : 0, M->stream); })))
+        return rc;
+      M->last_bdt = b * dt;
+      M->has_lam = true;
+    }
+  }
+  return finish(M, true);
+}
+
+int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!p_elem) return fail(DG_ERR_INVALID_ARG, "NULL p_elem");
+  int rc = reset_flags(M);
+  if (rc) return rc;
+  dgdf::StageArgs a{};
+  a.mode = dgdf::MODE_PRESSURE;
+  a.up = M->dm.u;
+  a.un = M->dm.u;
+  if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
+  if ((rc = solve(M, 0.0, 0))) return rc;
+  if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_pressure(M->dm, M->wbuf, M->stream); }))) return rc;
+  if ((rc = launch(M, KC_PRESSURE, [&] {
+         return dgdf::launch_pressure_lattice(M->dm, M->wbuf, M->pe, p_facet ? M->pfac : nullptr, M->stream);
+       })))
+    return rc;
+  M->has_lam = false;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(p_elem, M->pe, size_t(M->dm.n_tri) * M->hm.nw * sizeof(double), kind, M->stream));
+  if (p_facet)
+    CK(cudaMemcpyAsync(p_facet, M->pfac, size_t(M->dm.n_facet) * M->hm.nl * sizeof(double), kind, M->stream));
+  return finish(M, true);
+}
+
+int dg_eval_residual(dg_mesh* M, double* vals, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!vals) return fail(DG_ERR_INVALID_ARG, "NULL vals");
+  dgdf::StageArgs a{};
+  a.mode = dgdf::MODE_RESIDUAL;
+  a.up = M->dm.u;
+  a.un = M->dm.u;
+  int rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); });
+  if (rc) return rc;
+  if ((rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_coef_to_lattice(M->dm, M->dm.h, M->lattice, M->stream); })))
+    return rc;
+  const size_t n = size_t(M->dm.n_tri) * M->hm.ns * 2;
+  CK(cudaMemcpyAsync(vals, M->lattice, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     M->stream));
+  return finish(M, false);
+}
+
+int dg_get_diagnostics(dg_mesh* M, double out[8]) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!out) return fail(DG_ERR_INVALID_ARG, "NULL out");
+  int rc = launch(M, KC_DIAG, [&] { return dgdf::launch_diagnostics(M->dm, M->dm.u, M->stream); });
+  if (rc) return rc;
+  double d4[4];
+  CK(cudaMemcpyAsync(d4, M->dm.diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaMemcpyAsync(M->host_stats, M->dm.stats, sizeof(dgdf::DevStats), cudaMemcpyDeviceToHost, M->stream));
+  if ((rc = finish(M, false))) return rc;
+  for (int i = 0; i < 4; ++i) out[i] = d4[i];
+  out[4] = M->host_stats->last_iters;
+  out[5] = double(M->host_stats->total_iters);
+  out[6] = double(M->host_stats->solves);
+  out[7] = M->host_stats->last_relres;
+  return DG_OK;
+}
+
+int dg_profile(dg_mesh* M, int enable, double* out_ms, int64_t* out_launches, int n) {
+  if (int rc = check_mesh(M)) return rc;
+  CK(cudaStreamSynchronize(M->stream));
+  collect_profile(M);
+  if (enable == 2) {
+    for (int i = 0; i < KC_COUNT; ++i) {
+      M->prof_ms[i] = 0.0;
+      M->prof_n[i] = 0;
+    }
+  } else if (enable == 0 || enable == 1) {
+    M->prof = enable == 1;
+  } else {
+    return fail(DG_ERR_INVALID_ARG, "enable must be 0, 1 or 2");
+  }
+  for (int i = 0; i < n && i < KC_COUNT; ++i) {
+    if (out_ms) out_ms[i] = M->prof_ms[i];
+    if (out_launches) out_launches[i] = M->prof_n[i];
+  }
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Device-side data of one mesh and the launch interface between api.cu and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dgdf {
+
+// Error bits the kernels set in DevStats::flags.
+enum : int {
+  kFlagNotConverged = 1,
+  kFlagNonFinite = 2,
+  kFlagBarrierTimeout = 4,
+};
+
+// Per-class geometry record (doubles): Jinv[4] row-major (d xi_r / d x_d),
+// det = 2|T|, s = 1/sqrt(det), normal[3][2], flen[3], zint0 = integral of the
+// constant basis function, cinv0 = coefficient of the constant 1 in the first
+// basis function's scale; padded to 20.
+constexpr int kGeo = 20;
+enum GeoSlot { G_JINV = 0, G_DET = 4, G_S = 5, G_NRM = 6, G_FLEN = 12, G_ZINT0 = 15, G_CINV0 = 16 };
+
+struct DevStats {
+  int flags;
+  int last_iters;
+  long long total_iters;
+  long long solves;
+  double last_relres;
+  int last_sweeps;
+  int pad;
+};
+
+// Grid-barrier state for the persistent solver kernel.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+struct DevMesh {
+  int k, ns, nd, nw, nl, nq, nqf;
+  int n_tri, n_facet, n_class, n_stencil;
+  double nu;
+  double area_total;
+  // reference tables
+  const double *vw, *vphi, *vdphi, *fw, *fphi, *fdphi;
+  const double *lat_inv, *lat_phi, *plat_phi, *mu_lat;
+  // element classes
+  const double *geo;     // [n_class][kGeo]
+  const double *P, *G, *W, *WCt;     // [n_class][...]
+  const float *Pf, *Gf;              // FP32 copies
+  const int32_t *tri_class, *tri_nbr, *tri_facet;
+  const int8_t *tri_nbr_loc, *tri_orient;
+  const double *facet_sigma;
+  // facet-system stencil
+  const int32_t *facet_nbr, *facet_stencil, *facet_tri;
+  const int8_t *facet_loc;
+  const double *st_blk, *st_binv;     // [n_stencil][5][nl][nl], [n_stencil][nl][nl]
+  const float *st_blk_f, *st_binv_f;
+  // state and work arrays
+  double *u, *ustage, *h, *gl;        // [n_tri][nd] x3, [n_tri][3 nl]
+  float *hf, *glf;                    // FP32 stage increment and its condensation
+  double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
+  float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
+  double *red;                        // reduction scratch [kRedSlots][max_blocks]
+  GridBar *bar;
+  DevStats *stats;
+  double *diag;                       // [8] diagnostics output
+};
+
+constexpr int kRedSlots = 8;
+constexpr int kMaxSolverBlocks = 2048;
+
+// Stage kernel modes.
+enum StageMode : int {
+  MODE_STAGE = 0,      // f = a u^n + b (u' + dt L(u')), h = P f, gl = G f          (FP64 form)
+  MODE_RESIDUAL = 1,   // h = L(u') (Riesz representer, no solve)
+  MODE_PRESSURE = 2,   // h = f = L(u'), gl = G f
+  MODE_PROJECT = 3,    // f = u', h = P f, gl = G f
+  MODE_INCREMENT = 4,  // FP32: hf = P (b dt L(u')), glf = G (b dt L(u'))        (mixed form)
+};
+
+struct StageArgs {
+  int mode;
+  double a, b, dt;
+  const double* un;    // u^n
+  const double* up;    // u'
+};
+
+struct SolveArgs {
+  double warm_scale;   // lam0 = warm_scale * lam (0: cold start)
+  double rtol;
+  int maxit;
+  int mixed;           // 1: FP32 PCG inside FP64 refinement
+  double inner_rtol;   // relative tolerance of each inner FP32 solve
+  int max_sweeps;
+  int from_float;      // 1: assemble g from glf (FP32 stage increment)
+};
+
+// Launchers (k dispatched at run time). Return the launch error.
+cudaError_t launch_lattice_to_coef(const DevMesh& m, const double* vals, double* coef, cudaStream_t s);
+cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double* vals, cudaStream_t s);
+cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_recover(const DevMesh& m, double* out, const double* un, const double* up, double a, double b,
+                           int from_float, cudaStream_t s);
+cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
+cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
+cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);
+cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
+cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
+int solver_max_blocks(const DevMesh& m, int mixed);
+
+}  // namespace dgdf

@@ -1,0 +1,60 @@
+// Host-only introspection entry points (include/dgdf_host.h): the set-up of
+// setup.cpp without any device, for checks on machines without a GPU.
+#include <cstring>
+#include <string>
+
+#include "../../include/dgdf.h"
+#include "../../include/dgdf_host.h"
+#include "setup.hpp"
+
+extern "C" {
+
+int dg_host_topology(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int64_t* n_facet,
+                     int32_t* tri_facet, int8_t* tri_orient, int32_t* facet_tri) {
+  if (!n_facet) return DG_ERR_INVALID_ARG;
+  dgdf::Topology topo;
+  std::string err;
+  int rc = dgdf::build_topology(n_tri, tri_vertex_ids, tri_coords, topo, err);
+  if (rc) return rc;
+  *n_facet = topo.n_facet;
+  if (tri_facet) std::memcpy(tri_facet, topo.tri_facet.data(), topo.tri_facet.size() * sizeof(int32_t));
+  if (tri_orient) std::memcpy(tri_orient, topo.tri_orient.data(), topo.tri_orient.size() * sizeof(int8_t));
+  if (facet_tri) std::memcpy(facet_tri, topo.facet_tri.data(), topo.facet_tri.size() * sizeof(int32_t));
+  return DG_OK;
+}
+
+int dg_host_reference(int k, int table, double* out, int64_t cap, int64_t* n_out) {
+  if (!n_out) return DG_ERR_INVALID_ARG;
+  dgdf::RefTables ref;
+  std::string err;
+  int rc = dgdf::build_reference(k, ref, err);
+  if (rc) return rc;
+  std::vector<double> v;
+  switch (table) {
+    case 0:
+      for (int q = 0; q < ref.nq; ++q) {
+        v.push_back(ref.vxi[2 * q]);
+        v.push_back(ref.vxi[2 * q + 1]);
+        v.push_back(ref.vw[q]);
+      }
+      break;
+    case 1:
+      for (int q = 0; q < ref.nqf; ++q) {
+        v.push_back(ref.ft[q]);
+        v.push_back(ref.fw[q]);
+      }
+      break;
+    case 2: v = ref.vphi; break;
+    case 3: v = ref.vdphi; break;
+    case 4: v = ref.lat_phi; break;
+    default: return DG_ERR_INVALID_ARG;
+  }
+  *n_out = int64_t(v.size());
+  if (out) {
+    if (cap < int64_t(v.size())) return DG_ERR_INVALID_ARG;
+    std::memcpy(out, v.data(), v.size() * sizeof(double));
+  }
+  return DG_OK;
+}
+
+}  // extern "C"

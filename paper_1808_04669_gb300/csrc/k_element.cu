@@ -1,0 +1,553 @@
+// Element kernels: stage residual + condensation (K1-K3), recovery (K5), pressure,
+// lattice conversion and diagnostics. One thread per triangle; the reference
+// tables sit in shared memory and are read as warp broadcasts.
+#include "device.cuh"
+#include "kcommon.cuh"
+
+namespace dgdf {
+
+// Reference tables staged in shared memory in precision R.
+template <int K, typename R>
+struct SmemTables {
+  using D = Dims<K>;
+  R vw[D::NQ];
+  R vphi[D::NQ][D::NS];
+  R vdphi[D::NQ][D::NS][2];
+  R fw[D::NQF];
+  R fphi[3][D::NQF][D::NS];
+  R fdphi[3][D::NQF][D::NS][2];
+};
+
+template <int K, typename R>
+__device__ void load_tables(const DevMesh& m, SmemTables<K, R>& T) {
+  using D = Dims<K>;
+  for (int i = threadIdx.x; i < D::NQ; i += blockDim.x) T.vw[i] = R(m.vw[i]);
+  for (int i = threadIdx.x; i < D::NQ * D::NS; i += blockDim.x) (&T.vphi[0][0])[i] = R(m.vphi[i]);
+  for (int i = threadIdx.x; i < D::NQ * D::NS * 2; i += blockDim.x) (&T.vdphi[0][0][0])[i] = R(m.vdphi[i]);
+  for (int i = threadIdx.x; i < D::NQF; i += blockDim.x) T.fw[i] = R(m.fw[i]);
+  for (int i = threadIdx.x; i < 3 * D::NQF * D::NS; i += blockDim.x) (&T.fphi[0][0][0])[i] = R(m.fphi[i]);
+  for (int i = threadIdx.x; i < 3 * D::NQF * D::NS * 2; i += blockDim.x) (&T.fdphi[0][0][0][0])[i] = R(m.fdphi[i]);
+}
+
+// acc[i] = L(u)(phi_i) on triangle t: -C_h(u;u,phi_i) - B_h(u,phi_i) (eq. (7), eq. (18)).
+// Volume: int (u x u - nu grad u) : grad phi. Facets: the upwind flux with u.n the
+// average of both traces, and the SIPG consistency, symmetry and penalty terms,
+// at the facet Gauss points (the neighbour traverses the facet the other way,
+// so its point q is our point NQF-1-q). ug is the global coefficient array of u.
+template <int K, typename R>
+__device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, int t, const double* __restrict__ ug,
+                                 const R (&up)[Dims<K>::ND], R (&acc)[Dims<K>::ND]) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS;
+  const R nu = R(m.nu);
+  const double* geo = m.geo + size_t(m.tri_class[t]) * kGeo;
+  const R Ji[4] = {R(geo[G_JINV + 0]), R(geo[G_JINV + 1]), R(geo[G_JINV + 2]), R(geo[G_JINV + 3])};
+  const R det = R(geo[G_DET]), s = R(geo[G_S]);
+#pragma unroll
+  for (int i = 0; i < D::ND; ++i) acc[i] = R(0);
+  // ---- volume terms
+#pragma unroll 1
+  for (int q = 0; q < D::NQ; ++q) {
+    R u0 = 0, u1 = 0, a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const R ph = T.vphi[q][j], d0 = T.vdphi[q][j][0], d1 = T.vdphi[q][j][1];
+      u0 += ph * up[j];
+      u1 += ph * up[NS + j];
+      a00 += d0 * up[j];
+      a01 += d1 * up[j];
+      a10 += d0 * up[NS + j];
+      a11 += d1 * up[NS + j];
+    }
+    u0 *= s;
+    u1 *= s;
+    // physical gradient du_c/dx_d = s sum_r a_cr Jinv[r][d]
+    const R g00 = s * (a00 * Ji[0] + a01 * Ji[2]), g01 = s * (a00 * Ji[1] + a01 * Ji[3]);
+    const R g10 = s * (a10 * Ji[0] + a11 * Ji[2]), g11 = s * (a10 * Ji[1] + a11 * Ji[3]);
+    const R F00 = u0 * u0 - nu * g00, F01 = u0 * u1 - nu * g01;
+    const R F10 = u1 * u0 - nu * g10, F11 = u1 * u1 - nu * g11;
+    const R w = T.vw[q] * det * s;
+    // H_cr = sum_d F_cd Jinv[r][d]
+    const R H00 = w * (F00 * Ji[0] + F01 * Ji[1]), H01 = w * (F00 * Ji[2] + F01 * Ji[3]);
+    const R H10 = w * (F10 * Ji[0] + F11 * Ji[1]), H11 = w * (F10 * Ji[2] + F11 * Ji[3]);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const R d0 = T.vdphi[q][j][0], d1 = T.vdphi[q][j][1];
+      acc[j] += H00 * d0 + H01 * d1;
+      acc[NS + j] += H10 * d0 + H11 * d1;
+    }
+  }
+  // ---- facet terms
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int tn = m.tri_nbr[size_t(t) * 3 + e];
+    const int en = m.tri_nbr_loc[size_t(t) * 3 + e];
+    const double* geon = m.geo + size_t(m.tri_class[tn]) * kGeo;
+    const R sn = R(geon[G_S]);
+    const R n0 = R(geo[G_NRM + 2 * e]), n1 = R(geo[G_NRM + 2 * e + 1]);
+    const R len = R(geo[G_FLEN + e]);
+    const R sig = R(m.facet_sigma[m.tri_facet[size_t(t) * 3 + e]]);
+    // normal derivative in reference gradients: d_n psi = s sum_r d_r psihat (Jinv n)_r
+    const R mo0 = Ji[0] * n0 + Ji[1] * n1, mo1 = Ji[2] * n0 + Ji[3] * n1;
+    const R mn0 = R(geon[G_JINV + 0]) * n0 + R(geon[G_JINV + 1]) * n1;
+    const R mn1 = R(geon[G_JINV + 2]) * n0 + R(geon[G_JINV + 3]) * n1;
+    R un[D::ND];
+    load_coef<D::ND>(ug + size_t(tn) * D::ND, un);
+#pragma unroll 1
+    for (int q = 0; q < D::NQF; ++q) {
+      const int qn = D::NQF - 1 - q;
+      R ui0 = 0, ui1 = 0, di0 = 0, di1 = 0, uo0 = 0, uo1 = 0, do0 = 0, do1 = 0;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const R ph = T.fphi[e][q][j];
+        const R dn = T.fdphi[e][q][j][0] * mo0 + T.fdphi[e][q][j][1] * mo1;
+        ui0 += ph * up[j];
+        ui1 += ph * up[NS + j];
+        di0 += dn * up[j];
+        di1 += dn * up[NS + j];
+        const R phn = T.fphi[en][qn][j];
+        const R dnn = T.fdphi[en][qn][j][0] * mn0 + T.fdphi[en][qn][j][1] * mn1;
+        uo0 += phn * un[j];
+        uo1 += phn * un[NS + j];
+        do0 += dnn * un[j];
+        do1 += dnn * un[NS + j];
+      }
+      ui0 *= s;
+      ui1 *= s;
+      di0 *= s;
+      di1 *= s;
+      uo0 *= sn;
+      uo1 *= sn;
+      do0 *= sn;
+      do1 *= sn;
+      const R vn = R(0.5) * ((ui0 + uo0) * n0 + (ui1 + uo1) * n1);
+      const R w0 = vn >= R(0) ? ui0 : uo0, w1 = vn >= R(0) ? ui1 : uo1;
+      const R j0 = ui0 - uo0, j1 = ui1 - uo1;
+      const R w = T.fw[q] * len * s;
+      const R A0 = w * (-vn * w0 + nu * R(0.5) * (di0 + do0) - nu * sig * j0);
+      const R A1 = w * (-vn * w1 + nu * R(0.5) * (di1 + do1) - nu * sig * j1);
+      const R B0 = w * R(0.5) * nu * j0, B1 = w * R(0.5) * nu * j1;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const R ph = T.fphi[e][q][j];
+        const R dn = T.fdphi[e][q][j][0] * mo0 + T.fdphi[e][q][j][1] * mo1;
+        acc[j] += A0 * ph + B0 * dn;
+        acc[NS + j] += A1 * ph + B1 * dn;
+      }
+    }
+  }
+}
+
+// Stage kernel. Modes (StageMode): the FP64 stage functional and its
+// condensation (h = P f, gl = G f), the residual alone, the pressure functional,
+// the projection functional, or the FP32 stage increment b dt L(u').
+template <int K, typename R>
+__global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
+  using D = Dims<K>;
+  constexpr int ND = D::ND, L3 = 3 * D::NL;
+  __shared__ SmemTables<K, R> T;
+  load_tables<K, R>(m, T);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_tri) return;
+  R up[ND];
+  load_coef<ND>(a.up + size_t(t) * ND, up);
+  R f[ND];
+  if (a.mode == MODE_PROJECT) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) f[i] = up[i];
+  } else {
+    element_residual<K, R>(m, T, t, a.up, up, f);
+    if (a.mode == MODE_STAGE) {
+      R un[ND];
+      load_coef<ND>(a.un + size_t(t) * ND, un);
+      const R ca = R(a.a), cb = R(a.b), dt = R(a.dt);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) f[i] = ca * un[i] + cb * (up[i] + dt * f[i]);
+    } else if (a.mode == MODE_INCREMENT) {
+      const R sc = R(a.b * a.dt);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) f[i] *= sc;
+    }
+  }
+  const int c = m.tri_class[t];
+  if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = double(f[i]);
+  }
+  if (a.mode == MODE_RESIDUAL) return;
+  if (a.mode == MODE_INCREMENT) {
+    const float* P = m.Pf + size_t(c) * ND * ND;
+    const float* G = m.Gf + size_t(c) * L3 * ND;
+    for (int i = 0; i < ND; ++i) {
+      float v = 0.f;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * float(f[j]);
+      m.hf[size_t(t) * ND + i] = v;
+    }
+    for (int i = 0; i < L3; ++i) {
+      float v = 0.f;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) v += G[i * ND + j] * float(f[j]);
+      m.glf[size_t(t) * L3 + i] = v;
+    }
+    return;
+  }
+  const double* P = m.P + size_t(c) * ND * ND;
+  const double* G = m.G + size_t(c) * L3 * ND;
+  if (a.mode != MODE_PRESSURE) {
+    for (int i = 0; i < ND; ++i) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * double(f[j]);
+      m.h[size_t(t) * ND + i] = v;
+    }
+  }
+  for (int i = 0; i < L3; ++i) {
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) v += G[i * ND + j] * double(f[j]);
+    m.gl[size_t(t) * L3 + i] = v;
+  }
+}
+
+// Recovery (eq. (12) eliminated locally): u_T = P_T f_T - G_T^T lam_T, with
+// lam_T the multipliers of T's three facets mapped to T's own orientation.
+// from_float: u_T = a u^n + b u' + (hf_T - Gf_T^T lam_T) (mixed form).
+template <int K>
+__global__ void __launch_bounds__(128) k_recover(DevMesh m, double* out, const double* un, const double* up,
+                                                 double ca, double cb, int from_float) {
+  using D = Dims<K>;
+  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_tri) return;
+  double lam[L3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int f = m.tri_facet[size_t(t) * 3 + e];
+    const bool flip = m.tri_orient[size_t(t) * 3 + e] < 0;
+#pragma unroll
+    for (int mm = 0; mm < NL; ++mm) {
+      const double v = m.lam[size_t(f) * NL + mm];
+      lam[e * NL + mm] = (flip && (mm & 1)) ? -v : v;
+    }
+  }
+  const int c = m.tri_class[t];
+  if (!from_float) {
+    const double* G = m.G + size_t(c) * L3 * ND;
+#pragma unroll 4
+    for (int i = 0; i < ND; ++i) {
+      double v = m.h[size_t(t) * ND + i];
+#pragma unroll
+      for (int l = 0; l < L3; ++l) v -= G[l * ND + i] * lam[l];
+      out[size_t(t) * ND + i] = v;
+    }
+  } else {
+    const float* G = m.Gf + size_t(c) * L3 * ND;
+    float lf[L3];
+#pragma unroll
+    for (int l = 0; l < L3; ++l) lf[l] = float(lam[l]);
+#pragma unroll 4
+    for (int i = 0; i < ND; ++i) {
+      float v = m.hf[size_t(t) * ND + i];
+#pragma unroll
+      for (int l = 0; l < L3; ++l) v -= G[l * ND + i] * lf[l];
+      const size_t o = size_t(t) * ND + i;
+      out[o] = ca * un[o] + cb * up[o] + double(v);
+    }
+  }
+}
+
+// Element pressure w_T = W_T f_T - (W C^T)_T lam_T; block partial sums of the
+// integral of w for the L^2_0 shift go to red[0][block].
+template <int K>
+__global__ void __launch_bounds__(128) k_pressure(DevMesh m, double* w) {
+  using D = Dims<K>;
+  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL, NW = D::NW;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double integral = 0.0;
+  if (t < m.n_tri) {
+    double lam[L3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int f = m.tri_facet[size_t(t) * 3 + e];
+      const bool flip = m.tri_orient[size_t(t) * 3 + e] < 0;
+#pragma unroll
+      for (int mm = 0; mm < NL; ++mm) {
+        const double v = m.lam[size_t(f) * NL + mm];
+        lam[e * NL + mm] = (flip && (mm & 1)) ? -v : v;
+      }
+    }
+    const int c = m.tri_class[t];
+    const double* W = m.W + size_t(c) * NW * ND;
+    const double* WC = m.WCt + size_t(c) * NW * L3;
+    for (int i = 0; i < NW; ++i) {
+      double v = 0.0;
+      for (int j = 0; j < ND; ++j) v += W[i * ND + j] * m.h[size_t(t) * ND + j];
+      for (int l = 0; l < L3; ++l) v -= WC[i * L3 + l] * lam[l];
+      w[size_t(t) * NW + i] = v;
+    }
+    integral = w[size_t(t) * NW] * m.geo[size_t(c) * kGeo + G_ZINT0];
+  }
+  integral = block_sum(integral);
+  if (threadIdx.x == 0) m.red[blockIdx.x] = integral;
+}
+
+// Lattice output of the shifted pressure: c = (integral of w) / |Omega| from the
+// block partials, w <- w - c, lam <- lam - c (the constant is mode 0 on facets).
+template <int K>
+__global__ void __launch_bounds__(128) k_pressure_lattice(DevMesh m, const double* w, double* pe, double* pf,
+                                                          int nparts) {
+  using D = Dims<K>;
+  constexpr int NW = D::NW, NL = D::NL;
+  __shared__ double cshift;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 32) v += m.red[i];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) cshift = v / m.area_total;
+  }
+  __syncthreads();
+  const double c = cshift;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m.n_tri) {
+    const double* geo = m.geo + size_t(m.tri_class[i]) * kGeo;
+    double wl[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) wl[j] = w[size_t(i) * NW + j];
+    wl[0] -= c * geo[G_CINV0];
+    const double s = geo[G_S];
+#pragma unroll
+    for (int p = 0; p < NW; ++p) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) v += m.plat_phi[p * NW + j] * wl[j];
+      pe[size_t(i) * NW + p] = s * v;
+    }
+  }
+  if (pf && i < m.n_facet) {
+    double lam[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) lam[j] = m.lam[size_t(i) * NL + j];
+    lam[0] -= c;
+#pragma unroll
+    for (int p = 0; p < NL; ++p) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) v += m.mu_lat[p * NL + j] * lam[j];
+      pf[size_t(i) * NL + p] = v;
+    }
+  }
+}
+
+// Lattice values -> orthonormal coefficients: coef = sqrt(det) Vhat^-1 vals per component.
+template <int K>
+__global__ void k_lattice_to_coef(DevMesh m, const double* vals, double* coef) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_tri) return;
+  const double sq = 1.0 / m.geo[size_t(m.tri_class[t]) * kGeo + G_S];
+  double v[NS][2];
+#pragma unroll
+  for (int p = 0; p < NS; ++p) {
+    v[p][0] = vals[(size_t(t) * NS + p) * 2];
+    v[p][1] = vals[(size_t(t) * NS + p) * 2 + 1];
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    double c0 = 0.0, c1 = 0.0;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      c0 += m.lat_inv[j * NS + p] * v[p][0];
+      c1 += m.lat_inv[j * NS + p] * v[p][1];
+    }
+    coef[size_t(t) * 2 * NS + j] = sq * c0;
+    coef[size_t(t) * 2 * NS + NS + j] = sq * c1;
+  }
+}
+
+template <int K>
+__global__ void k_coef_to_lattice(DevMesh m, const double* coef, double* vals) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_tri) return;
+  const double s = m.geo[size_t(m.tri_class[t]) * kGeo + G_S];
+  double c[2 * NS];
+#pragma unroll
+  for (int i = 0; i < 2 * NS; ++i) c[i] = coef[size_t(t) * 2 * NS + i];
+#pragma unroll
+  for (int p = 0; p < NS; ++p) {
+    double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      v0 += m.lat_phi[p * NS + j] * c[j];
+      v1 += m.lat_phi[p * NS + j] * c[NS + j];
+    }
+    vals[(size_t(t) * NS + p) * 2] = s * v0;
+    vals[(size_t(t) * NS + p) * 2 + 1] = s * v1;
+  }
+}
+
+// Diagnostics partials per block: red[0] energy, red[1] enstrophy, red[2] max |div|,
+// red[3] max |[u.n]| (each facet is seen from both sides).
+template <int K>
+__global__ void __launch_bounds__(128) k_diagnostics(DevMesh m, const double* coef) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, ND = D::ND;
+  __shared__ SmemTables<K, double> T;
+  load_tables<K, double>(m, T);
+  __syncthreads();
+  double en = 0.0, ens = 0.0, dmax = 0.0, jmax = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.n_tri; t += gridDim.x * blockDim.x) {
+    double c[ND];
+    load_coef<ND>(coef + size_t(t) * ND, c);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) en += c[i] * c[i];
+    const double* geo = m.geo + size_t(m.tri_class[t]) * kGeo;
+    const double Ji[4] = {geo[0], geo[1], geo[2], geo[3]};
+    const double det = geo[G_DET], s = geo[G_S];
+    for (int q = 0; q < D::NQ; ++q) {
+      double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        a00 += T.vdphi[q][j][0] * c[j];
+        a01 += T.vdphi[q][j][1] * c[j];
+        a10 += T.vdphi[q][j][0] * c[NS + j];
+        a11 += T.vdphi[q][j][1] * c[NS + j];
+      }
+      const double g00 = s * (a00 * Ji[0] + a01 * Ji[2]), g01 = s * (a00 * Ji[1] + a01 * Ji[3]);
+      const double g10 = s * (a10 * Ji[0] + a11 * Ji[2]), g11 = s * (a10 * Ji[1] + a11 * Ji[3]);
+      const double om = g10 - g01;
+      ens += T.vw[q] * det * om * om;
+      dmax = fmax(dmax, fabs(g00 + g11));
+    }
+    for (int e = 0; e < 3; ++e) {
+      const int tn = m.tri_nbr[size_t(t) * 3 + e];
+      const int el = m.tri_nbr_loc[size_t(t) * 3 + e];
+      const double sn = m.geo[size_t(m.tri_class[tn]) * kGeo + G_S];
+      const double n0 = geo[G_NRM + 2 * e], n1 = geo[G_NRM + 2 * e + 1];
+      double cn[ND];
+      load_coef<ND>(coef + size_t(tn) * ND, cn);
+      for (int q = 0; q < D::NQF; ++q) {
+        const int qn = D::NQF - 1 - q;
+        double a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          a0 += T.fphi[e][q][j] * c[j];
+          a1 += T.fphi[e][q][j] * c[NS + j];
+          b0 += T.fphi[el][qn][j] * cn[j];
+          b1 += T.fphi[el][qn][j] * cn[NS + j];
+        }
+        jmax = fmax(jmax, fabs((s * a0 - sn * b0) * n0 + (s * a1 - sn * b1) * n1));
+      }
+    }
+  }
+  en = block_sum(en);
+  ens = block_sum(ens);
+  dmax = block_max(dmax);
+  jmax = block_max(jmax);
+  if (threadIdx.x == 0) {
+    m.red[0 * kMaxSolverBlocks + blockIdx.x] = en;
+    m.red[1 * kMaxSolverBlocks + blockIdx.x] = ens;
+    m.red[2 * kMaxSolverBlocks + blockIdx.x] = dmax;
+    m.red[3 * kMaxSolverBlocks + blockIdx.x] = jmax;
+  }
+}
+
+__global__ void k_diag_finish(DevMesh m, int nparts) {
+  if (threadIdx.x >= 32) return;
+  double a = 0, b = 0, c = 0, d = 0;
+  for (int i = threadIdx.x; i < nparts; i += 32) {
+    a += m.red[0 * kMaxSolverBlocks + i];
+    b += m.red[1 * kMaxSolverBlocks + i];
+    c = fmax(c, m.red[2 * kMaxSolverBlocks + i]);
+    d = fmax(d, m.red[3 * kMaxSolverBlocks + i]);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_max(c);
+  d = warp_max(d);
+  if (threadIdx.x == 0) {
+    m.diag[0] = a;
+    m.diag[1] = b;
+    m.diag[2] = c;
+    m.diag[3] = d;
+  }
+}
+
+__global__ void k_check_finite(const double* v, long long n, int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, kFlagNonFinite);
+}
+
+// ------------------------------------------------------------------- launchers
+namespace {
+inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
+}
+
+#define DGDF_DISPATCH_K(kv, CALL) \
+  switch (kv) {                   \
+    case 1: { constexpr int K = 1; CALL; break; } \
+    case 2: { constexpr int K = 2; CALL; break; } \
+    case 3: { constexpr int K = 3; CALL; break; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t launch_lattice_to_coef(const DevMesh& m, const double* vals, double* coef, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_lattice_to_coef<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, vals, coef)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double* vals, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_coef_to_lattice<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, coef, vals)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
+  if (a.mode == MODE_INCREMENT) {
+    DGDF_DISPATCH_K(m.k, (k_stage<K, float><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
+  } else {
+    DGDF_DISPATCH_K(m.k, (k_stage<K, double><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const DevMesh& m, double* out, const double* un, const double* up, double a, double b,
+                           int from_float, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_recover<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out, un, up, a, b, from_float)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_pressure<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, w)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s) {
+  const int nparts = blocks_for(m.n_tri, 128);
+  const long long n = m.n_tri > m.n_facet ? m.n_tri : m.n_facet;
+  DGDF_DISPATCH_K(m.k, (k_pressure_lattice<K><<<blocks_for(n, 128), 128, 0, s>>>(m, w, pe, pf, nparts)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s) {
+  int nb = blocks_for(m.n_tri, 128);
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  DGDF_DISPATCH_K(m.k, (k_diagnostics<K><<<nb, 128, 0, s>>>(m, coef)));
+  k_diag_finish<<<1, 32, 0, s>>>(m, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s) {
+  long long nb = (n + 255) / 256;
+  if (nb > 1024) nb = 1024;
+  if (nb < 1) nb = 1;
+  k_check_finite<<<int(nb), 256, 0, s>>>(v, n, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace dgdf

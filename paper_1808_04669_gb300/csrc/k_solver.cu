@@ -1,0 +1,388 @@
+// Facet-system solve of the hybrid-mixed scheme (eq. (12) after static
+// condensation; SPD up to the constant multiplier, Sec. 2.4): one persistent
+// cooperative kernel per solve running preconditioned CG with block-Jacobi
+// (one (k+1) x (k+1) block per facet).
+//
+// Matrix-free stencil: row F of S couples F to the other two facets of each
+// adjacent triangle; rows with equal blocks share one stencil class, so on a
+// translation-invariant mesh the operator is a handful of small blocks held in
+// L1 and the SpMV streams only the vectors and 4 neighbour indices per facet.
+//
+// FP64 form: CG in FP64. Mixed form: FP64 iterative refinement
+// (r = g - S lam in FP64) around an inner CG in FP32 on S d = r.
+//
+// Each CG iteration has two grid-wide reductions; the direction update
+// p = z + beta p is fused into the next SpMV (two p buffers), so every
+// iteration costs two grid barriers. Reductions sum block partials in a fixed
+// order, so results are bitwise reproducible for a given launch shape.
+#include "device.cuh"
+#include "kcommon.cuh"
+
+namespace dgdf {
+
+namespace {
+
+constexpr int kSolverThreads = 256;
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 26;
+
+// Grid barrier with a bounded wait. All blocks are co-resident (cooperative
+// launch). Returns false if the wait ran out, after setting kFlagBarrierTimeout.
+__device__ bool grid_sync(GridBar* bar, DevStats* st) {
+  __shared__ int ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int prev = atomicAdd(&bar->count, 1u);
+    int good = 1;
+    if (prev == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicOr(&st->flags, kFlagBarrierTimeout);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Writes up to 3 block partials to red slots, synchronises the grid, and returns
+// the grid sums in every thread (same summation order in every block).
+template <int N>
+__device__ bool grid_reduce(const DevMesh& m, int slot0, double (&v)[N], GridBar* bar) {
+  double s[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) s[i] = block_sum(v[i]);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) m.red[size_t(slot0 + i) * kMaxSolverBlocks + blockIdx.x] = s[i];
+  }
+  if (!grid_sync(bar, m.stats)) return false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) a += __ldcg(&m.red[size_t(slot0 + i) * kMaxSolverBlocks + b]);
+    v[i] = block_sum(a);
+  }
+  return true;
+}
+
+template <int NL, typename R>
+__device__ __forceinline__ void stencil_rows(const R* __restrict__ blk, const R (&x)[5][NL], R (&y)[NL]) {
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    R v = R(0);
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) v += __ldg(&blk[(b * NL + i) * NL + j]) * x[b][j];
+    y[i] = v;
+  }
+}
+
+template <int NL, typename R>
+__device__ __forceinline__ void block_apply(const R* __restrict__ B, const R (&x)[NL], R (&y)[NL]) {
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    R v = R(0);
+#pragma unroll
+    for (int j = 0; j < NL; ++j) v += __ldg(&B[i * NL + j]) * x[j];
+    y[i] = v;
+  }
+}
+
+template <int NL>
+__device__ __forceinline__ void facet_nbrs(const DevMesh& m, int f, int (&nb)[5]) {
+  nb[0] = f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) nb[i + 1] = __ldg(&m.facet_nbr[size_t(f) * 4 + i]);
+}
+
+// y_F = (S x)_F in FP64
+template <int NL>
+__device__ __forceinline__ void spmv64(const DevMesh& m, int f, const double* x, double (&y)[NL]) {
+  int nb[5];
+  facet_nbrs<NL>(m, f, nb);
+  double xs[5][NL];
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+#pragma unroll
+    for (int j = 0; j < NL; ++j) xs[b][j] = __ldcg(&x[size_t(nb[b]) * NL + j]);
+  stencil_rows<NL, double>(m.st_blk + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
+}
+
+// Preconditioned CG on S x = b (precision R) starting from x = 0; b is given
+// through the initial residual already stored in rv. Vectors: x, r, z, pa/pb
+// (two direction buffers), q. Returns iterations; sets *conv.
+template <int NL, typename R>
+__device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, const R* blk_all, const R* binv_all,
+                   double stop_abs, int maxit, bool x_zero, GridBar* bar, bool* conv, double* rr_out) {
+  const int nF = m.n_facet;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  // z = B r, rho = r.z, rr = r.r ; x = 0 if requested
+  double red[2] = {0.0, 0.0};
+  for (int f = gtid; f < nF; f += gsz) {
+    R r[NL], z[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) r[j] = rv[size_t(f) * NL + j];
+    block_apply<NL, R>(binv_all + size_t(__ldg(&m.facet_stencil[f])) * NL * NL, r, z);
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      zv[size_t(f) * NL + j] = z[j];
+      if (x_zero) x[size_t(f) * NL + j] = R(0);
+      red[0] += double(r[j]) * double(z[j]);
+      red[1] += double(r[j]) * double(r[j]);
+    }
+  }
+  if (!grid_reduce<2>(m, 1, red, bar)) return 0;
+  double rho = red[0], rr = red[1];
+  double beta = 0.0;
+  R* pold = pa;
+  R* pnew = pb;
+  int it = 0;
+  *conv = false;
+  for (; it <= maxit; ++it) {
+    if (!isfinite(rr) || !isfinite(rho)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+      break;
+    }
+    if (sqrt(rr) <= stop_abs) {
+      *conv = true;
+      break;
+    }
+    if (it == maxit) break;
+    // p_new = z + beta p_old (own rows), q = S p_new (from the neighbours' z, p_old)
+    const R rb = R(beta);
+    double pq[1] = {0.0};
+    for (int f = gtid; f < nF; f += gsz) {
+      int nb[5];
+      facet_nbrs<NL>(m, f, nb);
+      R xs[5][NL];
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(nb[b]) * NL + j;
+          xs[b][j] = (it == 0) ? __ldcg(&zv[o]) : __ldcg(&zv[o]) + rb * __ldcg(&pold[o]);
+        }
+      R y[NL];
+      stencil_rows<NL, R>(blk_all + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        pnew[size_t(f) * NL + j] = xs[0][j];
+        qv[size_t(f) * NL + j] = y[j];
+        pq[0] += double(xs[0][j]) * double(y[j]);
+      }
+    }
+    if (!grid_reduce<1>(m, 0, pq, bar)) return it;
+    if (!(pq[0] > 0.0)) {
+      if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+      break;
+    }
+    const double alpha = rho / pq[0];
+    const R ra = R(alpha);
+    double red2[2] = {0.0, 0.0};
+    for (int f = gtid; f < nF; f += gsz) {
+      R r[NL], z[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const size_t o = size_t(f) * NL + j;
+        x[o] += ra * pnew[o];
+        r[j] = rv[o] - ra * qv[o];
+        rv[o] = r[j];
+      }
+      block_apply<NL, R>(binv_all + size_t(__ldg(&m.facet_stencil[f])) * NL * NL, r, z);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        zv[size_t(f) * NL + j] = z[j];
+        red2[0] += double(r[j]) * double(z[j]);
+        red2[1] += double(r[j]) * double(r[j]);
+      }
+    }
+    if (!grid_reduce<2>(m, 1, red2, bar)) return it + 1;
+    beta = red2[0] / rho;
+    rho = red2[0];
+    rr = red2[1];
+    R* t = pold;
+    pold = pnew;
+    pnew = t;
+  }
+  *rr_out = rr;
+  return it;
+}
+
+// One solve: g = assembled element contributions, lam0 = warm_scale * lam, then
+// FP64 PCG (mixed = 0) or FP64 refinement around FP32 PCG (mixed = 1).
+template <int K, int MIXED>
+__global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a) {
+  constexpr int NL = K + 1;
+  const int nF = m.n_facet;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  GridBar* bar = m.bar;
+  // g_F = sum over both sides of the side's contribution mapped to canonical orientation
+  double gg[1] = {0.0};
+  for (int f = gtid; f < nF; f += gsz) {
+    double gv[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) gv[j] = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+      const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
+      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const size_t o = size_t(t) * 3 * NL + e * NL + j;
+        const double v = a.from_float ? double(m.glf[o]) : m.gl[o];
+        gv[j] += (flip && (j & 1)) ? -v : v;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const size_t o = size_t(f) * NL + j;
+      m.g[o] = gv[j];
+      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
+      gg[0] += gv[j] * gv[j];
+    }
+  }
+  if (!grid_reduce<1>(m, 3, gg, bar)) return;
+  const double gnorm = sqrt(gg[0]);
+  const double stop = a.rtol * gnorm;
+  int iters = 0, sweeps = 0;
+  bool conv = false;
+  double relres = 0.0;
+  if (gnorm == 0.0) {
+    for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
+    conv = true;
+  } else {
+    // residual r = g - S lam (lam from the first loop: visible after the barrier)
+    for (int sweep = 0;; ++sweep) {
+      double rr[1] = {0.0};
+      for (int f = gtid; f < nF; f += gsz) {
+        double y[NL];
+        spmv64<NL>(m, f, m.lam, y);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(f) * NL + j;
+          const double r = m.g[o] - y[j];
+          if (MIXED) m.rf[o] = float(r);
+          else m.r[o] = r;
+          rr[0] += r * r;
+        }
+      }
+      if (!MIXED) {
+        // FP64 CG directly on S d = r with lam as the iterate (no refinement needed)
+        bool c = false;
+        double rr_end = 0.0;
+        if (!grid_sync(bar, m.stats)) return;
+        iters = pcg<NL, double>(m, m.lam, m.r, m.z, m.pa, m.pb, m.q, m.st_blk, m.st_binv, stop, a.maxit, false, bar,
+                                &c, &rr_end);
+        conv = c;
+        relres = sqrt(rr_end) / gnorm;
+        sweeps = 1;
+        break;
+      }
+      if (!grid_reduce<1>(m, 4, rr, bar)) return;
+      relres = sqrt(rr[0]) / gnorm;
+      if (!isfinite(rr[0])) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      if (sqrt(rr[0]) <= stop) {
+        conv = true;
+        break;
+      }
+      if (sweep >= a.max_sweeps || iters >= a.maxit) break;
+      // inner FP32 solve of S d = r to inner_rtol relative, d in xf
+      bool c = false;
+      double rr_end = 0.0;
+      const double inner_stop = fmax(a.inner_rtol * sqrt(rr[0]), 0.5 * stop);
+      const int it = pcg<NL, float>(m, m.xf, m.rf, m.zf, m.paf, m.pbf, m.qf, m.st_blk_f, m.st_binv_f, inner_stop,
+                                    a.maxit - iters, true, bar, &c, &rr_end);
+      iters += it;
+      ++sweeps;
+      // lam += d
+      for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(f) * NL + j;
+          m.lam[o] += double(m.xf[o]);
+        }
+      if (!grid_sync(bar, m.stats)) return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats* st = m.stats;
+    st->last_iters = iters;
+    st->total_iters += iters;
+    st->solves += 1;
+    st->last_relres = relres;
+    st->last_sweeps = sweeps;
+    if (!conv) atomicOr(&st->flags, kFlagNotConverged);
+  }
+}
+
+template <int K, int MIXED>
+int max_blocks_for() {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<K, MIXED>, kSolverThreads, 0);
+  return per_sm * sms;
+}
+
+}  // namespace
+
+int solver_max_blocks(const DevMesh& m, int mixed) {
+  int nb = 0;
+  switch (m.k * 2 + (mixed ? 1 : 0)) {
+    case 2: nb = max_blocks_for<1, 0>(); break;
+    case 3: nb = max_blocks_for<1, 1>(); break;
+    case 4: nb = max_blocks_for<2, 0>(); break;
+    case 5: nb = max_blocks_for<2, 1>(); break;
+    case 6: nb = max_blocks_for<3, 0>(); break;
+    case 7: nb = max_blocks_for<3, 1>(); break;
+    default: nb = 0;
+  }
+  const int need = (m.n_facet + kSolverThreads - 1) / kSolverThreads;
+  if (nb > need) nb = need;
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  if (nb < 1) nb = 1;
+  return nb;
+}
+
+cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  DevMesh mm = m;
+  SolveArgs aa = a;
+  void* args[] = {&mm, &aa};
+  const void* fn = nullptr;
+  switch (m.k * 2 + (a.mixed ? 1 : 0)) {
+    case 2: fn = (const void*)k_solve<1, 0>; break;
+    case 3: fn = (const void*)k_solve<1, 1>; break;
+    case 4: fn = (const void*)k_solve<2, 0>; break;
+    case 5: fn = (const void*)k_solve<2, 1>; break;
+    case 6: fn = (const void*)k_solve<3, 0>; break;
+    case 7: fn = (const void*)k_solve<3, 1>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kSolverThreads), args, 0, s);
+}
+
+}  // namespace dgdf

@@ -1,0 +1,642 @@
+// Host-side FP64 set-up of libdgdf (see setup.hpp).
+#include "setup.hpp"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+#include "../../include/dgdf.h"
+
+namespace dgdf {
+namespace {
+
+// ---------------------------------------------------------------- small dense LA
+// In-place inverse of an n x n row-major matrix by Gauss-Jordan with partial pivoting.
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) I[size_t(i) * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[size_t(r) * n + c]) > std::fabs(A[size_t(piv) * n + c])) piv = r;
+    if (A[size_t(piv) * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[size_t(c) * n + j], A[size_t(piv) * n + j]);
+        std::swap(I[size_t(c) * n + j], I[size_t(piv) * n + j]);
+      }
+    double d = 1.0 / A[size_t(c) * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[size_t(c) * n + j] *= d;
+      I[size_t(c) * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[size_t(r) * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[size_t(r) * n + j] -= f * A[size_t(c) * n + j];
+        I[size_t(r) * n + j] -= f * I[size_t(c) * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// C[m x n] = A[m x p] B[p x n]
+std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int m, int p, int n) {
+  std::vector<double> C(size_t(m) * n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int l = 0; l < p; ++l) {
+      double a = A[size_t(i) * p + l];
+      if (a == 0.0) continue;
+      for (int j = 0; j < n; ++j) C[size_t(i) * n + j] += a * B[size_t(l) * n + j];
+    }
+  return C;
+}
+
+std::vector<double> transpose(const std::vector<double>& A, int m, int n) {
+  std::vector<double> T(size_t(m) * n);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) T[size_t(j) * m + i] = A[size_t(i) * n + j];
+  return T;
+}
+
+// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations.
+void sym_eig(std::vector<double> A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
+  evecs.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) evecs[size_t(i) * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[size_t(i) * n + j] * A[size_t(i) * n + j];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[size_t(p) * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double app = A[size_t(p) * n + p], aqq = A[size_t(q) * n + q];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[size_t(k) * n + p], akq = A[size_t(k) * n + q];
+          A[size_t(k) * n + p] = c * akp - s * akq;
+          A[size_t(k) * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[size_t(p) * n + k], aqk = A[size_t(q) * n + k];
+          A[size_t(p) * n + k] = c * apk - s * aqk;
+          A[size_t(q) * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = evecs[size_t(k) * n + p], vkq = evecs[size_t(k) * n + q];
+          evecs[size_t(k) * n + p] = c * vkp - s * vkq;
+          evecs[size_t(k) * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  evals.resize(n);
+  for (int i = 0; i < n; ++i) evals[i] = A[size_t(i) * n + i];
+}
+
+// ------------------------------------------------------------- orthogonal polys
+// Jacobi polynomial P_n^{(a,b)}(x) by its three-term recurrence (Abramowitz-Stegun 22.7.1).
+double jacobi(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = 0.5 * ((a + b + 2.0) * x + (a - b));
+  for (int m = 1; m < n; ++m) {
+    double c = 2.0 * m + a + b;
+    double a1 = 2.0 * (m + 1) * (m + a + b + 1) * c;
+    double a2 = (c + 1) * (a * a - b * b);
+    double a3 = c * (c + 1) * (c + 2);
+    double a4 = 2.0 * (m + a) * (m + b) * (c + 2);
+    double p2 = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// d/dx P_n^{(a,b)} = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)} (Abramowitz-Stegun 22.8.1 in derivative form).
+double djacobi(int n, double a, double b, double x) {
+  if (n == 0) return 0.0;
+  return 0.5 * (n + a + b + 1.0) * jacobi(n - 1, a + 1.0, b + 1.0, x);
+}
+
+double legendre(int n, double x) { return jacobi(n, 0.0, 0.0, x); }
+
+// Gauss-Jacobi rule for the weight (1-x)^a (1+x)^b on [-1,1] by Golub-Welsch.
+void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+  std::vector<double> T(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double c = 2.0 * i + a + b;
+    T[size_t(i) * n + i] = (i == 0 && std::fabs(a + b) < 1e-300) ? (b - a) / (a + b + 2.0)
+                                                                  : (b * b - a * a) / (c * (c + 2.0));
+    if (i + 1 < n) {
+      double m = i + 1.0;
+      double cm = 2.0 * m + a + b;
+      double off = std::sqrt(4.0 * m * (m + a) * (m + b) * (m + a + b) / (cm * cm * (cm + 1.0) * (cm - 1.0)));
+      T[size_t(i) * n + i + 1] = off;
+      T[size_t(i + 1) * n + i] = off;
+    }
+  }
+  std::vector<double> ev, V;
+  sym_eig(T, n, ev, V);
+  double mu0 = std::pow(2.0, a + b + 1.0) * std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 2.0);
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return ev[i] < ev[j]; });
+  x.resize(n);
+  w.resize(n);
+  for (int r = 0; r < n; ++r) {
+    int i = idx[r];
+    double xi = ev[i];
+    // Newton polish on P_n^{(a,b)}
+    for (int it = 0; it < 3; ++it) {
+      double d = djacobi(n, a, b, xi);
+      if (d != 0.0) xi -= jacobi(n, a, b, xi) / d;
+    }
+    x[r] = xi;
+    w[r] = mu0 * V[size_t(0) * n + i] * V[size_t(0) * n + i];
+  }
+}
+
+// Dubiner basis psi_{pq}(xi) = Q_p(xi) P_q^{(2p+1,0)}(2 xi2 - 1), where
+// Q_p = (1-xi2)^p P_p((2 xi1 - 1 + xi2)/(1 - xi2)) is evaluated through the
+// homogenised Legendre recurrence (no division by 1 - xi2).
+struct Dubiner {
+  int k, ns;
+  std::vector<int> pp, qq;
+  std::vector<double> norm;
+  explicit Dubiner(int k_) : k(k_) {
+    for (int d = 0; d <= k; ++d)
+      for (int q = 0; q <= d; ++q) {
+        pp.push_back(d - q);
+        qq.push_back(q);
+      }
+    ns = int(pp.size());
+    norm.assign(ns, 1.0);
+  }
+  // values [ns], gradients [ns][2] at one reference point
+  void eval(double x1, double x2, double* v, double* g) const {
+    double s = 2.0 * x1 - 1.0 + x2, t = 1.0 - x2;
+    const double ds[2] = {2.0, 1.0}, dt[2] = {0.0, -1.0};
+    std::vector<double> Q(k + 1), Qx(k + 1), Qy(k + 1);
+    Q[0] = 1.0;
+    Qx[0] = Qy[0] = 0.0;
+    if (k >= 1) {
+      Q[1] = s;
+      Qx[1] = ds[0];
+      Qy[1] = ds[1];
+    }
+    for (int n = 1; n < k; ++n) {
+      double a = (2.0 * n + 1.0), b = double(n);
+      Q[n + 1] = (a * s * Q[n] - b * t * t * Q[n - 1]) / (n + 1.0);
+      Qx[n + 1] = (a * (ds[0] * Q[n] + s * Qx[n]) - b * (2.0 * t * dt[0] * Q[n - 1] + t * t * Qx[n - 1])) / (n + 1.0);
+      Qy[n + 1] = (a * (ds[1] * Q[n] + s * Qy[n]) - b * (2.0 * t * dt[1] * Q[n - 1] + t * t * Qy[n - 1])) / (n + 1.0);
+    }
+    for (int j = 0; j < ns; ++j) {
+      int p = pp[j], q = qq[j];
+      double y = 2.0 * x2 - 1.0;
+      double R = jacobi(q, 2.0 * p + 1.0, 0.0, y);
+      double dR = 2.0 * djacobi(q, 2.0 * p + 1.0, 0.0, y);
+      double c = norm[j];
+      if (v) v[j] = c * Q[p] * R;
+      if (g) {
+        g[2 * j + 0] = c * Qx[p] * R;
+        g[2 * j + 1] = c * (Qy[p] * R + Q[p] * dR);
+      }
+    }
+  }
+};
+
+// Collapsed rule on the reference triangle: Gauss-Legendre in a, Gauss-Jacobi(1,0) in b,
+// xi1 = (1+a)(1-b)/4, xi2 = (1+b)/2, d xi = (1-b)/8 da db.
+void triangle_rule(int n, std::vector<double>& xi, std::vector<double>& w) {
+  std::vector<double> xa, wa, xb, wb;
+  gauss_jacobi(n, 0.0, 0.0, xa, wa);
+  gauss_jacobi(n, 1.0, 0.0, xb, wb);
+  xi.clear();
+  w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      xi.push_back(0.25 * (1.0 + xa[i]) * (1.0 - xb[j]));
+      xi.push_back(0.5 * (1.0 + xb[j]));
+      w.push_back(wa[i] * wb[j] / 8.0);
+    }
+}
+
+const double kRefV[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+
+}  // namespace
+
+// ------------------------------------------------------------------- topology
+int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology& topo, std::string& err) {
+  if (n_tri < 1 || !vid || !X) {
+    err = "mesh: need n_tri >= 1 and non-NULL arrays";
+    return DG_ERR_INVALID_ARG;
+  }
+  double scale = 1.0;
+  for (int64_t i = 0; i < n_tri * 6; ++i) {
+    if (!std::isfinite(X[i])) {
+      err = "mesh: non-finite coordinate";
+      return DG_ERR_INVALID_ARG;
+    }
+    scale = std::max(scale, std::fabs(X[i]) + 1.0);
+  }
+  const double tol = 1e-9 * scale;
+  for (int64_t t = 0; t < n_tri; ++t) {
+    const double* x = X + t * 6;
+    double det = (x[2] - x[0]) * (x[5] - x[1]) - (x[4] - x[0]) * (x[3] - x[1]);
+    if (!(det > 0.0)) {
+      err = "mesh: triangle " + std::to_string(t) + " is degenerate or clockwise";
+      return DG_ERR_MESH;
+    }
+  }
+  struct Key {
+    int64_t a, b, qx, qy;
+    int64_t slot;  // 3 t + e
+    int8_t orient;
+  };
+  std::vector<Key> keys(size_t(n_tri) * 3);
+  for (int64_t t = 0; t < n_tri; ++t)
+    for (int e = 0; e < 3; ++e) {
+      int ia = (e + 1) % 3, ib = (e + 2) % 3;
+      double dx = X[t * 6 + ib * 2] - X[t * 6 + ia * 2];
+      double dy = X[t * 6 + ib * 2 + 1] - X[t * 6 + ia * 2 + 1];
+      bool pos = dx > tol || (std::fabs(dx) <= tol && dy > 0.0);
+      Key k;
+      if (pos) {
+        k.a = vid[t * 3 + ia];
+        k.b = vid[t * 3 + ib];
+        k.orient = 1;
+      } else {
+        k.a = vid[t * 3 + ib];
+        k.b = vid[t * 3 + ia];
+        k.orient = -1;
+        dx = -dx;
+        dy = -dy;
+      }
+      k.qx = std::llround(dx / tol);
+      k.qy = std::llround(dy / tol);
+      k.slot = t * 3 + e;
+      keys[size_t(t) * 3 + e] = k;
+    }
+  std::vector<int64_t> order(keys.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int64_t i, int64_t j) {
+    const Key &p = keys[i], &q = keys[j];
+    return std::tie(p.a, p.b, p.qx, p.qy, p.slot) < std::tie(q.a, q.b, q.qx, q.qy, q.slot);
+  });
+  // groups of equal keys; each must hold exactly two slots with opposite orientation
+  struct Group {
+    int64_t s0, s1;
+  };
+  std::vector<Group> groups;
+  groups.reserve(keys.size() / 2);
+  for (size_t i = 0; i < order.size();) {
+    size_t j = i + 1;
+    const Key& p = keys[order[i]];
+    while (j < order.size()) {
+      const Key& q = keys[order[j]];
+      if (q.a != p.a || q.b != p.b || q.qx != p.qx || q.qy != p.qy) break;
+      ++j;
+    }
+    size_t cnt = j - i;
+    if (cnt == 1) {
+      err = "mesh: edge of triangle " + std::to_string(p.slot / 3) + " has no neighbour (boundary facets are not supported)";
+      return DG_ERR_UNSUPPORTED;
+    }
+    if (cnt != 2) {
+      err = "mesh: an edge is shared by " + std::to_string(cnt) + " triangles";
+      return DG_ERR_MESH;
+    }
+    if (keys[order[i]].orient == keys[order[i + 1]].orient) {
+      err = "mesh: a facet is traversed in the same direction by both triangles";
+      return DG_ERR_MESH;
+    }
+    groups.push_back({keys[order[i]].slot, keys[order[i + 1]].slot});  // slot order: first appearance first
+    i = j;
+  }
+  std::sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.s0 < b.s0; });
+  topo.n_tri = n_tri;
+  topo.n_facet = int64_t(groups.size());
+  if (topo.n_facet > INT32_MAX / 4 || n_tri > INT32_MAX / 4) {
+    err = "mesh too large for 32-bit indices";
+    return DG_ERR_INVALID_ARG;
+  }
+  topo.tri_facet.assign(size_t(n_tri) * 3, -1);
+  topo.tri_orient.assign(size_t(n_tri) * 3, 0);
+  topo.facet_tri.resize(size_t(topo.n_facet) * 2);
+  topo.facet_loc.resize(size_t(topo.n_facet) * 2);
+  for (int64_t f = 0; f < topo.n_facet; ++f) {
+    int64_t sl[2] = {groups[f].s0, groups[f].s1};
+    for (int s = 0; s < 2; ++s) {
+      topo.facet_tri[f * 2 + s] = int32_t(sl[s] / 3);
+      topo.facet_loc[f * 2 + s] = int8_t(sl[s] % 3);
+      topo.tri_facet[sl[s]] = int32_t(f);
+      topo.tri_orient[sl[s]] = keys[sl[s]].orient;
+    }
+  }
+  return DG_OK;
+}
+
+// ------------------------------------------------------------ reference tables
+int build_reference(int k, RefTables& ref, std::string& err) {
+  if (k < 1 || k > kMaxDegree) {
+    err = "degree k must be 1.." + std::to_string(kMaxDegree);
+    return DG_ERR_UNSUPPORTED;
+  }
+  ref.k = k;
+  ref.ns = n_lat(k);
+  ref.nw = n_lat(k - 1);
+  ref.nl = k + 1;
+  Dubiner B(k);
+  // normalise on the reference triangle with a rule exact to degree 2k
+  {
+    std::vector<double> xi, w;
+    triangle_rule(k + 2, xi, w);
+    std::vector<double> v(B.ns);
+    std::vector<double> nrm(B.ns, 0.0);
+    for (size_t q = 0; q < w.size(); ++q) {
+      B.eval(xi[2 * q], xi[2 * q + 1], v.data(), nullptr);
+      for (int j = 0; j < B.ns; ++j) nrm[j] += w[q] * v[j] * v[j];
+    }
+    for (int j = 0; j < B.ns; ++j) B.norm[j] = 1.0 / std::sqrt(nrm[j]);
+  }
+  const int ns = ref.ns;
+  // volume rule exact to degree 3k - 1: n points per direction with 2n - 1 >= 3k - 1
+  int n = (3 * k + 1) / 2;
+  triangle_rule(n, ref.vxi, ref.vw);
+  ref.nq = int(ref.vw.size());
+  ref.vphi.resize(size_t(ref.nq) * ns);
+  ref.vdphi.resize(size_t(ref.nq) * ns * 2);
+  for (int q = 0; q < ref.nq; ++q)
+    B.eval(ref.vxi[2 * q], ref.vxi[2 * q + 1], &ref.vphi[size_t(q) * ns], &ref.vdphi[size_t(q) * ns * 2]);
+  // facet rule: ceil((3k+1)/2) Gauss-Legendre points on [0,1]
+  ref.nqf = (3 * k + 2) / 2;
+  {
+    std::vector<double> x, w;
+    gauss_jacobi(ref.nqf, 0.0, 0.0, x, w);
+    ref.ft.resize(ref.nqf);
+    ref.fw.resize(ref.nqf);
+    for (int q = 0; q < ref.nqf; ++q) {
+      ref.ft[q] = 0.5 * (x[q] + 1.0);
+      ref.fw[q] = 0.5 * w[q];
+    }
+  }
+  ref.fphi.resize(size_t(3) * ref.nqf * ns);
+  ref.fdphi.resize(size_t(3) * ref.nqf * ns * 2);
+  for (int e = 0; e < 3; ++e) {
+    const double* a = kRefV[(e + 1) % 3];
+    const double* b = kRefV[(e + 2) % 3];
+    for (int q = 0; q < ref.nqf; ++q) {
+      double t = ref.ft[q];
+      double x1 = a[0] + t * (b[0] - a[0]), x2 = a[1] + t * (b[1] - a[1]);
+      B.eval(x1, x2, &ref.fphi[(size_t(e) * ref.nqf + q) * ns], &ref.fdphi[(size_t(e) * ref.nqf + q) * ns * 2]);
+    }
+  }
+  // lattice tables
+  ref.lat_phi.resize(size_t(ns) * ns);
+  {
+    int p = 0;
+    for (int j = 0; j <= k; ++j)
+      for (int i = 0; i <= k - j; ++i, ++p) B.eval(double(i) / k, double(j) / k, &ref.lat_phi[size_t(p) * ns], nullptr);
+  }
+  ref.lat_inv = ref.lat_phi;
+  if (!invert(ref.lat_inv, ns)) {
+    err = "lattice Vandermonde singular";
+    return DG_ERR_UNSUPPORTED;
+  }
+  const int nw = ref.nw;
+  ref.plat_phi.resize(size_t(nw) * nw);
+  {
+    std::vector<double> v(ns);
+    int m = k - 1, p = 0;
+    if (m == 0) {
+      B.eval(1.0 / 3.0, 1.0 / 3.0, v.data(), nullptr);
+      for (int j = 0; j < nw; ++j) ref.plat_phi[j] = v[j];
+    } else {
+      for (int jj = 0; jj <= m; ++jj)
+        for (int ii = 0; ii <= m - jj; ++ii, ++p) {
+          B.eval(double(ii) / m, double(jj) / m, v.data(), nullptr);
+          for (int j = 0; j < nw; ++j) ref.plat_phi[size_t(p) * nw + j] = v[j];
+        }
+    }
+  }
+  ref.mu_lat.resize(size_t(k + 1) * ref.nl);
+  for (int i = 0; i <= k; ++i)
+    for (int m = 0; m < ref.nl; ++m)
+      ref.mu_lat[size_t(i) * ref.nl + m] = std::sqrt(2.0 * m + 1.0) * legendre(m, 2.0 * (double(i) / k) - 1.0);
+  return DG_OK;
+}
+
+// ------------------------------------------------------------ element classes
+namespace {
+
+// Operators of eq. (12) for one triangle with orthonormal bases (so M_T = I):
+// D_T[m][(c,j)] = (z_m, d_c psi_j)_T, C_T[(e,m)][(c,j)] = <mu_m, psi_j n_{e,c}>_{F_e}
+// with mu_m(s) = sqrt(2m+1) P_m(2s-1) in the element's counter-clockwise parameter s.
+void class_ops(const RefTables& ref, const double* x, ClassOps& co) {
+  const int ns = ref.ns, nd = 2 * ns, nw = ref.nw, nl = ref.nl;
+  co.J[0] = x[2] - x[0];
+  co.J[1] = x[4] - x[0];
+  co.J[2] = x[3] - x[1];
+  co.J[3] = x[5] - x[1];
+  co.det = co.J[0] * co.J[3] - co.J[1] * co.J[2];
+  co.Jinv[0] = co.J[3] / co.det;
+  co.Jinv[1] = -co.J[1] / co.det;
+  co.Jinv[2] = -co.J[2] / co.det;
+  co.Jinv[3] = co.J[0] / co.det;
+  for (int e = 0; e < 3; ++e) {
+    int a = (e + 1) % 3, b = (e + 2) % 3;
+    double dx = x[2 * b] - x[2 * a], dy = x[2 * b + 1] - x[2 * a + 1];
+    double l = std::sqrt(dx * dx + dy * dy);
+    co.flen[e] = l;
+    co.normal[e][0] = dy / l;
+    co.normal[e][1] = -dx / l;
+  }
+  const double s = 1.0 / std::sqrt(co.det);
+  // D (volume rule is exact to 3k-1 >= 2k-2); 2|T| s^2 = 1
+  std::vector<double> D(size_t(nw) * nd, 0.0);
+  for (int q = 0; q < ref.nq; ++q) {
+    double w = ref.vw[q];
+    for (int m = 0; m < nw; ++m) {
+      double z = ref.vphi[size_t(q) * ns + m];
+      for (int j = 0; j < ns; ++j) {
+        double g0 = ref.vdphi[(size_t(q) * ns + j) * 2], g1 = ref.vdphi[(size_t(q) * ns + j) * 2 + 1];
+        for (int c = 0; c < 2; ++c) {
+          double dc = g0 * co.Jinv[0 * 2 + c] + g1 * co.Jinv[1 * 2 + c];
+          D[size_t(m) * nd + c * ns + j] += w * z * dc;
+        }
+      }
+    }
+  }
+  std::vector<double> C(size_t(3 * nl) * nd, 0.0);
+  for (int e = 0; e < 3; ++e)
+    for (int q = 0; q < ref.nqf; ++q) {
+      double w = ref.fw[q] * co.flen[e] * s;
+      for (int m = 0; m < nl; ++m) {
+        double mu = std::sqrt(2.0 * m + 1.0) * legendre(m, 2.0 * ref.ft[q] - 1.0);
+        for (int j = 0; j < ns; ++j) {
+          double v = ref.fphi[(size_t(e) * ref.nqf + q) * ns + j];
+          for (int c = 0; c < 2; ++c) C[size_t(e * nl + m) * nd + c * ns + j] += w * mu * v * co.normal[e][c];
+        }
+      }
+    }
+  // P = I - D^T (D D^T)^-1 D, W = -(D D^T)^-1 D
+  std::vector<double> Dt = transpose(D, nw, nd);
+  std::vector<double> DDt = matmul(D, Dt, nw, nd, nw);
+  invert(DDt, nw);
+  std::vector<double> Wm = matmul(DDt, D, nw, nw, nd);
+  for (double& v : Wm) v = -v;
+  std::vector<double> P = matmul(Dt, Wm, nd, nw, nd);  // -D^T (DD^T)^-1 D
+  for (int i = 0; i < nd; ++i) P[size_t(i) * nd + i] += 1.0;
+  // symmetrise (exact in exact arithmetic)
+  for (int i = 0; i < nd; ++i)
+    for (int j = i + 1; j < nd; ++j) {
+      double a = 0.5 * (P[size_t(i) * nd + j] + P[size_t(j) * nd + i]);
+      P[size_t(i) * nd + j] = P[size_t(j) * nd + i] = a;
+    }
+  co.P = P;
+  co.W = Wm;
+  co.G = matmul(C, P, 3 * nl, nd, nd);
+  std::vector<double> Ct = transpose(C, 3 * nl, nd);
+  co.S = matmul(co.G, Ct, 3 * nl, nd, 3 * nl);
+  for (int i = 0; i < 3 * nl; ++i)
+    for (int j = i + 1; j < 3 * nl; ++j) {
+      double a = 0.5 * (co.S[size_t(i) * 3 * nl + j] + co.S[size_t(j) * 3 * nl + i]);
+      co.S[size_t(i) * 3 * nl + j] = co.S[size_t(j) * 3 * nl + i] = a;
+    }
+  co.WCt = matmul(Wm, Ct, nw, nd, 3 * nl);
+}
+
+}  // namespace
+
+int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha, HostMesh& hm,
+                    std::string& err) {
+  int rc = build_reference(k, hm.ref, err);
+  if (rc) return rc;
+  rc = build_topology(n_tri, vid, X, hm.topo, err);
+  if (rc) return rc;
+  const RefTables& ref = hm.ref;
+  hm.k = k;
+  hm.ns = ref.ns;
+  hm.nd = 2 * ref.ns;
+  hm.nw = ref.nw;
+  hm.nl = ref.nl;
+  hm.alpha = alpha;
+  const int nl = hm.nl;
+  const Topology& T = hm.topo;
+  // geometry classes: Jacobians equal to 1e-11 of the largest entry share one set of operators
+  double jmax = 0.0;
+  for (int64_t t = 0; t < n_tri; ++t) {
+    const double* x = X + t * 6;
+    for (int c = 1; c < 3; ++c)
+      for (int d = 0; d < 2; ++d) jmax = std::max(jmax, std::fabs(x[2 * c + d] - x[d]));
+  }
+  const double jtol = 1e-11 * jmax;
+  std::map<std::array<int64_t, 4>, int32_t> cls;
+  hm.tri_class.resize(n_tri);
+  std::vector<int64_t> rep;
+  for (int64_t t = 0; t < n_tri; ++t) {
+    const double* x = X + t * 6;
+    std::array<int64_t, 4> key = {std::llround((x[2] - x[0]) / jtol), std::llround((x[4] - x[0]) / jtol),
+                                  std::llround((x[3] - x[1]) / jtol), std::llround((x[5] - x[1]) / jtol)};
+    auto it = cls.find(key);
+    if (it == cls.end()) {
+      it = cls.emplace(key, int32_t(rep.size())).first;
+      rep.push_back(t);
+    }
+    hm.tri_class[t] = it->second;
+  }
+  hm.classes.resize(rep.size());
+  for (size_t c = 0; c < rep.size(); ++c) class_ops(ref, X + rep[c] * 6, hm.classes[c]);
+  hm.area_total = 0.0;
+  for (int64_t t = 0; t < n_tri; ++t) hm.area_total += 0.5 * hm.classes[hm.tri_class[t]].det;
+  // neighbours and penalties
+  hm.tri_nbr.resize(size_t(n_tri) * 3);
+  hm.tri_nbr_loc.resize(size_t(n_tri) * 3);
+  for (int64_t f = 0; f < T.n_facet; ++f)
+    for (int s = 0; s < 2; ++s) {
+      int32_t t = T.facet_tri[f * 2 + s], o = T.facet_tri[f * 2 + 1 - s];
+      int e = T.facet_loc[f * 2 + s];
+      hm.tri_nbr[size_t(t) * 3 + e] = o;
+      hm.tri_nbr_loc[size_t(t) * 3 + e] = T.facet_loc[f * 2 + 1 - s];
+    }
+  auto diam = [&](int32_t t) {
+    const ClassOps& c = hm.classes[hm.tri_class[t]];
+    return std::max(c.flen[0], std::max(c.flen[1], c.flen[2]));
+  };
+  hm.facet_sigma.resize(T.n_facet);
+  for (int64_t f = 0; f < T.n_facet; ++f)
+    hm.facet_sigma[f] = alpha * k * k / std::max(diam(T.facet_tri[f * 2]), diam(T.facet_tri[f * 2 + 1]));
+  // facet stencils: row F = sum over both sides T of D(sigma_e) S_T[e][e'] D(sigma_e') lam_{F_e'}
+  // with D(sigma) = diag(sigma^m) mapping the global (canonical) coefficients to T's own.
+  hm.facet_nbr.resize(size_t(T.n_facet) * 4);
+  hm.facet_stencil.resize(T.n_facet);
+  std::map<std::vector<int64_t>, int32_t> st;
+  hm.stencil_blocks.clear();
+  hm.stencil_binv.clear();
+  const int L3 = 3 * nl;
+  for (int64_t f = 0; f < T.n_facet; ++f) {
+    int side_order[2] = {0, 1};
+    {
+      int32_t t0 = T.facet_tri[f * 2], t1 = T.facet_tri[f * 2 + 1];
+      auto key0 = std::make_pair(hm.tri_class[t0], int(T.facet_loc[f * 2]));
+      auto key1 = std::make_pair(hm.tri_class[t1], int(T.facet_loc[f * 2 + 1]));
+      if (key1 < key0) std::swap(side_order[0], side_order[1]);
+    }
+    std::vector<int64_t> key;
+    for (int si = 0; si < 2; ++si) {
+      int s = side_order[si];
+      int32_t t = T.facet_tri[f * 2 + s];
+      int e = T.facet_loc[f * 2 + s];
+      key.push_back(hm.tri_class[t]);
+      key.push_back(e);
+      for (int ee = 0; ee < 3; ++ee) key.push_back(T.tri_orient[size_t(t) * 3 + ee]);
+      hm.facet_nbr[f * 4 + si * 2 + 0] = T.tri_facet[size_t(t) * 3 + (e + 1) % 3];
+      hm.facet_nbr[f * 4 + si * 2 + 1] = T.tri_facet[size_t(t) * 3 + (e + 2) % 3];
+    }
+    auto it = st.find(key);
+    if (it == st.end()) {
+      int32_t id = int32_t(st.size());
+      it = st.emplace(key, id).first;
+      std::vector<double> blk(size_t(5) * nl * nl, 0.0);
+      for (int si = 0; si < 2; ++si) {
+        int s = side_order[si];
+        int32_t t = T.facet_tri[f * 2 + s];
+        int e = T.facet_loc[f * 2 + s];
+        const ClassOps& co = hm.classes[hm.tri_class[t]];
+        auto sgn = [&](int ee, int m) { return (T.tri_orient[size_t(t) * 3 + ee] < 0 && (m & 1)) ? -1.0 : 1.0; };
+        const int targets[3] = {e, (e + 1) % 3, (e + 2) % 3};
+        for (int b = 0; b < 3; ++b) {
+          int ee = targets[b];
+          int slot = (b == 0) ? 0 : 1 + si * 2 + (b - 1);
+          for (int m = 0; m < nl; ++m)
+            for (int mm = 0; mm < nl; ++mm)
+              blk[(size_t(slot) * nl + m) * nl + mm] +=
+                  sgn(e, m) * co.S[size_t(e * nl + m) * L3 + ee * nl + mm] * sgn(ee, mm);
+        }
+      }
+      std::vector<double> inv(blk.begin(), blk.begin() + nl * nl);
+      if (!invert(inv, nl)) {
+        err = "singular facet block";
+        return DG_ERR_MESH;
+      }
+      hm.stencil_blocks.insert(hm.stencil_blocks.end(), blk.begin(), blk.end());
+      hm.stencil_binv.insert(hm.stencil_binv.end(), inv.begin(), inv.end());
+    }
+    hm.facet_stencil[f] = it->second;
+  }
+  hm.n_stencil = int(st.size());
+  return DG_OK;
+}
+
+}  // namespace dgdf

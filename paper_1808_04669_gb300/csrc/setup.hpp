@@ -1,0 +1,81 @@
+// Host-side FP64 set-up of libdgdf: topology, reference tables, element operators.
+//
+// Everything here runs once per mesh on the CPU (the hybrid-mixed matrix does
+// not depend on dt, Remark 2, so its element blocks are precomputed) and is
+// then uploaded. No CUDA in this translation unit.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dgdf {
+
+constexpr int kMaxDegree = 3;
+
+inline int n_lat(int m) { return (m + 1) * (m + 2) / 2; }
+
+// Reference quadrature rules and the orthonormal (Dubiner) basis of P^k on the
+// triangle {xi1, xi2 >= 0, xi1 + xi2 <= 1}, ordered by total degree so that the
+// first n_lat(k-1) functions span P^{k-1}.
+struct RefTables {
+  int k = 0, ns = 0, nw = 0, nl = 0, nq = 0, nqf = 0;
+  std::vector<double> vxi, vw;        // volume rule: [nq][2], [nq] (weights sum to 1/2)
+  std::vector<double> vphi, vdphi;    // [nq][ns], [nq][ns][2]
+  std::vector<double> ft, fw;         // facet rule on [0,1]: [nqf]
+  std::vector<double> fphi, fdphi;    // local facet e, element-CCW point order: [3][nqf][ns], [3][nqf][ns][2]
+  std::vector<double> lat_phi;        // basis at the k-lattice, [ns][ns] (row = point)
+  std::vector<double> lat_inv;        // its inverse [ns][ns]
+  std::vector<double> plat_phi;       // first nw functions at the (k-1)-lattice, [nw][nw]
+  std::vector<double> mu_lat;         // facet basis mu_m at t = i/k, [k+1][nl]
+};
+
+// Operators of one element geometry class (elements equal up to translation).
+struct ClassOps {
+  double J[4];      // [v1-v0, v2-v0] as columns, row-major
+  double Jinv[4];   // row-major, (J^-1)_{r d} = d xi_r / d x_d
+  double det;       // 2 |T|
+  double normal[3][2];
+  double flen[3];
+  std::vector<double> P;    // [nd][nd]    (A_T^-1)_uu: M-orthogonal projector onto ker D_T
+  std::vector<double> G;    // [3nl][nd]   C_T P_T
+  std::vector<double> S;    // [3nl][3nl]  C_T P_T C_T^T
+  std::vector<double> W;    // [nw][nd]    (A_T^-1)_wu
+  std::vector<double> WCt;  // [nw][3nl]   W_T C_T^T
+};
+
+struct Topology {
+  int64_t n_tri = 0, n_facet = 0;
+  std::vector<int32_t> tri_facet;   // [n_tri][3]
+  std::vector<int8_t> tri_orient;   // [n_tri][3] +1 along canonical direction, -1 against
+  std::vector<int32_t> facet_tri;   // [n_facet][2] first appearance first
+  std::vector<int8_t> facet_loc;    // [n_facet][2]
+};
+
+struct HostMesh {
+  int k = 0, ns = 0, nd = 0, nw = 0, nl = 0;
+  double alpha = 2.0;
+  Topology topo;
+  RefTables ref;
+  std::vector<int32_t> tri_class;   // [n_tri]
+  std::vector<ClassOps> classes;
+  std::vector<int32_t> tri_nbr;     // [n_tri][3] neighbour across local facet e
+  std::vector<int8_t> tri_nbr_loc;  // [n_tri][3] the neighbour's local index of that facet
+  std::vector<double> facet_sigma;  // [n_facet] alpha k^2 / h_F, h_F = max diameter of the two triangles
+  // Facet-system stencil: row F couples to itself and to the other two facets of
+  // each adjacent triangle. Rows with equal blocks share a stencil class.
+  std::vector<int32_t> facet_nbr;   // [n_facet][4]
+  std::vector<int32_t> facet_stencil;   // [n_facet]
+  std::vector<double> stencil_blocks;   // [n_stencil][5][nl][nl] (own, then the 4 neighbours)
+  std::vector<double> stencil_binv;     // [n_stencil][nl][nl] inverse of the own block (block Jacobi)
+  int n_stencil = 0;
+  double area_total = 0.0;
+};
+
+// Returns 0 or a dg_status code; message in err.
+int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology& topo, std::string& err);
+int build_reference(int k, RefTables& ref, std::string& err);
+int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha,
+                    HostMesh& hm, std::string& err);
+
+}  // namespace dgdf

@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the same seeded inputs.
+
+Tolerances (relative L2 over all lattice values): 1e-12 for the FP64 form,
+1e-9 for the mixed-precision form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import Discretization
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-9
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1808_04669_gb300 import build
+    build.build()
+    import paper_1808_04669_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def pair(g, N, k, nu, L=2 * np.pi, precision=0, perturb=0.0, seed=0, **kw):
+    vid, X = synth.split_square_mesh(N, L=L)
+    if perturb:
+        rng = np.random.default_rng(seed)
+        X = X + (perturb * L / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
+    mesh = g.DGMesh(vid, X, k, nu, precision=precision, **kw)
+    d = Discretization(vid, X, k, nu)
+    return mesh, d, X
+
+
+def random_lattice(n_tri, k, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_tri, (k + 1) * (k + 2) // 2, 2))
+
+
+# ------------------------------------------------------------------- basics
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_lattice_roundtrip(g, k):
+    mesh, d, X = pair(g, 3, k, 0.0)
+    v = random_lattice(mesh.n_tri, k, 1)
+    mesh.set_velocity(v)
+    assert np.abs(mesh.get_velocity() - v).max() < 1e-13
+
+
+def test_mesh_info_uniform_classes(g):
+    mesh, d, X = pair(g, 8, 2, 0.0)
+    assert mesh.n_tri == 128 and mesh.n_facet == 192
+    assert mesh.n_class == 2 and mesh.n_stencil == 3
+
+
+# ----------------------------------------------------------------- residual
+@pytest.mark.parametrize("N,k,nu,perturb", [(1, 1, 0.0, 0.0), (2, 2, 0.05, 0.0), (3, 3, 0.01, 0.0),
+                                            (5, 2, 0.02, 0.0), (4, 3, 0.0, 0.12), (3, 1, 0.3, 0.1)])
+def test_residual_parity(g, N, k, nu, perturb):
+    mesh, d, X = pair(g, N, k, nu, perturb=perturb, seed=N)
+    v = random_lattice(mesh.n_tri, k, 10 + N)
+    mesh.set_velocity(v)
+    gpu = mesh.eval_residual()
+    U = d.from_lattice(v)
+    ref = d.to_lattice(d.riesz(d.residual(U)))
+    assert rel(gpu, ref) < TOL64
+
+
+def test_residual_parity_projected_field(g):
+    # divergence-free field: the upwind switch sees the same u.n on both sides
+    mesh, d, X = pair(g, 6, 3, 1e-3)
+    v = synth.sample_lattice(synth.double_shear_layer(), X, 3)
+    mesh.set_velocity(v)
+    mesh.project_divfree()
+    U = d.project(d.from_lattice(v))
+    gpu = mesh.eval_residual()
+    ref = d.to_lattice(d.riesz(d.residual(U)))
+    assert rel(gpu, ref) < TOL64
+
+
+# --------------------------------------------------------------- projection
+@pytest.mark.parametrize("N,k,perturb", [(1, 1, 0.0), (2, 3, 0.0), (4, 2, 0.0), (5, 3, 0.0), (4, 2, 0.1)])
+def test_projection_parity(g, N, k, perturb):
+    mesh, d, X = pair(g, N, k, 0.0, perturb=perturb, seed=3)
+    v = random_lattice(mesh.n_tri, k, 20 + N)
+    mesh.set_velocity(v)
+    mesh.project_divfree()
+    gpu = mesh.get_velocity()
+    ref = d.to_lattice(d.project(d.from_lattice(v)))
+    assert rel(gpu, ref) < TOL64
+    dg = mesh.diagnostics()
+    assert dg["max_div"] < 1e-11 * max(1.0, np.abs(ref).max()) * N
+    assert dg["max_jump"] < 1e-10
+
+
+def test_projection_idempotent_and_orthogonal(g):
+    mesh, d, X = pair(g, 8, 3, 0.0)
+    v = random_lattice(mesh.n_tri, 3, 5)
+    mesh.set_velocity(v)
+    e0 = mesh.diagnostics()["energy"]
+    mesh.project_divfree()
+    u1 = mesh.get_velocity()
+    e1 = mesh.diagnostics()["energy"]
+    mesh.project_divfree()
+    u2 = mesh.get_velocity()
+    assert rel(u2, u1) < 1e-12
+    assert e1 <= e0
+
+
+# ------------------------------------------------------------------- RK3
+def test_rk3_parity_taylor_green_n8_k2(g):
+    # Taylor-Green, 8x8 split squares, BDM_2, nu = 1e-2, 100 SSP-RK3 steps, FP64
+    vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
+    mesh = g.DGMesh(vid, X, 2, 1e-2)
+    d = Discretization(vid, X, 2, 1e-2)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    mesh.rk3_step(dt, 100)
+    gpu = mesh.get_velocity()
+    U = d.rk3_step(d.project(d.from_lattice(vals)), dt, 100)
+    ref = d.to_lattice(U)
+    assert rel(gpu, ref) < TOL64
+    # closed form u(t) = u0 exp(-2 nu t): the GPU error equals the oracle's
+    T = 100 * dt
+    ex = synth.sample_lattice(synth.taylor_green(), X, 2) * math.exp(-2e-2 * T)
+    assert abs(rel(gpu, ex) - rel(ref, ex)) < 1e-9
+    dg = mesh.diagnostics()
+    assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_rk3_parity_shear_layer(g, k):
+    N, nu = 12, 1e-4
+    vid, X = synth.split_square_mesh(N)
+    vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
+    vmax = float(np.sqrt((vals ** 2).sum(-1)).max())
+    dt = synth.cfl_dt(X, k, vmax, nu)
+    d = Discretization(vid, X, k, nu)
+    U = d.rk3_step(d.project(d.from_lattice(vals)), dt, 5)
+    ref = d.to_lattice(U)
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.rk3_step(dt, 5)
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+
+
+def test_mixed_precision_taylor_green(g):
+    vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
+    mesh = g.DGMesh(vid, X, 2, 1e-2, precision=1)
+    d = Discretization(vid, X, 2, 1e-2)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    mesh.rk3_step(dt, 30)
+    U = d.rk3_step(d.project(d.from_lattice(vals)), dt, 30)
+    assert rel(mesh.get_velocity(), d.to_lattice(U)) < TOLMIX
+    dg = mesh.diagnostics()
+    assert dg["max_jump"] < 1e-10
+
+
+def test_euler_energy_non_increasing(g):
+    vid, X = synth.split_square_mesh(16, L=1.0)
+    f = synth.random_spectrum_velocity(0, kmax=6, L=1.0)
+    vals = synth.sample_lattice(f, X, 2)
+    dt = synth.cfl_dt(X, 2, float(np.sqrt((vals ** 2).sum(-1)).max()), 0.0)
+    mesh = g.DGMesh(vid, X, 2, 0.0)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    E = [mesh.diagnostics()["energy"]]
+    for _ in range(10):
+        mesh.rk3_step(dt, 1)
+        E.append(mesh.diagnostics()["energy"])
+    assert np.all(np.diff(E) <= 1e-14 * E[0])
+
+
+# ---------------------------------------------------------------- pressure
+@pytest.mark.parametrize("N,k", [(4, 2), (3, 3), (2, 1)])
+def test_pressure_parity(g, N, k):
+    mesh, d, X = pair(g, N, k, 1e-2)
+    v = synth.sample_lattice(synth.taylor_green(), X, k) + 0.3 * random_lattice(mesh.n_tri, k, 7)
+    mesh.set_velocity(v)
+    mesh.project_divfree()
+    pe, pf = mesh.get_pressure()
+    U = d.project(d.from_lattice(v))
+    w, lam = d.pressure(U)
+    pe_ref, pf_ref = d.pressure_lattice(w, lam)
+    assert rel(pe, pe_ref) < 1e-11
+    assert rel(pf, pf_ref) < 1e-11
+
+
+def test_diagnostics_parity(g):
+    mesh, d, X = pair(g, 5, 3, 0.0)
+    v = random_lattice(mesh.n_tri, 3, 9)
+    mesh.set_velocity(v)
+    dg = mesh.diagnostics()
+    ref = d.diagnostics(d.from_lattice(v))
+    for key in ("energy", "enstrophy", "max_div", "max_jump"):
+        assert abs(dg[key] - ref[key]) < 1e-12 * max(1.0, abs(ref[key])), key
+
+
+# --------------------------------------------------------------- edge cases
+def test_zero_state_and_zero_steps(g):
+    mesh, d, X = pair(g, 2, 2, 0.1)
+    mesh.project_divfree()
+    mesh.rk3_step(0.01, 0)
+    mesh.rk3_step(0.01, 3)
+    assert np.abs(mesh.get_velocity()).max() == 0.0
+
+
+def test_constant_velocity_preserved(g):
+    mesh, d, X = pair(g, 3, 3, 0.05)
+    v = synth.sample_lattice(synth.constant_field((0.4, -0.2)), X, 3)
+    mesh.set_velocity(v)
+    mesh.project_divfree()
+    mesh.rk3_step(0.02, 5)
+    assert np.abs(mesh.get_velocity() - v).max() < 1e-12
+
+
+def test_invalid_inputs_raise(g):
+    from paper_1808_04669_gb300 import DGError
+    mesh, d, X = pair(g, 2, 1, 0.0)
+    with pytest.raises(DGError):
+        mesh.rk3_step(-1.0, 1)
+    v = random_lattice(mesh.n_tri, 1, 0)
+    v[0, 0, 0] = np.nan
+    with pytest.raises(DGError) as e:
+        mesh.set_velocity(v)
+    assert e.value.code == -6
+    vid, X = synth.split_square_mesh(2)
+    with pytest.raises(DGError) as e:
+        g.DGMesh(vid, X, 4, 0.0)
+    assert e.value.code == -3
+
+
+def test_iteration_cap_reports_not_converged(g):
+    from paper_1808_04669_gb300 import DGError
+    vid, X = synth.split_square_mesh(8)
+    mesh = g.DGMesh(vid, X, 2, 0.0, cg_maxit=1)
+    mesh.set_velocity(random_lattice(mesh.n_tri, 2, 4))
+    with pytest.raises(DGError) as e:
+        mesh.project_divfree()
+    assert e.value.code == -5

