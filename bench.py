@@ -1,0 +1,373 @@
+"""Benchmark: velocity DOF-stage updates per second of SSP-RK3 with the hybrid-mixed solve.
+
+One step = one SSP-RK3 time step (three stages; each stage = element residual
+and condensation, facet PCG solve, recovery) on the double shear layer,
+256 x 256 split squares of [0, 2pi]^2 (131072 triangles), BDM_3, nu = 1e-4.
+The timed form is the mixed-precision one (FP64 element kernels, facet system
+solved by FP32 PCG inside FP64 refinement); the FP64 form is timed on the same
+workload and its state compared with the mixed one.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): every rank advances its own replica of the
+workload (independent instances, weak scaling); rank 0 prints the line.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "velocity DOF-stage updates/s incl. hybrid-mixed solve; mixed vs FP64 at 1e-9 rel"
+UNIT = "velocity DOF-stage updates/s"
+WORKLOAD = "shear_n256_k3"
+SAMPLE_N = 32          # oracle sample: same workload on a 32 x 32 split-square mesh
+L2_FLUSH_BYTES = 512 << 20
+
+# DRAM traffic of one mixed-solver launch per inner CG iteration, from the ncu capture
+# summarised in profiles/ (None until captured for the current kernel source).
+NCU_TRAFFIC = {"k_solver_sha": None, "bytes_per_iter": None}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dof_stage_units(n_tri, k, steps):
+    return n_tri * (k + 1) * (k + 2) * 3 * steps
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def k_solver_sha():
+    with open(os.path.join(ROOT, "paper_1808_04669_gb300", "csrc", "k_solver.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def solver_bytes(n_facet, k, iters, sweeps, solves):
+    """Algorithmic DRAM bytes of the mixed facet solves (facet PCG row).
+
+    Per inner FP32 CG iteration: 11 vector passes of 4 B per multiplier DOF
+    (read z, p_old; write p_new, q; read x, p_new, r, q; write x, r, z) plus
+    24 B of stencil indices per facet. Per FP64 refinement sweep: read lam and
+    g (8 B each), write the FP32 residual (4 B), then lam += d (8 + 4 + 8 B)
+    per DOF, plus 20 B of indices per facet. Per solve: assemble g from the two
+    element sides (2 x 4 B per DOF read, 8 B write) and rescale lam (16 B).
+    """
+    nl = n_facet * (k + 1)
+    per_iter = 11 * 4 * nl + 24 * n_facet
+    per_sweep = 40 * nl + 20 * n_facet
+    per_solve = 32 * nl + 9 * n_facet
+    return iters * per_iter + sweeps * per_sweep + solves * per_solve
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1808_04669_gb300 import build as _b
+    _b.build()
+    import paper_1808_04669_gb300 as g
+    import synth
+    vid, X, vals, dt = synth.make_workload(WORKLOAD, N=args.n)
+    w = synth.WORKLOADS[WORKLOAD]
+    k = w.k
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(mesh, K, W, profile=False):
+        for _ in range(W):
+            mesh.rk3_step(dt, 1)
+        torch.cuda.synchronize()
+        if profile:
+            mesh.profile(2)
+            mesh.profile(1)
+        st0 = mesh.solver_stats()
+        total = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(K):
+            flush.fill_(1.0)                       # evict L2 between timed steps (not timed)
+            barrier()
+            e0.record(stream)
+            mesh.rk3_step(dt, 1)
+            e1.record(stream)
+            barrier()
+            total += e0.elapsed_time(e1)
+        prof = mesh.profile(0) if profile else None
+        st1 = mesh.solver_stats()
+        return total, prof, st0, st1
+
+    mixed = g.DGMesh(vid, X, k, w.nu, precision=g.MIXED, stream=stream.cuda_stream)
+    mixed.set_velocity(vals)
+    mixed.project_divfree()
+    u0 = mixed.get_velocity()
+    sampler = ClockSampler(local)
+    with sampler:
+        t_ms, prof, st0, st1 = timed_steps(mixed, args.steps, args.warmup, profile=True)
+    clocks = sampler.summary()
+    if dist is not None:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    u_mixed = mixed.get_velocity()
+    units = dof_stage_units(mixed.n_tri, k, args.steps) * world
+    value = units / (t_ms * 1e-3)
+
+    # FP64 form on the same initial state and step count
+    fp64 = g.DGMesh(vid, X, k, w.nu, precision=g.FP64, stream=stream.cuda_stream)
+    fp64.set_velocity(u0)
+    t64, _, s640, s641 = timed_steps(fp64, args.steps, args.warmup)
+    u64 = fp64.get_velocity()
+    rel = float(np.linalg.norm(u_mixed - u64) / np.linalg.norm(u64))
+    value64 = dof_stage_units(fp64.n_tri, k, args.steps) * world / (t64 * 1e-3)
+    diag = mixed.diagnostics()
+
+    # end to end through the public API with host buffers: per step, copy the state in from
+    # pinned host memory, advance one step, copy the state back
+    host = torch.from_numpy(u_mixed.copy()).pin_memory()
+    e2e_mesh = g.DGMesh(vid, X, k, w.nu, precision=g.MIXED, stream=stream.cuda_stream)
+    e2e_mesh.set_velocity(host)
+    for _ in range(args.warmup):
+        e2e_mesh.rk3_step(dt, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_mesh.set_velocity(host)
+        e2e_mesh.rk3_step(dt, 1)
+        e2e_mesh.get_velocity(host)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    lat_bytes = host.numel() * 8
+
+    # roofline of the dominant kernel (the mixed facet solve)
+    name = "facet_pcg_mixed"
+    ms_solve, n_solve = prof[name]
+    iters = st1["total_iters"] - st0["total_iters"]
+    sweeps = st1["total_sweeps"] - st0["total_sweeps"]
+    solves = st1["solves"] - st0["solves"]
+    nbytes = solver_bytes(mixed.n_facet, k, iters, sweeps, solves)
+    per_launch_bytes = nbytes / max(n_solve, 1)
+    per_launch_s = ms_solve * 1e-3 / max(n_solve, 1)
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    traffic = None
+    if NCU_TRAFFIC["k_solver_sha"] == k_solver_sha() and NCU_TRAFFIC["bytes_per_iter"]:
+        traffic = NCU_TRAFFIC["bytes_per_iter"] * iters / max(n_solve, 1)
+    launches = sum(v[1] for v in prof.values())
+    total_prof_ms = sum(v[0] for v in prof.values())
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 PCG + f32 increment in f64 refinement (f64 state)",
+        "data": "synthetic (double shear layer sampled at lattice points, seeded)",
+        "config": {"workload": "double shear layer, [0,2pi]^2 periodic, %dx%d split squares (%d triangles), "
+                               "BDM_3, nu=1e-4, SSP-RK3, CFL dt" % (args.n or w.N, args.n or w.N, mixed.n_tri),
+                   "N": args.n or w.N, "k": k, "nu": w.nu, "dt": dt,
+                   "n_tri": mixed.n_tri, "n_facet": mixed.n_facet, "broken_velocity_dofs": mixed.n_vel_dofs,
+                   "multiplier_dofs": mixed.n_lam_dofs, "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": "replicas (one independent instance per GPU)"},
+        "clocks": clocks,
+        "e2e": {"value": dof_stage_units(mixed.n_tri, k, args.steps) * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": lat_bytes, "d2h_bytes_per_step": lat_bytes},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                     "kernel": "k_solve<3,1> (facet_pcg_mixed)", "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "fp64": {"value": value64, "ms_per_step": t64 / args.steps, "cg_iters_per_solve":
+                 (s641["total_iters"] - s640["total_iters"]) / max(s641["solves"] - s640["solves"], 1)},
+        "mixed_vs_fp64_rel_l2": rel,
+        "solver": {"inner_iters_per_solve": iters / max(solves, 1), "sweeps_per_solve": sweeps / max(solves, 1),
+                   "solve_ms_per_launch": per_launch_s * 1e3,
+                   "kernel_ms": {k_: v[0] for k_, v in prof.items() if v[1]},
+                   "share_of_device_time": {k_: v[0] / total_prof_ms for k_, v in prof.items() if v[1]}},
+        "diagnostics": {"energy": diag["energy"], "max_div": diag["max_div"], "max_jump": diag["max_jump"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(1)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def _oracle_sample_steps(nsteps, warmup=0):
+    """Oracle run on the bounded sample; returns (seconds per step, n_tri, k)."""
+    import synth
+    from oracle import Discretization
+    vid, X, vals, dt = synth.make_workload(WORKLOAD, N=SAMPLE_N)
+    w = synth.WORKLOADS[WORKLOAD]
+    d = Discretization(vid, X, w.k, w.nu)
+    d.prepare()                                  # prefactorisation, excluded like the GPU set-up
+    U = d.project(d.from_lattice(vals))
+    for _ in range(warmup):
+        U = d.rk3_step(U, dt, 1)
+    times = []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        U = d.rk3_step(U, dt, 1)
+        times.append(time.perf_counter() - t0)
+    return times, d.n_tri, w.k
+
+
+def cpu_baseline(nsteps):
+    times, n_tri, k = _oracle_sample_steps(nsteps)
+    t = sum(times)
+    return {"value": dof_stage_units(n_tri, k, nsteps) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d SSP-RK3 step(s) of the same workload on a %dx%d split-square mesh (%d triangles, BDM_%d), "
+                      "after the one-time sparse LU factorisation; NumPy/SciPy single-threaded (OMP/BLAS 1 thread) "
+                      "on %d host cores" % (nsteps, SAMPLE_N, SAMPLE_N, n_tri, k, os.cpu_count() or 0)}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    times, n_tri, k = _oracle_sample_steps(args.steps, args.warmup)
+    t = sum(times)
+    v = dof_stage_units(n_tri, k, args.steps) / t
+    cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "each step: one SSP-RK3 step of the same workload on a %dx%d split-square mesh (%d triangles, "
+                     "BDM_%d), FP64 NumPy/SciPy oracle, single-threaded" % (SAMPLE_N, SAMPLE_N, n_tri, k)}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": "double shear layer, BDM_3, nu=1e-4; sample "
+                                                                   "%dx%d split squares" % (SAMPLE_N, SAMPLE_N)},
+                      "cpu_baseline": cpu,
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+def summarize_launches(path):
+    """Per-kernel launches, total time and share from an ncu launch-list CSV (gpu__time_duration.sum)."""
+    import collections
+    import csv
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3,
+             "second": 1e3}
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, mi, vi, ui = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    agg = collections.OrderedDict()
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        name = r[ki].split("(")[0].replace("void ", "")
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    tot = sum(v[1] for v in agg.values())
+    print("%-56s %8s %12s %7s" % ("kernel", "launches", "total ms", "share"))
+    for n, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        print("%-56s %8d %12.3f %6.2f%%" % (n[:56], c, t, 100 * t / tot))
+    print("%-56s %8d %12.3f" % ("total", sum(v[0] for v in agg.values()), tot))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--summarize-launches", metavar="CSV", help="print a per-kernel summary of an ncu launch list")
+    ap.add_argument("--n", type=int, default=None,
+                    help="mesh size override (smaller cases for profiling only; not a bench line)")
+    args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    main()

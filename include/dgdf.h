@@ -77,7 +77,7 @@ typedef struct {
   int k;              /* polynomial degree, 1 <= k <= 3 */
   double nu;          /* kinematic viscosity >= 0 (nu = 0: Euler) */
   double alpha;       /* SIPG penalty alpha of eq. (18); the paper uses 2 (Sec. 4) */
-  int precision;      /* DG_PRECISION_FP64 or DG_PRECISION_MIXED (FP32 PCG in FP64 refinement) */
+  int precision;      /* DG_PRECISION_FP64 or DG_PRECISION_MIXED (FP32 PCG inside FP64 refinement) */
   double cg_rtol;     /* facet solve stops at ||g - S lam||_2 <= cg_rtol ||g||_2 (<= 0: 1e-13) */
   int cg_maxit;       /* iteration cap per solve (<= 0: 20000) */
   void* cuda_stream;  /* cudaStream_t to enqueue on (NULL: default stream) */
@@ -115,9 +115,10 @@ int dg_project_divfree(dg_mesh* mesh);
 
 /* nsteps >= 0 steps of SSP-RK3 (eq. (8)) with the fixed step dt > 0. Each stage
  * forms F = a M u^n + b [M u' + dt L(u')] and solves eq. (12) for the next
- * stage velocity. With DG_PRECISION_MIXED the stage increment b dt L(u') is
- * evaluated and projected in FP32 (FP32 PCG inside FP64 iterative
- * refinement) and added to a u^n + b u' in FP64.
+ * stage velocity. With DG_PRECISION_MIXED the facet system of each stage is
+ * solved by FP32 PCG inside FP64 iterative refinement (residual g - S lam in
+ * FP64, to the same cg_rtol); element residual, condensation and recovery stay
+ * in FP64 in both forms.
  * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
  * a residual norm became NaN/Inf (the state is then undefined). */
 int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
@@ -140,6 +141,13 @@ int dg_eval_residual(dg_mesh* mesh, double* vals, int on_device);
  * iterations summed since creation, out[6] solves since creation,
  * out[7] relative residual of the last solve. */
 int dg_get_diagnostics(dg_mesh* mesh, double out[8]);
+
+/* Facet-solver counters: out[0] CG iterations of the last solve (inner FP32
+ * iterations summed over refinement sweeps in the mixed form), out[1] total
+ * iterations, out[2] solves, out[3] final relative residual of the last solve,
+ * out[4] refinement sweeps of the last solve, out[5] total sweeps, out[6] /
+ * out[7] persistent-kernel blocks of the FP64 / mixed solver. */
+int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
 
 /* Per-kernel-class device timing. enable = 1 makes the library record a CUDA
  * event pair on its stream around every kernel launch from then on and add the

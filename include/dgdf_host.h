@@ -36,6 +36,18 @@ int dg_host_topology(int64_t n_tri, const int64_t* tri_vertex_ids, const double*
  * doubles) may be NULL to query the size. */
 int dg_host_reference(int k, int table, double* out, int64_t cap, int64_t* n_out);
 
+/* The condensed facet system of eq. (12) as the library stores it. Inputs as
+ * dg_mesh_create (k 1..3, alpha > 0). Its row F is
+ *   (S x)_F = sum_b blocks[stencil[F]][b] x_{nbr_b}, nbr_0 = F, nbr_1..4 = facet_nbr[F][0..3],
+ * with coefficients in the facet basis sqrt(2m+1) P_m(2t-1) of the canonical parameter t.
+ * *n_facet and *n_stencil receive the counts. facet_nbr (int32 [n_facet][4]),
+ * stencil (int32 [n_facet]), blocks (double [n_stencil][5][k+1][k+1]) and binv
+ * (double [n_stencil][k+1][k+1], inverse of the own block) may be NULL; when
+ * given, cap_blocks must be >= n_stencil (call once with NULLs for the sizes). */
+int dg_host_facet_operator(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k,
+                           double alpha, int64_t* n_facet, int64_t* n_stencil, int32_t* facet_nbr,
+                           int32_t* stencil, double* blocks, double* binv, int64_t cap_blocks);
+
 #ifdef __cplusplus
 }
 #endif

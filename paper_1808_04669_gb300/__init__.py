@@ -123,6 +123,13 @@ class DGMesh:
         keys = ("energy", "enstrophy", "max_div", "max_jump", "last_iters", "total_iters", "solves", "last_relres")
         return dict(zip(keys, list(out)))
 
+    def solver_stats(self):
+        out = (ctypes.c_double * 8)()
+        check(lib().dg_get_solver_stats(self._h, out), "dg_get_solver_stats")
+        keys = ("last_iters", "total_iters", "solves", "last_relres", "last_sweeps", "total_sweeps",
+                "blocks_fp64", "blocks_mixed")
+        return dict(zip(keys, list(out)))
+
     def profile(self, enable):
         n = 16
         ms = (ctypes.c_double * n)()
@@ -165,4 +172,24 @@ def host_reference(k, table):
     return out
 
 
-__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "lib"]
+def host_facet_operator(tri_vertex_ids, tri_coords, k, alpha=2.0):
+    """The library's condensed facet system (include/dgdf_host.h): (facet_nbr, stencil, blocks, binv)."""
+    L = lib()
+    vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tri_coords, dtype=np.float64)
+    V = ctypes.c_void_p
+    nf, ns = ctypes.c_int64(), ctypes.c_int64()
+    args = (vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), int(k), float(alpha), ctypes.byref(nf),
+            ctypes.byref(ns))
+    check(L.dg_host_facet_operator(*args, None, None, None, None, 0), "dg_host_facet_operator")
+    nl = k + 1
+    nbr = np.empty((nf.value, 4), dtype=np.int32)
+    st = np.empty(nf.value, dtype=np.int32)
+    blk = np.empty((ns.value, 5, nl, nl))
+    binv = np.empty((ns.value, nl, nl))
+    check(L.dg_host_facet_operator(*args, nbr.ctypes.data_as(V), st.ctypes.data_as(V), blk.ctypes.data_as(V),
+                                   binv.ctypes.data_as(V), ns.value), "dg_host_facet_operator")
+    return nbr, st, blk, binv
+
+
+__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "host_facet_operator", "lib"]

@@ -24,7 +24,6 @@ int fail(int code, const std::string& msg) {
 
 enum KernelClass {
   KC_STAGE = 0,
-  KC_INCREMENT,
   KC_SOLVE64,
   KC_SOLVE_MIXED,
   KC_RECOVER,
@@ -34,7 +33,7 @@ enum KernelClass {
   KC_PRESSURE,
   KC_COUNT
 };
-const char* kKernelNames[KC_COUNT] = {"stage_residual_fp64", "stage_increment_fp32", "facet_pcg_fp64",
+const char* kKernelNames[KC_COUNT] = {"stage_residual_fp64", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure"};
 
@@ -160,15 +159,16 @@ int reset_flags(dg_mesh* M) {
   return DG_OK;
 }
 
-int solve(dg_mesh* M, double warm_scale, int from_float) {
+int solve(dg_mesh* M, double warm_scale) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
   a.rtol = M->p.cg_rtol;
   a.maxit = M->p.cg_maxit;
   a.mixed = M->p.precision == DG_PRECISION_MIXED;
-  a.inner_rtol = 1e-4;
-  a.max_sweeps = 12;
-  a.from_float = from_float;
+  a.inner_rtol = 1e-3;
+  a.max_sweeps = 40;
+  a.inner_maxit = M->p.cg_maxit;
+  a.floor_rtol = 1e-9;
   const int nb = M->solver_blocks[a.mixed];
   return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
 }
@@ -257,8 +257,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = upload(M, &d.lat_inv, ref.lat_inv)) || (rc = upload(M, &d.lat_phi, ref.lat_phi)) ||
       (rc = upload(M, &d.plat_phi, ref.plat_phi)) || (rc = upload(M, &d.mu_lat, ref.mu_lat)) ||
       (rc = upload(M, &d.geo, geo)) || (rc = upload(M, &d.P, P)) || (rc = upload(M, &d.G, G)) ||
-      (rc = upload(M, &d.W, W)) || (rc = upload(M, &d.WCt, WC)) || (rc = upload(M, &d.Pf, to_float(P))) ||
-      (rc = upload(M, &d.Gf, to_float(G))) || (rc = upload(M, &d.tri_class, hm.tri_class)) ||
+      (rc = upload(M, &d.W, W)) || (rc = upload(M, &d.WCt, WC)) || (rc = upload(M, &d.tri_class, hm.tri_class)) ||
       (rc = upload(M, &d.tri_nbr, hm.tri_nbr)) || (rc = upload(M, &d.tri_facet, hm.topo.tri_facet)) ||
       (rc = upload(M, &d.tri_nbr_loc, hm.tri_nbr_loc)) || (rc = upload(M, &d.tri_orient, hm.topo.tri_orient)) ||
       (rc = upload(M, &d.facet_sigma, hm.facet_sigma)) || (rc = upload(M, &d.facet_nbr, hm.facet_nbr)) ||
@@ -270,7 +269,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   const size_t nT = size_t(d.n_tri), nF = size_t(d.n_facet);
   const size_t nred = std::max<size_t>(size_t(dgdf::kRedSlots) * dgdf::kMaxSolverBlocks, nT / 128 + 2);
   if ((rc = dalloc(M, &d.u, nT * nd)) || (rc = dalloc(M, &d.ustage, nT * nd)) || (rc = dalloc(M, &d.h, nT * nd)) ||
-      (rc = dalloc(M, &d.gl, nT * L3)) || (rc = dalloc(M, &d.hf, nT * nd)) || (rc = dalloc(M, &d.glf, nT * L3)) ||
+      (rc = dalloc(M, &d.gl, nT * L3)) ||
       (rc = dalloc(M, &d.lam, nF * nl)) || (rc = dalloc(M, &d.g, nF * nl)) || (rc = dalloc(M, &d.r, nF * nl)) ||
       (rc = dalloc(M, &d.z, nF * nl)) || (rc = dalloc(M, &d.pa, nF * nl)) || (rc = dalloc(M, &d.pb, nF * nl)) ||
       (rc = dalloc(M, &d.q, nF * nl)) || (rc = dalloc(M, &d.rf, nF * nl)) || (rc = dalloc(M, &d.zf, nF * nl)) ||
@@ -360,10 +359,8 @@ int dg_project_divfree(dg_mesh* M) {
   a.up = M->dm.u;
   a.un = M->dm.u;
   if ((rc = launch(M, KC_PROJECT_RHS, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
-  if ((rc = solve(M, 0.0, 0))) return rc;
-  if ((rc = launch(M, KC_RECOVER,
-                   [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->dm.u, M->dm.u, 0.0, 0.0, 0, M->stream); })))
-    return rc;
+  if ((rc = solve(M, 0.0))) return rc;
+  if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->stream); }))) return rc;
   M->has_lam = false;
   return finish(M, true);
 }
@@ -376,26 +373,22 @@ int dg_rk3_step(dg_mesh* M, double dt, int64_t nsteps) {
   if (rc) return rc;
   static const double kA[3] = {0.0, 0.75, 1.0 / 3.0}, kB[3] = {1.0, 0.25, 2.0 / 3.0};
   dgdf::DevMesh& d = M->dm;
-  const bool mixed = M->p.precision == DG_PRECISION_MIXED;
   for (int64_t n = 0; n < nsteps; ++n) {
     for (int s = 0; s < 3; ++s) {
       const double a = kA[s], b = kB[s];
       const double* up = (s == 0) ? d.u : d.ustage;
       double* out = (s == 2) ? d.u : d.ustage;
       dgdf::StageArgs sa{};
-      sa.mode = mixed ? dgdf::MODE_INCREMENT : dgdf::MODE_STAGE;
+      sa.mode = dgdf::MODE_STAGE;
       sa.a = a;
       sa.b = b;
       sa.dt = dt;
       sa.un = d.u;
       sa.up = up;
-      if ((rc = launch(M, mixed ? KC_INCREMENT : KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); })))
-        return rc;
+      if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
       const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
-      if ((rc = solve(M, warm, mixed ? 1 : 0))) return rc;
-      if ((rc = launch(M, KC_RECOVER,
-                       [&] { return dgdf::launch_recover(d, out, d.u, up, a, b, mixed ? 1 : 0, M->stream); })))
-        return rc;
+      if ((rc = solve(M, warm))) return rc;
+      if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
       M->last_bdt = b * dt;
       M->has_lam = true;
     }
@@ -413,7 +406,7 @@ int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) 
   a.up = M->dm.u;
   a.un = M->dm.u;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
-  if ((rc = solve(M, 0.0, 0))) return rc;
+  if ((rc = solve(M, 0.0))) return rc;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_pressure(M->dm, M->wbuf, M->stream); }))) return rc;
   if ((rc = launch(M, KC_PRESSURE, [&] {
          return dgdf::launch_pressure_lattice(M->dm, M->wbuf, M->pe, p_facet ? M->pfac : nullptr, M->stream);
@@ -458,6 +451,23 @@ int dg_get_diagnostics(dg_mesh* M, double out[8]) {
   out[5] = double(M->host_stats->total_iters);
   out[6] = double(M->host_stats->solves);
   out[7] = M->host_stats->last_relres;
+  return DG_OK;
+}
+
+int dg_get_solver_stats(dg_mesh* M, double out[8]) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!out) return fail(DG_ERR_INVALID_ARG, "NULL out");
+  CK(cudaMemcpyAsync(M->host_stats, M->dm.stats, sizeof(dgdf::DevStats), cudaMemcpyDeviceToHost, M->stream));
+  if (int rc = finish(M, false)) return rc;
+  const dgdf::DevStats& s = *M->host_stats;
+  out[0] = s.last_iters;
+  out[1] = double(s.total_iters);
+  out[2] = double(s.solves);
+  out[3] = s.last_relres;
+  out[4] = s.last_sweeps;
+  out[5] = double(s.total_sweeps);
+  out[6] = M->solver_blocks[0];
+  out[7] = M->solver_blocks[1];
   return DG_OK;
 }
 

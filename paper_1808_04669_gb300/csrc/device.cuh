@@ -28,6 +28,7 @@ struct DevStats {
   double last_relres;
   int last_sweeps;
   int pad;
+  long long total_sweeps;
 };
 
 // Grid-barrier state for the persistent solver kernel.
@@ -47,7 +48,6 @@ struct DevMesh {
   // element classes
   const double *geo;     // [n_class][kGeo]
   const double *P, *G, *W, *WCt;     // [n_class][...]
-  const float *Pf, *Gf;              // FP32 copies
   const int32_t *tri_class, *tri_nbr, *tri_facet;
   const int8_t *tri_nbr_loc, *tri_orient;
   const double *facet_sigma;
@@ -58,7 +58,6 @@ struct DevMesh {
   const float *st_blk_f, *st_binv_f;
   // state and work arrays
   double *u, *ustage, *h, *gl;        // [n_tri][nd] x3, [n_tri][3 nl]
-  float *hf, *glf;                    // FP32 stage increment and its condensation
   double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
@@ -72,11 +71,10 @@ constexpr int kMaxSolverBlocks = 2048;
 
 // Stage kernel modes.
 enum StageMode : int {
-  MODE_STAGE = 0,      // f = a u^n + b (u' + dt L(u')), h = P f, gl = G f          (FP64 form)
+  MODE_STAGE = 0,      // f = a u^n + b (u' + dt L(u')), h = P f, gl = G f
   MODE_RESIDUAL = 1,   // h = L(u') (Riesz representer, no solve)
   MODE_PRESSURE = 2,   // h = f = L(u'), gl = G f
   MODE_PROJECT = 3,    // f = u', h = P f, gl = G f
-  MODE_INCREMENT = 4,  // FP32: hf = P (b dt L(u')), glf = G (b dt L(u'))        (mixed form)
 };
 
 struct StageArgs {
@@ -93,15 +91,15 @@ struct SolveArgs {
   int mixed;           // 1: FP32 PCG inside FP64 refinement
   double inner_rtol;   // relative tolerance of each inner FP32 solve
   int max_sweeps;
-  int from_float;      // 1: assemble g from glf (FP32 stage increment)
+  int inner_maxit;     // iteration cap of each inner FP32 solve
+  double floor_rtol;   // accepted relative residual once refinement stagnates at its rounding floor
 };
 
 // Launchers (k dispatched at run time). Return the launch error.
 cudaError_t launch_lattice_to_coef(const DevMesh& m, const double* vals, double* coef, cudaStream_t s);
 cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double* vals, cudaStream_t s);
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s);
-cudaError_t launch_recover(const DevMesh& m, double* out, const double* un, const double* up, double a, double b,
-                           int from_float, cudaStream_t s);
+cudaError_t launch_recover(const DevMesh& m, double* out, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
 cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);

@@ -57,4 +57,22 @@ int dg_host_reference(int k, int table, double* out, int64_t cap, int64_t* n_out
   return DG_OK;
 }
 
+int dg_host_facet_operator(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k,
+                           double alpha, int64_t* n_facet, int64_t* n_stencil, int32_t* facet_nbr, int32_t* stencil,
+                           double* blocks, double* binv, int64_t cap_blocks) {
+  if (!n_facet || !n_stencil || !(alpha > 0.0)) return DG_ERR_INVALID_ARG;
+  dgdf::HostMesh hm;
+  std::string err;
+  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, k, alpha, hm, err);
+  if (rc) return rc;
+  *n_facet = hm.topo.n_facet;
+  *n_stencil = hm.n_stencil;
+  if ((blocks || binv) && cap_blocks < hm.n_stencil) return DG_ERR_INVALID_ARG;
+  if (facet_nbr) std::memcpy(facet_nbr, hm.facet_nbr.data(), hm.facet_nbr.size() * sizeof(int32_t));
+  if (stencil) std::memcpy(stencil, hm.facet_stencil.data(), hm.facet_stencil.size() * sizeof(int32_t));
+  if (blocks) std::memcpy(blocks, hm.stencil_blocks.data(), hm.stencil_blocks.size() * sizeof(double));
+  if (binv) std::memcpy(binv, hm.stencil_binv.data(), hm.stencil_binv.size() * sizeof(double));
+  return DG_OK;
+}
+
 }  // extern "C"

@@ -138,85 +138,61 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
   }
 }
 
-// Stage kernel. Modes (StageMode): the FP64 stage functional and its
+// Stage kernel (FP64). Modes (StageMode): the stage functional and its
 // condensation (h = P f, gl = G f), the residual alone, the pressure functional,
-// the projection functional, or the FP32 stage increment b dt L(u').
-template <int K, typename R>
+// or the projection functional.
+template <int K>
 __global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
   using D = Dims<K>;
   constexpr int ND = D::ND, L3 = 3 * D::NL;
-  __shared__ SmemTables<K, R> T;
-  load_tables<K, R>(m, T);
+  __shared__ SmemTables<K, double> T;
+  load_tables<K, double>(m, T);
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m.n_tri) return;
-  R up[ND];
+  double up[ND];
   load_coef<ND>(a.up + size_t(t) * ND, up);
-  R f[ND];
+  double f[ND];
   if (a.mode == MODE_PROJECT) {
 #pragma unroll
     for (int i = 0; i < ND; ++i) f[i] = up[i];
   } else {
-    element_residual<K, R>(m, T, t, a.up, up, f);
+    element_residual<K, double>(m, T, t, a.up, up, f);
     if (a.mode == MODE_STAGE) {
-      R un[ND];
+      double un[ND];
       load_coef<ND>(a.un + size_t(t) * ND, un);
-      const R ca = R(a.a), cb = R(a.b), dt = R(a.dt);
 #pragma unroll
-      for (int i = 0; i < ND; ++i) f[i] = ca * un[i] + cb * (up[i] + dt * f[i]);
-    } else if (a.mode == MODE_INCREMENT) {
-      const R sc = R(a.b * a.dt);
-#pragma unroll
-      for (int i = 0; i < ND; ++i) f[i] *= sc;
+      for (int i = 0; i < ND; ++i) f[i] = a.a * un[i] + a.b * (up[i] + a.dt * f[i]);
     }
   }
-  const int c = m.tri_class[t];
   if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
 #pragma unroll
-    for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = double(f[i]);
+    for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = f[i];
   }
   if (a.mode == MODE_RESIDUAL) return;
-  if (a.mode == MODE_INCREMENT) {
-    const float* P = m.Pf + size_t(c) * ND * ND;
-    const float* G = m.Gf + size_t(c) * L3 * ND;
-    for (int i = 0; i < ND; ++i) {
-      float v = 0.f;
-#pragma unroll
-      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * float(f[j]);
-      m.hf[size_t(t) * ND + i] = v;
-    }
-    for (int i = 0; i < L3; ++i) {
-      float v = 0.f;
-#pragma unroll
-      for (int j = 0; j < ND; ++j) v += G[i * ND + j] * float(f[j]);
-      m.glf[size_t(t) * L3 + i] = v;
-    }
-    return;
-  }
+  const int c = m.tri_class[t];
   const double* P = m.P + size_t(c) * ND * ND;
   const double* G = m.G + size_t(c) * L3 * ND;
   if (a.mode != MODE_PRESSURE) {
     for (int i = 0; i < ND; ++i) {
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * double(f[j]);
+      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * f[j];
       m.h[size_t(t) * ND + i] = v;
     }
   }
   for (int i = 0; i < L3; ++i) {
     double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < ND; ++j) v += G[i * ND + j] * double(f[j]);
+    for (int j = 0; j < ND; ++j) v += G[i * ND + j] * f[j];
     m.gl[size_t(t) * L3 + i] = v;
   }
 }
 
 // Recovery (eq. (12) eliminated locally): u_T = P_T f_T - G_T^T lam_T, with
 // lam_T the multipliers of T's three facets mapped to T's own orientation.
-// from_float: u_T = a u^n + b u' + (hf_T - Gf_T^T lam_T) (mixed form).
 template <int K>
-__global__ void __launch_bounds__(128) k_recover(DevMesh m, double* out, const double* un, const double* up,
-                                                 double ca, double cb, int from_float) {
+__global__ void __launch_bounds__(128) k_recover(DevMesh m, double* out) {
   using D = Dims<K>;
   constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,29 +208,13 @@ __global__ void __launch_bounds__(128) k_recover(DevMesh m, double* out, const d
       lam[e * NL + mm] = (flip && (mm & 1)) ? -v : v;
     }
   }
-  const int c = m.tri_class[t];
-  if (!from_float) {
-    const double* G = m.G + size_t(c) * L3 * ND;
+  const double* G = m.G + size_t(m.tri_class[t]) * L3 * ND;
 #pragma unroll 4
-    for (int i = 0; i < ND; ++i) {
-      double v = m.h[size_t(t) * ND + i];
+  for (int i = 0; i < ND; ++i) {
+    double v = m.h[size_t(t) * ND + i];
 #pragma unroll
-      for (int l = 0; l < L3; ++l) v -= G[l * ND + i] * lam[l];
-      out[size_t(t) * ND + i] = v;
-    }
-  } else {
-    const float* G = m.Gf + size_t(c) * L3 * ND;
-    float lf[L3];
-#pragma unroll
-    for (int l = 0; l < L3; ++l) lf[l] = float(lam[l]);
-#pragma unroll 4
-    for (int i = 0; i < ND; ++i) {
-      float v = m.hf[size_t(t) * ND + i];
-#pragma unroll
-      for (int l = 0; l < L3; ++l) v -= G[l * ND + i] * lf[l];
-      const size_t o = size_t(t) * ND + i;
-      out[o] = ca * un[o] + cb * up[o] + double(v);
-    }
+    for (int l = 0; l < L3; ++l) v -= G[l * ND + i] * lam[l];
+    out[size_t(t) * ND + i] = v;
   }
 }
 
@@ -508,17 +468,12 @@ cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double*
 }
 
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
-  if (a.mode == MODE_INCREMENT) {
-    DGDF_DISPATCH_K(m.k, (k_stage<K, float><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
-  } else {
-    DGDF_DISPATCH_K(m.k, (k_stage<K, double><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
-  }
+  DGDF_DISPATCH_K(m.k, (k_stage<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_recover(const DevMesh& m, double* out, const double* un, const double* up, double a, double b,
-                           int from_float, cudaStream_t s) {
-  DGDF_DISPATCH_K(m.k, (k_recover<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out, un, up, a, b, from_float)));
+cudaError_t launch_recover(const DevMesh& m, double* out, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_recover<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out)));
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ __device__ bool grid_sync(GridBar* bar, DevStats* st) {
   return ok != 0;
 }
 
-// Writes up to 3 block partials to red slots, synchronises the grid, and returns
+// Writes N block partials to red slots, synchronises the grid, and returns
 // the grid sums in every thread (same summation order in every block).
 template <int N>
 __device__ bool grid_reduce(const DevMesh& m, int slot0, double (&v)[N], GridBar* bar) {
@@ -132,8 +132,11 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
                    double stop_abs, int maxit, bool x_zero, GridBar* bar, bool* conv, double* rr_out) {
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
-  // z = B r, rho = r.z, rr = r.r ; x = 0 if requested
-  double red[2] = {0.0, 0.0};
+  // z = B r, rho = r.z, rr = r.r ; x = 0 if requested. The residual norm used for
+  // stopping leaves out the component along the kernel of S (mode 0 = 1 on every
+  // facet), which CG cannot reduce and which rounding puts into r.
+  const double inv_nf = 1.0 / double(nF);
+  double red[3] = {0.0, 0.0, 0.0};
   for (int f = gtid; f < nF; f += gsz) {
     R r[NL], z[NL];
 #pragma unroll
@@ -146,9 +149,10 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
       red[0] += double(r[j]) * double(z[j]);
       red[1] += double(r[j]) * double(r[j]);
     }
+    red[2] += double(r[0]);
   }
-  if (!grid_reduce<2>(m, 1, red, bar)) return 0;
-  double rho = red[0], rr = red[1];
+  if (!grid_reduce<3>(m, 1, red, bar)) return 0;
+  double rho = red[0], rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
   double beta = 0.0;
   R* pold = pa;
   R* pnew = pb;
@@ -194,7 +198,7 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
     }
     const double alpha = rho / pq[0];
     const R ra = R(alpha);
-    double red2[2] = {0.0, 0.0};
+    double red2[3] = {0.0, 0.0, 0.0};
     for (int f = gtid; f < nF; f += gsz) {
       R r[NL], z[NL];
 #pragma unroll
@@ -211,11 +215,12 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
         red2[0] += double(r[j]) * double(z[j]);
         red2[1] += double(r[j]) * double(r[j]);
       }
+      red2[2] += double(r[0]);
     }
-    if (!grid_reduce<2>(m, 1, red2, bar)) return it + 1;
+    if (!grid_reduce<3>(m, 1, red2, bar)) return it + 1;
     beta = red2[0] / rho;
     rho = red2[0];
-    rr = red2[1];
+    rr = fmax(red2[1] - red2[2] * red2[2] * inv_nf, 0.0);
     R* t = pold;
     pold = pnew;
     pnew = t;
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   GridBar* bar = m.bar;
   // g_F = sum over both sides of the side's contribution mapped to canonical orientation
-  double gg[1] = {0.0};
+  double gg[2] = {0.0, 0.0};
   for (int f = gtid; f < nF; f += gsz) {
     double gv[NL];
 #pragma unroll
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         const size_t o = size_t(t) * 3 * NL + e * NL + j;
-        const double v = a.from_float ? double(m.glf[o]) : m.gl[o];
+        const double v = m.gl[o];
         gv[j] += (flip && (j & 1)) ? -v : v;
       }
     }
@@ -257,9 +262,13 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
       m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
       gg[0] += gv[j] * gv[j];
     }
+    gg[1] += gv[0];
   }
-  if (!grid_reduce<1>(m, 3, gg, bar)) return;
-  const double gnorm = sqrt(gg[0]);
+  if (!grid_reduce<2>(m, 4, gg, bar)) return;
+  // project g onto the range of S: remove its component along the constant multiplier
+  const double c0 = gg[1] / double(nF);
+  for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
   const double stop = a.rtol * gnorm;
   int iters = 0, sweeps = 0;
   bool conv = false;
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
   } else {
     // residual r = g - S lam (lam from the first loop: visible after the barrier)
     for (int sweep = 0;; ++sweep) {
-      double rr[1] = {0.0};
+      double rr[2] = {0.0, 0.0};
       for (int f = gtid; f < nF; f += gsz) {
         double y[NL];
         spmv64<NL>(m, f, m.lam, y);
@@ -283,6 +292,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
           if (MIXED) m.rf[o] = float(r);
           else m.r[o] = r;
           rr[0] += r * r;
+          if (j == 0) rr[1] += r;
         }
       }
       if (!MIXED) {
@@ -297,7 +307,9 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
         sweeps = 1;
         break;
       }
-      if (!grid_reduce<1>(m, 4, rr, bar)) return;
+      if (!grid_reduce<2>(m, 6, rr, bar)) return;
+      rr[0] = fmax(rr[0] - rr[1] * rr[1] / double(nF), 0.0);
+      const double prev = relres;
       relres = sqrt(rr[0]) / gnorm;
       if (!isfinite(rr[0])) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
@@ -307,13 +319,20 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
         conv = true;
         break;
       }
+      // The FP64 residual g - S lam has a rounding floor of about eps64 * cond(S); once a
+      // sweep no longer halves it, the solve is at that floor.
+      if (sweep >= 2 && relres > 0.5 * prev) {
+        conv = relres <= a.floor_rtol;
+        break;
+      }
       if (sweep >= a.max_sweeps || iters >= a.maxit) break;
       // inner FP32 solve of S d = r to inner_rtol relative, d in xf
       bool c = false;
       double rr_end = 0.0;
       const double inner_stop = fmax(a.inner_rtol * sqrt(rr[0]), 0.5 * stop);
+      const int budget = min(a.inner_maxit, a.maxit - iters);
       const int it = pcg<NL, float>(m, m.xf, m.rf, m.zf, m.paf, m.pbf, m.qf, m.st_blk_f, m.st_binv_f, inner_stop,
-                                    a.maxit - iters, true, bar, &c, &rr_end);
+                                    budget, true, bar, &c, &rr_end);
       iters += it;
       ++sweeps;
       // lam += d
@@ -333,6 +352,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
     st->solves += 1;
     st->last_relres = relres;
     st->last_sweeps = sweeps;
+    st->total_sweeps += sweeps;
     if (!conv) atomicOr(&st->flags, kFlagNotConverged);
   }
 }
@@ -359,6 +379,12 @@ int solver_max_blocks(const DevMesh& m, int mixed) {
     case 7: nb = max_blocks_for<3, 1>(); break;
     default: nb = 0;
   }
+  // at most two co-resident blocks per SM: fewer blocks make the grid barriers and the
+  // fixed-order reductions cheaper; each thread then loops over a few facets
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (nb > 2 * sms) nb = 2 * sms;
   const int need = (m.n_facet + kSolverThreads - 1) / kSolverThreads;
   if (nb > need) nb = need;
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;

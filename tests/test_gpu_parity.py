@@ -75,10 +75,11 @@ def test_residual_parity(g, N, k, nu, perturb):
     assert rel(gpu, ref) < TOL64
 
 
-def test_residual_parity_projected_field(g):
-    # divergence-free field: the upwind switch sees the same u.n on both sides
-    mesh, d, X = pair(g, 6, 3, 1e-3)
-    v = synth.sample_lattice(synth.double_shear_layer(), X, 3)
+@pytest.mark.parametrize("k", [2, 3])
+def test_residual_parity_projected_field(g, k):
+    # divergence-free field: u.n is continuous, so the upwind side is decided by the traces' average
+    mesh, d, X = pair(g, 6, k, 1e-3)
+    v = random_lattice(mesh.n_tri, k, 33)
     mesh.set_velocity(v)
     mesh.project_divfree()
     U = d.project(d.from_lattice(v))
@@ -199,13 +200,16 @@ def test_pressure_parity(g, N, k):
 
 
 def test_diagnostics_parity(g):
+    # integrals match; the normal jump is taken at the same facet Gauss points on both sides
+    # (the max of the divergence is over different volume point sets, so it is only bounded)
     mesh, d, X = pair(g, 5, 3, 0.0)
     v = random_lattice(mesh.n_tri, 3, 9)
     mesh.set_velocity(v)
     dg = mesh.diagnostics()
     ref = d.diagnostics(d.from_lattice(v))
-    for key in ("energy", "enstrophy", "max_div", "max_jump"):
+    for key in ("energy", "enstrophy", "max_jump"):
         assert abs(dg[key] - ref[key]) < 1e-12 * max(1.0, abs(ref[key])), key
+    assert 0.5 * ref["max_div"] < dg["max_div"] < 2.0 * ref["max_div"]
 
 
 # --------------------------------------------------------------- edge cases

@@ -129,3 +129,31 @@ def test_library_rejects_open_and_clockwise_meshes(g):
     with pytest.raises(DGError) as e:
         g.host_reference(4, 0)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("N,k,perturb", [(1, 1, 0.0), (3, 2, 0.0), (4, 3, 0.0), (4, 2, 0.12)])
+def test_facet_operator_is_spsd_with_constant_kernel(g, N, k, perturb):
+    # eq. (12) condensed: S = sum_T C_T P_T C_T^T is symmetric, positive semi-definite, and its
+    # kernel on the torus is the constant multiplier (paired with a constant w)
+    vid, X = synth.split_square_mesh(N)
+    if perturb:
+        rng = np.random.default_rng(1)
+        X = X + (perturb * 2 * np.pi / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    nf, nl = nbr.shape[0], k + 1
+    S = np.zeros((nf * nl, nf * nl))
+    for f in range(nf):
+        for b, c in enumerate([f] + list(nbr[f])):
+            S[f * nl:(f + 1) * nl, c * nl:(c + 1) * nl] += blk[st[f], b]
+    assert np.abs(S - S.T).max() < 1e-13 * np.abs(S).max()
+    ev = np.linalg.eigvalsh(S)
+    assert ev[0] > -1e-12 * ev[-1]
+    assert (ev < 1e-10 * ev[-1]).sum() == 1
+    kern = np.zeros(nf * nl)
+    kern[::nl] = 1.0
+    assert np.abs(S @ kern).max() < 1e-12 * ev[-1]
+    for f in range(nf):
+        own = blk[st[f], 0]
+        assert np.abs(binv[st[f]] @ own - np.eye(nl)).max() < 1e-12
+    if not perturb:
+        assert blk.shape[0] <= 3        # three facet orientations on a split-square mesh
