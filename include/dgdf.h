@@ -149,6 +149,31 @@ int dg_get_diagnostics(dg_mesh* mesh, double out[8]);
  * out[7] persistent-kernel blocks of the FP64 / mixed solver. */
 int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
 
+/* FP64 facet-system solve that allocates nothing, for callers that cannot call
+ * cudaMalloc at all (for example code that must run inside someone else's
+ * memory budget or pool, or in a context where allocation is forbidden), and
+ * so cannot create a dg_mesh. The paper has no counterpart: it is the same
+ * block-Jacobi PCG as the mesh solver (stop at ||g - S lam|| <= rtol ||g||
+ * with the constant-multiplier component left out), on an operator the caller
+ * holds. All pointers are device memory on the current device, owned by the
+ * caller: facet_nbr int32 [n_facet][4], stencil int32 [n_facet], blocks double
+ * [n_stencil][5][k+1][k+1], binv double [n_stencil][k+1][k+1] (the layout of
+ * dg_host_facet_operator), g double [n_facet][k+1], lam double [n_facet][k+1]
+ * (in: initial guess; out: solution, defined up to the constant multiplier).
+ * Work vectors, reductions, the grid barrier and counters live in one static
+ * device array sized for n_facet*(k+1) <= 262144 multiplier DOFs (about 12.7 MB,
+ * held by every GPU that loads the library until exit); larger sizes return
+ * DG_ERR_INVALID_ARG with a message and launch nothing. The first call on a
+ * device looks up that array's address (cudaGetSymbolAddress), so make the
+ * first call on each device before any stream capture. Every call shares the
+ * array: calls that overlap on the GPU (other streams, other threads) race.
+ * The call synchronises cuda_stream. *iterations and *relres (may be NULL)
+ * receive the CG iterations and final relative residual.
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_NONFINITE. */
+int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, const int32_t* stencil,
+                           const double* blocks, const double* binv, const double* g, double* lam, double rtol,
+                           int maxit, void* cuda_stream, int* iterations, double* relres);
+
 /* Per-kernel-class device timing. enable = 1 makes the library record a CUDA
  * event pair on its stream around every kernel launch from then on and add the
  * elapsed times up at the end of each call; enable = 0 stops recording,

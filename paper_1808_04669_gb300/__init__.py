@@ -192,4 +192,28 @@ def host_facet_operator(tri_vertex_ids, tri_coords, k, alpha=2.0):
     return nbr, st, blk, binv
 
 
-__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "host_facet_operator", "lib"]
+def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13, maxit=20000, stream=None):
+    """dg_facet_solve_noalloc on caller-owned CUDA tensors (torch); lam is updated in place.
+
+    For callers that cannot allocate: the library allocates nothing here (see include/dgdf.h).
+    Returns (iterations, relative residual).
+    """
+    import torch
+    for t, dt in ((facet_nbr, torch.int32), (stencil, torch.int32), (blocks, torch.float64), (binv, torch.float64),
+                  (g, torch.float64), (lam, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError("need contiguous CUDA tensors of the documented dtypes")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    V = ctypes.c_void_p
+    check(lib().dg_facet_solve_noalloc(int(k), int(facet_nbr.shape[0]), V(facet_nbr.data_ptr()), V(stencil.data_ptr()),
+                                       V(blocks.data_ptr()), V(binv.data_ptr()), V(g.data_ptr()), V(lam.data_ptr()),
+                                       float(rtol), int(maxit), V(int(stream)), ctypes.byref(it), ctypes.byref(rr)),
+          "dg_facet_solve_noalloc")
+    return it.value, rr.value
+
+
+__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "host_facet_operator", "facet_solve_noalloc",
+           "lib"]

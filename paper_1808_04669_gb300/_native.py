@@ -14,7 +14,7 @@ STATUS = {0: "DG_OK", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_U
           -5: "DG_ERR_NOT_CONVERGED", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_OOM"}
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
-           "dg_project_divfree", "dg_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_get_diagnostics", "dg_get_solver_stats",
+           "dg_project_divfree", "dg_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
            "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
            "dg_host_facet_operator"]
 
@@ -48,6 +48,7 @@ def lib():
         "dg_eval_residual": (ctypes.c_int, [P, P, ctypes.c_int]),
         "dg_get_diagnostics": (ctypes.c_int, [P, P]),
         "dg_get_solver_stats": (ctypes.c_int, [P, P]),
+        "dg_facet_solve_noalloc": (ctypes.c_int, [ctypes.c_int, I64, P, P, P, P, P, P, D, ctypes.c_int, P, P, P]),
         "dg_profile": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
         "dg_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "dg_last_error": (ctypes.c_char_p, []),

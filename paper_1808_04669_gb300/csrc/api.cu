@@ -471,6 +471,31 @@ int dg_get_solver_stats(dg_mesh* M, double out[8]) {
   return DG_OK;
 }
 
+int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, const int32_t* stencil,
+                           const double* blocks, const double* binv, const double* g, double* lam, double rtol,
+                           int maxit, void* cuda_stream, int* iterations, double* relres) {
+  g_err.clear();
+  if (k < 1 || k > dgdf::kMaxDegree) return fail(DG_ERR_UNSUPPORTED, "k must be 1..3");
+  if (!facet_nbr || !stencil || !blocks || !binv || !g || !lam) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  if (n_facet < 1) return fail(DG_ERR_INVALID_ARG, "n_facet must be >= 1");
+  const long long dofs = (long long)n_facet * (k + 1);
+  if (dofs > dgdf::noalloc_max_dofs())
+    return fail(DG_ERR_INVALID_ARG, "dg_facet_solve_noalloc: n_facet*(k+1) = " + std::to_string(dofs) +
+                                        " exceeds the static scratch limit of " +
+                                        std::to_string(dgdf::noalloc_max_dofs()) + " multiplier DOFs");
+  if (!(rtol > 0.0) || maxit < 1) return fail(DG_ERR_INVALID_ARG, "need rtol > 0 and maxit >= 1");
+  dgdf::DevStats st{};
+  cudaError_t e = dgdf::solve_noalloc(k, int(n_facet), facet_nbr, stencil, blocks, binv, g, lam, rtol, maxit,
+                                      static_cast<cudaStream_t>(cuda_stream), &st);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("dg_facet_solve_noalloc: ") + cudaGetErrorString(e));
+  if (iterations) *iterations = st.last_iters;
+  if (relres) *relres = st.last_relres;
+  if (st.flags & dgdf::kFlagBarrierTimeout) return fail(DG_ERR_CUDA, "solver grid barrier timed out");
+  if (st.flags & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
+  if (st.flags & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached maxit");
+  return DG_OK;
+}
+
 int dg_profile(dg_mesh* M, int enable, double* out_ms, int64_t* out_launches, int n) {
   if (int rc = check_mesh(M)) return rc;
   CK(cudaStreamSynchronize(M->stream));

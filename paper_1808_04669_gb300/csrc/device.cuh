@@ -106,5 +106,9 @@ cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
+long long noalloc_max_dofs();
+cudaError_t solve_noalloc(int k, int n_facet, const int32_t* facet_nbr, const int32_t* stencil, const double* blocks,
+                          const double* binv, const double* g, double* lam, double rtol, int maxit, cudaStream_t s,
+                          DevStats* host_stats);
 
 }  // namespace dgdf

@@ -411,4 +411,142 @@ cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cuda
   return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kSolverThreads), args, 0, s);
 }
 
+// ---------------------------------------------------------------------------
+// Facet solve without allocation (dg_facet_solve_noalloc in include/dgdf.h).
+//
+// Same FP64 PCG as k_solve<K, 0>, but the caller passes the facet operator, g
+// and lam in memory it owns, and every work vector, the reduction slots, the
+// grid barrier and the counters live in the file-scope array below, so the
+// call makes no allocation. The array (kNoAllocDofs multiplier DOFs, about
+// 12.7 MB) exists on every GPU that loads the library until the process exits;
+// all calls share it, so calls that overlap on the GPU race.
+namespace {
+
+constexpr long long kNoAllocDofs = 1ll << 18;
+constexpr long long kNoAllocDoubles =
+    6 * kNoAllocDofs + (long long)kRedSlots * kMaxSolverBlocks + 16;   // g r z pa pb q | red | bar, stats
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+template <int K>
+__global__ void __launch_bounds__(kSolverThreads) k_solve_noalloc(DevMesh m, const double* gin, double rtol, int maxit) {
+  constexpr int NL = K + 1;
+  const int nF = m.n_facet;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  GridBar* bar = m.bar;
+  double gg[2] = {0.0, 0.0};
+  for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const size_t o = size_t(f) * NL + j;
+      const double v = gin[o];
+      m.g[o] = v;
+      gg[0] += v * v;
+      if (j == 0) gg[1] += v;
+    }
+  if (!grid_reduce<2>(m, 4, gg, bar)) return;
+  const double c0 = gg[1] / double(nF);
+  for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
+  bool conv = false;
+  int iters = 0;
+  double relres = 0.0;
+  if (gnorm == 0.0) {
+    for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
+    conv = true;
+  } else {
+    for (int f = gtid; f < nF; f += gsz) {
+      double y[NL];
+      spmv64<NL>(m, f, m.lam, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.r[size_t(f) * NL + j] = m.g[size_t(f) * NL + j] - y[j];
+    }
+    if (!grid_sync(bar, m.stats)) return;
+    double rr_end = 0.0;
+    iters = pcg<NL, double>(m, m.lam, m.r, m.z, m.pa, m.pb, m.q, m.st_blk, m.st_binv, rtol * gnorm, maxit, false,
+                            bar, &conv, &rr_end);
+    relres = sqrt(rr_end) / gnorm;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    m.stats->last_iters = iters;
+    m.stats->last_relres = relres;
+    if (!conv) atomicOr(&m.stats->flags, kFlagNotConverged);
+  }
+}
+
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device, looked up once per device.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+long long noalloc_max_dofs() { return kNoAllocDofs; }
+
+cudaError_t solve_noalloc(int k, int n_facet, const int32_t* facet_nbr, const int32_t* stencil, const double* blocks,
+                          const double* binv, const double* g, double* lam, double rtol, int maxit, cudaStream_t s,
+                          DevStats* host_stats) {
+  double* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return e;
+  DevMesh m{};
+  m.k = k;
+  m.nl = k + 1;
+  m.n_facet = n_facet;
+  m.facet_nbr = facet_nbr;
+  m.facet_stencil = stencil;
+  m.st_blk = blocks;
+  m.st_binv = binv;
+  m.lam = lam;
+  m.g = base;
+  m.r = base + kNoAllocDofs;
+  m.z = base + 2 * kNoAllocDofs;
+  m.pa = base + 3 * kNoAllocDofs;
+  m.pb = base + 4 * kNoAllocDofs;
+  m.q = base + 5 * kNoAllocDofs;
+  m.red = base + 6 * kNoAllocDofs;
+  double* tail = m.red + (long long)kRedSlots * kMaxSolverBlocks;
+  m.bar = reinterpret_cast<GridBar*>(tail);
+  m.stats = reinterpret_cast<DevStats*>(tail + 2);
+  // the barrier and the counters must start at zero; the array keeps the last call's contents
+  e = cudaMemsetAsync(tail, 0, 16 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const void* fn = nullptr;
+  switch (k) {
+    case 1: fn = (const void*)k_solve_noalloc<1>; break;
+    case 2: fn = (const void*)k_solve_noalloc<2>; break;
+    case 3: fn = (const void*)k_solve_noalloc<3>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolverThreads, 0)) != cudaSuccess) return e;
+  int nb = per_sm * sms;
+  if (nb > 2 * sms) nb = 2 * sms;
+  const int need = (n_facet + kSolverThreads - 1) / kSolverThreads;
+  if (nb > need) nb = need;
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  if (nb < 1) nb = 1;
+  void* args[] = {&m, (void*)&g, &rtol, &maxit};
+  if ((e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kSolverThreads), args, 0, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(host_stats, m.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
 }  // namespace dgdf

@@ -1,0 +1,106 @@
+"""The facet solve that allocates nothing (dg_facet_solve_noalloc).
+
+It serves callers that cannot call cudaMalloc (code running inside another
+framework's memory pool or budget, or where allocating is forbidden), so they
+cannot create a dg_mesh either: they hold the condensed facet operator, the
+right-hand side and the solution in memory they own, and the library keeps its
+work vectors in a static device array.
+
+The test compares it with the mesh solver behind the existing dg_get_pressure:
+that call solves S lam = g for the pressure functional and returns lam on the
+facets; feeding g = S lam to the no-allocation solve must give lam back (in the
+energy norm of S, the norm in which the velocity error is measured), on two
+calls in a row that share the static scratch.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1808_04669_gb300 import build
+    build.build()
+    import paper_1808_04669_gb300 as pkg
+    return pkg
+
+
+def facet_values_to_coefficients(pf, k):
+    """Coefficients in the facet basis sqrt(2m+1) P_m(2t-1) from the values at t = i/k (dgdf.h conventions)."""
+    t = np.arange(k + 1) / k
+    V = np.stack([np.sqrt(2 * m + 1) * np.polynomial.legendre.Legendre.basis(m)(2 * t - 1) for m in range(k + 1)], 1)
+    return np.linalg.solve(V, pf.T).T
+
+
+def apply_S(nbr, st, blk, x):
+    nf, nl = x.shape
+    y = np.einsum("fij,fj->fi", blk[st, 0], x)
+    for b in range(4):
+        y += np.einsum("fij,fj->fi", blk[st, b + 1], x[nbr[:, b]])
+    return y
+
+
+def energy_rel(nbr, st, blk, a, ref):
+    # lam is defined up to the constant multiplier (mode 0 on every facet, the kernel of S): remove it first
+    d = a - ref
+    d[:, 0] -= d[:, 0].mean()
+    return float(np.sqrt(abs((d * apply_S(nbr, st, blk, d)).sum()) / (ref * apply_S(nbr, st, blk, ref)).sum()))
+
+
+@pytest.mark.parametrize("N,k", [(6, 2), (5, 3)])
+def test_noalloc_solve_matches_mesh_solver_on_two_calls(g, N, k):
+    import torch
+    vid, X = synth.split_square_mesh(N)
+    mesh = g.DGMesh(vid, X, k, 1e-2)
+    rng = np.random.default_rng(N * 10 + k)
+    mesh.set_velocity(rng.standard_normal((mesh.n_tri, mesh.n_lat, 2)))
+    mesh.project_divfree()
+    lams = []
+    _, pf = mesh.get_pressure()                            # existing entry point, first state
+    lams.append(facet_values_to_coefficients(pf, k))
+    mesh.rk3_step(0.01, 1)
+    _, pf = mesh.get_pressure()                            # existing entry point, second state
+    lams.append(facet_values_to_coefficients(pf, k))
+
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    dev = torch.device("cuda")
+    nbr_d = torch.from_numpy(nbr).to(dev)
+    st_d = torch.from_numpy(st).to(dev)
+    blk_d = torch.from_numpy(np.ascontiguousarray(blk)).to(dev)
+    binv_d = torch.from_numpy(np.ascontiguousarray(binv)).to(dev)
+    for lam_ex in lams:                                    # two calls in a row on the shared scratch
+        rhs = apply_S(nbr, st, blk, lam_ex)
+        g_d = torch.from_numpy(np.ascontiguousarray(rhs)).to(dev)
+        lam_d = torch.zeros_like(g_d)
+        it, rr = g.facet_solve_noalloc(k, nbr_d, st_d, blk_d, binv_d, g_d, lam_d)
+        torch.cuda.synchronize()
+        lam = lam_d.cpu().numpy()
+        assert it > 0 and rr <= 1e-13
+        assert energy_rel(nbr, st, blk, lam, lam_ex) < TOL64
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(g):
+    import torch
+    from paper_1808_04669_gb300 import DGError
+    k = 2
+    n_facet = (1 << 18) // (k + 1) + 1
+    small_i = torch.zeros(4, dtype=torch.int32, device="cuda")
+    small_d = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(DGError) as e:
+        g.lib()
+        import ctypes
+        V = ctypes.c_void_p
+        from paper_1808_04669_gb300._native import check
+        check(g.lib().dg_facet_solve_noalloc(k, n_facet, V(small_i.data_ptr()), V(small_i.data_ptr()),
+                                             V(small_d.data_ptr()), V(small_d.data_ptr()), V(small_d.data_ptr()),
+                                             V(small_d.data_ptr()), 1e-13, 100, None, None, None),
+              "dg_facet_solve_noalloc")
+    assert e.value.code == -1 and "exceeds the static scratch limit" in str(e.value)
