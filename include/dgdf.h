@@ -72,6 +72,7 @@ typedef enum {
 } dg_status;
 
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
+enum { DG_PRECOND_AUTO = 0, DG_PRECOND_BLOCK_JACOBI = 1 };
 
 typedef struct {
   int k;              /* polynomial degree, 1 <= k <= 3 */
@@ -81,6 +82,10 @@ typedef struct {
   double cg_rtol;     /* facet solve stops at ||g - S lam||_2 <= cg_rtol ||g||_2 (<= 0: 1e-13) */
   int cg_maxit;       /* iteration cap per solve (<= 0: 20000) */
   void* cuda_stream;  /* cudaStream_t to enqueue on (NULL: default stream) */
+  int precond;        /* DG_PRECOND_AUTO: on a translation-invariant split-square mesh with N a
+                         power of two, precondition with the exact Fourier-space inverse of the
+                         block-circulant facet operator (FP32 in the mixed form, FP64 in the FP64
+                         form), else block Jacobi; DG_PRECOND_BLOCK_JACOBI: always block Jacobi */
 } dg_params;
 
 /* Build a mesh: topology, reference tables and the per-element operators of
@@ -116,9 +121,10 @@ int dg_project_divfree(dg_mesh* mesh);
 /* nsteps >= 0 steps of SSP-RK3 (eq. (8)) with the fixed step dt > 0. Each stage
  * forms F = a M u^n + b [M u' + dt L(u')] and solves eq. (12) for the next
  * stage velocity. With DG_PRECISION_MIXED the facet system of each stage is
- * solved by FP32 PCG inside FP64 iterative refinement (residual g - S lam in
- * FP64, to the same cg_rtol); element residual, condensation and recovery stay
- * in FP64 in both forms.
+ * solved with FP32 preconditioning and FP64 residuals: FP32 PCG inside FP64
+ * iterative refinement (block Jacobi), or FP64 PCG with the FP32 Fourier-space
+ * preconditioner (lattice meshes), to the same cg_rtol; element residual,
+ * condensation and recovery stay in FP64 in both forms.
  * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
  * a residual norm became NaN/Inf (the state is then undefined). */
 int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
@@ -145,8 +151,9 @@ int dg_get_diagnostics(dg_mesh* mesh, double out[8]);
 /* Facet-solver counters: out[0] CG iterations of the last solve (inner FP32
  * iterations summed over refinement sweeps in the mixed form), out[1] total
  * iterations, out[2] solves, out[3] final relative residual of the last solve,
- * out[4] refinement sweeps of the last solve, out[5] total sweeps, out[6] /
- * out[7] persistent-kernel blocks of the FP64 / mixed solver. */
+ * out[4] refinement sweeps of the last solve, out[5] total sweeps, out[6] 1 if
+ * the Fourier-space (lattice) preconditioner is in use, 0 for block Jacobi,
+ * out[7] persistent-kernel blocks of the solver in use. */
 int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
 
 /* FP64 facet-system solve that allocates nothing, for callers that cannot call

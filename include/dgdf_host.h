@@ -48,6 +48,16 @@ int dg_host_facet_operator(int64_t n_tri, const int64_t* tri_vertex_ids, const d
                            double alpha, int64_t* n_facet, int64_t* n_stencil, int32_t* facet_nbr,
                            int32_t* stencil, double* blocks, double* binv, int64_t cap_blocks);
 
+/* Lattice structure used by DG_PRECOND_AUTO: returns DG_ERR_UNSUPPORTED when the
+ * mesh is not a translation-invariant split-square mesh with N a power of two.
+ * *N receives the cells per direction; facet_of (int32 [3][N][N], row j, column
+ * i) the facet of each (type, cell); sinv (double [N][N][C][C][2], C = 3(k+1))
+ * the inverse of the Fourier symbol of the facet operator at (k_i, k_j), as
+ * (re, im), pseudo-inverse at (0, 0); cap is the capacity of sinv in doubles.
+ * Pass NULL arrays to query N. */
+int dg_host_lattice(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k, double alpha,
+                    int64_t* N, int32_t* facet_of, double* sinv, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

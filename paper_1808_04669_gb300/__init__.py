@@ -14,6 +14,8 @@ from ._native import DGError, DGParams, check, lib
 
 FP64 = 0
 MIXED = 1
+PRECOND_AUTO = 0
+PRECOND_BLOCK_JACOBI = 1
 
 
 def _ptr(a):
@@ -34,7 +36,7 @@ class DGMesh:
     """One mesh and its state, owned by libdgdf (dg_mesh_create ... dg_mesh_destroy)."""
 
     def __init__(self, tri_vertex_ids, tri_coords, k, nu, alpha=2.0, precision=FP64, cg_rtol=1e-13,
-                 cg_maxit=20000, stream=None):
+                 cg_maxit=20000, stream=None, precond=PRECOND_AUTO):
         L = lib()
         vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
         X = np.ascontiguousarray(tri_coords, dtype=np.float64)
@@ -47,7 +49,7 @@ class DGMesh:
             except Exception:
                 stream = 0
         self.params = DGParams(int(k), float(nu), float(alpha), int(precision), float(cg_rtol), int(cg_maxit),
-                               ctypes.c_void_p(int(stream)))
+                               ctypes.c_void_p(int(stream)), int(precond))
         h = ctypes.c_void_p()
         check(L.dg_mesh_create(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
                                ctypes.byref(self.params), ctypes.byref(h)), "dg_mesh_create")
@@ -127,7 +129,7 @@ class DGMesh:
         out = (ctypes.c_double * 8)()
         check(lib().dg_get_solver_stats(self._h, out), "dg_get_solver_stats")
         keys = ("last_iters", "total_iters", "solves", "last_relres", "last_sweeps", "total_sweeps",
-                "blocks_fp64", "blocks_mixed")
+                "lattice", "blocks")
         return dict(zip(keys, list(out)))
 
     def profile(self, enable):
@@ -192,6 +194,29 @@ def host_facet_operator(tri_vertex_ids, tri_coords, k, alpha=2.0):
     return nbr, st, blk, binv
 
 
+def host_lattice(tri_vertex_ids, tri_coords, k, alpha=2.0):
+    """The lattice structure and inverse Fourier symbol of the facet operator (include/dgdf_host.h).
+
+    Returns (N, facet_of [3][N][N], sinv [N][N][C][C] complex) or None if the mesh is not a lattice.
+    """
+    L = lib()
+    vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tri_coords, dtype=np.float64)
+    V = ctypes.c_void_p
+    N = ctypes.c_int64()
+    args = (vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), int(k), float(alpha), ctypes.byref(N))
+    rc = L.dg_host_lattice(*args, None, None, 0)
+    if rc == -3:
+        return None
+    check(rc, "dg_host_lattice")
+    n = N.value
+    C = 3 * (k + 1)
+    fo = np.empty((3, n, n), dtype=np.int32)
+    s = np.empty((n, n, C, C, 2))
+    check(L.dg_host_lattice(*args, fo.ctypes.data_as(V), s.ctypes.data_as(V), s.size), "dg_host_lattice")
+    return n, fo, s[..., 0] + 1j * s[..., 1]
+
+
 def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13, maxit=20000, stream=None):
     """dg_facet_solve_noalloc on caller-owned CUDA tensors (torch); lam is updated in place.
 
@@ -215,5 +240,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "host_topology", "host_reference", "host_facet_operator", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "facet_solve_noalloc",
            "lib"]

@@ -16,13 +16,13 @@ STATUS = {0: "DG_OK", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_U
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
            "dg_project_divfree", "dg_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
            "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
-           "dg_host_facet_operator"]
+           "dg_host_facet_operator", "dg_host_lattice"]
 
 
 class DGParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("precision", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("precond", ctypes.c_int)]
 
 
 _lib = None
@@ -55,6 +55,7 @@ def lib():
         "dg_host_topology": (ctypes.c_int, [I64, P, P, P, P, P, P]),
         "dg_host_reference": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, I64, P]),
         "dg_host_facet_operator": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, P, P, P, P, P, I64]),
+        "dg_host_lattice": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, P, P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

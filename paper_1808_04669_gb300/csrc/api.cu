@@ -31,11 +31,14 @@ enum KernelClass {
   KC_LATTICE,
   KC_DIAG,
   KC_PRESSURE,
+  KC_SOLVE_LAT64,
+  KC_SOLVE_LAT32,
   KC_COUNT
 };
 const char* kKernelNames[KC_COUNT] = {"stage_residual_fp64", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
-                                      "lattice",             "diagnostics",          "pressure"};
+                                      "lattice",             "diagnostics",          "pressure",
+                                      "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32"};
 
 }  // namespace
 
@@ -46,6 +49,9 @@ struct dg_mesh {
   cudaStream_t stream = nullptr;
   std::vector<void*> allocs;
   int solver_blocks[2] = {1, 1};
+  bool use_lattice = false;
+  int lattice_blocks = 0;
+  std::string lattice_why;
   double last_bdt = 0.0;
   bool has_lam = false;
   double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
@@ -169,6 +175,11 @@ int solve(dg_mesh* M, double warm_scale) {
   a.max_sweeps = 40;
   a.inner_maxit = M->p.cg_maxit;
   a.floor_rtol = 1e-9;
+  if (M->use_lattice) {
+    const int nb = M->lattice_blocks;
+    return launch(M, a.mixed ? KC_SOLVE_LAT32 : KC_SOLVE_LAT64,
+                  [&] { return dgdf::launch_solve_lattice(M->dm, a, nb, a.mixed, M->stream); });
+  }
   const int nb = M->solver_blocks[a.mixed];
   return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
 }
@@ -199,6 +210,8 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     return fail(DG_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
   if (!(p.cg_rtol > 0.0)) p.cg_rtol = 1e-13;
   if (p.cg_maxit <= 0) p.cg_maxit = 20000;
+  if (p.precond != DG_PRECOND_AUTO && p.precond != DG_PRECOND_BLOCK_JACOBI)
+    return fail(DG_ERR_INVALID_ARG, "precond must be DG_PRECOND_AUTO or DG_PRECOND_BLOCK_JACOBI");
   dg_mesh* M = new dg_mesh();
   M->p = p;
   M->stream = static_cast<cudaStream_t>(p.cuda_stream);
@@ -288,6 +301,56 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
   M->solver_blocks[0] = dgdf::solver_max_blocks(d, 0);
   M->solver_blocks[1] = dgdf::solver_max_blocks(d, 1);
+  if (p.precond == DG_PRECOND_AUTO) {
+    dgdf::Lattice lat;
+    dgdf::build_lattice(M->hm, tri_coords, lat);
+    const int fp32 = p.precision == DG_PRECISION_MIXED;
+    int nb = lat.ok ? dgdf::lattice_blocks(hm.k, lat.N, fp32) : 0;
+    if (lat.ok && nb > 0) {
+      const int C = lat.C, N = lat.N;
+      const size_t nS = size_t(N) * N * C * C;
+      std::vector<double> sd;
+      std::vector<float> sf;
+      if (fp32) sf.resize(2 * nS); else sd.resize(2 * nS);
+      // host layout [ki][kj][C][C][2] -> device [ki][C][C][kj] complex
+      for (int ki = 0; ki < N; ++ki)
+        for (int kj = 0; kj < N; ++kj)
+          for (int cc = 0; cc < C * C; ++cc)
+            for (int ri = 0; ri < 2; ++ri) {
+              const double v = lat.sinv[((size_t(ki) * N + kj) * C * C + cc) * 2 + ri];
+              const size_t o = ((size_t(ki) * C * C + cc) * N + kj) * 2 + ri;
+              if (fp32) sf[o] = float(v); else sd[o] = v;
+            }
+      const int32_t* fo = nullptr;
+      const double* tw = nullptr;
+      if ((rc = upload(M, &fo, lat.facet_of)) || (rc = upload(M, &tw, lat.twiddle))) return cleanup(rc);
+      if (fp32) {
+        const float* sp = nullptr;
+        if ((rc = upload(M, &sp, sf))) return cleanup(rc);
+        d.lat_sinv = sp;
+        float* xp = nullptr;
+        if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+        d.lat_x = xp;
+      } else {
+        const double* sp = nullptr;
+        if ((rc = upload(M, &sp, sd))) return cleanup(rc);
+        d.lat_sinv = sp;
+        double* xp = nullptr;
+        if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+        d.lat_x = xp;
+      }
+      d.lat_facet_of = fo;
+      d.lat_tw = tw;
+      d.lat_N = N;
+      int logn = 0;
+      while ((1 << logn) < N) ++logn;
+      d.lat_logn = logn;
+      M->use_lattice = true;
+      M->lattice_blocks = nb;
+    } else {
+      M->lattice_why = lat.ok ? "lattice solver does not fit on this device" : lat.why;
+    }
+  }
   *out = M;
   return DG_OK;
 }
@@ -466,8 +529,8 @@ int dg_get_solver_stats(dg_mesh* M, double out[8]) {
   out[3] = s.last_relres;
   out[4] = s.last_sweeps;
   out[5] = double(s.total_sweeps);
-  out[6] = M->solver_blocks[0];
-  out[7] = M->solver_blocks[1];
+  out[6] = M->use_lattice ? 1.0 : 0.0;
+  out[7] = M->use_lattice ? M->lattice_blocks : M->solver_blocks[M->p.precision == DG_PRECISION_MIXED];
   return DG_OK;
 }
 

@@ -61,6 +61,12 @@ struct DevMesh {
   double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
+  // lattice (translation-invariant split-square) solver data
+  int lat_N, lat_logn;
+  const int32_t* lat_facet_of;        // [3][N][N]
+  const void* lat_sinv;               // [N][C][C][N] complex (float2 or double2)
+  const double* lat_tw;               // [N][2]
+  void* lat_x;                        // [C][N][N] complex work array
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
@@ -106,6 +112,9 @@ cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
+size_t lattice_smem_bytes(int k, int N, int fp32);
+int lattice_blocks(int k, int N, int fp32);
+cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nblocks, int fp32, cudaStream_t s);
 long long noalloc_max_dofs();
 cudaError_t solve_noalloc(int k, int n_facet, const int32_t* facet_nbr, const int32_t* stencil, const double* blocks,
                           const double* binv, const double* g, double* lam, double rtol, int maxit, cudaStream_t s,

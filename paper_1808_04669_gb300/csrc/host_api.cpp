@@ -75,4 +75,23 @@ int dg_host_facet_operator(int64_t n_tri, const int64_t* tri_vertex_ids, const d
   return DG_OK;
 }
 
+int dg_host_lattice(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k, double alpha,
+                    int64_t* N, int32_t* facet_of, double* sinv, int64_t cap) {
+  if (!N || !(alpha > 0.0)) return DG_ERR_INVALID_ARG;
+  dgdf::HostMesh hm;
+  std::string err;
+  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, k, alpha, hm, err);
+  if (rc) return rc;
+  dgdf::Lattice lat;
+  dgdf::build_lattice(hm, tri_coords, lat);
+  if (!lat.ok) return DG_ERR_UNSUPPORTED;
+  *N = lat.N;
+  if (facet_of) std::memcpy(facet_of, lat.facet_of.data(), lat.facet_of.size() * sizeof(int32_t));
+  if (sinv) {
+    if (cap < int64_t(lat.sinv.size())) return DG_ERR_INVALID_ARG;
+    std::memcpy(sinv, lat.sinv.data(), lat.sinv.size() * sizeof(double));
+  }
+  return DG_OK;
+}
+
 }  // extern "C"

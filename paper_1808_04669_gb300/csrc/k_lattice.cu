@@ -1,0 +1,429 @@
+// Facet-system solve on translation-invariant split-square meshes (the lattice
+// path of the condensed hybrid-mixed system, eq. (12) of Sec. 2.4).
+//
+// On such a mesh the facet operator S is block circulant over the N x N cell
+// grid: a 2-D discrete Fourier transform turns it into one Hermitian block
+// S^(kappa) of size C = 3(k+1) per wavenumber, and S^+ r = IDFT(S^(kappa)^-1 DFT(r))
+// (pseudo-inverse at kappa = 0, the constant multiplier). This kernel runs PCG
+// with FP64 vectors and FP64 SpMV, preconditioned by that Fourier-space inverse
+// evaluated in precision R (FP32 in the mixed form, FP64 in the FP64 form):
+// the preconditioned operator is the identity up to R's rounding, so a solve
+// takes one or two iterations (FP64) or a few (FP32), instead of O(N).
+// The transforms are radix-2 FFTs in shared memory (N a power of two):
+//   rows  : DFT along i of r gathered from facet order, tile of 8 rows per pass
+//   column: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j
+//   rows  : inverse DFT along i, scattered back to facet order (scaled 1/N^2)
+// with a grid barrier between the three passes. One persistent cooperative
+// kernel per solve, one block per SM.
+#include "device.cuh"
+#include "kcommon.cuh"
+#include "solver_common.cuh"
+
+namespace dgdf {
+namespace {
+
+constexpr int kLatThreads = 512;
+constexpr int kTileRows = 8;
+
+template <typename R>
+struct CxT;
+template <>
+struct CxT<float> {
+  using T = float2;
+};
+template <>
+struct CxT<double> {
+  using T = double2;
+};
+
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C2>
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename C2>
+__device__ __forceinline__ C2 csub(C2 a, C2 b) {
+  return {a.x - b.x, a.y - b.y};
+}
+
+__device__ __forceinline__ int brev(int t, int logn) { return logn == 0 ? 0 : int(__brev(unsigned(t)) >> (32 - logn)); }
+
+// Radix-2 decimation in time on `rows` rows of length n = 2^logn in shared memory:
+// input in bit-reversed order, output in natural order. tw[t] = exp(-2 pi i t / n).
+template <typename C2>
+__device__ void fft_dit(C2* buf, int rows, int logn, const C2* tw, bool inverse) {
+  const int n = 1 << logn, hn = n >> 1;
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1), step = n >> s;
+    for (int b = threadIdx.x; b < rows * hn; b += blockDim.x) {
+      const int row = b / hn, k = b - row * hn;
+      const int grp = k >> (s - 1), pos = k & (half - 1);
+      const int i0 = row * n + (grp << s) + pos, i1 = i0 + half;
+      C2 w = tw[pos * step];
+      if (inverse) w.y = -w.y;
+      const C2 u = buf[i0], v = cmul(buf[i1], w);
+      buf[i0] = cadd(u, v);
+      buf[i1] = csub(u, v);
+    }
+    __syncthreads();
+  }
+}
+
+// Radix-2 decimation in frequency: input natural, output bit-reversed.
+template <typename C2>
+__device__ void fft_dif(C2* buf, int rows, int logn, const C2* tw, bool inverse) {
+  const int n = 1 << logn, hn = n >> 1;
+  for (int s = logn; s >= 1; --s) {
+    const int half = 1 << (s - 1), step = n >> s;
+    for (int b = threadIdx.x; b < rows * hn; b += blockDim.x) {
+      const int row = b / hn, k = b - row * hn;
+      const int grp = k >> (s - 1), pos = k & (half - 1);
+      const int i0 = row * n + (grp << s) + pos, i1 = i0 + half;
+      C2 w = tw[pos * step];
+      if (inverse) w.y = -w.y;
+      const C2 u = buf[i0], v = buf[i1];
+      buf[i0] = cadd(u, v);
+      buf[i1] = cmul(csub(u, v), w);
+    }
+    __syncthreads();
+  }
+}
+
+template <int K, typename R>
+struct LatCtx {
+  using C2 = typename CxT<R>::T;
+  static constexpr int NL = K + 1, C = 3 * NL;
+  int N, logn, ntj;
+  C2* tw;
+  C2* buf;
+  C2* X;          // [C][N(ki)][N(j)]
+  const C2* S;    // [N(ki)][C][C][N(kj)]
+  const int32_t* fo;   // [3][N(j)][N(i)] -> facet
+};
+
+// Row pass, forward: gather r (optionally first updating r -= alpha q, lam += alpha p),
+// DFT along i, store transposed. Accumulates r.r into *rr.
+template <int K, typename R>
+__device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool update, double alpha, const double* p,
+                             double* rr) {
+  using C2 = typename CxT<R>::T;
+  constexpr int NL = K + 1, C = 3 * NL;
+  const int N = L.N, logn = L.logn;
+  const int ntiles = C * L.ntj;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c = tile / L.ntj, j0 = (tile - c * L.ntj) * kTileRows;
+    const int rows = min(kTileRows, N - j0);
+    const int ty = c / NL, mm = c - ty * NL;
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+      const int r_ = e >> logn, i = e & (N - 1);
+      const int f = __ldg(&L.fo[(size_t(ty) * N + j0 + r_) * N + i]);
+      const size_t o = size_t(f) * NL + mm;
+      double rv = __ldcg(&m.r[o]);
+      if (update) {
+        rv -= alpha * __ldcg(&m.q[o]);
+        m.r[o] = rv;
+        m.lam[o] += alpha * __ldcg(&p[o]);
+      }
+      *rr += rv * rv;
+      L.buf[r_ * N + brev(i, logn)] = C2{R(rv), R(0)};
+    }
+    __syncthreads();
+    fft_dit(L.buf, rows, logn, L.tw, false);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+      const int ki = e / rows, r_ = e - ki * rows;
+      L.X[(size_t(c) * N + ki) * N + j0 + r_] = L.buf[r_ * N + ki];
+    }
+    __syncthreads();
+  }
+}
+
+// Column pass: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j.
+template <int K, typename R>
+__device__ void columns(const LatCtx<K, R>& L) {
+  using C2 = typename CxT<R>::T;
+  constexpr int C = LatCtx<K, R>::C;
+  const int N = L.N, logn = L.logn;
+  for (int ki = blockIdx.x; ki < N; ki += gridDim.x) {
+    for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
+      const int c = e >> logn, j = e & (N - 1);
+      L.buf[c * N + brev(j, logn)] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j]);
+    }
+    __syncthreads();
+    fft_dit(L.buf, C, logn, L.tw, false);
+    const C2* S = L.S + size_t(ki) * C * C * N;
+    for (int kj0 = 0; kj0 < N; kj0 += blockDim.x) {
+      const int kj = kj0 + threadIdx.x;
+      C2 x[C];
+      if (kj < N)
+#pragma unroll
+        for (int c = 0; c < C; ++c) x[c] = L.buf[c * N + kj];
+      __syncthreads();
+      if (kj < N) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          C2 y = {R(0), R(0)};
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(c) * C + cc) * N + kj]), x[cc]));
+          L.buf[c * N + kj] = y;
+        }
+      }
+      __syncthreads();
+    }
+    fft_dif(L.buf, C, logn, L.tw, true);
+    for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
+      const int c = e >> logn, p = e & (N - 1);
+      L.X[(size_t(c) * N + ki) * N + brev(p, logn)] = L.buf[c * N + p];
+    }
+    __syncthreads();
+  }
+}
+
+// Row pass, inverse: inverse DFT along i, z = result / N^2 scattered to facet order.
+// Accumulates r.z_new into *rz and, if with_old, r.z_old into *rzo.
+template <int K, typename R>
+__device__ void rows_inverse(const DevMesh& m, const LatCtx<K, R>& L, bool with_old, double* rz, double* rzo) {
+  constexpr int NL = K + 1, C = 3 * NL;
+  const int N = L.N, logn = L.logn;
+  const double scale = 1.0 / (double(N) * double(N));
+  const int ntiles = C * L.ntj;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c = tile / L.ntj, j0 = (tile - c * L.ntj) * kTileRows;
+    const int rows = min(kTileRows, N - j0);
+    const int ty = c / NL, mm = c - ty * NL;
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+      const int ki = e / rows, r_ = e - ki * rows;
+      L.buf[r_ * N + ki] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j0 + r_]);
+    }
+    __syncthreads();
+    fft_dif(L.buf, rows, logn, L.tw, true);
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+      const int r_ = e >> logn, p = e & (N - 1);
+      const int i = brev(p, logn);
+      const int f = __ldg(&L.fo[(size_t(ty) * N + j0 + r_) * N + i]);
+      const size_t o = size_t(f) * NL + mm;
+      const double zv = double(L.buf[r_ * N + p].x) * scale;
+      const double rv = __ldcg(&m.r[o]);
+      if (with_old) *rzo += rv * __ldcg(&m.z[o]);
+      *rz += rv * zv;
+      m.z[o] = zv;
+    }
+    __syncthreads();
+  }
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveArgs a) {
+  using C2 = typename CxT<R>::T;
+  constexpr int NL = K + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LatCtx<K, R> L;
+  L.N = m.lat_N;
+  L.logn = m.lat_logn;
+  L.ntj = (L.N + kTileRows - 1) / kTileRows;
+  L.tw = reinterpret_cast<C2*>(smem_raw);
+  L.buf = L.tw + (L.N > 1 ? L.N / 2 : 1);
+  L.X = reinterpret_cast<C2*>(m.lat_x);
+  L.S = reinterpret_cast<const C2*>(m.lat_sinv);
+  L.fo = m.lat_facet_of;
+  for (int t = threadIdx.x; t < L.N / 2; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
+  __syncthreads();
+  const int nF = m.n_facet;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  GridBar* bar = m.bar;
+  // g from both sides of every facet; warm-started lam
+  double gg[2] = {0.0, 0.0};
+  for (int f = gtid; f < nF; f += gsz) {
+    double gv[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) gv[j] = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+      const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
+      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const double v = m.gl[size_t(t) * 3 * NL + e * NL + j];
+        gv[j] += (flip && (j & 1)) ? -v : v;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const size_t o = size_t(f) * NL + j;
+      m.g[o] = gv[j];
+      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
+      gg[0] += gv[j] * gv[j];
+    }
+    gg[1] += gv[0];
+  }
+  if (!grid_reduce<2>(m, 4, gg, bar)) return;
+  const double c0 = gg[1] / double(nF);
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
+  const double stop = a.rtol * gnorm;
+  int it = 0;
+  bool conv = false;
+  double relres = 0.0;
+  if (gnorm == 0.0) {
+    for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
+    conv = true;
+  } else {
+    // r = g - S lam with the constant component of g removed
+    for (int f = gtid; f < nF; f += gsz) {
+      double y[NL];
+      spmv64<NL>(m, f, m.lam, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const size_t o = size_t(f) * NL + j;
+        const double gv = m.g[o] - (j == 0 ? c0 : 0.0);
+        m.g[o] = gv;
+        m.r[o] = gv - y[j];
+      }
+    }
+    if (!grid_sync(bar, m.stats)) return;
+    // z = M r
+    double rr[1] = {0.0};
+    rows_forward<K, R>(m, L, false, 0.0, nullptr, &rr[0]);
+    if (!grid_reduce<1>(m, 6, rr, bar)) return;
+    columns<K, R>(L);
+    if (!grid_sync(bar, m.stats)) return;
+    double rz[2] = {0.0, 0.0};
+    rows_inverse<K, R>(m, L, false, &rz[0], &rz[1]);
+    if (!grid_reduce<2>(m, 1, rz, bar)) return;
+    double rho = rz[0], rrv = rr[0];
+    double beta = 0.0;
+    double* pold = m.pa;
+    double* pnew = m.pb;
+    for (;; ++it) {
+      relres = sqrt(rrv) / gnorm;
+      if (!isfinite(rrv) || !isfinite(rho)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      if (sqrt(rrv) <= stop) {
+        conv = true;
+        break;
+      }
+      if (it >= a.maxit) break;
+      // p_new = z + beta p_old, q = S p_new
+      double pq[1] = {0.0};
+      for (int f = gtid; f < nF; f += gsz) {
+        int nb[5];
+        facet_nbrs<NL>(m, f, nb);
+        double xs[5][NL];
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+#pragma unroll
+          for (int j = 0; j < NL; ++j) {
+            const size_t o = size_t(nb[b]) * NL + j;
+            xs[b][j] = (it == 0) ? __ldcg(&m.z[o]) : __ldcg(&m.z[o]) + beta * __ldcg(&pold[o]);
+          }
+        double y[NL];
+        stencil_rows<NL, double>(m.st_blk + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          pnew[size_t(f) * NL + j] = xs[0][j];
+          m.q[size_t(f) * NL + j] = y[j];
+          pq[0] += xs[0][j] * y[j];
+        }
+      }
+      if (!grid_reduce<1>(m, 0, pq, bar)) return;
+      if (!(pq[0] > 0.0)) {
+        if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      const double alpha = rho / pq[0];
+      // r -= alpha q, lam += alpha p, and the forward row pass of z = M r
+      rr[0] = 0.0;
+      rows_forward<K, R>(m, L, true, alpha, pnew, &rr[0]);
+      if (!grid_reduce<1>(m, 6, rr, bar)) return;
+      rrv = rr[0];
+      if (sqrt(rrv) <= stop || !isfinite(rrv)) {
+        ++it;
+        relres = sqrt(rrv) / gnorm;
+        conv = isfinite(rrv);
+        if (!conv && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      columns<K, R>(L);
+      if (!grid_sync(bar, m.stats)) return;
+      rz[0] = rz[1] = 0.0;
+      rows_inverse<K, R>(m, L, true, &rz[0], &rz[1]);
+      if (!grid_reduce<2>(m, 1, rz, bar)) return;
+      // flexible (Polak-Ribiere) beta: the FP32 preconditioner is symmetric only up to rounding
+      beta = (rz[0] - rz[1]) / rho;
+      rho = rz[0];
+      double* t = pold;
+      pold = pnew;
+      pnew = t;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats* st = m.stats;
+    st->last_iters = it;
+    st->total_iters += it;
+    st->solves += 1;
+    st->last_relres = relres;
+    st->last_sweeps = 1;
+    st->total_sweeps += 1;
+    if (!conv) atomicOr(&st->flags, kFlagNotConverged);
+  }
+}
+
+template <int K, typename R>
+const void* lat_fn() {
+  return (const void*)k_solve_lat<K, R>;
+}
+
+const void* lattice_kernel(int k, int fp32) {
+  switch (k * 2 + (fp32 ? 1 : 0)) {
+    case 2: return lat_fn<1, double>();
+    case 3: return lat_fn<1, float>();
+    case 4: return lat_fn<2, double>();
+    case 5: return lat_fn<2, float>();
+    case 6: return lat_fn<3, double>();
+    case 7: return lat_fn<3, float>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+size_t lattice_smem_bytes(int k, int N, int fp32) {
+  const int C = 3 * (k + 1);
+  const size_t cx = fp32 ? 8 : 16;
+  return (size_t(N > 1 ? N / 2 : 1) + size_t(C > kTileRows ? C : kTileRows) * N) * cx;
+}
+
+int lattice_blocks(int k, int N, int fp32) {
+  const void* fn = lattice_kernel(k, fp32);
+  if (!fn) return 0;
+  const size_t smem = lattice_smem_bytes(k, N, fp32);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLatThreads, smem) != cudaSuccess) return 0;
+  if (per_sm < 1) return 0;
+  int nb = sms;   // one block per SM
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  return nb;
+}
+
+cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nblocks, int fp32, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  const void* fn = lattice_kernel(m.k, fp32);
+  if (!fn) return cudaErrorInvalidValue;
+  DevMesh mm = m;
+  SolveArgs aa = a;
+  void* args[] = {&mm, &aa};
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kLatThreads), args,
+                                     lattice_smem_bytes(m.k, m.lat_N, fp32), s);
+}
+
+}  // namespace dgdf

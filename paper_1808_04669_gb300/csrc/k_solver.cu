@@ -17,112 +17,11 @@
 // order, so results are bitwise reproducible for a given launch shape.
 #include "device.cuh"
 #include "kcommon.cuh"
+#include "solver_common.cuh"
 
 namespace dgdf {
 
 namespace {
-
-constexpr int kSolverThreads = 256;
-constexpr unsigned long long kBarrierSpinLimit = 1ull << 26;
-
-// Grid barrier with a bounded wait. All blocks are co-resident (cooperative
-// launch). Returns false if the wait ran out, after setting kFlagBarrierTimeout.
-__device__ bool grid_sync(GridBar* bar, DevStats* st) {
-  __shared__ int ok;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int prev = atomicAdd(&bar->count, 1u);
-    int good = 1;
-    if (prev == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*vgen == g) {
-        if (++spins > kBarrierSpinLimit) {
-          atomicOr(&st->flags, kFlagBarrierTimeout);
-          good = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// Writes N block partials to red slots, synchronises the grid, and returns
-// the grid sums in every thread (same summation order in every block).
-template <int N>
-__device__ bool grid_reduce(const DevMesh& m, int slot0, double (&v)[N], GridBar* bar) {
-  double s[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) s[i] = block_sum(v[i]);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) m.red[size_t(slot0 + i) * kMaxSolverBlocks + blockIdx.x] = s[i];
-  }
-  if (!grid_sync(bar, m.stats)) return false;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    double a = 0.0;
-    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) a += __ldcg(&m.red[size_t(slot0 + i) * kMaxSolverBlocks + b]);
-    v[i] = block_sum(a);
-  }
-  return true;
-}
-
-template <int NL, typename R>
-__device__ __forceinline__ void stencil_rows(const R* __restrict__ blk, const R (&x)[5][NL], R (&y)[NL]) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    R v = R(0);
-#pragma unroll
-    for (int b = 0; b < 5; ++b)
-#pragma unroll
-      for (int j = 0; j < NL; ++j) v += __ldg(&blk[(b * NL + i) * NL + j]) * x[b][j];
-    y[i] = v;
-  }
-}
-
-template <int NL, typename R>
-__device__ __forceinline__ void block_apply(const R* __restrict__ B, const R (&x)[NL], R (&y)[NL]) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    R v = R(0);
-#pragma unroll
-    for (int j = 0; j < NL; ++j) v += __ldg(&B[i * NL + j]) * x[j];
-    y[i] = v;
-  }
-}
-
-template <int NL>
-__device__ __forceinline__ void facet_nbrs(const DevMesh& m, int f, int (&nb)[5]) {
-  nb[0] = f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) nb[i + 1] = __ldg(&m.facet_nbr[size_t(f) * 4 + i]);
-}
-
-// y_F = (S x)_F in FP64
-template <int NL>
-__device__ __forceinline__ void spmv64(const DevMesh& m, int f, const double* x, double (&y)[NL]) {
-  int nb[5];
-  facet_nbrs<NL>(m, f, nb);
-  double xs[5][NL];
-#pragma unroll
-  for (int b = 0; b < 5; ++b)
-#pragma unroll
-    for (int j = 0; j < NL; ++j) xs[b][j] = __ldcg(&x[size_t(nb[b]) * NL + j]);
-  stencil_rows<NL, double>(m.st_blk + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
-}
 
 // Preconditioned CG on S x = b (precision R) starting from x = 0; b is given
 // through the initial residual already stored in rv. Vectors: x, r, z, pa/pb

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <thread>
 #include <tuple>
 
 #include "../../include/dgdf.h"
@@ -581,6 +582,7 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
   // with D(sigma) = diag(sigma^m) mapping the global (canonical) coefficients to T's own.
   hm.facet_nbr.resize(size_t(T.n_facet) * 4);
   hm.facet_stencil.resize(T.n_facet);
+  hm.facet_side0.resize(T.n_facet);
   std::map<std::vector<int64_t>, int32_t> st;
   hm.stencil_blocks.clear();
   hm.stencil_binv.clear();
@@ -594,6 +596,7 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
       if (key1 < key0) std::swap(side_order[0], side_order[1]);
     }
     std::vector<int64_t> key;
+    hm.facet_side0[f] = T.facet_tri[f * 2 + side_order[0]];
     for (int si = 0; si < 2; ++si) {
       int s = side_order[si];
       int32_t t = T.facet_tri[f * 2 + s];
@@ -637,6 +640,203 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
   }
   hm.n_stencil = int(st.size());
   return DG_OK;
+}
+
+// ----------------------------------------------------------------- lattice
+namespace {
+
+// Inverse (or, with pinv, pseudo-inverse) of a Hermitian C x C matrix given as [C][C][2].
+bool hermitian_inverse(const double* A, int C, double* out, bool pinv) {
+  if (!pinv) {
+    // real embedding [[Re, -Im], [Im, Re]] is symmetric; invert it and read the blocks back
+    const int n = 2 * C;
+    std::vector<double> E(size_t(n) * n);
+    for (int i = 0; i < C; ++i)
+      for (int j = 0; j < C; ++j) {
+        const double re = A[(i * C + j) * 2], im = A[(i * C + j) * 2 + 1];
+        E[size_t(i) * n + j] = re;
+        E[size_t(i) * n + C + j] = -im;
+        E[size_t(C + i) * n + j] = im;
+        E[size_t(C + i) * n + C + j] = re;
+      }
+    if (!invert(E, n)) return false;
+    for (int i = 0; i < C; ++i)
+      for (int j = 0; j < C; ++j) {
+        out[(i * C + j) * 2] = E[size_t(i) * n + j];
+        out[(i * C + j) * 2 + 1] = E[size_t(C + i) * n + j];
+      }
+    return true;
+  }
+  // kappa = 0: the symbol is real symmetric; invert its eigenvalues above 1e-10 of the largest
+  std::vector<double> R(size_t(C) * C), ev, V;
+  for (int i = 0; i < C * C; ++i) R[i] = A[2 * i];
+  sym_eig(R, C, ev, V);
+  double emax = 0.0;
+  for (double e : ev) emax = std::max(emax, std::fabs(e));
+  for (int i = 0; i < C; ++i)
+    for (int j = 0; j < C; ++j) {
+      double v = 0.0;
+      for (int l = 0; l < C; ++l)
+        if (std::fabs(ev[l]) > 1e-10 * emax) v += V[size_t(i) * C + l] * V[size_t(j) * C + l] / ev[l];
+      out[(i * C + j) * 2] = v;
+      out[(i * C + j) * 2 + 1] = 0.0;
+    }
+  return true;
+}
+
+}  // namespace
+
+void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
+  L = Lattice();
+  const Topology& T = hm.topo;
+  const int64_t n = T.n_tri;
+  const int N = int(std::llround(std::sqrt(double(n) / 2.0)));
+  if (int64_t(2) * N * N != n) {
+    L.why = "triangle count is not 2 N^2";
+    return;
+  }
+  if ((N & (N - 1)) != 0) {
+    L.why = "N is not a power of two";
+    return;
+  }
+  if (hm.classes.size() != 2 || hm.n_stencil != 3) {
+    L.why = "not two element classes and three facet stencils";
+    return;
+  }
+  // lower triangles: v1 - v0 = (h, 0), v2 - v0 = (h, h); upper: v1 - v0 = (h, h), v2 - v0 = (0, h)
+  int lower = -1;
+  double h = 0.0;
+  for (int c = 0; c < 2; ++c) {
+    const double* J = hm.classes[c].J;   // row-major [v1-v0, v2-v0] as columns
+    const double a = J[0];
+    if (a > 0 && std::fabs(J[2]) <= 1e-9 * a && std::fabs(J[1] - a) <= 1e-9 * a && std::fabs(J[3] - a) <= 1e-9 * a) {
+      lower = c;
+      h = a;
+    }
+  }
+  if (lower < 0) {
+    L.why = "element classes are not split-square triangles";
+    return;
+  }
+  const ClassOps& up = hm.classes[1 - lower];
+  if (!(std::fabs(up.J[0] - h) <= 1e-9 * h && std::fabs(up.J[2] - h) <= 1e-9 * h && std::fabs(up.J[1]) <= 1e-9 * h &&
+        std::fabs(up.J[3] - h) <= 1e-9 * h)) {
+    L.why = "element classes are not split-square triangles";
+    return;
+  }
+  const double x0 = X[0], y0 = X[1];
+  std::vector<int32_t> cell(size_t(n) * 2);
+  std::vector<int32_t> seen(size_t(2) * N * N, -1);
+  for (int64_t t = 0; t < n; ++t) {
+    const double fx = (X[t * 6] - x0) / h, fy = (X[t * 6 + 1] - y0) / h;
+    const double rx = std::round(fx), ry = std::round(fy);
+    if (std::fabs(fx - rx) > 1e-6 || std::fabs(fy - ry) > 1e-6) {
+      L.why = "corner 0 off the lattice";
+      return;
+    }
+    const int ci = int(((long long)rx % N + N) % N), cj = int(((long long)ry % N + N) % N);
+    cell[t * 2] = ci;
+    cell[t * 2 + 1] = cj;
+    const int cls = hm.tri_class[t] == lower ? 0 : 1;
+    int32_t& s = seen[(size_t(cls) * N + cj) * N + ci];
+    if (s >= 0) {
+      L.why = "two triangles in one lattice slot";
+      return;
+    }
+    s = int32_t(t);
+  }
+  const int nl = hm.nl, ntype = hm.n_stencil, C = ntype * nl;
+  L.facet_of.assign(size_t(ntype) * N * N, -1);
+  std::vector<int32_t> fcell(size_t(T.n_facet) * 2);
+  for (int64_t f = 0; f < T.n_facet; ++f) {
+    const int32_t t0 = hm.facet_side0[f];
+    const int ty = hm.facet_stencil[f];
+    const int ci = cell[size_t(t0) * 2], cj = cell[size_t(t0) * 2 + 1];
+    fcell[f * 2] = ci;
+    fcell[f * 2 + 1] = cj;
+    int32_t& s = L.facet_of[(size_t(ty) * N + cj) * N + ci];
+    if (s >= 0) {
+      L.why = "two facets in one lattice slot";
+      return;
+    }
+    s = int32_t(f);
+  }
+  // neighbour offsets (mod N) and types must be the same for every facet of a type
+  std::vector<int> off(size_t(ntype) * 4 * 3, -1);   // per type, per neighbour: (type, di, dj)
+  for (int64_t f = 0; f < T.n_facet; ++f) {
+    const int ty = hm.facet_stencil[f];
+    for (int b = 0; b < 4; ++b) {
+      const int32_t nb = hm.facet_nbr[f * 4 + b];
+      const int tb = hm.facet_stencil[nb];
+      const int di = ((fcell[size_t(nb) * 2] - fcell[f * 2]) % N + N) % N;
+      const int dj = ((fcell[size_t(nb) * 2 + 1] - fcell[f * 2 + 1]) % N + N) % N;
+      int* o = &off[(size_t(ty) * 4 + b) * 3];
+      if (o[0] < 0) {
+        o[0] = tb;
+        o[1] = di;
+        o[2] = dj;
+      } else if (o[0] != tb || o[1] != di || o[2] != dj) {
+        L.why = "facet stencil is not translation invariant";
+        return;
+      }
+    }
+  }
+  // symbol and its inverse, one wavenumber at a time (threads over k_i)
+  L.N = N;
+  L.ntype = ntype;
+  L.C = C;
+  L.sinv.assign(size_t(N) * N * C * C * 2, 0.0);
+  const double two_pi = 6.283185307179586476925286766559;
+  const std::vector<double>& B = hm.stencil_blocks;
+  bool fail = false;
+  auto work = [&](int k0, int k1) {
+    std::vector<double> S(size_t(C) * C * 2);
+    for (int ki = k0; ki < k1; ++ki)
+      for (int kj = 0; kj < N; ++kj) {
+        std::fill(S.begin(), S.end(), 0.0);
+        for (int ty = 0; ty < ntype; ++ty)
+          for (int b = 0; b < 5; ++b) {
+            int tb = ty, di = 0, dj = 0;
+            if (b > 0) {
+              const int* o = &off[(size_t(ty) * 4 + (b - 1)) * 3];
+              tb = o[0];
+              di = o[1];
+              dj = o[2];
+            }
+            const double ang = two_pi * double((long long)ki * di + (long long)kj * dj) / double(N);
+            const double cr = std::cos(ang), cim = std::sin(ang);
+            const double* blk = &B[(size_t(ty) * 5 + b) * nl * nl];
+            for (int m = 0; m < nl; ++m)
+              for (int mm = 0; mm < nl; ++mm) {
+                const double v = blk[m * nl + mm];
+                double* d = &S[((size_t(ty * nl + m) * C) + tb * nl + mm) * 2];
+                d[0] += v * cr;
+                d[1] += v * cim;
+              }
+          }
+        double* out = &L.sinv[(size_t(ki) * N + kj) * C * C * 2];
+        if (!hermitian_inverse(S.data(), C, out, ki == 0 && kj == 0)) fail = true;
+      }
+  };
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (N < 8) nth = 1;
+  std::vector<std::thread> th;
+  for (unsigned i = 0; i < nth; ++i) {
+    const int a = int(int64_t(N) * i / nth), b = int(int64_t(N) * (i + 1) / nth);
+    th.emplace_back(work, a, b);
+  }
+  for (auto& t : th) t.join();
+  if (fail) {
+    L.why = "singular Fourier symbol";
+    L.sinv.clear();
+    return;
+  }
+  L.twiddle.resize(size_t(N) * 2);
+  for (int t = 0; t < N; ++t) {
+    L.twiddle[2 * t] = std::cos(two_pi * t / N);
+    L.twiddle[2 * t + 1] = -std::sin(two_pi * t / N);
+  }
+  L.ok = true;
 }
 
 }  // namespace dgdf

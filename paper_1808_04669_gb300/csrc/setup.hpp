@@ -52,6 +52,21 @@ struct Topology {
   std::vector<int8_t> facet_loc;    // [n_facet][2]
 };
 
+// Split-square lattice structure of a translation-invariant periodic mesh: facets
+// are (type, cell) with type = stencil class and cell in an N x N grid, and row
+// (type, c) of the facet system couples to (type_b, c + delta_b) with offsets that
+// do not depend on c, so S is block circulant. Its Fourier symbol S^(kappa) is a
+// (3(k+1)) x (3(k+1)) Hermitian block per wavenumber; sinv holds its inverse
+// (pseudo-inverse at kappa = 0, where the constant multiplier is the kernel).
+struct Lattice {
+  bool ok = false;
+  std::string why;             // reason when not ok
+  int N = 0, ntype = 0, C = 0; // cells per direction, facet types, components C = ntype * (k+1)
+  std::vector<int32_t> facet_of;   // [ntype][N(j)][N(i)] -> facet id
+  std::vector<double> sinv;        // [N(ki)][N(kj)][C][C][2] (re, im)
+  std::vector<double> twiddle;     // [N][2] exp(-2 pi i t / N)
+};
+
 struct HostMesh {
   int k = 0, ns = 0, nd = 0, nw = 0, nl = 0;
   double alpha = 2.0;
@@ -69,6 +84,7 @@ struct HostMesh {
   std::vector<double> stencil_blocks;   // [n_stencil][5][nl][nl] (own, then the 4 neighbours)
   std::vector<double> stencil_binv;     // [n_stencil][nl][nl] inverse of the own block (block Jacobi)
   int n_stencil = 0;
+  std::vector<int32_t> facet_side0;     // [n_facet] triangle on the stencil's first (canonical) side
   double area_total = 0.0;
 };
 
@@ -77,5 +93,7 @@ int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology&
 int build_reference(int k, RefTables& ref, std::string& err);
 int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha,
                     HostMesh& hm, std::string& err);
+// Detects the split-square lattice structure and computes the inverse Fourier symbol.
+void build_lattice(const HostMesh& hm, const double* X, Lattice& lat);
 
 }  // namespace dgdf

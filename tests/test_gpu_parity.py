@@ -89,9 +89,10 @@ def test_residual_parity_projected_field(g, k):
 
 
 # --------------------------------------------------------------- projection
-@pytest.mark.parametrize("N,k,perturb", [(1, 1, 0.0), (2, 3, 0.0), (4, 2, 0.0), (5, 3, 0.0), (4, 2, 0.1)])
-def test_projection_parity(g, N, k, perturb):
-    mesh, d, X = pair(g, N, k, 0.0, perturb=perturb, seed=3)
+@pytest.mark.parametrize("N,k,perturb,precond", [(1, 1, 0.0, 0), (2, 3, 0.0, 0), (4, 2, 0.0, 0), (4, 2, 0.0, 1),
+                                                  (5, 3, 0.0, 0), (4, 2, 0.1, 0), (8, 3, 0.0, 0)])
+def test_projection_parity(g, N, k, perturb, precond):
+    mesh, d, X = pair(g, N, k, 0.0, perturb=perturb, seed=3, precond=precond)
     v = random_lattice(mesh.n_tri, k, 20 + N)
     mesh.set_velocity(v)
     mesh.project_divfree()
@@ -118,10 +119,13 @@ def test_projection_idempotent_and_orthogonal(g):
 
 
 # ------------------------------------------------------------------- RK3
-def test_rk3_parity_taylor_green_n8_k2(g):
-    # Taylor-Green, 8x8 split squares, BDM_2, nu = 1e-2, 100 SSP-RK3 steps, FP64
+@pytest.mark.parametrize("precond", [0, 1])
+def test_rk3_parity_taylor_green_n8_k2(g, precond):
+    # Taylor-Green, 8x8 split squares, BDM_2, nu = 1e-2, 100 SSP-RK3 steps, FP64; lattice (Fourier)
+    # preconditioner and block Jacobi
     vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
-    mesh = g.DGMesh(vid, X, 2, 1e-2)
+    mesh = g.DGMesh(vid, X, 2, 1e-2, precond=precond)
+    assert mesh.solver_stats()["lattice"] == (1.0 if precond == 0 else 0.0)
     d = Discretization(vid, X, 2, 1e-2)
     mesh.set_velocity(vals)
     mesh.project_divfree()
@@ -138,9 +142,10 @@ def test_rk3_parity_taylor_green_n8_k2(g):
     assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-11
 
 
-@pytest.mark.parametrize("k", [1, 3])
-def test_rk3_parity_shear_layer(g, k):
-    N, nu = 12, 1e-4
+@pytest.mark.parametrize("N,k", [(12, 1), (12, 3), (16, 3), (8, 2)])
+def test_rk3_parity_shear_layer(g, N, k):
+    # N = 12: block Jacobi (not a power of two); N = 8, 16: the lattice preconditioner
+    nu = 1e-4
     vid, X = synth.split_square_mesh(N)
     vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
     vmax = float(np.sqrt((vals ** 2).sum(-1)).max())
@@ -154,11 +159,16 @@ def test_rk3_parity_shear_layer(g, k):
         mesh.project_divfree()
         mesh.rk3_step(dt, 5)
         assert rel(mesh.get_velocity(), ref) < tol, prec
+        st = mesh.solver_stats()
+        assert st["lattice"] == (1.0 if N in (8, 16) else 0.0)
+        if st["lattice"]:
+            assert st["total_iters"] / st["solves"] <= 6
 
 
-def test_mixed_precision_taylor_green(g):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_mixed_precision_taylor_green(g, precond):
     vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
-    mesh = g.DGMesh(vid, X, 2, 1e-2, precision=1)
+    mesh = g.DGMesh(vid, X, 2, 1e-2, precision=1, precond=precond)
     d = Discretization(vid, X, 2, 1e-2)
     mesh.set_velocity(vals)
     mesh.project_divfree()

@@ -157,3 +157,46 @@ def test_facet_operator_is_spsd_with_constant_kernel(g, N, k, perturb):
         assert np.abs(binv[st[f]] @ own - np.eye(nl)).max() < 1e-12
     if not perturb:
         assert blk.shape[0] <= 3        # three facet orientations on a split-square mesh
+
+
+def _dense_S(nbr, st, blk):
+    nf, nl = nbr.shape[0], blk.shape[-1]
+    S = np.zeros((nf * nl, nf * nl))
+    for f in range(nf):
+        for b, c in enumerate([f] + list(nbr[f])):
+            S[f * nl:(f + 1) * nl, c * nl:(c + 1) * nl] += blk[st[f], b]
+    return S
+
+
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 2), (4, 3), (8, 2)])
+def test_lattice_fourier_inverse_solves_the_facet_system(g, N, k):
+    # the preconditioner of DG_PRECOND_AUTO: z = IDFT(S^(kappa)^+ DFT(r)) must satisfy S z = r for any r
+    # without a constant-multiplier component (S is block circulant on the split-square torus)
+    vid, X = synth.split_square_mesh(N)
+    lat = g.host_lattice(vid, X, k)
+    assert lat is not None
+    n, fo, sinv = lat
+    assert n == N and sorted(fo.ravel().tolist()) == list(range(3 * N * N))
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    S = _dense_S(nbr, st, blk)
+    nl = k + 1
+    rng = np.random.default_rng(N + k)
+    r = rng.standard_normal((3 * N * N, nl))
+    r[:, 0] -= r[:, 0].mean()
+    # gather into [type, mode, j, i], transform over (j, i), multiply per wavenumber, transform back
+    R = np.transpose(r[fo], (0, 3, 1, 2)).reshape(3 * nl, N, N)
+    Rh = np.fft.fft2(R)                                  # axes (j, i) -> (kj, ki)
+    Zh = np.einsum("ijab,bji->aji", sinv, Rh)            # sinv indexed [ki][kj][C][C]
+    Z = np.fft.ifft2(Zh).real.reshape(3, nl, N, N)
+    z = np.empty_like(r)
+    z[fo] = np.transpose(Z, (0, 2, 3, 1))
+    assert np.abs(S @ z.ravel() - r.ravel()).max() < 1e-10 * np.abs(r).max()
+
+
+def test_lattice_detection_rejects_other_meshes(g):
+    vid, X = synth.split_square_mesh(3)                  # N not a power of two
+    assert g.host_lattice(vid, X, 2) is None
+    vid, X = synth.split_square_mesh(4)
+    rng = np.random.default_rng(0)
+    Xp = X + (0.1 * rng.uniform(-1, 1, size=(16, 2)))[vid]
+    assert g.host_lattice(vid, Xp, 2) is None            # not translation invariant
