@@ -259,7 +259,7 @@ def test_invalid_inputs_raise(g):
 def test_iteration_cap_reports_not_converged(g):
     from paper_1808_04669_gb300 import DGError
     vid, X = synth.split_square_mesh(8)
-    mesh = g.DGMesh(vid, X, 2, 0.0, cg_maxit=1)
+    mesh = g.DGMesh(vid, X, 2, 0.0, cg_maxit=1, precond=1)   # block Jacobi (the Fourier path converges in 1)
     mesh.set_velocity(random_lattice(mesh.n_tri, 2, 4))
     with pytest.raises(DGError) as e:
         mesh.project_divfree()
