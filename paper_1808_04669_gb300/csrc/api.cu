@@ -35,7 +35,7 @@ enum KernelClass {
   KC_SOLVE_LAT32,
   KC_COUNT
 };
-const char* kKernelNames[KC_COUNT] = {"stage_residual_fp64", "facet_pcg_fp64",
+const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure",
                                       "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32"};
@@ -104,6 +104,16 @@ int upload(dg_mesh* M, const T** out, const std::vector<T>& v) {
 }
 
 std::vector<float> to_float(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+// double -> (hi, lo) float pairs with hi + lo = v to about 48 bits
+std::vector<float2> to_dfloat(const std::vector<double>& v) {
+  std::vector<float2> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float h = float(v[i]);
+    out[i] = make_float2(h, float(v[i] - double(h)));
+  }
+  return out;
+}
 
 cudaEvent_t get_event(dg_mesh* M) {
   if (!M->pool.empty()) {
@@ -241,6 +251,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   d.n_stencil = hm.n_stencil;
   d.nu = p.nu;
   d.area_total = hm.area_total;
+  d.elem_df = p.precision == DG_PRECISION_MIXED ? 1 : 0;
   const int nd = hm.nd, nw = hm.nw, nl = hm.nl, L3 = 3 * nl;
   // class data
   std::vector<double> geo(size_t(d.n_class) * dgdf::kGeo, 0.0), P, G, W, WC;
@@ -270,7 +281,8 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = upload(M, &d.lat_inv, ref.lat_inv)) || (rc = upload(M, &d.lat_phi, ref.lat_phi)) ||
       (rc = upload(M, &d.plat_phi, ref.plat_phi)) || (rc = upload(M, &d.mu_lat, ref.mu_lat)) ||
       (rc = upload(M, &d.geo, geo)) || (rc = upload(M, &d.P, P)) || (rc = upload(M, &d.G, G)) ||
-      (rc = upload(M, &d.W, W)) || (rc = upload(M, &d.WCt, WC)) || (rc = upload(M, &d.tri_class, hm.tri_class)) ||
+      (rc = upload(M, &d.W, W)) || (rc = upload(M, &d.WCt, WC)) || (rc = upload(M, &d.Pdf, to_dfloat(P))) ||
+      (rc = upload(M, &d.Gdf, to_dfloat(G))) || (rc = upload(M, &d.tri_class, hm.tri_class)) ||
       (rc = upload(M, &d.tri_nbr, hm.tri_nbr)) || (rc = upload(M, &d.tri_facet, hm.topo.tri_facet)) ||
       (rc = upload(M, &d.tri_nbr_loc, hm.tri_nbr_loc)) || (rc = upload(M, &d.tri_orient, hm.topo.tri_orient)) ||
       (rc = upload(M, &d.facet_sigma, hm.facet_sigma)) || (rc = upload(M, &d.facet_nbr, hm.facet_nbr)) ||

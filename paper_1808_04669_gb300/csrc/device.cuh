@@ -42,12 +42,14 @@ struct DevMesh {
   int n_tri, n_facet, n_class, n_stencil;
   double nu;
   double area_total;
+  int elem_df;     // 1: element kernels in double-float (mixed form), 0: FP64
   // reference tables
   const double *vw, *vphi, *vdphi, *fw, *fphi, *fdphi;
   const double *lat_inv, *lat_phi, *plat_phi, *mu_lat;
   // element classes
   const double *geo;     // [n_class][kGeo]
   const double *P, *G, *W, *WCt;     // [n_class][...]
+  const float2 *Pdf, *Gdf;           // P and G as double-float (hi, lo) pairs
   const int32_t *tri_class, *tri_nbr, *tri_facet;
   const int8_t *tri_nbr_loc, *tri_orient;
   const double *facet_sigma;

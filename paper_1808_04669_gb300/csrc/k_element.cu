@@ -2,6 +2,7 @@
 // lattice conversion and diagnostics. One thread per triangle; the reference
 // tables sit in shared memory and are read as warp broadcasts.
 #include "device.cuh"
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 
 namespace dgdf {
@@ -138,54 +139,67 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
   }
 }
 
-// Stage kernel (FP64). Modes (StageMode): the stage functional and its
-// condensation (h = P f, gl = G f), the residual alone, the pressure functional,
-// or the projection functional.
-template <int K>
+// Operator entry in precision R (double-float copies avoid FP64 conversions).
+template <typename R>
+__device__ __forceinline__ R op_entry(const double* d, const float2* f, size_t i);
+template <>
+__device__ __forceinline__ double op_entry<double>(const double* d, const float2*, size_t i) {
+  return d[i];
+}
+template <>
+__device__ __forceinline__ dfl op_entry<dfl>(const double*, const float2* f, size_t i) {
+  const float2 v = f[i];
+  return dfl(v.x, v.y);
+}
+
+// Stage kernel. Modes (StageMode): the stage functional and its condensation
+// (h = P f, gl = G f), the residual alone, the pressure functional, or the
+// projection functional. R = double (FP64 form) or dfl (double-float on the
+// FP32 units, mixed form); inputs and outputs are FP64 either way.
+template <int K, typename R>
 __global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
   using D = Dims<K>;
   constexpr int ND = D::ND, L3 = 3 * D::NL;
-  __shared__ SmemTables<K, double> T;
-  load_tables<K, double>(m, T);
+  __shared__ SmemTables<K, R> T;
+  load_tables<K, R>(m, T);
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m.n_tri) return;
-  double up[ND];
+  R up[ND];
   load_coef<ND>(a.up + size_t(t) * ND, up);
-  double f[ND];
+  R f[ND];
   if (a.mode == MODE_PROJECT) {
 #pragma unroll
     for (int i = 0; i < ND; ++i) f[i] = up[i];
   } else {
-    element_residual<K, double>(m, T, t, a.up, up, f);
+    element_residual<K, R>(m, T, t, a.up, up, f);
     if (a.mode == MODE_STAGE) {
-      double un[ND];
+      R un[ND];
       load_coef<ND>(a.un + size_t(t) * ND, un);
+      const R ca = R(a.a), cb = R(a.b), dt = R(a.dt);
 #pragma unroll
-      for (int i = 0; i < ND; ++i) f[i] = a.a * un[i] + a.b * (up[i] + a.dt * f[i]);
+      for (int i = 0; i < ND; ++i) f[i] = ca * un[i] + cb * (up[i] + dt * f[i]);
     }
   }
   if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
 #pragma unroll
-    for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = f[i];
+    for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = double(f[i]);
   }
   if (a.mode == MODE_RESIDUAL) return;
   const int c = m.tri_class[t];
-  const double* P = m.P + size_t(c) * ND * ND;
-  const double* G = m.G + size_t(c) * L3 * ND;
   if (a.mode != MODE_PRESSURE) {
     for (int i = 0; i < ND; ++i) {
-      double v = 0.0;
+      R v = R(0);
 #pragma unroll
-      for (int j = 0; j < ND; ++j) v += P[i * ND + j] * f[j];
-      m.h[size_t(t) * ND + i] = v;
+      for (int j = 0; j < ND; ++j) v += op_entry<R>(m.P, m.Pdf, (size_t(c) * ND + i) * ND + j) * f[j];
+      m.h[size_t(t) * ND + i] = double(v);
     }
   }
   for (int i = 0; i < L3; ++i) {
-    double v = 0.0;
+    R v = R(0);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) v += G[i * ND + j] * f[j];
-    m.gl[size_t(t) * L3 + i] = v;
+    for (int j = 0; j < ND; ++j) v += op_entry<R>(m.G, m.Gdf, (size_t(c) * L3 + i) * ND + j) * f[j];
+    m.gl[size_t(t) * L3 + i] = double(v);
   }
 }
 
@@ -468,7 +482,11 @@ cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double*
 }
 
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
-  DGDF_DISPATCH_K(m.k, (k_stage<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
+  if (m.elem_df) {
+    DGDF_DISPATCH_K(m.k, (k_stage<K, dfl><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
+  } else {
+    DGDF_DISPATCH_K(m.k, (k_stage<K, double><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
+  }
   return cudaGetLastError();
 }
 

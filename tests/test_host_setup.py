@@ -46,7 +46,7 @@ def test_kernel_names(g):
     while L.dg_kernel_name(i) is not None:
         names.append(L.dg_kernel_name(i).decode())
         i += 1
-    assert "facet_pcg_fp64" in names and "stage_residual_fp64" in names
+    assert "facet_pcg_fp64" in names and "stage_residual" in names
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
