@@ -235,6 +235,17 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     dg_mesh_destroy(M);
     return code;
   };
+  // lattice structure (translation-invariant split-square mesh): renumber facets in lattice
+  // order before anything facet-indexed is uploaded
+  dgdf::Lattice lat;
+  const int lat_fp32 = p.precision == DG_PRECISION_MIXED;
+  int lat_blocks = 0;
+  if (p.precond == DG_PRECOND_AUTO) {
+    dgdf::build_lattice(M->hm, tri_coords, lat);
+    if (lat.ok) lat_blocks = dgdf::lattice_blocks(M->hm.k, lat.N, lat_fp32);
+    if (lat.ok && lat_blocks > 0) dgdf::renumber_facets_lattice(M->hm, lat);
+    else M->lattice_why = lat.ok ? "lattice solver does not fit on this device" : lat.why;
+  }
   const dgdf::HostMesh& hm = M->hm;
   const dgdf::RefTables& ref = hm.ref;
   dgdf::DevMesh& d = M->dm;
@@ -313,55 +324,54 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
   M->solver_blocks[0] = dgdf::solver_max_blocks(d, 0);
   M->solver_blocks[1] = dgdf::solver_max_blocks(d, 1);
-  if (p.precond == DG_PRECOND_AUTO) {
-    dgdf::Lattice lat;
-    dgdf::build_lattice(M->hm, tri_coords, lat);
-    const int fp32 = p.precision == DG_PRECISION_MIXED;
-    int nb = lat.ok ? dgdf::lattice_blocks(hm.k, lat.N, fp32) : 0;
-    if (lat.ok && nb > 0) {
-      const int C = lat.C, N = lat.N;
-      const size_t nS = size_t(N) * N * C * C;
-      std::vector<double> sd;
-      std::vector<float> sf;
-      if (fp32) sf.resize(2 * nS); else sd.resize(2 * nS);
-      // host layout [ki][kj][C][C][2] -> device [ki][C][C][kj] complex
-      for (int ki = 0; ki < N; ++ki)
-        for (int kj = 0; kj < N; ++kj)
-          for (int cc = 0; cc < C * C; ++cc)
-            for (int ri = 0; ri < 2; ++ri) {
-              const double v = lat.sinv[((size_t(ki) * N + kj) * C * C + cc) * 2 + ri];
-              const size_t o = ((size_t(ki) * C * C + cc) * N + kj) * 2 + ri;
-              if (fp32) sf[o] = float(v); else sd[o] = v;
-            }
-      const int32_t* fo = nullptr;
-      const double* tw = nullptr;
-      if ((rc = upload(M, &fo, lat.facet_of)) || (rc = upload(M, &tw, lat.twiddle))) return cleanup(rc);
-      if (fp32) {
-        const float* sp = nullptr;
-        if ((rc = upload(M, &sp, sf))) return cleanup(rc);
-        d.lat_sinv = sp;
-        float* xp = nullptr;
-        if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
-        d.lat_x = xp;
-      } else {
-        const double* sp = nullptr;
-        if ((rc = upload(M, &sp, sd))) return cleanup(rc);
-        d.lat_sinv = sp;
-        double* xp = nullptr;
-        if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
-        d.lat_x = xp;
-      }
-      d.lat_facet_of = fo;
-      d.lat_tw = tw;
-      d.lat_N = N;
-      int logn = 0;
-      while ((1 << logn) < N) ++logn;
-      d.lat_logn = logn;
-      M->use_lattice = true;
-      M->lattice_blocks = nb;
+  if (lat.ok && lat_blocks > 0) {
+    const int fp32 = lat_fp32;
+    const int C = lat.C, N = lat.N;
+    const size_t nS = size_t(N) * N * C * C;
+    std::vector<double> sd;
+    std::vector<float> sf;
+    if (fp32) sf.resize(2 * nS); else sd.resize(2 * nS);
+    // host layout [ki][kj][C][C][2] -> device [ki][C][C][kj] complex
+    for (int ki = 0; ki < N; ++ki)
+      for (int kj = 0; kj < N; ++kj)
+        for (int cc = 0; cc < C * C; ++cc)
+          for (int ri = 0; ri < 2; ++ri) {
+            const double v = lat.sinv[((size_t(ki) * N + kj) * C * C + cc) * 2 + ri];
+            const size_t o = ((size_t(ki) * C * C + cc) * N + kj) * 2 + ri;
+            if (fp32) sf[o] = float(v); else sd[o] = v;
+          }
+    std::vector<double>().swap(lat.sinv);
+    const int32_t* fo = nullptr;
+    const int32_t* fe = nullptr;
+    const double* tw = nullptr;
+    if ((rc = upload(M, &fo, lat.facet_of)) || (rc = upload(M, &tw, lat.twiddle)) ||
+        (rc = upload(M, &fe, hm.facet_ext)))
+      return cleanup(rc);
+    if (fp32) {
+      const float* sp = nullptr;
+      if ((rc = upload(M, &sp, sf))) return cleanup(rc);
+      d.lat_sinv = sp;
+      float* xp = nullptr;
+      if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+      d.lat_x = xp;
     } else {
-      M->lattice_why = lat.ok ? "lattice solver does not fit on this device" : lat.why;
+      const double* sp = nullptr;
+      if ((rc = upload(M, &sp, sd))) return cleanup(rc);
+      d.lat_sinv = sp;
+      double* xp = nullptr;
+      if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+      d.lat_x = xp;
     }
+    d.lat_facet_of = fo;
+    d.facet_ext = fe;
+    d.lat_tw = tw;
+    d.lat_N = N;
+    d.lat_tr = dgdf::lattice_tile_rows(hm.k, N, fp32);
+    int logn = 0;
+    while ((1 << logn) < N) ++logn;
+    d.lat_logn = logn;
+    M->use_lattice = true;
+    M->lattice_blocks = lat_blocks;
   }
   *out = M;
   return DG_OK;

@@ -55,6 +55,7 @@ struct DevMesh {
   const double *facet_sigma;
   // facet-system stencil
   const int32_t *facet_nbr, *facet_stencil, *facet_tri;
+  const int32_t *facet_ext;           // internal -> external facet id (NULL: identity)
   const int8_t *facet_loc;
   const double *st_blk, *st_binv;     // [n_stencil][5][nl][nl], [n_stencil][nl][nl]
   const float *st_blk_f, *st_binv_f;
@@ -64,7 +65,7 @@ struct DevMesh {
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
   // lattice (translation-invariant split-square) solver data
-  int lat_N, lat_logn;
+  int lat_N, lat_logn, lat_tr;      // cells per direction, log2 N, rows per tile of the row passes
   const int32_t* lat_facet_of;        // [3][N][N]
   const void* lat_sinv;               // [N][C][C][N] complex (float2 or double2)
   const double* lat_tw;               // [N][2]
@@ -114,6 +115,7 @@ cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
+int lattice_tile_rows(int k, int N, int fp32);
 size_t lattice_smem_bytes(int k, int N, int fp32);
 int lattice_blocks(int k, int N, int fp32);
 cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nblocks, int fp32, cudaStream_t s);

@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(128) k_pressure_lattice(DevMesh m, const doubl
     }
   }
   if (pf && i < m.n_facet) {
+    const int fo = m.facet_ext ? m.facet_ext[i] : i;
     double lam[NL];
 #pragma unroll
     for (int j = 0; j < NL; ++j) lam[j] = m.lam[size_t(i) * NL + j];
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(128) k_pressure_lattice(DevMesh m, const doubl
       double v = 0.0;
 #pragma unroll
       for (int j = 0; j < NL; ++j) v += m.mu_lat[p * NL + j] * lam[j];
-      pf[size_t(i) * NL + p] = v;
+      pf[size_t(fo) * NL + p] = v;
     }
   }
 }

@@ -10,7 +10,7 @@
 // the preconditioned operator is the identity up to R's rounding, so a solve
 // takes one or two iterations (FP64) or a few (FP32), instead of O(N).
 // The transforms are radix-2 FFTs in shared memory (N a power of two):
-//   rows  : DFT along i of r gathered from facet order, tile of 8 rows per pass
+//   rows  : DFT along i of r (facets numbered in lattice order), tiles of rows
 //   column: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j
 //   rows  : inverse DFT along i, scattered back to facet order (scaled 1/N^2)
 // with a grid barrier between the three passes. One persistent cooperative
@@ -23,7 +23,6 @@ namespace dgdf {
 namespace {
 
 constexpr int kLatThreads = 512;
-constexpr int kTileRows = 8;
 
 template <typename R>
 struct CxT;
@@ -96,31 +95,34 @@ template <int K, typename R>
 struct LatCtx {
   using C2 = typename CxT<R>::T;
   static constexpr int NL = K + 1, C = 3 * NL;
-  int N, logn, ntj;
+  int N, logn, tr, ntj;
   C2* tw;
   C2* buf;
   C2* X;          // [C][N(ki)][N(j)]
   const C2* S;    // [N(ki)][C][C][N(kj)]
-  const int32_t* fo;   // [3][N(j)][N(i)] -> facet
 };
 
-// Row pass, forward: gather r (optionally first updating r -= alpha q, lam += alpha p),
+// Facets are numbered (type, j, i) on a lattice mesh, so a tile of tr rows of one
+// facet type with all k+1 modes is one contiguous range of the facet-major vectors:
+// DOF index ((type N + j) N + i)(k+1) + m.
+
+// Row pass, forward: read r (optionally first updating r -= alpha q, lam += alpha p),
 // DFT along i, store transposed. Accumulates r.r into *rr.
 template <int K, typename R>
 __device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool update, double alpha, const double* p,
                              double* rr) {
   using C2 = typename CxT<R>::T;
-  constexpr int NL = K + 1, C = 3 * NL;
+  constexpr int NL = K + 1;
   const int N = L.N, logn = L.logn;
-  const int ntiles = C * L.ntj;
+  const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int c = tile / L.ntj, j0 = (tile - c * L.ntj) * kTileRows;
-    const int rows = min(kTileRows, N - j0);
-    const int ty = c / NL, mm = c - ty * NL;
-    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
-      const int r_ = e >> logn, i = e & (N - 1);
-      const int f = __ldg(&L.fo[(size_t(ty) * N + j0 + r_) * N + i]);
-      const size_t o = size_t(f) * NL + mm;
+    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * L.tr;
+    const int rows = min(L.tr, N - j0);
+    const size_t base = (size_t(ty) * N + j0) * N * NL;
+    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
+      const int mm = e % NL, rest = e / NL;
+      const int i = rest & (N - 1), r_ = rest >> logn;
+      const size_t o = base + e;
       double rv = __ldcg(&m.r[o]);
       if (update) {
         rv -= alpha * __ldcg(&m.q[o]);
@@ -128,24 +130,27 @@ __device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool updat
         m.lam[o] += alpha * __ldcg(&p[o]);
       }
       *rr += rv * rv;
-      L.buf[r_ * N + brev(i, logn)] = C2{R(rv), R(0)};
+      L.buf[(mm * rows + r_) * N + brev(i, logn)] = C2{R(rv), R(0)};
     }
     __syncthreads();
-    fft_dit(L.buf, rows, logn, L.tw, false);
-    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
-      const int ki = e / rows, r_ = e - ki * rows;
-      L.X[(size_t(c) * N + ki) * N + j0 + r_] = L.buf[r_ * N + ki];
+    fft_dit(L.buf, NL * rows, logn, L.tw, false);
+    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
+      const int r_ = e % rows, rest = e / rows;
+      const int ki = rest & (N - 1), mm = rest >> logn;
+      L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_] = L.buf[(mm * rows + r_) * N + ki];
     }
     __syncthreads();
   }
 }
 
-// Column pass: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j.
+// Column pass: DFT along j, multiply by S^(kappa)^-1 (warp c computes component c of 32
+// consecutive k_j), inverse DFT along j.
 template <int K, typename R>
 __device__ void columns(const LatCtx<K, R>& L) {
   using C2 = typename CxT<R>::T;
   constexpr int C = LatCtx<K, R>::C;
   const int N = L.N, logn = L.logn;
+  const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
   for (int ki = blockIdx.x; ki < N; ki += gridDim.x) {
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
       const int c = e >> logn, j = e & (N - 1);
@@ -154,22 +159,16 @@ __device__ void columns(const LatCtx<K, R>& L) {
     __syncthreads();
     fft_dit(L.buf, C, logn, L.tw, false);
     const C2* S = L.S + size_t(ki) * C * C * N;
-    for (int kj0 = 0; kj0 < N; kj0 += blockDim.x) {
-      const int kj = kj0 + threadIdx.x;
-      C2 x[C];
-      if (kj < N)
+    for (int kj0 = 0; kj0 < N; kj0 += 32) {
+      const int kj = kj0 + lane;
+      const bool act = wc < C && kj < N;
+      C2 y = {R(0), R(0)};
+      if (act) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) x[c] = L.buf[c * N + kj];
-      __syncthreads();
-      if (kj < N) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          C2 y = {R(0), R(0)};
-#pragma unroll
-          for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(c) * C + cc) * N + kj]), x[cc]));
-          L.buf[c * N + kj] = y;
-        }
+        for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(wc) * C + cc) * N + kj]), L.buf[cc * N + kj]));
       }
+      __syncthreads();
+      if (act) L.buf[wc * N + kj] = y;
       __syncthreads();
     }
     fft_dif(L.buf, C, logn, L.tw, true);
@@ -181,30 +180,30 @@ __device__ void columns(const LatCtx<K, R>& L) {
   }
 }
 
-// Row pass, inverse: inverse DFT along i, z = result / N^2 scattered to facet order.
+// Row pass, inverse: inverse DFT along i, z = result / N^2 in facet order.
 // Accumulates r.z_new into *rz and, if with_old, r.z_old into *rzo.
 template <int K, typename R>
 __device__ void rows_inverse(const DevMesh& m, const LatCtx<K, R>& L, bool with_old, double* rz, double* rzo) {
-  constexpr int NL = K + 1, C = 3 * NL;
+  constexpr int NL = K + 1;
   const int N = L.N, logn = L.logn;
   const double scale = 1.0 / (double(N) * double(N));
-  const int ntiles = C * L.ntj;
+  const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int c = tile / L.ntj, j0 = (tile - c * L.ntj) * kTileRows;
-    const int rows = min(kTileRows, N - j0);
-    const int ty = c / NL, mm = c - ty * NL;
-    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
-      const int ki = e / rows, r_ = e - ki * rows;
-      L.buf[r_ * N + ki] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j0 + r_]);
+    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * L.tr;
+    const int rows = min(L.tr, N - j0);
+    const size_t base = (size_t(ty) * N + j0) * N * NL;
+    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
+      const int r_ = e % rows, rest = e / rows;
+      const int ki = rest & (N - 1), mm = rest >> logn;
+      L.buf[(mm * rows + r_) * N + ki] = __ldcg(&L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_]);
     }
     __syncthreads();
-    fft_dif(L.buf, rows, logn, L.tw, true);
-    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
-      const int r_ = e >> logn, p = e & (N - 1);
-      const int i = brev(p, logn);
-      const int f = __ldg(&L.fo[(size_t(ty) * N + j0 + r_) * N + i]);
-      const size_t o = size_t(f) * NL + mm;
-      const double zv = double(L.buf[r_ * N + p].x) * scale;
+    fft_dif(L.buf, NL * rows, logn, L.tw, true);
+    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
+      const int mm = e % NL, rest = e / NL;
+      const int i = rest & (N - 1), r_ = rest >> logn;
+      const size_t o = base + e;
+      const double zv = double(L.buf[(mm * rows + r_) * N + brev(i, logn)].x) * scale;
       const double rv = __ldcg(&m.r[o]);
       if (with_old) *rzo += rv * __ldcg(&m.z[o]);
       *rz += rv * zv;
@@ -222,12 +221,12 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
   LatCtx<K, R> L;
   L.N = m.lat_N;
   L.logn = m.lat_logn;
-  L.ntj = (L.N + kTileRows - 1) / kTileRows;
+  L.tr = m.lat_tr;
+  L.ntj = (L.N + L.tr - 1) / L.tr;
   L.tw = reinterpret_cast<C2*>(smem_raw);
   L.buf = L.tw + (L.N > 1 ? L.N / 2 : 1);
   L.X = reinterpret_cast<C2*>(m.lat_x);
   L.S = reinterpret_cast<const C2*>(m.lat_sinv);
-  L.fo = m.lat_facet_of;
   for (int t = threadIdx.x; t < L.N / 2; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
   __syncthreads();
   const int nF = m.n_facet;
@@ -393,10 +392,21 @@ const void* lattice_kernel(int k, int fp32) {
 
 }  // namespace
 
+int lattice_tile_rows(int k, int N, int fp32) {
+  const size_t cx = fp32 ? 8 : 16;
+  const size_t budget = 96 * 1024;
+  long long tr = (long long)(budget / (size_t(k + 1) * N * cx));
+  if (tr > 8) tr = 8;
+  if (tr < 1) tr = 1;
+  if (tr > N) tr = N;
+  return int(tr);
+}
+
 size_t lattice_smem_bytes(int k, int N, int fp32) {
   const int C = 3 * (k + 1);
   const size_t cx = fp32 ? 8 : 16;
-  return (size_t(N > 1 ? N / 2 : 1) + size_t(C > kTileRows ? C : kTileRows) * N) * cx;
+  const size_t rows_buf = size_t(k + 1) * lattice_tile_rows(k, N, fp32);
+  return (size_t(N > 1 ? N / 2 : 1) + (size_t(C) > rows_buf ? size_t(C) : rows_buf) * N) * cx;
 }
 
 int lattice_blocks(int k, int N, int fp32) {

@@ -839,4 +839,30 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
   L.ok = true;
 }
 
+void renumber_facets_lattice(HostMesh& hm, Lattice& L) {
+  Topology& T = hm.topo;
+  const int64_t nF = T.n_facet;
+  std::vector<int32_t> nw(nF), old_of_new(nF);
+  for (int64_t n = 0; n < nF; ++n) {
+    old_of_new[n] = L.facet_of[n];
+    nw[L.facet_of[n]] = int32_t(n);
+  }
+  auto permute = [&](auto& v, int width) {
+    auto w = v;
+    for (int64_t n = 0; n < nF; ++n)
+      for (int c = 0; c < width; ++c) w[n * width + c] = v[size_t(old_of_new[n]) * width + c];
+    v.swap(w);
+  };
+  permute(T.facet_tri, 2);
+  permute(T.facet_loc, 2);
+  permute(hm.facet_sigma, 1);
+  permute(hm.facet_nbr, 4);
+  for (auto& x : hm.facet_nbr) x = nw[x];
+  permute(hm.facet_stencil, 1);
+  permute(hm.facet_side0, 1);
+  for (auto& x : T.tri_facet) x = nw[x];
+  for (int64_t n = 0; n < nF; ++n) L.facet_of[n] = int32_t(n);
+  hm.facet_ext = old_of_new;
+}
+
 }  // namespace dgdf

@@ -85,6 +85,7 @@ struct HostMesh {
   std::vector<double> stencil_binv;     // [n_stencil][nl][nl] inverse of the own block (block Jacobi)
   int n_stencil = 0;
   std::vector<int32_t> facet_side0;     // [n_facet] triangle on the stencil's first (canonical) side
+  std::vector<int32_t> facet_ext;       // internal -> external (first-appearance) facet id; empty = identity
   double area_total = 0.0;
 };
 
@@ -95,5 +96,8 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
                     HostMesh& hm, std::string& err);
 // Detects the split-square lattice structure and computes the inverse Fourier symbol.
 void build_lattice(const HostMesh& hm, const double* X, Lattice& lat);
+// Renumbers the facets of a lattice mesh internally in (type, j, i) order, so that the
+// facet-major vectors are the Fourier passes' row order; records the external ids.
+void renumber_facets_lattice(HostMesh& hm, Lattice& lat);
 
 }  // namespace dgdf
