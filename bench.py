@@ -160,6 +160,13 @@ def fp64_peak_tflops(sm_mhz):
     return 2 * 2 * 152 * sm_mhz * 1e6 / 1e12
 
 
+def workload_label(w, N, n_tri):
+    ic = {"shear": "double shear layer", "tgv": "Taylor-Green", "spectrum": "random-spectrum field (seed %d)" % w.seed}
+    dom = "[0,2pi]^2" if w.L > 1.5 else "unit square"
+    return "%s, %s periodic, %dx%d split squares (%d triangles), BDM_%d, nu=%g, SSP-RK3, CFL dt" % (
+        ic.get(w.ic, w.ic), dom, N, N, n_tri, w.k, w.nu)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -173,8 +180,9 @@ def run_ours(args):
     _b.build()
     import paper_1808_04669_gb300 as g
     import synth
-    vid, X, vals, dt = synth.make_workload(WORKLOAD, N=args.n)
-    w = synth.WORKLOADS[WORKLOAD]
+    workload = args.workload or WORKLOAD
+    vid, X, vals, dt = synth.make_workload(workload, N=args.n)
+    w = synth.WORKLOADS[workload]
     k = w.k
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -288,8 +296,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 PCG + f32 increment in f64 refinement (f64 state)",
         "data": "synthetic (double shear layer sampled at lattice points, seeded)",
-        "config": {"workload": "double shear layer, [0,2pi]^2 periodic, %dx%d split squares (%d triangles), "
-                               "BDM_3, nu=1e-4, SSP-RK3, CFL dt" % (args.n or w.N, args.n or w.N, mixed.n_tri),
+        "config": {"workload": workload_label(w, args.n or w.N, mixed.n_tri),
                    "N": args.n or w.N, "k": k, "nu": w.nu, "dt": dt,
                    "n_tri": mixed.n_tri, "n_facet": mixed.n_facet, "broken_velocity_dofs": mixed.n_vel_dofs,
                    "multiplier_dofs": mixed.n_lam_dofs, "l2": "flushed between timed steps (512 MiB write)",
@@ -399,6 +406,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--summarize-launches", metavar="CSV", help="print a per-kernel summary of an ncu launch list")
+    ap.add_argument("--workload", default=None, help="named workload (default %s); the bench line is on the default" % WORKLOAD)
     ap.add_argument("--n", type=int, default=None,
                     help="mesh size override (smaller cases for profiling only; not a bench line)")
     args = ap.parse_args()

@@ -59,6 +59,7 @@ extern "C" {
 #endif
 
 typedef struct dg_mesh dg_mesh;
+typedef struct dg_batch dg_batch;
 
 typedef enum {
   DG_OK = 0,
@@ -128,6 +129,20 @@ int dg_project_divfree(dg_mesh* mesh);
  * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
  * a residual norm became NaN/Inf (the state is then undefined). */
 int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
+
+/* Ensembles: advance several independent meshes (any sizes, degrees, viscosities,
+ * precision forms) together. dg_batch_create records the members (the batch does
+ * not own them; destroy the batch before its members); all work of a batch call
+ * is enqueued on cuda_stream. dg_batch_rk3_step advances member i by nsteps
+ * SSP-RK3 steps of size dt[i] (host array of n). One step of all members is
+ * captured once as a CUDA graph and replayed per step; the first step after
+ * creation, a projection or a change of any dt runs eagerly (it warms the
+ * solver and fixes the step sizes the graph holds), and the graph is re-captured
+ * when the step sizes change. Results equal those of dg_rk3_step on each member.
+ * Returns the first member's non-OK status (all members are still advanced). */
+int dg_batch_create(int n, dg_mesh* const* meshes, void* cuda_stream, dg_batch** out);
+int dg_batch_destroy(dg_batch* batch);
+int dg_batch_rk3_step(dg_batch* batch, const double* dt, int64_t nsteps);
 
 /* Pressure of the current state: the (w, lam) of eq. (12) with the functional
  * L(u) alone, so w ~ p in the elements and lam ~ p on the skeleton (Theorem 2,

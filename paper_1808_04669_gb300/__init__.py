@@ -146,6 +146,37 @@ class DGMesh:
         return res
 
 
+class DGBatch:
+    """An ensemble of DGMesh members advanced together (dg_batch_create / dg_batch_rk3_step)."""
+
+    def __init__(self, meshes, stream=None):
+        L = lib()
+        self.meshes = list(meshes)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        check(L.dg_batch_create(len(self.meshes), arr, ctypes.c_void_p(int(stream)), ctypes.byref(h)),
+              "dg_batch_create")
+        self._h = h
+
+    def rk3_step(self, dt, nsteps=1):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self.meshes),)))
+        check(lib().dg_batch_rk3_step(self._h, d.ctypes.data_as(ctypes.c_void_p), int(nsteps)), "dg_batch_rk3_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def host_topology(tri_vertex_ids, tri_coords):
     """Facet topology computed by the library's host set-up (no GPU): (tri_facet, tri_orient, facet_tri)."""
     L = lib()
@@ -240,5 +271,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "facet_solve_noalloc",
            "lib"]

@@ -450,35 +450,161 @@ int dg_project_divfree(dg_mesh* M) {
   return finish(M, true);
 }
 
+}  // extern "C"
+
+namespace {
+
+const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0}, kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
+
+// Enqueue one SSP-RK3 step (eq. (8)) of M on its stream: per stage the residual +
+// condensation kernel, the facet solve (warm-started from the previous stage's
+// multipliers rescaled by b dt) and the recovery. No synchronisation.
+int enqueue_step(dg_mesh* M, double dt) {
+  dgdf::DevMesh& d = M->dm;
+  int rc = DG_OK;
+  for (int s = 0; s < 3; ++s) {
+    const double a = kRkA[s], b = kRkB[s];
+    const double* up = (s == 0) ? d.u : d.ustage;
+    double* out = (s == 2) ? d.u : d.ustage;
+    dgdf::StageArgs sa{};
+    sa.mode = dgdf::MODE_STAGE;
+    sa.a = a;
+    sa.b = b;
+    sa.dt = dt;
+    sa.un = d.u;
+    sa.up = up;
+    if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
+    const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
+    if ((rc = solve(M, warm))) return rc;
+    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
+    M->last_bdt = b * dt;
+    M->has_lam = true;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+struct dg_batch {
+  std::vector<dg_mesh*> members;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<double> graph_dt;
+};
+
+extern "C" {
+
 int dg_rk3_step(dg_mesh* M, double dt, int64_t nsteps) {
   if (int rc = check_mesh(M)) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
   int rc = reset_flags(M);
   if (rc) return rc;
-  static const double kA[3] = {0.0, 0.75, 1.0 / 3.0}, kB[3] = {1.0, 0.25, 2.0 / 3.0};
-  dgdf::DevMesh& d = M->dm;
-  for (int64_t n = 0; n < nsteps; ++n) {
-    for (int s = 0; s < 3; ++s) {
-      const double a = kA[s], b = kB[s];
-      const double* up = (s == 0) ? d.u : d.ustage;
-      double* out = (s == 2) ? d.u : d.ustage;
-      dgdf::StageArgs sa{};
-      sa.mode = dgdf::MODE_STAGE;
-      sa.a = a;
-      sa.b = b;
-      sa.dt = dt;
-      sa.un = d.u;
-      sa.up = up;
-      if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
-      const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
-      if ((rc = solve(M, warm))) return rc;
-      if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
-      M->last_bdt = b * dt;
-      M->has_lam = true;
-    }
-  }
+  for (int64_t n = 0; n < nsteps; ++n)
+    if ((rc = enqueue_step(M, dt))) return rc;
   return finish(M, true);
+}
+
+int dg_batch_create(int n, dg_mesh* const* meshes, void* cuda_stream, dg_batch** out) {
+  g_err.clear();
+  if (!out || n < 1 || !meshes) return fail(DG_ERR_INVALID_ARG, "need n >= 1 meshes and an output pointer");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!meshes[i]) return fail(DG_ERR_INVALID_ARG, "NULL member mesh");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(DG_ERR_INVALID_ARG, "a mesh appears twice in the batch");
+  }
+  dg_batch* B = new dg_batch();
+  B->members.assign(meshes, meshes + n);
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = B;
+  return DG_OK;
+}
+
+int dg_batch_destroy(dg_batch* B) {
+  if (!B) return DG_OK;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  delete B;
+  return DG_OK;
+}
+
+int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
+  if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
+  if (!dt) return fail(DG_ERR_INVALID_ARG, "NULL dt");
+  if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  const size_t n = B->members.size();
+  for (size_t i = 0; i < n; ++i)
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(DG_ERR_INVALID_ARG, "every dt must be finite and > 0");
+  if (nsteps == 0) return DG_OK;
+  // every member runs on the batch stream for the duration of the call
+  std::vector<cudaStream_t> saved(n);
+  std::vector<bool> saved_prof(n);
+  for (size_t i = 0; i < n; ++i) {
+    saved[i] = B->members[i]->stream;
+    saved_prof[i] = B->members[i]->prof;
+    B->members[i]->stream = B->stream;
+  }
+  auto restore = [&](int code) {
+    for (size_t i = 0; i < n; ++i) {
+      B->members[i]->stream = saved[i];
+      B->members[i]->prof = saved_prof[i];
+    }
+    return code;
+  };
+  int rc = DG_OK;
+  for (dg_mesh* M : B->members)
+    if ((rc = reset_flags(M))) return restore(rc);
+  // The captured step assumes warm-started solves with a fixed step size: run one step
+  // eagerly when any member is cold or the step sizes changed.
+  bool same_dt = B->exec && B->graph_dt.size() == n;
+  for (size_t i = 0; same_dt && i < n; ++i) same_dt = B->graph_dt[i] == dt[i];
+  bool warm = true;
+  for (dg_mesh* M : B->members) warm = warm && M->has_lam;
+  int64_t done = 0;
+  if (!warm || !same_dt) {
+    for (size_t i = 0; i < n; ++i)
+      if ((rc = enqueue_step(B->members[i], dt[i]))) return restore(rc);
+    done = 1;
+  }
+  if (done < nsteps && !same_dt) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    for (dg_mesh* M : B->members) M->prof = false;   // no timing events inside the graph
+    cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e)));
+    for (size_t i = 0; i < n && rc == DG_OK; ++i) rc = enqueue_step(B->members[i], dt[i]);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(B->stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return restore(rc);
+    }
+    if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e)));
+    e = cudaGraphInstantiate(&B->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return restore(fail(DG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)));
+    }
+    B->graph = g;
+    B->graph_dt.assign(dt, dt + n);
+  }
+  for (int64_t s = done; s < nsteps; ++s) {
+    cudaError_t e = cudaGraphLaunch(B->exec, B->stream);
+    if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e)));
+  }
+  cudaError_t e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e)));
+  restore(DG_OK);
+  int first = DG_OK;
+  for (dg_mesh* M : B->members) {
+    const int r = finish(M, true);
+    if (r != DG_OK && first == DG_OK) first = r;
+  }
+  return first;
 }
 
 int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) {
