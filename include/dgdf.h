@@ -132,8 +132,8 @@ int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
 
 /* Ensembles: advance several independent meshes (any sizes, degrees, viscosities,
  * precision forms) together. dg_batch_create records the members (the batch does
- * not own them; destroy the batch before its members); all work of a batch call
- * is enqueued on cuda_stream. dg_batch_rk3_step advances member i by nsteps
+ * not own them; destroy the batch before its members). A batch call runs after the
+ * work already on cuda_stream, on a stream the batch owns, and returns when it is done. dg_batch_rk3_step advances member i by nsteps
  * SSP-RK3 steps of size dt[i] (host array of n). One step of all members is
  * captured once as a CUDA graph and replayed per step; the first step after
  * creation, a projection or a change of any dt runs eagerly (it warms the

@@ -487,7 +487,9 @@ int enqueue_step(dg_mesh* M, double dt) {
 
 struct dg_batch {
   std::vector<dg_mesh*> members;
-  cudaStream_t stream = nullptr;
+  cudaStream_t user = nullptr;     // the caller's stream
+  cudaStream_t stream = nullptr;   // the batch's own stream: graphs are captured and replayed here
+  cudaEvent_t ev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<double> graph_dt;
@@ -517,15 +519,24 @@ int dg_batch_create(int n, dg_mesh* const* meshes, void* cuda_stream, dg_batch**
   }
   dg_batch* B = new dg_batch();
   B->members.assign(meshes, meshes + n);
-  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  B->user = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    dg_batch_destroy(B);
+    return fail(DG_ERR_CUDA, std::string("dg_batch_create: ") + cudaGetErrorString(e));
+  }
   *out = B;
   return DG_OK;
 }
 
 int dg_batch_destroy(dg_batch* B) {
   if (!B) return DG_OK;
+  if (B->stream) cudaStreamSynchronize(B->stream);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->ev) cudaEventDestroy(B->ev);
+  if (B->stream) cudaStreamDestroy(B->stream);
   delete B;
   return DG_OK;
 }
@@ -554,6 +565,10 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     return code;
   };
   int rc = DG_OK;
+  // order after the caller's stream, then work on the batch's own stream
+  cudaError_t e0 = cudaEventRecord(B->ev, B->user);
+  if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(B->stream, B->ev, 0);
+  if (e0 != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("dg_batch_rk3_step: ") + cudaGetErrorString(e0)));
   for (dg_mesh* M : B->members)
     if ((rc = reset_flags(M))) return restore(rc);
   // The captured step assumes warm-started solves with a fixed step size: run one step
