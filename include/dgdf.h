@@ -130,6 +130,32 @@ int dg_project_divfree(dg_mesh* mesh);
  * a residual norm became NaN/Inf (the state is then undefined). */
 int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
 
+/* State as coefficients in the library's orthonormal basis (per triangle: 2 x n_lat(k)
+ * scalar Dubiner polynomials scaled to unit L2 norm on the triangle; component-major,
+ * double [n_tri][2 n_lat(k)]). The Euclidean inner product of coefficient arrays is
+ * the L2 inner product of the fields, so gradients in this representation are L2
+ * Riesz representers. */
+int dg_set_coefficients(dg_mesh* mesh, const double* coef, int on_device);
+int dg_get_coefficients(dg_mesh* mesh, double* coef, int on_device);
+
+/* Change the viscosity nu >= 0 of an existing mesh (nothing else depends on it). */
+int dg_set_viscosity(dg_mesh* mesh, double nu);
+
+/* Vector-Jacobian product of nsteps SSP-RK3 steps (the hand-written adjoint of eq. (8)).
+ * With the current state u_0, it advances the state to u_K (K = nsteps, as dg_rk3_step
+ * would) and returns, for the output cotangent ubar (coefficients, [n_tri][2 n_lat(k)]),
+ * u0bar = (du_K/du_0)^T ubar in the same representation and *nubar = ubar . du_K/dnu.
+ * Each stage u_s = Q(a M u^n + b [M u' + dt L(u')]) is reversed with the symmetric
+ * hybrid-mixed solve Q (F-bar = Q u_s-bar), then u'-bar += b (F-bar + dt J_L(u')^T F-bar)
+ * and u^n-bar += a F-bar, with J_L^T the transposed Jacobian of the upwind/SIPG residual
+ * (d|s|/ds = sign(s), sign(0) = 0). u0bar is the gradient with respect to u_0 in the
+ * broken space; pair it with divergence-free directions (or project it) for the
+ * gradient on V_h^{k,-1}. States are kept every checkpoint_every steps and each segment
+ * is recomputed during the reverse sweep (device memory: (K/checkpoint_every +
+ * 3 checkpoint_every + 5) states, allocated for the call). */
+int dg_rk3_vjp(dg_mesh* mesh, double dt, int64_t nsteps, int64_t checkpoint_every, const double* ubar,
+               double* u0bar, double* nubar, int on_device);
+
 /* Ensembles: advance several independent meshes (any sizes, degrees, viscosities,
  * precision forms) together. dg_batch_create records the members (the batch does
  * not own them; destroy the batch before its members). A batch call runs after the

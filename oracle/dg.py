@@ -152,6 +152,82 @@ class Discretization:
         R += Rf.sum(axis=1)
         return R.reshape(self.n_tri, self.nd)
 
+    # ---------------------------------------------------------------- tangent
+    def residual_tangent(self, U, dU, dnu=0.0):
+        """Directional derivative of R = L(u)(phi_i) at u along (du, dnu) (used to check the adjoint).
+
+        Derivative of the volume term (u x u - nu grad u) : grad phi and of the facet
+        terms of eq. (7) and eq. (18). The upwind flux (u.n) u^up is differentiated in
+        its equivalent form 1/2 (u.n)(u0 + u1) + 1/2 |u.n| (u0 - u1) with d|s|/ds = sign(s),
+        sign(0) = 0.
+        """
+        nu = self.nu
+        ns = self.ns
+        U = np.asarray(U, dtype=np.float64).reshape(self.n_tri, 2, ns)
+        dU = np.asarray(dU, dtype=np.float64).reshape(self.n_tri, 2, ns)
+        R = np.zeros((self.n_tri, 2, ns))
+        for tri in self._chunks(self.n_tri):
+            P, W = self._vol(tri)
+            V, G = self._basis(self.exps, tri, P)
+            u = np.einsum("tqj,tcj->tqc", V, U[tri])
+            du = np.einsum("tqj,tcj->tqc", V, dU[tri])
+            gu = np.einsum("tqjd,tcj->tqcd", G, U[tri])
+            gdu = np.einsum("tqjd,tcj->tqcd", G, dU[tri])
+            Flx = du[..., :, None] * u[..., None, :] + u[..., :, None] * du[..., None, :] - nu * gdu - dnu * gu
+            R[tri] += np.einsum("tq,tqcd,tqjd->tcj", W, Flx, G, optimize=True)
+        T = self.topo
+        Rf = np.zeros((self.n_tri, 3, 2, ns))
+        sig_all = self.alpha * self.k ** 2 / np.maximum(T.diam[T.facet_tri[:, 0]], T.diam[T.facet_tri[:, 1]])
+        for f in self._chunks(self.n_facet):
+            t0, V0, G0 = self._facet_side(f, 0)
+            t1, V1, G1 = self._facet_side(f, 1)
+            n0 = T.normal[t0, T.facet_loc[f, 0]]
+            u0 = np.einsum("fqj,fcj->fqc", V0, U[t0])
+            u1 = np.einsum("fqj,fcj->fqc", V1, U[t1])
+            d0 = np.einsum("fqj,fcj->fqc", V0, dU[t0])
+            d1 = np.einsum("fqj,fcj->fqc", V1, dU[t1])
+            gu0 = np.einsum("fqjd,fcj->fqcd", G0, U[t0])
+            gu1 = np.einsum("fqjd,fcj->fqcd", G1, U[t1])
+            gd0 = np.einsum("fqjd,fcj->fqcd", G0, dU[t0])
+            gd1 = np.einsum("fqjd,fcj->fqcd", G1, dU[t1])
+            un = 0.5 * np.einsum("fqc,fc->fq", u0 + u1, n0)
+            dun = 0.5 * np.einsum("fqc,fc->fq", d0 + d1, n0)
+            sg = np.sign(un)
+            dflux = (0.5 * dun[..., None] * (u0 + u1) + 0.5 * un[..., None] * (d0 + d1)
+                     + 0.5 * (sg * dun)[..., None] * (u0 - u1) + 0.5 * np.abs(un)[..., None] * (d0 - d1))
+            jump, djump = u0 - u1, d0 - d1
+            dn_avg = 0.5 * np.einsum("fqcd,fd->fqc", gu0 + gu1, n0)
+            ddn_avg = 0.5 * np.einsum("fqcd,fd->fqc", gd0 + gd1, n0)
+            sig = sig_all[f][:, None, None]
+            wq = self.fw[None, :] * T.facet_len[f][:, None]
+            A0 = -dflux + nu * ddn_avg - nu * sig * djump + dnu * (dn_avg - sig * jump)
+            Bv = 0.5 * (nu * djump + dnu * jump)
+            dn0 = np.einsum("fqjd,fd->fqj", G0, n0)
+            dn1 = np.einsum("fqjd,fd->fqj", G1, n0)
+            c0 = np.einsum("fq,fqc,fqj->fcj", wq, A0, V0) + np.einsum("fq,fqc,fqj->fcj", wq, Bv, dn0)
+            c1 = np.einsum("fq,fqc,fqj->fcj", wq, -A0, V1) + np.einsum("fq,fqc,fqj->fcj", wq, Bv, dn1)
+            Rf[t0, T.facet_loc[f, 0]] = c0
+            Rf[t1, T.facet_loc[f, 1]] = c1
+        R += Rf.sum(axis=1)
+        return R.reshape(self.n_tri, self.nd)
+
+    def rk3_tangent(self, U, dU, dt, nsteps=1, dnu=0.0):
+        """Tangent-linear model of SSP-RK3 (eq. (8)): returns (u_K, du_K) for the perturbation (du_0, dnu).
+
+        Each stage is linear in its functional, so du_s = Q(a M du^n + b [M du' + dt dL(u')[du', dnu]])
+        with Q the same hybrid-mixed solve as the forward stage.
+        """
+        for _ in range(int(nsteps)):
+            Us, dUs = [U], [dU]
+            for s, (a, b) in enumerate(RK3_STAGES):
+                Up, dUp = Us[-1], dUs[-1]
+                F = a * self.apply_mass(U) + b * (self.apply_mass(Up) + dt * self.residual(Up))
+                dF = a * self.apply_mass(dU) + b * (self.apply_mass(dUp) + dt * self.residual_tangent(Up, dUp, dnu))
+                Us.append(self.solve_condensed(F)[0])
+                dUs.append(self.solve_condensed(dF)[0])
+            U, dU = Us[-1], dUs[-1]
+        return U, dU
+
     # ------------------------------------------------------------------- mass
     def scalar_mass(self, tri):
         P, W = self._vol(tri)

@@ -125,6 +125,35 @@ class DGMesh:
         keys = ("energy", "enstrophy", "max_div", "max_jump", "last_iters", "total_iters", "solves", "last_relres")
         return dict(zip(keys, list(out)))
 
+    def set_coefficients(self, coef):
+        if isinstance(coef, np.ndarray):
+            coef = np.ascontiguousarray(coef, dtype=np.float64)
+        p, dev = _ptr(coef)
+        check(lib().dg_set_coefficients(self._h, p, dev), "dg_set_coefficients")
+
+    def get_coefficients(self, out=None):
+        if out is None:
+            out = np.empty((self.n_tri, 2 * self.n_lat))
+        p, dev = _ptr(out)
+        check(lib().dg_get_coefficients(self._h, p, dev), "dg_get_coefficients")
+        return out
+
+    def set_viscosity(self, nu):
+        check(lib().dg_set_viscosity(self._h, float(nu)), "dg_set_viscosity")
+
+    def rk3_vjp(self, dt, nsteps, ubar, checkpoint_every=0, out=None):
+        """(u0bar, nubar) for the cotangent ubar of the state after nsteps steps (see dg_rk3_vjp)."""
+        if isinstance(ubar, np.ndarray):
+            ubar = np.ascontiguousarray(ubar, dtype=np.float64)
+        if out is None:
+            out = np.empty((self.n_tri, 2 * self.n_lat)) if isinstance(ubar, np.ndarray) else ubar.new_empty(ubar.shape)
+        p1, dev = _ptr(ubar)
+        p2, _ = _ptr(out)
+        nb = ctypes.c_double()
+        check(lib().dg_rk3_vjp(self._h, float(dt), int(nsteps), int(checkpoint_every), p1, p2, ctypes.byref(nb), dev),
+              "dg_rk3_vjp")
+        return out, nb.value
+
     def solver_stats(self):
         out = (ctypes.c_double * 8)()
         check(lib().dg_get_solver_stats(self._h, out), "dg_get_solver_stats")

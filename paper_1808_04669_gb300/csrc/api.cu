@@ -3,6 +3,7 @@
 // method runs in the kernels of k_element.cu and k_solver.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,12 +34,13 @@ enum KernelClass {
   KC_PRESSURE,
   KC_SOLVE_LAT64,
   KC_SOLVE_LAT32,
+  KC_ADJOINT,
   KC_COUNT
 };
 const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure",
-                                      "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32"};
+                                      "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32",   "adjoint"};
 
 }  // namespace
 
@@ -620,6 +622,169 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     if (r != DG_OK && first == DG_OK) first = r;
   }
   return first;
+}
+
+int dg_set_coefficients(dg_mesh* M, const double* coef, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!coef) return fail(DG_ERR_INVALID_ARG, "NULL coef");
+  const size_t n = size_t(M->dm.n_tri) * M->hm.nd;
+  CK(cudaMemcpyAsync(M->dm.u, coef, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     M->stream));
+  M->has_lam = false;
+  return finish(M, false);
+}
+
+int dg_get_coefficients(dg_mesh* M, double* coef, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!coef) return fail(DG_ERR_INVALID_ARG, "NULL coef");
+  const size_t n = size_t(M->dm.n_tri) * M->hm.nd;
+  CK(cudaMemcpyAsync(coef, M->dm.u, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     M->stream));
+  return finish(M, false);
+}
+
+int dg_set_viscosity(dg_mesh* M, double nu) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(DG_ERR_INVALID_ARG, "nu must be finite and >= 0");
+  M->p.nu = nu;
+  M->dm.nu = nu;
+  return DG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// y = Q x: the hybrid-mixed solve of eq. (12) applied to the functional with
+// coefficients x (orthonormal basis, M = I); Q is symmetric.
+int apply_Q(dg_mesh* M, const double* x, double* y) {
+  dgdf::StageArgs a{};
+  a.mode = dgdf::MODE_PROJECT;
+  a.up = x;
+  a.un = x;
+  int rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_stage(M->dm, a, M->stream); });
+  if (rc) return rc;
+  if ((rc = solve(M, 0.0))) return rc;
+  return launch(M, KC_ADJOINT, [&] { return dgdf::launch_recover(M->dm, y, M->stream); });
+}
+
+// One SSP-RK3 step that also keeps the stage inputs u^n, u^(1), u^(2) in st[0..2].
+int enqueue_step_keep(dg_mesh* M, double dt, double* const st[3]) {
+  dgdf::DevMesh& d = M->dm;
+  const size_t bytes = size_t(d.n_tri) * d.nd * sizeof(double);
+  int rc = DG_OK;
+  for (int s = 0; s < 3; ++s) {
+    const double* up = (s == 0) ? d.u : d.ustage;
+    CK(cudaMemcpyAsync(st[s], up, bytes, cudaMemcpyDeviceToDevice, M->stream));
+    dgdf::StageArgs sa{};
+    sa.mode = dgdf::MODE_STAGE;
+    sa.a = kRkA[s];
+    sa.b = kRkB[s];
+    sa.dt = dt;
+    sa.un = d.u;
+    sa.up = up;
+    if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
+    const double warm = M->has_lam ? (kRkB[s] * dt) / M->last_bdt : 0.0;
+    if ((rc = solve(M, warm))) return rc;
+    double* out = (s == 2) ? d.u : d.ustage;
+    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
+    M->last_bdt = kRkB[s] * dt;
+    M->has_lam = true;
+  }
+  return DG_OK;
+}
+
+struct DevBuffers {
+  std::vector<void*> p;
+  ~DevBuffers() {
+    for (void* q : p) cudaFree(q);
+  }
+  double* get(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(double)) != cudaSuccess) return nullptr;
+    p.push_back(q);
+    return static_cast<double*>(q);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, const double* ubar, double* u0bar,
+               double* nubar, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (nsteps < 1) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 1");
+  if (!ubar || !u0bar) return fail(DG_ERR_INVALID_ARG, "NULL ubar or u0bar");
+  if (checkpoint_every < 1 || checkpoint_every > nsteps) checkpoint_every = nsteps;
+  int rc = reset_flags(M);
+  if (rc) return rc;
+  dgdf::DevMesh& d = M->dm;
+  const size_t n = size_t(d.n_tri) * d.nd, bytes = n * sizeof(double);
+  const int64_t nseg = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  DevBuffers buf;
+  double* ck = buf.get(size_t(nseg) * n);                      // segment start states
+  double* stg = buf.get(size_t(checkpoint_every) * 3 * n);     // stage inputs of one segment
+  double* ub = buf.get(n);
+  double* acc = buf.get(n);
+  double* fb = buf.get(n);
+  double* uK = buf.get(n);
+  double* nu_acc = buf.get(1);
+  if (!ck || !stg || !ub || !acc || !fb || !uK || !nu_acc) return fail(DG_ERR_OOM, "dg_rk3_vjp: device memory for checkpoints");
+  // forward sweep, keeping the state at the start of every segment
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (s % checkpoint_every == 0)
+      CK(cudaMemcpyAsync(ck + size_t(s / checkpoint_every) * n, d.u, bytes, cudaMemcpyDeviceToDevice, M->stream));
+    if ((rc = enqueue_step(M, dt))) return rc;
+  }
+  CK(cudaMemcpyAsync(uK, d.u, bytes, cudaMemcpyDeviceToDevice, M->stream));
+  CK(cudaMemcpyAsync(ub, ubar, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, M->stream));
+  CK(cudaMemsetAsync(nu_acc, 0, sizeof(double), M->stream));
+  // reverse sweep: recompute each segment's stage inputs, then walk its steps backwards
+  for (int64_t g = nseg - 1; g >= 0; --g) {
+    const int64_t s0 = g * checkpoint_every;
+    const int64_t len = std::min<int64_t>(checkpoint_every, nsteps - s0);
+    CK(cudaMemcpyAsync(d.u, ck + size_t(g) * n, bytes, cudaMemcpyDeviceToDevice, M->stream));
+    M->has_lam = false;
+    for (int64_t i = 0; i < len; ++i) {
+      double* const st[3] = {stg + (size_t(i) * 3 + 0) * n, stg + (size_t(i) * 3 + 1) * n, stg + (size_t(i) * 3 + 2) * n};
+      if ((rc = enqueue_step_keep(M, dt, st))) return rc;
+    }
+    for (int64_t i = len - 1; i >= 0; --i) {
+      const double* U[3] = {stg + (size_t(i) * 3 + 0) * n, stg + (size_t(i) * 3 + 1) * n, stg + (size_t(i) * 3 + 2) * n};
+      // stage s: u_s = Q(a_s u^n + b_s (u' + dt L(u'))), u' = U[s]
+      for (int s = 2; s >= 0; --s) {
+        if ((rc = apply_Q(M, ub, fb))) return rc;                       // F-bar = Q u_s-bar
+        const double a = kRkA[s], b = kRkB[s];
+        if (s == 2) {
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, a, 0.0, 0, 0.0, nu_acc, M->stream); })))
+            return rc;                                                   // acc = a F-bar
+        } else if (a != 0.0) {
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, a, 0.0, 1, 0.0, nu_acc, M->stream); })))
+            return rc;                                                   // acc += a F-bar
+        }
+        if (s > 0) {
+          // u'-bar = b (F-bar + dt J_L(u')^T F-bar); nu-bar += b dt dL/dnu(u').F-bar
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, ub, b, b * dt, 0, b * dt, nu_acc, M->stream); })))
+            return rc;
+        } else {
+          // u' = u^n at the first stage: add into acc, which becomes u^n-bar
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, b, b * dt, 1, b * dt, nu_acc, M->stream); })))
+            return rc;
+          CK(cudaMemcpyAsync(ub, acc, bytes, cudaMemcpyDeviceToDevice, M->stream));
+        }
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(d.u, uK, bytes, cudaMemcpyDeviceToDevice, M->stream));
+  M->has_lam = false;
+  CK(cudaMemcpyAsync(u0bar, ub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, M->stream));
+  double nb = 0.0;
+  CK(cudaMemcpyAsync(&nb, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  rc = finish(M, true);
+  if (nubar) *nubar = nb;
+  return rc;
 }
 
 int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) {

@@ -112,6 +112,8 @@ cudaError_t launch_recover(const DevMesh& m, double* out, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
 cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);
+cudaError_t launch_adjoint(const DevMesh& m, const double* u, const double* w, double* out, double cw, double cj,
+                           int accumulate, double nu_coef, double* nu_acc, cudaStream_t s);
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);

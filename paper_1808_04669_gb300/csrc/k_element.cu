@@ -139,6 +139,182 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
   }
 }
 
+// Transposed Jacobian of the residual (adjoint of the stage functional): for the
+// state u and a functional w (coefficients), out = c_w w + c_J J_L(u)^T w with
+//   (J_L(u)^T w)_j = d/du_j L(u)(w)
+//     volume : int psi_j [(u.grad) w + (grad w)^T u]_c - nu int grad psi_j . grad w_c
+//     facets : -int psi_j [n_c (u^up . [w]) + max(u.n, 0) [w]_c]            (upwind flux in its
+//              1/2 (u.n)(u+ + u-) + 1/2 |u.n| (u+ - u-) form, sign(0) = 0)
+//              + nu int [psi_j ({d_n w}_c - sigma [w]_c) + 1/2 d_n psi_j [w]_c]  (SIPG, symmetric)
+// with [w] = w_T - w_neighbour and n the outward normal of T. The viscous part is the
+// SIPG residual of w itself (eq. (18) is symmetric). Block partials of
+// <u, dL/dnu(u)> = B_h(u, w)/nu with the sign of L, i.e. the nu-derivative of
+// L(u)(w), go to red[blockIdx].
+template <int K>
+__device__ void element_adjoint(const DevMesh& m, const SmemTables<K, double>& T, int t, const double* __restrict__ ug,
+                                const double* __restrict__ wg, double (&acc)[Dims<K>::ND], double& nupart) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, ND = D::ND;
+  const double nu = m.nu;
+  const double* geo = m.geo + size_t(m.tri_class[t]) * kGeo;
+  const double Ji[4] = {geo[G_JINV + 0], geo[G_JINV + 1], geo[G_JINV + 2], geo[G_JINV + 3]};
+  const double det = geo[G_DET], s = geo[G_S];
+  double uc[ND], wc[ND];
+  load_coef<ND>(ug + size_t(t) * ND, uc);
+  load_coef<ND>(wg + size_t(t) * ND, wc);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) acc[i] = 0.0;
+  nupart = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < D::NQ; ++q) {
+    double u0 = 0, u1 = 0, a[2][2] = {{0, 0}, {0, 0}}, b[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const double ph = T.vphi[q][j], d0 = T.vdphi[q][j][0], d1 = T.vdphi[q][j][1];
+      u0 += ph * uc[j];
+      u1 += ph * uc[NS + j];
+      a[0][0] += d0 * wc[j];
+      a[0][1] += d1 * wc[j];
+      a[1][0] += d0 * wc[NS + j];
+      a[1][1] += d1 * wc[NS + j];
+      b[0][0] += d0 * uc[j];
+      b[0][1] += d1 * uc[j];
+      b[1][0] += d0 * uc[NS + j];
+      b[1][1] += d1 * uc[NS + j];
+    }
+    u0 *= s;
+    u1 *= s;
+    double gw[2][2], gu[2][2];   // physical gradients d w_c / d x_d, d u_c / d x_d
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      gw[c][0] = s * (a[c][0] * Ji[0] + a[c][1] * Ji[2]);
+      gw[c][1] = s * (a[c][0] * Ji[1] + a[c][1] * Ji[3]);
+      gu[c][0] = s * (b[c][0] * Ji[0] + b[c][1] * Ji[2]);
+      gu[c][1] = s * (b[c][0] * Ji[1] + b[c][1] * Ji[3]);
+    }
+    const double w = T.vw[q] * det;
+    // value-type test terms A_c = (u.grad) w_c + sum_d u_d d_c w_d
+    const double A0 = w * s * (u0 * gw[0][0] + u1 * gw[0][1] + u0 * gw[0][0] + u1 * gw[1][0]);
+    const double A1 = w * s * (u0 * gw[1][0] + u1 * gw[1][1] + u0 * gw[0][1] + u1 * gw[1][1]);
+    // gradient-type test terms: -nu grad w_c . grad psi_j, written through reference gradients
+    const double H00 = -w * s * nu * (gw[0][0] * Ji[0] + gw[0][1] * Ji[1]);
+    const double H01 = -w * s * nu * (gw[0][0] * Ji[2] + gw[0][1] * Ji[3]);
+    const double H10 = -w * s * nu * (gw[1][0] * Ji[0] + gw[1][1] * Ji[1]);
+    const double H11 = -w * s * nu * (gw[1][0] * Ji[2] + gw[1][1] * Ji[3]);
+    nupart -= w * (gu[0][0] * gw[0][0] + gu[0][1] * gw[0][1] + gu[1][0] * gw[1][0] + gu[1][1] * gw[1][1]);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const double ph = T.vphi[q][j], d0 = T.vdphi[q][j][0], d1 = T.vdphi[q][j][1];
+      acc[j] += A0 * ph + H00 * d0 + H01 * d1;
+      acc[NS + j] += A1 * ph + H10 * d0 + H11 * d1;
+    }
+  }
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int tn = m.tri_nbr[size_t(t) * 3 + e];
+    const int en = m.tri_nbr_loc[size_t(t) * 3 + e];
+    const double* geon = m.geo + size_t(m.tri_class[tn]) * kGeo;
+    const double sn = geon[G_S];
+    const double n0 = geo[G_NRM + 2 * e], n1 = geo[G_NRM + 2 * e + 1];
+    const double len = geo[G_FLEN + e];
+    const double sig = m.facet_sigma[m.tri_facet[size_t(t) * 3 + e]];
+    const double mo0 = Ji[0] * n0 + Ji[1] * n1, mo1 = Ji[2] * n0 + Ji[3] * n1;
+    const double mn0 = geon[G_JINV + 0] * n0 + geon[G_JINV + 1] * n1;
+    const double mn1 = geon[G_JINV + 2] * n0 + geon[G_JINV + 3] * n1;
+    double un[ND], wn[ND];
+    load_coef<ND>(ug + size_t(tn) * ND, un);
+    load_coef<ND>(wg + size_t(tn) * ND, wn);
+#pragma unroll 1
+    for (int q = 0; q < D::NQF; ++q) {
+      const int qn = D::NQF - 1 - q;
+      double ui[2] = {0, 0}, uo[2] = {0, 0}, wi[2] = {0, 0}, wo[2] = {0, 0};
+      double dwi[2] = {0, 0}, dwo[2] = {0, 0}, dui[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const double ph = T.fphi[e][q][j];
+        const double dn = T.fdphi[e][q][j][0] * mo0 + T.fdphi[e][q][j][1] * mo1;
+        const double phn = T.fphi[en][qn][j];
+        const double dnn = T.fdphi[en][qn][j][0] * mn0 + T.fdphi[en][qn][j][1] * mn1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          ui[c] += ph * uc[c * NS + j];
+          wi[c] += ph * wc[c * NS + j];
+          dwi[c] += dn * wc[c * NS + j];
+          dui[c] += dn * uc[c * NS + j];
+          uo[c] += phn * un[c * NS + j];
+          wo[c] += phn * wn[c * NS + j];
+          dwo[c] += dnn * wn[c * NS + j];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        ui[c] *= s;
+        wi[c] *= s;
+        dwi[c] *= s;
+        dui[c] *= s;
+        uo[c] *= sn;
+        wo[c] *= sn;
+        dwo[c] *= sn;
+      }
+      const double vn = 0.5 * ((ui[0] + uo[0]) * n0 + (ui[1] + uo[1]) * n1);
+      const double sg = vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0);
+      const double up0 = 0.5 * ((ui[0] + uo[0]) + sg * (ui[0] - uo[0]));
+      const double up1 = 0.5 * ((ui[1] + uo[1]) + sg * (ui[1] - uo[1]));
+      const double jw0 = wi[0] - wo[0], jw1 = wi[1] - wo[1];
+      const double upj = up0 * jw0 + up1 * jw1;
+      const double vp = vn > 0.0 ? vn : 0.0;
+      const double w = T.fw[q] * len;
+      // value-type: convective adjoint + SIPG consistency and penalty of w (nu)
+      const double A0 = w * s * (-(n0 * upj + vp * jw0) + nu * (0.5 * (dwi[0] + dwo[0]) - sig * jw0));
+      const double A1 = w * s * (-(n1 * upj + vp * jw1) + nu * (0.5 * (dwi[1] + dwo[1]) - sig * jw1));
+      // normal-derivative test: SIPG symmetry term
+      const double B0 = w * s * 0.5 * nu * jw0, B1 = w * s * 0.5 * nu * jw1;
+      nupart += w * (ui[0] * (0.5 * (dwi[0] + dwo[0]) - sig * jw0) + ui[1] * (0.5 * (dwi[1] + dwo[1]) - sig * jw1) +
+                     0.5 * (dui[0] * jw0 + dui[1] * jw1));
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const double ph = T.fphi[e][q][j];
+        const double dn = T.fdphi[e][q][j][0] * mo0 + T.fdphi[e][q][j][1] * mo1;
+        acc[j] += A0 * ph + B0 * dn;
+        acc[NS + j] += A1 * ph + B1 * dn;
+      }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_adjoint(DevMesh m, const double* u, const double* w, double* out, double cw,
+                                                 double cj, int accumulate) {
+  using D = Dims<K>;
+  constexpr int ND = D::ND;
+  __shared__ SmemTables<K, double> T;
+  load_tables<K, double>(m, T);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double nupart = 0.0;
+  if (t < m.n_tri) {
+    double acc[ND];
+    element_adjoint<K>(m, T, t, u, w, acc, nupart);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      const size_t o = size_t(t) * ND + i;
+      const double v = cw * w[o] + cj * acc[i];
+      out[o] = accumulate ? out[o] + v : v;
+    }
+  }
+  nupart = block_sum(nupart);
+  if (threadIdx.x == 0) m.red[blockIdx.x] = nupart;
+}
+
+// acc_dev += coef * (sum of the k_adjoint block partials), in fixed order.
+__global__ void k_nu_accumulate(DevMesh m, int nparts, double coef, double* acc_dev) {
+  if (threadIdx.x >= 32) return;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) v += m.red[i];
+  v = warp_sum(v);
+  if (threadIdx.x == 0) *acc_dev += coef * v;
+}
+
 // Operator entry in precision R (double-float copies avoid FP64 conversions).
 template <typename R>
 __device__ __forceinline__ R op_entry(const double* d, const float2* f, size_t i);
@@ -513,6 +689,14 @@ cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
   DGDF_DISPATCH_K(m.k, (k_diagnostics<K><<<nb, 128, 0, s>>>(m, coef)));
   k_diag_finish<<<1, 32, 0, s>>>(m, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const DevMesh& m, const double* u, const double* w, double* out, double cw, double cj,
+                           int accumulate, double nu_coef, double* nu_acc, cudaStream_t s) {
+  const int nb = blocks_for(m.n_tri, 128);
+  DGDF_DISPATCH_K(m.k, (k_adjoint<K><<<nb, 128, 0, s>>>(m, u, w, out, cw, cj, accumulate)));
+  k_nu_accumulate<<<1, 32, 0, s>>>(m, nb, nu_coef, nu_acc);
   return cudaGetLastError();
 }
 

@@ -325,3 +325,20 @@ def test_euler_energy_rate_matches_semidiscrete_identity():
     for dt in (1e-3, 5e-4):
         est = (d.energy(d.rk3_step(U, dt, 1)) - d.energy(U)) / dt
         assert abs(est - rate) < 50 * dt * abs(rate) + 1e-12
+
+
+def test_oracle_tangent_matches_finite_differences():
+    # the tangent-linear model used to check the adjoint: central differences of the oracle's own
+    # RK3 (exact direct solves) in the state and in nu
+    vid, X = synth.split_square_mesh(4, L=1.0)
+    d = Discretization(vid, X, 2, 1e-2)
+    U = projected(d, X, synth.random_spectrum_velocity(3, kmax=3, L=1.0))
+    rng = np.random.default_rng(0)
+    dU = d.project(rng.standard_normal(U.shape))
+    for dnu in (0.0, 1.0):
+        _, dUk = d.rk3_tangent(U, dU, 0.01, 3, dnu=dnu)
+        eps = 1e-6
+        dp = Discretization(vid, X, 2, 1e-2 + eps * dnu)
+        dm = Discretization(vid, X, 2, 1e-2 - eps * dnu)
+        fd = (dp.rk3_step(U + eps * dU, 0.01, 3) - dm.rk3_step(U - eps * dU, 0.01, 3)) / (2 * eps)
+        assert np.linalg.norm(fd - dUk) / np.linalg.norm(dUk) < 1e-7
