@@ -143,7 +143,7 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
 // state u and a functional w (coefficients), out = c_w w + c_J J_L(u)^T w with
 //   (J_L(u)^T w)_j = d/du_j L(u)(w)
 //     volume : int psi_j [(u.grad) w + (grad w)^T u]_c - nu int grad psi_j . grad w_c
-//     facets : -int psi_j [n_c (u^up . [w]) + max(u.n, 0) [w]_c]            (upwind flux in its
+//     facets : -int psi_j [n_c (u^up . [w]) / 2 + max(u.n, 0) [w]_c]        (upwind flux in its
 //              1/2 (u.n)(u+ + u-) + 1/2 |u.n| (u+ - u-) form, sign(0) = 0)
 //              + nu int [psi_j ({d_n w}_c - sigma [w]_c) + 1/2 d_n psi_j [w]_c]  (SIPG, symmetric)
 // with [w] = w_T - w_neighbour and n the outward normal of T. The viscous part is the
@@ -265,8 +265,9 @@ __device__ void element_adjoint(const DevMesh& m, const SmemTables<K, double>& T
       const double vp = vn > 0.0 ? vn : 0.0;
       const double w = T.fw[q] * len;
       // value-type: convective adjoint + SIPG consistency and penalty of w (nu)
-      const double A0 = w * s * (-(n0 * upj + vp * jw0) + nu * (0.5 * (dwi[0] + dwo[0]) - sig * jw0));
-      const double A1 = w * s * (-(n1 * upj + vp * jw1) + nu * (0.5 * (dwi[1] + dwo[1]) - sig * jw1));
+      // u.n is the average of both traces: d(u.n)/du_T = n/2
+      const double A0 = w * s * (-(0.5 * n0 * upj + vp * jw0) + nu * (0.5 * (dwi[0] + dwo[0]) - sig * jw0));
+      const double A1 = w * s * (-(0.5 * n1 * upj + vp * jw1) + nu * (0.5 * (dwi[1] + dwo[1]) - sig * jw1));
       // normal-derivative test: SIPG symmetry term
       const double B0 = w * s * 0.5 * nu * jw0, B1 = w * s * 0.5 * nu * jw1;
       nupart += w * (ui[0] * (0.5 * (dwi[0] + dwo[0]) - sig * jw0) + ui[1] * (0.5 * (dwi[1] + dwo[1]) - sig * jw1) +
