@@ -369,6 +369,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     d.lat_tw = tw;
     d.lat_N = N;
     d.lat_tr = dgdf::lattice_tile_rows(hm.k, N, fp32);
+    d.lat_bufsz = int(dgdf::lattice_buffer_elems(hm.k, N, fp32));
     int logn = 0;
     while ((1 << logn) < N) ++logn;
     d.lat_logn = logn;

@@ -66,6 +66,7 @@ struct DevMesh {
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
   // lattice (translation-invariant split-square) solver data
   int lat_N, lat_logn, lat_tr;      // cells per direction, log2 N, rows per tile of the row passes
+  int lat_bufsz;                    // complex elements per shared-memory transform buffer
   const int32_t* lat_facet_of;        // [3][N][N]
   const void* lat_sinv;               // [N][C][C][N] complex (float2 or double2)
   const double* lat_tw;               // [N][2]
@@ -119,6 +120,7 @@ cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cuda
 int solver_max_blocks(const DevMesh& m, int mixed);
 int lattice_tile_rows(int k, int N, int fp32);
 size_t lattice_smem_bytes(int k, int N, int fp32);
+size_t lattice_buffer_elems(int k, int N, int fp32);
 int lattice_blocks(int k, int N, int fp32);
 cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nblocks, int fp32, cudaStream_t s);
 long long noalloc_max_dofs();

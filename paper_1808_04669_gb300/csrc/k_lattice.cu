@@ -9,10 +9,11 @@
 // evaluated in precision R (FP32 in the mixed form, FP64 in the FP64 form):
 // the preconditioned operator is the identity up to R's rounding, so a solve
 // takes one or two iterations (FP64) or a few (FP32), instead of O(N).
-// The transforms are radix-2 FFTs in shared memory (N a power of two):
+// The transforms run in shared memory (radix-2 FFTs when N is a power of two):
 //   rows  : DFT along i of r (facets numbered in lattice order), tiles of rows
 //   column: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j
 //   rows  : inverse DFT along i, scattered back to facet order (scaled 1/N^2)
+// (for N not a power of two a direct O(N^2) DFT per row in shared memory)
 // with a grid barrier between the three passes. One persistent cooperative
 // kernel per solve, one block per SM.
 #include "device.cuh"
@@ -91,16 +92,70 @@ __device__ void fft_dif(C2* buf, int rows, int logn, const C2* tw, bool inverse)
   }
 }
 
+// Direct DFT of `rows` rows of length n (any n): out[r][k] = sum_t in[r][t] w^(t k mod n),
+// w[m] = exp(-2 pi i m / n) (conjugated for the inverse). Natural order in and out.
+template <typename C2>
+__device__ void dft(const C2* in, C2* out, int rows, int n, const C2* tw, bool inverse) {
+  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+    const int row = e / n, k = e - row * n;
+    const C2* x = in + row * n;
+    C2 acc = {0, 0};
+    int idx = 0;
+    for (int t = 0; t < n; ++t) {
+      C2 w = tw[idx];
+      if (inverse) w.y = -w.y;
+      acc = cadd(acc, cmul(x[t], w));
+      idx += k;
+      if (idx >= n) idx -= n;
+    }
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
 template <int K, typename R>
 struct LatCtx {
   using C2 = typename CxT<R>::T;
   static constexpr int NL = K + 1, C = 3 * NL;
   int N, logn, tr, ntj;
-  C2* tw;
+  bool pow2;      // radix-2 FFT (N a power of two) or direct DFT
+  C2* tw;         // [N] exp(-2 pi i t / N)
   C2* buf;
+  C2* buf2;       // second buffer of the direct DFT
   C2* X;          // [C][N(ki)][N(j)]
   const C2* S;    // [N(ki)][C][C][N(kj)]
 };
+
+// Position in the transform buffer of the element with index i: bit-reversed for the
+// radix-2 passes (input of the forward one, output of the inverse one), natural for the DFT.
+template <int K, typename R>
+__device__ __forceinline__ int tpos(const LatCtx<K, R>& L, int i) {
+  return L.pow2 ? brev(i, L.logn) : i;
+}
+
+// Forward transform of rows loaded at tpos(); returns the buffer with the natural-order result.
+template <int K, typename R>
+__device__ typename CxT<R>::T* xform_fwd(const LatCtx<K, R>& L, typename CxT<R>::T* a, typename CxT<R>::T* b,
+                                         int rows) {
+  if (L.pow2) {
+    fft_dit(a, rows, L.logn, L.tw, false);
+    return a;
+  }
+  dft(a, b, rows, L.N, L.tw, false);
+  return b;
+}
+
+// Inverse transform of natural-order rows; index i of the result sits at tpos(i).
+template <int K, typename R>
+__device__ typename CxT<R>::T* xform_inv(const LatCtx<K, R>& L, typename CxT<R>::T* a, typename CxT<R>::T* b,
+                                         int rows) {
+  if (L.pow2) {
+    fft_dif(a, rows, L.logn, L.tw, true);
+    return a;
+  }
+  dft(a, b, rows, L.N, L.tw, true);
+  return b;
+}
 
 // Facets are numbered (type, j, i) on a lattice mesh, so a tile of tr rows of one
 // facet type with all k+1 modes is one contiguous range of the facet-major vectors:
@@ -113,7 +168,7 @@ __device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool updat
                              double* rr) {
   using C2 = typename CxT<R>::T;
   constexpr int NL = K + 1;
-  const int N = L.N, logn = L.logn;
+  const int N = L.N;
   const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * L.tr;
@@ -121,7 +176,7 @@ __device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool updat
     const size_t base = (size_t(ty) * N + j0) * N * NL;
     for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
       const int mm = e % NL, rest = e / NL;
-      const int i = rest & (N - 1), r_ = rest >> logn;
+      const int r_ = rest / N, i = rest - r_ * N;
       const size_t o = base + e;
       double rv = __ldcg(&m.r[o]);
       if (update) {
@@ -130,14 +185,14 @@ __device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool updat
         m.lam[o] += alpha * __ldcg(&p[o]);
       }
       *rr += rv * rv;
-      L.buf[(mm * rows + r_) * N + brev(i, logn)] = C2{R(rv), R(0)};
+      L.buf[(mm * rows + r_) * N + tpos(L, i)] = C2{R(rv), R(0)};
     }
     __syncthreads();
-    fft_dit(L.buf, NL * rows, logn, L.tw, false);
+    const C2* res = xform_fwd(L, L.buf, L.buf2, NL * rows);
     for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
       const int r_ = e % rows, rest = e / rows;
-      const int ki = rest & (N - 1), mm = rest >> logn;
-      L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_] = L.buf[(mm * rows + r_) * N + ki];
+      const int mm = rest / N, ki = rest - mm * N;
+      L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_] = res[(mm * rows + r_) * N + ki];
     }
     __syncthreads();
   }
@@ -149,15 +204,15 @@ template <int K, typename R>
 __device__ void columns(const LatCtx<K, R>& L) {
   using C2 = typename CxT<R>::T;
   constexpr int C = LatCtx<K, R>::C;
-  const int N = L.N, logn = L.logn;
+  const int N = L.N;
   const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
   for (int ki = blockIdx.x; ki < N; ki += gridDim.x) {
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
-      const int c = e >> logn, j = e & (N - 1);
-      L.buf[c * N + brev(j, logn)] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j]);
+      const int c = e / N, j = e - c * N;
+      L.buf[c * N + tpos(L, j)] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j]);
     }
     __syncthreads();
-    fft_dit(L.buf, C, logn, L.tw, false);
+    C2* cur = xform_fwd(L, L.buf, L.buf2, C);
     const C2* S = L.S + size_t(ki) * C * C * N;
     for (int kj0 = 0; kj0 < N; kj0 += 32) {
       const int kj = kj0 + lane;
@@ -165,16 +220,16 @@ __device__ void columns(const LatCtx<K, R>& L) {
       C2 y = {R(0), R(0)};
       if (act) {
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(wc) * C + cc) * N + kj]), L.buf[cc * N + kj]));
+        for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(wc) * C + cc) * N + kj]), cur[cc * N + kj]));
       }
       __syncthreads();
-      if (act) L.buf[wc * N + kj] = y;
+      if (act) cur[wc * N + kj] = y;
       __syncthreads();
     }
-    fft_dif(L.buf, C, logn, L.tw, true);
+    const C2* res = xform_inv(L, cur, cur == L.buf ? L.buf2 : L.buf, C);
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
-      const int c = e >> logn, p = e & (N - 1);
-      L.X[(size_t(c) * N + ki) * N + brev(p, logn)] = L.buf[c * N + p];
+      const int c = e / N, j = e - c * N;
+      L.X[(size_t(c) * N + ki) * N + j] = res[c * N + tpos(L, j)];
     }
     __syncthreads();
   }
@@ -184,8 +239,9 @@ __device__ void columns(const LatCtx<K, R>& L) {
 // Accumulates r.z_new into *rz and, if with_old, r.z_old into *rzo.
 template <int K, typename R>
 __device__ void rows_inverse(const DevMesh& m, const LatCtx<K, R>& L, bool with_old, double* rz, double* rzo) {
+  using C2 = typename CxT<R>::T;
   constexpr int NL = K + 1;
-  const int N = L.N, logn = L.logn;
+  const int N = L.N;
   const double scale = 1.0 / (double(N) * double(N));
   const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -194,16 +250,16 @@ __device__ void rows_inverse(const DevMesh& m, const LatCtx<K, R>& L, bool with_
     const size_t base = (size_t(ty) * N + j0) * N * NL;
     for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
       const int r_ = e % rows, rest = e / rows;
-      const int ki = rest & (N - 1), mm = rest >> logn;
+      const int mm = rest / N, ki = rest - mm * N;
       L.buf[(mm * rows + r_) * N + ki] = __ldcg(&L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_]);
     }
     __syncthreads();
-    fft_dif(L.buf, NL * rows, logn, L.tw, true);
+    const C2* res = xform_inv(L, L.buf, L.buf2, NL * rows);
     for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
       const int mm = e % NL, rest = e / NL;
-      const int i = rest & (N - 1), r_ = rest >> logn;
+      const int r_ = rest / N, i = rest - r_ * N;
       const size_t o = base + e;
-      const double zv = double(L.buf[(mm * rows + r_) * N + brev(i, logn)].x) * scale;
+      const double zv = double(res[(mm * rows + r_) * N + tpos(L, i)].x) * scale;
       const double rv = __ldcg(&m.r[o]);
       if (with_old) *rzo += rv * __ldcg(&m.z[o]);
       *rz += rv * zv;
@@ -223,11 +279,13 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
   L.logn = m.lat_logn;
   L.tr = m.lat_tr;
   L.ntj = (L.N + L.tr - 1) / L.tr;
+  L.pow2 = (L.N & (L.N - 1)) == 0;
   L.tw = reinterpret_cast<C2*>(smem_raw);
-  L.buf = L.tw + (L.N > 1 ? L.N / 2 : 1);
+  L.buf = L.tw + L.N;
+  L.buf2 = L.buf + m.lat_bufsz;
   L.X = reinterpret_cast<C2*>(m.lat_x);
   L.S = reinterpret_cast<const C2*>(m.lat_sinv);
-  for (int t = threadIdx.x; t < L.N / 2; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
+  for (int t = threadIdx.x; t < L.N; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
   __syncthreads();
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
@@ -402,11 +460,15 @@ int lattice_tile_rows(int k, int N, int fp32) {
   return int(tr);
 }
 
+size_t lattice_buffer_elems(int k, int N, int fp32) {
+  const size_t C = 3 * (k + 1), rows_buf = size_t(k + 1) * lattice_tile_rows(k, N, fp32);
+  return (C > rows_buf ? C : rows_buf) * N;
+}
+
 size_t lattice_smem_bytes(int k, int N, int fp32) {
-  const int C = 3 * (k + 1);
   const size_t cx = fp32 ? 8 : 16;
-  const size_t rows_buf = size_t(k + 1) * lattice_tile_rows(k, N, fp32);
-  return (size_t(N > 1 ? N / 2 : 1) + (size_t(C) > rows_buf ? size_t(C) : rows_buf) * N) * cx;
+  const bool pow2 = (N & (N - 1)) == 0;
+  return (size_t(N) + (pow2 ? 1 : 2) * lattice_buffer_elems(k, N, fp32)) * cx;
 }
 
 int lattice_blocks(int k, int N, int fp32) {

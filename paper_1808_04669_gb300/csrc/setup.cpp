@@ -695,10 +695,6 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
     L.why = "triangle count is not 2 N^2";
     return;
   }
-  if ((N & (N - 1)) != 0) {
-    L.why = "N is not a power of two";
-    return;
-  }
   if (hm.classes.size() != 2 || hm.n_stencil != 3) {
     L.why = "not two element classes and three facet stencils";
     return;

@@ -21,7 +21,7 @@ def g():
 
 MEMBERS = [  # (N, k, nu, precision, perturb, L)
     (4, 1, 1e-2, 0, 0.0, 2 * np.pi),     # lattice, FP64
-    (6, 2, 1e-3, 0, 0.0, 2 * np.pi),     # block Jacobi (N not a power of two)
+    (6, 2, 1e-3, 0, 0.0, 2 * np.pi),     # lattice, direct DFT (N not a power of two)
     (8, 3, 0.0, 1, 0.0, 1.0),            # lattice, mixed
     (5, 2, 1e-2, 1, 0.1, 1.0),           # perturbed (not translation invariant), mixed
 ]

@@ -90,7 +90,7 @@ def test_residual_parity_projected_field(g, k):
 
 # --------------------------------------------------------------- projection
 @pytest.mark.parametrize("N,k,perturb,precond", [(1, 1, 0.0, 0), (2, 3, 0.0, 0), (4, 2, 0.0, 0), (4, 2, 0.0, 1),
-                                                  (5, 3, 0.0, 0), (4, 2, 0.1, 0), (8, 3, 0.0, 0)])
+                                                  (5, 3, 0.0, 0), (5, 3, 0.0, 1), (4, 2, 0.1, 0), (8, 3, 0.0, 0)])
 def test_projection_parity(g, N, k, perturb, precond):
     mesh, d, X = pair(g, N, k, 0.0, perturb=perturb, seed=3, precond=precond)
     v = random_lattice(mesh.n_tri, k, 20 + N)
@@ -142,9 +142,9 @@ def test_rk3_parity_taylor_green_n8_k2(g, precond):
     assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-11
 
 
-@pytest.mark.parametrize("N,k", [(12, 1), (12, 3), (16, 3), (8, 2)])
-def test_rk3_parity_shear_layer(g, N, k):
-    # N = 12: block Jacobi (not a power of two); N = 8, 16: the lattice preconditioner
+@pytest.mark.parametrize("N,k,precond", [(12, 1, 0), (12, 3, 0), (12, 3, 1), (16, 3, 0), (8, 2, 0)])
+def test_rk3_parity_shear_layer(g, N, k, precond):
+    # lattice preconditioner: radix-2 FFT (N = 8, 16) or direct DFT (N = 12); block Jacobi (precond = 1)
     nu = 1e-4
     vid, X = synth.split_square_mesh(N)
     vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
@@ -154,13 +154,13 @@ def test_rk3_parity_shear_layer(g, N, k):
     U = d.rk3_step(d.project(d.from_lattice(vals)), dt, 5)
     ref = d.to_lattice(U)
     for prec, tol in ((0, TOL64), (1, TOLMIX)):
-        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec, precond=precond)
         mesh.set_velocity(vals)
         mesh.project_divfree()
         mesh.rk3_step(dt, 5)
         assert rel(mesh.get_velocity(), ref) < tol, prec
         st = mesh.solver_stats()
-        assert st["lattice"] == (1.0 if N in (8, 16) else 0.0)
+        assert st["lattice"] == (1.0 if precond == 0 else 0.0)
         if st["lattice"]:
             assert st["total_iters"] / st["solves"] <= 6
 
