@@ -325,6 +325,94 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
 
 
+def run_ensemble(args):
+    """Ensemble workload: 64 instances on the unit square, N ~ U{32..256}, k ~ U{1,2,3},
+    log10 nu ~ U[-5,-2], Taylor-Green or random-spectrum initial data (seeds 100+i), mixed
+    precision, advanced together by dg_batch_rk3_step (one captured CUDA graph per step)."""
+    import numpy as np
+    import torch
+    from paper_1808_04669_gb300 import build as _b
+    _b.build()
+    import paper_1808_04669_gb300 as g
+    import synth
+    rng = np.random.Generator(np.random.PCG64(1))
+    n_inst = args.instances
+    meshes, dts, units_per_step = [], [], 0
+    for i in range(n_inst):
+        N = int(rng.integers(32, 257))
+        k = int(rng.integers(1, 4))
+        nu = float(10.0 ** rng.uniform(-5, -2))
+        tgv = rng.uniform() < 0.5
+        vid, X = synth.split_square_mesh(N, L=1.0)
+        f = synth.taylor_green(1.0) if tgv else synth.random_spectrum_velocity(100 + i, L=1.0)
+        vals = synth.sample_lattice(f, X, k, grid=None if (tgv or k * N <= 64) else (k * N, 1.0))
+        dts.append(synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu))
+        m = g.DGMesh(vid, X, k, nu, precision=g.MIXED)
+        m.set_velocity(vals)
+        m.project_divfree()
+        meshes.append(m)
+        units_per_step += dof_stage_units(m.n_tri, k, 1)
+    batch = g.DGBatch(meshes)
+    dts = np.array(dts)
+    batch.rk3_step(dts, args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.rk3_step(dts, args.steps)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    lat = sum(int(m.solver_stats()["lattice"]) for m in meshes)
+    print(json.dumps({"mode": "ensemble", "metric": UNIT + " (ensemble, all instances)",
+                      "value": units_per_step * args.steps / t, "unit": UNIT, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "instances": n_inst,
+                      "triangles": int(sum(m.n_tri for m in meshes)), "lattice_instances": lat,
+                      "dtype": "f64 element + double-float element kernels, f32 Fourier preconditioner",
+                      "config": {"workload": "ensemble of %d periodic unit-square meshes, N~U{32..256}, "
+                                             "k~U{1,2,3}, log10 nu~U[-5,-2], seed 1" % n_inst,
+                                 "graph": "one captured CUDA graph per step (dg_batch_rk3_step)"}}), flush=True)
+    batch.close()
+
+
+def run_adjoint(args):
+    """Gradient workload: 128 x 128 unit square, BDM_2, nu = 1e-3, random-spectrum u0 (seed 3) and
+    target (seed 4), loss 1/2 ||u_K - u*||^2, K = 200 SSP-RK3 steps, checkpoints every 20 steps;
+    one timed gradient = dg_rk3_vjp (forward, segment recomputation, reverse sweep)."""
+    import numpy as np
+    import torch
+    from paper_1808_04669_gb300 import build as _b
+    _b.build()
+    import paper_1808_04669_gb300 as g
+    import synth
+    w = synth.WORKLOADS["adjoint_n128_k2"]
+    vid, X, vals, dt = synth.make_workload(w)
+    mesh = g.DGMesh(vid, X, w.k, w.nu)
+    tgt = synth.sample_lattice(synth.random_spectrum_velocity(4, L=1.0), X, w.k, grid=(w.k * w.N, 1.0))
+    mesh.set_velocity(tgt)
+    target = mesh.get_coefficients()
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    u0 = mesh.get_coefficients()
+    K = args.steps_adjoint
+    times = []
+    for rep in range(1 + args.reps):
+        mesh.set_coefficients(u0)
+        mesh.rk3_step(dt, K)
+        ubar = mesh.get_coefficients() - target
+        mesh.set_coefficients(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u0bar, nubar = mesh.rk3_vjp(dt, K, ubar, checkpoint_every=20)
+        torch.cuda.synchronize()
+        if rep > 0:
+            times.append(time.perf_counter() - t0)
+    t = min(times)
+    print(json.dumps({"mode": "adjoint", "metric": "gradients/s of a %d-step rollout (u0 and nu)" % K,
+                      "value": 1.0 / t, "unit": "gradients/s", "seconds_per_gradient": t,
+                      "forward_dof_stage_per_s": dof_stage_units(mesh.n_tri, w.k, K) / t,
+                      "nubar": nubar, "u0bar_norm": float(np.linalg.norm(u0bar)),
+                      "config": {"workload": "128x128 unit square, BDM_2, nu=1e-3, %d steps, checkpoint every 20" % K}}),
+          flush=True)
+
+
 def _oracle_sample_steps(nsteps, warmup=0):
     """Oracle run on the bounded sample; returns (seconds per step, n_tri, k)."""
     import synth
@@ -405,6 +493,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=("step", "ensemble", "adjoint"), default="step",
+                    help="step: the bench line; ensemble / adjoint: the batching and gradient workloads")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--steps-adjoint", type=int, default=200)
+    ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--summarize-launches", metavar="CSV", help="print a per-kernel summary of an ncu launch list")
     ap.add_argument("--workload", default=None, help="named workload (default %s); the bench line is on the default" % WORKLOAD)
     ap.add_argument("--n", type=int, default=None,
@@ -417,6 +510,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "ensemble":
+        run_ensemble(args)
+    elif args.mode == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -475,11 +475,27 @@ int lattice_blocks(int k, int N, int fp32) {
   const void* fn = lattice_kernel(k, fp32);
   if (!fn) return 0;
   const size_t smem = lattice_smem_bytes(k, N, fp32);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
-  int per_sm = 0, dev = 0, sms = 0;
+  int per_sm = 0, dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
+  // the attribute is per kernel, shared by all meshes: allow the device maximum once,
+  // so that meshes of different sizes can use the same instantiation
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int max_dyn = optin - int(fa.sharedSizeBytes);
+  if (max_dyn <= 0 || smem > size_t(max_dyn)) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLatThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLatThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   if (per_sm < 1) return 0;
   int nb = sms;   // one block per SM
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
