@@ -3,14 +3,18 @@
 One step = one SSP-RK3 time step (three stages; each stage = element residual
 and condensation, facet PCG solve, recovery) on the double shear layer,
 256 x 256 split squares of [0, 2pi]^2 (131072 triangles), BDM_3, nu = 1e-4.
-The timed form is the mixed-precision one (FP64 element kernels, facet system
-solved by FP32 PCG inside FP64 refinement); the FP64 form is timed on the same
-workload and its state compared with the mixed one.
+The timed form is the mixed-precision one: element kernels in double-float
+arithmetic on the FP32 units, facet PCG with FP64 vectors preconditioned by the
+FP32 Fourier-space inverse of the facet operator. The FP64 form is timed on the
+same workload and its state compared with the mixed one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode step|ensemble|adjoint] [--workload NAME]
 
-N > 1 (torchrun, one rank per GPU): every rank advances its own replica of the
-workload (independent instances, weak scaling); rank 0 prints the line.
+N > 1 (torchrun, one rank per GPU): in the step mode every rank advances its own
+replica of the workload (independent instances, weak scaling); in the ensemble
+mode the instances are dealt out to the ranks (strong scaling). Rank 0 prints
+the line; times are the maximum over ranks.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores.
 """
@@ -33,13 +37,36 @@ WORKLOAD = "shear_n256_k3"
 SAMPLE_N = 32          # oracle sample: same workload on a 32 x 32 split-square mesh
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM traffic of one mixed-solver launch per inner CG iteration, from the ncu capture
-# summarised in profiles/ (None until captured for the current kernel source).
-NCU_TRAFFIC = {"k_solver_sha": None, "bytes_per_iter": None}
+# DRAM bytes (read + write) of one launch of the dominant kernel on the bench workload, from the
+# ncu capture summarised in profiles/; used only while the element-kernel sources still hash to
+# the captured `sha`, else the line reports null.
+NCU_TRAFFIC = {"stage_residual": {"sha": None, "n_tri": 131072, "bytes": None}}
 
 
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_over_ranks(values, op, dist=None, device="cpu"):
+    """Element-wise max or sum of a list of floats over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(local_units, local_seconds, dist=None, device="cpu"):
+    """Whole-job throughput: the units processed by all ranks / the slowest rank's time."""
+    units, = reduce_over_ranks([local_units], "sum", dist, device)
+    secs, = reduce_over_ranks([local_seconds], "max", dist, device)
+    return units / secs, units, secs
+
+
+def shard(n, rank, world):
+    """Indices of the independent instances rank `rank` of `world` advances (round robin)."""
+    return list(range(rank, n, world))
 
 
 def dof_stage_units(n_tri, k, steps):
@@ -104,9 +131,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def k_solver_sha():
-    with open(os.path.join(ROOT, "paper_1808_04669_gb300", "csrc", "k_solver.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def element_kernel_sha():
+    h = hashlib.sha256()
+    for n in ("k_element.cu", "dfloat.cuh", "kcommon.cuh", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_1808_04669_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def stage_flops_per_triangle(k):
@@ -158,6 +188,16 @@ def solver_bytes(n_facet, k, iters, sweeps, solves):
 def fp64_peak_tflops(sm_mhz):
     """FP64 ALU peak: 2 FP64 FMA per clock per SM (measured FMA-chain probe: 1.20 TFLOP/s) x 152 SMs."""
     return 2 * 2 * 152 * sm_mhz * 1e6 / 1e12
+
+
+DF_OPS_PER_FMA = 12
+
+
+def dfl_peak_tflops(sm_mhz):
+    """Double-float ALU peak in algorithmic flops: 128 FP32 lanes per SM x 152 SMs x clock, divided
+    by the 12 FP32 operations of one double-float multiply-add (exact product 2, cross terms 2,
+    TwoSum 6, error accumulation 2), times 2 flops per multiply-add."""
+    return 128 * 152 * sm_mhz * 1e6 / DF_OPS_PER_FMA * 2 / 1e12
 
 
 def workload_label(w, N, n_tri):
@@ -222,13 +262,9 @@ def run_ours(args):
     with sampler:
         t_ms, prof, st0, st1 = timed_steps(mixed, args.steps, args.warmup, profile=True)
     clocks = sampler.summary()
-    if dist is not None:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    value, units, t_s = job_rate(dof_stage_units(mixed.n_tri, k, args.steps), t_ms * 1e-3, dist, "cuda")
+    t_ms = t_s * 1e3
     u_mixed = mixed.get_velocity()
-    units = dof_stage_units(mixed.n_tri, k, args.steps) * world
-    value = units / (t_ms * 1e-3)
 
     # FP64 form on the same initial state and step count
     fp64 = g.DGMesh(vid, X, k, w.nu, precision=g.FP64, stream=stream.cuda_stream)
@@ -236,7 +272,8 @@ def run_ours(args):
     t64, _, s640, s641 = timed_steps(fp64, args.steps, args.warmup)
     u64 = fp64.get_velocity()
     rel = float(np.linalg.norm(u_mixed - u64) / np.linalg.norm(u64))
-    value64 = dof_stage_units(fp64.n_tri, k, args.steps) * world / (t64 * 1e-3)
+    value64, _, t64_s = job_rate(dof_stage_units(fp64.n_tri, k, args.steps), t64 * 1e-3, dist, "cuda")
+    t64 = t64_s * 1e3
     diag = mixed.diagnostics()
 
     # end to end through the public API with host buffers: per step, copy the state in from
@@ -253,11 +290,7 @@ def run_ours(args):
         e2e_mesh.rk3_step(dt, 1)
         e2e_mesh.get_velocity(host)
     barrier()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    value_e2e, _, _ = job_rate(dof_stage_units(mixed.n_tri, k, args.steps), time.perf_counter() - t0, dist, "cuda")
     lat_bytes = host.numel() * 8
 
     # roofline of the dominant kernel in the timed region
@@ -273,11 +306,15 @@ def run_ours(args):
     if name.startswith("stage_residual"):
         flops = stage_flops_per_triangle(k) * mixed.n_tri
         achieved = flops / per_launch_s / 1e12
-        peak = fp64_peak_tflops(sm_mhz)
+        peak = dfl_peak_tflops(sm_mhz)
+        tr = NCU_TRAFFIC.get("stage_residual")
+        if tr and tr.get("sha") == element_kernel_sha() and tr.get("n_tri") == mixed.n_tri:
+            traffic = tr["bytes"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_stage<%d> (stage residual + condensation, FP64)" % k,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x median SM clock %.0f MHz "
-                               "(FMA-chain probe measured 1.20 TFLOP/s)" % sm_mhz}
+                "traffic": traffic,
+                "kernel": "k_stage<%d> (stage residual + condensation, double-float on the FP32 pipes)" % k,
+                "peak_source": "derived: 128 FP32 lanes/SM x 152 SMs x median SM clock %.0f MHz / %d FP32 ops "
+                               "per double-float multiply-add x 2 flops" % (sm_mhz, DF_OPS_PER_FMA)}
     else:
         if name.startswith("facet_pcg_fft"):
             nbytes = lattice_solver_bytes(mixed.n_facet, k, iters, solves)
@@ -294,7 +331,7 @@ def run_ours(args):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 PCG + f32 increment in f64 refinement (f64 state)",
+        "vs_baseline": None, "dtype": "f32x2 (double-float) element kernels, f64 PCG with f32 Fourier preconditioner, f64 state",
         "data": "synthetic (double shear layer sampled at lattice points, seeded)",
         "config": {"workload": workload_label(w, args.n or w.N, mixed.n_tri),
                    "N": args.n or w.N, "k": k, "nu": w.nu, "dt": dt,
@@ -302,7 +339,7 @@ def run_ours(args):
                    "multiplier_dofs": mixed.n_lam_dofs, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas (one independent instance per GPU)"},
         "clocks": clocks,
-        "e2e": {"value": dof_stage_units(mixed.n_tri, k, args.steps) * world / t_e2e, "unit": UNIT,
+        "e2e": {"value": value_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": lat_bytes, "d2h_bytes_per_step": lat_bytes},
         "gpu_launches": launches,
         "roofline": roof,
@@ -335,14 +372,23 @@ def run_ensemble(args):
     _b.build()
     import paper_1808_04669_gb300 as g
     import synth
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     rng = np.random.Generator(np.random.PCG64(1))
     n_inst = args.instances
+    mine = set(shard(n_inst, rank, world))
     meshes, dts, units_per_step = [], [], 0
     for i in range(n_inst):
         N = int(rng.integers(32, 257))
         k = int(rng.integers(1, 4))
         nu = float(10.0 ** rng.uniform(-5, -2))
         tgv = rng.uniform() < 0.5
+        if i not in mine:
+            continue
         vid, X = synth.split_square_mesh(N, L=1.0)
         f = synth.taylor_green(1.0) if tgv else synth.random_spectrum_velocity(100 + i, L=1.0)
         vals = synth.sample_lattice(f, X, k, grid=None if (tgv or k * N <= 64) else (k * N, 1.0))
@@ -359,17 +405,23 @@ def run_ensemble(args):
     t0 = time.perf_counter()
     batch.rk3_step(dts, args.steps)
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    lat = sum(int(m.solver_stats()["lattice"]) for m in meshes)
+    value, _, t = job_rate(units_per_step * args.steps, time.perf_counter() - t0, dist, "cuda")
+    lat, tris = reduce_over_ranks([sum(int(m.solver_stats()["lattice"]) for m in meshes),
+                                   sum(m.n_tri for m in meshes)], "sum", dist, "cuda")
+    batch.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     print(json.dumps({"mode": "ensemble", "metric": UNIT + " (ensemble, all instances)",
-                      "value": units_per_step * args.steps / t, "unit": UNIT, "steps": args.steps,
+                      "value": value, "unit": UNIT, "n_gpus": world, "scaling": "strong", "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "instances": n_inst,
-                      "triangles": int(sum(m.n_tri for m in meshes)), "lattice_instances": lat,
-                      "dtype": "f64 element + double-float element kernels, f32 Fourier preconditioner",
+                      "triangles": int(tris), "lattice_instances": int(lat),
+                      "dtype": "f32x2 (double-float) element kernels, f64 PCG with f32 preconditioner, f64 state",
                       "config": {"workload": "ensemble of %d periodic unit-square meshes, N~U{32..256}, "
                                              "k~U{1,2,3}, log10 nu~U[-5,-2], seed 1" % n_inst,
                                  "graph": "one captured CUDA graph per step (dg_batch_rk3_step)"}}), flush=True)
-    batch.close()
 
 
 def run_adjoint(args):
