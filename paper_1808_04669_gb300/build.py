@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgdf.so")
 
-CUDA_SOURCES = ["api.cu", "k_element.cu", "k_solver.cu", "k_lattice.cu"]
+CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu"]
 CXX_SOURCES = ["setup.cpp", "host_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -56,6 +56,7 @@ struct dg_mesh {
   std::string lattice_why;
   double last_bdt = 0.0;
   bool has_lam = false;
+  bool udf_valid = false;        // mixed form: u_df holds the double-float image of u
   double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
   double* wbuf = nullptr;        // [n_tri][nw] element pressure
   double* pe = nullptr;          // [n_tri][nw] pressure lattice staging
@@ -175,6 +176,16 @@ int finish(dg_mesh* M, bool check_solver) {
 int reset_flags(dg_mesh* M) {
   CK(cudaMemsetAsync(&M->dm.stats->flags, 0, sizeof(int), M->stream));
   return DG_OK;
+}
+
+// Mixed form: refresh the double-float twin of u after u was written by anything
+// but the recovery (which writes both).
+int ensure_udf(dg_mesh* M) {
+  if (!M->dm.elem_df || M->udf_valid) return DG_OK;
+  const long long n = (long long)M->dm.n_tri * M->dm.nd;
+  int rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_to_dfl(M->dm.u, M->dm.u_df, n, M->stream); });
+  if (rc == DG_OK) M->udf_valid = true;
+  return rc;
 }
 
 int solve(dg_mesh* M, double warm_scale) {
@@ -304,6 +315,15 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = upload(M, &d.st_binv, hm.stencil_binv)) || (rc = upload(M, &d.st_blk_f, to_float(hm.stencil_blocks))) ||
       (rc = upload(M, &d.st_binv_f, to_float(hm.stencil_binv))))
     return cleanup(rc);
+  if (d.elem_df) {
+    // reference tables in the field order of the kernels' shared-memory image
+    std::vector<double> tab;
+    for (const std::vector<double>* v : {&ref.vw, &ref.vphi, &ref.vdphi, &ref.fw, &ref.fphi, &ref.fdphi})
+      tab.insert(tab.end(), v->begin(), v->end());
+    if ((rc = upload(M, &d.tab_df, to_dfloat(tab))) || (rc = upload(M, &d.geo_df, to_dfloat(geo))) ||
+        (rc = upload(M, &d.sigma_df, to_dfloat(hm.facet_sigma))))
+      return cleanup(rc);
+  }
   const size_t nT = size_t(d.n_tri), nF = size_t(d.n_facet);
   const size_t nred = std::max<size_t>(size_t(dgdf::kRedSlots) * dgdf::kMaxSolverBlocks, nT / 128 + 2);
   if ((rc = dalloc(M, &d.u, nT * nd)) || (rc = dalloc(M, &d.ustage, nT * nd)) || (rc = dalloc(M, &d.h, nT * nd)) ||
@@ -316,6 +336,9 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = dalloc(M, &d.stats, 1)) || (rc = dalloc(M, &d.diag, 8)) ||
       (rc = dalloc(M, &M->lattice, nT * hm.ns * 2)) || (rc = dalloc(M, &M->wbuf, nT * nw)) ||
       (rc = dalloc(M, &M->pe, nT * nw)) || (rc = dalloc(M, &M->pfac, nF * nl)) || (rc = dalloc(M, &M->dflag, 1)))
+    return cleanup(rc);
+  if (d.elem_df && ((rc = dalloc(M, &d.u_df, nT * nd)) || (rc = dalloc(M, &d.ustage_df, nT * nd)) ||
+                    (rc = dalloc(M, &d.h_df, nT * nd)) || (rc = dalloc(M, &d.gl_df, nT * L3))))
     return cleanup(rc);
   cudaError_t e = cudaMallocHost(&M->host_stats, sizeof(dgdf::DevStats));
   if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e)));
@@ -424,6 +447,7 @@ int dg_set_velocity(dg_mesh* M, const double* vals, int on_device) {
   rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_lattice_to_coef(M->dm, M->lattice, M->dm.u, M->stream); });
   if (rc) return rc;
   M->has_lam = false;
+  M->udf_valid = false;
   return finish(M, false);
 }
 
@@ -446,9 +470,13 @@ int dg_project_divfree(dg_mesh* M) {
   a.mode = dgdf::MODE_PROJECT;
   a.up = M->dm.u;
   a.un = M->dm.u;
+  if ((rc = ensure_udf(M))) return rc;
+  a.up_df = M->dm.u_df;
+  a.un_df = M->dm.u_df;
   if ((rc = launch(M, KC_PROJECT_RHS, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
   if ((rc = solve(M, 0.0))) return rc;
-  if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->stream); }))) return rc;
+  if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->dm.u_df, M->stream); })))
+    return rc;
   M->has_lam = false;
   return finish(M, true);
 }
@@ -464,11 +492,13 @@ const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0}, kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
 // multipliers rescaled by b dt) and the recovery. No synchronisation.
 int enqueue_step(dg_mesh* M, double dt) {
   dgdf::DevMesh& d = M->dm;
-  int rc = DG_OK;
+  int rc = ensure_udf(M);
+  if (rc) return rc;
   for (int s = 0; s < 3; ++s) {
     const double a = kRkA[s], b = kRkB[s];
     const double* up = (s == 0) ? d.u : d.ustage;
     double* out = (s == 2) ? d.u : d.ustage;
+    float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
     dgdf::StageArgs sa{};
     sa.mode = dgdf::MODE_STAGE;
     sa.a = a;
@@ -476,10 +506,12 @@ int enqueue_step(dg_mesh* M, double dt) {
     sa.dt = dt;
     sa.un = d.u;
     sa.up = up;
+    sa.un_df = d.u_df;
+    sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
     const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
     if ((rc = solve(M, warm))) return rc;
-    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
+    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
     M->last_bdt = b * dt;
     M->has_lam = true;
   }
@@ -573,7 +605,7 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
   if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(B->stream, B->ev, 0);
   if (e0 != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("dg_batch_rk3_step: ") + cudaGetErrorString(e0)));
   for (dg_mesh* M : B->members)
-    if ((rc = reset_flags(M))) return restore(rc);
+    if ((rc = reset_flags(M)) || (rc = ensure_udf(M))) return restore(rc);
   // The captured step assumes warm-started solves with a fixed step size: run one step
   // eagerly when any member is cold or the step sizes changed.
   bool same_dt = B->exec && B->graph_dt.size() == n;
@@ -632,6 +664,7 @@ int dg_set_coefficients(dg_mesh* M, const double* coef, int on_device) {
   CK(cudaMemcpyAsync(M->dm.u, coef, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      M->stream));
   M->has_lam = false;
+  M->udf_valid = false;
   return finish(M, false);
 }
 
@@ -663,17 +696,26 @@ int apply_Q(dg_mesh* M, const double* x, double* y) {
   a.mode = dgdf::MODE_PROJECT;
   a.up = x;
   a.un = x;
-  int rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_stage(M->dm, a, M->stream); });
-  if (rc) return rc;
+  int rc = DG_OK;
+  if (M->dm.elem_df) {
+    // the stage buffer's twin is free outside a step: it takes the double-float image of x
+    const long long n = (long long)M->dm.n_tri * M->dm.nd;
+    if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_to_dfl(x, M->dm.ustage_df, n, M->stream); })))
+      return rc;
+    a.up_df = M->dm.ustage_df;
+    a.un_df = M->dm.ustage_df;
+  }
+  if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
   if ((rc = solve(M, 0.0))) return rc;
-  return launch(M, KC_ADJOINT, [&] { return dgdf::launch_recover(M->dm, y, M->stream); });
+  return launch(M, KC_ADJOINT, [&] { return dgdf::launch_recover(M->dm, y, nullptr, M->stream); });
 }
 
 // One SSP-RK3 step that also keeps the stage inputs u^n, u^(1), u^(2) in st[0..2].
 int enqueue_step_keep(dg_mesh* M, double dt, double* const st[3]) {
   dgdf::DevMesh& d = M->dm;
   const size_t bytes = size_t(d.n_tri) * d.nd * sizeof(double);
-  int rc = DG_OK;
+  int rc = ensure_udf(M);
+  if (rc) return rc;
   for (int s = 0; s < 3; ++s) {
     const double* up = (s == 0) ? d.u : d.ustage;
     CK(cudaMemcpyAsync(st[s], up, bytes, cudaMemcpyDeviceToDevice, M->stream));
@@ -684,11 +726,14 @@ int enqueue_step_keep(dg_mesh* M, double dt, double* const st[3]) {
     sa.dt = dt;
     sa.un = d.u;
     sa.up = up;
+    sa.un_df = d.u_df;
+    sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
     const double warm = M->has_lam ? (kRkB[s] * dt) / M->last_bdt : 0.0;
     if ((rc = solve(M, warm))) return rc;
     double* out = (s == 2) ? d.u : d.ustage;
-    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, M->stream); }))) return rc;
+    float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
+    if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
     M->last_bdt = kRkB[s] * dt;
     M->has_lam = true;
   }
@@ -748,6 +793,7 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
     const int64_t len = std::min<int64_t>(checkpoint_every, nsteps - s0);
     CK(cudaMemcpyAsync(d.u, ck + size_t(g) * n, bytes, cudaMemcpyDeviceToDevice, M->stream));
     M->has_lam = false;
+    M->udf_valid = false;
     for (int64_t i = 0; i < len; ++i) {
       double* const st[3] = {stg + (size_t(i) * 3 + 0) * n, stg + (size_t(i) * 3 + 1) * n, stg + (size_t(i) * 3 + 2) * n};
       if ((rc = enqueue_step_keep(M, dt, st))) return rc;
@@ -780,6 +826,7 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
   }
   CK(cudaMemcpyAsync(d.u, uK, bytes, cudaMemcpyDeviceToDevice, M->stream));
   M->has_lam = false;
+  M->udf_valid = false;
   CK(cudaMemcpyAsync(u0bar, ub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, M->stream));
   double nb = 0.0;
   CK(cudaMemcpyAsync(&nb, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
@@ -797,6 +844,9 @@ int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) 
   a.mode = dgdf::MODE_PRESSURE;
   a.up = M->dm.u;
   a.un = M->dm.u;
+  if ((rc = ensure_udf(M))) return rc;
+  a.up_df = M->dm.u_df;
+  a.un_df = M->dm.u_df;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
   if ((rc = solve(M, 0.0))) return rc;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_pressure(M->dm, M->wbuf, M->stream); }))) return rc;
@@ -819,7 +869,11 @@ int dg_eval_residual(dg_mesh* M, double* vals, int on_device) {
   a.mode = dgdf::MODE_RESIDUAL;
   a.up = M->dm.u;
   a.un = M->dm.u;
-  int rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); });
+  int rc = ensure_udf(M);
+  if (rc) return rc;
+  a.up_df = M->dm.u_df;
+  a.un_df = M->dm.u_df;
+  rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); });
   if (rc) return rc;
   if ((rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_coef_to_lattice(M->dm, M->dm.h, M->lattice, M->stream); })))
     return rc;

@@ -53,6 +53,9 @@ struct DevMesh {
   const int32_t *tri_class, *tri_nbr, *tri_facet;
   const int8_t *tri_nbr_loc, *tri_orient;
   const double *facet_sigma;
+  // double-float images (mixed form): reference tables in SmemTables order, class
+  // geometry [n_class][kGeo], penalty per facet
+  const float2 *tab_df, *geo_df, *sigma_df;
   // facet-system stencil
   const int32_t *facet_nbr, *facet_stencil, *facet_tri;
   const int32_t *facet_ext;           // internal -> external facet id (NULL: identity)
@@ -61,6 +64,9 @@ struct DevMesh {
   const float *st_blk_f, *st_binv_f;
   // state and work arrays
   double *u, *ustage, *h, *gl;        // [n_tri][nd] x3, [n_tri][3 nl]
+  // mixed form: double-float twins of u and u' (written with them by the recovery),
+  // and the condensation outputs h = P f, gl = G f in double-float
+  float2 *u_df, *ustage_df, *h_df, *gl_df;
   double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
@@ -92,6 +98,8 @@ struct StageArgs {
   double a, b, dt;
   const double* un;    // u^n
   const double* up;    // u'
+  const float2* un_df;   // their double-float twins (mixed form)
+  const float2* up_df;
 };
 
 struct SolveArgs {
@@ -109,7 +117,10 @@ struct SolveArgs {
 cudaError_t launch_lattice_to_coef(const DevMesh& m, const double* vals, double* coef, cudaStream_t s);
 cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double* vals, cudaStream_t s);
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s);
-cudaError_t launch_recover(const DevMesh& m, double* out, cudaStream_t s);
+cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
 cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);

@@ -57,6 +57,44 @@ __host__ __device__ __forceinline__ dfl operator*(dfl x, dfl y) {
   return dfl(h, l);
 }
 
+// Multiplication by 1/2 is exact on both words.
+__host__ __device__ __forceinline__ dfl half(dfl x) { return dfl(0.5f * x.hi, 0.5f * x.lo); }
+
+__host__ __device__ __forceinline__ double to_double(dfl x) { return double(x.hi) + double(x.lo); }
+__host__ __device__ __forceinline__ double to_double(float2 x) { return double(x.x) + double(x.y); }
+__host__ __device__ __forceinline__ dfl to_dfl(float2 x) { return dfl(x.x, x.y); }
+__host__ __device__ __forceinline__ float2 to_float2(dfl x) { return make_float2(x.hi, x.lo); }
+
+// Compensated accumulator for sums of double-float products (the Dot2 scheme of
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005), applied to double-float
+// operands): s carries the running FP32 sum of the leading products, c the sum of
+// every rounding error, each captured exactly by TwoProd / TwoSum. One
+// multiply-add costs 12 FP32 operations; the pair is normalised once, by val().
+struct dacc {
+  float s, c;
+};
+
+__host__ __device__ __forceinline__ dacc dacc_zero() { return dacc{0.f, 0.f}; }
+__host__ __device__ __forceinline__ dacc dacc_of(dfl x) { return dacc{x.hi, x.lo}; }
+
+// a += x * y (the lo * lo product is below the double-float rounding and dropped)
+__host__ __device__ __forceinline__ void mad(dacc& a, dfl x, dfl y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  float s, t;
+  two_sum(a.s, p, s, t);
+  a.s = s;
+  a.c += t + e;
+}
+
+__host__ __device__ __forceinline__ dfl val(dacc a) {
+  float h, l;
+  two_sum(a.s, a.c, h, l);
+  return dfl(h, l);
+}
+
 __host__ __device__ __forceinline__ dfl& operator+=(dfl& x, dfl y) { return x = x + y; }
 __host__ __device__ __forceinline__ dfl& operator-=(dfl& x, dfl y) { return x = x - y; }
 __host__ __device__ __forceinline__ dfl& operator*=(dfl& x, dfl y) { return x = x * y; }

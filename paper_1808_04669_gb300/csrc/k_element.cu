@@ -4,31 +4,9 @@
 #include "device.cuh"
 #include "dfloat.cuh"
 #include "kcommon.cuh"
+#include "ktables.cuh"
 
 namespace dgdf {
-
-// Reference tables staged in shared memory in precision R.
-template <int K, typename R>
-struct SmemTables {
-  using D = Dims<K>;
-  R vw[D::NQ];
-  R vphi[D::NQ][D::NS];
-  R vdphi[D::NQ][D::NS][2];
-  R fw[D::NQF];
-  R fphi[3][D::NQF][D::NS];
-  R fdphi[3][D::NQF][D::NS][2];
-};
-
-template <int K, typename R>
-__device__ void load_tables(const DevMesh& m, SmemTables<K, R>& T) {
-  using D = Dims<K>;
-  for (int i = threadIdx.x; i < D::NQ; i += blockDim.x) T.vw[i] = R(m.vw[i]);
-  for (int i = threadIdx.x; i < D::NQ * D::NS; i += blockDim.x) (&T.vphi[0][0])[i] = R(m.vphi[i]);
-  for (int i = threadIdx.x; i < D::NQ * D::NS * 2; i += blockDim.x) (&T.vdphi[0][0][0])[i] = R(m.vdphi[i]);
-  for (int i = threadIdx.x; i < D::NQF; i += blockDim.x) T.fw[i] = R(m.fw[i]);
-  for (int i = threadIdx.x; i < 3 * D::NQF * D::NS; i += blockDim.x) (&T.fphi[0][0][0])[i] = R(m.fphi[i]);
-  for (int i = threadIdx.x; i < 3 * D::NQF * D::NS * 2; i += blockDim.x) (&T.fdphi[0][0][0][0])[i] = R(m.fdphi[i]);
-}
 
 // acc[i] = L(u)(phi_i) on triangle t: -C_h(u;u,phi_i) - B_h(u,phi_i) (eq. (7), eq. (18)).
 // Volume: int (u x u - nu grad u) : grad phi. Facets: the upwind flux with u.n the
@@ -316,23 +294,10 @@ __global__ void k_nu_accumulate(DevMesh m, int nparts, double coef, double* acc_
   if (threadIdx.x == 0) *acc_dev += coef * v;
 }
 
-// Operator entry in precision R (double-float copies avoid FP64 conversions).
-template <typename R>
-__device__ __forceinline__ R op_entry(const double* d, const float2* f, size_t i);
-template <>
-__device__ __forceinline__ double op_entry<double>(const double* d, const float2*, size_t i) {
-  return d[i];
-}
-template <>
-__device__ __forceinline__ dfl op_entry<dfl>(const double*, const float2* f, size_t i) {
-  const float2 v = f[i];
-  return dfl(v.x, v.y);
-}
-
-// Stage kernel. Modes (StageMode): the stage functional and its condensation
-// (h = P f, gl = G f), the residual alone, the pressure functional, or the
-// projection functional. R = double (FP64 form) or dfl (double-float on the
-// FP32 units, mixed form); inputs and outputs are FP64 either way.
+// Stage kernel, FP64 form (the mixed form's is k_stage_df in k_stage_df.cu).
+// Modes (StageMode): the stage functional and its condensation (h = P f,
+// gl = G f), the residual alone, the pressure functional, or the projection
+// functional.
 template <int K, typename R>
 __global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
   using D = Dims<K>;
@@ -368,14 +333,14 @@ __global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
     for (int i = 0; i < ND; ++i) {
       R v = R(0);
 #pragma unroll
-      for (int j = 0; j < ND; ++j) v += op_entry<R>(m.P, m.Pdf, (size_t(c) * ND + i) * ND + j) * f[j];
+      for (int j = 0; j < ND; ++j) v += m.P[(size_t(c) * ND + i) * ND + j] * f[j];
       m.h[size_t(t) * ND + i] = double(v);
     }
   }
   for (int i = 0; i < L3; ++i) {
     R v = R(0);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) v += op_entry<R>(m.G, m.Gdf, (size_t(c) * L3 + i) * ND + j) * f[j];
+    for (int j = 0; j < ND; ++j) v += m.G[(size_t(c) * L3 + i) * ND + j] * f[j];
     m.gl[size_t(t) * L3 + i] = double(v);
   }
 }
@@ -660,15 +625,13 @@ cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double*
 }
 
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
-  if (m.elem_df) {
-    DGDF_DISPATCH_K(m.k, (k_stage<K, dfl><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
-  } else {
-    DGDF_DISPATCH_K(m.k, (k_stage<K, double><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
-  }
+  if (m.elem_df) return launch_stage_df(m, a, s);
+  DGDF_DISPATCH_K(m.k, (k_stage<K, double><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, a)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_recover(const DevMesh& m, double* out, cudaStream_t s) {
+cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
+  if (m.elem_df) return launch_recover_df(m, out, out_df, s);
   DGDF_DISPATCH_K(m.k, (k_recover<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out)));
   return cudaGetLastError();
 }

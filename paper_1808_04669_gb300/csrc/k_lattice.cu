@@ -294,19 +294,7 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
   double gg[2] = {0.0, 0.0};
   for (int f = gtid; f < nF; f += gsz) {
     double gv[NL];
-#pragma unroll
-    for (int j = 0; j < NL; ++j) gv[j] = 0.0;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
-      const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
-      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
-#pragma unroll
-      for (int j = 0; j < NL; ++j) {
-        const double v = m.gl[size_t(t) * 3 * NL + e * NL + j];
-        gv[j] += (flip && (j & 1)) ? -v : v;
-      }
-    }
+    assemble_g<NL>(m, f, gv);
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;

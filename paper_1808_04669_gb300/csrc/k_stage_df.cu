@@ -1,0 +1,266 @@
+// Element kernels of the mixed form: the stage residual + condensation (K1-K3)
+// and the recovery (K5) in double-float arithmetic on the FP32 units.
+//
+// Two threads per triangle, one per velocity component c: the residual of
+// eq. (7) + eq. (18) couples the components only through u (x) u and the normal
+// velocity u.n, which the pair exchanges by warp shuffles at every quadrature
+// point; every sum over basis functions belongs to one component. This halves
+// the registers a thread holds (its component's coefficients, its neighbour
+// traces and its accumulators) against one thread per triangle, so twice as many
+// warps hide the FP32 latency. Inputs are the double-float twins of u^n and u'
+// (no FP64 conversions on this path); sums of products use the compensated
+// accumulator dacc (12 FP32 operations per multiply-add).
+#include "device.cuh"
+#include "dfloat.cuh"
+#include "kcommon.cuh"
+#include "ktables.cuh"
+
+namespace dgdf {
+
+constexpr int kStageDfThreads = 256;   // 128 triangles per block
+
+namespace {
+
+__device__ __forceinline__ dfl shfl_pair(dfl v) {
+  return dfl(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+}
+
+template <int N>
+__device__ __forceinline__ void load_df(const float2* __restrict__ p, dfl (&c)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) c[i] = to_dfl(p[i]);
+}
+
+// acc[j] += the component-c part of L(u')(phi_j): -C_h(u;u,phi) - B_h(u,phi) of
+// eq. (7) and eq. (18). Volume: int (u_c u - nu grad u_c) . grad phi_j. Facets: the
+// upwind flux (u.n) u_c^up with u.n the average of both traces, and the SIPG
+// consistency, symmetry and penalty terms, at the facet Gauss points (the
+// neighbour's point q is our point NQF-1-q).
+template <int K>
+__device__ __forceinline__ void residual_component(const DevMesh& m, const SmemTables<K, dfl>& T, int t, int c,
+                                                   const float2* __restrict__ ug, const dfl (&up)[Dims<K>::NS],
+                                                   dacc (&acc)[Dims<K>::NS]) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, ND = D::ND;
+  const dfl nu(m.nu);
+  const float2* geo = m.geo_df + size_t(__ldg(&m.tri_class[t])) * kGeo;
+  const dfl Ji0 = to_dfl(geo[G_JINV + 0]), Ji1 = to_dfl(geo[G_JINV + 1]);
+  const dfl Ji2 = to_dfl(geo[G_JINV + 2]), Ji3 = to_dfl(geo[G_JINV + 3]);
+  const dfl s = to_dfl(geo[G_S]);
+  const dfl ds = to_dfl(geo[G_DET]) * s;
+  // ---- volume terms
+#pragma unroll 1
+  for (int q = 0; q < D::NQ; ++q) {
+    dacc U = dacc_zero(), A0 = dacc_zero(), A1 = dacc_zero();
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      mad(U, T.vphi[q][j], up[j]);
+      mad(A0, T.vdphi[q][j][0], up[j]);
+      mad(A1, T.vdphi[q][j][1], up[j]);
+    }
+    const dfl uc = s * val(U), a0 = val(A0), a1 = val(A1);
+    // physical gradient d u_c / d x_d = s sum_r a_r Jinv[r][d]
+    const dfl g0 = s * (a0 * Ji0 + a1 * Ji2), g1 = s * (a0 * Ji1 + a1 * Ji3);
+    const dfl uo = shfl_pair(uc);
+    const dfl u0 = c ? uo : uc, u1 = c ? uc : uo;
+    const dfl F0 = uc * u0 - nu * g0, F1 = uc * u1 - nu * g1;
+    const dfl w = T.vw[q] * ds;
+    // H_r = w sum_d F_d Jinv[r][d]
+    const dfl H0 = w * (F0 * Ji0 + F1 * Ji1), H1 = w * (F0 * Ji2 + F1 * Ji3);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      mad(acc[j], H0, T.vdphi[q][j][0]);
+      mad(acc[j], H1, T.vdphi[q][j][1]);
+    }
+  }
+  // ---- facet terms
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int tn = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
+    const int en = __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
+    const float2* geon = m.geo_df + size_t(__ldg(&m.tri_class[tn])) * kGeo;
+    const dfl sn = to_dfl(geon[G_S]);
+    const dfl n0 = to_dfl(geo[G_NRM + 2 * e]), n1 = to_dfl(geo[G_NRM + 2 * e + 1]);
+    const dfl nc = c ? n1 : n0;
+    const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
+    const dfl sig = to_dfl(m.sigma_df[__ldg(&m.tri_facet[size_t(t) * 3 + e])]);
+    const dfl nusig = nu * sig, hnu = half(nu);
+    // normal derivative in reference gradients: d_n psi = s sum_r d_r psihat (Jinv n)_r
+    const dfl mo0 = Ji0 * n0 + Ji1 * n1, mo1 = Ji2 * n0 + Ji3 * n1;
+    const dfl mn0 = to_dfl(geon[G_JINV + 0]) * n0 + to_dfl(geon[G_JINV + 1]) * n1;
+    const dfl mn1 = to_dfl(geon[G_JINV + 2]) * n0 + to_dfl(geon[G_JINV + 3]) * n1;
+    dfl un[NS];
+    load_df<NS>(ug + size_t(tn) * ND + c * NS, un);
+#pragma unroll 1
+    for (int q = 0; q < D::NQF; ++q) {
+      const int qn = D::NQF - 1 - q;
+      dacc V = dacc_zero(), D0 = dacc_zero(), D1 = dacc_zero();
+      dacc Vn = dacc_zero(), Dn0 = dacc_zero(), Dn1 = dacc_zero();
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        mad(V, T.fphi[e][q][j], up[j]);
+        mad(D0, T.fdphi[e][q][j][0], up[j]);
+        mad(D1, T.fdphi[e][q][j][1], up[j]);
+        mad(Vn, T.fphi[en][qn][j], un[j]);
+        mad(Dn0, T.fdphi[en][qn][j][0], un[j]);
+        mad(Dn1, T.fdphi[en][qn][j][1], un[j]);
+      }
+      const dfl ui = s * val(V), di = s * (mo0 * val(D0) + mo1 * val(D1));
+      const dfl uo = sn * val(Vn), dn = sn * (mn0 * val(Dn0) + mn1 * val(Dn1));
+      // u.n = 1/2 (u_in + u_out) . n, summed in the same order by both threads of the pair
+      const dfl pc = (ui + uo) * nc, po = shfl_pair(pc);
+      const dfl vn = half(c ? po + pc : pc + po);
+      const dfl wup = vn >= dfl(0) ? ui : uo;
+      const dfl jc = ui - uo;
+      const dfl w = T.fw[q] * lens;
+      const dfl A = w * (hnu * (di + dn) - vn * wup - nusig * jc);
+      const dfl B = w * hnu * jc;
+      const dfl B0 = B * mo0, B1 = B * mo1;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        mad(acc[j], A, T.fphi[e][q][j]);
+        mad(acc[j], B0, T.fdphi[e][q][j][0]);
+        mad(acc[j], B1, T.fdphi[e][q][j][1]);
+      }
+    }
+  }
+}
+
+// Stage kernel, mixed form (all modes, see StageMode): reads the double-float
+// twins a.up_df / a.un_df; writes h_df = P f and gl_df = G f (MODE_STAGE,
+// MODE_PROJECT), h = f in FP64 (MODE_RESIDUAL, MODE_PRESSURE) and gl_df
+// (MODE_PRESSURE). Thread c of a pair owns rows c*NS.. of f and h, and the rows
+// i = c (mod 2) of gl.
+template <int K>
+__global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, StageArgs a) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, ND = D::ND, L3 = 3 * D::NL;
+  __shared__ SmemTables<K, dfl> T;
+  load_tables_df<K>(m, T);
+  __syncthreads();
+  const int c = threadIdx.x & 1;
+  const int traw = blockIdx.x * (kStageDfThreads / 2) + (threadIdx.x >> 1);
+  const bool live = traw < m.n_tri;
+  const int t = live ? traw : m.n_tri - 1;   // both threads of a pair stay for the shuffles
+  dfl up[NS];
+  load_df<NS>(a.up_df + size_t(t) * ND + c * NS, up);
+  dfl f[NS];
+  if (a.mode == MODE_PROJECT) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) f[j] = up[j];
+  } else {
+    dacc acc[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) acc[j] = dacc_zero();
+    residual_component<K>(m, T, t, c, a.up_df, up, acc);
+    if (a.mode == MODE_STAGE) {
+      dfl un[NS];
+      load_df<NS>(a.un_df + size_t(t) * ND + c * NS, un);
+      const dfl ca(a.a), cb(a.b), dt(a.dt);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) f[j] = ca * un[j] + cb * (up[j] + dt * val(acc[j]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < NS; ++j) f[j] = val(acc[j]);
+    }
+  }
+  if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
+    if (live)
+#pragma unroll
+      for (int j = 0; j < NS; ++j) m.h[size_t(t) * ND + c * NS + j] = to_double(f[j]);
+  }
+  if (a.mode == MODE_RESIDUAL) return;   // uniform over the block
+  dfl fo[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) fo[j] = shfl_pair(f[j]);
+  const int cls = __ldg(&m.tri_class[t]);
+  // F[i] = f_i in triangle order: component 0 first
+  auto F = [&](int i) -> dfl { return (i < NS) == (c == 0) ? f[i % NS] : fo[i % NS]; };
+  if (a.mode != MODE_PRESSURE) {
+    const float2* P = m.Pdf + size_t(cls) * ND * ND;
+    for (int r = 0; r < NS; ++r) {
+      const int i = c * NS + r;
+      dacc v = dacc_zero();
+#pragma unroll
+      for (int j = 0; j < ND; ++j) mad(v, to_dfl(__ldg(&P[i * ND + j])), F(j));
+      if (live) m.h_df[size_t(t) * ND + i] = to_float2(val(v));
+    }
+  }
+  const float2* G = m.Gdf + size_t(cls) * L3 * ND;
+  for (int i = c; i < L3; i += 2) {
+    dacc v = dacc_zero();
+#pragma unroll
+    for (int j = 0; j < ND; ++j) mad(v, to_dfl(__ldg(&G[i * ND + j])), F(j));
+    if (live) m.gl_df[size_t(t) * L3 + i] = to_float2(val(v));
+  }
+}
+
+// Recovery, mixed form: u_T = h_T - G_T^T lam_T (h = P f from the stage kernel) in
+// double-float; writes u in FP64 and, if out_df is given, its double-float twin.
+template <int K>
+__global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, float2* out_df) {
+  using D = Dims<K>;
+  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_tri) return;
+  dfl lam[L3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int f = __ldg(&m.tri_facet[size_t(t) * 3 + e]);
+    const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+    for (int mm = 0; mm < NL; ++mm) {
+      const dfl v(m.lam[size_t(f) * NL + mm]);
+      lam[e * NL + mm] = (flip && (mm & 1)) ? v : -v;   // negated: u = h + sum (-G) lam
+    }
+  }
+  const float2* G = m.Gdf + size_t(__ldg(&m.tri_class[t])) * L3 * ND;
+#pragma unroll 4
+  for (int i = 0; i < ND; ++i) {
+    dacc v = dacc_of(to_dfl(m.h_df[size_t(t) * ND + i]));
+#pragma unroll
+    for (int l = 0; l < L3; ++l) mad(v, to_dfl(__ldg(&G[l * ND + i])), lam[l]);
+    const dfl u = val(v);
+    out[size_t(t) * ND + i] = to_double(u);
+    if (out_df) out_df[size_t(t) * ND + i] = to_float2(u);
+  }
+}
+
+__global__ void k_to_dfl(const double* __restrict__ x, float2* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = to_float2(dfl(x[i]));
+}
+
+inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
+
+}  // namespace
+
+#define DGDF_DISPATCH_K(kv, CALL) \
+  switch (kv) {                   \
+    case 1: { constexpr int K = 1; CALL; break; } \
+    case 2: { constexpr int K = 2; CALL; break; } \
+    case 3: { constexpr int K = 3; CALL; break; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
+  if (!a.up_df || (a.mode == MODE_STAGE && !a.un_df)) return cudaErrorInvalidValue;
+  const int nb = blocks_for(m.n_tri, kStageDfThreads / 2);
+  DGDF_DISPATCH_K(m.k, (k_stage_df<K><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
+  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out, out_df)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_to_dfl<<<int(nb), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dgdf

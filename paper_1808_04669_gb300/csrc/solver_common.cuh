@@ -3,6 +3,7 @@
 #pragma once
 
 #include "device.cuh"
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 
 namespace dgdf {
@@ -85,6 +86,46 @@ __device__ __forceinline__ void block_apply(const R* __restrict__ B, const R (&x
 #pragma unroll
     for (int j = 0; j < NL; ++j) v += __ldg(&B[i * NL + j]) * x[j];
     y[i] = v;
+  }
+}
+
+// g_F = sum over both sides of facet f of the side's condensation output mapped to
+// the facet's canonical orientation (odd Legendre modes change sign when a side
+// traverses the facet backwards). Mixed form: the sides' double-float values are
+// summed in double-float and rounded to FP64 once.
+template <int NL>
+__device__ __forceinline__ void assemble_g(const DevMesh& m, int f, double (&gv)[NL]) {
+  if (m.elem_df) {
+    dfl acc[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) acc[j] = dfl(0);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+      const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
+      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const dfl v = to_dfl(m.gl_df[size_t(t) * 3 * NL + e * NL + j]);
+        acc[j] += (flip && (j & 1)) ? -v : v;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) gv[j] = to_double(acc[j]);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < NL; ++j) gv[j] = 0.0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+    const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
+    const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const double v = m.gl[size_t(t) * 3 * NL + e * NL + j];
+      gv[j] += (flip && (j & 1)) ? -v : v;
+    }
   }
 }
 
