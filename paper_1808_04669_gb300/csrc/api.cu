@@ -352,19 +352,45 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   if (lat.ok && lat_blocks > 0) {
     const int fp32 = lat_fp32;
     const int C = lat.C, N = lat.N;
-    const size_t nS = size_t(N) * N * C * C;
+    // device layout [ki < N/2+1][entry][kj] complex: the residual is real, so only half the
+    // wavenumbers along i are needed. FP32: entries (a, b), a <= b, of the Hermitian block;
+    // FP64: all C*C entries (the host inverse is Hermitian only to about cond * eps, which
+    // FP64 would resolve).
+    const int NK = N / 2 + 1, NP = fp32 ? C * (C + 1) / 2 : C * C;
+    const size_t nS = dgdf::lattice_symbol_elems(hm.k, N, fp32);
     std::vector<double> sd;
     std::vector<float> sf;
     if (fp32) sf.resize(2 * nS); else sd.resize(2 * nS);
-    // host layout [ki][kj][C][C][2] -> device [ki][C][C][kj] complex
-    for (int ki = 0; ki < N; ++ki)
-      for (int kj = 0; kj < N; ++kj)
-        for (int cc = 0; cc < C * C; ++cc)
-          for (int ri = 0; ri < 2; ++ri) {
-            const double v = lat.sinv[((size_t(ki) * N + kj) * C * C + cc) * 2 + ri];
-            const size_t o = ((size_t(ki) * C * C + cc) * N + kj) * 2 + ri;
-            if (fp32) sf[o] = float(v); else sd[o] = v;
+    // The half-spectrum transform takes S^(-kappa) = conj S^(kappa) for granted; the
+    // self-conjugate columns ki = 0 and ki = N/2 are symmetrised here (the host inverts
+    // each wavenumber on its own, so the pairs agree only to rounding).
+    auto H = [&](int ki, int kj, int ca, int cb, int ri) {
+      return lat.sinv[((size_t(ki) * N + kj) * C * C + size_t(ca) * C + cb) * 2 + ri];
+    };
+    for (int ki = 0; ki < NK; ++ki) {
+      const bool selfconj = ki == 0 || 2 * ki == N;
+      for (int kj = 0; kj < N; ++kj) {
+        const int mj = (N - kj) % N;
+        int pi = 0;
+        for (int ca = 0; ca < C; ++ca)
+          for (int cb = fp32 ? ca : 0; cb < C; ++cb, ++pi) {
+            double re = H(ki, kj, ca, cb, 0), im = H(ki, kj, ca, cb, 1);
+            if (selfconj) {
+              re = 0.5 * (re + H(ki, mj, ca, cb, 0));
+              im = 0.5 * (im - H(ki, mj, ca, cb, 1));
+            }
+            if (fp32 && ca == cb) im = 0.0;
+            const size_t o = ((size_t(ki) * NP + pi) * N + kj) * 2;
+            if (fp32) {
+              sf[o] = float(re);
+              sf[o + 1] = float(im);
+            } else {
+              sd[o] = re;
+              sd[o + 1] = im;
+            }
           }
+      }
+    }
     std::vector<double>().swap(lat.sinv);
     const int32_t* fo = nullptr;
     const int32_t* fe = nullptr;
@@ -377,22 +403,28 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       if ((rc = upload(M, &sp, sf))) return cleanup(rc);
       d.lat_sinv = sp;
       float* xp = nullptr;
-      if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+      if ((rc = dalloc(M, &xp, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
       d.lat_x = xp;
+      // the mixed lattice solver keeps its multipliers in double-float
+      if ((rc = dalloc(M, &d.lam_df, nF * nl)) || (rc = upload(M, &d.st_blk_df, to_dfloat(hm.stencil_blocks))))
+        return cleanup(rc);
+      if (cudaMemsetAsync(d.lam_df, 0, nF * nl * sizeof(float2), M->stream) != cudaSuccess)
+        return cleanup(fail(DG_ERR_CUDA, "initialise the double-float multipliers"));
+      d.lam_is_df = 1;
     } else {
       const double* sp = nullptr;
       if ((rc = upload(M, &sp, sd))) return cleanup(rc);
       d.lat_sinv = sp;
       double* xp = nullptr;
-      if ((rc = dalloc(M, &xp, size_t(2) * C * N * N))) return cleanup(rc);
+      if ((rc = dalloc(M, &xp, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
       d.lat_x = xp;
     }
     d.lat_facet_of = fo;
     d.facet_ext = fe;
     d.lat_tw = tw;
     d.lat_N = N;
-    d.lat_tr = dgdf::lattice_tile_rows(hm.k, N, fp32);
     d.lat_bufsz = int(dgdf::lattice_buffer_elems(hm.k, N, fp32));
+    d.lat_grp = dgdf::lattice_group_rows(hm.k, N, fp32);
     int logn = 0;
     while ((1 << logn) < N) ++logn;
     d.lat_logn = logn;
@@ -849,6 +881,11 @@ int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) 
   a.un_df = M->dm.u_df;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
   if ((rc = solve(M, 0.0))) return rc;
+  if (M->dm.lam_is_df) {   // the pressure kernels read the multipliers in FP64
+    const long long n = (long long)M->dm.n_facet * M->dm.nl;
+    if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_to_double(M->dm.lam_df, M->dm.lam, n, M->stream); })))
+      return rc;
+  }
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_pressure(M->dm, M->wbuf, M->stream); }))) return rc;
   if ((rc = launch(M, KC_PRESSURE, [&] {
          return dgdf::launch_pressure_lattice(M->dm, M->wbuf, M->pe, p_facet ? M->pfac : nullptr, M->stream);

@@ -62,6 +62,7 @@ struct DevMesh {
   const int8_t *facet_loc;
   const double *st_blk, *st_binv;     // [n_stencil][5][nl][nl], [n_stencil][nl][nl]
   const float *st_blk_f, *st_binv_f;
+  const float2* st_blk_df;            // stencil blocks in double-float (mixed lattice solver)
   // state and work arrays
   double *u, *ustage, *h, *gl;        // [n_tri][nd] x3, [n_tri][3 nl]
   // mixed form: double-float twins of u and u' (written with them by the recovery),
@@ -69,14 +70,17 @@ struct DevMesh {
   float2 *u_df, *ustage_df, *h_df, *gl_df;
   double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
+  float2* lam_df;                     // mixed lattice solver: the multipliers in double-float
+  int lam_is_df;                      // 1: the last solve left lam in lam_df (recovery reads it)
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
   // lattice (translation-invariant split-square) solver data
-  int lat_N, lat_logn, lat_tr;      // cells per direction, log2 N, rows per tile of the row passes
-  int lat_bufsz;                    // complex elements per shared-memory transform buffer
+  int lat_N, lat_logn;              // cells per direction, log2 N
+  int lat_bufsz;                    // complex elements of the shared-memory transform buffer
+  int lat_grp;                      // rows per transform group (scratch of lat_grp rows)
   const int32_t* lat_facet_of;        // [3][N][N]
-  const void* lat_sinv;               // [N][C][C][N] complex (float2 or double2)
+  const void* lat_sinv;               // [N/2+1][C(C+1)/2 (FP32) or C*C (FP64)][N] complex
   const double* lat_tw;               // [N][2]
-  void* lat_x;                        // [C][N][N] complex work array
+  void* lat_x;                        // [C][N/2+1][N] complex work array
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
@@ -121,6 +125,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s);
+cudaError_t launch_to_double(const float2* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
 cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);
@@ -129,8 +134,10 @@ cudaError_t launch_adjoint(const DevMesh& m, const double* u, const double* w, d
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
-int lattice_tile_rows(int k, int N, int fp32);
-size_t lattice_smem_bytes(int k, int N, int fp32);
+size_t lattice_smem_bytes(int k, int N, int fp32, int grp);
+int lattice_group_rows(int k, int N, int fp32);          // rows per transform group (0: no fit)
+size_t lattice_symbol_elems(int k, int N, int fp32);   // complex entries of the stored inverse symbol
+size_t lattice_spectrum_elems(int k, int N);   // complex entries of the spectrum work array
 size_t lattice_buffer_elems(int k, int N, int fp32);
 int lattice_blocks(int k, int N, int fp32);
 cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nblocks, int fp32, cudaStream_t s);

@@ -89,6 +89,17 @@ __host__ __device__ __forceinline__ void mad(dacc& a, dfl x, dfl y) {
   a.c += t + e;
 }
 
+// a += x * z for a double-float x and an FP32 z
+__host__ __device__ __forceinline__ void mad(dacc& a, dfl x, float z) {
+  const float p = x.hi * z;
+  float e = fmaf(x.hi, z, -p);
+  e = fmaf(x.lo, z, e);
+  float s, t;
+  two_sum(a.s, p, s, t);
+  a.s = s;
+  a.c += t + e;
+}
+
 __host__ __device__ __forceinline__ dfl val(dacc a) {
   float h, l;
   two_sum(a.s, a.c, h, l);

@@ -3,38 +3,75 @@
 //
 // On such a mesh the facet operator S is block circulant over the N x N cell
 // grid: a 2-D discrete Fourier transform turns it into one Hermitian block
-// S^(kappa) of size C = 3(k+1) per wavenumber, and S^+ r = IDFT(S^(kappa)^-1 DFT(r))
+// S^(kappa) of size C = 3(k+1) per wavenumber, and S^+ r = IDFT(S^(kappa)^+ DFT(r))
 // (pseudo-inverse at kappa = 0, the constant multiplier). This kernel runs PCG
-// with FP64 vectors and FP64 SpMV, preconditioned by that Fourier-space inverse
-// evaluated in precision R (FP32 in the mixed form, FP64 in the FP64 form):
-// the preconditioned operator is the identity up to R's rounding, so a solve
-// takes one or two iterations (FP64) or a few (FP32), instead of O(N).
-// The transforms run in shared memory (radix-2 FFTs when N is a power of two):
-//   rows  : DFT along i of r (facets numbered in lattice order), tiles of rows
-//   column: DFT along j, multiply by S^(kappa)^-1, inverse DFT along j
-//   rows  : inverse DFT along i, scattered back to facet order (scaled 1/N^2)
-// (for N not a power of two a direct O(N^2) DFT per row in shared memory)
-// with a grid barrier between the three passes. One persistent cooperative
-// kernel per solve, one block per SM.
+// preconditioned by that Fourier-space inverse:
+//   FP64 form : FP64 vectors, FP64 SpMV, FP64 transforms (one or two iterations);
+//   mixed form: double-float vectors and SpMV on the FP32 units, FP32 transforms
+//               (a few iterations: the preconditioned operator is I + O(FP32 rounding)).
+// The residual is real, so only the wavenumbers ki in [0, N/2] are transformed:
+//   rows   : two facet rows j, j+1 packed as one complex row, FFT along i, split
+//            into the two half spectra (Hermitian symmetry)
+//   columns: per ki, FFT along j, multiply by S^(kappa)^+ (upper triangle stored,
+//            the lower one is its conjugate), inverse FFT along j
+//   rows   : inverse FFT along i of two rows packed the same way (scaled 1/N^2)
+// with a grid barrier between the passes. Transforms run in shared memory:
+// self-sorting (Stockham) radix-2 FFTs when N is a power of two, a direct DFT
+// otherwise. One persistent cooperative kernel per solve, two blocks per SM.
 #include "device.cuh"
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 #include "solver_common.cuh"
 
 namespace dgdf {
 namespace {
 
-constexpr int kLatThreads = 512;
+constexpr int kLatThreads = 256;
+constexpr int kLatTJ = 4;          // facet rows j per row-pass tile (two packed pairs)
 
-template <typename R>
-struct CxT;
+template <bool MIXED>
+struct LatT;
 template <>
-struct CxT<float> {
-  using T = float2;
+struct LatT<false> {   // FP64 form
+  using R = double;
+  using C2 = double2;
+  using V = double;     // vector storage (lam, g, r, p, q)
+  using A = double;     // arithmetic on vector values
+  using Z = double;     // preconditioned residual z
+  using Acc = double;
 };
 template <>
-struct CxT<double> {
-  using T = double2;
+struct LatT<true> {    // mixed form
+  using R = float;
+  using C2 = float2;
+  using V = float2;
+  using A = dfl;
+  using Z = float;
+  using Acc = dacc;
 };
+
+// ---- typed vector access and accumulation
+__device__ __forceinline__ double ldv(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ dfl ldv(const float2* p) { return to_dfl(__ldcg(p)); }
+__device__ __forceinline__ double ldz(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldz(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ void stv(double* p, double v) { *p = v; }
+__device__ __forceinline__ void stv(float2* p, dfl v) { *p = to_float2(v); }
+__device__ __forceinline__ void mad(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ dacc acc_zero(dacc) { return dacc_zero(); }
+__device__ __forceinline__ double acc_val(double a) { return a; }
+__device__ __forceinline__ double acc_val(const dacc& a) { return double(a.s) + double(a.c); }
+__device__ __forceinline__ double fin(double a) { return a; }
+__device__ __forceinline__ dfl fin(const dacc& a) { return val(a); }
+__device__ __forceinline__ double fft_in(double v) { return v; }
+__device__ __forceinline__ float fft_in(dfl v) { return v.hi; }
+__device__ __forceinline__ double as_a(double v) { return v; }
+__device__ __forceinline__ double lead_d(double v) { return v; }
+__device__ __forceinline__ double lead_d(dfl v) { return double(v.hi); }
+__device__ __forceinline__ dfl as_a(float v) { return dfl(v, 0.f); }
+__device__ __forceinline__ double stencil_entry(const DevMesh& m, size_t i, double) { return __ldg(&m.st_blk[i]); }
+__device__ __forceinline__ dfl stencil_entry(const DevMesh& m, size_t i, dfl) { return to_dfl(__ldg(&m.st_blk_df[i])); }
 
 template <typename C2>
 __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
@@ -48,48 +85,47 @@ template <typename C2>
 __device__ __forceinline__ C2 csub(C2 a, C2 b) {
   return {a.x - b.x, a.y - b.y};
 }
-
-__device__ __forceinline__ int brev(int t, int logn) { return logn == 0 ? 0 : int(__brev(unsigned(t)) >> (32 - logn)); }
-
-// Radix-2 decimation in time on `rows` rows of length n = 2^logn in shared memory:
-// input in bit-reversed order, output in natural order. tw[t] = exp(-2 pi i t / n).
+// a += h b
 template <typename C2>
-__device__ void fft_dit(C2* buf, int rows, int logn, const C2* tw, bool inverse) {
-  const int n = 1 << logn, hn = n >> 1;
-  for (int s = 1; s <= logn; ++s) {
-    const int half = 1 << (s - 1), step = n >> s;
-    for (int b = threadIdx.x; b < rows * hn; b += blockDim.x) {
-      const int row = b / hn, k = b - row * hn;
-      const int grp = k >> (s - 1), pos = k & (half - 1);
-      const int i0 = row * n + (grp << s) + pos, i1 = i0 + half;
-      C2 w = tw[pos * step];
-      if (inverse) w.y = -w.y;
-      const C2 u = buf[i0], v = cmul(buf[i1], w);
-      buf[i0] = cadd(u, v);
-      buf[i1] = csub(u, v);
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void cmad(C2& a, C2 h, C2 b) {
+  a.x += h.x * b.x - h.y * b.y;
+  a.y += h.x * b.y + h.y * b.x;
+}
+// a += conj(h) b
+template <typename C2>
+__device__ __forceinline__ void cmad_conj(C2& a, C2 h, C2 b) {
+  a.x += h.x * b.x + h.y * b.y;
+  a.y += h.x * b.y - h.y * b.x;
 }
 
-// Radix-2 decimation in frequency: input natural, output bit-reversed.
+// Self-sorting (Stockham) radix-2 FFT of `rows` rows of length n = 2^logn, natural
+// order in and out, ping-ponging between a and b; returns the buffer holding the
+// result. Stage s combines pairs (j, j + n/2) of the input into outputs
+// (j / l) 2l + j % l and that + l, l = 2^s, with twiddle exp(-+2 pi i (j % l) / (2l)).
+// tw[t] = exp(-2 pi i t / n).
 template <typename C2>
-__device__ void fft_dif(C2* buf, int rows, int logn, const C2* tw, bool inverse) {
+__device__ C2* fft_stockham(C2* a, C2* b, int rows, int logn, const C2* tw, bool inverse) {
   const int n = 1 << logn, hn = n >> 1;
-  for (int s = logn; s >= 1; --s) {
-    const int half = 1 << (s - 1), step = n >> s;
-    for (int b = threadIdx.x; b < rows * hn; b += blockDim.x) {
-      const int row = b / hn, k = b - row * hn;
-      const int grp = k >> (s - 1), pos = k & (half - 1);
-      const int i0 = row * n + (grp << s) + pos, i1 = i0 + half;
-      C2 w = tw[pos * step];
+  for (int s = 0; s < logn; ++s) {
+    const int l = 1 << s;
+    for (int e = threadIdx.x; e < rows * hn; e += blockDim.x) {
+      const int row = e >> (logn - 1), j = e & (hn - 1);
+      const C2* x = a + row * n;
+      C2* y = b + row * n;
+      const int k = j & (l - 1);
+      C2 w = tw[k << (logn - 1 - s)];
       if (inverse) w.y = -w.y;
-      const C2 u = buf[i0], v = buf[i1];
-      buf[i0] = cadd(u, v);
-      buf[i1] = cmul(csub(u, v), w);
+      const C2 c0 = x[j], c1 = cmul(x[j + hn], w);
+      const int d = ((j - k) << 1) + k;
+      y[d] = cadd(c0, c1);
+      y[d + l] = csub(c0, c1);
     }
     __syncthreads();
+    C2* t = a;
+    a = b;
+    b = t;
   }
+  return a;
 }
 
 // Direct DFT of `rows` rows of length n (any n): out[r][k] = sum_t in[r][t] w^(t k mod n),
@@ -113,200 +149,332 @@ __device__ void dft(const C2* in, C2* out, int rows, int n, const C2* tw, bool i
   __syncthreads();
 }
 
-template <int K, typename R>
+template <int K, bool MIXED>
 struct LatCtx {
-  using C2 = typename CxT<R>::T;
+  using T = LatT<MIXED>;
+  using C2 = typename T::C2;
   static constexpr int NL = K + 1, C = 3 * NL;
-  int N, logn, tr, ntj;
-  bool pow2;      // radix-2 FFT (N a power of two) or direct DFT
-  C2* tw;         // [N] exp(-2 pi i t / N)
-  C2* buf;
-  C2* buf2;       // second buffer of the direct DFT
-  C2* X;          // [C][N(ki)][N(j)]
-  const C2* S;    // [N(ki)][C][C][N(kj)]
+  // stored entries per wavenumber: the packed upper triangle in FP32 (its rounding hides the
+  // host inverse's departure from Hermitian), the full block in FP64
+  static constexpr int NP = MIXED ? C * (C + 1) / 2 : C * C;
+  int N, logn, NK, ntj;   // NK = N/2 + 1 wavenumbers ki; ntj row tiles per facet type
+  int grp;                // rows transformed at a time (the scratch holds grp rows)
+  bool pow2;              // Stockham FFT (N a power of two) or direct DFT
+  C2* tw;                 // [N] exp(-2 pi i t / N)
+  C2* bufa;               // transform data, max(C, 2(k+1)) rows of N
+  C2* scr;                // scratch, grp rows of N
+  C2* X;                  // [C][NK][N] spectrum: half along i, full along j (then along kj)
+  const C2* S;            // [NK][NP][N] S^(kappa)^+ (packed upper triangle or full), kj fastest
+  // vectors, facet-major [n_facet][NL] in lattice order
+  typename T::V *lam, *g, *r, *q;
+  typename T::Z* z;
 };
 
-// Position in the transform buffer of the element with index i: bit-reversed for the
-// radix-2 passes (input of the forward one, output of the inverse one), natural for the DFT.
-template <int K, typename R>
-__device__ __forceinline__ int tpos(const LatCtx<K, R>& L, int i) {
-  return L.pow2 ? brev(i, L.logn) : i;
-}
-
-// Forward transform of rows loaded at tpos(); returns the buffer with the natural-order result.
-template <int K, typename R>
-__device__ typename CxT<R>::T* xform_fwd(const LatCtx<K, R>& L, typename CxT<R>::T* a, typename CxT<R>::T* b,
-                                         int rows) {
-  if (L.pow2) {
-    fft_dit(a, rows, L.logn, L.tw, false);
-    return a;
+// Forward or inverse transform, in place, of `rows` natural-order rows held in a: groups
+// of L.grp rows go through the scratch buffer (the Stockham passes and the direct DFT
+// are out of place; a result left in the scratch is copied back).
+template <int K, bool MIXED>
+__device__ void xform(const LatCtx<K, MIXED>& L, typename LatT<MIXED>::C2* a, int rows, bool inverse) {
+  using C2 = typename LatT<MIXED>::C2;
+  const int N = L.N;
+  for (int r0 = 0; r0 < rows; r0 += L.grp) {
+    const int gr = min(L.grp, rows - r0);
+    C2* d = a + size_t(r0) * N;
+    const C2* res;
+    if (L.pow2) {
+      res = fft_stockham(d, L.scr, gr, L.logn, L.tw, inverse);
+    } else {
+      dft(d, L.scr, gr, N, L.tw, inverse);
+      res = L.scr;
+    }
+    if (res != d) {
+      for (int e = threadIdx.x; e < gr * N; e += blockDim.x) d[e] = res[e];
+      __syncthreads();
+    }
   }
-  dft(a, b, rows, L.N, L.tw, false);
-  return b;
 }
 
-// Inverse transform of natural-order rows; index i of the result sits at tpos(i).
-template <int K, typename R>
-__device__ typename CxT<R>::T* xform_inv(const LatCtx<K, R>& L, typename CxT<R>::T* a, typename CxT<R>::T* b,
-                                         int rows) {
-  if (L.pow2) {
-    fft_dif(a, rows, L.logn, L.tw, true);
-    return a;
-  }
-  dft(a, b, rows, L.N, L.tw, true);
-  return b;
-}
-
-// Facets are numbered (type, j, i) on a lattice mesh, so a tile of tr rows of one
+// Facets are numbered (type, j, i) on a lattice mesh, so a tile of kLatTJ rows of one
 // facet type with all k+1 modes is one contiguous range of the facet-major vectors:
 // DOF index ((type N + j) N + i)(k+1) + m.
 
-// Row pass, forward: read r (optionally first updating r -= alpha q, lam += alpha p),
-// DFT along i, store transposed. Accumulates r.r into *rr.
-template <int K, typename R>
-__device__ void rows_forward(const DevMesh& m, const LatCtx<K, R>& L, bool update, double alpha, const double* p,
-                             double* rr) {
-  using C2 = typename CxT<R>::T;
+// Row pass, forward: per tile read r (first updating r -= alpha q, lam += alpha_lam p
+// when `update`), accumulate r.r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per
+// mode, FFT along i, split into the two rows' half spectra and store them in X.
+template <int K, bool MIXED>
+__device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename LatT<MIXED>::A alpha,
+                             typename LatT<MIXED>::A alpha_lam, const typename LatT<MIXED>::V* p,
+                             typename LatT<MIXED>::Acc& rr) {
+  using T = LatT<MIXED>;
+  using C2 = typename T::C2;
+  using R = typename T::R;
+  using A = typename T::A;
   constexpr int NL = K + 1;
-  const int N = L.N;
+  const int N = L.N, NK = L.NK;
   const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * L.tr;
-    const int rows = min(L.tr, N - j0);
+    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * kLatTJ;
+    const int rows = min(kLatTJ, N - j0), npair = (rows + 1) >> 1;
     const size_t base = (size_t(ty) * N + j0) * N * NL;
-    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
-      const int mm = e % NL, rest = e / NL;
-      const int r_ = rest / N, i = rest - r_ * N;
-      const size_t o = base + e;
-      double rv = __ldcg(&m.r[o]);
-      if (update) {
-        rv -= alpha * __ldcg(&m.q[o]);
-        m.r[o] = rv;
-        m.lam[o] += alpha * __ldcg(&p[o]);
-      }
-      *rr += rv * rv;
-      L.buf[(mm * rows + r_) * N + tpos(L, i)] = C2{R(rv), R(0)};
-    }
-    __syncthreads();
-    const C2* res = xform_fwd(L, L.buf, L.buf2, NL * rows);
-    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
-      const int r_ = e % rows, rest = e / rows;
-      const int mm = rest / N, ki = rest - mm * N;
-      L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_] = res[(mm * rows + r_) * N + ki];
-    }
-    __syncthreads();
-  }
-}
-
-// Column pass: DFT along j, multiply by S^(kappa)^-1 (warp c computes component c of 32
-// consecutive k_j), inverse DFT along j.
-template <int K, typename R>
-__device__ void columns(const LatCtx<K, R>& L) {
-  using C2 = typename CxT<R>::T;
-  constexpr int C = LatCtx<K, R>::C;
-  const int N = L.N;
-  const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
-  for (int ki = blockIdx.x; ki < N; ki += gridDim.x) {
-    for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
-      const int c = e / N, j = e - c * N;
-      L.buf[c * N + tpos(L, j)] = __ldcg(&L.X[(size_t(c) * N + ki) * N + j]);
-    }
-    __syncthreads();
-    C2* cur = xform_fwd(L, L.buf, L.buf2, C);
-    const C2* S = L.S + size_t(ki) * C * C * N;
-    for (int kj0 = 0; kj0 < N; kj0 += 32) {
-      const int kj = kj0 + lane;
-      const bool act = wc < C && kj < N;
-      C2 y = {R(0), R(0)};
-      if (act) {
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {   // one facet (row r_, column i)
+      const int r_ = e / N, i = e - r_ * N;
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) y = cadd(y, cmul(__ldg(&S[(size_t(wc) * C + cc) * N + kj]), cur[cc * N + kj]));
+      for (int mm = 0; mm < NL; ++mm) {
+        const size_t o = base + size_t(e) * NL + mm;
+        A rv = ldv(L.r + o);
+        if (update) {
+          rv = rv - alpha * ldv(L.q + o);
+          stv(L.r + o, rv);
+          stv(L.lam + o, ldv(L.lam + o) + alpha_lam * ldv(p + o));
+        }
+        mad(rr, rv, rv);
+        C2* slot = &L.bufa[((r_ >> 1) * NL + mm) * N + i];
+        if (r_ & 1) slot->y = fft_in(rv);
+        else slot->x = fft_in(rv);
       }
-      __syncthreads();
-      if (act) cur[wc * N + kj] = y;
-      __syncthreads();
     }
-    const C2* res = xform_inv(L, cur, cur == L.buf ? L.buf2 : L.buf, C);
+    if (rows & 1)   // the last pair has no odd row
+      for (int e = threadIdx.x; e < NL * N; e += blockDim.x) L.bufa[((npair - 1) * NL) * N + e].y = R(0);
+    __syncthreads();
+    xform(L, L.bufa, npair * NL, false);
+    const C2* res = L.bufa;
+    // Z = X_even + i X_odd: X_even[k] = (Z[k] + conj Z[-k]) / 2, X_odd[k] = (Z[k] - conj Z[-k]) / (2i)
+    for (int e = threadIdx.x; e < rows * NK * NL; e += blockDim.x) {
+      const int r_ = e % rows, rest = e / rows;
+      const int ki = rest % NK, mm = rest / NK;
+      const C2* row = res + ((r_ >> 1) * NL + mm) * N;
+      const C2 Z = row[ki], Zc = row[ki == 0 ? 0 : N - ki];
+      C2 out;
+      if (r_ & 1) {
+        out.x = R(0.5) * (Z.y + Zc.y);
+        out.y = R(-0.5) * (Z.x - Zc.x);
+      } else {
+        out.x = R(0.5) * (Z.x + Zc.x);
+        out.y = R(0.5) * (Z.y - Zc.y);
+      }
+      L.X[(size_t(ty * NL + mm) * NK + ki) * N + j0 + r_] = out;
+    }
+    __syncthreads();
+  }
+}
+
+// Column pass: per ki, FFT along j, y_a = sum_b H_ab x_b with H = S^(kappa)^+ (mixed
+// form: packed upper triangle, H_ba = conj H_ab), inverse FFT along j.
+template <int K, bool MIXED>
+__device__ void columns(const LatCtx<K, MIXED>& L) {
+  using C2 = typename LatT<MIXED>::C2;
+  constexpr int C = LatCtx<K, MIXED>::C;
+  constexpr int NP = LatCtx<K, MIXED>::NP;
+  const int N = L.N, NK = L.NK;
+  for (int ki = blockIdx.x; ki < NK; ki += gridDim.x) {
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
       const int c = e / N, j = e - c * N;
-      L.X[(size_t(c) * N + ki) * N + j] = res[c * N + tpos(L, j)];
+      L.bufa[e] = __ldcg(&L.X[(size_t(c) * NK + ki) * N + j]);
+    }
+    __syncthreads();
+    xform(L, L.bufa, C, false);
+    C2* cur = L.bufa;
+    const C2* S = L.S + size_t(ki) * NP * N;
+    for (int kj = threadIdx.x; kj < N; kj += blockDim.x) {
+      C2 x[C], y[C];
+#pragma unroll
+      for (int b = 0; b < C; ++b) {
+        x[b] = cur[b * N + kj];
+        y[b] = C2{0, 0};
+      }
+      if constexpr (MIXED) {
+        int pi = 0;
+#pragma unroll
+        for (int a = 0; a < C; ++a)
+#pragma unroll
+          for (int b = a; b < C; ++b, ++pi) {
+            const C2 h = __ldg(&S[size_t(pi) * N + kj]);
+            cmad(y[a], h, x[b]);
+            if (b != a) cmad_conj(y[b], h, x[a]);
+          }
+      } else {
+#pragma unroll
+        for (int a = 0; a < C; ++a)
+#pragma unroll
+          for (int b = 0; b < C; ++b) cmad(y[a], __ldg(&S[size_t(a * C + b) * N + kj]), x[b]);
+      }
+#pragma unroll
+      for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
+    }
+    __syncthreads();
+    xform(L, L.bufa, C, true);
+    const C2* res = L.bufa;
+    for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
+      const int c = e / N, j = e - c * N;
+      L.X[(size_t(c) * NK + ki) * N + j] = res[e];
     }
     __syncthreads();
   }
 }
 
-// Row pass, inverse: inverse DFT along i, z = result / N^2 in facet order.
-// Accumulates r.z_new into *rz and, if with_old, r.z_old into *rzo.
-template <int K, typename R>
-__device__ void rows_inverse(const DevMesh& m, const LatCtx<K, R>& L, bool with_old, double* rz, double* rzo) {
-  using C2 = typename CxT<R>::T;
+// Row pass, inverse: rebuild W = Y_even + i Y_odd over all k (Y[N-k] = conj Y[k]),
+// inverse FFT along i, z = the real / imaginary parts scaled by 1/N^2 in facet order.
+// Accumulates r.z_new into rz and, if with_old, r.z_old into rzo.
+template <int K, bool MIXED>
+__device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename LatT<MIXED>::Acc& rz,
+                             typename LatT<MIXED>::Acc& rzo) {
+  using T = LatT<MIXED>;
+  using C2 = typename T::C2;
+  using R = typename T::R;
+  using Z = typename T::Z;
   constexpr int NL = K + 1;
-  const int N = L.N;
-  const double scale = 1.0 / (double(N) * double(N));
+  const int N = L.N, NK = L.NK;
+  const R scale = R(1.0 / (double(N) * double(N)));
   const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * L.tr;
-    const int rows = min(L.tr, N - j0);
-    const size_t base = (size_t(ty) * N + j0) * N * NL;
-    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
-      const int r_ = e % rows, rest = e / rows;
-      const int mm = rest / N, ki = rest - mm * N;
-      L.buf[(mm * rows + r_) * N + ki] = __ldcg(&L.X[(size_t(ty * NL + mm) * N + ki) * N + j0 + r_]);
+    const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * kLatTJ;
+    const int rows = min(kLatTJ, N - j0), npair = (rows + 1) >> 1;
+    for (int e = threadIdx.x; e < npair * NK * NL; e += blockDim.x) {
+      const int pr = e % npair, rest = e / npair;
+      const int ki = rest % NK, mm = rest / NK;
+      const C2* src = &L.X[(size_t(ty * NL + mm) * NK + ki) * N + j0 + 2 * pr];
+      const C2 ya = __ldcg(src);
+      const C2 yb = (2 * pr + 1 < rows) ? __ldcg(src + 1) : C2{0, 0};
+      C2* w = L.bufa + (pr * NL + mm) * N;
+      w[ki] = C2{ya.x - yb.y, ya.y + yb.x};
+      if (ki > 0 && N - ki >= NK) w[N - ki] = C2{ya.x + yb.y, yb.x - ya.y};
     }
     __syncthreads();
-    const C2* res = xform_inv(L, L.buf, L.buf2, NL * rows);
-    for (int e = threadIdx.x; e < rows * N * NL; e += blockDim.x) {
-      const int mm = e % NL, rest = e / NL;
-      const int r_ = rest / N, i = rest - r_ * N;
-      const size_t o = base + e;
-      const double zv = double(res[(mm * rows + r_) * N + tpos(L, i)].x) * scale;
-      const double rv = __ldcg(&m.r[o]);
-      if (with_old) *rzo += rv * __ldcg(&m.z[o]);
-      *rz += rv * zv;
-      m.z[o] = zv;
+    xform(L, L.bufa, npair * NL, true);
+    const C2* res = L.bufa;
+    const size_t base = (size_t(ty) * N + j0) * N * NL;
+    for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
+      const int r_ = e / N, i = e - r_ * N;
+#pragma unroll
+      for (int mm = 0; mm < NL; ++mm) {
+        const size_t o = base + size_t(e) * NL + mm;
+        const C2 v = res[((r_ >> 1) * NL + mm) * N + i];
+        const Z zv = Z((r_ & 1) ? v.y : v.x) * Z(scale);
+        const auto rv = ldv(L.r + o);
+        if (with_old) mad(rzo, rv, ldz(L.z + o));
+        mad(rz, rv, zv);
+        L.z[o] = zv;
+      }
     }
     __syncthreads();
   }
 }
 
-template <int K, typename R>
-__global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveArgs a) {
-  using C2 = typename CxT<R>::T;
+// ---- loads of any vector type as the arithmetic type of its form
+__device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ dfl ldx(const float2* p) { return to_dfl(__ldcg(p)); }
+__device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ void acc_add(double& a, double v) { a += v; }
+__device__ __forceinline__ void acc_add(dacc& a, dfl v) {
+  float s, t;
+  two_sum(a.s, v.hi, s, t);
+  a.s = s;
+  a.c += t + v.lo;
+}
+
+// y = (S x)_f: the facet's own block and its four neighbours' (stencil class of f)
+template <int NL, bool MIXED, typename X>
+__device__ __forceinline__ void spmv_lat(const DevMesh& m, int f, const X* x, typename LatT<MIXED>::A (&y)[NL]) {
+  using A = typename LatT<MIXED>::A;
+  using Acc = typename LatT<MIXED>::Acc;
+  int nb[5];
+  facet_nbrs<NL>(m, f, nb);
+  const size_t sb = size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL;
+  Acc acc[NL];
+#pragma unroll
+  for (int i = 0; i < NL; ++i) acc[i] = acc_zero(Acc{});
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const auto xv = ldx(x + size_t(nb[b]) * NL + j);
+#pragma unroll
+      for (int i = 0; i < NL; ++i) mad(acc[i], stencil_entry(m, sb + (b * NL + i) * NL + j, A{}), xv);
+    }
+#pragma unroll
+  for (int i = 0; i < NL; ++i) y[i] = fin(acc[i]);
+}
+
+// g of facet f in the arithmetic type of the form
+template <int NL>
+__device__ __forceinline__ void facet_g(const DevMesh& m, int f, double (&gv)[NL]) {
+  assemble_g<NL>(m, f, gv);
+}
+template <int NL>
+__device__ __forceinline__ void facet_g(const DevMesh& m, int f, dfl (&gv)[NL]) {
+  assemble_g_df<NL>(m, f, gv);
+}
+
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveArgs a) {
+  using T = LatT<MIXED>;
+  using C2 = typename T::C2;
+  using R = typename T::R;
+  using V = typename T::V;
+  using A = typename T::A;
+  using Acc = typename T::Acc;
   constexpr int NL = K + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LatCtx<K, R> L;
+  LatCtx<K, MIXED> L;
   L.N = m.lat_N;
   L.logn = m.lat_logn;
-  L.tr = m.lat_tr;
-  L.ntj = (L.N + L.tr - 1) / L.tr;
+  L.NK = L.N / 2 + 1;
+  L.ntj = (L.N + kLatTJ - 1) / kLatTJ;
   L.pow2 = (L.N & (L.N - 1)) == 0;
+  L.grp = m.lat_grp;
   L.tw = reinterpret_cast<C2*>(smem_raw);
-  L.buf = L.tw + L.N;
-  L.buf2 = L.buf + m.lat_bufsz;
+  L.bufa = L.tw + L.N;
+  L.scr = L.bufa + m.lat_bufsz;
   L.X = reinterpret_cast<C2*>(m.lat_x);
   L.S = reinterpret_cast<const C2*>(m.lat_sinv);
+  V* p;
+  if constexpr (MIXED) {
+    L.lam = m.lam_df;
+    L.g = reinterpret_cast<float2*>(m.g);
+    L.r = reinterpret_cast<float2*>(m.r);
+    L.q = reinterpret_cast<float2*>(m.q);
+    L.z = m.zf;
+    p = reinterpret_cast<float2*>(m.pa);
+  } else {
+    L.lam = m.lam;
+    L.g = m.g;
+    L.r = m.r;
+    L.q = m.q;
+    L.z = m.z;
+    p = m.pa;
+  }
   for (int t = threadIdx.x; t < L.N; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
   __syncthreads();
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   GridBar* bar = m.bar;
   // g from both sides of every facet; warm-started lam
-  double gg[2] = {0.0, 0.0};
+  const A warm = A(a.warm_scale);
+  double ga = 0.0;
+  Acc g0 = acc_zero(Acc{});
   for (int f = gtid; f < nF; f += gsz) {
-    double gv[NL];
-    assemble_g<NL>(m, f, gv);
+    A gv[NL];
+    facet_g<NL>(m, f, gv);
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;
-      m.g[o] = gv[j];
-      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
-      gg[0] += gv[j] * gv[j];
+      stv(L.g + o, gv[j]);
+      stv(L.lam + o, a.warm_scale == 0.0 ? A(0) : warm * ldx(L.lam + o));
+      const double lead = lead_d(gv[j]);
+      ga = fma(lead, lead, ga);
     }
-    gg[1] += gv[0];
+    acc_add(g0, gv[0]);
   }
+  double gg[2] = {ga, acc_val(g0)};
   if (!grid_reduce<2>(m, 4, gg, bar)) return;
   const double c0 = gg[1] / double(nF);
-  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
+  const double gnorm0 = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
+  // PCG runs on the system scaled by sigma = 2^-e, e the exponent of the RMS entry of g
+  // (exact in any precision): residuals and dot products stay near 1 whatever the size
+  // of g, away from the FP32 exponent limits of the double-float form. r and p are
+  // scaled, lam is not: lam += (alpha / sigma) p.
+  const double sigma = gnorm0 > 0.0 ? ldexp(1.0, -ilogb(gnorm0 / sqrt(double(nF) * NL))) : 1.0;
+  const double gnorm = sigma * gnorm0;
   const double stop = a.rtol * gnorm;
   int it = 0;
   bool conv = false;
@@ -314,35 +482,40 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
   if (gnorm == 0.0) {
     for (int f = gtid; f < nF; f += gsz)
 #pragma unroll
-      for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
+      for (int j = 0; j < NL; ++j) stv(L.lam + size_t(f) * NL + j, A(0));
     conv = true;
   } else {
-    // r = g - S lam with the constant component of g removed
+    // r = sigma (g - S lam) with the constant component of g removed
+    const A c0a = A(c0), sg = A(sigma);
     for (int f = gtid; f < nF; f += gsz) {
-      double y[NL];
-      spmv64<NL>(m, f, m.lam, y);
+      A y[NL];
+      spmv_lat<NL, MIXED>(m, f, L.lam, y);
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         const size_t o = size_t(f) * NL + j;
-        const double gv = m.g[o] - (j == 0 ? c0 : 0.0);
-        m.g[o] = gv;
-        m.r[o] = gv - y[j];
+        const A gv = (j == 0) ? ldx(L.g + o) - c0a : ldx(L.g + o);
+        if (j == 0) stv(L.g + o, gv);
+        stv(L.r + o, sg * (gv - y[j]));
       }
     }
     if (!grid_sync(bar, m.stats)) return;
     // z = M r
-    double rr[1] = {0.0};
-    rows_forward<K, R>(m, L, false, 0.0, nullptr, &rr[0]);
+    Acc rra = acc_zero(Acc{});
+    rows_forward<K, MIXED>(L, false, A(0), A(0), p, rra);
+    double rr[1] = {acc_val(rra)};
     if (!grid_reduce<1>(m, 6, rr, bar)) return;
-    columns<K, R>(L);
+    columns<K, MIXED>(L);
     if (!grid_sync(bar, m.stats)) return;
-    double rz[2] = {0.0, 0.0};
-    rows_inverse<K, R>(m, L, false, &rz[0], &rz[1]);
+    Acc rza = acc_zero(Acc{}), rzo = acc_zero(Acc{});
+    rows_inverse<K, MIXED>(L, false, rza, rzo);
+    double rz[2] = {acc_val(rza), 0.0};
     if (!grid_reduce<2>(m, 1, rz, bar)) return;
     double rho = rz[0], rrv = rr[0];
     double beta = 0.0;
-    double* pold = m.pa;
-    double* pnew = m.pb;
+    // mixed form: double-float vectors carry 48 bits, so the residual reaches a rounding
+    // floor near 1e-14..1e-12 relative on large meshes; once an iteration no longer halves
+    // the residual and it is below floor_rtol, the solve is accepted there
+    const double floor_stop = a.floor_rtol * gnorm;
     for (;; ++it) {
       relres = sqrt(rrv) / gnorm;
       if (!isfinite(rrv) || !isfinite(rho)) {
@@ -354,28 +527,24 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
         break;
       }
       if (it >= a.maxit) break;
-      // p_new = z + beta p_old, q = S p_new
-      double pq[1] = {0.0};
+      // p = z + beta p, q = S p = S z + beta q (each facet updates only its own entries)
+      const A bt = A(beta);
+      Acc pqa = acc_zero(Acc{});
       for (int f = gtid; f < nF; f += gsz) {
-        int nb[5];
-        facet_nbrs<NL>(m, f, nb);
-        double xs[5][NL];
-#pragma unroll
-        for (int b = 0; b < 5; ++b)
-#pragma unroll
-          for (int j = 0; j < NL; ++j) {
-            const size_t o = size_t(nb[b]) * NL + j;
-            xs[b][j] = (it == 0) ? __ldcg(&m.z[o]) : __ldcg(&m.z[o]) + beta * __ldcg(&pold[o]);
-          }
-        double y[NL];
-        stencil_rows<NL, double>(m.st_blk + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
+        A y[NL];
+        spmv_lat<NL, MIXED>(m, f, L.z, y);
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
-          pnew[size_t(f) * NL + j] = xs[0][j];
-          m.q[size_t(f) * NL + j] = y[j];
-          pq[0] += xs[0][j] * y[j];
+          const size_t o = size_t(f) * NL + j;
+          const A zv = as_a(ldx(L.z + o));
+          const A pv = (it == 0) ? zv : zv + bt * ldx(p + o);
+          const A qv = (it == 0) ? y[j] : y[j] + bt * ldx(L.q + o);
+          stv(p + o, pv);
+          stv(L.q + o, qv);
+          mad(pqa, pv, qv);
         }
       }
+      double pq[1] = {acc_val(pqa)};
       if (!grid_reduce<1>(m, 0, pq, bar)) return;
       if (!(pq[0] > 0.0)) {
         if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
@@ -383,28 +552,31 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
       }
       const double alpha = rho / pq[0];
       // r -= alpha q, lam += alpha p, and the forward row pass of z = M r
-      rr[0] = 0.0;
-      rows_forward<K, R>(m, L, true, alpha, pnew, &rr[0]);
+      rra = acc_zero(Acc{});
+      rows_forward<K, MIXED>(L, true, A(alpha), A(alpha / sigma), p, rra);
+      rr[0] = acc_val(rra);
       if (!grid_reduce<1>(m, 6, rr, bar)) return;
+      const double rr_prev = rrv;
       rrv = rr[0];
-      if (sqrt(rrv) <= stop || !isfinite(rrv)) {
+      const bool stagnated = MIXED && sqrt(rrv) <= floor_stop && rrv > 0.25 * rr_prev;
+      if (sqrt(rrv) <= stop || !isfinite(rrv) || stagnated) {
         ++it;
         relres = sqrt(rrv) / gnorm;
         conv = isfinite(rrv);
         if (!conv && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
         break;
       }
-      columns<K, R>(L);
+      columns<K, MIXED>(L);
       if (!grid_sync(bar, m.stats)) return;
-      rz[0] = rz[1] = 0.0;
-      rows_inverse<K, R>(m, L, true, &rz[0], &rz[1]);
+      rza = acc_zero(Acc{});
+      rzo = acc_zero(Acc{});
+      rows_inverse<K, MIXED>(L, true, rza, rzo);
+      rz[0] = acc_val(rza);
+      rz[1] = acc_val(rzo);
       if (!grid_reduce<2>(m, 1, rz, bar)) return;
       // flexible (Polak-Ribiere) beta: the FP32 preconditioner is symmetric only up to rounding
       beta = (rz[0] - rz[1]) / rho;
       rho = rz[0];
-      double* t = pold;
-      pold = pnew;
-      pnew = t;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -419,50 +591,64 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_solve_lat(DevMesh m, SolveAr
   }
 }
 
-template <int K, typename R>
+template <int K, bool MIXED>
 const void* lat_fn() {
-  return (const void*)k_solve_lat<K, R>;
+  return (const void*)k_solve_lat<K, MIXED>;
 }
 
 const void* lattice_kernel(int k, int fp32) {
   switch (k * 2 + (fp32 ? 1 : 0)) {
-    case 2: return lat_fn<1, double>();
-    case 3: return lat_fn<1, float>();
-    case 4: return lat_fn<2, double>();
-    case 5: return lat_fn<2, float>();
-    case 6: return lat_fn<3, double>();
-    case 7: return lat_fn<3, float>();
+    case 2: return lat_fn<1, false>();
+    case 3: return lat_fn<1, true>();
+    case 4: return lat_fn<2, false>();
+    case 5: return lat_fn<2, true>();
+    case 6: return lat_fn<3, false>();
+    case 7: return lat_fn<3, true>();
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-int lattice_tile_rows(int k, int N, int fp32) {
-  const size_t cx = fp32 ? 8 : 16;
-  const size_t budget = 96 * 1024;
-  long long tr = (long long)(budget / (size_t(k + 1) * N * cx));
-  if (tr > 8) tr = 8;
-  if (tr < 1) tr = 1;
-  if (tr > N) tr = N;
-  return int(tr);
-}
-
 size_t lattice_buffer_elems(int k, int N, int fp32) {
-  const size_t C = 3 * (k + 1), rows_buf = size_t(k + 1) * lattice_tile_rows(k, N, fp32);
+  (void)fp32;
+  const size_t C = 3 * (k + 1), rows_buf = size_t(k + 1) * (kLatTJ / 2);
   return (C > rows_buf ? C : rows_buf) * N;
 }
 
-size_t lattice_smem_bytes(int k, int N, int fp32) {
+size_t lattice_smem_bytes(int k, int N, int fp32, int grp) {
   const size_t cx = fp32 ? 8 : 16;
-  const bool pow2 = (N & (N - 1)) == 0;
-  return (size_t(N) + (pow2 ? 1 : 2) * lattice_buffer_elems(k, N, fp32)) * cx;
+  return (size_t(N) + lattice_buffer_elems(k, N, fp32) + size_t(grp) * N) * cx;
 }
+
+// Rows per transform group: all of them if two blocks per SM still fit, else the most
+// that fit at two blocks per SM, else at one block per SM; 0 if not even one row fits.
+int lattice_group_rows(int k, int N, int fp32) {
+  int dev = 0, optin = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int rows = int(lattice_buffer_elems(k, N, fp32) / size_t(N));
+  const size_t two = size_t(per_sm) / 2 - 2048, one = size_t(optin) - 2048;
+  for (size_t budget : {two, one})
+    for (int g = rows; g >= 1; --g)
+      if (lattice_smem_bytes(k, N, fp32, g) <= budget) return g;
+  return 0;
+}
+
+size_t lattice_symbol_elems(int k, int N, int fp32) {
+  const size_t C = 3 * (k + 1);
+  return size_t(N / 2 + 1) * (fp32 ? C * (C + 1) / 2 : C * C) * N;
+}
+
+size_t lattice_spectrum_elems(int k, int N) { return size_t(3 * (k + 1)) * (N / 2 + 1) * N; }
 
 int lattice_blocks(int k, int N, int fp32) {
   const void* fn = lattice_kernel(k, fp32);
   if (!fn) return 0;
-  const size_t smem = lattice_smem_bytes(k, N, fp32);
+  const int grp = lattice_group_rows(k, N, fp32);
+  if (grp < 1) return 0;
+  const size_t smem = lattice_smem_bytes(k, N, fp32, grp);
   int per_sm = 0, dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   // the attribute is per kernel, shared by all meshes: allow the device maximum once,
@@ -485,7 +671,7 @@ int lattice_blocks(int k, int N, int fp32) {
     return 0;
   }
   if (per_sm < 1) return 0;
-  int nb = sms;   // one block per SM
+  int nb = sms * (per_sm < 2 ? per_sm : 2);
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
   return nb;
 }
@@ -499,7 +685,7 @@ cudaError_t launch_solve_lattice(const DevMesh& m, const SolveArgs& a, int nbloc
   SolveArgs aa = a;
   void* args[] = {&mm, &aa};
   return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kLatThreads), args,
-                                     lattice_smem_bytes(m.k, m.lat_N, fp32), s);
+                                     lattice_smem_bytes(m.k, m.lat_N, fp32, m.lat_grp), s);
 }
 
 }  // namespace dgdf

@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, Stag
 }
 
 // Recovery, mixed form: u_T = h_T - G_T^T lam_T (h = P f from the stage kernel) in
-// double-float; writes u in FP64 and, if out_df is given, its double-float twin.
+// double-float, with lam from the double-float solver (lam_is_df) or the FP64 one;
+// writes u in FP64 and, if out_df is given, its double-float twin.
 template <int K>
 __global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, float2* out_df) {
   using D = Dims<K>;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, floa
     const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
 #pragma unroll
     for (int mm = 0; mm < NL; ++mm) {
-      const dfl v(m.lam[size_t(f) * NL + mm]);
+      const dfl v = m.lam_is_df ? to_dfl(m.lam_df[size_t(f) * NL + mm]) : dfl(m.lam[size_t(f) * NL + mm]);
       lam[e * NL + mm] = (flip && (mm & 1)) ? v : -v;   // negated: u = h + sum (-G) lam
     }
   }
@@ -229,6 +230,11 @@ __global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, floa
 __global__ void k_to_dfl(const double* __restrict__ x, float2* __restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = to_float2(dfl(x[i]));
+}
+
+__global__ void k_to_double(const float2* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = to_double(x[i]);
 }
 
 inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
@@ -260,6 +266,14 @@ cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t 
   long long nb = (n + 255) / 256;
   if (nb > 4096) nb = 4096;
   k_to_dfl<<<int(nb), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_double(const float2* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_to_double<<<int(nb), 256, 0, s>>>(x, y, n);
   return cudaGetLastError();
 }
 

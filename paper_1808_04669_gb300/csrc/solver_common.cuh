@@ -94,22 +94,13 @@ __device__ __forceinline__ void block_apply(const R* __restrict__ B, const R (&x
 // traverses the facet backwards). Mixed form: the sides' double-float values are
 // summed in double-float and rounded to FP64 once.
 template <int NL>
+__device__ __forceinline__ void assemble_g_df(const DevMesh& m, int f, dfl (&gv)[NL]);
+
+template <int NL>
 __device__ __forceinline__ void assemble_g(const DevMesh& m, int f, double (&gv)[NL]) {
   if (m.elem_df) {
     dfl acc[NL];
-#pragma unroll
-    for (int j = 0; j < NL; ++j) acc[j] = dfl(0);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
-      const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
-      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
-#pragma unroll
-      for (int j = 0; j < NL; ++j) {
-        const dfl v = to_dfl(m.gl_df[size_t(t) * 3 * NL + e * NL + j]);
-        acc[j] += (flip && (j & 1)) ? -v : v;
-      }
-    }
+    assemble_g_df<NL>(m, f, acc);
 #pragma unroll
     for (int j = 0; j < NL; ++j) gv[j] = to_double(acc[j]);
     return;
@@ -124,6 +115,24 @@ __device__ __forceinline__ void assemble_g(const DevMesh& m, int f, double (&gv)
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const double v = m.gl[size_t(t) * 3 * NL + e * NL + j];
+      gv[j] += (flip && (j & 1)) ? -v : v;
+    }
+  }
+}
+
+// The same in double-float (mixed form), from the double-float condensation outputs.
+template <int NL>
+__device__ __forceinline__ void assemble_g_df(const DevMesh& m, int f, dfl (&gv)[NL]) {
+#pragma unroll
+  for (int j = 0; j < NL; ++j) gv[j] = dfl(0);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+    const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
+    const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const dfl v = to_dfl(m.gl_df[size_t(t) * 3 * NL + e * NL + j]);
       gv[j] += (flip && (j & 1)) ? -v : v;
     }
   }
