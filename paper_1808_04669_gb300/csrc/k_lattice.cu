@@ -108,6 +108,7 @@ __device__ C2* fft_stockham(C2* a, C2* b, int rows, int logn, const C2* tw, bool
   const int n = 1 << logn, hn = n >> 1;
   for (int s = 0; s < logn; ++s) {
     const int l = 1 << s;
+#pragma unroll 4
     for (int e = threadIdx.x; e < rows * hn; e += blockDim.x) {
       const int row = e >> (logn - 1), j = e & (hn - 1);
       const C2* x = a + row * n;
@@ -216,6 +217,7 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
     const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * kLatTJ;
     const int rows = min(kLatTJ, N - j0), npair = (rows + 1) >> 1;
     const size_t base = (size_t(ty) * N + j0) * N * NL;
+#pragma unroll 4
     for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {   // one facet (row r_, column i)
       const int r_ = e / N, i = e - r_ * N;
 #pragma unroll
@@ -267,6 +269,7 @@ __device__ void columns(const LatCtx<K, MIXED>& L) {
   constexpr int NP = LatCtx<K, MIXED>::NP;
   const int N = L.N, NK = L.NK;
   for (int ki = blockIdx.x; ki < NK; ki += gridDim.x) {
+#pragma unroll 12
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
       const int c = e / N, j = e - c * N;
       L.bufa[e] = __ldcg(&L.X[(size_t(c) * NK + ki) * N + j]);
@@ -329,6 +332,7 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * kLatTJ;
     const int rows = min(kLatTJ, N - j0), npair = (rows + 1) >> 1;
+#pragma unroll 8
     for (int e = threadIdx.x; e < npair * NK * NL; e += blockDim.x) {
       const int pr = e % npair, rest = e / npair;
       const int ki = rest % NK, mm = rest / NK;
@@ -343,6 +347,7 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
     xform(L, L.bufa, npair * NL, true);
     const C2* res = L.bufa;
     const size_t base = (size_t(ty) * N + j0) * N * NL;
+#pragma unroll 4
     for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
       const int r_ = e / N, i = e - r_ * N;
 #pragma unroll
@@ -405,6 +410,87 @@ __device__ __forceinline__ void facet_g(const DevMesh& m, int f, dfl (&gv)[NL]) 
   assemble_g_df<NL>(m, f, gv);
 }
 
+// ---- grid reductions of the per-thread partials, in the accumulator's own arithmetic
+// (FP32 TwoSum pairs in the mixed form: no FP64 pipe): warps, then warp 0 for the block;
+// the block partial goes to m.red (a dacc pair occupies the 8 bytes of a double slot);
+// after the barrier every thread loads at most a couple of block partials, and the same
+// warp / block steps give the grid sum, broadcast through shared memory. Fixed order:
+// bitwise reproducible and identical in every block.
+__device__ __forceinline__ double acc_combine(double a, double b) { return a + b; }
+__device__ __forceinline__ dacc acc_combine(dacc a, dacc b) {
+  float s, t;
+  two_sum(a.s, b.s, s, t);
+  return dacc{s, a.c + b.c + t};
+}
+__device__ __forceinline__ double shfl_acc(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dacc shfl_acc(dacc v, int o) {
+  return dacc{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+}
+template <typename Acc>
+__device__ __forceinline__ Acc warp_acc(Acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = acc_combine(v, shfl_acc(v, o));
+  return v;
+}
+__device__ __forceinline__ void red_store(double* p, double v) { *p = v; }
+__device__ __forceinline__ void red_store(double* p, dacc v) { *reinterpret_cast<float2*>(p) = make_float2(v.s, v.c); }
+__device__ __forceinline__ double red_load(const double* p, double) { return __ldcg(p); }
+__device__ __forceinline__ dacc red_load(const double* p, dacc) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return dacc{v.x, v.y};
+}
+
+// Block sum of v in every thread (all threads of the block call it).
+template <int N, typename Acc>
+__device__ __forceinline__ void block_acc(Acc (&v)[N]) {
+  __shared__ Acc part[kLatThreads / 32][N];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const Acc ws = warp_acc(v[i]);
+    if (l == 0) part[w][i] = ws;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Acc b = (l < kLatThreads / 32) ? part[l][i] : acc_zero(Acc{});
+    v[i] = warp_acc(b);
+  }
+  __syncthreads();
+}
+
+template <int N, typename Acc>
+__device__ bool lat_reduce(const DevMesh& m, int slot0, const Acc (&v)[N], GridBar* bar, double (&out)[N]) {
+  Acc b[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) b[i] = v[i];
+  block_acc<N>(b);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < N; ++i) red_store(&m.red[size_t(slot0 + i) * kMaxSolverBlocks + blockIdx.x], b[i]);
+  if (!grid_sync(bar, m.stats)) return false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Acc gsum = acc_zero(Acc{});
+    for (int k = threadIdx.x; k < gridDim.x; k += blockDim.x)
+      gsum = acc_combine(gsum, red_load(&m.red[size_t(slot0 + i) * kMaxSolverBlocks + k], Acc{}));
+    b[i] = gsum;
+  }
+  block_acc<N>(b);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[i] = acc_val(b[i]);
+  return true;
+}
+
+// Scalars of one PCG step, computed by thread 0 of each block (identically in every
+// block) and broadcast through shared memory.
+template <typename A>
+struct LatScal {
+  A alpha, alpha_lam, beta;
+  int done, conv;
+  double relres;
+};
+
 template <int K, bool MIXED>
 __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveArgs a) {
   using T = LatT<MIXED>;
@@ -415,6 +501,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   using Acc = typename T::Acc;
   constexpr int NL = K + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ LatScal<A> sc;
   LatCtx<K, MIXED> L;
   L.N = m.lat_N;
   L.logn = m.lat_logn;
@@ -452,6 +539,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   const A warm = A(a.warm_scale);
   double ga = 0.0;
   Acc g0 = acc_zero(Acc{});
+#pragma unroll 2
   for (int f = gtid; f < nF; f += gsz) {
     A gv[NL];
     facet_g<NL>(m, f, gv);
@@ -465,8 +553,11 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     }
     acc_add(g0, gv[0]);
   }
-  double gg[2] = {ga, acc_val(g0)};
-  if (!grid_reduce<2>(m, 4, gg, bar)) return;
+  double gg[2];
+  {
+    const double gv2[2] = {ga, acc_val(g0)};
+    if (!lat_reduce<2>(m, 4, gv2, bar, gg)) return;
+  }
   const double c0 = gg[1] / double(nF);
   const double gnorm0 = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
   // PCG runs on the system scaled by sigma = 2^-e, e the exponent of the RMS entry of g
@@ -475,7 +566,11 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   // scaled, lam is not: lam += (alpha / sigma) p.
   const double sigma = gnorm0 > 0.0 ? ldexp(1.0, -ilogb(gnorm0 / sqrt(double(nF) * NL))) : 1.0;
   const double gnorm = sigma * gnorm0;
-  const double stop = a.rtol * gnorm;
+  const double stop2 = (a.rtol * gnorm) * (a.rtol * gnorm);
+  // mixed form: double-float vectors carry 48 bits, so the residual reaches a rounding
+  // floor near 1e-14..1e-12 relative on large meshes; once an iteration no longer halves
+  // the residual and it is below floor_rtol, the solve is accepted there
+  const double floor2 = (a.floor_rtol * gnorm) * (a.floor_rtol * gnorm);
   int it = 0;
   bool conv = false;
   double relres = 0.0;
@@ -487,6 +582,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   } else {
     // r = sigma (g - S lam) with the constant component of g removed
     const A c0a = A(c0), sg = A(sigma);
+#pragma unroll 2
     for (int f = gtid; f < nF; f += gsz) {
       A y[NL];
       spmv_lat<NL, MIXED>(m, f, L.lam, y);
@@ -500,36 +596,49 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     }
     if (!grid_sync(bar, m.stats)) return;
     // z = M r
-    Acc rra = acc_zero(Acc{});
-    rows_forward<K, MIXED>(L, false, A(0), A(0), p, rra);
-    double rr[1] = {acc_val(rra)};
-    if (!grid_reduce<1>(m, 6, rr, bar)) return;
+    Acc rra[1] = {acc_zero(Acc{})};
+    rows_forward<K, MIXED>(L, false, A(0), A(0), p, rra[0]);
+    double rr[1];
+    if (!lat_reduce<1>(m, 6, rra, bar, rr)) return;
     columns<K, MIXED>(L);
     if (!grid_sync(bar, m.stats)) return;
-    Acc rza = acc_zero(Acc{}), rzo = acc_zero(Acc{});
-    rows_inverse<K, MIXED>(L, false, rza, rzo);
-    double rz[2] = {acc_val(rza), 0.0};
-    if (!grid_reduce<2>(m, 1, rz, bar)) return;
+    Acc rza[2] = {acc_zero(Acc{}), acc_zero(Acc{})};
+    rows_inverse<K, MIXED>(L, false, rza[0], rza[1]);
+    double rz[2];
+    {
+      const Acc rz1[1] = {rza[0]};
+      double rzt[1];
+      if (!lat_reduce<1>(m, 1, rz1, bar, rzt)) return;
+      rz[0] = rzt[0];
+    }
     double rho = rz[0], rrv = rr[0];
     double beta = 0.0;
-    // mixed form: double-float vectors carry 48 bits, so the residual reaches a rounding
-    // floor near 1e-14..1e-12 relative on large meshes; once an iteration no longer halves
-    // the residual and it is below floor_rtol, the solve is accepted there
-    const double floor_stop = a.floor_rtol * gnorm;
     for (;; ++it) {
-      relres = sqrt(rrv) / gnorm;
-      if (!isfinite(rrv) || !isfinite(rho)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+      // convergence and the scalars of this step, once per block
+      if (threadIdx.x == 0) {
+        sc.done = 0;
+        sc.conv = 0;
+        sc.relres = sqrt(rrv) / gnorm;
+        if (!isfinite(rrv) || !isfinite(rho)) {
+          if (blockIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+          sc.done = 1;
+        } else if (rrv <= stop2) {
+          sc.done = sc.conv = 1;
+        } else if (it >= a.maxit) {
+          sc.done = 1;
+        }
+        sc.beta = A(beta);
+      }
+      __syncthreads();
+      relres = sc.relres;
+      if (sc.done) {
+        conv = sc.conv != 0;
         break;
       }
-      if (sqrt(rrv) <= stop) {
-        conv = true;
-        break;
-      }
-      if (it >= a.maxit) break;
       // p = z + beta p, q = S p = S z + beta q (each facet updates only its own entries)
-      const A bt = A(beta);
-      Acc pqa = acc_zero(Acc{});
+      const A bt = sc.beta;
+      Acc pqa[1] = {acc_zero(Acc{})};
+#pragma unroll 2
       for (int f = gtid; f < nF; f += gsz) {
         A y[NL];
         spmv_lat<NL, MIXED>(m, f, L.z, y);
@@ -541,39 +650,54 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
           const A qv = (it == 0) ? y[j] : y[j] + bt * ldx(L.q + o);
           stv(p + o, pv);
           stv(L.q + o, qv);
-          mad(pqa, pv, qv);
+          mad(pqa[0], pv, qv);
         }
       }
-      double pq[1] = {acc_val(pqa)};
-      if (!grid_reduce<1>(m, 0, pq, bar)) return;
-      if (!(pq[0] > 0.0)) {
-        if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
-        break;
+      double pq[1];
+      if (!lat_reduce<1>(m, 0, pqa, bar, pq)) return;
+      if (threadIdx.x == 0) {
+        sc.done = 0;
+        if (!(pq[0] > 0.0)) {
+          if (!isfinite(pq[0]) && blockIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+          sc.done = 1;
+        } else {
+          const double alpha = rho / pq[0];
+          sc.alpha = A(alpha);
+          sc.alpha_lam = A(alpha / sigma);
+        }
       }
-      const double alpha = rho / pq[0];
+      __syncthreads();
+      if (sc.done) break;
       // r -= alpha q, lam += alpha p, and the forward row pass of z = M r
-      rra = acc_zero(Acc{});
-      rows_forward<K, MIXED>(L, true, A(alpha), A(alpha / sigma), p, rra);
-      rr[0] = acc_val(rra);
-      if (!grid_reduce<1>(m, 6, rr, bar)) return;
+      rra[0] = acc_zero(Acc{});
+      rows_forward<K, MIXED>(L, true, sc.alpha, sc.alpha_lam, p, rra[0]);
+      if (!lat_reduce<1>(m, 6, rra, bar, rr)) return;
       const double rr_prev = rrv;
       rrv = rr[0];
-      const bool stagnated = MIXED && sqrt(rrv) <= floor_stop && rrv > 0.25 * rr_prev;
-      if (sqrt(rrv) <= stop || !isfinite(rrv) || stagnated) {
+      if (threadIdx.x == 0) {
+        sc.done = 0;
+        sc.conv = 0;
+        const bool stagnated = MIXED && rrv <= floor2 && rrv > 0.25 * rr_prev;
+        if (rrv <= stop2 || !isfinite(rrv) || stagnated) {
+          sc.done = 1;
+          sc.relres = sqrt(rrv) / gnorm;
+          sc.conv = isfinite(rrv) ? 1 : 0;
+          if (!sc.conv && blockIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        }
+      }
+      __syncthreads();
+      if (sc.done) {
         ++it;
-        relres = sqrt(rrv) / gnorm;
-        conv = isfinite(rrv);
-        if (!conv && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        relres = sc.relres;
+        conv = sc.conv != 0;
         break;
       }
       columns<K, MIXED>(L);
       if (!grid_sync(bar, m.stats)) return;
-      rza = acc_zero(Acc{});
-      rzo = acc_zero(Acc{});
-      rows_inverse<K, MIXED>(L, true, rza, rzo);
-      rz[0] = acc_val(rza);
-      rz[1] = acc_val(rzo);
-      if (!grid_reduce<2>(m, 1, rz, bar)) return;
+      rza[0] = acc_zero(Acc{});
+      rza[1] = acc_zero(Acc{});
+      rows_inverse<K, MIXED>(L, true, rza[0], rza[1]);
+      if (!lat_reduce<2>(m, 1, rza, bar, rz)) return;
       // flexible (Polak-Ribiere) beta: the FP32 preconditioner is symmetric only up to rounding
       beta = (rz[0] - rz[1]) / rho;
       rho = rz[0];
