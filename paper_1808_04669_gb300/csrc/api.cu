@@ -405,10 +405,15 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       float* xp = nullptr;
       if ((rc = dalloc(M, &xp, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
       d.lat_x = xp;
-      // the mixed lattice solver keeps its multipliers in double-float
-      if ((rc = dalloc(M, &d.lam_df, nF * nl)) || (rc = upload(M, &d.st_blk_df, to_dfloat(hm.stencil_blocks))))
+      // the mixed lattice solver keeps its multipliers and work vectors in double-float,
+      // facet stride padded to an aligned access (4 for k = 2)
+      d.lat_vs = nl == 3 ? 4 : nl;
+      const size_t nv = nF * size_t(d.lat_vs);
+      if ((rc = dalloc(M, &d.lam_df, nv)) || (rc = dalloc(M, &d.lv_g, nv)) || (rc = dalloc(M, &d.lv_r, nv)) ||
+          (rc = dalloc(M, &d.lv_q, nv)) || (rc = dalloc(M, &d.lv_p, nv)) || (rc = dalloc(M, &d.lv_z, nv)) ||
+          (rc = upload(M, &d.st_blk_df, to_dfloat(hm.stencil_blocks))))
         return cleanup(rc);
-      if (cudaMemsetAsync(d.lam_df, 0, nF * nl * sizeof(float2), M->stream) != cudaSuccess)
+      if (cudaMemsetAsync(d.lam_df, 0, nv * sizeof(float2), M->stream) != cudaSuccess)
         return cleanup(fail(DG_ERR_CUDA, "initialise the double-float multipliers"));
       d.lam_is_df = 1;
     } else {
@@ -882,8 +887,9 @@ int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) 
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
   if ((rc = solve(M, 0.0))) return rc;
   if (M->dm.lam_is_df) {   // the pressure kernels read the multipliers in FP64
-    const long long n = (long long)M->dm.n_facet * M->dm.nl;
-    if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_to_double(M->dm.lam_df, M->dm.lam, n, M->stream); })))
+    if ((rc = launch(M, KC_PRESSURE, [&] {
+           return dgdf::launch_to_double(M->dm.lam_df, M->dm.lat_vs, M->dm.lam, M->dm.nl, M->dm.n_facet, M->stream);
+         })))
       return rc;
   }
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_pressure(M->dm, M->wbuf, M->stream); }))) return rc;

@@ -70,7 +70,11 @@ struct DevMesh {
   float2 *u_df, *ustage_df, *h_df, *gl_df;
   double *lam, *g, *r, *z, *pa, *pb, *q;   // [n_facet][nl]
   float *rf, *zf, *paf, *pbf, *qf, *xf;    // FP32 inner-solve vectors
-  float2* lam_df;                     // mixed lattice solver: the multipliers in double-float
+  float2* lam_df;                     // mixed lattice solver: the multipliers in double-float,
+                                      // facet stride lat_vs
+  float2 *lv_g, *lv_r, *lv_q, *lv_p;  // mixed lattice solver vectors [n_facet][lat_vs]
+  float* lv_z;
+  int lat_vs;                         // facet stride of those vectors (k = 2: padded to 4)
   int lam_is_df;                      // 1: the last solve left lam in lam_df (recovery reads it)
   double *red;                        // reduction scratch [kRedSlots][max_blocks]
   // lattice (translation-invariant split-square) solver data
@@ -125,7 +129,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s);
-cudaError_t launch_to_double(const float2* x, double* y, long long n, cudaStream_t s);
+cudaError_t launch_to_double(const float2* x, int sx, double* y, int ny, long long nrow, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);
 cudaError_t launch_pressure_lattice(const DevMesh& m, const double* w, double* pe, double* pf, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_t s);

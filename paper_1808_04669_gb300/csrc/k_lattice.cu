@@ -15,9 +15,11 @@
 //   columns: per ki, FFT along j, multiply by S^(kappa)^+ (upper triangle stored,
 //            the lower one is its conjugate), inverse FFT along j
 //   rows   : inverse FFT along i of two rows packed the same way (scaled 1/N^2)
-// with a grid barrier between the passes. Transforms run in shared memory:
-// self-sorting (Stockham) radix-2 FFTs when N is a power of two, a direct DFT
-// otherwise. One persistent cooperative kernel per solve, two blocks per SM.
+// with a grid barrier between the passes. Transforms run in shared memory: for N a
+// power of two up to 1024 (FP32) / 256 (FP64) a two-pass FFT whose radix-sqrt(N)
+// DFTs run in registers, self-sorting (Stockham) radix-2 passes for larger powers of
+// two, a direct DFT otherwise. One persistent cooperative kernel per solve, two blocks
+// per SM.
 #include "device.cuh"
 #include "dfloat.cuh"
 #include "kcommon.cuh"
@@ -129,6 +131,87 @@ __device__ C2* fft_stockham(C2* a, C2* b, int rows, int logn, const C2* tw, bool
   return a;
 }
 
+// In-register DFT of size R (a power of two), natural order in and out: radix-2
+// decimation in frequency with twiddles w^j = tw[j tstep] (w = exp(-+2 pi i / R)),
+// then the bit-reversal permutation of the registers (resolved at compile time).
+template <int R, typename C2>
+__device__ __forceinline__ void reg_dft(C2 (&v)[R], const C2* tw, int tstep, bool inverse) {
+#pragma unroll
+  for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int blk = 0; blk < R; blk += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const C2 a = v[blk + j], b = v[blk + j + half];
+        v[blk + j] = cadd(a, b);
+        const C2 d = csub(a, b);
+        if (j == 0) {
+          v[blk + j + half] = d;
+        } else {
+          C2 w = tw[j * (R / (2 * half)) * tstep];
+          if (inverse) w.y = -w.y;
+          v[blk + j + half] = cmul(d, w);
+        }
+      }
+    }
+  }
+  C2 t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int b = 0;
+#pragma unroll
+    for (int q = 1; q < R; q <<= 1) b = (b << 1) | ((i / q) & 1);
+    t[i] = v[b];
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// Two-pass ("four-step") FFT of `rows` rows of length N = R1 R2 held in a (natural
+// order, in place), through the scratch s (rows of stride R2 (R1 + 1), padded against
+// bank conflicts): x[n1 + R1 n2] -> DFT over n2 (thread per (row, n1)) -> twiddle
+// w_N^(n1 k2) -> DFT over n1 (thread per (row, k2)) -> X[k2 + R2 k1].
+template <int R1, int R2, typename C2>
+__device__ void fft_four_step(C2* a, C2* s, int rows, const C2* tw, bool inverse) {
+  constexpr int N = R1 * R2, SR = R2 * (R1 + 1);
+  for (int t = threadIdx.x; t < rows * R1; t += blockDim.x) {
+    const int row = t / R1, n1 = t - row * R1;
+    C2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = a[row * N + n1 + R1 * n2];
+    reg_dft<R2>(v, tw, R1, inverse);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      C2 w = tw[n1 * k2];
+      if (inverse) w.y = -w.y;
+      s[row * SR + k2 * (R1 + 1) + n1] = k2 == 0 ? v[k2] : cmul(v[k2], w);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < rows * R2; t += blockDim.x) {
+    const int row = t / R2, k2 = t - row * R2;
+    C2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[row * SR + k2 * (R1 + 1) + n1];
+    reg_dft<R1>(v, tw, R2, inverse);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[row * N + k2 + R2 * k1] = v[k1];
+  }
+  __syncthreads();
+}
+
+// Largest log2 N handled by the two-pass FFT (register budget of one radix-R pass).
+template <typename C2>
+struct FourStepMax;
+template <>
+struct FourStepMax<float2> {
+  static constexpr int logn = 10;
+};
+template <>
+struct FourStepMax<double2> {
+  static constexpr int logn = 8;
+};
+
 // Direct DFT of `rows` rows of length n (any n): out[r][k] = sum_t in[r][t] w^(t k mod n),
 // w[m] = exp(-2 pi i m / n) (conjugated for the inverse). Natural order in and out.
 template <typename C2>
@@ -155,15 +238,18 @@ struct LatCtx {
   using T = LatT<MIXED>;
   using C2 = typename T::C2;
   static constexpr int NL = K + 1, C = 3 * NL;
+  // facet stride of the solver vectors: padded to 4 for k = 2 in the mixed form, so that
+  // every facet's values are one aligned 16- or 32-byte access
+  static constexpr int VS = (MIXED && NL == 3) ? 4 : NL;
   // stored entries per wavenumber: the packed upper triangle in FP32 (its rounding hides the
   // host inverse's departure from Hermitian), the full block in FP64
   static constexpr int NP = MIXED ? C * (C + 1) / 2 : C * C;
   int N, logn, NK, ntj;   // NK = N/2 + 1 wavenumbers ki; ntj row tiles per facet type
   int grp;                // rows transformed at a time (the scratch holds grp rows)
-  bool pow2;              // Stockham FFT (N a power of two) or direct DFT
+  bool pow2;              // FFT (N a power of two) or direct DFT
   C2* tw;                 // [N] exp(-2 pi i t / N)
   C2* bufa;               // transform data, max(C, 2(k+1)) rows of N
-  C2* scr;                // scratch, grp rows of N
+  C2* scr;                // scratch, grp rows of lattice_scratch_row(N)
   C2* X;                  // [C][NK][N] spectrum: half along i, full along j (then along kj)
   const C2* S;            // [NK][NP][N] S^(kappa)^+ (packed upper triangle or full), kj fastest
   // vectors, facet-major [n_facet][NL] in lattice order
@@ -172,8 +258,9 @@ struct LatCtx {
 };
 
 // Forward or inverse transform, in place, of `rows` natural-order rows held in a: groups
-// of L.grp rows go through the scratch buffer (the Stockham passes and the direct DFT
-// are out of place; a result left in the scratch is copied back).
+// of L.grp rows go through the scratch buffer. Powers of two up to FourStepMax: the
+// two-pass FFT; larger powers of two: Stockham passes; other N: the direct DFT (both
+// out of place; a result left in the scratch is copied back).
 template <int K, bool MIXED>
 __device__ void xform(const LatCtx<K, MIXED>& L, typename LatT<MIXED>::C2* a, int rows, bool inverse) {
   using C2 = typename LatT<MIXED>::C2;
@@ -181,6 +268,26 @@ __device__ void xform(const LatCtx<K, MIXED>& L, typename LatT<MIXED>::C2* a, in
   for (int r0 = 0; r0 < rows; r0 += L.grp) {
     const int gr = min(L.grp, rows - r0);
     C2* d = a + size_t(r0) * N;
+    if (L.pow2 && L.logn <= FourStepMax<C2>::logn) {
+      switch (L.logn) {
+        case 0: break;
+        case 1: fft_four_step<2, 1>(d, L.scr, gr, L.tw, inverse); break;
+        case 2: fft_four_step<2, 2>(d, L.scr, gr, L.tw, inverse); break;
+        case 3: fft_four_step<4, 2>(d, L.scr, gr, L.tw, inverse); break;
+        case 4: fft_four_step<4, 4>(d, L.scr, gr, L.tw, inverse); break;
+        case 5: fft_four_step<8, 4>(d, L.scr, gr, L.tw, inverse); break;
+        case 6: fft_four_step<8, 8>(d, L.scr, gr, L.tw, inverse); break;
+        case 7: fft_four_step<16, 8>(d, L.scr, gr, L.tw, inverse); break;
+        case 8: fft_four_step<16, 16>(d, L.scr, gr, L.tw, inverse); break;
+        default:
+          if constexpr (FourStepMax<C2>::logn >= 10) {
+            if (L.logn == 9) fft_four_step<32, 16>(d, L.scr, gr, L.tw, inverse);
+            else fft_four_step<32, 32>(d, L.scr, gr, L.tw, inverse);
+          }
+          break;
+      }
+      continue;
+    }
     const C2* res;
     if (L.pow2) {
       res = fft_stockham(d, L.scr, gr, L.logn, L.tw, inverse);
@@ -195,9 +302,94 @@ __device__ void xform(const LatCtx<K, MIXED>& L, typename LatT<MIXED>::C2* a, in
   }
 }
 
+// ---- one facet's NL values of a solver vector (facet stride VS), as aligned vector
+// accesses where the stride allows (coherent L2 loads: the data was written by other
+// blocks before the last grid barrier)
+template <int NL, int VS>
+__device__ __forceinline__ void ldf(const float2* p, dfl (&v)[NL]) {
+  if constexpr (VS % 2 == 0) {
+#pragma unroll
+    for (int h = 0; h < VS / 2; ++h) {
+      const float4 w = __ldcg(reinterpret_cast<const float4*>(p) + h);
+      if (2 * h < NL) v[2 * h] = dfl(w.x, w.y);
+      if (2 * h + 1 < NL) v[2 * h + 1] = dfl(w.z, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) v[j] = to_dfl(__ldcg(p + j));
+  }
+}
+template <int NL, int VS>
+__device__ __forceinline__ void stf(float2* p, const dfl (&v)[NL]) {
+  if constexpr (VS % 2 == 0) {
+#pragma unroll
+    for (int h = 0; h < VS / 2; ++h) {
+      const dfl a = (2 * h < NL) ? v[2 * h] : dfl(0), b = (2 * h + 1 < NL) ? v[2 * h + 1] : dfl(0);
+      reinterpret_cast<float4*>(p)[h] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) p[j] = to_float2(v[j]);
+  }
+}
+template <int NL, int VS>
+__device__ __forceinline__ void ldf(const float* p, float (&v)[NL]) {
+  if constexpr (VS == 4) {
+    const float4 w = __ldcg(reinterpret_cast<const float4*>(p));
+    const float t[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int j = 0; j < NL; ++j) v[j] = t[j];
+  } else if constexpr (VS == 2) {
+    const float2 w = __ldcg(reinterpret_cast<const float2*>(p));
+    v[0] = w.x;
+    v[NL - 1] = w.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) v[j] = __ldcg(p + j);
+  }
+}
+template <int NL, int VS>
+__device__ __forceinline__ void stf(float* p, const float (&v)[NL]) {
+  if constexpr (VS == 4) {
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NL; ++j) t[j] = v[j];
+    *reinterpret_cast<float4*>(p) = make_float4(t[0], t[1], t[2], t[3]);
+  } else if constexpr (VS == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[NL - 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) p[j] = v[j];
+  }
+}
+template <int NL, int VS>
+__device__ __forceinline__ void ldf(const double* p, double (&v)[NL]) {
+  if constexpr (VS % 2 == 0) {
+#pragma unroll
+    for (int h = 0; h < VS / 2; ++h) {
+      const double2 w = __ldcg(reinterpret_cast<const double2*>(p) + h);
+      if (2 * h < NL) v[2 * h] = w.x;
+      if (2 * h + 1 < NL) v[2 * h + 1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) v[j] = __ldcg(p + j);
+  }
+}
+template <int NL, int VS>
+__device__ __forceinline__ void stf(double* p, const double (&v)[NL]) {
+  if constexpr (VS % 2 == 0) {
+#pragma unroll
+    for (int h = 0; h < VS / 2; ++h) reinterpret_cast<double2*>(p)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) p[j] = v[j];
+  }
+}
+
 // Facets are numbered (type, j, i) on a lattice mesh, so a tile of kLatTJ rows of one
 // facet type with all k+1 modes is one contiguous range of the facet-major vectors:
-// DOF index ((type N + j) N + i)(k+1) + m.
+// DOF index ((type N + j) N + i) VS + m.
 
 // Row pass, forward: per tile read r (first updating r -= alpha q, lam += alpha_lam p
 // when `update`), accumulate r.r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per
@@ -210,29 +402,38 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
   using C2 = typename T::C2;
   using R = typename T::R;
   using A = typename T::A;
-  constexpr int NL = K + 1;
+  constexpr int NL = K + 1, VS = LatCtx<K, MIXED>::VS;
   const int N = L.N, NK = L.NK;
   const int ntiles = 3 * L.ntj;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ty = tile / L.ntj, j0 = (tile - ty * L.ntj) * kLatTJ;
     const int rows = min(kLatTJ, N - j0), npair = (rows + 1) >> 1;
-    const size_t base = (size_t(ty) * N + j0) * N * NL;
+    const size_t base = (size_t(ty) * N + j0) * N * VS;
 #pragma unroll 4
     for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {   // one facet (row r_, column i)
       const int r_ = e / N, i = e - r_ * N;
+      const size_t o = base + size_t(e) * VS;
+      A rv[NL];
+      ldf<NL, VS>(L.r + o, rv);
+      if (update) {
+        A qv[NL], lv[NL], pv[NL];
+        ldf<NL, VS>(L.q + o, qv);
+        ldf<NL, VS>(L.lam + o, lv);
+        ldf<NL, VS>(p + o, pv);
+#pragma unroll
+        for (int mm = 0; mm < NL; ++mm) {
+          rv[mm] = rv[mm] - alpha * qv[mm];
+          lv[mm] = lv[mm] + alpha_lam * pv[mm];
+        }
+        stf<NL, VS>(L.r + o, rv);
+        stf<NL, VS>(L.lam + o, lv);
+      }
 #pragma unroll
       for (int mm = 0; mm < NL; ++mm) {
-        const size_t o = base + size_t(e) * NL + mm;
-        A rv = ldv(L.r + o);
-        if (update) {
-          rv = rv - alpha * ldv(L.q + o);
-          stv(L.r + o, rv);
-          stv(L.lam + o, ldv(L.lam + o) + alpha_lam * ldv(p + o));
-        }
-        mad(rr, rv, rv);
+        mad(rr, rv[mm], rv[mm]);
         C2* slot = &L.bufa[((r_ >> 1) * NL + mm) * N + i];
-        if (r_ & 1) slot->y = fft_in(rv);
-        else slot->x = fft_in(rv);
+        if (r_ & 1) slot->y = fft_in(rv[mm]);
+        else slot->x = fft_in(rv[mm]);
       }
     }
     if (rows & 1)   // the last pair has no odd row
@@ -325,7 +526,7 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
   using C2 = typename T::C2;
   using R = typename T::R;
   using Z = typename T::Z;
-  constexpr int NL = K + 1;
+  constexpr int NL = K + 1, VS = LatCtx<K, MIXED>::VS;
   const int N = L.N, NK = L.NK;
   const R scale = R(1.0 / (double(N) * double(N)));
   const int ntiles = 3 * L.ntj;
@@ -346,20 +547,23 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
     __syncthreads();
     xform(L, L.bufa, npair * NL, true);
     const C2* res = L.bufa;
-    const size_t base = (size_t(ty) * N + j0) * N * NL;
+    const size_t base = (size_t(ty) * N + j0) * N * VS;
 #pragma unroll 4
     for (int e = threadIdx.x; e < rows * N; e += blockDim.x) {
       const int r_ = e / N, i = e - r_ * N;
+      const size_t o = base + size_t(e) * VS;
+      typename T::A rv[NL];
+      Z zv[NL], zo[NL];
+      ldf<NL, VS>(L.r + o, rv);
+      if (with_old) ldf<NL, VS>(L.z + o, zo);
 #pragma unroll
       for (int mm = 0; mm < NL; ++mm) {
-        const size_t o = base + size_t(e) * NL + mm;
         const C2 v = res[((r_ >> 1) * NL + mm) * N + i];
-        const Z zv = Z((r_ & 1) ? v.y : v.x) * Z(scale);
-        const auto rv = ldv(L.r + o);
-        if (with_old) mad(rzo, rv, ldz(L.z + o));
-        mad(rz, rv, zv);
-        L.z[o] = zv;
+        zv[mm] = Z((r_ & 1) ? v.y : v.x) * Z(scale);
+        if (with_old) mad(rzo, rv[mm], zo[mm]);
+        mad(rz, rv[mm], zv[mm]);
       }
+      stf<NL, VS>(L.z + o, zv);
     }
     __syncthreads();
   }
@@ -378,13 +582,16 @@ __device__ __forceinline__ void acc_add(dacc& a, dfl v) {
 }
 
 // y = (S x)_f: the facet's own block and its four neighbours' (stencil class of f)
-template <int NL, bool MIXED, typename X>
-__device__ __forceinline__ void spmv_lat(const DevMesh& m, int f, const X* x, typename LatT<MIXED>::A (&y)[NL]) {
+template <int NL, int VS, bool MIXED, typename X, typename XV>
+__device__ __forceinline__ void spmv_lat(const DevMesh& m, int f, const X* x, XV, typename LatT<MIXED>::A (&y)[NL]) {
   using A = typename LatT<MIXED>::A;
   using Acc = typename LatT<MIXED>::Acc;
   int nb[5];
   facet_nbrs<NL>(m, f, nb);
   const size_t sb = size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL;
+  XV xs[5][NL];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) ldf<NL, VS>(x + size_t(nb[b]) * VS, xs[b]);
   Acc acc[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) acc[i] = acc_zero(Acc{});
@@ -392,7 +599,7 @@ __device__ __forceinline__ void spmv_lat(const DevMesh& m, int f, const X* x, ty
   for (int b = 0; b < 5; ++b)
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
-      const auto xv = ldx(x + size_t(nb[b]) * NL + j);
+      const XV xv = xs[b][j];
 #pragma unroll
       for (int i = 0; i < NL; ++i) mad(acc[i], stencil_entry(m, sb + (b * NL + i) * NL + j, A{}), xv);
     }
@@ -499,7 +706,8 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   using V = typename T::V;
   using A = typename T::A;
   using Acc = typename T::Acc;
-  constexpr int NL = K + 1;
+  using Z = typename T::Z;
+  constexpr int NL = K + 1, VS = LatCtx<K, MIXED>::VS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ LatScal<A> sc;
   LatCtx<K, MIXED> L;
@@ -517,11 +725,11 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   V* p;
   if constexpr (MIXED) {
     L.lam = m.lam_df;
-    L.g = reinterpret_cast<float2*>(m.g);
-    L.r = reinterpret_cast<float2*>(m.r);
-    L.q = reinterpret_cast<float2*>(m.q);
-    L.z = m.zf;
-    p = reinterpret_cast<float2*>(m.pa);
+    L.g = m.lv_g;
+    L.r = m.lv_r;
+    L.q = m.lv_q;
+    L.z = m.lv_z;
+    p = m.lv_p;
   } else {
     L.lam = m.lam;
     L.g = m.g;
@@ -541,16 +749,18 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   Acc g0 = acc_zero(Acc{});
 #pragma unroll 2
   for (int f = gtid; f < nF; f += gsz) {
-    A gv[NL];
+    const size_t o = size_t(f) * VS;
+    A gv[NL], lv[NL];
     facet_g<NL>(m, f, gv);
+    if (a.warm_scale != 0.0) ldf<NL, VS>(L.lam + o, lv);
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
-      const size_t o = size_t(f) * NL + j;
-      stv(L.g + o, gv[j]);
-      stv(L.lam + o, a.warm_scale == 0.0 ? A(0) : warm * ldx(L.lam + o));
+      lv[j] = a.warm_scale == 0.0 ? A(0) : warm * lv[j];
       const double lead = lead_d(gv[j]);
       ga = fma(lead, lead, ga);
     }
+    stf<NL, VS>(L.g + o, gv);
+    stf<NL, VS>(L.lam + o, lv);
     acc_add(g0, gv[0]);
   }
   double gg[2];
@@ -575,24 +785,27 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   bool conv = false;
   double relres = 0.0;
   if (gnorm == 0.0) {
-    for (int f = gtid; f < nF; f += gsz)
+    for (int f = gtid; f < nF; f += gsz) {
+      A zero[NL];
 #pragma unroll
-      for (int j = 0; j < NL; ++j) stv(L.lam + size_t(f) * NL + j, A(0));
+      for (int j = 0; j < NL; ++j) zero[j] = A(0);
+      stf<NL, VS>(L.lam + size_t(f) * VS, zero);
+    }
     conv = true;
   } else {
     // r = sigma (g - S lam) with the constant component of g removed
     const A c0a = A(c0), sg = A(sigma);
 #pragma unroll 2
     for (int f = gtid; f < nF; f += gsz) {
-      A y[NL];
-      spmv_lat<NL, MIXED>(m, f, L.lam, y);
+      const size_t o = size_t(f) * VS;
+      A y[NL], gv[NL], rv[NL];
+      spmv_lat<NL, VS, MIXED>(m, f, L.lam, A{}, y);
+      ldf<NL, VS>(L.g + o, gv);
+      gv[0] = gv[0] - c0a;
 #pragma unroll
-      for (int j = 0; j < NL; ++j) {
-        const size_t o = size_t(f) * NL + j;
-        const A gv = (j == 0) ? ldx(L.g + o) - c0a : ldx(L.g + o);
-        if (j == 0) stv(L.g + o, gv);
-        stv(L.r + o, sg * (gv - y[j]));
-      }
+      for (int j = 0; j < NL; ++j) rv[j] = sg * (gv[j] - y[j]);
+      stf<NL, VS>(L.g + o, gv);
+      stf<NL, VS>(L.r + o, rv);
     }
     if (!grid_sync(bar, m.stats)) return;
     // z = M r
@@ -640,18 +853,24 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
       Acc pqa[1] = {acc_zero(Acc{})};
 #pragma unroll 2
       for (int f = gtid; f < nF; f += gsz) {
-        A y[NL];
-        spmv_lat<NL, MIXED>(m, f, L.z, y);
+        const size_t o = size_t(f) * VS;
+        A y[NL], pv[NL], qv[NL];
+        Z zz[NL];
+        spmv_lat<NL, VS, MIXED>(m, f, L.z, Z{}, y);
+        ldf<NL, VS>(L.z + o, zz);
+        if (it > 0) {
+          ldf<NL, VS>(p + o, pv);
+          ldf<NL, VS>(L.q + o, qv);
+        }
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
-          const size_t o = size_t(f) * NL + j;
-          const A zv = as_a(ldx(L.z + o));
-          const A pv = (it == 0) ? zv : zv + bt * ldx(p + o);
-          const A qv = (it == 0) ? y[j] : y[j] + bt * ldx(L.q + o);
-          stv(p + o, pv);
-          stv(L.q + o, qv);
-          mad(pqa[0], pv, qv);
+          const A zv = as_a(zz[j]);
+          pv[j] = (it == 0) ? zv : zv + bt * pv[j];
+          qv[j] = (it == 0) ? y[j] : y[j] + bt * qv[j];
+          mad(pqa[0], pv[j], qv[j]);
         }
+        stf<NL, VS>(p + o, pv);
+        stf<NL, VS>(L.q + o, qv);
       }
       double pq[1];
       if (!lat_reduce<1>(m, 0, pqa, bar, pq)) return;
@@ -740,9 +959,16 @@ size_t lattice_buffer_elems(int k, int N, int fp32) {
   return (C > rows_buf ? C : rows_buf) * N;
 }
 
+// Scratch row: N, plus the padding of the two-pass FFT (R2 = 2^floor(log2 N / 2)).
+size_t lattice_scratch_row(int N) {
+  int logn = 0;
+  while ((1 << logn) < N) ++logn;
+  return (1 << logn) == N ? size_t(N) + (size_t(1) << (logn / 2)) : size_t(N);
+}
+
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp) {
   const size_t cx = fp32 ? 8 : 16;
-  return (size_t(N) + lattice_buffer_elems(k, N, fp32) + size_t(grp) * N) * cx;
+  return (size_t(N) + lattice_buffer_elems(k, N, fp32) + size_t(grp) * lattice_scratch_row(N)) * cx;
 }
 
 // Rows per transform group: all of them if two blocks per SM still fit, else the most

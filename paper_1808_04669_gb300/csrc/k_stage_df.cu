@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, floa
     const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
 #pragma unroll
     for (int mm = 0; mm < NL; ++mm) {
-      const dfl v = m.lam_is_df ? to_dfl(m.lam_df[size_t(f) * NL + mm]) : dfl(m.lam[size_t(f) * NL + mm]);
+      const dfl v = m.lam_is_df ? to_dfl(m.lam_df[size_t(f) * m.lat_vs + mm]) : dfl(m.lam[size_t(f) * NL + mm]);
       lam[e * NL + mm] = (flip && (mm & 1)) ? v : -v;   // negated: u = h + sum (-G) lam
     }
   }
@@ -232,9 +232,11 @@ __global__ void k_to_dfl(const double* __restrict__ x, float2* __restrict__ y, l
     y[i] = to_float2(dfl(x[i]));
 }
 
-__global__ void k_to_double(const float2* __restrict__ x, double* __restrict__ y, long long n) {
+// y[f][j] = x[f][j] for j < ny: facet-major rows of stride sx (double-float) and ny (FP64)
+__global__ void k_to_double(const float2* __restrict__ x, int sx, double* __restrict__ y, int ny, long long nrow) {
+  const long long n = nrow * ny;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = to_double(x[i]);
+    y[i] = to_double(x[(i / ny) * sx + i % ny]);
 }
 
 inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
@@ -269,11 +271,11 @@ cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_double(const float2* x, double* y, long long n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  long long nb = (n + 255) / 256;
+cudaError_t launch_to_double(const float2* x, int sx, double* y, int ny, long long nrow, cudaStream_t s) {
+  if (nrow <= 0) return cudaSuccess;
+  long long nb = (nrow * ny + 255) / 256;
   if (nb > 4096) nb = 4096;
-  k_to_double<<<int(nb), 256, 0, s>>>(x, y, n);
+  k_to_double<<<int(nb), 256, 0, s>>>(x, sx, y, ny, nrow);
   return cudaGetLastError();
 }
 
