@@ -3,9 +3,9 @@
 One step = one SSP-RK3 time step (three stages; each stage = element residual
 and condensation, facet PCG solve, recovery) on the double shear layer,
 256 x 256 split squares of [0, 2pi]^2 (131072 triangles), BDM_3, nu = 1e-4.
-The timed form is the mixed-precision one: element kernels in double-float
-arithmetic on the FP32 units, facet PCG with FP64 vectors preconditioned by the
-FP32 Fourier-space inverse of the facet operator. The FP64 form is timed on the
+The timed form is the mixed-precision one: element kernels and the facet PCG in
+double-float arithmetic on the FP32 units, the PCG preconditioned by the FP32
+Fourier-space inverse of the facet operator. The FP64 form is timed on the
 same workload and its state compared with the mixed one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -37,10 +37,12 @@ WORKLOAD = "shear_n256_k3"
 SAMPLE_N = 32          # oracle sample: same workload on a 32 x 32 split-square mesh
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM bytes (read + write) of one launch of the dominant kernel on the bench workload, from the
-# ncu capture summarised in profiles/; used only while the element-kernel sources still hash to
+# DRAM bytes (read + write) per launch of the dominant kernel on the bench workload, averaged
+# over the three stages of a step (the first stage reads one state, the others two), from the
+# ncu capture summarised in profiles/; used only while the stage-kernel sources still hash to
 # the captured `sha`, else the line reports null.
-NCU_TRAFFIC = {"stage_residual": {"sha": None, "n_tri": 131072, "bytes": None}}
+NCU_TRAFFIC = {"stage_residual": {"sha": "4ff6b630c4472b56", "n_tri": 131072, "bytes": 42661973,
+                                  "source": "profiles/k_stage_df_shear_n256_k3.md"}}
 
 
 def env_rank():
@@ -133,7 +135,7 @@ class ClockSampler:
 
 def element_kernel_sha():
     h = hashlib.sha256()
-    for n in ("k_element.cu", "dfloat.cuh", "kcommon.cuh", "device.cuh"):
+    for n in ("k_stage_df.cu", "ktables.cuh", "dfloat.cuh", "kcommon.cuh", "device.cuh"):
         with open(os.path.join(ROOT, "paper_1808_04669_gb300", "csrc", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -331,7 +333,7 @@ def run_ours(args):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32x2 (double-float) element kernels, f64 PCG with f32 Fourier preconditioner, f64 state",
+        "vs_baseline": None, "dtype": "f32x2 (double-float) element kernels and PCG vectors, f32 Fourier preconditioner, f64 state",
         "data": "synthetic (double shear layer sampled at lattice points, seeded)",
         "config": {"workload": workload_label(w, args.n or w.N, mixed.n_tri),
                    "N": args.n or w.N, "k": k, "nu": w.nu, "dt": dt,
@@ -418,7 +420,7 @@ def run_ensemble(args):
                       "value": value, "unit": UNIT, "n_gpus": world, "scaling": "strong", "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "instances": n_inst,
                       "triangles": int(tris), "lattice_instances": int(lat),
-                      "dtype": "f32x2 (double-float) element kernels, f64 PCG with f32 preconditioner, f64 state",
+                      "dtype": "f32x2 (double-float) element kernels and PCG vectors, f32 Fourier preconditioner, f64 state",
                       "config": {"workload": "ensemble of %d periodic unit-square meshes, N~U{32..256}, "
                                              "k~U{1,2,3}, log10 nu~U[-5,-2], seed 1" % n_inst,
                                  "graph": "one captured CUDA graph per step (dg_batch_rk3_step)"}}), flush=True)
