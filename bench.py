@@ -154,19 +154,19 @@ def stage_flops_per_triangle(k):
 
 
 def lattice_solver_bytes(n_facet, k, iters, solves):
-    """Algorithmic DRAM bytes of the lattice (Fourier-preconditioned) facet solves.
+    """Algorithmic DRAM bytes of the mixed-form lattice (Fourier-preconditioned) facet solves.
 
-    Per multiplier DOF and CG iteration: SpMV pass 32 B (read z, p_old; write p_new, q, FP64),
-    update + forward row pass 48 B (read r, q, p, lam; write r, lam) + 8 B complex write,
-    column pass 16 B complex read/write + 8 C B of the inverse symbol (C = 3(k+1), FP32 complex),
-    inverse row pass 8 B complex read + 24 B (read r, z_old; write z), 8 B of facet-map reads;
-    plus 20 B of stencil indices per facet. Per solve: one more preconditioner application and
-    g assembly / residual 64 B per DOF.
+    Vectors are double-float (8 B per DOF), z is FP32 (4 B); the spectrum holds half the
+    wavenumbers (4 B per DOF per pass) and the packed FP32 symbol 2(C+1) B per DOF, C = 3(k+1).
+    Per DOF and CG iteration: SpMV pass 36 B (read z, p, q; write p, q); update + forward rows
+    52 B (read r, q, lam, p; write r, lam, spectrum); columns 8 B + symbol; inverse rows 20 B
+    (read spectrum, r, z_old; write z); plus 20 B of stencil ids per facet. Per solve: g assembly,
+    the first residual and one more preconditioner application, 108 B + symbol per DOF.
     """
     nl = n_facet * (k + 1)
-    C = 3 * (k + 1)
-    per_iter = nl * (32 + 56 + 16 + 8 * C + 32 + 8) + 20 * n_facet
-    per_solve = nl * (64 + 16 + 8 * C + 40) + 20 * n_facet
+    sym = 2 * (3 * (k + 1) + 1)
+    per_iter = nl * (36 + 52 + 8 + sym + 20) + 20 * n_facet
+    per_solve = nl * (108 + sym) + 20 * n_facet
     return iters * per_iter + solves * per_solve
 
 
