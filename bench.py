@@ -142,10 +142,11 @@ def element_kernel_sha():
 
 
 def stage_flops_per_triangle(k):
-    """FP64 flops of k_stage<k> per triangle (FMA = 2), counted from the kernel's loops."""
+    """Flops of the stage kernel per triangle (FMA = 2), counted from its loops:
+    the volume rule has 3, 7, 16 points for k = 1, 2, 3 (fully symmetric, degree 3k - 1)."""
     ns = (k + 1) * (k + 2) // 2
     nd = 2 * ns
-    nq = ((3 * k + 1) // 2) ** 2
+    nq = {1: 3, 2: 7, 3: 16}[k]
     nqf = (3 * k + 2) // 2
     vol = nq * (2 * (6 * ns + 4 * ns) + 40)              # trace/gradient sums, flux, test sums
     fac = 3 * nqf * (2 * (12 * ns + 6 * ns) + 30)         # both traces + normal derivatives, flux, test sums

@@ -12,7 +12,12 @@
 
 #include "../../include/dgdf.h"
 #include "device.cuh"
+#include "kcommon.cuh"
 #include "setup.hpp"
+
+static_assert(dgdf::Dims<1>::NQ == dgdf::kVolumePoints(1) && dgdf::Dims<2>::NQ == dgdf::kVolumePoints(2) &&
+                  dgdf::Dims<3>::NQ == dgdf::kVolumePoints(3),
+              "host and device volume rules differ in size");
 
 namespace {
 
@@ -534,7 +539,9 @@ int enqueue_step(dg_mesh* M, double dt) {
   for (int s = 0; s < 3; ++s) {
     const double a = kRkA[s], b = kRkB[s];
     const double* up = (s == 0) ? d.u : d.ustage;
-    double* out = (s == 2) ? d.u : d.ustage;
+    // mixed form: the next stage reads only the double-float twin, so the FP64 copy of an
+    // intermediate stage is not written
+    double* out = (s == 2) ? d.u : (d.elem_df ? nullptr : d.ustage);
     float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
     dgdf::StageArgs sa{};
     sa.mode = dgdf::MODE_STAGE;

@@ -127,6 +127,7 @@ cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double*
 cudaError_t launch_stage(const DevMesh& m, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+// out may be NULL in the mixed form (only the double-float twin is written)
 cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s);
 cudaError_t launch_to_double(const float2* x, int sx, double* y, int ny, long long nrow, cudaStream_t s);

@@ -777,9 +777,10 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   const double sigma = gnorm0 > 0.0 ? ldexp(1.0, -ilogb(gnorm0 / sqrt(double(nF) * NL))) : 1.0;
   const double gnorm = sigma * gnorm0;
   const double stop2 = (a.rtol * gnorm) * (a.rtol * gnorm);
-  // mixed form: double-float vectors carry 48 bits, so the residual reaches a rounding
-  // floor near 1e-14..1e-12 relative on large meshes; once an iteration no longer halves
-  // the residual and it is below floor_rtol, the solve is accepted there
+  // rounding floor: the recursive residual stops decreasing near eps * cond(S) relative
+  // (double-float vectors: 1e-14..1e-12 on large meshes; FP64: near 1e-13 at N = 1024);
+  // once an iteration no longer halves the residual and it is below floor_rtol, the
+  // solve is accepted there
   const double floor2 = (a.floor_rtol * gnorm) * (a.floor_rtol * gnorm);
   int it = 0;
   bool conv = false;
@@ -896,7 +897,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
       if (threadIdx.x == 0) {
         sc.done = 0;
         sc.conv = 0;
-        const bool stagnated = MIXED && rrv <= floor2 && rrv > 0.25 * rr_prev;
+        const bool stagnated = rrv <= floor2 && rrv > 0.25 * rr_prev;
         if (rrv <= stop2 || !isfinite(rrv) || stagnated) {
           sc.done = 1;
           sc.relres = sqrt(rrv) / gnorm;

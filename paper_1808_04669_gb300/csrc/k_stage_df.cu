@@ -196,34 +196,50 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, Stag
 }
 
 // Recovery, mixed form: u_T = h_T - G_T^T lam_T (h = P f from the stage kernel) in
-// double-float, with lam from the double-float solver (lam_is_df) or the FP64 one;
-// writes u in FP64 and, if out_df is given, its double-float twin.
+// double-float, with lam from the double-float solver (lam_is_df) or the FP64 one.
+// Writes the double-float twin out_df and, if out is given, u in FP64. A block's rows of
+// h and u pass through shared memory (padded rows), so that global reads and writes are
+// coalesced; each thread computes one triangle.
+constexpr int kRecoverThreads = 128;
+
 template <int K>
-__global__ void __launch_bounds__(128) k_recover_df(DevMesh m, double* out, float2* out_df) {
+__global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, double* out, float2* out_df) {
   using D = Dims<K>;
-  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.n_tri) return;
-  dfl lam[L3];
+  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL, RS = ND + 1;
+  __shared__ float2 tile[kRecoverThreads * RS];
+  const int t0 = blockIdx.x * kRecoverThreads;
+  const int nt = min(kRecoverThreads, m.n_tri - t0);
+  const float2* hb = m.h_df + size_t(t0) * ND;
+  for (int e = threadIdx.x; e < nt * ND; e += kRecoverThreads) tile[(e / ND) * RS + e % ND] = hb[e];
+  __syncthreads();
+  if (int(threadIdx.x) < nt) {
+    const int t = t0 + threadIdx.x;
+    dfl lam[L3];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const int f = __ldg(&m.tri_facet[size_t(t) * 3 + e]);
-    const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+    for (int e = 0; e < 3; ++e) {
+      const int f = __ldg(&m.tri_facet[size_t(t) * 3 + e]);
+      const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
 #pragma unroll
-    for (int mm = 0; mm < NL; ++mm) {
-      const dfl v = m.lam_is_df ? to_dfl(m.lam_df[size_t(f) * m.lat_vs + mm]) : dfl(m.lam[size_t(f) * NL + mm]);
-      lam[e * NL + mm] = (flip && (mm & 1)) ? v : -v;   // negated: u = h + sum (-G) lam
+      for (int mm = 0; mm < NL; ++mm) {
+        const dfl v = m.lam_is_df ? to_dfl(m.lam_df[size_t(f) * m.lat_vs + mm]) : dfl(m.lam[size_t(f) * NL + mm]);
+        lam[e * NL + mm] = (flip && (mm & 1)) ? v : -v;   // negated: u = h + sum (-G) lam
+      }
+    }
+    const float2* G = m.Gdf + size_t(__ldg(&m.tri_class[t])) * L3 * ND;
+    float2* row = tile + threadIdx.x * RS;
+#pragma unroll 4
+    for (int i = 0; i < ND; ++i) {
+      dacc v = dacc_of(to_dfl(row[i]));
+#pragma unroll
+      for (int l = 0; l < L3; ++l) mad(v, to_dfl(__ldg(&G[l * ND + i])), lam[l]);
+      row[i] = to_float2(val(v));
     }
   }
-  const float2* G = m.Gdf + size_t(__ldg(&m.tri_class[t])) * L3 * ND;
-#pragma unroll 4
-  for (int i = 0; i < ND; ++i) {
-    dacc v = dacc_of(to_dfl(m.h_df[size_t(t) * ND + i]));
-#pragma unroll
-    for (int l = 0; l < L3; ++l) mad(v, to_dfl(__ldg(&G[l * ND + i])), lam[l]);
-    const dfl u = val(v);
-    out[size_t(t) * ND + i] = to_double(u);
-    if (out_df) out_df[size_t(t) * ND + i] = to_float2(u);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nt * ND; e += kRecoverThreads) {
+    const float2 u = tile[(e / ND) * RS + e % ND];
+    if (out_df) out_df[size_t(t0) * ND + e] = u;
+    if (out) out[size_t(t0) * ND + e] = to_double(u);
   }
 }
 
@@ -259,7 +275,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 }
 
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
-  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, out, out_df)));
+  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverThreads), kRecoverThreads, 0, s>>>(m, out, out_df)));
   return cudaGetLastError();
 }
 

@@ -13,8 +13,7 @@ struct Dims {
   static constexpr int ND = 2 * NS;                  // broken vector DOFs per triangle
   static constexpr int NW = K * (K + 1) / 2;         // P^{k-1} per triangle
   static constexpr int NL = K + 1;                   // P^k per facet
-  static constexpr int NA = (3 * K + 1) / 2;         // collapsed volume rule points per direction
-  static constexpr int NQ = NA * NA;                 // exact to degree 3k-1
+  static constexpr int NQ = K == 1 ? 3 : (K == 2 ? 7 : 16);   // symmetric volume rule, exact to degree 3k-1
   static constexpr int NQF = (3 * K + 2) / 2;        // ceil((3k+1)/2) Gauss-Legendre points per facet
 };
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <tuple>
@@ -233,6 +234,186 @@ void triangle_rule(int n, std::vector<double>& xi, std::vector<double>& w) {
     }
 }
 
+// Fully symmetric volume rules exact to degree 3k - 1 (positive weights, interior points),
+// written as orbits in barycentric coordinates: the centroid, orbits (a, a, 1-2a) of 3
+// points, and orbits (a, b, 1-a-b) of 6 points. k = 1: one 3-point orbit (degree 2);
+// k = 2: Radon's 7-point rule (degree 5, closed form); k = 3: a 16-point rule of degree 8
+// with Dunavant's orbit structure (centroid, three 3-point orbits, one 6-point orbit),
+// solved here by Gauss-Newton on the moment equations from approximate starting values.
+// Weights sum to 1 here and are scaled to the reference area 1/2.
+struct SymRule {
+  using real = long double;
+  real w0 = 0.0;                          // centroid weight (0: no centroid)
+  std::vector<real> a3, w3;               // 3-point orbits
+  std::vector<real> a6, b6, w6;           // 6-point orbits
+  template <typename T>
+  void points(std::vector<T>& xi, std::vector<T>& w) const {
+    xi.clear();
+    w.clear();
+    auto add = [&](real l2, real l3, real wt) {
+      xi.push_back(T(l2));
+      xi.push_back(T(l3));
+      w.push_back(T(0.5L * wt));
+    };
+    if (w0 != 0.0L) add(1.0L / 3.0L, 1.0L / 3.0L, w0);
+    for (size_t o = 0; o < a3.size(); ++o) {
+      const real a = a3[o], c = 1.0L - 2.0L * a;
+      add(a, a, w3[o]);
+      add(a, c, w3[o]);
+      add(c, a, w3[o]);
+    }
+    for (size_t o = 0; o < a6.size(); ++o) {
+      const real a = a6[o], b = b6[o], c = 1.0L - a - b;
+      add(a, b, w6[o]);
+      add(b, a, w6[o]);
+      add(a, c, w6[o]);
+      add(c, a, w6[o]);
+      add(b, c, w6[o]);
+      add(c, b, w6[o]);
+    }
+  }
+  void get(std::vector<real>& p) const {
+    p.clear();
+    if (w0 != 0.0L) p.push_back(w0);
+    for (size_t o = 0; o < a3.size(); ++o) { p.push_back(a3[o]); p.push_back(w3[o]); }
+    for (size_t o = 0; o < a6.size(); ++o) { p.push_back(a6[o]); p.push_back(b6[o]); p.push_back(w6[o]); }
+  }
+  void set(const std::vector<real>& p) {
+    size_t i = 0;
+    if (w0 != 0.0L) w0 = p[i++];
+    for (size_t o = 0; o < a3.size(); ++o) { a3[o] = p[i++]; w3[o] = p[i++]; }
+    for (size_t o = 0; o < a6.size(); ++o) { a6[o] = p[i++]; b6[o] = p[i++]; w6[o] = p[i++]; }
+  }
+};
+
+// Relative moment residuals of the rule with points xi and weights w: for i + j <= deg,
+// (rule(xi1^i xi2^j) - exact) / exact, exact = i! j! / (i+j+2)! on the reference triangle.
+template <typename T>
+void moment_residual(const std::vector<T>& xi, const std::vector<T>& w, int deg, std::vector<T>& res) {
+  res.clear();
+  for (int i = 0; i <= deg; ++i)
+    for (int j = 0; i + j <= deg; ++j) {
+      T exact = 1;
+      for (int t = 2; t <= i; ++t) exact *= t;
+      for (int t = 2; t <= j; ++t) exact *= t;
+      for (int t = 2; t <= i + j + 2; ++t) exact /= t;
+      T q = 0;
+      for (size_t p = 0; p < w.size(); ++p) {
+        T v = w[p];
+        for (int t = 0; t < i; ++t) v *= xi[2 * p];
+        for (int t = 0; t < j; ++t) v *= xi[2 * p + 1];
+        q += v;
+      }
+      res.push_back((q - exact) / exact);
+    }
+}
+
+// Gauss-Newton with a finite-difference Jacobian on the relative moment equations (a
+// consistent system), in extended precision so that the rule rounds to double correctly.
+void refine_rule(SymRule& R, int deg) {
+  using real = SymRule::real;
+  std::vector<real> p, r, rp, rm, xi, w;
+  R.get(p);
+  const int np = int(p.size());
+  for (int it = 0; it < 40; ++it) {
+    R.points(xi, w);
+    moment_residual(xi, w, deg, r);
+    real mx = 0;
+    for (real v : r) mx = std::max(mx, std::fabs(v));
+    if (mx < 1e-18L) break;
+    const int ne = int(r.size());
+    std::vector<real> J(size_t(ne) * np);
+    for (int c = 0; c < np; ++c) {
+      const real h = 1e-9L * std::max(real(1e-3L), std::fabs(p[c]));
+      std::vector<real> q = p;
+      q[c] = p[c] + h;
+      R.set(q);
+      R.points(xi, w);
+      moment_residual(xi, w, deg, rp);
+      q[c] = p[c] - h;
+      R.set(q);
+      R.points(xi, w);
+      moment_residual(xi, w, deg, rm);
+      for (int e = 0; e < ne; ++e) J[size_t(e) * np + c] = (rp[e] - rm[e]) / (2 * h);
+    }
+    R.set(p);
+    // normal equations J^T J d = -J^T r, Gaussian elimination with partial pivoting
+    std::vector<real> A(size_t(np) * np, 0), b(np, 0);
+    for (int e = 0; e < ne; ++e)
+      for (int c = 0; c < np; ++c) {
+        b[c] -= J[size_t(e) * np + c] * r[e];
+        for (int d = 0; d < np; ++d) A[size_t(c) * np + d] += J[size_t(e) * np + c] * J[size_t(e) * np + d];
+      }
+    for (int c = 0; c < np; ++c) {
+      int piv = c;
+      for (int d = c + 1; d < np; ++d)
+        if (std::fabs(A[size_t(d) * np + c]) > std::fabs(A[size_t(piv) * np + c])) piv = d;
+      for (int d = 0; d < np; ++d) std::swap(A[size_t(c) * np + d], A[size_t(piv) * np + d]);
+      std::swap(b[c], b[piv]);
+      for (int d = c + 1; d < np; ++d) {
+        const real f = A[size_t(d) * np + c] / A[size_t(c) * np + c];
+        for (int e = c; e < np; ++e) A[size_t(d) * np + e] -= f * A[size_t(c) * np + e];
+        b[d] -= f * b[c];
+      }
+    }
+    std::vector<real> dlt(np);
+    for (int c = np - 1; c >= 0; --c) {
+      real v = b[c];
+      for (int d = c + 1; d < np; ++d) v -= A[size_t(c) * np + d] * dlt[d];
+      dlt[c] = v / A[size_t(c) * np + c];
+    }
+    for (int c = 0; c < np; ++c) p[c] += dlt[c];
+    R.set(p);
+  }
+}
+
+// The rule of degree 3k - 1 with kVolumePoints(k) points; false if it cannot be built.
+bool build_symmetric_rule(int k, std::vector<double>& xi, std::vector<double>& w) {
+  using real = SymRule::real;
+  SymRule R;
+  if (k == 1) {
+    R.a3 = {1.0L / 6.0L};
+    R.w3 = {1.0L / 3.0L};
+  } else if (k == 2) {
+    const real s15 = std::sqrt(15.0L);
+    R.w0 = 9.0L / 40.0L;
+    R.a3 = {(6.0L - s15) / 21.0L, (6.0L + s15) / 21.0L};
+    R.w3 = {(155.0L - s15) / 1200.0L, (155.0L + s15) / 1200.0L};
+  } else if (k == 3) {
+    R.w0 = 0.1443L;
+    R.a3 = {0.4593L, 0.1706L, 0.0505L};
+    R.w3 = {0.0951L, 0.1032L, 0.0325L};
+    R.a6 = {0.2631L};
+    R.b6 = {0.0084L};
+    R.w6 = {0.0272L};
+    refine_rule(R, 3 * k - 1);
+  } else {
+    return false;
+  }
+  R.points(xi, w);
+  // the rounded rule must be exact to rounding on every monomial up to the degree
+  std::vector<double> r;
+  moment_residual(xi, w, 3 * k - 1, r);
+  for (double v : r)
+    if (!(std::fabs(v) < 1e-14)) return false;
+  for (size_t q = 0; q < w.size(); ++q)
+    if (!(w[q] > 0.0) || !(xi[2 * q] > 0.0) || !(xi[2 * q + 1] > 0.0) || !(xi[2 * q] + xi[2 * q + 1] < 1.0))
+      return false;
+  return int(w.size()) == kVolumePoints(k);
+}
+
+// The rules are built once per process (the k = 3 refinement runs in extended precision).
+bool symmetric_triangle_rule(int k, std::vector<double>& xi, std::vector<double>& w) {
+  static std::once_flag once[4];
+  static std::vector<double> rx[4], rw[4];
+  static bool ok[4] = {false, false, false, false};
+  if (k < 1 || k > 3) return false;
+  std::call_once(once[k], [k] { ok[k] = build_symmetric_rule(k, rx[k], rw[k]); });
+  xi = rx[k];
+  w = rw[k];
+  return ok[k];
+}
+
 const double kRefV[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
 
 }  // namespace
@@ -372,9 +553,11 @@ int build_reference(int k, RefTables& ref, std::string& err) {
     for (int j = 0; j < B.ns; ++j) B.norm[j] = 1.0 / std::sqrt(nrm[j]);
   }
   const int ns = ref.ns;
-  // volume rule exact to degree 3k - 1: n points per direction with 2n - 1 >= 3k - 1
-  int n = (3 * k + 1) / 2;
-  triangle_rule(n, ref.vxi, ref.vw);
+  // volume rule exact to degree 3k - 1: the fully symmetric rule (3, 7, 16 points)
+  if (!symmetric_triangle_rule(k, ref.vxi, ref.vw)) {
+    err = "reference set-up: the symmetric volume rule for k = " + std::to_string(k) + " is not exact";
+    return DG_ERR_MESH;
+  }
   ref.nq = int(ref.vw.size());
   ref.vphi.resize(size_t(ref.nq) * ns);
   ref.vdphi.resize(size_t(ref.nq) * ns * 2);

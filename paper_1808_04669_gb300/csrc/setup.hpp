@@ -91,6 +91,9 @@ struct HostMesh {
 
 // Returns 0 or a dg_status code; message in err.
 int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology& topo, std::string& err);
+// Points of the volume rule of degree 3k - 1 (fully symmetric rules; Dims<K>::NQ on the device).
+constexpr int kVolumePoints(int k) { return k == 1 ? 3 : (k == 2 ? 7 : 16); }
+
 int build_reference(int k, RefTables& ref, std::string& err);
 int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha,
                     HostMesh& hm, std::string& err);
