@@ -61,6 +61,12 @@ struct dg_mesh {
   std::string lattice_why;
   double last_bdt = 0.0;
   bool has_lam = false;
+  // lattice solver: multipliers of each RK stage in the last two steps (device, the layout of
+  // the solver's lam), their step sizes, and how many are valid
+  void* hist[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  double hist_dt[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  int hist_n[3] = {0, 0, 0};
+  size_t hist_bytes = 0;
   bool udf_valid = false;        // mixed form: u_df holds the double-float image of u
   double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
   double* wbuf = nullptr;        // [n_tri][nw] element pressure
@@ -193,9 +199,29 @@ int ensure_udf(dg_mesh* M) {
   return rc;
 }
 
-int solve(dg_mesh* M, double warm_scale) {
+void forget_history(dg_mesh* M) {
+  for (int s = 0; s < 3; ++s) M->hist_n[s] = 0;
+}
+
+int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
+  // lattice solver inside a step: warm start from the same stage of the last two steps.
+  // lam_s is b_s dt times a smooth function of time, so with equal step sizes the linear
+  // extrapolation 2 lam(n-1) - lam(n-2) is second-order accurate; one entry, or a changed
+  // step size, gives lam(n-1) rescaled by dt / dt(n-1).
+  if (M->use_lattice && stage >= 0 && M->hist_n[stage] >= 1) {
+    const double* hd = M->hist_dt[stage];
+    a.hist1 = M->hist[stage][0];
+    a.hist2 = M->hist[stage][1];
+    if (M->hist_n[stage] >= 2 && hd[0] == dt && hd[1] == dt) {
+      a.c1 = 2.0;
+      a.c2 = -1.0;
+    } else {
+      a.c1 = dt / hd[0];
+      a.c2 = 0.0;
+    }
+  }
   a.rtol = M->p.cg_rtol;
   a.maxit = M->p.cg_maxit;
   a.mixed = M->p.precision == DG_PRECISION_MIXED;
@@ -210,6 +236,18 @@ int solve(dg_mesh* M, double warm_scale) {
   }
   const int nb = M->solver_blocks[a.mixed];
   return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
+}
+
+// After the solve of RK stage s with step size dt: the new multipliers become the newest
+// history entry (the solver already moved the previous one into the second slot).
+int push_history(dg_mesh* M, int s, double dt) {
+  if (!M->use_lattice) return DG_OK;
+  const void* lam = M->dm.lam_is_df ? static_cast<const void*>(M->dm.lam_df) : static_cast<const void*>(M->dm.lam);
+  CK(cudaMemcpyAsync(M->hist[s][0], lam, M->hist_bytes, cudaMemcpyDeviceToDevice, M->stream));
+  M->hist_dt[s][1] = M->hist_dt[s][0];
+  M->hist_dt[s][0] = dt;
+  M->hist_n[s] = M->hist_n[s] < 2 ? M->hist_n[s] + 1 : 2;
+  return DG_OK;
 }
 
 int check_mesh(const dg_mesh* M) {
@@ -259,7 +297,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   const int lat_fp32 = p.precision == DG_PRECISION_MIXED;
   int lat_blocks = 0;
   if (p.precond == DG_PRECOND_AUTO) {
-    dgdf::build_lattice(M->hm, tri_coords, lat);
+    dgdf::build_lattice(M->hm, tri_coords, lat, lat_fp32);
     if (lat.ok) lat_blocks = dgdf::lattice_blocks(M->hm.k, lat.N, lat_fp32);
     if (lat.ok && lat_blocks > 0) dgdf::renumber_facets_lattice(M->hm, lat);
     else M->lattice_why = lat.ok ? "lattice solver does not fit on this device" : lat.why;
@@ -358,45 +396,51 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     const int fp32 = lat_fp32;
     const int C = lat.C, N = lat.N;
     // device layout [ki < N/2+1][entry][kj] complex: the residual is real, so only half the
-    // wavenumbers along i are needed. FP32: entries (a, b), a <= b, of the Hermitian block;
-    // FP64: all C*C entries (the host inverse is Hermitian only to about cond * eps, which
-    // FP64 would resolve).
-    const int NK = N / 2 + 1, NP = fp32 ? C * (C + 1) / 2 : C * C;
+    // wavenumbers along i are needed.
+    //  FP32: the eigen form of each Hermitian block, entries V[b][i] (b, i < C) then 1/mu_i
+    //        (real): applied as V diag(1/mu) V^H, every eigen-component keeps its FP32
+    //        relative accuracy (the explicit inverse loses it to cancellation in the
+    //        near-singular blocks at small kappa);
+    //  FP64: all C*C entries of the inverse, the self-conjugate columns ki = 0 and ki = N/2
+    //        symmetrised (the half-spectrum transform takes S^(-kappa) = conj S^(kappa) for
+    //        granted, and the host inverts each wavenumber on its own).
+    const int NK = N / 2 + 1, NP = fp32 ? C * C + C : C * C;
     const size_t nS = dgdf::lattice_symbol_elems(hm.k, N, fp32);
     std::vector<double> sd;
     std::vector<float> sf;
-    if (fp32) sf.resize(2 * nS); else sd.resize(2 * nS);
-    // The half-spectrum transform takes S^(-kappa) = conj S^(kappa) for granted; the
-    // self-conjugate columns ki = 0 and ki = N/2 are symmetrised here (the host inverts
-    // each wavenumber on its own, so the pairs agree only to rounding).
-    auto H = [&](int ki, int kj, int ca, int cb, int ri) {
-      return lat.sinv[((size_t(ki) * N + kj) * C * C + size_t(ca) * C + cb) * 2 + ri];
-    };
-    for (int ki = 0; ki < NK; ++ki) {
-      const bool selfconj = ki == 0 || 2 * ki == N;
-      for (int kj = 0; kj < N; ++kj) {
-        const int mj = (N - kj) % N;
-        int pi = 0;
-        for (int ca = 0; ca < C; ++ca)
-          for (int cb = fp32 ? ca : 0; cb < C; ++cb, ++pi) {
-            double re = H(ki, kj, ca, cb, 0), im = H(ki, kj, ca, cb, 1);
-            if (selfconj) {
-              re = 0.5 * (re + H(ki, mj, ca, cb, 0));
-              im = 0.5 * (im - H(ki, mj, ca, cb, 1));
-            }
-            if (fp32 && ca == cb) im = 0.0;
-            const size_t o = ((size_t(ki) * NP + pi) * N + kj) * 2;
-            if (fp32) {
-              sf[o] = float(re);
-              sf[o + 1] = float(im);
-            } else {
+    if (fp32) {
+      sf.resize(2 * nS);
+      for (int ki = 0; ki < NK; ++ki)
+        for (int kj = 0; kj < N; ++kj)
+          for (int e = 0; e < NP; ++e)
+            for (int ri = 0; ri < 2; ++ri)
+              sf[((size_t(ki) * NP + e) * N + kj) * 2 + ri] =
+                  float(lat.seig[((size_t(ki) * N + kj) * NP + e) * 2 + ri]);
+    } else {
+      sd.resize(2 * nS);
+      auto H = [&](int ki, int kj, int ca, int cb, int ri) {
+        return lat.sinv[((size_t(ki) * N + kj) * C * C + size_t(ca) * C + cb) * 2 + ri];
+      };
+      for (int ki = 0; ki < NK; ++ki) {
+        const bool selfconj = ki == 0 || 2 * ki == N;
+        for (int kj = 0; kj < N; ++kj) {
+          const int mj = (N - kj) % N;
+          for (int ca = 0; ca < C; ++ca)
+            for (int cb = 0; cb < C; ++cb) {
+              double re = H(ki, kj, ca, cb, 0), im = H(ki, kj, ca, cb, 1);
+              if (selfconj) {
+                re = 0.5 * (re + H(ki, mj, ca, cb, 0));
+                im = 0.5 * (im - H(ki, mj, ca, cb, 1));
+              }
+              const size_t o = ((size_t(ki) * NP + ca * C + cb) * N + kj) * 2;
               sd[o] = re;
               sd[o + 1] = im;
             }
-          }
+        }
       }
     }
     std::vector<double>().swap(lat.sinv);
+    std::vector<double>().swap(lat.seig);
     const int32_t* fo = nullptr;
     const int32_t* fe = nullptr;
     const double* tw = nullptr;
@@ -440,6 +484,14 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     d.lat_logn = logn;
     M->use_lattice = true;
     M->lattice_blocks = lat_blocks;
+    // multiplier history of the three RK stages (warm starts), in the layout of the solver's lam
+    M->hist_bytes = nF * size_t(fp32 ? d.lat_vs : nl) * 8;
+    for (int s = 0; s < 3; ++s)
+      for (int h = 0; h < 2; ++h) {
+        double* p = nullptr;
+        if ((rc = dalloc(M, &p, M->hist_bytes / 8))) return cleanup(rc);
+        M->hist[s][h] = p;
+      }
   }
   *out = M;
   return DG_OK;
@@ -490,6 +542,7 @@ int dg_set_velocity(dg_mesh* M, const double* vals, int on_device) {
   if (rc) return rc;
   M->has_lam = false;
   M->udf_valid = false;
+  forget_history(M);
   return finish(M, false);
 }
 
@@ -520,6 +573,7 @@ int dg_project_divfree(dg_mesh* M) {
   if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(M->dm, M->dm.u, M->dm.u_df, M->stream); })))
     return rc;
   M->has_lam = false;
+  forget_history(M);
   return finish(M, true);
 }
 
@@ -554,7 +608,7 @@ int enqueue_step(dg_mesh* M, double dt) {
     sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
     const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
-    if ((rc = solve(M, warm))) return rc;
+    if ((rc = solve(M, warm, s, dt)) || (rc = push_history(M, s, dt))) return rc;
     if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
     M->last_bdt = b * dt;
     M->has_lam = true;
@@ -654,13 +708,27 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
   // eagerly when any member is cold or the step sizes changed.
   bool same_dt = B->exec && B->graph_dt.size() == n;
   for (size_t i = 0; same_dt && i < n; ++i) same_dt = B->graph_dt[i] == dt[i];
-  bool warm = true;
-  for (dg_mesh* M : B->members) warm = warm && M->has_lam;
+  // A member is in steady mode when its solves are warm and, on the lattice path, every
+  // stage has two history entries taken with the current step size; the captured step
+  // replays that mode, so steps run eagerly until all members reach it.
+  auto steady = [&](size_t i) {
+    const dg_mesh* M = B->members[i];
+    if (!M->has_lam) return false;
+    if (!M->use_lattice) return true;
+    for (int s = 0; s < 3; ++s)
+      if (M->hist_n[s] < 2 || M->hist_dt[s][0] != dt[i] || M->hist_dt[s][1] != dt[i]) return false;
+    return true;
+  };
   int64_t done = 0;
-  if (!warm || !same_dt) {
+  for (;;) {
+    bool all = true;
+    for (size_t i = 0; i < n; ++i) all = all && steady(i);
+    if ((all && same_dt) || done >= nsteps) break;
+    if (all && !same_dt) break;   // capture below
     for (size_t i = 0; i < n; ++i)
       if ((rc = enqueue_step(B->members[i], dt[i]))) return restore(rc);
-    done = 1;
+    ++done;
+    same_dt = false;              // the graph (if any) predates these eager steps
   }
   if (done < nsteps && !same_dt) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
@@ -709,6 +777,7 @@ int dg_set_coefficients(dg_mesh* M, const double* coef, int on_device) {
                      M->stream));
   M->has_lam = false;
   M->udf_valid = false;
+  forget_history(M);
   return finish(M, false);
 }
 
@@ -774,7 +843,7 @@ int enqueue_step_keep(dg_mesh* M, double dt, double* const st[3]) {
     sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
     const double warm = M->has_lam ? (kRkB[s] * dt) / M->last_bdt : 0.0;
-    if ((rc = solve(M, warm))) return rc;
+    if ((rc = solve(M, warm, s, dt)) || (rc = push_history(M, s, dt))) return rc;
     double* out = (s == 2) ? d.u : d.ustage;
     float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
@@ -838,6 +907,7 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
     CK(cudaMemcpyAsync(d.u, ck + size_t(g) * n, bytes, cudaMemcpyDeviceToDevice, M->stream));
     M->has_lam = false;
     M->udf_valid = false;
+    forget_history(M);
     for (int64_t i = 0; i < len; ++i) {
       double* const st[3] = {stg + (size_t(i) * 3 + 0) * n, stg + (size_t(i) * 3 + 1) * n, stg + (size_t(i) * 3 + 2) * n};
       if ((rc = enqueue_step_keep(M, dt, st))) return rc;
@@ -871,6 +941,7 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
   CK(cudaMemcpyAsync(d.u, uK, bytes, cudaMemcpyDeviceToDevice, M->stream));
   M->has_lam = false;
   M->udf_valid = false;
+  forget_history(M);
   CK(cudaMemcpyAsync(u0bar, ub, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, M->stream));
   double nb = 0.0;
   CK(cudaMemcpyAsync(&nb, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, M->stream));

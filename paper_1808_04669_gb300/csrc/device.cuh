@@ -119,6 +119,12 @@ struct SolveArgs {
   int max_sweeps;
   int inner_maxit;     // iteration cap of each inner FP32 solve
   double floor_rtol;   // accepted relative residual once refinement stagnates at its rounding floor
+  // lattice solver, warm start from the same stage of earlier steps (overrides warm_scale):
+  // lam0 = c1 hist1 + c2 hist2 (hist2 read only if c2 != 0); the kernel then moves hist1
+  // into hist2, and the caller stores the new lam in hist1. Layout of lam.
+  void* hist1;
+  void* hist2;
+  double c1, c2;
 };
 
 // Launchers (k dispatched at run time). Return the launch error.

@@ -12,8 +12,9 @@
 // The residual is real, so only the wavenumbers ki in [0, N/2] are transformed:
 //   rows   : two facet rows j, j+1 packed as one complex row, FFT along i, split
 //            into the two half spectra (Hermitian symmetry)
-//   columns: per ki, FFT along j, multiply by S^(kappa)^+ (upper triangle stored,
-//            the lower one is its conjugate), inverse FFT along j
+//   columns: per ki, FFT along j, multiply by S^(kappa)^+ (FP32: from its eigen form
+//            V diag(1/mu) V^H, accurate to FP32 in every eigen-component), inverse FFT
+//            along j
 //   rows   : inverse FFT along i of two rows packed the same way (scaled 1/N^2)
 // with a grid barrier between the passes. Transforms run in shared memory: for N a
 // power of two up to 1024 (FP32) / 256 (FP64) a two-pass FFT whose radix-sqrt(N)
@@ -60,6 +61,13 @@ __device__ __forceinline__ float ldz(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ void stv(double* p, double v) { *p = v; }
 __device__ __forceinline__ void stv(float2* p, dfl v) { *p = to_float2(v); }
 __device__ __forceinline__ void mad(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void acc_add(double& a, double v) { a += v; }
+__device__ __forceinline__ void acc_add(dacc& a, dfl v) {
+  float s, t;
+  two_sum(a.s, v.hi, s, t);
+  a.s = s;
+  a.c += t + v.lo;
+}
 __device__ __forceinline__ double acc_zero(double) { return 0.0; }
 __device__ __forceinline__ dacc acc_zero(dacc) { return dacc_zero(); }
 __device__ __forceinline__ double acc_val(double a) { return a; }
@@ -241,9 +249,9 @@ struct LatCtx {
   // facet stride of the solver vectors: padded to 4 for k = 2 in the mixed form, so that
   // every facet's values are one aligned 16- or 32-byte access
   static constexpr int VS = (MIXED && NL == 3) ? 4 : NL;
-  // stored entries per wavenumber: the packed upper triangle in FP32 (its rounding hides the
-  // host inverse's departure from Hermitian), the full block in FP64
-  static constexpr int NP = MIXED ? C * (C + 1) / 2 : C * C;
+  // stored entries per wavenumber: FP32, the eigen form (unitary V, C x C, then the C
+  // inverse eigenvalues); FP64, the full inverse block
+  static constexpr int NP = MIXED ? C * C + C : C * C;
   int N, logn, NK, ntj;   // NK = N/2 + 1 wavenumbers ki; ntj row tiles per facet type
   int grp;                // rows transformed at a time (the scratch holds grp rows)
   bool pow2;              // FFT (N a power of two) or direct DFT
@@ -391,13 +399,15 @@ __device__ __forceinline__ void stf(double* p, const double (&v)[NL]) {
 // facet type with all k+1 modes is one contiguous range of the facet-major vectors:
 // DOF index ((type N + j) N + i) VS + m.
 
-// Row pass, forward: per tile read r (first updating r -= alpha q, lam += alpha_lam p
-// when `update`), accumulate r.r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per
+// Row pass, forward: per tile read r (first updating r -= alpha q + c_prev 1,
+// lam += alpha_lam p when `update`; 1 is the constant multiplier, mode 0 on every facet),
+// accumulate r.r and the sum of the mode-0 entries of r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per
 // mode, FFT along i, split into the two rows' half spectra and store them in X.
 template <int K, bool MIXED>
 __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename LatT<MIXED>::A alpha,
-                             typename LatT<MIXED>::A alpha_lam, const typename LatT<MIXED>::V* p,
-                             typename LatT<MIXED>::Acc& rr) {
+                             typename LatT<MIXED>::A alpha_lam, typename LatT<MIXED>::A c_prev,
+                             const typename LatT<MIXED>::V* p, typename LatT<MIXED>::Acc& rr,
+                             typename LatT<MIXED>::Acc& r0sum) {
   using T = LatT<MIXED>;
   using C2 = typename T::C2;
   using R = typename T::R;
@@ -425,9 +435,11 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
           rv[mm] = rv[mm] - alpha * qv[mm];
           lv[mm] = lv[mm] + alpha_lam * pv[mm];
         }
+        rv[0] = rv[0] - c_prev;   // the constant-multiplier component measured last pass
         stf<NL, VS>(L.r + o, rv);
         stf<NL, VS>(L.lam + o, lv);
       }
+      acc_add(r0sum, rv[0]);
 #pragma unroll
       for (int mm = 0; mm < NL; ++mm) {
         mad(rr, rv[mm], rv[mm]);
@@ -461,8 +473,8 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
   }
 }
 
-// Column pass: per ki, FFT along j, y_a = sum_b H_ab x_b with H = S^(kappa)^+ (mixed
-// form: packed upper triangle, H_ba = conj H_ab), inverse FFT along j.
+// Column pass: per ki, FFT along j, y = S^(kappa)^+ x (mixed form: from its eigen form,
+// FP64: the full block), inverse FFT along j.
 template <int K, bool MIXED>
 __device__ void columns(const LatCtx<K, MIXED>& L) {
   using C2 = typename LatT<MIXED>::C2;
@@ -480,30 +492,45 @@ __device__ void columns(const LatCtx<K, MIXED>& L) {
     C2* cur = L.bufa;
     const C2* S = L.S + size_t(ki) * NP * N;
     for (int kj = threadIdx.x; kj < N; kj += blockDim.x) {
-      C2 x[C], y[C];
-#pragma unroll
-      for (int b = 0; b < C; ++b) {
-        x[b] = cur[b * N + kj];
-        y[b] = C2{0, 0};
-      }
       if constexpr (MIXED) {
-        int pi = 0;
+        // y = V diag(1/mu) V^H x: t_i = sum_b conj(V_bi) x_b, t_i /= mu_i, y_a = sum_i V_ai t_i;
+        // x and y stream through the shared-memory column, t stays in registers
+        C2 t[C];
 #pragma unroll
-        for (int a = 0; a < C; ++a)
+        for (int i = 0; i < C; ++i) t[i] = C2{0, 0};
+#pragma unroll 1
+        for (int b = 0; b < C; ++b) {
+          const C2 xb = cur[b * N + kj];
 #pragma unroll
-          for (int b = a; b < C; ++b, ++pi) {
-            const C2 h = __ldg(&S[size_t(pi) * N + kj]);
-            cmad(y[a], h, x[b]);
-            if (b != a) cmad_conj(y[b], h, x[a]);
-          }
+          for (int i = 0; i < C; ++i) cmad_conj(t[i], __ldg(&S[size_t(b * C + i) * N + kj]), xb);
+        }
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+          const typename LatT<MIXED>::R d = __ldg(&S[size_t(C * C + i) * N + kj]).x;
+          t[i].x *= d;
+          t[i].y *= d;
+        }
+#pragma unroll 1
+        for (int a = 0; a < C; ++a) {
+          C2 ya = {0, 0};
+#pragma unroll
+          for (int i = 0; i < C; ++i) cmad(ya, __ldg(&S[size_t(a * C + i) * N + kj]), t[i]);
+          cur[a * N + kj] = ya;
+        }
       } else {
+        C2 x[C], y[C];
+#pragma unroll
+        for (int b = 0; b < C; ++b) {
+          x[b] = cur[b * N + kj];
+          y[b] = C2{0, 0};
+        }
 #pragma unroll
         for (int a = 0; a < C; ++a)
 #pragma unroll
           for (int b = 0; b < C; ++b) cmad(y[a], __ldg(&S[size_t(a * C + b) * N + kj]), x[b]);
-      }
 #pragma unroll
-      for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
+        for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
+      }
     }
     __syncthreads();
     xform(L, L.bufa, C, true);
@@ -573,13 +600,6 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ dfl ldx(const float2* p) { return to_dfl(__ldcg(p)); }
 __device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ void acc_add(double& a, double v) { a += v; }
-__device__ __forceinline__ void acc_add(dacc& a, dfl v) {
-  float s, t;
-  two_sum(a.s, v.hi, s, t);
-  a.s = s;
-  a.c += t + v.lo;
-}
 
 // y = (S x)_f: the facet's own block and its four neighbours' (stencil class of f)
 template <int NL, int VS, bool MIXED, typename X, typename XV>
@@ -744,7 +764,9 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   GridBar* bar = m.bar;
   // g from both sides of every facet; warm-started lam
-  const A warm = A(a.warm_scale);
+  const A warm = A(a.warm_scale), hc1 = A(a.c1), hc2 = A(a.c2);
+  V* hist1 = static_cast<V*>(a.hist1);
+  V* hist2 = static_cast<V*>(a.hist2);
   double ga = 0.0;
   Acc g0 = acc_zero(Acc{});
 #pragma unroll 2
@@ -752,10 +774,24 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     const size_t o = size_t(f) * VS;
     A gv[NL], lv[NL];
     facet_g<NL>(m, f, gv);
-    if (a.warm_scale != 0.0) ldf<NL, VS>(L.lam + o, lv);
+    if (hist1) {
+      // extrapolation from the same stage of earlier steps; the history shifts by one
+      A h1[NL];
+      ldf<NL, VS>(hist1 + o, h1);
+      if (a.c2 != 0.0) ldf<NL, VS>(hist2 + o, lv);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) lv[j] = a.c2 != 0.0 ? hc1 * h1[j] + hc2 * lv[j] : hc1 * h1[j];
+      stf<NL, VS>(hist2 + o, h1);
+    } else if (a.warm_scale != 0.0) {
+      ldf<NL, VS>(L.lam + o, lv);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) lv[j] = warm * lv[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) lv[j] = A(0);
+    }
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
-      lv[j] = a.warm_scale == 0.0 ? A(0) : warm * lv[j];
       const double lead = lead_d(gv[j]);
       ga = fma(lead, lead, ga);
     }
@@ -810,10 +846,16 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     }
     if (!grid_sync(bar, m.stats)) return;
     // z = M r
-    Acc rra[1] = {acc_zero(Acc{})};
-    rows_forward<K, MIXED>(L, false, A(0), A(0), p, rra[0]);
-    double rr[1];
-    if (!lat_reduce<1>(m, 6, rra, bar, rr)) return;
+    // The constant multiplier is in the kernel of S and of the preconditioner, so PCG cannot
+    // reduce r's component along it; rounding in every update adds to it (relative size
+    // eps times the cancellation in S q). It is measured with r.r (the sum of the mode-0
+    // entries), left out of the convergence test, and subtracted from r in the next update.
+    Acc rra[2] = {acc_zero(Acc{}), acc_zero(Acc{})};
+    rows_forward<K, MIXED>(L, false, A(0), A(0), A(0), p, rra[0], rra[1]);
+    double rr[2];
+    if (!lat_reduce<2>(m, 6, rra, bar, rr)) return;
+    double cmode = rr[1] / double(nF);
+    rr[0] = fmax(rr[0] - rr[1] * rr[1] / double(nF), 0.0);
     columns<K, MIXED>(L);
     if (!grid_sync(bar, m.stats)) return;
     Acc rza[2] = {acc_zero(Acc{}), acc_zero(Acc{})};
@@ -890,10 +932,12 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
       if (sc.done) break;
       // r -= alpha q, lam += alpha p, and the forward row pass of z = M r
       rra[0] = acc_zero(Acc{});
-      rows_forward<K, MIXED>(L, true, sc.alpha, sc.alpha_lam, p, rra[0]);
-      if (!lat_reduce<1>(m, 6, rra, bar, rr)) return;
+      rra[1] = acc_zero(Acc{});
+      rows_forward<K, MIXED>(L, true, sc.alpha, sc.alpha_lam, A(cmode), p, rra[0], rra[1]);
+      if (!lat_reduce<2>(m, 6, rra, bar, rr)) return;
+      cmode = rr[1] / double(nF);
       const double rr_prev = rrv;
-      rrv = rr[0];
+      rrv = fmax(rr[0] - rr[1] * rr[1] / double(nF), 0.0);
       if (threadIdx.x == 0) {
         sc.done = 0;
         sc.conv = 0;
@@ -989,7 +1033,7 @@ int lattice_group_rows(int k, int N, int fp32) {
 
 size_t lattice_symbol_elems(int k, int N, int fp32) {
   const size_t C = 3 * (k + 1);
-  return size_t(N / 2 + 1) * (fp32 ? C * (C + 1) / 2 : C * C) * N;
+  return size_t(N / 2 + 1) * (fp32 ? C * C + C : C * C) * N;
 }
 
 size_t lattice_spectrum_elems(int k, int N) { return size_t(3 * (k + 1)) * (N / 2 + 1) * N; }

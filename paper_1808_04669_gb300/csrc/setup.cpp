@@ -867,9 +867,78 @@ bool hermitian_inverse(const double* A, int C, double* out, bool pinv) {
   return true;
 }
 
+// Eigen-decomposition of a Hermitian C x C matrix A ([C][C][2]) by cyclic complex Jacobi
+// rotations: A = V diag(ev) V^H with V unitary, V[b][i] = component b of eigenvector i
+// ([C][C][2]). Each rotation first turns A_pq into |A_pq| by a phase on index q, then
+// applies the real rotation that zeros it.
+void hermitian_eig(const double* A0, int C, std::vector<double>& ev, std::vector<double>& V) {
+  std::vector<double> A(A0, A0 + size_t(C) * C * 2);
+  V.assign(size_t(C) * C * 2, 0.0);
+  for (int i = 0; i < C; ++i) V[(size_t(i) * C + i) * 2] = 1.0;
+  auto re = [&](std::vector<double>& M, int i, int j) -> double& { return M[(size_t(i) * C + j) * 2]; };
+  auto im = [&](std::vector<double>& M, int i, int j) -> double& { return M[(size_t(i) * C + j) * 2 + 1]; };
+  double scale = 0.0;
+  for (int i = 0; i < C; ++i) scale = std::max(scale, std::fabs(re(A, i, i)));
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < C; ++i)
+      for (int j = i + 1; j < C; ++j) off += re(A, i, j) * re(A, i, j) + im(A, i, j) * im(A, i, j);
+    if (off <= 1e-64 * scale * scale) break;
+    for (int p = 0; p < C; ++p)
+      for (int q = p + 1; q < C; ++q) {
+        const double br = re(A, p, q), bi = im(A, p, q), bm = std::hypot(br, bi);
+        if (bm <= 1e-300) continue;
+        // phase w = conj(b) / |b| on index q: A_iq *= w, A_qj *= conj(w), V_iq *= w
+        const double wr = br / bm, wi = -bi / bm;
+        for (int i = 0; i < C; ++i) {
+          if (i == q) continue;
+          const double xr = re(A, i, q), xi = im(A, i, q);
+          re(A, i, q) = xr * wr - xi * wi;
+          im(A, i, q) = xr * wi + xi * wr;
+          re(A, q, i) = re(A, i, q);
+          im(A, q, i) = -im(A, i, q);
+        }
+        for (int i = 0; i < C; ++i) {
+          const double xr = re(V, i, q), xi = im(V, i, q);
+          re(V, i, q) = xr * wr - xi * wi;
+          im(V, i, q) = xr * wi + xi * wr;
+        }
+        // real rotation in the (p, q) plane: tan 2t = 2 |b| / (A_qq - A_pp)
+        const double app = re(A, p, p), aqq = re(A, q, q);
+        const double theta = (aqq - app) / (2.0 * bm);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < C; ++k) {   // columns p, q
+          const double pr = re(A, k, p), pi = im(A, k, p), qr = re(A, k, q), qi = im(A, k, q);
+          re(A, k, p) = c * pr - sn * qr;
+          im(A, k, p) = c * pi - sn * qi;
+          re(A, k, q) = sn * pr + c * qr;
+          im(A, k, q) = sn * pi + c * qi;
+        }
+        for (int k = 0; k < C; ++k) {   // rows p, q
+          const double pr = re(A, p, k), pi = im(A, p, k), qr = re(A, q, k), qi = im(A, q, k);
+          re(A, p, k) = c * pr - sn * qr;
+          im(A, p, k) = c * pi - sn * qi;
+          re(A, q, k) = sn * pr + c * qr;
+          im(A, q, k) = sn * pi + c * qi;
+        }
+        for (int k = 0; k < C; ++k) {
+          const double pr = re(V, k, p), pi = im(V, k, p), qr = re(V, k, q), qi = im(V, k, q);
+          re(V, k, p) = c * pr - sn * qr;
+          im(V, k, p) = c * pi - sn * qi;
+          re(V, k, q) = sn * pr + c * qr;
+          im(V, k, q) = sn * pi + c * qi;
+        }
+        re(A, p, q) = im(A, p, q) = re(A, q, p) = im(A, q, p) = 0.0;
+      }
+  }
+  ev.resize(C);
+  for (int i = 0; i < C; ++i) ev[i] = re(A, i, i);
+}
+
 }  // namespace
 
-void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
+void build_lattice(const HostMesh& hm, const double* X, Lattice& L, bool eig_half) {
   L = Lattice();
   const Topology& T = hm.topo;
   const int64_t n = T.n_tri;
@@ -964,12 +1033,14 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
   L.N = N;
   L.ntype = ntype;
   L.C = C;
-  L.sinv.assign(size_t(N) * N * C * C * 2, 0.0);
+  const int NK = N / 2 + 1, NE = C * C + C;
+  if (eig_half) L.seig.assign(size_t(NK) * N * NE * 2, 0.0);
+  else L.sinv.assign(size_t(N) * N * C * C * 2, 0.0);
   const double two_pi = 6.283185307179586476925286766559;
   const std::vector<double>& B = hm.stencil_blocks;
   bool fail = false;
   auto work = [&](int k0, int k1) {
-    std::vector<double> S(size_t(C) * C * 2);
+    std::vector<double> S(size_t(C) * C * 2), ev, V;
     for (int ki = k0; ki < k1; ++ki)
       for (int kj = 0; kj < N; ++kj) {
         std::fill(S.begin(), S.end(), 0.0);
@@ -993,21 +1064,37 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& L) {
                 d[1] += v * cim;
               }
           }
-        double* out = &L.sinv[(size_t(ki) * N + kj) * C * C * 2];
-        if (!hermitian_inverse(S.data(), C, out, ki == 0 && kj == 0)) fail = true;
+        if (!eig_half) {
+          double* out = &L.sinv[(size_t(ki) * N + kj) * C * C * 2];
+          if (!hermitian_inverse(S.data(), C, out, ki == 0 && kj == 0)) fail = true;
+          continue;
+        }
+        // eigen form: V (C x C) then the inverse eigenvalues (0 for the kernel at kappa = 0)
+        hermitian_eig(S.data(), C, ev, V);
+        double emax = 0.0;
+        for (double e : ev) emax = std::max(emax, std::fabs(e));
+        double* out = &L.seig[(size_t(ki) * N + kj) * NE * 2];
+        for (int i = 0; i < C * C * 2; ++i) out[i] = V[i];
+        for (int i = 0; i < C; ++i) {
+          const bool kernel = ki == 0 && kj == 0 && std::fabs(ev[i]) <= 1e-10 * emax;
+          if (!kernel && !(ev[i] > 0.0)) fail = true;
+          out[C * C * 2 + 2 * i] = kernel ? 0.0 : 1.0 / ev[i];
+        }
       }
   };
   unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   if (N < 8) nth = 1;
   std::vector<std::thread> th;
+  const int nki = eig_half ? NK : N;
   for (unsigned i = 0; i < nth; ++i) {
-    const int a = int(int64_t(N) * i / nth), b = int(int64_t(N) * (i + 1) / nth);
+    const int a = int(int64_t(nki) * i / nth), b = int(int64_t(nki) * (i + 1) / nth);
     th.emplace_back(work, a, b);
   }
   for (auto& t : th) t.join();
   if (fail) {
     L.why = "singular Fourier symbol";
     L.sinv.clear();
+    L.seig.clear();
     return;
   }
   L.twiddle.resize(size_t(N) * 2);

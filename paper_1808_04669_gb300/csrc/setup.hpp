@@ -64,6 +64,9 @@ struct Lattice {
   int N = 0, ntype = 0, C = 0; // cells per direction, facet types, components C = ntype * (k+1)
   std::vector<int32_t> facet_of;   // [ntype][N(j)][N(i)] -> facet id
   std::vector<double> sinv;        // [N(ki)][N(kj)][C][C][2] (re, im)
+  // eigen form of the half spectrum (FP32 preconditioner): [N/2+1 (ki)][N (kj)][C*C + C][2]:
+  // V[b][i] (component b of eigenvector i, unitary), then 1/eigenvalue i in the real slots
+  std::vector<double> seig;
   std::vector<double> twiddle;     // [N][2] exp(-2 pi i t / N)
 };
 
@@ -98,7 +101,8 @@ int build_reference(int k, RefTables& ref, std::string& err);
 int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha,
                     HostMesh& hm, std::string& err);
 // Detects the split-square lattice structure and computes the inverse Fourier symbol.
-void build_lattice(const HostMesh& hm, const double* X, Lattice& lat);
+// eig_half: the eigen form of the half spectrum (seig) instead of the full inverse (sinv).
+void build_lattice(const HostMesh& hm, const double* X, Lattice& lat, bool eig_half = false);
 // Renumbers the facets of a lattice mesh internally in (type, j, i) order, so that the
 // facet-major vectors are the Fourier passes' row order; records the external ids.
 void renumber_facets_lattice(HostMesh& hm, Lattice& lat);
