@@ -158,16 +158,18 @@ def lattice_solver_bytes(n_facet, k, iters, solves):
     """Algorithmic DRAM bytes of the mixed-form lattice (Fourier-preconditioned) facet solves.
 
     Vectors are double-float (8 B per DOF), z is FP32 (4 B); the spectrum holds half the
-    wavenumbers (4 B per DOF per pass) and the packed FP32 symbol 2(C+1) B per DOF, C = 3(k+1).
-    Per DOF and CG iteration: SpMV pass 36 B (read z, p, q; write p, q); update + forward rows
-    52 B (read r, q, lam, p; write r, lam, spectrum); columns 8 B + symbol; inverse rows 20 B
-    (read spectrum, r, z_old; write z); plus 20 B of stencil ids per facet. Per solve: g assembly,
-    the first residual and one more preconditioner application, 108 B + symbol per DOF.
+    wavenumbers (4 B per DOF per pass) and the FP32 eigen-form symbol 4(C+1) B per DOF,
+    C = 3(k+1). Per DOF and CG iteration: SpMV pass 36 B (read z, p, q; write p, q); update +
+    forward rows 52 B (read r, q, lam, p; write r, lam, spectrum); columns 8 B + symbol; inverse
+    rows 20 B (read spectrum, r, z_old; write z); plus 20 B of stencil ids per facet. Per solve:
+    g assembly with the warm-start history (read two entries, shift one), the first residual and
+    one more preconditioner application, 124 B + symbol per DOF; the new multipliers are copied
+    into the history, 16 B per DOF.
     """
     nl = n_facet * (k + 1)
-    sym = 2 * (3 * (k + 1) + 1)
+    sym = 4 * (3 * (k + 1) + 1)
     per_iter = nl * (36 + 52 + 8 + sym + 20) + 20 * n_facet
-    per_solve = nl * (108 + sym) + 20 * n_facet
+    per_solve = nl * (124 + 16 + sym) + 20 * n_facet
     return iters * per_iter + solves * per_solve
 
 
