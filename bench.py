@@ -141,15 +141,18 @@ def element_kernel_sha():
     return h.hexdigest()[:16]
 
 
-def stage_flops_per_triangle(k):
+def stage_flops_per_triangle(k, tabulated=True):
     """Flops of the stage kernel per triangle (FMA = 2), counted from its loops:
-    the volume rule has 3, 7, 16 points for k = 1, 2, 3 (fully symmetric, degree 3k - 1)."""
+    the volume rule has 3, 7, 16 points for k = 1, 2, 3 (fully symmetric, degree 3k - 1). With
+    `tabulated` (meshes of at most 4 geometry classes, mixed form) the facet normal derivatives
+    of the basis come from per-class tables: two sums per trace and per test instead of three."""
     ns = (k + 1) * (k + 2) // 2
     nd = 2 * ns
     nq = {1: 3, 2: 7, 3: 16}[k]
     nqf = (3 * k + 2) // 2
     vol = nq * (2 * (6 * ns + 4 * ns) + 40)              # trace/gradient sums, flux, test sums
-    fac = 3 * nqf * (2 * (12 * ns + 6 * ns) + 30)         # both traces + normal derivatives, flux, test sums
+    per_pt = (8 * ns + 4 * ns) if tabulated else (12 * ns + 6 * ns)
+    fac = 3 * nqf * (2 * per_pt + 30)                      # both traces, flux, test sums
     out = 3 * nd + 2 * nd * nd + 2 * 3 * (k + 1) * nd    # stage combination, P f, G f
     return vol + fac + out
 
@@ -309,7 +312,7 @@ def run_ours(args):
     traffic = None
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     if name.startswith("stage_residual"):
-        flops = stage_flops_per_triangle(k) * mixed.n_tri
+        flops = stage_flops_per_triangle(k, tabulated=mixed.n_class <= 4) * mixed.n_tri
         achieved = flops / per_launch_s / 1e12
         peak = dfl_peak_tflops(sm_mhz)
         tr = NCU_TRAFFIC.get("stage_residual")

@@ -358,6 +358,24 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = upload(M, &d.st_binv, hm.stencil_binv)) || (rc = upload(M, &d.st_blk_f, to_float(hm.stencil_blocks))) ||
       (rc = upload(M, &d.st_binv_f, to_float(hm.stencil_binv))))
     return cleanup(rc);
+  if (d.elem_df && d.n_class <= dgdf::kDnClasses) {
+    // normal derivatives of the basis at the facet points, per class
+    const int nqf = ref.nqf, ns = hm.ns;
+    std::vector<double> dn(size_t(d.n_class) * 3 * nqf * ns);
+    for (int c = 0; c < d.n_class; ++c) {
+      const dgdf::ClassOps& co = hm.classes[c];
+      for (int e = 0; e < 3; ++e) {
+        const double m0 = co.Jinv[0] * co.normal[e][0] + co.Jinv[1] * co.normal[e][1];
+        const double m1 = co.Jinv[2] * co.normal[e][0] + co.Jinv[3] * co.normal[e][1];
+        for (int q = 0; q < nqf; ++q)
+          for (int j = 0; j < ns; ++j) {
+            const double* g = &ref.fdphi[((size_t(e) * nqf + q) * ns + j) * 2];
+            dn[((size_t(c) * 3 + e) * nqf + q) * ns + j] = g[0] * m0 + g[1] * m1;
+          }
+      }
+    }
+    if ((rc = upload(M, &d.dn_df, to_dfloat(dn)))) return cleanup(rc);
+  }
   if (d.elem_df) {
     // reference tables in the field order of the kernels' shared-memory image
     std::vector<double> tab;

@@ -56,6 +56,9 @@ struct DevMesh {
   // double-float images (mixed form): reference tables in SmemTables order, class
   // geometry [n_class][kGeo], penalty per facet
   const float2 *tab_df, *geo_df, *sigma_df;
+  // meshes with at most kDnClasses geometry classes: normal derivatives of the basis at the
+  // facet points per class, fdphi . (Jinv n_e), [n_class][3][nqf][ns] (NULL otherwise)
+  const float2* dn_df;
   // facet-system stencil
   const int32_t *facet_nbr, *facet_stencil, *facet_tri;
   const int32_t *facet_ext;           // internal -> external facet id (NULL: identity)
@@ -91,6 +94,7 @@ struct DevMesh {
 };
 
 constexpr int kRedSlots = 8;
+constexpr int kDnClasses = 4;
 constexpr int kMaxSolverBlocks = 2048;
 
 // Stage kernel modes.

@@ -36,14 +36,25 @@ __device__ __forceinline__ void load_df(const float2* __restrict__ p, dfl (&c)[N
 // upwind flux (u.n) u_c^up with u.n the average of both traces, and the SIPG
 // consistency, symmetry and penalty terms, at the facet Gauss points (the
 // neighbour's point q is our point NQF-1-q).
+// Normal derivatives of the basis at the facet points per geometry class, dfl image of
+// m.dn_df (meshes with few classes).
 template <int K>
-__device__ __forceinline__ void residual_component(const DevMesh& m, const SmemTables<K, dfl>& T, int t, int c,
+struct DnTable {
+  dfl v[kDnClasses][3][Dims<K>::NQF][Dims<K>::NS];
+};
+
+// TAB: facet normal derivatives from the per-class table (two sums per trace instead of
+// three, and one instead of two for the test derivative).
+template <int K, bool TAB>
+__device__ __forceinline__ void residual_component(const DevMesh& m, const SmemTables<K, dfl>& T,
+                                                   const DnTable<K>& DN, int t, int c,
                                                    const float2* __restrict__ ug, const dfl (&up)[Dims<K>::NS],
                                                    dacc (&acc)[Dims<K>::NS]) {
   using D = Dims<K>;
   constexpr int NS = D::NS, ND = D::ND;
   const dfl nu(m.nu);
-  const float2* geo = m.geo_df + size_t(__ldg(&m.tri_class[t])) * kGeo;
+  const int cls = __ldg(&m.tri_class[t]);
+  const float2* geo = m.geo_df + size_t(cls) * kGeo;
   const dfl Ji0 = to_dfl(geo[G_JINV + 0]), Ji1 = to_dfl(geo[G_JINV + 1]);
   const dfl Ji2 = to_dfl(geo[G_JINV + 2]), Ji3 = to_dfl(geo[G_JINV + 3]);
   const dfl s = to_dfl(geo[G_S]);
@@ -78,19 +89,52 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
   for (int e = 0; e < 3; ++e) {
     const int tn = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
     const int en = __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
-    const float2* geon = m.geo_df + size_t(__ldg(&m.tri_class[tn])) * kGeo;
+    const int ncls = __ldg(&m.tri_class[tn]);
+    const float2* geon = m.geo_df + size_t(ncls) * kGeo;
     const dfl sn = to_dfl(geon[G_S]);
     const dfl n0 = to_dfl(geo[G_NRM + 2 * e]), n1 = to_dfl(geo[G_NRM + 2 * e + 1]);
     const dfl nc = c ? n1 : n0;
     const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
     const dfl sig = to_dfl(m.sigma_df[__ldg(&m.tri_facet[size_t(t) * 3 + e])]);
     const dfl nusig = nu * sig, hnu = half(nu);
+    dfl un[NS];
+    load_df<NS>(ug + size_t(tn) * ND + c * NS, un);
+    if constexpr (TAB) {
+      // the neighbour's table holds derivatives along its own outward normal, -n
+      const dfl msn = -sn;
+#pragma unroll 1
+      for (int q = 0; q < D::NQF; ++q) {
+        const int qn = D::NQF - 1 - q;
+        dacc V = dacc_zero(), Dd = dacc_zero(), Vn = dacc_zero(), Dnd = dacc_zero();
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          mad(V, T.fphi[e][q][j], up[j]);
+          mad(Dd, DN.v[cls][e][q][j], up[j]);
+          mad(Vn, T.fphi[en][qn][j], un[j]);
+          mad(Dnd, DN.v[ncls][en][qn][j], un[j]);
+        }
+        const dfl ui = s * val(V), di = s * val(Dd);
+        const dfl uo = sn * val(Vn), dn = msn * val(Dnd);
+        // u.n = 1/2 (u_in + u_out) . n, summed in the same order by both threads of the pair
+        const dfl pc = (ui + uo) * nc, po = shfl_pair(pc);
+        const dfl vn = half(c ? po + pc : pc + po);
+        const dfl wup = vn >= dfl(0) ? ui : uo;
+        const dfl jc = ui - uo;
+        const dfl w = T.fw[q] * lens;
+        const dfl A = w * (hnu * (di + dn) - vn * wup - nusig * jc);
+        const dfl B = w * hnu * jc;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          mad(acc[j], A, T.fphi[e][q][j]);
+          mad(acc[j], B, DN.v[cls][e][q][j]);
+        }
+      }
+      continue;
+    }
     // normal derivative in reference gradients: d_n psi = s sum_r d_r psihat (Jinv n)_r
     const dfl mo0 = Ji0 * n0 + Ji1 * n1, mo1 = Ji2 * n0 + Ji3 * n1;
     const dfl mn0 = to_dfl(geon[G_JINV + 0]) * n0 + to_dfl(geon[G_JINV + 1]) * n1;
     const dfl mn1 = to_dfl(geon[G_JINV + 2]) * n0 + to_dfl(geon[G_JINV + 3]) * n1;
-    dfl un[NS];
-    load_df<NS>(ug + size_t(tn) * ND + c * NS, un);
 #pragma unroll 1
     for (int q = 0; q < D::NQF; ++q) {
       const int qn = D::NQF - 1 - q;
@@ -131,12 +175,17 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
 // MODE_PROJECT), h = f in FP64 (MODE_RESIDUAL, MODE_PRESSURE) and gl_df
 // (MODE_PRESSURE). Thread c of a pair owns rows c*NS.. of f and h, and the rows
 // i = c (mod 2) of gl.
-template <int K>
+template <int K, bool TAB>
 __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, StageArgs a) {
   using D = Dims<K>;
   constexpr int NS = D::NS, ND = D::ND, L3 = 3 * D::NL;
   __shared__ SmemTables<K, dfl> T;
+  __shared__ DnTable<K> DN;
   load_tables_df<K>(m, T);
+  if constexpr (TAB) {
+    const int nw = m.n_class * 3 * D::NQF * NS;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) (&DN.v[0][0][0][0])[i] = to_dfl(m.dn_df[i]);
+  }
   __syncthreads();
   const int c = threadIdx.x & 1;
   const int traw = blockIdx.x * (kStageDfThreads / 2) + (threadIdx.x >> 1);
@@ -152,7 +201,7 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, Stag
     dacc acc[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) acc[j] = dacc_zero();
-    residual_component<K>(m, T, t, c, a.up_df, up, acc);
+    residual_component<K, TAB>(m, T, DN, t, c, a.up_df, up, acc);
     if (a.mode == MODE_STAGE) {
       dfl un[NS];
       load_df<NS>(a.un_df + size_t(t) * ND + c * NS, un);
@@ -270,7 +319,11 @@ inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
 cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
   if (!a.up_df || (a.mode == MODE_STAGE && !a.un_df)) return cudaErrorInvalidValue;
   const int nb = blocks_for(m.n_tri, kStageDfThreads / 2);
-  DGDF_DISPATCH_K(m.k, (k_stage_df<K><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+  if (m.dn_df) {
+    DGDF_DISPATCH_K(m.k, (k_stage_df<K, true><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+  } else {
+    DGDF_DISPATCH_K(m.k, (k_stage_df<K, false><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+  }
   return cudaGetLastError();
 }
 
