@@ -161,7 +161,8 @@ def lattice_solver_bytes(n_facet, k, iters, solves):
     """Algorithmic DRAM bytes of the mixed-form lattice (Fourier-preconditioned) facet solves.
 
     Vectors are double-float (8 B per DOF), z is FP32 (4 B); the spectrum holds half the
-    wavenumbers (4 B per DOF per pass) and the FP32 eigen-form symbol 4(C+1) B per DOF,
+    wavenumbers (4 B per DOF per pass) and the FP32 deflated eigen form of the symbol
+    (C + 1 + C(C+1)/2 complex entries per wavenumber: 4 (C + 1 + C(C+1)/2) / C B per DOF),
     C = 3(k+1). Per DOF and CG iteration: SpMV pass 36 B (read z, p, q; write p, q); update +
     forward rows 52 B (read r, q, lam, p; write r, lam, spectrum); columns 8 B + symbol; inverse
     rows 20 B (read spectrum, r, z_old; write z); plus 20 B of stencil ids per facet. Per solve:
@@ -170,7 +171,8 @@ def lattice_solver_bytes(n_facet, k, iters, solves):
     into the history, 16 B per DOF.
     """
     nl = n_facet * (k + 1)
-    sym = 4 * (3 * (k + 1) + 1)
+    C = 3 * (k + 1)
+    sym = 4 * (C + 1 + C * (C + 1) // 2) / C
     per_iter = nl * (36 + 52 + 8 + sym + 20) + 20 * n_facet
     per_solve = nl * (124 + 16 + sym) + 20 * n_facet
     return iters * per_iter + solves * per_solve

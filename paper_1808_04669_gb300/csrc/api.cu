@@ -415,25 +415,55 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     const int C = lat.C, N = lat.N;
     // device layout [ki < N/2+1][entry][kj] complex: the residual is real, so only half the
     // wavenumbers along i are needed.
-    //  FP32: the eigen form of each Hermitian block, entries V[b][i] (b, i < C) then 1/mu_i
-    //        (real): applied as V diag(1/mu) V^H, every eigen-component keeps its FP32
-    //        relative accuracy (the explicit inverse loses it to cancellation in the
-    //        near-singular blocks at small kappa);
+    //  FP32: the deflated eigen form of each Hermitian block: the eigen-pair of its largest
+    //        eigenvalue (v1, 1/mu1), then the packed upper triangle of the rest. The one
+    //        near-singular direction of the symbol at small kappa is applied on its own,
+    //        so no cancellation happens in FP32; the explicit inverse rounded to FP32 loses
+    //        accuracy there;
     //  FP64: all C*C entries of the inverse, the self-conjugate columns ki = 0 and ki = N/2
     //        symmetrised (the half-spectrum transform takes S^(-kappa) = conj S^(kappa) for
     //        granted, and the host inverts each wavenumber on its own).
-    const int NK = N / 2 + 1, NP = fp32 ? C * C + C : C * C;
+    const int NK = N / 2 + 1, NP = fp32 ? C + 1 + C * (C + 1) / 2 : C * C;
     const size_t nS = dgdf::lattice_symbol_elems(hm.k, N, fp32);
     std::vector<double> sd;
     std::vector<float> sf;
     if (fp32) {
+      // deflated eigen form: the dominant pair (v1, 1/mu1) of the inverse, kept apart, and
+      // the packed upper triangle of the remainder sum_{i != 1} v_i v_i^H / mu_i (cond ~ 10)
       sf.resize(2 * nS);
+      const int NE = C * C + C;
+      std::vector<double> Hr(size_t(C) * C * 2);
       for (int ki = 0; ki < NK; ++ki)
-        for (int kj = 0; kj < N; ++kj)
-          for (int e = 0; e < NP; ++e)
-            for (int ri = 0; ri < 2; ++ri)
-              sf[((size_t(ki) * NP + e) * N + kj) * 2 + ri] =
-                  float(lat.seig[((size_t(ki) * N + kj) * NP + e) * 2 + ri]);
+        for (int kj = 0; kj < N; ++kj) {
+          const double* E = &lat.seig[(size_t(ki) * N + kj) * NE * 2];
+          auto V = [&](int b, int i, int ri) { return E[(b * C + i) * 2 + ri]; };
+          auto dinv = [&](int i) { return E[(C * C + i) * 2]; };
+          int i1 = 0;
+          for (int i = 1; i < C; ++i)
+            if (dinv(i) > dinv(i1)) i1 = i;
+          std::fill(Hr.begin(), Hr.end(), 0.0);
+          for (int i = 0; i < C; ++i) {
+            if (i == i1) continue;
+            for (int ca = 0; ca < C; ++ca)
+              for (int cb = 0; cb < C; ++cb) {
+                // V_ai conj(V_bi) d_i
+                const double ar = V(ca, i, 0), ai = V(ca, i, 1), br = V(cb, i, 0), bi = V(cb, i, 1);
+                Hr[(ca * C + cb) * 2] += dinv(i) * (ar * br + ai * bi);
+                Hr[(ca * C + cb) * 2 + 1] += dinv(i) * (ai * br - ar * bi);
+              }
+          }
+          auto put = [&](int e, double re, double im) {
+            const size_t o = ((size_t(ki) * NP + e) * N + kj) * 2;
+            sf[o] = float(re);
+            sf[o + 1] = float(im);
+          };
+          for (int b = 0; b < C; ++b) put(b, V(b, i1, 0), V(b, i1, 1));
+          put(C, dinv(i1), 0.0);
+          int pi = C + 1;
+          for (int ca = 0; ca < C; ++ca)
+            for (int cb = ca; cb < C; ++cb, ++pi)
+              put(pi, Hr[(ca * C + cb) * 2], ca == cb ? 0.0 : Hr[(ca * C + cb) * 2 + 1]);
+        }
     } else {
       sd.resize(2 * nS);
       auto H = [&](int ki, int kj, int ca, int cb, int ri) {

@@ -12,9 +12,9 @@
 // The residual is real, so only the wavenumbers ki in [0, N/2] are transformed:
 //   rows   : two facet rows j, j+1 packed as one complex row, FFT along i, split
 //            into the two half spectra (Hermitian symmetry)
-//   columns: per ki, FFT along j, multiply by S^(kappa)^+ (FP32: from its eigen form
-//            V diag(1/mu) V^H, accurate to FP32 in every eigen-component), inverse FFT
-//            along j
+//   columns: per ki, FFT along j, multiply by S^(kappa)^+ (FP32: its near-singular
+//            eigen-direction applied on its own plus the packed Hermitian remainder, so
+//            FP32 rounding causes no cancellation), inverse FFT along j
 //   rows   : inverse FFT along i of two rows packed the same way (scaled 1/N^2)
 // with a grid barrier between the passes. Transforms run in shared memory: for N a
 // power of two up to 1024 (FP32) / 256 (FP64) a two-pass FFT whose radix-sqrt(N)
@@ -249,9 +249,10 @@ struct LatCtx {
   // facet stride of the solver vectors: padded to 4 for k = 2 in the mixed form, so that
   // every facet's values are one aligned 16- or 32-byte access
   static constexpr int VS = (MIXED && NL == 3) ? 4 : NL;
-  // stored entries per wavenumber: FP32, the eigen form (unitary V, C x C, then the C
-  // inverse eigenvalues); FP64, the full inverse block
-  static constexpr int NP = MIXED ? C * C + C : C * C;
+  // stored entries per wavenumber: FP32, the deflated eigen form (the eigenvector v1 of the
+  // largest inverse eigenvalue, that eigenvalue, the packed upper triangle of the rest);
+  // FP64, the full inverse block
+  static constexpr int NP = MIXED ? C + 1 + C * (C + 1) / 2 : C * C;
   int N, logn, NK, ntj;   // NK = N/2 + 1 wavenumbers ki; ntj row tiles per facet type
   int grp;                // rows transformed at a time (the scratch holds grp rows)
   bool pow2;              // FFT (N a power of two) or direct DFT
@@ -473,8 +474,8 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
   }
 }
 
-// Column pass: per ki, FFT along j, y = S^(kappa)^+ x (mixed form: from its eigen form,
-// FP64: the full block), inverse FFT along j.
+// Column pass: per ki, FFT along j, y = S^(kappa)^+ x (mixed form: from its deflated eigen
+// form, FP64: the full block), inverse FFT along j.
 template <int K, bool MIXED>
 __device__ void columns(const LatCtx<K, MIXED>& L) {
   using C2 = typename LatT<MIXED>::C2;
@@ -493,30 +494,30 @@ __device__ void columns(const LatCtx<K, MIXED>& L) {
     const C2* S = L.S + size_t(ki) * NP * N;
     for (int kj = threadIdx.x; kj < N; kj += blockDim.x) {
       if constexpr (MIXED) {
-        // y = V diag(1/mu) V^H x: t_i = sum_b conj(V_bi) x_b, t_i /= mu_i, y_a = sum_i V_ai t_i;
-        // x and y stream through the shared-memory column, t stays in registers
-        C2 t[C];
+        // y = v1 (v1^H x) / mu1 + R x, R the packed Hermitian remainder (R_ba = conj R_ab)
+        C2 x[C], y[C];
+        C2 s1 = {0, 0};
 #pragma unroll
-        for (int i = 0; i < C; ++i) t[i] = C2{0, 0};
-#pragma unroll 1
         for (int b = 0; b < C; ++b) {
-          const C2 xb = cur[b * N + kj];
-#pragma unroll
-          for (int i = 0; i < C; ++i) cmad_conj(t[i], __ldg(&S[size_t(b * C + i) * N + kj]), xb);
+          x[b] = cur[b * N + kj];
+          cmad_conj(s1, __ldg(&S[size_t(b) * N + kj]), x[b]);
         }
+        const typename LatT<MIXED>::R d1 = __ldg(&S[size_t(C) * N + kj]).x;
+        s1.x *= d1;
+        s1.y *= d1;
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-          const typename LatT<MIXED>::R d = __ldg(&S[size_t(C * C + i) * N + kj]).x;
-          t[i].x *= d;
-          t[i].y *= d;
-        }
-#pragma unroll 1
-        for (int a = 0; a < C; ++a) {
-          C2 ya = {0, 0};
+        for (int a = 0; a < C; ++a) y[a] = cmul(__ldg(&S[size_t(a) * N + kj]), s1);
+        int pi = C + 1;
 #pragma unroll
-          for (int i = 0; i < C; ++i) cmad(ya, __ldg(&S[size_t(a * C + i) * N + kj]), t[i]);
-          cur[a * N + kj] = ya;
-        }
+        for (int a = 0; a < C; ++a)
+#pragma unroll
+          for (int b = a; b < C; ++b, ++pi) {
+            const C2 h = __ldg(&S[size_t(pi) * N + kj]);
+            cmad(y[a], h, x[b]);
+            if (b != a) cmad_conj(y[b], h, x[a]);
+          }
+#pragma unroll
+        for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
       } else {
         C2 x[C], y[C];
 #pragma unroll
@@ -1033,7 +1034,7 @@ int lattice_group_rows(int k, int N, int fp32) {
 
 size_t lattice_symbol_elems(int k, int N, int fp32) {
   const size_t C = 3 * (k + 1);
-  return size_t(N / 2 + 1) * (fp32 ? C * C + C : C * C) * N;
+  return size_t(N / 2 + 1) * (fp32 ? C + 1 + C * (C + 1) / 2 : C * C) * N;
 }
 
 size_t lattice_spectrum_elems(int k, int N) { return size_t(3 * (k + 1)) * (N / 2 + 1) * N; }
