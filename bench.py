@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 # over the three stages of a step (the first stage reads one state, the others two), from the
 # ncu capture summarised in profiles/; used only while the stage-kernel sources still hash to
 # the captured `sha`, else the line reports null.
-NCU_TRAFFIC = {"stage_residual": {"sha": "4ff6b630c4472b56", "n_tri": 131072, "bytes": 42661973,
+NCU_TRAFFIC = {"stage_residual": {"sha": "bdf1e9622a4f6c49", "n_tri": 131072, "bytes": 41033984,
                                   "source": "profiles/k_stage_df_shear_n256_k3.md"}}
 
 
