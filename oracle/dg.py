@@ -460,6 +460,30 @@ class Discretization:
             U = self.stage(U, U2, *RK3_STAGES[2], dt)
         return U
 
+    def slope(self, U):
+        """Time derivative of the semi-discrete system eq. (6) on V_h^{k,-1}: the hybrid-mixed
+        solve of eq. (12) with the functional L(u) alone (the mass inversion of Sec. 3.1)."""
+        du, _, _ = self.solve_condensed(self.residual(U))
+        return du
+
+    def euler_step(self, U, dt, nsteps=1):
+        """Forward Euler, eq. (FE) of Sec. 3.1, with the full L of eq. (6) (viscous terms
+        included): M u^(n+1) = M u^n + dt L(u^n), one hybrid-mixed solve per step."""
+        for _ in range(int(nsteps)):
+            U, _, _ = self.solve_condensed(self.apply_mass(U) + dt * self.residual(U))
+        return U
+
+    def rk4_step(self, U, dt, nsteps=1):
+        """The classical four-stage, fourth-order Runge-Kutta scheme used for the temporal
+        accuracy test (Example 1b, Table 2), applied to du/dt = slope(u)."""
+        for _ in range(int(nsteps)):
+            k1 = self.slope(U)
+            k2 = self.slope(U + 0.5 * dt * k1)
+            k3 = self.slope(U + 0.5 * dt * k2)
+            k4 = self.slope(U + dt * k3)
+            U = U + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        return U
+
     def pressure(self, U):
         """(w, lam) of eq. (12) with the functional L(u) alone: w ~ p, lam ~ p on the skeleton (Theorem 2, Remark 2)."""
         _, w, lam = self.solve_condensed(self.residual(U))

@@ -300,6 +300,40 @@ def test_rk3_is_third_order_in_time():
     assert all(abs(b - 3.0) < 0.05 for b in tab)
 
 
+def _time_order(step, n_list, ref, U0, d, T):
+    e = [np.sqrt(d.energy(step(U0, T / n, n) - ref)) for n in n_list]
+    return [math.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)], e
+
+
+def test_rk4_is_fourth_order_and_euler_first_order_in_time():
+    # Table 2 (RK4 eoc 4) and eq. (FE): errors against a fine-step solution of the same
+    # semi-discrete system on a fixed mesh. The upwind flux makes L(u) only piecewise smooth
+    # (|u.n| has a kink where u.n changes sign), which blurs the observed orders; a strong mean
+    # flow (4, 2) keeps u.n sign-definite on every facet of the split-square mesh, so L is
+    # smooth along the trajectory. The fine RK4 and RK3 solutions must agree (the two schemes
+    # converge to one ODE solution), so a wrong RK4 stage weight cannot hide.
+    d, X = disc(4, 2, nu=1e-2)
+    U0 = projected(d, X, synth.advected_taylor_green((4.0, 2.0), nu=1e-2))
+    T = 0.4
+    ref = d.rk4_step(U0, T / 256, 256)
+    ref3 = d.rk3_step(U0, T / 1024, 1024)
+    assert np.sqrt(d.energy(ref - ref3)) < 1e-9 * np.sqrt(d.energy(ref))
+    eoc4, _ = _time_order(d.rk4_step, (8, 16, 32), ref, U0, d, T)
+    assert all(abs(a - 4.0) < 0.1 for a in eoc4), eoc4
+    eoc1, _ = _time_order(d.euler_step, (64, 128, 256), ref, U0, d, T)
+    assert all(abs(a - 1.0) < 0.05 for a in eoc1), eoc1
+    tab = [r[2] for r in load_golden("table2_eoc.txt")]
+    assert all(abs(b - 4.0) < 0.05 for b in tab)
+
+
+def test_euler_step_is_one_solve_of_the_stage_form():
+    # eq. (FE) is the first SSP-RK3 stage (a = 0, b = 1) of eq. (8) taken as the whole step
+    d, X = disc(3, 2, nu=1e-2)
+    U = projected(d, X, synth.advected_taylor_green((0.3, -0.7), nu=1e-2))
+    a, b = 0.0, 1.0
+    assert np.abs(d.euler_step(U, 0.05) - d.stage(U, U, a, b, 0.05)).max() < 1e-14 * np.abs(U).max()
+
+
 def test_euler_energy_non_increasing():
     # Sec. 2.2: with nu = 0 and upwinding the discrete energy does not grow
     vid, X = synth.split_square_mesh(6, L=1.0)
