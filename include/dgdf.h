@@ -74,6 +74,8 @@ typedef enum {
 
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
 enum { DG_PRECOND_AUTO = 0, DG_PRECOND_BLOCK_JACOBI = 1 };
+/* explicit time-stepping schemes of dg_step */
+enum { DG_SCHEME_SSPRK3 = 0, DG_SCHEME_EULER = 1, DG_SCHEME_RK4 = 2 };
 
 typedef struct {
   int k;              /* polynomial degree, 1 <= k <= 3 */
@@ -122,13 +124,26 @@ int dg_project_divfree(dg_mesh* mesh);
 /* nsteps >= 0 steps of SSP-RK3 (eq. (8)) with the fixed step dt > 0. Each stage
  * forms F = a M u^n + b [M u' + dt L(u')] and solves eq. (12) for the next
  * stage velocity. With DG_PRECISION_MIXED the facet system of each stage is
- * solved with FP32 preconditioning and FP64 residuals: FP32 PCG inside FP64
- * iterative refinement (block Jacobi), or FP64 PCG with the FP32 Fourier-space
- * preconditioner (lattice meshes), to the same cg_rtol; element residual,
- * condensation and recovery stay in FP64 in both forms.
+ * solved with FP32 preconditioning: FP32 PCG inside FP64 iterative refinement
+ * (block Jacobi), or PCG on double-float vectors with the FP32 Fourier-space
+ * preconditioner (lattice meshes), to the same cg_rtol; the element residual,
+ * condensation and recovery run in double-float arithmetic (FP32 pairs, about
+ * 48 significant bits) in the mixed form and in FP64 in the FP64 form.
  * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
- * a residual norm became NaN/Inf (the state is then undefined). */
+ * a residual norm became NaN/Inf (the state is then undefined).
+ * Same as dg_step(mesh, DG_SCHEME_SSPRK3, dt, nsteps). */
 int dg_rk3_step(dg_mesh* mesh, double dt, int64_t nsteps);
+
+/* nsteps >= 0 steps of an explicit scheme with the fixed step dt > 0, each stage a
+ * hybrid-mixed solve of eq. (12) with F = a M x + b M u' + c dt L(u'):
+ *   DG_SCHEME_SSPRK3  SSP-RK3 of eq. (8) (three stages);
+ *   DG_SCHEME_EULER   forward Euler, eq. (FE) of Sec. 3.1 with the full L (one stage);
+ *   DG_SCHEME_RK4     classical four-stage RK4 of Example 1b (Table 2): stages
+ *                     u_i = u^n + (dt/2, dt/2, dt) Q L(u_(i-1)), then
+ *                     u^(n+1) = W + u_3 / 3 + dt/6 Q L(u_3), W = (-u^n + u_1 + 2 u_2) / 3,
+ *                     Q the hybrid-mixed solve; the first RK4 step allocates W (one state).
+ * Errors: DG_ERR_INVALID_ARG (unknown scheme, dt, nsteps), otherwise as dg_rk3_step. */
+int dg_step(dg_mesh* mesh, int scheme, double dt, int64_t nsteps);
 
 /* State as coefficients in the library's orthonormal basis (per triangle: 2 x n_lat(k)
  * scalar Dubiner polynomials scaled to unit L2 norm on the triangle; component-major,

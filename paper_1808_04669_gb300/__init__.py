@@ -14,6 +14,10 @@ from ._native import DGError, DGParams, check, lib
 
 FP64 = 0
 MIXED = 1
+# explicit schemes of DGMesh.step
+SSPRK3 = 0
+EULER = 1
+RK4 = 2
 PRECOND_AUTO = 0
 PRECOND_BLOCK_JACOBI = 1
 
@@ -100,6 +104,10 @@ class DGMesh:
 
     def rk3_step(self, dt, nsteps=1):
         check(lib().dg_rk3_step(self._h, float(dt), int(nsteps)), "dg_rk3_step")
+
+    def step(self, dt, nsteps=1, scheme=SSPRK3):
+        """nsteps steps of SSPRK3, EULER or RK4 (dg_step)."""
+        check(lib().dg_step(self._h, int(scheme), float(dt), int(nsteps)), "dg_step")
 
     def get_pressure(self, with_facet=True, out=None):
         if out is None:

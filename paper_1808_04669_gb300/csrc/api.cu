@@ -40,12 +40,14 @@ enum KernelClass {
   KC_SOLVE_LAT64,
   KC_SOLVE_LAT32,
   KC_ADJOINT,
+  KC_COMBINE,
   KC_COUNT
 };
 const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure",
-                                      "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32",   "adjoint"};
+                                      "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32",   "adjoint",
+                                      "combine"};
 
 }  // namespace
 
@@ -59,14 +61,20 @@ struct dg_mesh {
   bool use_lattice = false;
   int lattice_blocks = 0;
   std::string lattice_why;
-  double last_bdt = 0.0;
+  double last_c = 0.0;            // coefficient of L(u') in the last stage solved
   bool has_lam = false;
-  // lattice solver: multipliers of each RK stage in the last two steps (device, the layout of
-  // the solver's lam), their step sizes, and how many are valid
-  void* hist[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-  double hist_dt[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  int hist_n[3] = {0, 0, 0};
+  // lattice solver: multipliers of each stage of the current scheme in the last two steps
+  // (device, the layout of the solver's lam), their step sizes, and how many are valid
+  static constexpr int kMaxStages = 4;
+  void* hist[kMaxStages][2] = {};
+  double hist_dt[kMaxStages][2] = {};
+  int hist_n[kMaxStages] = {};
+  int hist_scheme = -1;           // the scheme the history belongs to
   size_t hist_bytes = 0;
+  // classical RK4: the running combination of the stage states (FP64 form, or its
+  // double-float twin in the mixed form), allocated at the first RK4 step
+  double* rk_w = nullptr;
+  float2* rk_w_df = nullptr;
   bool udf_valid = false;        // mixed form: u_df holds the double-float image of u
   double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
   double* wbuf = nullptr;        // [n_tri][nw] element pressure
@@ -113,6 +121,16 @@ int upload(dg_mesh* M, const T** out, const std::vector<T>& v) {
   int rc = dalloc(M, &p, v.size());
   if (rc) return rc;
   if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = p;
+  return DG_OK;
+}
+
+// a float vector (a multiple of 4 long) as float4 words
+int upload_f4(dg_mesh* M, const float4** out, const std::vector<float>& v) {
+  float4* p = nullptr;
+  int rc = dalloc(M, &p, v.size() / 4);
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
   *out = p;
   return DG_OK;
 }
@@ -200,7 +218,7 @@ int ensure_udf(dg_mesh* M) {
 }
 
 void forget_history(dg_mesh* M) {
-  for (int s = 0; s < 3; ++s) M->hist_n[s] = 0;
+  for (int s = 0; s < dg_mesh::kMaxStages; ++s) M->hist_n[s] = 0;
 }
 
 int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
@@ -374,7 +392,65 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
           }
       }
     }
-    if ((rc = upload(M, &d.dn_df, to_dfloat(dn)))) return cleanup(rc);
+    // paired image for k_stage_df2: rows of ns values as ceil(ns/2) pairs
+    // {hi_j, hi_j+1, lo_j, lo_j+1} (a missing j+1 is 0), in the order of PairTables<K>
+    const int ns2 = (ns + 1) / 2, nq = ref.nq;
+    std::vector<float> pt;
+    auto split = [](double v, float& h, float& l) {
+      h = float(v);
+      l = float(v - double(h));
+    };
+    // value (r, j) = src[r * rstride + j * jstride]
+    auto rows = [&](const double* src, int nrow, int rstride, int jstride) {
+      for (int r = 0; r < nrow; ++r)
+        for (int jp = 0; jp < ns2; ++jp) {
+          float h0, l0, h1 = 0.f, l1 = 0.f;
+          const int j = 2 * jp;
+          split(src[size_t(r) * rstride + size_t(j) * jstride], h0, l0);
+          if (j + 1 < ns) split(src[size_t(r) * rstride + size_t(j + 1) * jstride], h1, l1);
+          pt.insert(pt.end(), {h0, h1, l0, l1});
+        }
+    };
+    rows(ref.vphi.data(), nq, ns, 1);                  // vphi[q][j]
+    rows(ref.vdphi.data(), nq, 2 * ns, 2);             // d/dxi1 psi_j at q
+    rows(ref.vdphi.data() + 1, nq, 2 * ns, 2);         // d/dxi2
+    rows(ref.fphi.data(), 3 * nqf, ns, 1);             // fphi[e][q][j]
+    {
+      std::vector<double> dnfull(size_t(dgdf::kDnClasses) * 3 * nqf * ns, 0.0);
+      std::copy(dn.begin(), dn.end(), dnfull.begin());
+      rows(dnfull.data(), dgdf::kDnClasses * 3 * nqf, ns, 1);
+    }
+    for (int q = 0; q < nq; ++q) {
+      float h, l;
+      split(ref.vw[q], h, l);
+      pt.push_back(h);
+      pt.push_back(l);
+    }
+    for (int q = 0; q < nqf; ++q) {
+      float h, l;
+      split(ref.fw[q], h, l);
+      pt.push_back(h);
+      pt.push_back(l);
+    }
+    while (pt.size() % 4) pt.push_back(0.f);
+    d.ptab_words = int(pt.size() / 4);
+    // class operators, pairs of consecutive columns
+    auto pairs = [&](const std::vector<double>& Mx, int nrow) {
+      std::vector<float> out;
+      const int nc2 = nd / 2;
+      for (int c = 0; c < d.n_class; ++c)
+        for (int r = 0; r < nrow; ++r)
+          for (int jp = 0; jp < nc2; ++jp) {
+            float h0, l0, h1, l1;
+            split(Mx[(size_t(c) * nrow + r) * nd + 2 * jp], h0, l0);
+            split(Mx[(size_t(c) * nrow + r) * nd + 2 * jp + 1], h1, l1);
+            out.insert(out.end(), {h0, h1, l0, l1});
+          }
+      return out;
+    };
+    std::vector<float> p2 = pairs(P, nd), g2 = pairs(G, L3);
+    if ((rc = upload_f4(M, &d.ptab, pt)) || (rc = upload_f4(M, &d.P2, p2)) || (rc = upload_f4(M, &d.G2, g2)))
+      return cleanup(rc);
   }
   if (d.elem_df) {
     // reference tables in the field order of the kernels' shared-memory image
@@ -532,9 +608,9 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     d.lat_logn = logn;
     M->use_lattice = true;
     M->lattice_blocks = lat_blocks;
-    // multiplier history of the three RK stages (warm starts), in the layout of the solver's lam
+    // multiplier history of the stages (warm starts), in the layout of the solver's lam
     M->hist_bytes = nF * size_t(fp32 ? d.lat_vs : nl) * 8;
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < dg_mesh::kMaxStages; ++s)
       for (int h = 0; h < 2; ++h) {
         double* p = nullptr;
         if ((rc = dalloc(M, &p, M->hist_bytes / 8))) return cleanup(rc);
@@ -629,37 +705,98 @@ int dg_project_divfree(dg_mesh* M) {
 
 namespace {
 
-const double kRkA[3] = {0.0, 0.75, 1.0 / 3.0}, kRkB[3] = {1.0, 0.25, 2.0 / 3.0};
+// Explicit schemes in stage form. Stage s solves M u_s = a M x + b M u' + c dt L(u') on the
+// divergence-free space, with u' = u^n for s = 0 and the previous stage's state otherwise,
+// and x = u^n, or (xw) the running combination W. After stage s, W <- wx X + wb u_s with
+// X = u^n, or (wacc) X = W. The last stage's state is u^(n+1).
+struct StageCoef {
+  bool xw;
+  double a, b, c;
+  int wop;   // 0: W unchanged; 1: W = wx u^n + wb u_s; 2: W = wx W + wb u_s
+  double wx, wb;
+};
+struct Scheme {
+  int n;
+  StageCoef st[dg_mesh::kMaxStages];
+};
+const Scheme kSchemes[3] = {
+    // SSP-RK3, eq. (8): u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+    // u^(n+1) = 1/3 u + 2/3 (u2 + dt L(u2))
+    {3,
+     {{false, 0.0, 1.0, 1.0, 0, 0.0, 0.0},
+      {false, 0.75, 0.25, 0.25, 0, 0.0, 0.0},
+      {false, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, 0.0, 0.0}}},
+    // forward Euler, eq. (FE) of Sec. 3.1 (with the full L, viscous terms included)
+    {1, {{false, 0.0, 1.0, 1.0, 0, 0.0, 0.0}}},
+    // classical RK4 (Example 1b): u1 = u + dt/2 k1, u2 = u + dt/2 k2, u3 = u + dt k3 with
+    // k_i the projected L of the previous state; u^(n+1) = u + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    // = W + 1/3 u3 + dt/6 L(u3) with W = (-u + u1 + 2 u2) / 3
+    {4,
+     {{false, 0.0, 1.0, 0.5, 1, -1.0 / 3.0, 1.0 / 3.0},
+      {false, 1.0, 0.0, 0.5, 2, 1.0, 2.0 / 3.0},
+      {false, 1.0, 0.0, 1.0, 0, 0.0, 0.0},
+      {true, 1.0, 1.0 / 3.0, 1.0 / 6.0, 0, 0.0, 0.0}}},
+};
 
-// Enqueue one SSP-RK3 step (eq. (8)) of M on its stream: per stage the residual +
+// the warm-start history holds multipliers of one scheme's stages
+void use_scheme(dg_mesh* M, int scheme) {
+  if (M->hist_scheme != scheme) {
+    forget_history(M);
+    M->hist_scheme = scheme;
+  }
+}
+
+int ensure_rk_w(dg_mesh* M) {
+  const size_t n = size_t(M->dm.n_tri) * M->dm.nd;
+  if (M->dm.elem_df) return M->rk_w_df ? DG_OK : dalloc(M, &M->rk_w_df, n);
+  return M->rk_w ? DG_OK : dalloc(M, &M->rk_w, n);
+}
+
+// Enqueue one step of the given scheme on M's stream: per stage the residual +
 // condensation kernel, the facet solve (warm-started from the previous stage's
-// multipliers rescaled by b dt) and the recovery. No synchronisation.
-int enqueue_step(dg_mesh* M, double dt) {
+// multipliers rescaled by the ratio of the L coefficients, or from the same stage of the
+// last steps) and the recovery. No synchronisation.
+int enqueue_step(dg_mesh* M, double dt, int scheme = DG_SCHEME_SSPRK3) {
   dgdf::DevMesh& d = M->dm;
+  const Scheme& sc = kSchemes[scheme];
   int rc = ensure_udf(M);
   if (rc) return rc;
-  for (int s = 0; s < 3; ++s) {
-    const double a = kRkA[s], b = kRkB[s];
-    const double* up = (s == 0) ? d.u : d.ustage;
+  if (sc.st[sc.n - 1].xw || sc.st[0].wop) {
+    if ((rc = ensure_rk_w(M))) return rc;
+  }
+  use_scheme(M, scheme);
+  const long long n = (long long)d.n_tri * d.nd;
+  for (int s = 0; s < sc.n; ++s) {
+    const StageCoef& k = sc.st[s];
+    const bool last = s == sc.n - 1;
     // mixed form: the next stage reads only the double-float twin, so the FP64 copy of an
     // intermediate stage is not written
-    double* out = (s == 2) ? d.u : (d.elem_df ? nullptr : d.ustage);
-    float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
+    double* out = last ? d.u : (d.elem_df ? nullptr : d.ustage);
+    float2* out_df = last ? d.u_df : d.ustage_df;
     dgdf::StageArgs sa{};
     sa.mode = dgdf::MODE_STAGE;
-    sa.a = a;
-    sa.b = b;
-    sa.dt = dt;
-    sa.un = d.u;
-    sa.up = up;
-    sa.un_df = d.u_df;
+    sa.a = k.a;
+    sa.b = k.b;
+    sa.c = k.c * dt;
+    sa.un = k.xw ? M->rk_w : d.u;
+    sa.up = (s == 0) ? d.u : d.ustage;
+    sa.un_df = k.xw ? M->rk_w_df : d.u_df;
     sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
-    const double warm = M->has_lam ? (b * dt) / M->last_bdt : 0.0;
+    const double warm = M->has_lam ? sa.c / M->last_c : 0.0;
     if ((rc = solve(M, warm, s, dt)) || (rc = push_history(M, s, dt))) return rc;
     if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
-    M->last_bdt = b * dt;
+    M->last_c = sa.c;
     M->has_lam = true;
+    if (k.wop) {
+      const bool acc = k.wop == 2;
+      rc = launch(M, KC_COMBINE, [&] {
+        return d.elem_df ? dgdf::launch_axpby_df(acc ? M->rk_w_df : d.u_df, d.ustage_df, M->rk_w_df, k.wx, k.wb, n,
+                                                 M->stream)
+                         : dgdf::launch_axpby64(acc ? M->rk_w : d.u, d.ustage, M->rk_w, k.wx, k.wb, n, M->stream);
+      });
+      if (rc) return rc;
+    }
   }
   return DG_OK;
 }
@@ -678,16 +815,20 @@ struct dg_batch {
 
 extern "C" {
 
-int dg_rk3_step(dg_mesh* M, double dt, int64_t nsteps) {
+int dg_step(dg_mesh* M, int scheme, double dt, int64_t nsteps) {
   if (int rc = check_mesh(M)) return rc;
+  if (scheme != DG_SCHEME_SSPRK3 && scheme != DG_SCHEME_EULER && scheme != DG_SCHEME_RK4)
+    return fail(DG_ERR_INVALID_ARG, "scheme must be DG_SCHEME_SSPRK3, DG_SCHEME_EULER or DG_SCHEME_RK4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
   int rc = reset_flags(M);
   if (rc) return rc;
   for (int64_t n = 0; n < nsteps; ++n)
-    if ((rc = enqueue_step(M, dt))) return rc;
+    if ((rc = enqueue_step(M, dt, scheme))) return rc;
   return finish(M, true);
 }
+
+int dg_rk3_step(dg_mesh* M, double dt, int64_t nsteps) { return dg_step(M, DG_SCHEME_SSPRK3, dt, nsteps); }
 
 int dg_batch_create(int n, dg_mesh* const* meshes, void* cuda_stream, dg_batch** out) {
   g_err.clear();
@@ -877,25 +1018,27 @@ int enqueue_step_keep(dg_mesh* M, double dt, double* const st[3]) {
   const size_t bytes = size_t(d.n_tri) * d.nd * sizeof(double);
   int rc = ensure_udf(M);
   if (rc) return rc;
+  use_scheme(M, DG_SCHEME_SSPRK3);
   for (int s = 0; s < 3; ++s) {
     const double* up = (s == 0) ? d.u : d.ustage;
     CK(cudaMemcpyAsync(st[s], up, bytes, cudaMemcpyDeviceToDevice, M->stream));
     dgdf::StageArgs sa{};
     sa.mode = dgdf::MODE_STAGE;
-    sa.a = kRkA[s];
-    sa.b = kRkB[s];
-    sa.dt = dt;
+    const StageCoef& k = kSchemes[DG_SCHEME_SSPRK3].st[s];
+    sa.a = k.a;
+    sa.b = k.b;
+    sa.c = k.c * dt;
     sa.un = d.u;
     sa.up = up;
     sa.un_df = d.u_df;
     sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
-    const double warm = M->has_lam ? (kRkB[s] * dt) / M->last_bdt : 0.0;
+    const double warm = M->has_lam ? sa.c / M->last_c : 0.0;
     if ((rc = solve(M, warm, s, dt)) || (rc = push_history(M, s, dt))) return rc;
     double* out = (s == 2) ? d.u : d.ustage;
     float2* out_df = (s == 2) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
-    M->last_bdt = kRkB[s] * dt;
+    M->last_c = sa.c;
     M->has_lam = true;
   }
   return DG_OK;
@@ -962,10 +1105,11 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
     }
     for (int64_t i = len - 1; i >= 0; --i) {
       const double* U[3] = {stg + (size_t(i) * 3 + 0) * n, stg + (size_t(i) * 3 + 1) * n, stg + (size_t(i) * 3 + 2) * n};
-      // stage s: u_s = Q(a_s u^n + b_s (u' + dt L(u'))), u' = U[s]
+      // stage s: u_s = Q(a_s u^n + b_s u' + c_s L(u')), u' = U[s], c_s = b_s dt
       for (int s = 2; s >= 0; --s) {
         if ((rc = apply_Q(M, ub, fb))) return rc;                       // F-bar = Q u_s-bar
-        const double a = kRkA[s], b = kRkB[s];
+        const StageCoef& k = kSchemes[DG_SCHEME_SSPRK3].st[s];
+        const double a = k.a, b = k.b, c = k.c * dt;
         if (s == 2) {
           if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, a, 0.0, 0, 0.0, nu_acc, M->stream); })))
             return rc;                                                   // acc = a F-bar
@@ -975,11 +1119,11 @@ int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, 
         }
         if (s > 0) {
           // u'-bar = b (F-bar + dt J_L(u')^T F-bar); nu-bar += b dt dL/dnu(u').F-bar
-          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, ub, b, b * dt, 0, b * dt, nu_acc, M->stream); })))
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, ub, b, c, 0, c, nu_acc, M->stream); })))
             return rc;
         } else {
           // u' = u^n at the first stage: add into acc, which becomes u^n-bar
-          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, b, b * dt, 1, b * dt, nu_acc, M->stream); })))
+          if ((rc = launch(M, KC_ADJOINT, [&] { return dgdf::launch_adjoint(d, U[s], fb, acc, b, c, 1, c, nu_acc, M->stream); })))
             return rc;
           CK(cudaMemcpyAsync(ub, acc, bytes, cudaMemcpyDeviceToDevice, M->stream));
         }

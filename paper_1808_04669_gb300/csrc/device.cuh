@@ -56,9 +56,13 @@ struct DevMesh {
   // double-float images (mixed form): reference tables in SmemTables order, class
   // geometry [n_class][kGeo], penalty per facet
   const float2 *tab_df, *geo_df, *sigma_df;
-  // meshes with at most kDnClasses geometry classes: normal derivatives of the basis at the
-  // facet points per class, fdphi . (Jinv n_e), [n_class][3][nqf][ns] (NULL otherwise)
-  const float2* dn_df;
+  // meshes with at most kDnClasses geometry classes (NULL otherwise), for the paired
+  // (FP32x2) stage kernel: ptab = reference tables and the normal derivatives of the basis
+  // at the facet points per class, fdphi . (Jinv n_e), in the layout of PairTables<K>;
+  // P2 [n_class][nd][nd/2] and G2 [n_class][3(k+1)][nd/2] (pairs of consecutive columns:
+  // both leading words, then both trailing words)
+  const float4 *ptab, *P2, *G2;
+  int ptab_words;   // float4 words of ptab
   // facet-system stencil
   const int32_t *facet_nbr, *facet_stencil, *facet_tri;
   const int32_t *facet_ext;           // internal -> external facet id (NULL: identity)
@@ -99,7 +103,7 @@ constexpr int kMaxSolverBlocks = 2048;
 
 // Stage kernel modes.
 enum StageMode : int {
-  MODE_STAGE = 0,      // f = a u^n + b (u' + dt L(u')), h = P f, gl = G f
+  MODE_STAGE = 0,      // f = a u^n + b u' + c L(u'), h = P f, gl = G f
   MODE_RESIDUAL = 1,   // h = L(u') (Riesz representer, no solve)
   MODE_PRESSURE = 2,   // h = f = L(u'), gl = G f
   MODE_PROJECT = 3,    // f = u', h = P f, gl = G f
@@ -107,7 +111,7 @@ enum StageMode : int {
 
 struct StageArgs {
   int mode;
-  double a, b, dt;
+  double a, b, c;      // MODE_STAGE: f = a M u^n + b M u' + c L(u') (c carries the step size)
   const double* un;    // u^n
   const double* up;    // u'
   const float2* un_df;   // their double-float twins (mixed form)
@@ -139,6 +143,11 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 // out may be NULL in the mixed form (only the double-float twin is written)
 cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+// z = alpha x + beta y over n entries: double-float (mixed form) or FP64; z may alias x
+cudaError_t launch_axpby_df(const float2* x, const float2* y, float2* z, double alpha, double beta, long long n,
+                            cudaStream_t s);
+cudaError_t launch_axpby64(const double* x, const double* y, double* z, double alpha, double beta, long long n,
+                           cudaStream_t s);
 cudaError_t launch_to_dfl(const double* x, float2* y, long long n, cudaStream_t s);
 cudaError_t launch_to_double(const float2* x, int sx, double* y, int ny, long long nrow, cudaStream_t s);
 cudaError_t launch_pressure(const DevMesh& m, double* w, cudaStream_t s);

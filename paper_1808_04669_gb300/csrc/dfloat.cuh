@@ -106,6 +106,52 @@ __host__ __device__ __forceinline__ dfl val(dacc a) {
   return dfl(h, l);
 }
 
+// ---- two double-float values side by side: their leading words in one float2 and their
+// trailing words in another, so that the packed FP32x2 instructions of sm_100+ act on both
+// at once (same FP32 throughput as scalar instructions, half the issue slots).
+struct dfl2 {
+  float2 hi, lo;
+};
+// paired compensated accumulators (two independent dacc)
+struct dacc2 {
+  float2 s, c;
+};
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ dacc2 dacc2_zero() { return dacc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
+// a += x * y for both halves (Dot2 step, as mad() on dacc, in packed form)
+__device__ __forceinline__ void mad2(dacc2& a, const dfl2& x, const dfl2& y) {
+  const float2 p = f2mul(x.hi, y.hi);
+  float2 e = f2fma(x.hi, y.hi, make_float2(-p.x, -p.y));
+  e = f2fma(x.hi, y.lo, e);
+  e = f2fma(x.lo, y.hi, e);
+  const float2 s = f2add(a.s, p);
+  const float2 bb = f2sub(s, a.s);
+  const float2 t = f2add(f2sub(a.s, f2sub(s, bb)), f2sub(p, bb));
+  a.s = s;
+  a.c = f2add(a.c, f2add(t, e));
+}
+
+// the same value y for both halves
+__device__ __forceinline__ dfl2 splat(dfl y) {
+  return dfl2{make_float2(y.hi, y.hi), make_float2(y.lo, y.lo)};
+}
+
+// the two accumulated values
+__device__ __forceinline__ dfl val_x(const dacc2& a) { return val(dacc{a.s.x, a.c.x}); }
+__device__ __forceinline__ dfl val_y(const dacc2& a) { return val(dacc{a.s.y, a.c.y}); }
+// their sum (a sum split over even and odd terms)
+__device__ __forceinline__ dfl val_sum(const dacc2& a) {
+  float s, t;
+  two_sum(a.s.x, a.s.y, s, t);
+  return val(dacc{s, (a.c.x + a.c.y) + t});
+}
+
 __host__ __device__ __forceinline__ dfl& operator+=(dfl& x, dfl y) { return x = x + y; }
 __host__ __device__ __forceinline__ dfl& operator-=(dfl& x, dfl y) { return x = x - y; }
 __host__ __device__ __forceinline__ dfl& operator*=(dfl& x, dfl y) { return x = x * y; }

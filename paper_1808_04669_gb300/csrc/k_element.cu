@@ -318,9 +318,9 @@ __global__ void __launch_bounds__(128) k_stage(DevMesh m, StageArgs a) {
     if (a.mode == MODE_STAGE) {
       R un[ND];
       load_coef<ND>(a.un + size_t(t) * ND, un);
-      const R ca = R(a.a), cb = R(a.b), dt = R(a.dt);
+      const R ca = R(a.a), cb = R(a.b), cc = R(a.c);
 #pragma unroll
-      for (int i = 0; i < ND; ++i) f[i] = ca * un[i] + cb * (up[i] + dt * f[i]);
+      for (int i = 0; i < ND; ++i) f[i] = ca * un[i] + cb * up[i] + cc * f[i];
     }
   }
   if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {

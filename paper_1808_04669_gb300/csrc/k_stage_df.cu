@@ -10,6 +10,8 @@
 // warps hide the FP32 latency. Inputs are the double-float twins of u^n and u'
 // (no FP64 conversions on this path); sums of products use the compensated
 // accumulator dacc (12 FP32 operations per multiply-add).
+#include <algorithm>
+
 #include "device.cuh"
 #include "dfloat.cuh"
 #include "kcommon.cuh"
@@ -17,7 +19,9 @@
 
 namespace dgdf {
 
-constexpr int kStageDfThreads = 256;   // 128 triangles per block
+// 192 threads (96 triangles) per block and two blocks per SM leave 168 registers a thread,
+// enough for either stage kernel at k = 3 without spills.
+constexpr int kStageDfThreads = 192;
 
 namespace {
 
@@ -36,18 +40,8 @@ __device__ __forceinline__ void load_df(const float2* __restrict__ p, dfl (&c)[N
 // upwind flux (u.n) u_c^up with u.n the average of both traces, and the SIPG
 // consistency, symmetry and penalty terms, at the facet Gauss points (the
 // neighbour's point q is our point NQF-1-q).
-// Normal derivatives of the basis at the facet points per geometry class, dfl image of
-// m.dn_df (meshes with few classes).
 template <int K>
-struct DnTable {
-  dfl v[kDnClasses][3][Dims<K>::NQF][Dims<K>::NS];
-};
-
-// TAB: facet normal derivatives from the per-class table (two sums per trace instead of
-// three, and one instead of two for the test derivative).
-template <int K, bool TAB>
-__device__ __forceinline__ void residual_component(const DevMesh& m, const SmemTables<K, dfl>& T,
-                                                   const DnTable<K>& DN, int t, int c,
+__device__ __forceinline__ void residual_component(const DevMesh& m, const SmemTables<K, dfl>& T, int t, int c,
                                                    const float2* __restrict__ ug, const dfl (&up)[Dims<K>::NS],
                                                    dacc (&acc)[Dims<K>::NS]) {
   using D = Dims<K>;
@@ -99,38 +93,6 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
     const dfl nusig = nu * sig, hnu = half(nu);
     dfl un[NS];
     load_df<NS>(ug + size_t(tn) * ND + c * NS, un);
-    if constexpr (TAB) {
-      // the neighbour's table holds derivatives along its own outward normal, -n
-      const dfl msn = -sn;
-#pragma unroll 1
-      for (int q = 0; q < D::NQF; ++q) {
-        const int qn = D::NQF - 1 - q;
-        dacc V = dacc_zero(), Dd = dacc_zero(), Vn = dacc_zero(), Dnd = dacc_zero();
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          mad(V, T.fphi[e][q][j], up[j]);
-          mad(Dd, DN.v[cls][e][q][j], up[j]);
-          mad(Vn, T.fphi[en][qn][j], un[j]);
-          mad(Dnd, DN.v[ncls][en][qn][j], un[j]);
-        }
-        const dfl ui = s * val(V), di = s * val(Dd);
-        const dfl uo = sn * val(Vn), dn = msn * val(Dnd);
-        // u.n = 1/2 (u_in + u_out) . n, summed in the same order by both threads of the pair
-        const dfl pc = (ui + uo) * nc, po = shfl_pair(pc);
-        const dfl vn = half(c ? po + pc : pc + po);
-        const dfl wup = vn >= dfl(0) ? ui : uo;
-        const dfl jc = ui - uo;
-        const dfl w = T.fw[q] * lens;
-        const dfl A = w * (hnu * (di + dn) - vn * wup - nusig * jc);
-        const dfl B = w * hnu * jc;
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          mad(acc[j], A, T.fphi[e][q][j]);
-          mad(acc[j], B, DN.v[cls][e][q][j]);
-        }
-      }
-      continue;
-    }
     // normal derivative in reference gradients: d_n psi = s sum_r d_r psihat (Jinv n)_r
     const dfl mo0 = Ji0 * n0 + Ji1 * n1, mo1 = Ji2 * n0 + Ji3 * n1;
     const dfl mn0 = to_dfl(geon[G_JINV + 0]) * n0 + to_dfl(geon[G_JINV + 1]) * n1;
@@ -175,17 +137,12 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
 // MODE_PROJECT), h = f in FP64 (MODE_RESIDUAL, MODE_PRESSURE) and gl_df
 // (MODE_PRESSURE). Thread c of a pair owns rows c*NS.. of f and h, and the rows
 // i = c (mod 2) of gl.
-template <int K, bool TAB>
+template <int K>
 __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, StageArgs a) {
   using D = Dims<K>;
   constexpr int NS = D::NS, ND = D::ND, L3 = 3 * D::NL;
   __shared__ SmemTables<K, dfl> T;
-  __shared__ DnTable<K> DN;
   load_tables_df<K>(m, T);
-  if constexpr (TAB) {
-    const int nw = m.n_class * 3 * D::NQF * NS;
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) (&DN.v[0][0][0][0])[i] = to_dfl(m.dn_df[i]);
-  }
   __syncthreads();
   const int c = threadIdx.x & 1;
   const int traw = blockIdx.x * (kStageDfThreads / 2) + (threadIdx.x >> 1);
@@ -201,13 +158,13 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, Stag
     dacc acc[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) acc[j] = dacc_zero();
-    residual_component<K, TAB>(m, T, DN, t, c, a.up_df, up, acc);
+    residual_component<K>(m, T, t, c, a.up_df, up, acc);
     if (a.mode == MODE_STAGE) {
       dfl un[NS];
       load_df<NS>(a.un_df + size_t(t) * ND + c * NS, un);
-      const dfl ca(a.a), cb(a.b), dt(a.dt);
+      const dfl ca(a.a), cb(a.b), cc(a.c);
 #pragma unroll
-      for (int j = 0; j < NS; ++j) f[j] = ca * un[j] + cb * (up[j] + dt * val(acc[j]));
+      for (int j = 0; j < NS; ++j) f[j] = ca * un[j] + cb * up[j] + cc * val(acc[j]);
     } else {
 #pragma unroll
       for (int j = 0; j < NS; ++j) f[j] = val(acc[j]);
@@ -241,6 +198,202 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df(DevMesh m, Stag
 #pragma unroll
     for (int j = 0; j < ND; ++j) mad(v, to_dfl(__ldg(&G[i * ND + j])), F(j));
     if (live) m.gl_df[size_t(t) * L3 + i] = to_float2(val(v));
+  }
+}
+
+// ---- paired form (meshes with at most kDnClasses geometry classes). The normal
+// derivatives of the basis at the facet points come from a per-class table, so a trace
+// takes two sums (value, normal derivative) instead of three and the test derivative one
+// instead of two. Every sum over basis functions takes two consecutive indices j, j+1 at
+// once in the packed FP32x2 instructions (dacc2 / mad2), with the tables laid out as
+// pairs {hi_j, hi_j+1, lo_j, lo_j+1}. The terms and the per-point arithmetic are those of
+// k_stage_df; only the order of summation inside each dot product differs (even and odd
+// j apart).
+template <int K>
+struct PairTables {
+  static constexpr int NS2 = (Dims<K>::NS + 1) / 2, NQ = Dims<K>::NQ, NQF = Dims<K>::NQF;
+  float4 vphi[NQ][NS2];
+  float4 vd0[NQ][NS2];   // d/dxi1 of the reference basis
+  float4 vd1[NQ][NS2];   // d/dxi2
+  float4 fphi[3][NQF][NS2];
+  float4 dn[kDnClasses][3][NQF][NS2];   // d/dn of the basis at the facet points, per class
+  float2 vw[NQ], fw[NQF];
+};
+
+__device__ __forceinline__ dfl2 pair(float4 v) { return dfl2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+
+// coefficients j = 0..N-1 of a double-float row as pairs (a missing j+1 is zero)
+template <int N>
+__device__ __forceinline__ void load_pairs(const float2* __restrict__ p, dfl2 (&c)[(N + 1) / 2]) {
+#pragma unroll
+  for (int jp = 0; jp < (N + 1) / 2; ++jp) {
+    const float2 x = p[2 * jp];
+    const float2 y = 2 * jp + 1 < N ? p[2 * jp + 1] : make_float2(0.f, 0.f);
+    c[jp] = dfl2{make_float2(x.x, y.x), make_float2(x.y, y.y)};
+  }
+}
+
+__device__ __forceinline__ dfl lane(const dfl2& v, int l) { return l ? dfl(v.hi.y, v.lo.y) : dfl(v.hi.x, v.lo.x); }
+
+template <int K>
+__device__ __forceinline__ void residual_pairs(const DevMesh& m, const PairTables<K>& T, int t, int c,
+                                               const float2* __restrict__ ug, const dfl2 (&up)[PairTables<K>::NS2],
+                                               dacc2 (&acc)[PairTables<K>::NS2]) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, ND = D::ND, NS2 = PairTables<K>::NS2;
+  const dfl nu(m.nu);
+  const int cls = __ldg(&m.tri_class[t]);
+  const float2* geo = m.geo_df + size_t(cls) * kGeo;
+  const dfl Ji0 = to_dfl(geo[G_JINV + 0]), Ji1 = to_dfl(geo[G_JINV + 1]);
+  const dfl Ji2 = to_dfl(geo[G_JINV + 2]), Ji3 = to_dfl(geo[G_JINV + 3]);
+  const dfl s = to_dfl(geo[G_S]);
+  const dfl ds = to_dfl(geo[G_DET]) * s;
+  // ---- volume terms
+#pragma unroll 1
+  for (int q = 0; q < D::NQ; ++q) {
+    dacc2 U = dacc2_zero(), A0 = dacc2_zero(), A1 = dacc2_zero();
+#pragma unroll
+    for (int jp = 0; jp < NS2; ++jp) {
+      mad2(U, pair(T.vphi[q][jp]), up[jp]);
+      mad2(A0, pair(T.vd0[q][jp]), up[jp]);
+      mad2(A1, pair(T.vd1[q][jp]), up[jp]);
+    }
+    const dfl uc = s * val_sum(U), a0 = val_sum(A0), a1 = val_sum(A1);
+    const dfl g0 = s * (a0 * Ji0 + a1 * Ji2), g1 = s * (a0 * Ji1 + a1 * Ji3);
+    const dfl uo = shfl_pair(uc);
+    const dfl u0 = c ? uo : uc, u1 = c ? uc : uo;
+    const dfl F0 = uc * u0 - nu * g0, F1 = uc * u1 - nu * g1;
+    const dfl w = to_dfl(T.vw[q]) * ds;
+    const dfl2 H0 = splat(w * (F0 * Ji0 + F1 * Ji1)), H1 = splat(w * (F0 * Ji2 + F1 * Ji3));
+#pragma unroll
+    for (int jp = 0; jp < NS2; ++jp) {
+      mad2(acc[jp], H0, pair(T.vd0[q][jp]));
+      mad2(acc[jp], H1, pair(T.vd1[q][jp]));
+    }
+  }
+  // ---- facet terms
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int tn = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
+    const int en = __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
+    const int ncls = __ldg(&m.tri_class[tn]);
+    const dfl sn = to_dfl(m.geo_df[size_t(ncls) * kGeo + G_S]);
+    const dfl n0 = to_dfl(geo[G_NRM + 2 * e]), n1 = to_dfl(geo[G_NRM + 2 * e + 1]);
+    const dfl nc = c ? n1 : n0;
+    const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
+    const dfl sig = to_dfl(m.sigma_df[__ldg(&m.tri_facet[size_t(t) * 3 + e])]);
+    const dfl nusig = nu * sig, hnu = half(nu);
+    const dfl msn = -sn;   // the neighbour's table holds derivatives along its own normal, -n
+    dfl2 un[NS2];
+    load_pairs<NS>(ug + size_t(tn) * ND + c * NS, un);
+#pragma unroll 1
+    for (int q = 0; q < D::NQF; ++q) {
+      const int qn = D::NQF - 1 - q;
+      dacc2 V = dacc2_zero(), Dd = dacc2_zero(), Vn = dacc2_zero(), Dnd = dacc2_zero();
+#pragma unroll
+      for (int jp = 0; jp < NS2; ++jp) {
+        mad2(V, pair(T.fphi[e][q][jp]), up[jp]);
+        mad2(Dd, pair(T.dn[cls][e][q][jp]), up[jp]);
+        mad2(Vn, pair(T.fphi[en][qn][jp]), un[jp]);
+        mad2(Dnd, pair(T.dn[ncls][en][qn][jp]), un[jp]);
+      }
+      const dfl ui = s * val_sum(V), di = s * val_sum(Dd);
+      const dfl uo = sn * val_sum(Vn), dn = msn * val_sum(Dnd);
+      const dfl pc = (ui + uo) * nc, po = shfl_pair(pc);
+      const dfl vn = half(c ? po + pc : pc + po);
+      const dfl wup = vn >= dfl(0) ? ui : uo;
+      const dfl jc = ui - uo;
+      const dfl w = to_dfl(T.fw[q]) * lens;
+      const dfl2 A = splat(w * (hnu * (di + dn) - vn * wup - nusig * jc));
+      const dfl2 B = splat(w * hnu * jc);
+#pragma unroll
+      for (int jp = 0; jp < NS2; ++jp) {
+        mad2(acc[jp], A, pair(T.fphi[e][q][jp]));
+        mad2(acc[jp], B, pair(T.dn[cls][e][q][jp]));
+      }
+    }
+  }
+}
+
+// Stage kernel, paired form: the modes, inputs and outputs of k_stage_df; the class
+// operators P and G are read as column pairs (m.P2, m.G2).
+template <int K>
+__global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df2(DevMesh m, StageArgs a) {
+  using D = Dims<K>;
+  using PT = PairTables<K>;
+  constexpr int NS = D::NS, ND = D::ND, L3 = 3 * D::NL, NS2 = PT::NS2, NDP = ND / 2;
+  __shared__ PT T;
+  {
+    float4* dst = reinterpret_cast<float4*>(&T);
+    for (int i = threadIdx.x; i < int(sizeof(PT) / sizeof(float4)); i += blockDim.x) dst[i] = __ldg(&m.ptab[i]);
+  }
+  __syncthreads();
+  const int c = threadIdx.x & 1;
+  const int traw = blockIdx.x * (kStageDfThreads / 2) + (threadIdx.x >> 1);
+  const bool live = traw < m.n_tri;
+  const int t = live ? traw : m.n_tri - 1;   // both threads of a pair stay for the shuffles
+  dfl2 up[NS2];
+  load_pairs<NS>(a.up_df + size_t(t) * ND + c * NS, up);
+  dfl f[NS];
+  if (a.mode == MODE_PROJECT) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) f[j] = lane(up[j / 2], j & 1);
+  } else {
+    dacc2 acc[NS2];
+#pragma unroll
+    for (int jp = 0; jp < NS2; ++jp) acc[jp] = dacc2_zero();
+    residual_pairs<K>(m, T, t, c, a.up_df, up, acc);
+    if (a.mode == MODE_STAGE) {
+      dfl un[NS];
+      load_df<NS>(a.un_df + size_t(t) * ND + c * NS, un);
+      const dfl ca(a.a), cb(a.b), cc(a.c);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const dfl r = (j & 1) ? val_y(acc[j / 2]) : val_x(acc[j / 2]);
+        f[j] = ca * un[j] + cb * lane(up[j / 2], j & 1) + cc * r;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NS; ++j) f[j] = (j & 1) ? val_y(acc[j / 2]) : val_x(acc[j / 2]);
+    }
+  }
+  if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
+    if (live)
+#pragma unroll
+      for (int j = 0; j < NS; ++j) m.h[size_t(t) * ND + c * NS + j] = to_double(f[j]);
+  }
+  if (a.mode == MODE_RESIDUAL) return;   // uniform over the block
+  // F = f in triangle order (component 0 first), as column pairs
+  dfl2 F[NDP];
+  {
+    dfl fo[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) fo[j] = shfl_pair(f[j]);
+#pragma unroll
+    for (int jp = 0; jp < NDP; ++jp) {
+      const int i0 = 2 * jp, i1 = 2 * jp + 1;
+      const dfl x = (i0 < NS) == (c == 0) ? f[i0 % NS] : fo[i0 % NS];
+      const dfl y = (i1 < NS) == (c == 0) ? f[i1 % NS] : fo[i1 % NS];
+      F[jp] = dfl2{make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)};
+    }
+  }
+  const int cls = __ldg(&m.tri_class[t]);
+  if (a.mode != MODE_PRESSURE) {
+    const float4* P = m.P2 + size_t(cls) * ND * NDP;
+    for (int r = 0; r < NS; ++r) {
+      const int i = c * NS + r;
+      dacc2 v = dacc2_zero();
+#pragma unroll
+      for (int jp = 0; jp < NDP; ++jp) mad2(v, pair(__ldg(&P[i * NDP + jp])), F[jp]);
+      if (live) m.h_df[size_t(t) * ND + i] = to_float2(val_sum(v));
+    }
+  }
+  const float4* G = m.G2 + size_t(cls) * L3 * NDP;
+  for (int i = c; i < L3; i += 2) {
+    dacc2 v = dacc2_zero();
+#pragma unroll
+    for (int jp = 0; jp < NDP; ++jp) mad2(v, pair(__ldg(&G[i * NDP + jp])), F[jp]);
+    if (live) m.gl_df[size_t(t) * L3 + i] = to_float2(val_sum(v));
   }
 }
 
@@ -304,9 +457,31 @@ __global__ void k_to_double(const float2* __restrict__ x, int sx, double* __rest
     y[i] = to_double(x[(i / ny) * sx + i % ny]);
 }
 
+// z = alpha x + beta y in double-float (the RK4 combination of stage states)
+__global__ void k_axpby_df(const float2* x, const float2* __restrict__ y, float2* z, double alpha, double beta,
+                           long long n) {
+  const dfl al(alpha), be(beta);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = to_float2(al * to_dfl(x[i]) + be * to_dfl(y[i]));
+}
+
+__global__ void k_axpby64(const double* x, const double* __restrict__ y, double* z, double alpha, double beta,
+                          long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = alpha * x[i] + beta * y[i];
+}
+
 inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
 
 }  // namespace
+
+template <int K>
+cudaError_t launch_pairs(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
+  // the host image must have the layout of PairTables<K>
+  if (m.ptab_words != int(sizeof(PairTables<K>) / sizeof(float4))) return cudaErrorInvalidValue;
+  k_stage_df2<K><<<blocks_for(m.n_tri, kStageDfThreads / 2), kStageDfThreads, 0, s>>>(m, a);
+  return cudaSuccess;
+}
 
 #define DGDF_DISPATCH_K(kv, CALL) \
   switch (kv) {                   \
@@ -319,16 +494,32 @@ inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
 cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s) {
   if (!a.up_df || (a.mode == MODE_STAGE && !a.un_df)) return cudaErrorInvalidValue;
   const int nb = blocks_for(m.n_tri, kStageDfThreads / 2);
-  if (m.dn_df) {
-    DGDF_DISPATCH_K(m.k, (k_stage_df<K, true><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+  if (m.ptab) {
+    cudaError_t e = cudaSuccess;
+    DGDF_DISPATCH_K(m.k, (e = launch_pairs<K>(m, a, s)));
+    if (e != cudaSuccess) return e;
   } else {
-    DGDF_DISPATCH_K(m.k, (k_stage_df<K, false><<<nb, kStageDfThreads, 0, s>>>(m, a)));
+    DGDF_DISPATCH_K(m.k, (k_stage_df<K><<<nb, kStageDfThreads, 0, s>>>(m, a)));
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
   DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverThreads), kRecoverThreads, 0, s>>>(m, out, out_df)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby_df(const float2* x, const float2* y, float2* z, double alpha, double beta, long long n,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_axpby_df<<<int(std::min<long long>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(x, y, z, alpha, beta, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby64(const double* x, const double* y, double* z, double alpha, double beta, long long n,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_axpby64<<<int(std::min<long long>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(x, y, z, alpha, beta, n);
   return cudaGetLastError();
 }
 

@@ -165,6 +165,63 @@ def test_rk3_parity_shear_layer(g, N, k, precond):
             assert st["total_iters"] / st["solves"] <= 6
 
 
+# ------------------------------------------------------- other explicit schemes
+@pytest.mark.parametrize("scheme", ["EULER", "RK4"])
+@pytest.mark.parametrize("N,k,precond", [(8, 2, 0), (12, 3, 0), (6, 3, 1)])
+def test_scheme_parity_shear_layer(g, scheme, N, k, precond):
+    # forward Euler (eq. (FE)) and classical RK4 (Example 1b) through dg_step, against the
+    # oracle's own forms (one solve per Euler step; RK4 from the four projected slopes)
+    nu = 1e-3
+    vid, X = synth.split_square_mesh(N)
+    vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
+    vmax = float(np.sqrt((vals ** 2).sum(-1)).max())
+    dt = synth.cfl_dt(X, k, vmax, nu)
+    d = Discretization(vid, X, k, nu)
+    U0 = d.project(d.from_lattice(vals))
+    ref = d.to_lattice((d.euler_step if scheme == "EULER" else d.rk4_step)(U0, dt, 4))
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec, precond=precond)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.step(dt, 4, scheme=getattr(g, scheme))
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+        dg = mesh.diagnostics()
+        assert dg["max_jump"] < 1e-10 and dg["max_div"] < 1e-10
+
+
+def test_scheme_switching_parity(g):
+    # RK3, RK4, Euler and RK3 again on one mesh: each switch drops the multiplier history of
+    # the previous scheme's stages (warm starts only), the results follow the oracle
+    N, k, nu = 8, 3, 1e-3
+    vid, X = synth.split_square_mesh(N)
+    vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    U = d.project(d.from_lattice(vals))
+    U = d.rk3_step(U, dt, 2)
+    U = d.rk4_step(U, dt, 2)
+    U = d.euler_step(U, 0.5 * dt, 1)
+    U = d.rk3_step(U, dt, 2)
+    ref = d.to_lattice(U)
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.rk3_step(dt, 2)
+        mesh.step(dt, 2, scheme=g.RK4)
+        mesh.step(0.5 * dt, 1, scheme=g.EULER)
+        mesh.step(dt, 2, scheme=g.SSPRK3)
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+
+
+def test_step_rejects_unknown_scheme(g):
+    from paper_1808_04669_gb300 import DGError
+    mesh, d, X = pair(g, 2, 1, 0.0)
+    with pytest.raises(DGError) as e:
+        mesh.step(0.01, 1, scheme=7)
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("precond", [0, 1])
 def test_mixed_precision_taylor_green(g, precond):
     vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
