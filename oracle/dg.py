@@ -96,6 +96,20 @@ class Discretization:
         for s in range(0, n, self.chunk):
             yield np.arange(s, min(n, s + self.chunk))
 
+    def _interior_chunks(self):
+        """Interior facets in chunks. A wall (boundary facet) adds no term to L(u): u.n = 0
+        there for every u of the space, so the convective flux of eq. (7) vanishes, and the
+        SIPG form eq. (18) sums over interior facets only (free slip, Sec. 3)."""
+        ii = self.topo.interior
+        for s in range(0, len(ii), self.chunk):
+            yield ii[s:s + self.chunk]
+
+    def _penalty(self):
+        """alpha k^2 / h_F per facet, h_F the larger diameter of the facet's triangles (eq. (18))."""
+        T = self.topo
+        t1 = np.where(T.boundary, T.facet_tri[:, 0], T.facet_tri[:, 1])
+        return self.alpha * self.k ** 2 / np.maximum(T.diam[T.facet_tri[:, 0]], T.diam[t1])
+
     def _facet_side(self, f, s):
         P = self.topo.facet_points(f, np.full(f.shape, s), self.ft)
         tri = self.topo.facet_tri[f, s]
@@ -125,8 +139,8 @@ class Discretization:
             R[tri] += np.einsum("tq,tqcd,tqjd->tcj", W, Flx, G, optimize=True)
         T = self.topo
         Rf = np.zeros((self.n_tri, 3, 2, ns))
-        sig_all = self.alpha * self.k ** 2 / np.maximum(T.diam[T.facet_tri[:, 0]], T.diam[T.facet_tri[:, 1]])
-        for f in self._chunks(self.n_facet):
+        sig_all = self._penalty()
+        for f in self._interior_chunks():
             t0, V0, G0 = self._facet_side(f, 0)
             t1, V1, G1 = self._facet_side(f, 1)
             n0 = T.normal[t0, T.facet_loc[f, 0]]                   # outward from side 0
@@ -177,8 +191,8 @@ class Discretization:
             R[tri] += np.einsum("tq,tqcd,tqjd->tcj", W, Flx, G, optimize=True)
         T = self.topo
         Rf = np.zeros((self.n_tri, 3, 2, ns))
-        sig_all = self.alpha * self.k ** 2 / np.maximum(T.diam[T.facet_tri[:, 0]], T.diam[T.facet_tri[:, 1]])
-        for f in self._chunks(self.n_facet):
+        sig_all = self._penalty()
+        for f in self._interior_chunks():
             t0, V0, G0 = self._facet_side(f, 0)
             t1, V1, G1 = self._facet_side(f, 1)
             n0 = T.normal[t0, T.facet_loc[f, 0]]
@@ -547,10 +561,12 @@ class Discretization:
         T = self.topo
         f = np.arange(self.n_facet)
         t0, V0, _ = self._facet_side(f, 0)
-        t1, V1, _ = self._facet_side(f, 1)
         n0 = T.normal[t0, T.facet_loc[:, 0]]
         u0 = np.einsum("fqj,fcj->fqc", V0, U[t0])
-        u1 = np.einsum("fqj,fcj->fqc", V1, U[t1])
+        u1 = np.zeros_like(u0)                      # walls: the jump is u.n itself
+        fi = T.interior
+        _, V1, _ = self._facet_side(fi, 1)
+        u1[fi] = np.einsum("fqj,fcj->fqc", V1, U[T.facet_tri[fi, 1]])
         jmax = float(np.abs(np.einsum("fqc,fc->fq", u0 - u1, n0)).max())
         return dict(energy=self.energy(U.reshape(self.n_tri, -1)), enstrophy=ens, max_div=divmax, max_jump=jmax)
 
@@ -558,14 +574,14 @@ class Discretization:
         """(1/2) sum_F int_F |u.n| |u^+ - u^-|^2 at the facet Gauss points (energy identity of Sec. 2.2)."""
         T = self.topo
         U = np.asarray(U).reshape(self.n_tri, 2, self.ns)
-        f = np.arange(self.n_facet)
+        f = T.interior                              # walls carry no flux (u.n = 0)
         t0, V0, _ = self._facet_side(f, 0)
         t1, V1, _ = self._facet_side(f, 1)
-        n0 = T.normal[t0, T.facet_loc[:, 0]]
+        n0 = T.normal[t0, T.facet_loc[f, 0]]
         u0 = np.einsum("fqj,fcj->fqc", V0, U[t0])
         u1 = np.einsum("fqj,fcj->fqc", V1, U[t1])
         un = 0.5 * np.einsum("fqc,fc->fq", u0 + u1, n0)
-        wq = self.fw[None, :] * T.facet_len[:, None]
+        wq = self.fw[None, :] * T.facet_len[f][:, None]
         return 0.5 * float((wq * np.abs(un) * ((u0 - u1) ** 2).sum(-1)).sum())
 
     def l2_error(self, U, field, rule_degree=None):

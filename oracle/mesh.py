@@ -9,7 +9,9 @@ Definitions (shared with the C-ABI as conventions, implemented independently):
 * two element edges are the same facet when they join the same pair of
   identified vertices in the same canonical order and have the same edge
   vector (this separates the periodic images on meshes as coarse as 1 x 1);
-* facets are numbered in order of first appearance over (triangle, local facet).
+* facets are numbered in order of first appearance over (triangle, local facet);
+* an edge that no other triangle shares is a boundary facet (a wall of the domain): it has
+  one side, and facet_tri / facet_loc / facet_orient hold -1 for the missing second side.
 """
 import numpy as np
 
@@ -58,17 +60,21 @@ class Topology:
                     facet_sides.append([])
                 facet_sides[f].append((t, e, orient))
         for f, s in enumerate(facet_sides):
-            if len(s) != 2:
-                raise ValueError("facet %d has %d triangles: the mesh must be closed (periodic)" % (f, len(s)))
-            if s[0][2] == s[1][2]:
+            if len(s) > 2:
+                raise ValueError("facet %d has %d triangles" % (f, len(s)))
+            if len(s) == 2 and s[0][2] == s[1][2]:
                 raise ValueError("facet %d traversed in the same direction by both triangles" % f)
+            if len(s) == 1:
+                s.append((-1, -1, -1))
         self.n_facet = len(facet_sides)
         self.facet_tri = np.array([[s[0][0], s[1][0]] for s in facet_sides], dtype=np.int64)
         self.facet_loc = np.array([[s[0][1], s[1][1]] for s in facet_sides], dtype=np.int64)
         self.facet_orient = np.array([[s[0][2], s[1][2]] for s in facet_sides], dtype=np.int64)
+        self.boundary = self.facet_tri[:, 1] < 0
+        self.interior = np.flatnonzero(~self.boundary)
         self.tri_facet = np.empty((n, 3), dtype=np.int64)
         for f in range(self.n_facet):
-            for s in range(2):
+            for s in range(2 if not self.boundary[f] else 1):
                 self.tri_facet[self.facet_tri[f, s], self.facet_loc[f, s]] = f
         self.facet_len = self.edge_len[self.facet_tri[:, 0], self.facet_loc[:, 0]]
 

@@ -9,8 +9,12 @@ element next to the periodic seam keeps its true shape.
 import numpy as np
 
 
-def split_square_mesh(N, L=2.0 * np.pi, origin=(0.0, 0.0)):
-    """Return (tri_vertex_ids [2N^2,3] int64, tri_coords [2N^2,3,2] float64)."""
+def split_square_mesh(N, L=2.0 * np.pi, origin=(0.0, 0.0), periodic=True):
+    """Return (tri_vertex_ids [2N^2,3] int64, tri_coords [2N^2,3,2] float64).
+
+    periodic: vertices on opposite sides of the square are identified (a torus); otherwise
+    every vertex has its own id and the square's edges are walls (boundary facets).
+    """
     N = int(N)
     if N < 1:
         raise ValueError("N must be >= 1")
@@ -27,7 +31,10 @@ def split_square_mesh(N, L=2.0 * np.pi, origin=(0.0, 0.0)):
     for which, corners in enumerate((corners_lo, corners_up)):
         t = 2 * cell + which
         for c, (di, dj) in enumerate(corners):
-            vid[t, c] = ((i + di) % N) + N * ((j + dj) % N)
+            if periodic:
+                vid[t, c] = ((i + di) % N) + N * ((j + dj) % N)
+            else:
+                vid[t, c] = (i + di) + (N + 1) * (j + dj)
             X[t, c, 0] = origin[0] + (i + di) * h
             X[t, c, 1] = origin[1] + (j + dj) * h
     return vid, X

@@ -78,10 +78,90 @@ def test_periodic_split_square_topology(N):
     assert np.allclose(shift, np.round(shift), atol=1e-12)
 
 
-def test_open_mesh_rejected():
+def test_nonmanifold_mesh_rejected():
+    # a repeated triangle puts three triangles on its edges
     vid, X = synth.split_square_mesh(3)
     with pytest.raises(ValueError):
-        Discretization(vid[:-1], X[:-1], 1, 0.0)
+        Discretization(np.concatenate([vid, vid[:1]]), np.concatenate([X, X[:1]]), 1, 0.0)
+
+
+def test_box_topology_has_walls():
+    # N x N split squares of the unit square: 3N^2 + 2N facets, 4N of them on the walls
+    for N in (1, 3):
+        vid, X = synth.split_square_mesh(N, L=1.0, periodic=False)
+        T = Discretization(vid, X, 1, 0.0).topo
+        assert T.n_facet == 3 * N * N + 2 * N and T.boundary.sum() == 4 * N
+        # every wall facet lies on the square's boundary and its normal points outward
+        f = np.flatnonzero(T.boundary)
+        mid = T.facet_points(f, np.zeros_like(f), np.array([0.5]))[:, 0]
+        on = np.minimum(np.minimum(mid[:, 0], 1 - mid[:, 0]), np.minimum(mid[:, 1], 1 - mid[:, 1]))
+        assert np.abs(on).max() < 1e-14
+        n = T.normal[T.facet_tri[f, 0], T.facet_loc[f, 0]]
+        assert np.all(((mid - 0.5) * n).sum(-1) > 0)
+
+
+# ------------------------------------------------------------ walls (free slip)
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 1), (2, 2), (2, 3), (3, 2)])
+def test_divfree_dimension_in_box_with_walls(N, k):
+    # V_h with u.n = 0 on the walls is curl of the continuous P^{k+1} stream functions that
+    # vanish on the boundary (exact sequence on a simply connected domain): one per interior
+    # Lagrange node of degree k+1, ((k+1) N - 1)^2 on the split-square mesh
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=False)
+    d = Discretization(vid, X, k, 0.0)
+    assert d.divfree_basis().shape[1] == ((k + 1) * N - 1) ** 2
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_wall_projection_routes_agree(k):
+    # condensed solve = uncondensed saddle solve = projection through the explicit basis, and
+    # the result has no normal velocity on the walls
+    vid, X = synth.split_square_mesh(2, L=1.0, periodic=False)
+    d = Discretization(vid, X, k, 0.0)
+    rng = np.random.default_rng(k)
+    F = d.apply_mass(rng.standard_normal((d.n_tri, d.nd)))
+    u1, _, _ = d.solve_condensed(F)
+    u2, _, _ = d.solve_full(F)
+    u3 = d.project_nullspace(F)
+    assert np.abs(u1 - u2).max() < 1e-12 and np.abs(u1 - u3).max() < 1e-12
+    dg = d.diagnostics(u1)
+    assert dg["max_jump"] < 1e-12 and dg["max_div"] < 1e-11
+
+
+def test_taylor_green_cell_with_free_slip_walls():
+    # u = (sin pi x cos pi y, -cos pi x sin pi y) on the unit square has u.n = 0 and zero
+    # vorticity (hence zero tangential stress) on the walls and solves Navier-Stokes with
+    # u(t) = u0 exp(-2 nu pi^2 t): velocity error of order k+1 (Table 1 shape)
+    nu, k, T = 1e-2, 2, 0.1
+    tg = synth.taylor_green(L=2.0)
+    errs = []
+    for N in (4, 8):
+        vid, X = synth.split_square_mesh(N, L=1.0, periodic=False)
+        d = Discretization(vid, X, k, nu)
+        U = d.project(d.from_lattice(synth.sample_lattice(tg, X, k)))
+        n = 2 * N
+        U = d.rk3_step(U, T / n, n)
+        dec = math.exp(-2.0 * nu * math.pi ** 2 * T)
+        errs.append(d.l2_error(U, lambda x, y: tuple(v * dec for v in tg(x, y))))
+        assert d.diagnostics(U)["max_jump"] < 1e-12
+    assert abs(math.log2(errs[0] / errs[1]) - (k + 1)) < 0.35, errs
+
+
+def test_wall_energy_non_increasing_and_identity():
+    # nu = 0, walls: the wall facets carry no flux, so the energy identity of Sec. 2.2 keeps
+    # only the interior upwind dissipation and the energy does not grow
+    vid, X = synth.split_square_mesh(5, L=1.0, periodic=False)
+    d = Discretization(vid, X, 2, 0.0)
+    U = d.project(d.from_lattice(synth.sample_lattice(synth.random_spectrum_velocity(5, kmax=4, L=1.0), X, 2)))
+    dt = synth.cfl_dt(X, 2, np.abs(d.to_lattice(U)).max(), 0.0)
+    E = [d.energy(U)]
+    for _ in range(6):
+        U = d.rk3_step(U, dt, 1)
+        E.append(d.energy(U))
+    assert np.all(np.diff(E) <= 1e-14 * E[0]) and E[-1] < E[0]
+    rate = -2.0 * d.upwind_dissipation(U)
+    for h in (1e-3, 5e-4):
+        est = (d.energy(d.rk3_step(U, h, 1)) - d.energy(U)) / h
+        assert abs(est - rate) < 50 * h * abs(rate) + 1e-12
 
 
 # ------------------------------------------------------------ space dimensions
