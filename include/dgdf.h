@@ -23,10 +23,14 @@
  * Mesh: n_tri counter-clockwise triangles. tri_vertex_ids[t][c] (int64) is the
  *   id of corner c after periodic identification; tri_coords[t][c][0..1]
  *   (double) are the unwrapped corner coordinates, so every triangle keeps its
- *   true shape next to a periodic seam. The mesh must be closed: every edge is
- *   shared by exactly two triangles (periodic or interior facets, Sec. 2.1);
- *   an edge with one triangle is a boundary facet, which this version rejects
- *   with DG_ERR_UNSUPPORTED.
+ *   true shape next to a periodic seam. An edge shared by two triangles is an
+ *   interior (or periodic) facet; an edge with one triangle is a wall, a
+ *   free-slip boundary facet (the wall conditions of the Navier-Stokes system
+ *   of Sec. 3: u.n = 0 and zero tangential stress). There the facet multiplier
+ *   enforces u.n = 0 and L(u) has no term: the convective flux vanishes with
+ *   u.n, and the SIPG form of eq. (18) sums over interior facets only. An edge
+ *   with three or more triangles is DG_ERR_MESH. Inflow and outflow boundaries
+ *   are not supported.
  * Local facet e of a triangle is the edge opposite corner e. Two edges are the
  *   same facet when they join the same identified vertices in the same
  *   canonical order and have equal edge vectors; the canonical direction of a
@@ -65,7 +69,7 @@ typedef enum {
   DG_OK = 0,
   DG_ERR_INVALID_ARG = -1,   /* bad pointer, size or parameter */
   DG_ERR_MESH = -2,          /* degenerate / clockwise triangle, inconsistent facet */
-  DG_ERR_UNSUPPORTED = -3,   /* boundary facets, degree out of range */
+  DG_ERR_UNSUPPORTED = -3,   /* degree out of range, lattice structure absent where required */
   DG_ERR_CUDA = -4,          /* a CUDA runtime call failed */
   DG_ERR_NOT_CONVERGED = -5, /* a facet-system solve hit cg_maxit (state is still updated) */
   DG_ERR_NONFINITE = -6,     /* NaN/Inf in an input or in a solver residual */
@@ -85,8 +89,8 @@ typedef struct {
   double cg_rtol;     /* facet solve stops at ||g - S lam||_2 <= cg_rtol ||g||_2 (<= 0: 1e-13) */
   int cg_maxit;       /* iteration cap per solve (<= 0: 20000) */
   void* cuda_stream;  /* cudaStream_t to enqueue on (NULL: default stream) */
-  int precond;        /* DG_PRECOND_AUTO: on a translation-invariant split-square mesh with N a
-                         power of two, precondition with the exact Fourier-space inverse of the
+  int precond;        /* DG_PRECOND_AUTO: on a translation-invariant split-square mesh (a torus,
+                         no walls), precondition with the exact Fourier-space inverse of the
                          block-circulant facet operator (FP32 in the mixed form, FP64 in the FP64
                          form), else block Jacobi; DG_PRECOND_BLOCK_JACOBI: always block Jacobi */
 } dg_params;

@@ -21,8 +21,9 @@ extern "C" {
  * NULL it receives the facet of each local facet; tri_orient (int8 [n_tri][3])
  * +1 / -1 when the triangle traverses it along / against its canonical
  * direction; facet_tri (int32 [n_facet][2]) its two triangles, first
- * appearance first; all three must then hold the sizes above (call once with
- * NULLs to get n_facet). Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED. */
+ * appearance first, -1 as the second on a wall (an edge with one triangle);
+ * all three must then hold the sizes above (call once with NULLs to get
+ * n_facet). Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH. */
 int dg_host_topology(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords,
                      int64_t* n_facet, int32_t* tri_facet, int8_t* tri_orient, int32_t* facet_tri);
 

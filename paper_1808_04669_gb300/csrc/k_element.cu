@@ -60,6 +60,7 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
     const int tn = m.tri_nbr[size_t(t) * 3 + e];
+    if (tn < 0) continue;   // a wall adds no term (u.n = 0 there; SIPG on interior facets only)
     const int en = m.tri_nbr_loc[size_t(t) * 3 + e];
     const double* geon = m.geo + size_t(m.tri_class[tn]) * kGeo;
     const R sn = R(geon[G_S]);
@@ -190,6 +191,7 @@ __device__ void element_adjoint(const DevMesh& m, const SmemTables<K, double>& T
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
     const int tn = m.tri_nbr[size_t(t) * 3 + e];
+    if (tn < 0) continue;   // walls: no term in the forward residual, none in its transpose
     const int en = m.tri_nbr_loc[size_t(t) * 3 + e];
     const double* geon = m.geo + size_t(m.tri_class[tn]) * kGeo;
     const double sn = geon[G_S];
@@ -541,9 +543,11 @@ __global__ void __launch_bounds__(128) k_diagnostics(DevMesh m, const double* co
       dmax = fmax(dmax, fabs(g00 + g11));
     }
     for (int e = 0; e < 3; ++e) {
-      const int tn = m.tri_nbr[size_t(t) * 3 + e];
-      const int el = m.tri_nbr_loc[size_t(t) * 3 + e];
-      const double sn = m.geo[size_t(m.tri_class[tn]) * kGeo + G_S];
+      // on a wall the jump is u.n itself: the missing side counts as zero
+      const int tnr = m.tri_nbr[size_t(t) * 3 + e];
+      const int tn = tnr < 0 ? t : tnr;
+      const int el = tnr < 0 ? e : m.tri_nbr_loc[size_t(t) * 3 + e];
+      const double sn = tnr < 0 ? 0.0 : m.geo[size_t(m.tri_class[tn]) * kGeo + G_S];
       const double n0 = geo[G_NRM + 2 * e], n1 = geo[G_NRM + 2 * e + 1];
       double cn[ND];
       load_coef<ND>(coef + size_t(tn) * ND, cn);

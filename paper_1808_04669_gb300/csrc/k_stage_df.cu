@@ -81,14 +81,18 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
   // ---- facet terms
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
-    const int tn = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
-    const int en = __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
+    // A wall (no neighbour) adds no term. It is evaluated against its own trace with weight
+    // zero, so that both threads of every pair still reach each shuffle.
+    const int tnr = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
+    const bool wall = tnr < 0;
+    const int tn = wall ? t : tnr;
+    const int en = wall ? e : __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
     const int ncls = __ldg(&m.tri_class[tn]);
     const float2* geon = m.geo_df + size_t(ncls) * kGeo;
     const dfl sn = to_dfl(geon[G_S]);
     const dfl n0 = to_dfl(geo[G_NRM + 2 * e]), n1 = to_dfl(geo[G_NRM + 2 * e + 1]);
     const dfl nc = c ? n1 : n0;
-    const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
+    const dfl lens = wall ? dfl(0) : to_dfl(geo[G_FLEN + e]) * s;
     const dfl sig = to_dfl(m.sigma_df[__ldg(&m.tri_facet[size_t(t) * 3 + e])]);
     const dfl nusig = nu * sig, hnu = half(nu);
     dfl un[NS];
@@ -274,13 +278,16 @@ __device__ __forceinline__ void residual_pairs(const DevMesh& m, const PairTable
   // ---- facet terms
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
-    const int tn = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
-    const int en = __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
+    // a wall: own trace, weight zero (see residual_component)
+    const int tnr = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
+    const bool wall = tnr < 0;
+    const int tn = wall ? t : tnr;
+    const int en = wall ? e : __ldg(&m.tri_nbr_loc[size_t(t) * 3 + e]);
     const int ncls = __ldg(&m.tri_class[tn]);
     const dfl sn = to_dfl(m.geo_df[size_t(ncls) * kGeo + G_S]);
     const dfl n0 = to_dfl(geo[G_NRM + 2 * e]), n1 = to_dfl(geo[G_NRM + 2 * e + 1]);
     const dfl nc = c ? n1 : n0;
-    const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
+    const dfl lens = wall ? dfl(0) : to_dfl(geo[G_FLEN + e]) * s;
     const dfl sig = to_dfl(m.sigma_df[__ldg(&m.tri_facet[size_t(t) * 3 + e])]);
     const dfl nusig = nu * sig, hnu = half(nu);
     const dfl msn = -sn;   // the neighbour's table holds derivatives along its own normal, -n

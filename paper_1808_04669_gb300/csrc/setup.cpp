@@ -491,9 +491,10 @@ int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology&
       ++j;
     }
     size_t cnt = j - i;
-    if (cnt == 1) {
-      err = "mesh: edge of triangle " + std::to_string(p.slot / 3) + " has no neighbour (boundary facets are not supported)";
-      return DG_ERR_UNSUPPORTED;
+    if (cnt == 1) {   // a wall: the facet has one side
+      groups.push_back({keys[order[i]].slot, -1});
+      i = j;
+      continue;
     }
     if (cnt != 2) {
       err = "mesh: an edge is shared by " + std::to_string(cnt) + " triangles";
@@ -515,11 +516,13 @@ int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology&
   }
   topo.tri_facet.assign(size_t(n_tri) * 3, -1);
   topo.tri_orient.assign(size_t(n_tri) * 3, 0);
-  topo.facet_tri.resize(size_t(topo.n_facet) * 2);
-  topo.facet_loc.resize(size_t(topo.n_facet) * 2);
+  topo.facet_tri.assign(size_t(topo.n_facet) * 2, -1);
+  topo.facet_loc.assign(size_t(topo.n_facet) * 2, -1);
+  topo.n_boundary = 0;
   for (int64_t f = 0; f < topo.n_facet; ++f) {
     int64_t sl[2] = {groups[f].s0, groups[f].s1};
-    for (int s = 0; s < 2; ++s) {
+    if (sl[1] < 0) ++topo.n_boundary;
+    for (int s = 0; s < (sl[1] < 0 ? 1 : 2); ++s) {
       topo.facet_tri[f * 2 + s] = int32_t(sl[s] / 3);
       topo.facet_loc[f * 2 + s] = int8_t(sl[s] % 3);
       topo.tri_facet[sl[s]] = int32_t(f);
@@ -747,9 +750,11 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
   // neighbours and penalties
   hm.tri_nbr.resize(size_t(n_tri) * 3);
   hm.tri_nbr_loc.resize(size_t(n_tri) * 3);
+  // (a wall side has no neighbour: -1, -1)
   for (int64_t f = 0; f < T.n_facet; ++f)
     for (int s = 0; s < 2; ++s) {
       int32_t t = T.facet_tri[f * 2 + s], o = T.facet_tri[f * 2 + 1 - s];
+      if (t < 0) continue;
       int e = T.facet_loc[f * 2 + s];
       hm.tri_nbr[size_t(t) * 3 + e] = o;
       hm.tri_nbr_loc[size_t(t) * 3 + e] = T.facet_loc[f * 2 + 1 - s];
@@ -759,8 +764,10 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
     return std::max(c.flen[0], std::max(c.flen[1], c.flen[2]));
   };
   hm.facet_sigma.resize(T.n_facet);
-  for (int64_t f = 0; f < T.n_facet; ++f)
-    hm.facet_sigma[f] = alpha * k * k / std::max(diam(T.facet_tri[f * 2]), diam(T.facet_tri[f * 2 + 1]));
+  for (int64_t f = 0; f < T.n_facet; ++f) {
+    const int32_t t0 = T.facet_tri[f * 2], t1 = T.facet_tri[f * 2 + 1];
+    hm.facet_sigma[f] = alpha * k * k / std::max(diam(t0), diam(t1 < 0 ? t0 : t1));
+  }
   // facet stencils: row F = sum over both sides T of D(sigma_e) S_T[e][e'] D(sigma_e') lam_{F_e'}
   // with D(sigma) = diag(sigma^m) mapping the global (canonical) coefficients to T's own.
   hm.facet_nbr.resize(size_t(T.n_facet) * 4);
@@ -770,9 +777,12 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
   hm.stencil_blocks.clear();
   hm.stencil_binv.clear();
   const int L3 = 3 * nl;
+  // A wall facet has one side: its row couples only to the other two facets of that side
+  // (slots 3 and 4 point at the facet itself with zero blocks).
   for (int64_t f = 0; f < T.n_facet; ++f) {
     int side_order[2] = {0, 1};
-    {
+    const int nside = T.facet_tri[f * 2 + 1] < 0 ? 1 : 2;
+    if (nside == 2) {
       int32_t t0 = T.facet_tri[f * 2], t1 = T.facet_tri[f * 2 + 1];
       auto key0 = std::make_pair(hm.tri_class[t0], int(T.facet_loc[f * 2]));
       auto key1 = std::make_pair(hm.tri_class[t1], int(T.facet_loc[f * 2 + 1]));
@@ -780,7 +790,12 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
     }
     std::vector<int64_t> key;
     hm.facet_side0[f] = T.facet_tri[f * 2 + side_order[0]];
-    for (int si = 0; si < 2; ++si) {
+    if (nside == 1) {
+      key.push_back(-1);
+      hm.facet_nbr[f * 4 + 2] = int32_t(f);
+      hm.facet_nbr[f * 4 + 3] = int32_t(f);
+    }
+    for (int si = 0; si < nside; ++si) {
       int s = side_order[si];
       int32_t t = T.facet_tri[f * 2 + s];
       int e = T.facet_loc[f * 2 + s];
@@ -795,7 +810,7 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
       int32_t id = int32_t(st.size());
       it = st.emplace(key, id).first;
       std::vector<double> blk(size_t(5) * nl * nl, 0.0);
-      for (int si = 0; si < 2; ++si) {
+      for (int si = 0; si < nside; ++si) {
         int s = side_order[si];
         int32_t t = T.facet_tri[f * 2 + s];
         int e = T.facet_loc[f * 2 + s];
@@ -942,6 +957,10 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& L, bool eig_hal
   L = Lattice();
   const Topology& T = hm.topo;
   const int64_t n = T.n_tri;
+  if (T.n_boundary > 0) {
+    L.why = "the mesh has walls (boundary facets)";
+    return;
+  }
   const int N = int(std::llround(std::sqrt(double(n) / 2.0)));
   if (int64_t(2) * N * N != n) {
     L.why = "triangle count is not 2 N^2";

@@ -48,8 +48,9 @@ struct Topology {
   int64_t n_tri = 0, n_facet = 0;
   std::vector<int32_t> tri_facet;   // [n_tri][3]
   std::vector<int8_t> tri_orient;   // [n_tri][3] +1 along canonical direction, -1 against
-  std::vector<int32_t> facet_tri;   // [n_facet][2] first appearance first
-  std::vector<int8_t> facet_loc;    // [n_facet][2]
+  std::vector<int32_t> facet_tri;   // [n_facet][2] first appearance first; -1: a wall's missing side
+  std::vector<int8_t> facet_loc;    // [n_facet][2] (-1 likewise)
+  int64_t n_boundary = 0;           // wall facets (one side)
 };
 
 // Split-square lattice structure of a translation-invariant periodic mesh: facets
@@ -77,8 +78,8 @@ struct HostMesh {
   RefTables ref;
   std::vector<int32_t> tri_class;   // [n_tri]
   std::vector<ClassOps> classes;
-  std::vector<int32_t> tri_nbr;     // [n_tri][3] neighbour across local facet e
-  std::vector<int8_t> tri_nbr_loc;  // [n_tri][3] the neighbour's local index of that facet
+  std::vector<int32_t> tri_nbr;     // [n_tri][3] neighbour across local facet e (-1: wall)
+  std::vector<int8_t> tri_nbr_loc;  // [n_tri][3] the neighbour's local index of that facet (-1: wall)
   std::vector<double> facet_sigma;  // [n_facet] alpha k^2 / h_F, h_F = max diameter of the two triangles
   // Facet-system stencil: row F couples to itself and to the other two facets of
   // each adjacent triangle. Rows with equal blocks share a stencil class.

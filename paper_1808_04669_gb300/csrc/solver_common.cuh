@@ -89,7 +89,7 @@ __device__ __forceinline__ void block_apply(const R* __restrict__ B, const R (&x
   }
 }
 
-// g_F = sum over both sides of facet f of the side's condensation output mapped to
+// g_F = sum over both sides of facet f (one on a wall) of the side's condensation output mapped to
 // the facet's canonical orientation (odd Legendre modes change sign when a side
 // traverses the facet backwards). Mixed form: the sides' double-float values are
 // summed in double-float and rounded to FP64 once.
@@ -110,6 +110,7 @@ __device__ __forceinline__ void assemble_g(const DevMesh& m, int f, double (&gv)
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+    if (t < 0) break;   // a wall has one side
     const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
     const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
 #pragma unroll
@@ -128,6 +129,7 @@ __device__ __forceinline__ void assemble_g_df(const DevMesh& m, int f, dfl (&gv)
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const int t = __ldg(&m.facet_tri[size_t(f) * 2 + s]);
+    if (t < 0) break;   // a wall has one side
     const int e = __ldg(&m.facet_loc[size_t(f) * 2 + s]);
     const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
 #pragma unroll

@@ -222,6 +222,68 @@ def test_step_rejects_unknown_scheme(g):
     assert e.value.code == -1
 
 
+# ------------------------------------------------------- walls (free slip)
+def box(g, N, k, nu, precision=0):
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=False)
+    return g.DGMesh(vid, X, k, nu, precision=precision), Discretization(vid, X, k, nu), X
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_wall_projection_parity(g, k):
+    # a random field in a box: the projection has no normal velocity on the walls
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh, d, X = box(g, 3, k, 0.0, prec)
+        v = random_lattice(mesh.n_tri, k, 11 + k)
+        mesh.set_velocity(v)
+        mesh.project_divfree()
+        ref = d.to_lattice(d.project(d.from_lattice(v)))
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+        assert mesh.solver_stats()["lattice"] == 0.0
+        dg = mesh.diagnostics()
+        assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-10
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_wall_taylor_green_cell_rk3_parity(g, k):
+    # Taylor-Green cell on the unit square with free-slip walls, 12 SSP-RK3 steps
+    nu = 1e-2
+    vid, X = synth.split_square_mesh(6, L=1.0, periodic=False)
+    vals = synth.sample_lattice(synth.taylor_green(L=2.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.abs(vals).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    U = d.rk3_step(d.project(d.from_lattice(vals)), dt, 12)
+    ref = d.to_lattice(U)
+    od = d.diagnostics(U)
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.rk3_step(dt, 12)
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+        dg = mesh.diagnostics()
+        assert abs(dg["energy"] - od["energy"]) < 1e-9 * od["energy"]
+        assert dg["max_jump"] < 1e-11
+
+
+def test_wall_rk4_and_pressure_parity(g):
+    # RK4 through dg_step and the pressure of the final state, with walls
+    k, nu = 2, 1e-3
+    vid, X = synth.split_square_mesh(5, L=1.0, periodic=False)
+    vals = synth.sample_lattice(synth.random_spectrum_velocity(3, kmax=3, L=1.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.abs(vals).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    U = d.rk4_step(d.project(d.from_lattice(vals)), dt, 3)
+    w, lam = d.pressure(U)
+    pe_ref, pf_ref = d.pressure_lattice(w, lam)
+    mesh = g.DGMesh(vid, X, k, nu)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    mesh.step(dt, 3, scheme=g.RK4)
+    assert rel(mesh.get_velocity(), d.to_lattice(U)) < TOL64
+    pe, pf = mesh.get_pressure()
+    assert rel(pe, pe_ref) < 1e-11 and rel(pf, pf_ref) < 1e-11
+
+
 @pytest.mark.parametrize("precond", [0, 1])
 def test_mixed_precision_taylor_green(g, precond):
     vid, X, vals, dt = synth.make_workload("tgv_n8_k2")

@@ -113,12 +113,49 @@ def test_library_topology_on_a_perturbed_periodic_mesh(g):
     assert np.array_equal(tf, T.tri_facet) and np.array_equal(ft, T.facet_tri)
 
 
-def test_library_rejects_open_and_clockwise_meshes(g):
+def test_library_topology_with_walls_matches_oracle(g):
+    # an edge with one triangle is a wall: its second side is -1 in both conventions
+    from oracle.mesh import Topology
+    box = synth.split_square_mesh(3, L=1.0, periodic=False)
+    vid, X = synth.split_square_mesh(3)
+    holed = (vid[:-1], X[:-1])                   # the torus with one triangle cut out
+    for vid, X in (box, holed):
+        tf, to, ft = g.host_topology(vid, X)
+        T = Topology(vid, X)
+        assert np.array_equal(tf, T.tri_facet) and np.array_equal(ft, T.facet_tri)
+        assert (ft[:, 1] < 0).sum() == T.boundary.sum() > 0
+
+
+def _legendre_from_bernstein(k):
+    # columns: sqrt(2m+1) P_m(2t-1) in the Bernstein basis C(k,j) t^j (1-t)^(k-j) of [0, 1]
+    from math import comb
+    from numpy.polynomial import legendre
+    t = np.linspace(0.05, 0.95, k + 1)
+    bern = np.array([[comb(k, j) * x ** j * (1 - x) ** (k - j) for j in range(k + 1)] for x in t])
+    leg = np.array([[np.sqrt(2 * m + 1) * legendre.legval(2 * x - 1, [0] * m + [1]) for m in range(k + 1)] for x in t])
+    return np.linalg.solve(bern, leg)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_facet_operator_with_walls_matches_oracle(g, k):
+    # the library's condensed facet system on a box equals the oracle's (Bernstein multipliers)
+    # after the change to the library's Legendre facet basis; one-dimensional kernel
+    from oracle import Discretization
+    vid, X = synth.split_square_mesh(3, L=1.0, periodic=False)
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    S = _dense_S(nbr, st, blk)
+    d = Discretization(vid, X, k, 0.0)
+    B = np.kron(np.eye(d.n_facet), _legendre_from_bernstein(k))
+    So = B.T @ d.prepare()["S"].toarray() @ B
+    assert np.abs(So - S).max() < 1e-13 * np.abs(S).max()
+    ev = np.linalg.eigvalsh(S)
+    assert (ev < 1e-10 * ev[-1]).sum() == 1
+    assert g.host_lattice(vid, X, k) is None           # walls: no Fourier preconditioner
+
+
+def test_library_rejects_clockwise_meshes(g):
     from paper_1808_04669_gb300 import DGError
     vid, X = synth.split_square_mesh(3)
-    with pytest.raises(DGError) as e:
-        g.host_topology(vid[:-1], X[:-1])
-    assert e.value.code == -3            # DG_ERR_UNSUPPORTED: boundary facets
     Xc = X.copy()
     Xc[0, [1, 2]] = Xc[0, [2, 1]]
     vc = vid.copy()
