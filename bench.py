@@ -41,8 +41,8 @@ L2_FLUSH_BYTES = 512 << 20
 # over the three stages of a step (the first stage reads one state, the others two), from the
 # ncu capture summarised in profiles/; used only while the stage-kernel sources still hash to
 # the captured `sha`, else the line reports null.
-NCU_TRAFFIC = {"stage_residual": {"sha": "bdf1e9622a4f6c49", "n_tri": 131072, "bytes": 41033984,
-                                  "source": "profiles/k_stage_df_shear_n256_k3.md"}}
+NCU_TRAFFIC = {"stage_residual": {"sha": "6d6a54d8a1a24d6c", "n_tri": 131072, "bytes": 40977237,
+                                  "source": "profiles/k_stage_df2_shear_n256_k3.md"}}
 
 
 def env_rank():
@@ -322,7 +322,8 @@ def run_ours(args):
             traffic = tr["bytes"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "kernel": "k_stage<%d> (stage residual + condensation, double-float on the FP32 pipes)" % k,
+                "kernel": "%s<%d> (stage residual + condensation, double-float on the FP32 pipes)"
+                          % ("k_stage_df2" if mixed.n_class <= 4 else "k_stage_df", k),
                 "peak_source": "derived: 128 FP32 lanes/SM x 152 SMs x median SM clock %.0f MHz / %d FP32 ops "
                                "per double-float multiply-add x 2 flops" % (sm_mhz, DF_OPS_PER_FMA)}
     else:
