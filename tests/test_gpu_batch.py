@@ -19,17 +19,18 @@ def g():
     return pkg
 
 
-MEMBERS = [  # (N, k, nu, precision, perturb, L)
-    (4, 1, 1e-2, 0, 0.0, 2 * np.pi),     # lattice, FP64
-    (6, 2, 1e-3, 0, 0.0, 2 * np.pi),     # lattice, direct DFT (N not a power of two)
-    (8, 3, 0.0, 1, 0.0, 1.0),            # lattice, mixed
-    (5, 2, 1e-2, 1, 0.1, 1.0),           # perturbed (not translation invariant), mixed
+MEMBERS = [  # (N, k, nu, precision, perturb, L, periodic)
+    (4, 1, 1e-2, 0, 0.0, 2 * np.pi, True),     # lattice, FP64
+    (6, 2, 1e-3, 0, 0.0, 2 * np.pi, True),     # lattice, direct DFT (N not a power of two)
+    (8, 3, 0.0, 1, 0.0, 1.0, True),            # lattice, mixed
+    (5, 2, 1e-2, 1, 0.1, 1.0, True),           # perturbed (not translation invariant), mixed
+    (4, 3, 1e-3, 1, 0.0, 1.0, False),          # box with walls, mixed
 ]
 
 
 def make(g, spec, seed):
-    N, k, nu, prec, perturb, L = spec
-    vid, X = synth.split_square_mesh(N, L=L)
+    N, k, nu, prec, perturb, L, periodic = spec
+    vid, X = synth.split_square_mesh(N, L=L, periodic=periodic)
     if perturb:
         rng = np.random.default_rng(seed)
         X = X + (perturb * L / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
