@@ -500,6 +500,9 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     //        symmetrised (the half-spectrum transform takes S^(-kappa) = conj S^(kappa) for
     //        granted, and the host inverts each wavenumber on its own).
     const int NK = N / 2 + 1, NP = fp32 ? C + 1 + C * (C + 1) / 2 : C * C;
+    // split column pass: within a wavenumber row the even kj come first, then the odd ones
+    const bool split = dgdf::lattice_split(N);
+    auto kjs = [&](int kj) { return split ? (kj & 1) * (N / 2) + (kj >> 1) : kj; };
     const size_t nS = dgdf::lattice_symbol_elems(hm.k, N, fp32);
     std::vector<double> sd;
     std::vector<float> sf;
@@ -529,7 +532,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
               }
           }
           auto put = [&](int e, double re, double im) {
-            const size_t o = ((size_t(ki) * NP + e) * N + kj) * 2;
+            const size_t o = ((size_t(ki) * NP + e) * N + kjs(kj)) * 2;
             sf[o] = float(re);
             sf[o + 1] = float(im);
           };
@@ -556,7 +559,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
                 re = 0.5 * (re + H(ki, mj, ca, cb, 0));
                 im = 0.5 * (im - H(ki, mj, ca, cb, 1));
               }
-              const size_t o = ((size_t(ki) * NP + ca * C + cb) * N + kj) * 2;
+              const size_t o = ((size_t(ki) * NP + ca * C + cb) * N + kjs(kj)) * 2;
               sd[o] = re;
               sd[o + 1] = im;
             }
@@ -578,6 +581,11 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       float* xp = nullptr;
       if ((rc = dalloc(M, &xp, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
       d.lat_x = xp;
+      if (split) {
+        float* x2 = nullptr;
+        if ((rc = dalloc(M, &x2, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
+        d.lat_x2 = x2;
+      }
       // the mixed lattice solver keeps its multipliers and work vectors in double-float,
       // facet stride padded to an aligned access (4 for k = 2)
       d.lat_vs = nl == 3 ? 4 : nl;
@@ -596,6 +604,11 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       double* xp = nullptr;
       if ((rc = dalloc(M, &xp, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
       d.lat_x = xp;
+      if (split) {
+        double* x2 = nullptr;
+        if ((rc = dalloc(M, &x2, 2 * dgdf::lattice_spectrum_elems(hm.k, N)))) return cleanup(rc);
+        d.lat_x2 = x2;
+      }
     }
     d.lat_facet_of = fo;
     d.facet_ext = fe;
@@ -603,6 +616,8 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     d.lat_N = N;
     d.lat_bufsz = int(dgdf::lattice_buffer_elems(hm.k, N, fp32));
     d.lat_grp = dgdf::lattice_group_rows(hm.k, N, fp32);
+    d.lat_split = split ? 1 : 0;
+    d.lat_tw2_off = int(dgdf::lattice_tw2_offset(hm.k, N, fp32, d.lat_grp));
     int logn = 0;
     while ((1 << logn) < N) ++logn;
     d.lat_logn = logn;

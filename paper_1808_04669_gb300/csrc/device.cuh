@@ -92,6 +92,9 @@ struct DevMesh {
   const void* lat_sinv;               // [N/2+1][C(C+1)/2 (FP32) or C*C (FP64)][N] complex
   const double* lat_tw;               // [N][2]
   void* lat_x;                        // [C][N/2+1][N] complex work array
+  void* lat_x2;                       // the same size: inverse halves of the split column pass
+  int lat_split;                      // column pass split into even / odd wavenumbers
+  int lat_tw2_off;                    // complex elements before the N/2 twiddles in shared memory
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
@@ -159,6 +162,8 @@ cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStr
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp);
+bool lattice_split(int N);
+size_t lattice_tw2_offset(int k, int N, int fp32, int grp);
 int lattice_group_rows(int k, int N, int fp32);          // rows per transform group (0: no fit)
 size_t lattice_symbol_elems(int k, int N, int fp32);   // complex entries of the stored inverse symbol
 size_t lattice_spectrum_elems(int k, int N);   // complex entries of the spectrum work array

@@ -260,6 +260,12 @@ struct LatCtx {
   C2* bufa;               // transform data, max(C, 2(k+1)) rows of N
   C2* scr;                // scratch, grp rows of lattice_scratch_row(N)
   C2* X;                  // [C][NK][N] spectrum: half along i, full along j (then along kj)
+  // split column pass (N even, N >= 64): each column ki is two work items, the even and the
+  // odd wavenumbers kj (one decimation-in-frequency step, then transforms of length N/2);
+  // their inverse halves go to X2 and the inverse row pass adds them
+  bool split;
+  C2* tw2;                // [N/2] exp(-2 pi i t / (N/2))
+  C2* X2;                 // [C][NK][N]: [0, N/2) the even half E, [N/2, N) w^-j times the odd half
   const C2* S;            // [NK][NP][N] S^(kappa)^+ (packed upper triangle or full), kj fastest
   // vectors, facet-major [n_facet][NL] in lattice order
   typename T::V *lam, *g, *r, *q;
@@ -474,14 +480,103 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
   }
 }
 
-// Column pass: per ki, FFT along j, y = S^(kappa)^+ x (mixed form: from its deflated eigen
-// form, FP64: the full block), inverse FFT along j.
+// y = S^(kappa)^+ x for the C values x_b = cur[b rs + kc], in place; the symbol entry e is
+// S[e N + ks] (mixed form: from its deflated eigen form, FP64: the full block).
+template <int K, bool MIXED>
+__device__ __forceinline__ void symbol_product(const typename LatT<MIXED>::C2* S, int N, int ks,
+                                               typename LatT<MIXED>::C2* cur, int rs, int kc) {
+  using C2 = typename LatT<MIXED>::C2;
+  constexpr int C = LatCtx<K, MIXED>::C;
+  if constexpr (MIXED) {
+    // y = v1 (v1^H x) / mu1 + R x, R the packed Hermitian remainder (R_ba = conj R_ab)
+    C2 x[C], y[C];
+    C2 s1 = {0, 0};
+#pragma unroll
+    for (int b = 0; b < C; ++b) {
+      x[b] = cur[b * rs + kc];
+      cmad_conj(s1, __ldg(&S[size_t(b) * N + ks]), x[b]);
+    }
+    const typename LatT<MIXED>::R d1 = __ldg(&S[size_t(C) * N + ks]).x;
+    s1.x *= d1;
+    s1.y *= d1;
+#pragma unroll
+    for (int a = 0; a < C; ++a) y[a] = cmul(__ldg(&S[size_t(a) * N + ks]), s1);
+    int pi = C + 1;
+#pragma unroll
+    for (int a = 0; a < C; ++a)
+#pragma unroll
+      for (int b = a; b < C; ++b, ++pi) {
+        const C2 h = __ldg(&S[size_t(pi) * N + ks]);
+        cmad(y[a], h, x[b]);
+        if (b != a) cmad_conj(y[b], h, x[a]);
+      }
+#pragma unroll
+    for (int a = 0; a < C; ++a) cur[a * rs + kc] = y[a];
+  } else {
+    C2 x[C], y[C];
+#pragma unroll
+    for (int b = 0; b < C; ++b) {
+      x[b] = cur[b * rs + kc];
+      y[b] = C2{0, 0};
+    }
+#pragma unroll
+    for (int a = 0; a < C; ++a)
+#pragma unroll
+      for (int b = 0; b < C; ++b) cmad(y[a], __ldg(&S[size_t(a * C + b) * N + ks]), x[b]);
+#pragma unroll
+    for (int a = 0; a < C; ++a) cur[a * rs + kc] = y[a];
+  }
+}
+
+// Column pass: per ki, FFT along j, y = S^(kappa)^+ x, inverse FFT along j.
+// Split form (L.split): the work items are (ki, parity p). With h = N/2 and w = exp(-2 pi i/N),
+// one decimation-in-frequency step gives the even wavenumbers X[2k] = DFT_h(x_j + x_(j+h)) and
+// the odd ones X[2k+1] = DFT_h((x_j - x_(j+h)) w^j); after the product, item p keeps the
+// inverse half E = IDFT_h(Y_even) (p = 0) or w^-j IDFT_h(Y_odd) (p = 1) in X2, and the inverse
+// row pass takes y_j = E_j + O_j, y_(j+h) = E_j - O_j. The symbol is stored with the even kj
+// first, then the odd ones, so that each item reads a contiguous half.
 template <int K, bool MIXED>
 __device__ void columns(const LatCtx<K, MIXED>& L) {
   using C2 = typename LatT<MIXED>::C2;
   constexpr int C = LatCtx<K, MIXED>::C;
   constexpr int NP = LatCtx<K, MIXED>::NP;
   const int N = L.N, NK = L.NK;
+  if (L.split) {
+    const int h = N / 2;
+    LatCtx<K, MIXED> Lh = L;
+    Lh.N = h;
+    Lh.logn = L.logn - 1;
+    Lh.pow2 = (h & (h - 1)) == 0;
+    Lh.tw = L.tw2;
+    for (int item = blockIdx.x; item < 2 * NK; item += gridDim.x) {
+      const int ki = item >> 1, par = item & 1;
+#pragma unroll 6
+      for (int e = threadIdx.x; e < C * h; e += blockDim.x) {
+        const int c = e / h, j = e - c * h;
+        const C2* col = &L.X[(size_t(c) * NK + ki) * N];
+        const C2 a = __ldcg(&col[j]), b = __ldcg(&col[j + h]);
+        L.bufa[e] = par ? cmul(csub(a, b), L.tw[j]) : cadd(a, b);
+      }
+      __syncthreads();
+      xform(Lh, L.bufa, C, false);
+      const C2* S = L.S + size_t(ki) * NP * N;
+      for (int k = threadIdx.x; k < h; k += blockDim.x) symbol_product<K, MIXED>(S, N, par * h + k, L.bufa, h, k);
+      __syncthreads();
+      xform(Lh, L.bufa, C, true);
+      for (int e = threadIdx.x; e < C * h; e += blockDim.x) {
+        const int c = e / h, j = e - c * h;
+        C2 v = L.bufa[e];
+        if (par) {
+          C2 w = L.tw[j];
+          w.y = -w.y;
+          v = cmul(v, w);
+        }
+        L.X2[(size_t(c) * NK + ki) * N + par * h + j] = v;
+      }
+      __syncthreads();
+    }
+    return;
+  }
   for (int ki = blockIdx.x; ki < NK; ki += gridDim.x) {
 #pragma unroll 12
     for (int e = threadIdx.x; e < C * N; e += blockDim.x) {
@@ -490,49 +585,8 @@ __device__ void columns(const LatCtx<K, MIXED>& L) {
     }
     __syncthreads();
     xform(L, L.bufa, C, false);
-    C2* cur = L.bufa;
     const C2* S = L.S + size_t(ki) * NP * N;
-    for (int kj = threadIdx.x; kj < N; kj += blockDim.x) {
-      if constexpr (MIXED) {
-        // y = v1 (v1^H x) / mu1 + R x, R the packed Hermitian remainder (R_ba = conj R_ab)
-        C2 x[C], y[C];
-        C2 s1 = {0, 0};
-#pragma unroll
-        for (int b = 0; b < C; ++b) {
-          x[b] = cur[b * N + kj];
-          cmad_conj(s1, __ldg(&S[size_t(b) * N + kj]), x[b]);
-        }
-        const typename LatT<MIXED>::R d1 = __ldg(&S[size_t(C) * N + kj]).x;
-        s1.x *= d1;
-        s1.y *= d1;
-#pragma unroll
-        for (int a = 0; a < C; ++a) y[a] = cmul(__ldg(&S[size_t(a) * N + kj]), s1);
-        int pi = C + 1;
-#pragma unroll
-        for (int a = 0; a < C; ++a)
-#pragma unroll
-          for (int b = a; b < C; ++b, ++pi) {
-            const C2 h = __ldg(&S[size_t(pi) * N + kj]);
-            cmad(y[a], h, x[b]);
-            if (b != a) cmad_conj(y[b], h, x[a]);
-          }
-#pragma unroll
-        for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
-      } else {
-        C2 x[C], y[C];
-#pragma unroll
-        for (int b = 0; b < C; ++b) {
-          x[b] = cur[b * N + kj];
-          y[b] = C2{0, 0};
-        }
-#pragma unroll
-        for (int a = 0; a < C; ++a)
-#pragma unroll
-          for (int b = 0; b < C; ++b) cmad(y[a], __ldg(&S[size_t(a * C + b) * N + kj]), x[b]);
-#pragma unroll
-        for (int a = 0; a < C; ++a) cur[a * N + kj] = y[a];
-      }
-    }
+    for (int kj = threadIdx.x; kj < N; kj += blockDim.x) symbol_product<K, MIXED>(S, N, kj, L.bufa, N, kj);
     __syncthreads();
     xform(L, L.bufa, C, true);
     const C2* res = L.bufa;
@@ -565,9 +619,24 @@ __device__ void rows_inverse(const LatCtx<K, MIXED>& L, bool with_old, typename 
     for (int e = threadIdx.x; e < npair * NK * NL; e += blockDim.x) {
       const int pr = e % npair, rest = e / npair;
       const int ki = rest % NK, mm = rest / NK;
-      const C2* src = &L.X[(size_t(ty * NL + mm) * NK + ki) * N + j0 + 2 * pr];
-      const C2 ya = __ldcg(src);
-      const C2 yb = (2 * pr + 1 < rows) ? __ldcg(src + 1) : C2{0, 0};
+      C2 ya, yb = C2{0, 0};
+      if (L.split) {
+        // y_j = E_j + O_j and y_(j+h) = E_j - O_j from the two halves of the split pass
+        const int h = N >> 1;
+        const C2* src = &L.X2[(size_t(ty * NL + mm) * NK + ki) * N];
+        const int ja = j0 + 2 * pr, jb = ja + 1;
+        const int ra = ja < h ? ja : ja - h, rb = jb < h ? jb : jb - h;
+        const C2 ea = __ldcg(&src[ra]), oa = __ldcg(&src[h + ra]);
+        ya = ja < h ? cadd(ea, oa) : csub(ea, oa);
+        if (2 * pr + 1 < rows) {
+          const C2 eb = __ldcg(&src[rb]), ob = __ldcg(&src[h + rb]);
+          yb = jb < h ? cadd(eb, ob) : csub(eb, ob);
+        }
+      } else {
+        const C2* src = &L.X[(size_t(ty * NL + mm) * NK + ki) * N + j0 + 2 * pr];
+        ya = __ldcg(src);
+        if (2 * pr + 1 < rows) yb = __ldcg(src + 1);
+      }
       C2* w = L.bufa + (pr * NL + mm) * N;
       w[ki] = C2{ya.x - yb.y, ya.y + yb.x};
       if (ki > 0 && N - ki >= NK) w[N - ki] = C2{ya.x + yb.y, yb.x - ya.y};
@@ -743,6 +812,9 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   L.scr = L.bufa + m.lat_bufsz;
   L.X = reinterpret_cast<C2*>(m.lat_x);
   L.S = reinterpret_cast<const C2*>(m.lat_sinv);
+  L.split = m.lat_split != 0;
+  L.tw2 = reinterpret_cast<C2*>(smem_raw) + m.lat_tw2_off;
+  L.X2 = reinterpret_cast<C2*>(m.lat_x2);
   V* p;
   if constexpr (MIXED) {
     L.lam = m.lam_df;
@@ -760,6 +832,9 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     p = m.pa;
   }
   for (int t = threadIdx.x; t < L.N; t += blockDim.x) L.tw[t] = C2{R(m.lat_tw[2 * t]), R(m.lat_tw[2 * t + 1])};
+  if (L.split)
+    for (int t = threadIdx.x; t < L.N / 2; t += blockDim.x)
+      L.tw2[t] = C2{R(m.lat_tw[4 * t]), R(m.lat_tw[4 * t + 1])};
   __syncthreads();
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
@@ -1012,9 +1087,15 @@ size_t lattice_scratch_row(int N) {
   return (1 << logn) == N ? size_t(N) + (size_t(1) << (logn / 2)) : size_t(N);
 }
 
+bool lattice_split(int N) { return N % 2 == 0 && N >= 64; }
+
+size_t lattice_tw2_offset(int k, int N, int fp32, int grp) {
+  return size_t(N) + lattice_buffer_elems(k, N, fp32) + size_t(grp) * lattice_scratch_row(N);
+}
+
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp) {
   const size_t cx = fp32 ? 8 : 16;
-  return (size_t(N) + lattice_buffer_elems(k, N, fp32) + size_t(grp) * lattice_scratch_row(N)) * cx;
+  return (lattice_tw2_offset(k, N, fp32, grp) + (lattice_split(N) ? size_t(N / 2) : 0)) * cx;
 }
 
 // Rows per transform group: all of them if two blocks per SM still fit, else the most
