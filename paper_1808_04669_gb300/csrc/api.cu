@@ -225,7 +225,7 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
   // lattice solver inside a step: warm start from the same stage of the last two steps.
-  // lam_s is b_s dt times a smooth function of time, so with equal step sizes the linear
+  // lam_s is c_s dt times a smooth function of time, so with equal step sizes the linear
   // extrapolation 2 lam(n-1) - lam(n-2) is second-order accurate; one entry, or a changed
   // step size, gives lam(n-1) rescaled by dt / dt(n-1).
   if (M->use_lattice && stage >= 0 && M->hist_n[stage] >= 1) {
