@@ -435,6 +435,68 @@ def run_ensemble(args):
                                  "graph": "one captured CUDA graph per step (dg_batch_rk3_step)"}}), flush=True)
 
 
+def run_schemes(args):
+    """The other explicit schemes and walls (mixed form, device-timed, L2 flushed between steps):
+    SSP-RK3, forward Euler and RK4 on the bench workload, and SSP-RK3 on the Taylor-Green cell
+    in a box with free-slip walls (block-Jacobi facet solves). Units: broken velocity DOFs times
+    the stages of each step."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(env_rank()[2])
+    from paper_1808_04669_gb300 import build as _b
+    _b.build()
+    import paper_1808_04669_gb300 as g
+    import synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(mesh, dt, scheme, K, W):
+        mesh.step(dt, W, scheme=scheme)
+        torch.cuda.synchronize()
+        st0 = mesh.solver_stats()
+        total = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(K):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            mesh.step(dt, 1, scheme=scheme)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        st1 = mesh.solver_stats()
+        its = (st1["total_iters"] - st0["total_iters"]) / max(st1["solves"] - st0["solves"], 1)
+        return total / K, its
+
+    out = {"mode": "schemes", "unit": UNIT, "dtype": "f32x2 (double-float) element kernels, f64 state",
+           "data": "synthetic", "steps": args.steps, "warmup": args.warmup, "results": []}
+    vid, X, vals, dt = synth.make_workload(WORKLOAD, N=args.n)
+    w = synth.WORKLOADS[WORKLOAD]
+    for name, scheme, stages in (("ssprk3", g.SSPRK3, 3), ("euler", g.EULER, 1), ("rk4", g.RK4, 4)):
+        m = g.DGMesh(vid, X, w.k, w.nu, precision=g.MIXED, stream=stream.cuda_stream)
+        m.set_velocity(vals)
+        m.project_divfree()
+        ms, its = timed(m, dt, scheme, args.steps, args.warmup)
+        out["results"].append({"workload": workload_label(w, args.n or w.N, m.n_tri), "scheme": name,
+                               "ms_per_step": ms, "iters_per_solve": its,
+                               "value": m.n_tri * (w.k + 1) * (w.k + 2) * stages / (ms * 1e-3)})
+        m.close()
+    N, k, nu = args.n or 128, 3, 1e-4
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=False)
+    vals = synth.sample_lattice(synth.taylor_green(L=2.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.abs(vals).max()), nu)
+    m = g.DGMesh(vid, X, k, nu, precision=g.MIXED, stream=stream.cuda_stream)
+    m.set_velocity(vals)
+    m.project_divfree()
+    ms, its = timed(m, dt, g.SSPRK3, args.steps, args.warmup)
+    out["results"].append({"workload": "Taylor-Green cell, unit square with free-slip walls, %dx%d split squares "
+                                       "(%d triangles), BDM_%d, nu=%g, block-Jacobi PCG" % (N, N, m.n_tri, k, nu),
+                           "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
+                           "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
+    m.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Gradient workload: 128 x 128 unit square, BDM_2, nu = 1e-3, random-spectrum u0 (seed 3) and
     target (seed 4), loss 1/2 ||u_K - u*||^2, K = 200 SSP-RK3 steps, checkpoints every 20 steps;
@@ -556,8 +618,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=("step", "ensemble", "adjoint"), default="step",
-                    help="step: the bench line; ensemble / adjoint: the batching and gradient workloads")
+    ap.add_argument("--mode", choices=("step", "ensemble", "adjoint", "schemes"), default="step",
+                    help="step: the bench line; ensemble / adjoint / schemes: the batching, gradient, "
+                         "time-scheme and wall workloads")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--steps-adjoint", type=int, default=200)
     ap.add_argument("--reps", type=int, default=1)
@@ -577,6 +640,8 @@ def main():
         run_ensemble(args)
     elif args.mode == "adjoint":
         run_adjoint(args)
+    elif args.mode == "schemes":
+        run_schemes(args)
     else:
         run_ours(args)
 
