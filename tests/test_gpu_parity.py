@@ -284,6 +284,26 @@ def test_wall_rk4_and_pressure_parity(g):
     assert rel(pe, pe_ref) < 1e-11 and rel(pf, pf_ref) < 1e-11
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_split_column_pass_parity_n64(g, k):
+    # N = 64: the lattice solver splits each column into even and odd wavenumbers (N/2+1 <= SMs);
+    # results follow the oracle and the warm-started solves keep their short iteration count
+    nu = 1e-4
+    vid, X = synth.split_square_mesh(64)
+    vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    ref = d.to_lattice(d.rk3_step(d.project(d.from_lattice(vals)), dt, 3))
+    for prec, tol in ((0, TOL64), (1, TOLMIX)):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.rk3_step(dt, 3)
+        assert rel(mesh.get_velocity(), ref) < tol, prec
+        st = mesh.solver_stats()
+        assert st["lattice"] == 1.0 and st["total_iters"] / st["solves"] <= 6
+
+
 @pytest.mark.parametrize("precond", [0, 1])
 def test_mixed_precision_taylor_green(g, precond):
     vid, X, vals, dt = synth.make_workload("tgv_n8_k2")
