@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   V* hist2 = static_cast<V*>(a.hist2);
   double ga = 0.0;
   Acc g0 = acc_zero(Acc{});
-#pragma unroll 2
+#pragma unroll 4
   for (int f = gtid; f < nF; f += gsz) {
     const size_t o = size_t(f) * VS;
     A gv[NL], lv[NL];
@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   } else {
     // r = sigma (g - S lam) with the constant component of g removed
     const A c0a = A(c0), sg = A(sigma);
-#pragma unroll 2
+#pragma unroll 4
     for (int f = gtid; f < nF; f += gsz) {
       const size_t o = size_t(f) * VS;
       A y[NL], gv[NL], rv[NL];
@@ -970,7 +970,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
       // p = z + beta p, q = S p = S z + beta q (each facet updates only its own entries)
       const A bt = sc.beta;
       Acc pqa[1] = {acc_zero(Acc{})};
-#pragma unroll 2
+#pragma unroll 4
       for (int f = gtid; f < nF; f += gsz) {
         const size_t o = size_t(f) * VS;
         A y[NL], pv[NL], qv[NL];
