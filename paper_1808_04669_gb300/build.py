@@ -11,6 +11,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgdf.so")
 
 CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu"]
+# (source, object name, extra flags): the lattice solver is compiled once per (k, form)
+CUDA_VARIANTS = [("k_lattice_inst.cu", "k_lattice_k%d_%d.o" % (k, m), ["-DDG_LAT_K=%d" % k, "-DDG_LAT_MIXED=%d" % m])
+                 for k in (1, 2, 3) for m in (0, 1)]
 CXX_SOURCES = ["setup.cpp", "host_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,7 +35,7 @@ def _run(cmd):
 def build(verbose=False, force=False):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in CUDA_SOURCES + CXX_SOURCES]
+    srcs = [os.path.join(CSRC, s) for s in CUDA_SOURCES + CXX_SOURCES + [v[0] for v in CUDA_VARIANTS]]
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".hpp"))]
     hdrs += [os.path.join(HERE, "..", "include", f) for f in ("dgdf.h", "dgdf_host.h")]
     if not force and os.path.exists(LIB):
@@ -44,6 +47,9 @@ def build(verbose=False, force=False):
         o = os.path.join(BUILD, s + ".o")
         jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
                      "-c", os.path.join(CSRC, s), "-o", o])
+    for s, oname, flags in CUDA_VARIANTS:
+        jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", *flags,
+                     "-c", os.path.join(CSRC, s), "-o", os.path.join(BUILD, oname)])
     for s in CXX_SOURCES:
         o = os.path.join(BUILD, s + ".o")
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-c", os.path.join(CSRC, s), "-o", o])
@@ -54,6 +60,7 @@ def build(verbose=False, force=False):
             if o.strip():
                 print(o)
     objs = [os.path.join(BUILD, s + ".o") for s in CUDA_SOURCES + CXX_SOURCES]
+    objs += [os.path.join(BUILD, v[1]) for v in CUDA_VARIANTS]
     tmp = LIB + ".tmp"
     _run([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
     os.replace(tmp, LIB)
