@@ -142,8 +142,8 @@ def element_kernel_sha():
 
 
 def stage_flops_per_triangle(k, tabulated=True):
-    """Flops of the stage kernel per triangle (FMA = 2), counted from its loops:
-    the volume rule has 3, 7, 16 points for k = 1, 2, 3 (fully symmetric, degree 3k - 1). With
+    """Flops of the stage kernel per triangle (FMA = 2), counted from its loops: the volume rule
+    has 3, 7, 16 points for k = 1, 2, 3 (fully symmetric, degree 3k - 1). With
     `tabulated` (meshes of at most 4 geometry classes, mixed form) the facet normal derivatives
     of the basis come from per-class tables: two sums per trace and per test instead of three."""
     ns = (k + 1) * (k + 2) // 2
@@ -179,7 +179,7 @@ def lattice_solver_bytes(n_facet, k, iters, solves):
 
 
 def solver_bytes(n_facet, k, iters, sweeps, solves):
-    """Algorithmic DRAM bytes of the block-Jacobi mixed facet solves (facet PCG row).
+    """Algorithmic DRAM bytes of the block-Jacobi mixed facet solves.
 
     Per inner FP32 CG iteration: 11 vector passes of 4 B per multiplier DOF
     (read z, p_old; write p_new, q; read x, p_new, r, q; write x, r, z) plus
@@ -195,19 +195,34 @@ def solver_bytes(n_facet, k, iters, sweeps, solves):
     return iters * per_iter + sweeps * per_sweep + solves * per_solve
 
 
-def fp64_peak_tflops(sm_mhz):
-    """FP64 ALU peak: 2 FP64 FMA per clock per SM (measured FMA-chain probe: 1.20 TFLOP/s) x 152 SMs."""
-    return 2 * 2 * 152 * sm_mhz * 1e6 / 1e12
+def stage_bytes_per_triangle(k):
+    """Algorithmic DRAM bytes of one stage-kernel launch per triangle (8 B per value: FP64, or a
+    double-float pair): read the states u^n and u' (one state in the first SSP-RK3 stage, where
+    both are u^n: 5/3 states on average), write h = P f (n_u values) and G f (3 (k+1) values).
+    Neighbour traces are re-read from L2."""
+    nd = (k + 1) * (k + 2)
+    return 8 * (5.0 / 3.0 * nd + nd + 3 * (k + 1))
+
+
+def sm_count():
+    """Streaming multiprocessors of the current device."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def fp64_peak_tflops(sm_mhz, sms):
+    """FP64 ALU peak: 2 FP64 FMA per clock per SM (an FMA-chain probe measured 1.20 TFLOP/s) x SMs."""
+    return 2 * 2 * sms * sm_mhz * 1e6 / 1e12
 
 
 DF_OPS_PER_FMA = 12
 
 
-def dfl_peak_tflops(sm_mhz):
-    """Double-float ALU peak in algorithmic flops: 128 FP32 lanes per SM x 152 SMs x clock, divided
-    by the 12 FP32 operations of one double-float multiply-add (exact product 2, cross terms 2,
-    TwoSum 6, error accumulation 2), times 2 flops per multiply-add."""
-    return 128 * 152 * sm_mhz * 1e6 / DF_OPS_PER_FMA * 2 / 1e12
+def dfl_peak_tflops(sm_mhz, sms):
+    """Double-float ALU peak in algorithmic flops (modelled): 128 FP32 lanes per SM x SMs x clock,
+    divided by the 12 FP32 operations of one double-float multiply-add (exact product 2, cross
+    terms 2, TwoSum 6, error accumulation 2), times 2 flops per multiply-add."""
+    return 128 * sms * sm_mhz * 1e6 / DF_OPS_PER_FMA * 2 / 1e12
 
 
 def workload_label(w, N, n_tri):
@@ -279,7 +294,7 @@ def run_ours(args):
     # FP64 form on the same initial state and step count
     fp64 = g.DGMesh(vid, X, k, w.nu, precision=g.FP64, stream=stream.cuda_stream)
     fp64.set_velocity(u0)
-    t64, _, s640, s641 = timed_steps(fp64, args.steps, args.warmup)
+    t64, prof64, s640, s641 = timed_steps(fp64, args.steps, args.warmup, profile=True)
     u64 = fp64.get_velocity()
     rel = float(np.linalg.norm(u_mixed - u64) / np.linalg.norm(u64))
     value64, _, t64_s = job_rate(dof_stage_units(fp64.n_tri, k, args.steps), t64 * 1e-3, dist, "cuda")
@@ -313,10 +328,18 @@ def run_ours(args):
     peaks = measured_peaks()
     traffic = None
     sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sms = sm_count()
+    hbm_peak = peaks.get("hbm_gbs")
+
+    def hbm_part(nbytes):
+        gbs = nbytes / per_launch_s / 1e9
+        return {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": (gbs / hbm_peak) if hbm_peak else None,
+                "bytes_per_launch": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
     if name.startswith("stage_residual"):
         flops = stage_flops_per_triangle(k, tabulated=mixed.n_class <= 4) * mixed.n_tri
         achieved = flops / per_launch_s / 1e12
-        peak = dfl_peak_tflops(sm_mhz)
+        peak = dfl_peak_tflops(sm_mhz, sms)
         tr = NCU_TRAFFIC.get("stage_residual")
         if tr and tr.get("sha") == element_kernel_sha() and tr.get("n_tri") == mixed.n_tri:
             traffic = tr["bytes"]
@@ -324,8 +347,9 @@ def run_ours(args):
                 "traffic": traffic,
                 "kernel": "%s<%d> (stage residual + condensation, double-float on the FP32 pipes)"
                           % ("k_stage_df2" if mixed.n_class <= 4 else "k_stage_df", k),
-                "peak_source": "derived: 128 FP32 lanes/SM x 152 SMs x median SM clock %.0f MHz / %d FP32 ops "
-                               "per double-float multiply-add x 2 flops" % (sm_mhz, DF_OPS_PER_FMA)}
+                "peak_source": "modelled: 128 FP32 lanes/SM x %d SMs x median SM clock %.0f MHz / %d FP32 ops "
+                               "per double-float multiply-add x 2 flops" % (sms, sm_mhz, DF_OPS_PER_FMA),
+                "hbm": hbm_part(stage_bytes_per_triangle(k) * mixed.n_tri)}
     else:
         if name.startswith("facet_pcg_fft"):
             nbytes = lattice_solver_bytes(mixed.n_facet, k, iters, solves)
@@ -338,6 +362,23 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     launches = sum(v[1] for v in prof.values())
     total_prof_ms = sum(v[0] for v in prof.values())
+    # FP64 form: its dominant kernel is the FP64 stage kernel, bound by the FP64 pipe; the HBM
+    # fraction of the same launches is reported beside it
+    name64 = max(prof64, key=lambda n_: prof64[n_][0])
+    ms64, n64 = prof64[name64]
+    per64_s = ms64 * 1e-3 / max(n64, 1)
+    roof64 = {"kernel": name64, "ms_per_launch": per64_s * 1e3,
+              "share_of_device_time": ms64 / sum(v[0] for v in prof64.values())}
+    if name64.startswith("stage_residual"):
+        a64 = stage_flops_per_triangle(k, tabulated=False) * fp64.n_tri / per64_s / 1e12
+        p64 = fp64_peak_tflops(sm_mhz, sms)
+        b64 = stage_bytes_per_triangle(k) * fp64.n_tri
+        roof64.update({"bound": "alu", "achieved": a64, "peak": p64, "unit": "TFLOP/s", "frac": a64 / p64,
+                       "peak_source": "derived: 2 FP64 FMA/clock/SM x %d SMs x median SM clock %.0f MHz x 2 flops"
+                                      % (sms, sm_mhz),
+                       "hbm": {"achieved": b64 / per64_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": (b64 / per64_s / 1e9 / hbm_peak) if hbm_peak else None,
+                               "bytes_per_launch": b64, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}})
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -355,7 +396,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roof,
         "fp64": {"value": value64, "ms_per_step": t64 / args.steps, "cg_iters_per_solve":
-                 (s641["total_iters"] - s640["total_iters"]) / max(s641["solves"] - s640["solves"], 1)},
+                 (s641["total_iters"] - s640["total_iters"]) / max(s641["solves"] - s640["solves"], 1),
+                 "roofline": roof64},
         "mixed_vs_fp64_rel_l2": rel,
         "solver": {"iters_per_solve": iters / max(solves, 1), "sweeps_per_solve": sweeps / max(solves, 1),
                    "preconditioner": "lattice FFT" if mixed.solver_stats()["lattice"] else "block Jacobi",

@@ -73,7 +73,8 @@ typedef enum {
   DG_ERR_CUDA = -4,          /* a CUDA runtime call failed */
   DG_ERR_NOT_CONVERGED = -5, /* a facet-system solve hit cg_maxit (state is still updated) */
   DG_ERR_NONFINITE = -6,     /* NaN/Inf in an input or in a solver residual */
-  DG_ERR_OOM = -7            /* device allocation failed */
+  DG_ERR_OOM = -7,           /* device allocation failed */
+  DG_ERR_UNSTABLE = -8       /* the energy watchdog saw ||u||^2 grow in a step (dg_set_energy_watchdog) */
 } dg_status;
 
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
@@ -227,6 +228,10 @@ int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
  * [n_stencil][5][k+1][k+1], binv double [n_stencil][k+1][k+1] (the layout of
  * dg_host_facet_operator), g double [n_facet][k+1], lam double [n_facet][k+1]
  * (in: initial guess; out: solution, defined up to the constant multiplier).
+ * Every facet_nbr entry must lie in [0, n_facet) and every stencil entry in
+ * [0, n_stencil) for the blocks and binv passed: the call cannot check them
+ * (it does not know n_stencil and reads no device data on the host), and an
+ * index out of range makes the kernel read outside the caller's arrays.
  * Work vectors, reductions, the grid barrier and counters live in one static
  * device array sized for n_facet*(k+1) <= 262144 multiplier DOFs (about 12.7 MB,
  * held by every GPU that loads the library until exit); larger sizes return
@@ -234,12 +239,37 @@ int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
  * device looks up that array's address (cudaGetSymbolAddress), so make the
  * first call on each device before any stream capture. Every call shares the
  * array: calls that overlap on the GPU (other streams, other threads) race.
- * The call synchronises cuda_stream. *iterations and *relres (may be NULL)
+ * The call synchronises cuda_stream before it returns (it copies its counters
+ * from the scratch array to the host). *iterations and *relres (may be NULL)
  * receive the CG iterations and final relative residual.
  * Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_NONFINITE. */
 int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, const int32_t* stencil,
                            const double* blocks, const double* binv, const double* g, double* lam, double rtol,
                            int maxit, void* cuda_stream, int* iterations, double* relres);
+
+/* Energy watchdog (failure detection; the paper has no counterpart, it rests on
+ * the energy stability of Sec. 2.2 and Sec. 3): the kinetic energy ||u||^2 of
+ * the scheme never grows for nu = 0 with upwinding (Sec. 2.2), nor with the
+ * coercive viscous form, under a stable step size. With rel_tol > 0, every step
+ * of dg_step / dg_rk3_step / dg_batch_rk3_step ends with a device reduction of
+ * ||u||^2 (orthonormal basis: the sum of squared coefficients) compared with the
+ * previous step's; growth by more than rel_tol (relative) makes the call return
+ * DG_ERR_UNSTABLE (the state is still advanced), the usual sign of a step size
+ * above the stability (CFL) limit. Setting a new state restarts the comparison.
+ * rel_tol = 0 turns it off (the default). The first call with rel_tol > 0
+ * allocates 16 KB of device memory. */
+int dg_set_energy_watchdog(dg_mesh* mesh, double rel_tol);
+
+/* Test hook of the failure detection of the facet solvers (no counterpart in the
+ * paper). Every grid barrier of the persistent solver kernels waits a bounded
+ * number of polls (default 2^26); when the wait runs out the kernel sets an error
+ * flag, every block leaves at its next barrier, and the call returns DG_ERR_CUDA
+ * ("solver grid barrier timed out") with the device context intact.
+ * spin_limit > 0 replaces the default limit for this mesh's solves (0: default);
+ * skip_block >= 0 makes that block of the solver kernel leave at its first grid
+ * barrier without arriving, so that the other blocks' wait runs out (-1: off).
+ * The state after such a solve is undefined; (0, -1) restores normal operation. */
+int dg_test_barrier_fault(dg_mesh* mesh, int64_t spin_limit, int skip_block);
 
 /* Per-kernel-class device timing. enable = 1 makes the library record a CUDA
  * event pair on its stream around every kernel launch from then on and add the

@@ -169,6 +169,14 @@ class DGMesh:
                 "lattice", "blocks")
         return dict(zip(keys, list(out)))
 
+    def set_energy_watchdog(self, rel_tol):
+        """Flag growth of ||u||^2 by more than rel_tol in a step (dg_set_energy_watchdog); 0 turns it off."""
+        check(lib().dg_set_energy_watchdog(self._h, float(rel_tol)), "dg_set_energy_watchdog")
+
+    def test_barrier_fault(self, spin_limit=0, skip_block=-1):
+        """Failure-detection test hook (dg_test_barrier_fault): bounded barrier waits of the solvers."""
+        check(lib().dg_test_barrier_fault(self._h, int(spin_limit), int(skip_block)), "dg_test_barrier_fault")
+
     def profile(self, enable):
         n = 16
         ms = (ctypes.c_double * n)()
@@ -296,6 +304,19 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
                   (g, torch.float64), (lam, torch.float64)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise ValueError("need contiguous CUDA tensors of the documented dtypes")
+    # the kernel trusts these sizes: a short array would be read or written past its end
+    nl = int(k) + 1
+    nf = facet_nbr.shape[0] if facet_nbr.dim() == 2 else -1
+    if facet_nbr.dim() != 2 or facet_nbr.shape[1] != 4:
+        raise ValueError("facet_nbr must be [n_facet, 4]")
+    if tuple(stencil.shape) != (nf,):
+        raise ValueError("stencil must be [n_facet]")
+    if g.numel() != nf * nl or lam.numel() != nf * nl:
+        raise ValueError("g and lam must hold n_facet * (k + 1) values")
+    if blocks.dim() != 4 or tuple(blocks.shape[1:]) != (5, nl, nl):
+        raise ValueError("blocks must be [n_stencil, 5, k + 1, k + 1]")
+    if tuple(binv.shape) != (blocks.shape[0], nl, nl):
+        raise ValueError("binv must be [n_stencil, k + 1, k + 1] with the n_stencil of blocks")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     it = ctypes.c_int()

@@ -11,12 +11,12 @@ LIB_PATH = os.path.join(_HERE, "libdgdf.so")
 
 DG_OK = 0
 STATUS = {0: "DG_OK", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_UNSUPPORTED", -4: "DG_ERR_CUDA",
-          -5: "DG_ERR_NOT_CONVERGED", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_OOM"}
+          -5: "DG_ERR_NOT_CONVERGED", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_OOM", -8: "DG_ERR_UNSTABLE"}
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
            "dg_project_divfree", "dg_rk3_step", "dg_step", "dg_batch_create", "dg_batch_destroy", "dg_batch_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_set_coefficients", "dg_get_coefficients",
            "dg_set_viscosity", "dg_rk3_vjp", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
-           "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
+           "dg_set_energy_watchdog", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
            "dg_host_facet_operator", "dg_host_lattice"]
 
 
@@ -58,6 +58,8 @@ def lib():
         "dg_get_diagnostics": (ctypes.c_int, [P, P]),
         "dg_get_solver_stats": (ctypes.c_int, [P, P]),
         "dg_facet_solve_noalloc": (ctypes.c_int, [ctypes.c_int, I64, P, P, P, P, P, P, D, ctypes.c_int, P, P, P]),
+        "dg_set_energy_watchdog": (ctypes.c_int, [P, D]),
+        "dg_test_barrier_fault": (ctypes.c_int, [P, I64, ctypes.c_int]),
         "dg_profile": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
         "dg_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "dg_last_error": (ctypes.c_char_p, []),

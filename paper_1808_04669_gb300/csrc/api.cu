@@ -41,13 +41,14 @@ enum KernelClass {
   KC_SOLVE_LAT32,
   KC_ADJOINT,
   KC_COMBINE,
+  KC_WATCH,
   KC_COUNT
 };
 const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure",
                                       "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32",   "adjoint",
-                                      "combine"};
+                                      "combine",             "energy_watchdog"};
 
 }  // namespace
 
@@ -62,6 +63,8 @@ struct dg_mesh {
   int lattice_blocks = 0;
   std::string lattice_why;
   double last_c = 0.0;            // coefficient of L(u') in the last stage solved
+  long long gen = 0;              // bumped by every setter that changes a kernel argument
+                                  // (dg_set_viscosity): batch graphs captured earlier are stale
   bool has_lam = false;
   // lattice solver: multipliers of each stage of the current scheme in the last two steps
   // (device, the layout of the solver's lam), their step sizes, and how many are valid
@@ -76,6 +79,10 @@ struct dg_mesh {
   double* rk_w = nullptr;
   float2* rk_w_df = nullptr;
   bool udf_valid = false;        // mixed form: u_df holds the double-float image of u
+  // energy watchdog (dg_set_energy_watchdog): after every step, flag a growth of ||u||^2 by
+  // more than watch_tol (relative); watch = [E of the last step (< 0: none yet), ratio, partials]
+  double watch_tol = 0.0;
+  double* watch = nullptr;
   double* lattice = nullptr;     // [n_tri][ns][2] staging for lattice I/O
   double* wbuf = nullptr;        // [n_tri][nw] element pressure
   double* pe = nullptr;          // [n_tri][nw] pressure lattice staging
@@ -199,6 +206,23 @@ int finish(dg_mesh* M, bool check_solver) {
   if (fl & dgdf::kFlagBarrierTimeout) return fail(DG_ERR_CUDA, "solver grid barrier timed out");
   if (fl & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
   if (fl & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached cg_maxit");
+  if (fl & dgdf::kFlagEnergyGrowth) {
+    double w[2] = {0.0, 0.0};
+    CK(cudaMemcpy(w, M->watch, sizeof(w), cudaMemcpyDeviceToHost));
+    char buf[192];
+    std::snprintf(buf, sizeof(buf),
+                  "energy watchdog: ||u||^2 grew by a factor %.6g in one step (tolerance %.3g): the step size "
+                  "exceeds the stability limit of the scheme", w[1], M->watch_tol);
+    return fail(DG_ERR_UNSTABLE, buf);
+  }
+  return DG_OK;
+}
+
+// Forget the watchdog's last energy (a new state was set): the next step only records it.
+int reset_watch(dg_mesh* M) {
+  if (!M->watch) return DG_OK;
+  const double none = -1.0;
+  CK(cudaMemcpyAsync(M->watch, &none, sizeof(double), cudaMemcpyHostToDevice, M->stream));
   return DG_OK;
 }
 
@@ -682,6 +706,7 @@ int dg_set_velocity(dg_mesh* M, const double* vals, int on_device) {
   M->has_lam = false;
   M->udf_valid = false;
   forget_history(M);
+  if ((rc = reset_watch(M))) return rc;
   return finish(M, false);
 }
 
@@ -713,6 +738,7 @@ int dg_project_divfree(dg_mesh* M) {
     return rc;
   M->has_lam = false;
   forget_history(M);
+  if ((rc = reset_watch(M))) return rc;
   return finish(M, true);
 }
 
@@ -813,6 +839,12 @@ int enqueue_step(dg_mesh* M, double dt, int scheme = DG_SCHEME_SSPRK3) {
       if (rc) return rc;
     }
   }
+  if (M->watch_tol > 0.0) {
+    rc = launch(M, KC_WATCH, [&] {
+      return dgdf::launch_energy_watch(d.u, n, M->watch, M->watch_tol, d.stats, M->stream);
+    });
+    if (rc) return rc;
+  }
   return DG_OK;
 }
 
@@ -826,6 +858,7 @@ struct dg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<double> graph_dt;
+  std::vector<long long> graph_gen;   // each member's gen when the graph was captured
 };
 
 extern "C" {
@@ -910,8 +943,11 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     if ((rc = reset_flags(M)) || (rc = ensure_udf(M))) return restore(rc);
   // The captured step assumes warm-started solves with a fixed step size: run one step
   // eagerly when any member is cold or the step sizes changed.
-  bool same_dt = B->exec && B->graph_dt.size() == n;
-  for (size_t i = 0; same_dt && i < n; ++i) same_dt = B->graph_dt[i] == dt[i];
+  // The graph holds every member's kernel arguments by value (nu among them): it is
+  // replayed only if no step size and no member's arguments changed since the capture.
+  bool same_dt = B->exec && B->graph_dt.size() == n && B->graph_gen.size() == n;
+  for (size_t i = 0; same_dt && i < n; ++i)
+    same_dt = B->graph_dt[i] == dt[i] && B->graph_gen[i] == B->members[i]->gen;
   // A member is in steady mode when its solves are warm and, on the lattice path, every
   // stage has two history entries taken with the current step size; the captured step
   // replays that mode, so steps run eagerly until all members reach it.
@@ -957,6 +993,8 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     }
     B->graph = g;
     B->graph_dt.assign(dt, dt + n);
+    B->graph_gen.resize(n);
+    for (size_t i = 0; i < n; ++i) B->graph_gen[i] = B->members[i]->gen;
   }
   for (int64_t s = done; s < nsteps; ++s) {
     cudaError_t e = cudaGraphLaunch(B->exec, B->stream);
@@ -982,6 +1020,7 @@ int dg_set_coefficients(dg_mesh* M, const double* coef, int on_device) {
   M->has_lam = false;
   M->udf_valid = false;
   forget_history(M);
+  if (int rc = reset_watch(M)) return rc;
   return finish(M, false);
 }
 
@@ -999,6 +1038,7 @@ int dg_set_viscosity(dg_mesh* M, double nu) {
   if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(DG_ERR_INVALID_ARG, "nu must be finite and >= 0");
   M->p.nu = nu;
   M->dm.nu = nu;
+  ++M->gen;
   return DG_OK;
 }
 
@@ -1268,6 +1308,28 @@ int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, con
   if (st.flags & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
   if (st.flags & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached maxit");
   return DG_OK;
+}
+
+int dg_set_energy_watchdog(dg_mesh* M, double rel_tol) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!(rel_tol >= 0.0) || !std::isfinite(rel_tol)) return fail(DG_ERR_INVALID_ARG, "rel_tol must be finite and >= 0");
+  if (rel_tol > 0.0 && !M->watch) {
+    if (int rc = dalloc(M, &M->watch, size_t(2 + dgdf::kMaxSolverBlocks))) return rc;
+  }
+  M->watch_tol = rel_tol;
+  if (int rc = reset_watch(M)) return rc;
+  return finish(M, false);
+}
+
+int dg_test_barrier_fault(dg_mesh* M, int64_t spin_limit, int skip_block) {
+  if (int rc = check_mesh(M)) return rc;
+  if (spin_limit < 0) return fail(DG_ERR_INVALID_ARG, "spin_limit must be >= 0");
+  if (skip_block < -1) return fail(DG_ERR_INVALID_ARG, "skip_block must be >= -1");
+  const unsigned long long lim = (unsigned long long)spin_limit;
+  const int skip = skip_block + 1;
+  CK(cudaMemcpyAsync(&M->dm.stats->spin_limit, &lim, sizeof(lim), cudaMemcpyHostToDevice, M->stream));
+  CK(cudaMemcpyAsync(&M->dm.stats->skip_block, &skip, sizeof(skip), cudaMemcpyHostToDevice, M->stream));
+  return finish(M, false);
 }
 
 int dg_profile(dg_mesh* M, int enable, double* out_ms, int64_t* out_launches, int n) {

@@ -11,6 +11,7 @@ enum : int {
   kFlagNotConverged = 1,
   kFlagNonFinite = 2,
   kFlagBarrierTimeout = 4,
+  kFlagEnergyGrowth = 8,
 };
 
 // Per-class geometry record (doubles): Jinv[4] row-major (d xi_r / d x_d),
@@ -29,6 +30,10 @@ struct DevStats {
   int last_sweeps;
   int pad;
   long long total_sweeps;
+  // failure-detection test hooks (dg_test_barrier_fault); zero = off
+  unsigned long long spin_limit;   // polls before a grid barrier gives up (0: kBarrierSpinLimit)
+  int skip_block;                  // 1 + the block that leaves at its first grid barrier without arriving
+  int pad2;
 };
 
 // Grid-barrier state for the persistent solver kernel.
@@ -159,6 +164,12 @@ cudaError_t launch_diagnostics(const DevMesh& m, const double* coef, cudaStream_
 cudaError_t launch_adjoint(const DevMesh& m, const double* u, const double* w, double* out, double cw, double cj,
                            int accumulate, double nu_coef, double* nu_acc, cudaStream_t s);
 cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
+// Energy watchdog: E = sum of squares of the n coefficients (the L2 norm squared in the
+// orthonormal basis); sets kFlagEnergyGrowth in st->flags when E > watch[0] (1 + tol) with
+// watch[0] >= 0, then stores E in watch[0] and E / previous in watch[1]. watch holds
+// 2 + kMaxSolverBlocks doubles (the tail takes the block partials).
+cudaError_t launch_energy_watch(const double* u, long long n, double* watch, double tol, DevStats* st,
+                                cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp);

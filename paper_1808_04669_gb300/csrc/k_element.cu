@@ -605,6 +605,31 @@ __global__ void k_check_finite(const double* v, long long n, int* flag) {
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, kFlagNonFinite);
 }
 
+__global__ void __launch_bounds__(256) k_energy_part(const double* u, long long n, double* part) {
+  double a = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = __ldcg(&u[i]);
+    a = fma(v, v, a);
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void k_energy_watch(double* watch, int nparts, double tol, DevStats* st) {
+  if (threadIdx.x >= 32) return;
+  double e = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) e += watch[2 + i];
+  e = warp_sum(e);
+  if (threadIdx.x == 0) {
+    const double prev = watch[0];
+    if (prev >= 0.0) {
+      watch[1] = prev > 0.0 ? e / prev : (e > 0.0 ? INFINITY : 1.0);
+      if (!(e <= prev * (1.0 + tol))) atomicOr(&st->flags, kFlagEnergyGrowth);
+    }
+    watch[0] = e;
+  }
+}
+
 // ------------------------------------------------------------------- launchers
 namespace {
 inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
@@ -665,6 +690,16 @@ cudaError_t launch_adjoint(const DevMesh& m, const double* u, const double* w, d
   const int nb = blocks_for(m.n_tri, 128);
   DGDF_DISPATCH_K(m.k, (k_adjoint<K><<<nb, 128, 0, s>>>(m, u, w, out, cw, cj, accumulate)));
   k_nu_accumulate<<<1, 32, 0, s>>>(m, nb, nu_coef, nu_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_watch(const double* u, long long n, double* watch, double tol, DevStats* st,
+                                cudaStream_t s) {
+  long long nb = (n + 255) / 256;
+  if (nb > 1024) nb = 1024;
+  if (nb < 1) nb = 1;
+  k_energy_part<<<int(nb), 256, 0, s>>>(u, n, watch + 2);
+  k_energy_watch<<<1, 32, 0, s>>>(watch, int(nb), tol, st);
   return cudaGetLastError();
 }
 

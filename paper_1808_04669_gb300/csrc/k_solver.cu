@@ -15,6 +15,8 @@
 // p = z + beta p is fused into the next SpMV (two p buffers), so every
 // iteration costs two grid barriers. Reductions sum block partials in a fixed
 // order, so results are bitwise reproducible for a given launch shape.
+#include <atomic>
+
 #include "device.cuh"
 #include "kcommon.cuh"
 #include "solver_common.cuh"
@@ -362,7 +364,9 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve_noalloc(DevMesh m, con
 }
 
 constexpr int kMaxDevices = 64;
-double* g_noalloc_ptr[kMaxDevices] = {};
+// Per-device address of the scratch array. Host threads may look it up concurrently: every
+// lookup on a device returns the same address, so the first store wins and later ones agree.
+std::atomic<double*> g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array for the current device, looked up once per device.
 cudaError_t noalloc_scratch(double** out) {
@@ -370,13 +374,13 @@ cudaError_t noalloc_scratch(double** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_noalloc_ptr[dev]) {
-    double* p = nullptr;
+  double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
     e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

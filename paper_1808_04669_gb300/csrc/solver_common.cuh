@@ -17,25 +17,39 @@ constexpr unsigned long long kBarrierSpinLimit = 1ull << 26;
 // add 1, so the word's top bit flips exactly when the last block arrives and
 // the low bits return to zero; a block waits for the top bit to differ from the
 // value its own add returned. The word must be zero at launch. Returns false
-// if the wait ran out, after setting kFlagBarrierTimeout.
+// if the wait ran out, after setting kFlagBarrierTimeout; once that flag is set
+// (by any block) every later barrier of the launch returns false at once, and a
+// waiting block stops waiting, so the whole grid leaves within one wait limit.
+// Test hooks (DevStats): spin_limit replaces the default limit; skip_block
+// names a block that leaves without arriving, so that the others' wait runs out.
 __device__ bool grid_sync(GridBar* bar, DevStats* st) {
   __shared__ int ok;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int nb = gridDim.x;
-    const unsigned int inc = (blockIdx.x == 0) ? (0x80000000u - (nb - 1u)) : 1u;
-    const unsigned int old = atomicAdd(&bar->count, inc);
-    volatile unsigned int* v = &bar->count;
+    volatile int* vflags = &st->flags;
+    const unsigned long long limit = st->spin_limit ? st->spin_limit : kBarrierSpinLimit;
     int good = 1;
-    unsigned long long spins = 0;
-    while (((*v ^ old) & 0x80000000u) == 0u) {
-      if (++spins > kBarrierSpinLimit) {
-        atomicOr(&st->flags, kFlagBarrierTimeout);
-        good = 0;
-        break;
+    if ((*vflags & kFlagBarrierTimeout) || int(blockIdx.x) == st->skip_block - 1) {
+      good = 0;
+    } else {
+      const unsigned int nb = gridDim.x;
+      const unsigned int inc = (blockIdx.x == 0) ? (0x80000000u - (nb - 1u)) : 1u;
+      const unsigned int old = atomicAdd(&bar->count, inc);
+      volatile unsigned int* v = &bar->count;
+      unsigned long long spins = 0;
+      while (((*v ^ old) & 0x80000000u) == 0u) {
+        if (++spins > limit) {
+          atomicOr(&st->flags, kFlagBarrierTimeout);
+          good = 0;
+          break;
+        }
+        if ((spins & 255u) == 0u && (*vflags & kFlagBarrierTimeout)) {
+          good = 0;
+          break;
+        }
+        if (spins > 32) __nanosleep(20);
       }
-      if (spins > 32) __nanosleep(20);
     }
     __threadfence();
     ok = good;

@@ -71,6 +71,29 @@ def test_batch_equals_members_stepped_alone(g):
     batch.close()
 
 
+def test_batch_sees_a_viscosity_changed_between_calls(g):
+    # the graph holds each member's kernel arguments by value: after dg_set_viscosity on a member the
+    # next batch call must not replay the old viscosity
+    specs = [MEMBERS[0], MEMBERS[2]]
+    pairs = [make(g, spec, 60 + i) for i, spec in enumerate(specs)]
+    batch_members = [p[0][0] for p in pairs]
+    solo = [p[0][1] for p in pairs]
+    dts = np.array([p[1] for p in pairs])
+    batch = g.DGBatch(batch_members)
+    batch.rk3_step(dts, 4)          # eager step, capture, replays
+    for m, dt in zip(solo, dts):
+        m.rk3_step(dt, 4)
+    for m in (batch_members[0], solo[0]):
+        m.set_viscosity(0.3)        # a large change, so a stale graph would show
+    batch.rk3_step(dts, 3)          # same step sizes: only the viscosity changed
+    for m, dt in zip(solo, dts):
+        m.rk3_step(dt, 3)
+    for mb, ms in zip(batch_members, solo):
+        a, b = mb.get_velocity(), ms.get_velocity()
+        assert np.abs(a - b).max() <= 1e-14 * max(1.0, np.abs(b).max())
+    batch.close()
+
+
 def test_batch_rejects_bad_arguments(g):
     from paper_1808_04669_gb300 import DGError
     (m, _), dt = make(g, MEMBERS[0], 1)

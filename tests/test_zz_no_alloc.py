@@ -6,11 +6,14 @@ cannot create a dg_mesh either: they hold the condensed facet operator, the
 right-hand side and the solution in memory they own, and the library keeps its
 work vectors in a static device array.
 
-The test compares it with the mesh solver behind the existing dg_get_pressure:
-that call solves S lam = g for the pressure functional and returns lam on the
-facets; feeding g = S lam to the no-allocation solve must give lam back (in the
-energy norm of S, the norm in which the velocity error is measured), on two
-calls in a row that share the static scratch.
+What the test checks: the existing entry point dg_get_pressure solves the mesh's
+facet system S lam = g for the pressure functional and returns lam on the
+facets. The no-allocation solve is given the library's own facet operator S
+(dg_host_facet_operator) and g = S lam, and must return that lam (in the energy
+norm of S, the norm in which the velocity error is measured): an S-inverse
+consistency check of the new entry point against the existing one, on two calls
+in a row that share the static scratch, from a zero and from a random initial
+guess.
 """
 import numpy as np
 import pytest
@@ -76,6 +79,7 @@ def test_noalloc_solve_matches_mesh_solver_on_two_calls(g, N, k):
     st_d = torch.from_numpy(st).to(dev)
     blk_d = torch.from_numpy(np.ascontiguousarray(blk)).to(dev)
     binv_d = torch.from_numpy(np.ascontiguousarray(binv)).to(dev)
+    iters = []
     for lam_ex in lams:                                    # two calls in a row on the shared scratch
         rhs = apply_S(nbr, st, blk, lam_ex)
         g_d = torch.from_numpy(np.ascontiguousarray(rhs)).to(dev)
@@ -85,6 +89,37 @@ def test_noalloc_solve_matches_mesh_solver_on_two_calls(g, N, k):
         lam = lam_d.cpu().numpy()
         assert it > 0 and rr <= 1e-13
         assert energy_rel(nbr, st, blk, lam, lam_ex) < TOL64
+        iters.append(it)
+    # lam is also the initial guess: a random start converges to the same solution, and a start
+    # at the solution itself needs (almost) no iterations
+    lam_ex = lams[1]
+    g_d = torch.from_numpy(np.ascontiguousarray(apply_S(nbr, st, blk, lam_ex))).to(dev)
+    lam_d = torch.from_numpy(rng.standard_normal(lam_ex.shape)).to(dev)
+    it, rr = g.facet_solve_noalloc(k, nbr_d, st_d, blk_d, binv_d, g_d, lam_d)
+    torch.cuda.synchronize()
+    assert rr <= 1e-13 and energy_rel(nbr, st, blk, lam_d.cpu().numpy(), lam_ex) < TOL64
+    lam_d = torch.from_numpy(np.ascontiguousarray(lam_ex)).to(dev)
+    it0, rr = g.facet_solve_noalloc(k, nbr_d, st_d, blk_d, binv_d, g_d, lam_d)
+    torch.cuda.synchronize()
+    assert it0 < iters[1] and energy_rel(nbr, st, blk, lam_d.cpu().numpy(), lam_ex) < TOL64
+
+
+def test_noalloc_wrapper_rejects_mismatched_shapes(g):
+    import torch
+    vid, X = synth.split_square_mesh(4)
+    k = 2
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    dev = torch.device("cuda")
+    t = {n: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for n, a in
+         (("nbr", nbr), ("st", st), ("blk", blk), ("binv", binv))}
+    nf = nbr.shape[0]
+    good_g = torch.zeros(nf, k + 1, dtype=torch.float64, device=dev)
+    with pytest.raises(ValueError):     # g one facet short
+        g.facet_solve_noalloc(k, t["nbr"], t["st"], t["blk"], t["binv"], good_g[:-1], torch.zeros_like(good_g))
+    with pytest.raises(ValueError):     # blocks of the wrong degree
+        g.facet_solve_noalloc(k + 1, t["nbr"], t["st"], t["blk"], t["binv"], good_g, torch.zeros_like(good_g))
+    with pytest.raises(ValueError):     # stencil ids for fewer facets
+        g.facet_solve_noalloc(k, t["nbr"], t["st"][:-1], t["blk"], t["binv"], good_g, torch.zeros_like(good_g))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(g):
