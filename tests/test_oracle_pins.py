@@ -317,7 +317,8 @@ def _tgv_error(N, k, nu, T, field_exact, field0, L=2 * np.pi, steps_per=None):
 
 
 def test_taylor_green_velocity_order():
-    # Example 1a / Table 1: L2 velocity error of order k + 1
+    # Example 1a / Table 1: L2 velocity error of order k + 1. For k = 3 the step shrinks as
+    # h^(4/3), so that the RK3 error (dt^3) stays below the spatial error (h^4).
     nu, T = 1e-2, 0.3
     tg = synth.taylor_green()
 
@@ -330,6 +331,58 @@ def test_taylor_green_velocity_order():
         e = [_tgv_error(N, k, nu, T, exact, tg)[0] for N in Ns]
         eoc = math.log2(e[0] / e[1])
         assert abs(eoc - table[k]) < 0.45, (k, eoc)
+    k, Ns = 3, (8, 16)
+    h0 = math.sqrt(2) * 2 * np.pi / Ns[0]
+    e = []
+    for N in Ns:
+        d, X = disc(N, k, nu=nu)
+        U = projected(d, X, tg)
+        h = math.sqrt(2) * 2 * np.pi / N
+        n = int(math.ceil(T / (0.1 * h0 / (2.0 * k * k) * (h / h0) ** (4.0 / 3.0))))
+        U = d.rk3_step(U, T / n, n)
+        e.append(d.l2_error(U, exact))
+    eoc = math.log2(e[0] / e[1])
+    assert abs(eoc - table[3]) < 0.45, (3, eoc)
+    # Example 2's enstrophy ||curl u||^2 of the same solution: 4 pi^2 exp(-4 nu t) for this field
+    # (curl u = 2 sin x sin y exp(-2 nu t)); exp(-2 nu t) would be off by 0.24
+    ens = d.diagnostics(U)["enstrophy"]
+    assert abs(ens - 4 * np.pi ** 2 * math.exp(-4 * nu * T)) < 0.02, ens
+
+
+def test_enstrophy_and_energy_exact_for_polynomial_fields():
+    # broken curl and L2 norm are exact for fields in the broken space: u = (a y + y^2, b x + x^2)
+    # on [0, 2pi]^2 has curl u = (b - a) + 2x - 2y, so ||curl u||^2 = (b-a)^2 (2pi)^2 + (2/3)(2pi)^4
+    # (the cross terms vanish: (b-a) * int (2x - 2y) = 0); ||u||^2 sums the two components' integrals
+    a, b = 0.7, -1.3
+    Lx = 2 * np.pi
+
+    def field(x, y):
+        return a * y + y * y, b * x + x * x
+    ens_ex = (b - a) ** 2 * Lx ** 2 + (2.0 / 3.0) * Lx ** 4
+    # int_0^L int_0^L (a y + y^2)^2 dx dy = L (a^2 L^3/3 + a L^4/2 + L^5/5), same for the other
+    one = Lx * (a * a * Lx ** 3 / 3 + a * Lx ** 4 / 2 + Lx ** 5 / 5)
+    two = Lx * (b * b * Lx ** 3 / 3 + b * Lx ** 4 / 2 + Lx ** 5 / 5)
+    for k in (2, 3):
+        d, X = disc(3, k)
+        U = d.from_lattice(synth.sample_lattice(field, X, k))
+        dg = d.diagnostics(U)
+        assert abs(dg["enstrophy"] - ens_ex) < 1e-10 * ens_ex, (k, dg["enstrophy"], ens_ex)
+        assert abs(dg["energy"] - (one + two)) < 1e-10 * (one + two), (k, dg["energy"])
+        assert dg["max_div"] < 1e-10                   # this field is divergence-free
+    # u = (x^2 / 2, 0) has div u = x: the largest divergence at the volume points is just below 2 pi
+    d, X = disc(3, 2)
+    U = d.from_lattice(synth.sample_lattice(lambda x, y: (0.5 * x * x, 0.0 * y), X, 2))
+    assert 0.9 * Lx < d.diagnostics(U)["max_div"] < Lx
+
+
+def test_taylor_green_enstrophy_converges_to_closed_form():
+    # projected Taylor-Green field: ||curl_h u_h||^2 -> 4 pi^2 at a rate of at least 3 (k = 2, 3)
+    for k in (2, 3):
+        err = []
+        for N in (8, 16):
+            d, X = disc(N, k)
+            err.append(abs(d.diagnostics(projected(d, X, synth.taylor_green()))["enstrophy"] - 4 * np.pi ** 2))
+        assert err[1] < err[0] / 8 and err[1] < 2e-2, (k, err)
 
 
 def test_advected_taylor_green_moves_downstream():
@@ -348,21 +401,27 @@ def test_advected_taylor_green_moves_downstream():
 
 
 def test_taylor_green_pressure():
-    # p = (cos 2x + cos 2y)/4 for u = (sin x cos y, -cos x sin y) (steady Euler); w ~ p (Remark 2)
-    errs = []
-    for N in (4, 8):
-        d, X = disc(N, 3, nu=0.0)
-        U = projected(d, X, synth.taylor_green())
-        w, lam = d.pressure(U)
-        errs.append(d.pressure_l2_error(w, lambda x, y: 0.25 * (np.cos(2 * x) + np.cos(2 * y))))
-        pe, pf = d.pressure_lattice(w, lam)
-    assert errs[1] < 0.3 * errs[0] and errs[1] < 0.05
-    # facet multiplier approximates the same pressure on the skeleton (Theorem 2)
-    T = d.topo
-    f = np.arange(d.n_facet)
-    pts = T.facet_points(f, np.zeros_like(f), np.arange(4) / 3.0)
-    ex = 0.25 * (np.cos(2 * pts[..., 0]) + np.cos(2 * pts[..., 1]))
-    assert np.abs(pf - ex).max() < 0.01
+    # p = (cos 2x + cos 2y)/4 for u = (sin x cos y, -cos x sin y) (steady Euler); w ~ p (Remark 2).
+    # The element pressure lives in broken P^(k-1): its L2 error has order k (measured 1.97 for
+    # k = 2 and 2.97 for k = 3 over N = 8 -> 16); the facet multiplier approximates the same
+    # pressure on the skeleton (Theorem 2) and its maximum error falls at least as fast.
+    pex = lambda x, y: 0.25 * (np.cos(2 * x) + np.cos(2 * y))  # noqa: E731
+    for k in (2, 3):
+        e_el, e_fa = [], []
+        for N in (8, 16):
+            d, X = disc(N, k, nu=0.0)
+            U = projected(d, X, synth.taylor_green())
+            w, lam = d.pressure(U)
+            e_el.append(d.pressure_l2_error(w, pex))
+            pe, pf = d.pressure_lattice(w, lam)
+            T = d.topo
+            f = np.arange(d.n_facet)
+            pts = T.facet_points(f, np.zeros_like(f), np.arange(k + 1) / k)
+            e_fa.append(np.abs(pf - pex(pts[..., 0], pts[..., 1])).max())
+        eoc_el = math.log2(e_el[0] / e_el[1])
+        eoc_fa = math.log2(e_fa[0] / e_fa[1])
+        assert abs(eoc_el - k) < 0.4, (k, eoc_el)
+        assert eoc_fa > k - 0.5 and e_fa[1] < 5e-3, (k, eoc_fa, e_fa)
 
 
 def test_rk3_is_third_order_in_time():
