@@ -78,7 +78,7 @@ typedef enum {
 } dg_status;
 
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
-enum { DG_PRECOND_AUTO = 0, DG_PRECOND_BLOCK_JACOBI = 1 };
+enum { DG_PRECOND_AUTO = 0, DG_PRECOND_BLOCK_JACOBI = 1, DG_PRECOND_MULTILEVEL = 2 };
 /* explicit time-stepping schemes of dg_step */
 enum { DG_SCHEME_SSPRK3 = 0, DG_SCHEME_EULER = 1, DG_SCHEME_RK4 = 2 };
 
@@ -93,7 +93,14 @@ typedef struct {
   int precond;        /* DG_PRECOND_AUTO: on a translation-invariant split-square mesh (a torus,
                          no walls), precondition with the exact Fourier-space inverse of the
                          block-circulant facet operator (FP32 in the mixed form, FP64 in the FP64
-                         form), else block Jacobi; DG_PRECOND_BLOCK_JACOBI: always block Jacobi */
+                         form), else with the multilevel preconditioner;
+                         DG_PRECOND_BLOCK_JACOBI: always block Jacobi (FP64 PCG, or FP32 PCG
+                         inside FP64 refinement in the mixed form);
+                         DG_PRECOND_MULTILEVEL: always the multilevel preconditioner: FP64 PCG
+                         with one V-cycle per iteration over p-levels of the facet space (k+1,
+                         2, 1 Legendre modes per facet) and smoothed aggregation on the
+                         facet-constant multipliers, Chebyshev(2) block-Jacobi smoothing, set up
+                         on the host at creation (dgdf_host.h, dg_host_multilevel) */
 } dg_params;
 
 /* Build a mesh: topology, reference tables and the per-element operators of
@@ -213,8 +220,8 @@ int dg_get_diagnostics(dg_mesh* mesh, double out[8]);
  * iterations summed over refinement sweeps in the mixed form), out[1] total
  * iterations, out[2] solves, out[3] final relative residual of the last solve,
  * out[4] refinement sweeps of the last solve, out[5] total sweeps, out[6] 1 if
- * the Fourier-space (lattice) preconditioner is in use, 0 for block Jacobi,
- * out[7] persistent-kernel blocks of the solver in use. */
+ * the Fourier-space (lattice) preconditioner is in use, 2 for the multilevel
+ * one, 0 for block Jacobi, out[7] persistent-kernel blocks of the solver in use. */
 int dg_get_solver_stats(dg_mesh* mesh, double out[8]);
 
 /* FP64 facet-system solve that allocates nothing, for callers that cannot call

@@ -59,6 +59,21 @@ int dg_host_facet_operator(int64_t n_tri, const int64_t* tri_vertex_ids, const d
 int dg_host_lattice(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k, double alpha,
                     int64_t* N, int32_t* facet_of, double* sinv, int64_t cap);
 
+/* The multilevel preconditioner of the facet system (DG_PRECOND_MULTILEVEL; no
+ * counterpart in the paper, which factorises the system directly, Sec. 4), built
+ * on the host as dg_mesh_create builds it. Inputs as dg_host_facet_operator.
+ * info[0] = smoothing levels L, info[1] = rows of the coarsest level, then for
+ * level l < L: info[2 + 2l] = rows, info[3 + 2l] = values per row (p-levels on the
+ * facets: k+1, 2, 1 modes; aggregation levels: 1). With nr > 0, z[i] = M r[i] for
+ * nr vectors of n_facet (k+1) values (one V-cycle each, FP64, in the coefficient
+ * layout of dg_host_facet_operator). With g and lam given, PCG with M from lam = 0
+ * on S lam = g (the constant multiplier left out) to relative residual rtol:
+ * lam receives the solution, *iters (may be NULL) the iterations.
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED. */
+int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k, double alpha,
+                       int64_t info[34], int nr, const double* r, double* z, const double* g, double* lam,
+                       double rtol, int64_t* iters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ EULER = 1
 RK4 = 2
 PRECOND_AUTO = 0
 PRECOND_BLOCK_JACOBI = 1
+PRECOND_MULTILEVEL = 2
 
 
 def _ptr(a):
@@ -166,8 +167,11 @@ class DGMesh:
         out = (ctypes.c_double * 8)()
         check(lib().dg_get_solver_stats(self._h, out), "dg_get_solver_stats")
         keys = ("last_iters", "total_iters", "solves", "last_relres", "last_sweeps", "total_sweeps",
-                "lattice", "blocks")
-        return dict(zip(keys, list(out)))
+                "precond_kind", "blocks")
+        d = dict(zip(keys, list(out)))
+        d["lattice"] = 1.0 if d["precond_kind"] == 1.0 else 0.0
+        d["preconditioner"] = {0.0: "block Jacobi", 1.0: "lattice FFT", 2.0: "multilevel"}[d["precond_kind"]]
+        return d
 
     def set_energy_watchdog(self, rel_tol):
         """Flag growth of ||u||^2 by more than rel_tol in a step (dg_set_energy_watchdog); 0 turns it off."""
@@ -293,6 +297,35 @@ def host_lattice(tri_vertex_ids, tri_coords, k, alpha=2.0):
     return n, fo, s[..., 0] + 1j * s[..., 1]
 
 
+def host_multilevel(tri_vertex_ids, tri_coords, k, alpha=2.0, r=None, g=None, rtol=1e-13):
+    """The multilevel preconditioner of the facet system built on the host (include/dgdf_host.h).
+
+    Returns a dict with the level sizes; with r ([nr, n_facet (k+1)]) also z = M r; with g also
+    the PCG solution lam and its iteration count.
+    """
+    L = lib()
+    vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tri_coords, dtype=np.float64)
+    V = ctypes.c_void_p
+    info = (ctypes.c_int64 * 34)()
+    nr, rp, zp, z = 0, None, None, None
+    if r is not None:
+        r = np.ascontiguousarray(np.atleast_2d(r), dtype=np.float64)
+        nr = r.shape[0]
+        z = np.empty_like(r)
+        rp, zp = r.ctypes.data_as(V), z.ctypes.data_as(V)
+    gp, lp, lam, it = None, None, None, ctypes.c_int64(0)
+    if g is not None:
+        g = np.ascontiguousarray(g, dtype=np.float64).ravel()
+        lam = np.empty_like(g)
+        gp, lp = g.ctypes.data_as(V), lam.ctypes.data_as(V)
+    check(L.dg_host_multilevel(vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), int(k), float(alpha), info,
+                               nr, rp, zp, gp, lp, float(rtol), ctypes.byref(it)), "dg_host_multilevel")
+    nlev = int(info[0])
+    return {"levels": [(int(info[2 + 2 * l]), int(info[3 + 2 * l])) for l in range(nlev)], "coarsest": int(info[1]),
+            "z": z, "lam": lam, "iters": int(it.value) if g is not None else None}
+
+
 def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13, maxit=20000, stream=None):
     """dg_facet_solve_noalloc on caller-owned CUDA tensors (torch); lam is updated in place.
 
@@ -329,5 +362,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "facet_solve_noalloc",
            "lib"]

@@ -17,7 +17,7 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity
            "dg_project_divfree", "dg_rk3_step", "dg_step", "dg_batch_create", "dg_batch_destroy", "dg_batch_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_set_coefficients", "dg_get_coefficients",
            "dg_set_viscosity", "dg_rk3_vjp", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
            "dg_set_energy_watchdog", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
-           "dg_host_facet_operator", "dg_host_lattice"]
+           "dg_host_facet_operator", "dg_host_lattice", "dg_host_multilevel"]
 
 
 class DGParams(ctypes.Structure):
@@ -67,6 +67,7 @@ def lib():
         "dg_host_reference": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, I64, P]),
         "dg_host_facet_operator": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, P, P, P, P, P, I64]),
         "dg_host_lattice": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, P, P, I64]),
+        "dg_host_multilevel": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, ctypes.c_int, P, P, P, P, D, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -13,6 +13,7 @@
 #include "../../include/dgdf.h"
 #include "device.cuh"
 #include "kcommon.cuh"
+#include "multilevel.hpp"
 #include "setup.hpp"
 
 static_assert(dgdf::Dims<1>::NQ == dgdf::kVolumePoints(1) && dgdf::Dims<2>::NQ == dgdf::kVolumePoints(2) &&
@@ -42,13 +43,14 @@ enum KernelClass {
   KC_ADJOINT,
   KC_COMBINE,
   KC_WATCH,
+  KC_SOLVE_ML,
   KC_COUNT
 };
 const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
                                       "facet_pcg_mixed",     "recover",              "project_rhs",
                                       "lattice",             "diagnostics",          "pressure",
                                       "facet_pcg_fft_fp64",  "facet_pcg_fft_fp32",   "adjoint",
-                                      "combine",             "energy_watchdog"};
+                                      "combine",             "energy_watchdog",      "facet_pcg_multilevel"};
 
 }  // namespace
 
@@ -61,6 +63,8 @@ struct dg_mesh {
   int solver_blocks[2] = {1, 1};
   bool use_lattice = false;
   int lattice_blocks = 0;
+  bool use_ml = false;            // multilevel-preconditioned PCG (k_multilevel.cu)
+  int ml_blocks = 0;
   std::string lattice_why;
   double last_c = 0.0;            // coefficient of L(u') in the last stage solved
   long long gen = 0;              // bumped by every setter that changes a kernel argument
@@ -276,6 +280,10 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
     return launch(M, a.mixed ? KC_SOLVE_LAT32 : KC_SOLVE_LAT64,
                   [&] { return dgdf::launch_solve_lattice(M->dm, a, nb, a.mixed, M->stream); });
   }
+  if (M->use_ml) {
+    const int nb = M->ml_blocks;
+    return launch(M, KC_SOLVE_ML, [&] { return dgdf::launch_solve_ml(M->dm, a, nb, M->stream); });
+  }
   const int nb = M->solver_blocks[a.mixed];
   return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
 }
@@ -318,8 +326,9 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     return fail(DG_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (mixed)");
   if (!(p.cg_rtol > 0.0)) p.cg_rtol = 1e-13;
   if (p.cg_maxit <= 0) p.cg_maxit = 20000;
-  if (p.precond != DG_PRECOND_AUTO && p.precond != DG_PRECOND_BLOCK_JACOBI)
-    return fail(DG_ERR_INVALID_ARG, "precond must be DG_PRECOND_AUTO or DG_PRECOND_BLOCK_JACOBI");
+  if (p.precond != DG_PRECOND_AUTO && p.precond != DG_PRECOND_BLOCK_JACOBI && p.precond != DG_PRECOND_MULTILEVEL)
+    return fail(DG_ERR_INVALID_ARG,
+                "precond must be DG_PRECOND_AUTO, DG_PRECOND_BLOCK_JACOBI or DG_PRECOND_MULTILEVEL");
   dg_mesh* M = new dg_mesh();
   M->p = p;
   M->stream = static_cast<cudaStream_t>(p.cuda_stream);
@@ -510,6 +519,52 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   if (e != cudaSuccess) return cleanup(fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
   M->solver_blocks[0] = dgdf::solver_max_blocks(d, 0);
   M->solver_blocks[1] = dgdf::solver_max_blocks(d, 1);
+  // multilevel preconditioner: asked for, or the default where the lattice path is not taken
+  if (p.precond == DG_PRECOND_MULTILEVEL || (p.precond == DG_PRECOND_AUTO && !(lat.ok && lat_blocks > 0))) {
+    dgdf::MLHost mlh;
+    std::string merr;
+    if ((rc = dgdf::build_multilevel(M->hm, mlh, merr))) return cleanup(fail(rc, merr));
+    std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
+    for (size_t l = 0; l < mlh.lv.size(); ++l) {
+      const dgdf::MLHostLevel& H = mlh.lv[l];
+      dgdf::MLLevelDev& L = lv[l];
+      L.stencil = H.stencil ? 1 : 0;
+      L.bs = H.bs;
+      L.n = H.n;
+      L.inject = H.inject ? 1 : 0;
+      L.n_next = H.n_next;
+      L.bs_next = H.bs_next;
+      L.c0 = H.cheb[0];
+      L.c1 = H.cheb[1];
+      L.c2 = H.cheb[2];
+      if ((rc = upload(M, &L.binv, H.binv))) return cleanup(rc);
+      if (!H.stencil && ((rc = upload(M, &L.a_rp, H.A.rp)) || (rc = upload(M, &L.a_ci, H.A.ci)) ||
+                         (rc = upload(M, &L.a_v, H.A.v))))
+        return cleanup(rc);
+      if (!H.inject && ((rc = upload(M, &L.p_rp, H.P.rp)) || (rc = upload(M, &L.p_ci, H.P.ci)) ||
+                        (rc = upload(M, &L.p_v, H.P.v)) || (rc = upload(M, &L.r_rp, H.R.rp)) ||
+                        (rc = upload(M, &L.r_ci, H.R.ci)) || (rc = upload(M, &L.r_v, H.R.v))))
+        return cleanup(rc);
+      const size_t nv = size_t(H.n) * H.bs;
+      if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
+        L.b = d.r;
+        L.x = d.z;
+      } else if ((rc = dalloc(M, &L.b, nv)) || (rc = dalloc(M, &L.x, nv))) {
+        return cleanup(rc);
+      }
+      if ((rc = dalloc(M, &L.r, nv)) || (rc = dalloc(M, &L.d, nv))) return cleanup(rc);
+    }
+    const dgdf::MLLevelDev* lvd = nullptr;
+    if ((rc = upload(M, &lvd, lv)) || (rc = upload(M, &d.ml_cpinv, mlh.cpinv)) ||
+        (rc = dalloc(M, &d.ml_xc, size_t(mlh.nc))) || (rc = dalloc(M, &d.ml_bc, size_t(mlh.nc))))
+      return cleanup(rc);
+    d.ml_lv = lvd;
+    d.ml_nlev = int(lv.size());
+    d.ml_nc = mlh.nc;
+    M->use_ml = d.ml_nlev >= 1;
+    M->ml_blocks = dgdf::solver_ml_blocks(d);
+    if (M->use_ml && M->ml_blocks < 1) return cleanup(fail(DG_ERR_CUDA, "multilevel solver does not fit"));
+  }
   if (lat.ok && lat_blocks > 0) {
     const int fp32 = lat_fp32;
     const int C = lat.C, N = lat.N;
@@ -1280,8 +1335,9 @@ int dg_get_solver_stats(dg_mesh* M, double out[8]) {
   out[3] = s.last_relres;
   out[4] = s.last_sweeps;
   out[5] = double(s.total_sweeps);
-  out[6] = M->use_lattice ? 1.0 : 0.0;
-  out[7] = M->use_lattice ? M->lattice_blocks : M->solver_blocks[M->p.precision == DG_PRECISION_MIXED];
+  out[6] = M->use_lattice ? 1.0 : (M->use_ml ? 2.0 : 0.0);
+  out[7] = M->use_lattice ? M->lattice_blocks
+                          : (M->use_ml ? M->ml_blocks : M->solver_blocks[M->p.precision == DG_PRECISION_MIXED]);
   return DG_OK;
 }
 

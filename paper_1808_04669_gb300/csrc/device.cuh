@@ -42,6 +42,23 @@ struct GridBar {
   unsigned int gen;
 };
 
+// One smoothing level of the multilevel preconditioner (multilevel.hpp), in device memory.
+struct MLLevelDev {
+  int stencil;        // 1: the facet stencil of S on the first bs modes; 0: the CSR matrix a_*
+  int bs, n;          // values per row, rows
+  int inject;         // 1: transfer to the next level keeps the leading bs_next modes (same facet rows)
+  int n_next, bs_next;
+  const double* binv; // stencil: [n_stencil][bs][bs]; CSR: [n] 1 / a_ii
+  const int32_t *a_rp, *a_ci;
+  const double* a_v;
+  const int32_t *p_rp, *p_ci;   // prolongation [n x n_next] (CSR transfer)
+  const double* p_v;
+  const int32_t *r_rp, *r_ci;   // restriction [n_next x n]
+  const double* r_v;
+  double c0, c1, c2;  // Chebyshev(2) coefficients
+  double *x, *b, *r, *d;   // work vectors [n * bs]
+};
+
 struct DevMesh {
   int k, ns, nd, nw, nl, nq, nqf;
   int n_tri, n_facet, n_class, n_stencil;
@@ -100,6 +117,11 @@ struct DevMesh {
   void* lat_x2;                       // the same size: inverse halves of the split column pass
   int lat_split;                      // column pass split into even / odd wavenumbers
   int lat_tw2_off;                    // complex elements before the N/2 twiddles in shared memory
+  // multilevel preconditioner (NULL ml_lv: none)
+  const MLLevelDev* ml_lv;            // [ml_nlev] in device memory
+  int ml_nlev, ml_nc;                 // smoothing levels, rows of the coarsest level
+  const double* ml_cpinv;             // [ml_nc][ml_nc] pseudo-inverse of the coarsest operator
+  double *ml_xc, *ml_bc;              // coarsest vectors
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
@@ -171,6 +193,9 @@ cudaError_t launch_check_finite(const double* v, long long n, int* flag, cudaStr
 cudaError_t launch_energy_watch(const double* u, long long n, double* watch, double tol, DevStats* st,
                                 cudaStream_t s);
 cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
+// FP64 PCG with the multilevel preconditioner (k_multilevel.cu)
+cudaError_t launch_solve_ml(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
+int solver_ml_blocks(const DevMesh& m);
 int solver_max_blocks(const DevMesh& m, int mixed);
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp);
 bool lattice_split(int N);

@@ -1,10 +1,13 @@
 // Host-only introspection entry points (include/dgdf_host.h): the set-up of
 // setup.cpp without any device, for checks on machines without a GPU.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 
 #include "../../include/dgdf.h"
 #include "../../include/dgdf_host.h"
+#include "multilevel.hpp"
 #include "setup.hpp"
 
 extern "C" {
@@ -90,6 +93,81 @@ int dg_host_lattice(int64_t n_tri, const int64_t* tri_vertex_ids, const double* 
   if (sinv) {
     if (cap < int64_t(lat.sinv.size())) return DG_ERR_INVALID_ARG;
     std::memcpy(sinv, lat.sinv.data(), lat.sinv.size() * sizeof(double));
+  }
+  return DG_OK;
+}
+
+int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, int k, double alpha,
+                       int64_t info[34], int nr, const double* r, double* z, const double* g, double* lam, double rtol,
+                       int64_t* iters) {
+  if (!info || !(alpha > 0.0) || nr < 0 || (nr > 0 && (!r || !z))) return DG_ERR_INVALID_ARG;
+  dgdf::HostMesh hm;
+  std::string err;
+  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, k, alpha, hm, err);
+  if (rc) return rc;
+  dgdf::MLHost ml;
+  if ((rc = dgdf::build_multilevel(hm, ml, err))) return rc;
+  for (int i = 0; i < 34; ++i) info[i] = 0;
+  info[0] = int64_t(ml.lv.size());
+  info[1] = ml.nc;
+  for (size_t l = 0; l < ml.lv.size() && l < 16; ++l) {
+    info[2 + 2 * l] = ml.lv[l].n;
+    info[3 + 2 * l] = ml.lv[l].bs;
+  }
+  const size_t n = size_t(hm.topo.n_facet) * hm.nl;
+  for (int i = 0; i < nr; ++i) dgdf::multilevel_apply_host(hm, ml, r + i * n, z + i * n);
+  if (g && lam) {
+    // PCG from zero, the constant multiplier left out of g and of the residual norm
+    const int nl = hm.nl;
+    const size_t nf = size_t(hm.topo.n_facet);
+    std::vector<double> b(g, g + n), rr(n), zz(n), p(n), q(n);
+    double c0 = 0.0;
+    for (size_t f = 0; f < nf; ++f) c0 += b[f * nl];
+    c0 /= double(nf);
+    for (size_t f = 0; f < nf; ++f) b[f * nl] -= c0;
+    auto norm_r = [&](const std::vector<double>& v) {
+      double s = 0.0, m = 0.0;
+      for (size_t i = 0; i < n; ++i) s += v[i] * v[i];
+      for (size_t f = 0; f < nf; ++f) m += v[f * nl];
+      return std::sqrt(std::max(s - m * m / double(nf), 0.0));
+    };
+    auto applyS = [&](const double* x, double* y) {
+      for (size_t f = 0; f < nf; ++f) {
+        const double* blk = &hm.stencil_blocks[size_t(hm.facet_stencil[f]) * 5 * nl * nl];
+        size_t nb[5] = {f, size_t(hm.facet_nbr[f * 4]), size_t(hm.facet_nbr[f * 4 + 1]), size_t(hm.facet_nbr[f * 4 + 2]),
+                        size_t(hm.facet_nbr[f * 4 + 3])};
+        for (int i = 0; i < nl; ++i) {
+          double v = 0.0;
+          for (int bb = 0; bb < 5; ++bb)
+            for (int j = 0; j < nl; ++j) v += blk[(size_t(bb) * nl + i) * nl + j] * x[nb[bb] * nl + j];
+          y[f * nl + i] = v;
+        }
+      }
+    };
+    for (size_t i = 0; i < n; ++i) lam[i] = 0.0;
+    rr = b;
+    const double stop = rtol * norm_r(b);
+    dgdf::multilevel_apply_host(hm, ml, rr.data(), zz.data());
+    p = zz;
+    double rz = 0.0;
+    for (size_t i = 0; i < n; ++i) rz += rr[i] * zz[i];
+    int64_t it = 0;
+    for (; it < 10000 && norm_r(rr) > stop; ++it) {
+      applyS(p.data(), q.data());
+      double pq = 0.0;
+      for (size_t i = 0; i < n; ++i) pq += p[i] * q[i];
+      const double a = rz / pq;
+      for (size_t i = 0; i < n; ++i) {
+        lam[i] += a * p[i];
+        rr[i] -= a * q[i];
+      }
+      dgdf::multilevel_apply_host(hm, ml, rr.data(), zz.data());
+      double rz2 = 0.0;
+      for (size_t i = 0; i < n; ++i) rz2 += rr[i] * zz[i];
+      for (size_t i = 0; i < n; ++i) p[i] = zz[i] + rz2 / rz * p[i];
+      rz = rz2;
+    }
+    if (iters) *iters = it;
   }
   return DG_OK;
 }

@@ -1,0 +1,403 @@
+// Facet-system solve with the multilevel preconditioner (multilevel.hpp): FP64
+// PCG on S lam = g (the condensed system of eq. (12), Sec. 2.4), preconditioned
+// by one V-cycle per iteration, in one persistent cooperative kernel.
+//
+// Every phase is a grid-stride loop over the rows of one level followed by a
+// bounded grid barrier (solver_common.cuh). A V-cycle with L smoothing levels:
+//   down, level l: [A] x = d + c1 d + c2 B (b - A d)  (d = c0 B b, set by the
+//                  previous phase: the second Chebyshev step from x = 0)
+//                  [B] r = b - A x; an injected transfer writes the next level's b
+//                  (and its first Chebyshev step) in the same phase
+//                  [C] a CSR transfer: b_next = R r (and its first step)
+//   coarsest:      x_c = pinv b_c (added into the last level's mode 0 if it injects)
+//   up, level l:   [U] a CSR transfer: x += P x_next
+//                  [Q] r = b - A x, d = c0 B r
+//                  [R] x += d + c1 d + c2 B (r - A d); an injected transfer adds x
+//                  into the finer level's leading modes in the same phase
+// so a level costs four or five barriers and the V-cycle is symmetric (the same
+// Chebyshev polynomial before and after). The level records live in shared memory.
+#include "device.cuh"
+#include "kcommon.cuh"
+#include "multilevel.hpp"
+#include "solver_common.cuh"
+
+namespace dgdf {
+
+namespace {
+
+constexpr int kMLThreads = 256;
+
+// y = (A x)_i for row i of level L (bs <= NL values; y[0] only on CSR levels)
+template <int NL>
+__device__ __forceinline__ void ml_row_apply(const DevMesh& m, const MLLevelDev& L, int i, const double* x,
+                                             double (&y)[NL]) {
+  if (L.stencil) {
+    const int bs = L.bs;
+    const double* blk = m.st_blk + size_t(__ldg(&m.facet_stencil[i])) * 5 * NL * NL;
+    int nb[5];
+    nb[0] = i;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) nb[b + 1] = __ldg(&m.facet_nbr[size_t(i) * 4 + b]);
+#pragma unroll
+    for (int ii = 0; ii < NL; ++ii) {
+      double v = 0.0;
+      if (ii < bs) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+#pragma unroll
+          for (int jj = 0; jj < NL; ++jj)
+            if (jj < bs) v += __ldg(&blk[(b * NL + ii) * NL + jj]) * __ldcg(&x[size_t(nb[b]) * bs + jj]);
+      }
+      y[ii] = v;
+    }
+  } else {
+    double v = 0.0;
+    const int p1 = __ldg(&L.a_rp[i + 1]);
+    for (int p = __ldg(&L.a_rp[i]); p < p1; ++p) v += __ldg(&L.a_v[p]) * __ldcg(&x[__ldg(&L.a_ci[p])]);
+    y[0] = v;
+  }
+}
+
+// out = B v for row i of level L
+template <int NL>
+__device__ __forceinline__ void ml_row_binv(const DevMesh& m, const MLLevelDev& L, int i, const double (&v)[NL],
+                                            double (&out)[NL]) {
+  if (L.stencil) {
+    const int bs = L.bs;
+    const double* B = L.binv + size_t(__ldg(&m.facet_stencil[i])) * bs * bs;
+#pragma unroll
+    for (int ii = 0; ii < NL; ++ii) {
+      double s = 0.0;
+      if (ii < bs) {
+#pragma unroll
+        for (int jj = 0; jj < NL; ++jj)
+          if (jj < bs) s += __ldg(&B[ii * bs + jj]) * v[jj];
+      }
+      out[ii] = s;
+    }
+  } else {
+    out[0] = __ldg(&L.binv[i]) * v[0];
+#pragma unroll
+    for (int ii = 1; ii < NL; ++ii) out[ii] = 0.0;
+  }
+}
+
+// First Chebyshev step from zero on row i of level L: d = c0 B b, x = d.
+template <int NL>
+__device__ __forceinline__ void ml_row_first_step(const DevMesh& m, const MLLevelDev& L, int i) {
+  const int bs = L.bs;
+  double bv[NL], t[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) bv[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) : 0.0;
+  ml_row_binv<NL>(m, L, i, bv, t);
+#pragma unroll
+  for (int j = 0; j < NL; ++j)
+    if (j < bs) {
+      const double d = L.c0 * t[j];
+      L.d[size_t(i) * bs + j] = d;
+      L.x[size_t(i) * bs + j] = d;
+    }
+}
+
+// One V-cycle: on entry lv[0].b holds the input and lv[0].d = lv[0].x = c0 B b (set by the
+// caller before a barrier); on return every thread has written its rows of lv[0].x (the
+// output z) and accumulated, over its level-0 rows, b.z, b.b and the sum of b's mode 0 into
+// red[0..2]. The caller's reduction is the closing barrier.
+template <int NL>
+__device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[3]) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  const int nlev = m.ml_nlev;
+  GridBar* bar = m.bar;
+  for (int l = 0; l < nlev; ++l) {
+    const MLLevelDev& L = lv[l];
+    const int bs = L.bs;
+    // [A] second Chebyshev step from zero
+    for (int i = gtid; i < L.n; i += gsz) {
+      double y[NL], res[NL], t[NL];
+      ml_row_apply<NL>(m, L, i, L.d, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
+      ml_row_binv<NL>(m, L, i, res, t);
+#pragma unroll
+      for (int j = 0; j < NL; ++j)
+        if (j < bs) {
+          const double d = __ldcg(&L.d[size_t(i) * bs + j]);
+          L.x[size_t(i) * bs + j] = d + L.c1 * d + L.c2 * t[j];
+        }
+    }
+    if (!grid_sync(bar, m.stats)) return false;
+    // [B] residual, injected restriction
+    const bool last = l + 1 == nlev;
+    for (int i = gtid; i < L.n; i += gsz) {
+      double y[NL];
+      ml_row_apply<NL>(m, L, i, L.x, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j)
+        if (j < bs) {
+          const double r = __ldcg(&L.b[size_t(i) * bs + j]) - y[j];
+          L.r[size_t(i) * bs + j] = r;
+          if (L.inject && j < L.bs_next) {
+            if (last) m.ml_bc[i] = r;   // bs_next = 1 into the coarsest level
+            else lv[l + 1].b[size_t(i) * L.bs_next + j] = r;
+          }
+        }
+      if (L.inject && !last) ml_row_first_step<NL>(m, lv[l + 1], i);
+    }
+    if (!grid_sync(bar, m.stats)) return false;
+    if (!L.inject) {
+      // [C] CSR restriction b_next = R r
+      for (int j = gtid; j < L.n_next; j += gsz) {
+        double v = 0.0;
+        const int p1 = __ldg(&L.r_rp[j + 1]);
+        for (int p = __ldg(&L.r_rp[j]); p < p1; ++p) v += __ldg(&L.r_v[p]) * __ldcg(&L.r[__ldg(&L.r_ci[p])]);
+        if (last) {
+          m.ml_bc[j] = v;
+        } else {
+          lv[l + 1].b[j] = v;
+          ml_row_first_step<NL>(m, lv[l + 1], j);
+        }
+      }
+      if (!grid_sync(bar, m.stats)) return false;
+    }
+  }
+  // coarsest level: x_c = pinv b_c
+  {
+    const int nc = m.ml_nc;
+    const MLLevelDev& Lz = lv[nlev - 1];
+    for (int i = gtid; i < nc; i += gsz) {
+      double v = 0.0;
+      const double* row = m.ml_cpinv + size_t(i) * nc;
+      for (int j = 0; j < nc; ++j) v += __ldg(&row[j]) * __ldcg(&m.ml_bc[j]);
+      m.ml_xc[i] = v;
+      if (Lz.inject) Lz.x[size_t(i) * Lz.bs] += v;
+    }
+    if (!grid_sync(bar, m.stats)) return false;
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    const MLLevelDev& L = lv[l];
+    const int bs = L.bs;
+    if (!L.inject) {
+      // [U] CSR prolongation x += P x_next
+      const double* xn = (l + 1 == nlev) ? m.ml_xc : lv[l + 1].x;
+      for (int i = gtid; i < L.n; i += gsz) {
+        double v = 0.0;
+        const int p1 = __ldg(&L.p_rp[i + 1]);
+        for (int p = __ldg(&L.p_rp[i]); p < p1; ++p) v += __ldg(&L.p_v[p]) * __ldcg(&xn[__ldg(&L.p_ci[p])]);
+        L.x[i] += v;
+      }
+      if (!grid_sync(bar, m.stats)) return false;
+    }
+    // [Q] r = b - A x, d = c0 B r
+    for (int i = gtid; i < L.n; i += gsz) {
+      double y[NL], res[NL], t[NL];
+      ml_row_apply<NL>(m, L, i, L.x, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
+      ml_row_binv<NL>(m, L, i, res, t);
+#pragma unroll
+      for (int j = 0; j < NL; ++j)
+        if (j < bs) {
+          L.r[size_t(i) * bs + j] = res[j];
+          L.d[size_t(i) * bs + j] = L.c0 * t[j];
+        }
+    }
+    if (!grid_sync(bar, m.stats)) return false;
+    // [R] x += d + c1 d + c2 B (r - A d); inject into the finer level (same facet rows)
+    const MLLevelDev* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
+    for (int i = gtid; i < L.n; i += gsz) {
+      double y[NL], res[NL], t[NL];
+      ml_row_apply<NL>(m, L, i, L.d, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.r[size_t(i) * bs + j]) - y[j] : 0.0;
+      ml_row_binv<NL>(m, L, i, res, t);
+#pragma unroll
+      for (int j = 0; j < NL; ++j)
+        if (j < bs) {
+          const double d = __ldcg(&L.d[size_t(i) * bs + j]);
+          const double x = __ldcg(&L.x[size_t(i) * bs + j]) + d + L.c1 * d + L.c2 * t[j];
+          L.x[size_t(i) * bs + j] = x;
+          if (F) F->x[size_t(i) * F->bs + j] += x;
+          if (l == 0) {
+            const double b = __ldcg(&L.b[size_t(i) * bs + j]);
+            red[0] += b * x;
+            red[1] += b * b;
+            if (j == 0) red[2] += b;
+          }
+        }
+    }
+    if (l > 0 && !grid_sync(bar, m.stats)) return false;
+  }
+  return true;
+}
+
+// One solve: g assembled from the element sides, lam0 = warm_scale * lam, constant multiplier
+// removed from g, then PCG with the V-cycle. Level 0's b and x are the PCG vectors r and z.
+template <int K>
+__global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a) {
+  constexpr int NL = K + 1;
+  __shared__ MLLevelDev lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = m.ml_lv[l];
+  __syncthreads();
+  const int nF = m.n_facet;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  GridBar* bar = m.bar;
+  double gg[2] = {0.0, 0.0};
+  for (int f = gtid; f < nF; f += gsz) {
+    double gv[NL];
+    assemble_g<NL>(m, f, gv);
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const size_t o = size_t(f) * NL + j;
+      m.g[o] = gv[j];
+      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
+      gg[0] += gv[j] * gv[j];
+    }
+    gg[1] += gv[0];
+  }
+  if (!grid_reduce<2>(m, 4, gg, bar)) return;
+  const double c0 = gg[1] / double(nF);
+  const double inv_nf = 1.0 / double(nF);
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] * inv_nf, 0.0));
+  const double stop = a.rtol * gnorm;
+  int it = 0;
+  bool conv = false;
+  double rr = 0.0;
+  if (gnorm == 0.0) {
+    for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
+    conv = true;
+  } else {
+    for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
+    if (!grid_sync(bar, m.stats)) return;
+    // r = g - S lam; first Chebyshev step of the V-cycle on r
+    for (int f = gtid; f < nF; f += gsz) {
+      double y[NL];
+      spmv64<NL>(m, f, m.lam, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m.r[size_t(f) * NL + j] = m.g[size_t(f) * NL + j] - y[j];
+      ml_row_first_step<NL>(m, lv[0], f);
+    }
+    if (!grid_sync(bar, m.stats)) return;
+    double red[3] = {0.0, 0.0, 0.0};
+    if (!ml_vcycle<NL>(m, lv, red)) return;
+    if (!grid_reduce<3>(m, 1, red, bar)) return;
+    double rho = red[0];
+    rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
+    double beta = 0.0;
+    double* pold = m.pa;
+    double* pnew = m.pb;
+    for (;; ++it) {
+      if (!isfinite(rr) || !isfinite(rho)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      if (sqrt(rr) <= stop) {
+        conv = true;
+        break;
+      }
+      if (it >= a.maxit) break;
+      // p_new = z + beta p_old, q = S p_new
+      double pq[1] = {0.0};
+      for (int f = gtid; f < nF; f += gsz) {
+        int nb[5];
+        facet_nbrs<NL>(m, f, nb);
+        double xs[5][NL];
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+#pragma unroll
+          for (int j = 0; j < NL; ++j) {
+            const size_t o = size_t(nb[b]) * NL + j;
+            xs[b][j] = (it == 0) ? __ldcg(&m.z[o]) : __ldcg(&m.z[o]) + beta * __ldcg(&pold[o]);
+          }
+        double y[NL];
+        stencil_rows<NL, double>(m.st_blk + size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL, xs, y);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          pnew[size_t(f) * NL + j] = xs[0][j];
+          m.q[size_t(f) * NL + j] = y[j];
+          pq[0] += xs[0][j] * y[j];
+        }
+      }
+      if (!grid_reduce<1>(m, 0, pq, bar)) return;
+      if (!(pq[0] > 0.0)) {
+        if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        break;
+      }
+      const double alpha = rho / pq[0];
+      // lam += alpha p, r -= alpha q, first Chebyshev step on the new r
+      for (int f = gtid; f < nF; f += gsz) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(f) * NL + j;
+          m.lam[o] += alpha * pnew[o];
+          m.r[o] -= alpha * m.q[o];
+        }
+        ml_row_first_step<NL>(m, lv[0], f);
+      }
+      if (!grid_sync(bar, m.stats)) return;
+      double red2[3] = {0.0, 0.0, 0.0};
+      if (!ml_vcycle<NL>(m, lv, red2)) return;
+      if (!grid_reduce<3>(m, 1, red2, bar)) return;
+      beta = red2[0] / rho;
+      rho = red2[0];
+      rr = fmax(red2[1] - red2[2] * red2[2] * inv_nf, 0.0);
+      double* t = pold;
+      pold = pnew;
+      pnew = t;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats* st = m.stats;
+    st->last_iters = it;
+    st->total_iters += it;
+    st->solves += 1;
+    st->last_relres = gnorm > 0.0 ? sqrt(rr) / gnorm : 0.0;
+    st->last_sweeps = 1;
+    st->total_sweeps += 1;
+    if (!conv) atomicOr(&st->flags, kFlagNotConverged);
+  }
+}
+
+const void* ml_kernel(int k) {
+  switch (k) {
+    case 1: return (const void*)k_solve_ml<1>;
+    case 2: return (const void*)k_solve_ml<2>;
+    case 3: return (const void*)k_solve_ml<3>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int solver_ml_blocks(const DevMesh& m) {
+  const void* fn = ml_kernel(m.k);
+  if (!fn) return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMLThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = per_sm * sms;
+  if (nb > 2 * sms) nb = 2 * sms;   // fewer blocks make the many grid barriers cheaper
+  const int need = (m.n_facet + kMLThreads - 1) / kMLThreads;
+  if (nb > need) nb = need;
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_solve_ml(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s) {
+  if (!m.ml_lv || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  const void* fn = ml_kernel(m.k);
+  if (!fn) return cudaErrorInvalidValue;
+  DevMesh mm = m;
+  SolveArgs aa = a;
+  void* args[] = {&mm, &aa};
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kMLThreads), args, 0, s);
+}
+
+}  // namespace dgdf

@@ -1151,3 +1151,9 @@ void renumber_facets_lattice(HostMesh& hm, Lattice& L) {
 }
 
 }  // namespace dgdf
+
+namespace dgdf {
+void symmetric_eigen(const std::vector<double>& A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
+  sym_eig(A, n, evals, evecs);
+}
+}  // namespace dgdf

@@ -104,6 +104,9 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
 // Detects the split-square lattice structure and computes the inverse Fourier symbol.
 // eig_half: the eigen form of the half spectrum (seig) instead of the full inverse (sinv).
 void build_lattice(const HostMesh& hm, const double* X, Lattice& lat, bool eig_half = false);
+// Eigen-decomposition of a small dense symmetric matrix (row-major [n][n]) by cyclic Jacobi
+// rotations: evals[i] and column i of evecs ([n][n], row-major).
+void symmetric_eigen(const std::vector<double>& A, int n, std::vector<double>& evals, std::vector<double>& evecs);
 // Renumbers the facets of a lattice mesh internally in (type, j, i) order, so that the
 // facet-major vectors are the Fourier passes' row order; records the external ids.
 void renumber_facets_lattice(HostMesh& hm, Lattice& lat);

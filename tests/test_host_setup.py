@@ -235,3 +235,57 @@ def test_lattice_detection_rejects_other_meshes(g):
     rng = np.random.default_rng(0)
     Xp = X + (0.1 * rng.uniform(-1, 1, size=(16, 2)))[vid]
     assert g.host_lattice(vid, Xp, 2) is None            # not translation invariant
+
+
+# ------------------------------------------------------ multilevel preconditioner (host set-up)
+def _ml_mesh(N, k, walls, perturb=0.0):
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=not walls)
+    if perturb:
+        rng = np.random.default_rng(3)
+        X = X + (perturb / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
+    return vid, X
+
+
+def _apply_S(nbr, st, blk, x):
+    nl = blk.shape[-1]
+    x = x.reshape(-1, nl)
+    y = np.einsum("fij,fj->fi", blk[st, 0], x)
+    for b in range(4):
+        y += np.einsum("fij,fj->fi", blk[st, b + 1], x[nbr[:, b]])
+    return y.ravel()
+
+
+@pytest.mark.parametrize("N,k,walls,perturb", [(32, 1, True, 0.0), (32, 2, True, 0.0), (32, 3, True, 0.0),
+                                               (32, 3, False, 0.15), (8, 2, True, 0.0)])
+def test_multilevel_pcg_solves_the_facet_system_in_few_iterations(g, N, k, walls, perturb):
+    # block Jacobi needs O(N) iterations (hundreds here); one V-cycle per iteration keeps it at ~35
+    vid, X = _ml_mesh(N, k, walls, perturb)
+    nbr, st, blk, binv = g.host_facet_operator(vid, X, k)
+    nl = k + 1
+    rhs = np.random.default_rng(N + k).standard_normal(nbr.shape[0] * nl)
+    res = g.host_multilevel(vid, X, k, g=rhs, rtol=1e-12)
+    sizes = [n for n, _ in res["levels"]]
+    assert res["levels"][0] == (nbr.shape[0], nl)
+    assert all(a >= b for a, b in zip(sizes, sizes[1:])) and res["coarsest"] <= 256
+    assert 0 < res["iters"] <= 45, res["iters"]
+    # the solution: S lam = g up to the constant multiplier (mode 0 on every facet)
+    b = rhs.reshape(-1, nl).copy()
+    b[:, 0] -= b[:, 0].mean()
+    r = b.ravel() - _apply_S(nbr, st, blk, res["lam"])
+    r = r.reshape(-1, nl)
+    r[:, 0] -= r[:, 0].mean()
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_multilevel_v_cycle_is_symmetric_positive_on_the_range(g):
+    # PCG needs a symmetric positive definite preconditioner (on the complement of the constant
+    # multiplier): the same Chebyshev polynomial before and after the coarse correction
+    vid, X = _ml_mesh(16, 2, True)
+    nf = g.host_facet_operator(vid, X, 2)[0].shape[0]
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal((4, nf * 3))
+    r.reshape(4, nf, 3)[:, :, 0] -= r.reshape(4, nf, 3)[:, :, 0].mean(1, keepdims=True)
+    z = g.host_multilevel(vid, X, 2, r=r)["z"]
+    G = r @ z.T
+    assert np.abs(G - G.T).max() <= 1e-12 * np.abs(G).max()
+    assert np.linalg.eigvalsh(0.5 * (G + G.T)).min() > 0
