@@ -267,6 +267,22 @@ int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, con
  * allocates 16 KB of device memory. */
 int dg_set_energy_watchdog(dg_mesh* mesh, double rel_tol);
 
+/* Convergence history of the multilevel facet solver (no counterpart in the paper).
+ * enable = 1 starts recording (allocates 16 KB of device memory once), 0 stops;
+ * any other value only reads. out (cap doubles, may be NULL) receives, for every
+ * PCG iteration i < 512 of the last solve, 4 values: the relative residual before
+ * the iteration, r.z, p.S p and the step length alpha (-1 where p.S p <= 0 ended
+ * the solve); *n_out (may be NULL) the iterations of the last solve.
+ * Errors: DG_ERR_UNSUPPORTED (the mesh uses another preconditioner). */
+int dg_solver_history(dg_mesh* mesh, int enable, double* out, int cap, int* n_out);
+
+/* Test hook of the multilevel preconditioner (no counterpart in the paper): z = M r
+ * for one V-cycle on the device, r and z [n_facet][k+1] in the coefficient layout of
+ * dg_host_facet_operator (host memory for on_device = 0, which allocates two device
+ * vectors for the mesh). Compares with dg_host_multilevel's host V-cycle.
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (the mesh uses another preconditioner). */
+int dg_test_multilevel_apply(dg_mesh* mesh, const double* r, double* z, int on_device);
+
 /* Test hook of the failure detection of the facet solvers (no counterpart in the
  * paper). Every grid barrier of the persistent solver kernels waits a bounded
  * number of polls (default 2^26); when the wait runs out the kernel sets an error

@@ -177,6 +177,24 @@ class DGMesh:
         """Flag growth of ||u||^2 by more than rel_tol in a step (dg_set_energy_watchdog); 0 turns it off."""
         check(lib().dg_set_energy_watchdog(self._h, float(rel_tol)), "dg_set_energy_watchdog")
 
+    def solver_history(self, enable=None):
+        """Per-iteration (relres, r.z, p.Sp, alpha) of the last multilevel solve (dg_solver_history);
+        enable=True/False starts/stops recording."""
+        mode = 2 if enable is None else (1 if enable else 0)
+        out = np.zeros(4 * 512)
+        n = ctypes.c_int(0)
+        check(lib().dg_solver_history(self._h, mode, out.ctypes.data_as(ctypes.c_void_p), out.size, ctypes.byref(n)),
+              "dg_solver_history")
+        return out.reshape(512, 4)[:min(n.value + 1, 512)]
+
+    def test_multilevel_apply(self, r):
+        """One device V-cycle z = M r of the multilevel preconditioner (dg_test_multilevel_apply)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.empty_like(r)
+        check(lib().dg_test_multilevel_apply(self._h, r.ctypes.data_as(ctypes.c_void_p),
+                                             z.ctypes.data_as(ctypes.c_void_p), 0), "dg_test_multilevel_apply")
+        return z
+
     def test_barrier_fault(self, spin_limit=0, skip_block=-1):
         """Failure-detection test hook (dg_test_barrier_fault): bounded barrier waits of the solvers."""
         check(lib().dg_test_barrier_fault(self._h, int(spin_limit), int(skip_block)), "dg_test_barrier_fault")

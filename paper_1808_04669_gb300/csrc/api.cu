@@ -1377,6 +1377,46 @@ int dg_set_energy_watchdog(dg_mesh* M, double rel_tol) {
   return finish(M, false);
 }
 
+int dg_test_multilevel_apply(dg_mesh* M, const double* r, double* z, int on_device) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!r || !z) return fail(DG_ERR_INVALID_ARG, "NULL r or z");
+  if (!M->use_ml) return fail(DG_ERR_UNSUPPORTED, "the mesh does not use the multilevel preconditioner");
+  const size_t n = size_t(M->dm.n_facet) * M->dm.nl;
+  double *rd = nullptr, *zd = nullptr;
+  if (!on_device) {
+    if (int rc = dalloc(M, &rd, n)) return rc;
+    if (int rc = dalloc(M, &zd, n)) return rc;
+    CK(cudaMemcpyAsync(rd, r, n * sizeof(double), cudaMemcpyHostToDevice, M->stream));
+  }
+  if (int rc = reset_flags(M)) return rc;
+  int rc = launch(M, KC_SOLVE_ML, [&] {
+    return dgdf::launch_ml_apply(M->dm, on_device ? r : rd, on_device ? z : zd, M->ml_blocks, M->stream);
+  });
+  if (rc) return rc;
+  if (!on_device) CK(cudaMemcpyAsync(z, zd, n * sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  return finish(M, true);
+}
+
+int dg_solver_history(dg_mesh* M, int enable, double* out, int cap, int* n_out) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!M->use_ml) return fail(DG_ERR_UNSUPPORTED, "the history is recorded by the multilevel solver only");
+  if (enable == 1 && !M->dm.ml_hist) {
+    if (int rc = dalloc(M, &M->dm.ml_hist, size_t(4) * dgdf::kMLHist)) return rc;
+  } else if (enable == 0) {
+    M->dm.ml_hist = nullptr;
+  }
+  if (out && M->dm.ml_hist) {
+    if (int rc = finish(M, false)) return rc;
+    const int n = std::min(std::max(cap, 0), 4 * dgdf::kMLHist);
+    CK(cudaMemcpy(out, M->dm.ml_hist, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (n_out) {
+    CK(cudaMemcpy(M->host_stats, M->dm.stats, sizeof(dgdf::DevStats), cudaMemcpyDeviceToHost));
+    *n_out = M->host_stats->last_iters;
+  }
+  return DG_OK;
+}
+
 int dg_test_barrier_fault(dg_mesh* M, int64_t spin_limit, int skip_block) {
   if (int rc = check_mesh(M)) return rc;
   if (spin_limit < 0) return fail(DG_ERR_INVALID_ARG, "spin_limit must be >= 0");

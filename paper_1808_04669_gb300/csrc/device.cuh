@@ -122,12 +122,15 @@ struct DevMesh {
   int ml_nlev, ml_nc;                 // smoothing levels, rows of the coarsest level
   const double* ml_cpinv;             // [ml_nc][ml_nc] pseudo-inverse of the coarsest operator
   double *ml_xc, *ml_bc;              // coarsest vectors
+  double* ml_hist;                    // NULL, or [kMLHist][4] per-iteration history of the last
+                                      // multilevel solve: relres, r.z, p.S p, alpha
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
 };
 
 constexpr int kRedSlots = 8;
+constexpr int kMLHist = 512;
 constexpr int kDnClasses = 4;
 constexpr int kMaxSolverBlocks = 2048;
 
@@ -196,6 +199,7 @@ cudaError_t launch_solve(const DevMesh& m, const SolveArgs& a, int nblocks, cuda
 // FP64 PCG with the multilevel preconditioner (k_multilevel.cu)
 cudaError_t launch_solve_ml(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s);
 int solver_ml_blocks(const DevMesh& m);
+cudaError_t launch_ml_apply(const DevMesh& m, const double* r, double* z, int nblocks, cudaStream_t s);
 int solver_max_blocks(const DevMesh& m, int mixed);
 size_t lattice_smem_bytes(int k, int N, int fp32, int grp);
 bool lattice_split(int N);

@@ -268,14 +268,26 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
       for (int j = 0; j < NL; ++j) m.lam[size_t(f) * NL + j] = 0.0;
     conv = true;
   } else {
+    // The V-cycle, unlike S, does not annihilate the constant multiplier (mode 0 = 1 on every
+    // facet, the kernel of S), and it amplifies that direction by about 1 / lambda_min(S):
+    // rounding that leaves a constant component in r would soon dominate z. So r is kept in the
+    // range of S: its mode-0 mean is subtracted before every V-cycle (the sum is carried along
+    // the updates: sum r_new = sum r_old - alpha sum q).
     for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
     if (!grid_sync(bar, m.stats)) return;
-    // r = g - S lam; first Chebyshev step of the V-cycle on r
+    // r = g - S lam, and its mode-0 sum
+    double r0s[1] = {0.0};
     for (int f = gtid; f < nF; f += gsz) {
       double y[NL];
       spmv64<NL>(m, f, m.lam, y);
 #pragma unroll
       for (int j = 0; j < NL; ++j) m.r[size_t(f) * NL + j] = m.g[size_t(f) * NL + j] - y[j];
+      r0s[0] += m.r[size_t(f) * NL];
+    }
+    if (!grid_reduce<1>(m, 0, r0s, bar)) return;
+    // remove the constant component; first Chebyshev step of the V-cycle on r
+    for (int f = gtid; f < nF; f += gsz) {
+      m.r[size_t(f) * NL] -= r0s[0] * inv_nf;
       ml_row_first_step<NL>(m, lv[0], f);
     }
     if (!grid_sync(bar, m.stats)) return;
@@ -284,9 +296,14 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
     if (!grid_reduce<3>(m, 1, red, bar)) return;
     double rho = red[0];
     rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
+    double rsum = red[2];   // mode-0 sum of r as the V-cycle saw it
     double beta = 0.0;
     double* pold = m.pa;
     double* pnew = m.pb;
+    // rounding floor: once 10 iterations in a row fail to halve the best residual, the solve
+    // ends, converged if that residual is below floor_rtol (as in the other solvers)
+    double best = rr;
+    int stall = 0;
     for (;; ++it) {
       if (!isfinite(rr) || !isfinite(rho)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
@@ -296,9 +313,16 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
         conv = true;
         break;
       }
+      if (rr < 0.25 * best) {
+        best = rr;
+        stall = 0;
+      } else if (++stall >= 10) {
+        conv = sqrt(best) <= a.floor_rtol * gnorm;
+        break;
+      }
       if (it >= a.maxit) break;
-      // p_new = z + beta p_old, q = S p_new
-      double pq[1] = {0.0};
+      // p_new = z + beta p_old, q = S p_new; reduce p.q and the mode-0 sum of q
+      double pq[2] = {0.0, 0.0};
       for (int f = gtid; f < nF; f += gsz) {
         int nb[5];
         facet_nbrs<NL>(m, f, nb);
@@ -318,20 +342,34 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
           m.q[size_t(f) * NL + j] = y[j];
           pq[0] += xs[0][j] * y[j];
         }
+        pq[1] += y[0];
       }
-      if (!grid_reduce<1>(m, 0, pq, bar)) return;
+      if (!grid_reduce<2>(m, 6, pq, bar)) return;
       if (!(pq[0] > 0.0)) {
         if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&m.stats->flags, kFlagNonFinite);
+        if (m.ml_hist && blockIdx.x == 0 && threadIdx.x == 0 && it < kMLHist) {
+          m.ml_hist[4 * it + 0] = sqrt(rr) / gnorm;
+          m.ml_hist[4 * it + 1] = rho;
+          m.ml_hist[4 * it + 2] = pq[0];
+          m.ml_hist[4 * it + 3] = -1.0;
+        }
         break;
       }
       const double alpha = rho / pq[0];
-      // lam += alpha p, r -= alpha q, first Chebyshev step on the new r
+      if (m.ml_hist && blockIdx.x == 0 && threadIdx.x == 0 && it < kMLHist) {
+        m.ml_hist[4 * it + 0] = sqrt(rr) / gnorm;
+        m.ml_hist[4 * it + 1] = rho;
+        m.ml_hist[4 * it + 2] = pq[0];
+        m.ml_hist[4 * it + 3] = alpha;
+      }
+      // lam += alpha p, r -= alpha q minus its constant component, first Chebyshev step on r
+      const double cmean = (rsum - alpha * pq[1]) * inv_nf;
       for (int f = gtid; f < nF; f += gsz) {
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
           const size_t o = size_t(f) * NL + j;
           m.lam[o] += alpha * pnew[o];
-          m.r[o] -= alpha * m.q[o];
+          m.r[o] -= alpha * m.q[o] + (j == 0 ? cmean : 0.0);
         }
         ml_row_first_step<NL>(m, lv[0], f);
       }
@@ -342,6 +380,7 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
       beta = red2[0] / rho;
       rho = red2[0];
       rr = fmax(red2[1] - red2[2] * red2[2] * inv_nf, 0.0);
+      rsum = red2[2];
       double* t = pold;
       pold = pnew;
       pnew = t;
@@ -359,6 +398,28 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
   }
 }
 
+// One V-cycle z = M r on its own (test hook dg_test_multilevel_apply): r and z are facet-major
+// [n_facet][k+1] in device memory. Uses the solver's level-0 vectors m.r and m.z.
+template <int K>
+__global__ void __launch_bounds__(kMLThreads) k_ml_apply(DevMesh m, const double* rin, double* zout) {
+  constexpr int NL = K + 1;
+  __shared__ MLLevelDev lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = m.ml_lv[l];
+  __syncthreads();
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  for (int f = gtid; f < m.n_facet; f += gsz) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) m.r[size_t(f) * NL + j] = rin[size_t(f) * NL + j];
+    ml_row_first_step<NL>(m, lv[0], f);
+  }
+  if (!grid_sync(m.bar, m.stats)) return;
+  double red[3] = {0.0, 0.0, 0.0};
+  if (!ml_vcycle<NL>(m, lv, red)) return;
+  for (int f = gtid; f < m.n_facet; f += gsz)
+#pragma unroll
+    for (int j = 0; j < NL; ++j) zout[size_t(f) * NL + j] = m.z[size_t(f) * NL + j];
+}
+
 const void* ml_kernel(int k) {
   switch (k) {
     case 1: return (const void*)k_solve_ml<1>;
@@ -369,6 +430,22 @@ const void* ml_kernel(int k) {
 }
 
 }  // namespace
+
+cudaError_t launch_ml_apply(const DevMesh& m, const double* r, double* z, int nblocks, cudaStream_t s) {
+  if (!m.ml_lv || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  const void* fn = nullptr;
+  switch (m.k) {
+    case 1: fn = (const void*)k_ml_apply<1>; break;
+    case 2: fn = (const void*)k_ml_apply<2>; break;
+    case 3: fn = (const void*)k_ml_apply<3>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  DevMesh mm = m;
+  void* args[] = {&mm, (void*)&r, (void*)&z};
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kMLThreads), args, 0, s);
+}
 
 int solver_ml_blocks(const DevMesh& m) {
   const void* fn = ml_kernel(m.k);

@@ -332,6 +332,42 @@ def test_multilevel_iterations_on_a_128_box_with_walls(g):
     assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multilevel_steps_on_a_128_box_with_walls(g, precision):
+    # SSP-RK3 steps on the 128 x 128 box: each stage's right-hand side is a small difference
+    # (the divergence-free u^n cancels in it), so the solve runs down to the rounding level, where
+    # the residual must be kept free of the constant multiplier that the V-cycle would amplify
+    k, nu = 3, 1e-4
+    vid, X = synth.split_square_mesh(128, L=1.0, periodic=False)
+    vals = synth.sample_lattice(synth.random_spectrum_velocity(5, kmax=3, L=1.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.abs(vals).max()), nu)
+    mesh = g.DGMesh(vid, X, k, nu, precision=precision)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    s0 = mesh.solver_stats()
+    mesh.rk3_step(dt, 2)
+    s1 = mesh.solver_stats()
+    assert s1["preconditioner"] == "multilevel"
+    assert (s1["total_iters"] - s0["total_iters"]) / (s1["solves"] - s0["solves"]) <= 40, s1
+    assert s1["last_relres"] <= 1e-13
+    dg = mesh.diagnostics()
+    assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-10
+
+
+@pytest.mark.parametrize("N,k,walls", [(8, 3, True), (64, 3, True), (64, 2, False)])
+def test_multilevel_device_v_cycle_matches_host_reference(g, N, k, walls):
+    # one V-cycle of the device kernel against the host set-up's reference V-cycle
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=not walls)
+    if not walls:
+        rng = np.random.default_rng(1)
+        X = X + (0.1 / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
+    mesh = g.DGMesh(vid, X, k, 1e-4, precond=g.PRECOND_MULTILEVEL)
+    r = np.random.default_rng(2).standard_normal((2, mesh.n_facet * (k + 1)))
+    host = g.host_multilevel(vid, X, k, r=r)["z"]
+    for i in range(2):
+        assert rel(mesh.test_multilevel_apply(r[i]), host[i]) < 1e-13
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_split_column_pass_parity_n64(g, k):
     # N = 64: the lattice solver splits each column into even and odd wavenumbers (N/2+1 <= SMs);
