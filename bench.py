@@ -400,7 +400,7 @@ def run_ours(args):
                  "roofline": roof64},
         "mixed_vs_fp64_rel_l2": rel,
         "solver": {"iters_per_solve": iters / max(solves, 1), "sweeps_per_solve": sweeps / max(solves, 1),
-                   "preconditioner": "lattice FFT" if mixed.solver_stats()["lattice"] else "block Jacobi",
+                   "preconditioner": mixed.solver_stats()["preconditioner"],
                    "dominant_kernel_ms_per_launch": per_launch_s * 1e3,
                    "kernel_ms": {k_: v[0] for k_, v in prof.items() if v[1]},
                    "share_of_device_time": {k_: v[0] / total_prof_ms for k_, v in prof.items() if v[1]}},
@@ -532,7 +532,8 @@ def run_schemes(args):
     m.project_divfree()
     ms, its = timed(m, dt, g.SSPRK3, args.steps, args.warmup)
     out["results"].append({"workload": "Taylor-Green cell, unit square with free-slip walls, %dx%d split squares "
-                                       "(%d triangles), BDM_%d, nu=%g, block-Jacobi PCG" % (N, N, m.n_tri, k, nu),
+                                       "(%d triangles), BDM_%d, nu=%g, %s PCG" % (N, N, m.n_tri, k, nu,
+                                                                                 m.solver_stats()["preconditioner"]),
                            "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
                            "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
     m.close()

@@ -107,3 +107,60 @@ def test_autograd_gradients_match_finite_differences(g):
     ad_u = float((x.grad * du).sum())
     assert abs(ad_u - float(fd_u)) < 1e-6 * abs(ad_u)
     assert abs(float(nu.grad) - float(fd_nu)) < 1e-6 * abs(float(nu.grad))
+
+
+def test_adjoint_gradient_at_the_gradient_workload_scale(g):
+    # The gradient workload: 128 x 128 unit square, BDM_2, nu = 1e-3, random-spectrum u0 (seed 3)
+    # and target (seed 4), J = 1/2 ||u_K - u*||^2 after K = 200 SSP-RK3 steps, checkpoints every 20.
+    # dg_rk3_vjp against central finite differences along a divergence-free direction and in nu.
+    w = synth.WORKLOADS["adjoint_n128_k2"]
+    vid, X, vals, dt = synth.make_workload(w)
+    mesh = g.DGMesh(vid, X, w.k, w.nu)
+    mesh.set_velocity(synth.sample_lattice(synth.random_spectrum_velocity(4, L=1.0), X, w.k, grid=(w.k * w.N, 1.0)))
+    target = mesh.get_coefficients()
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    u0 = mesh.get_coefficients()
+    K = w.steps
+
+    def J(u, nu):
+        mesh.set_viscosity(nu)
+        mesh.set_coefficients(u)
+        mesh.rk3_step(dt, K)
+        return 0.5 * float(((mesh.get_coefficients() - target) ** 2).sum())
+    mesh.set_coefficients(u0)
+    mesh.rk3_step(dt, K)
+    ubar = mesh.get_coefficients() - target
+    mesh.set_coefficients(u0)
+    u0bar, nubar = mesh.rk3_vjp(dt, K, ubar, checkpoint_every=20)
+    # divergence-free direction with the norm of u0
+    mesh.set_coefficients(np.random.default_rng(9).standard_normal(u0.shape))
+    mesh.project_divfree()
+    du = mesh.get_coefficients()
+    du *= np.linalg.norm(u0) / np.linalg.norm(du)
+    eps = 1e-5
+    fd_u = (J(u0 + eps * du, w.nu) - J(u0 - eps * du, w.nu)) / (2 * eps)
+    epsn = 1e-6
+    fd_nu = (J(u0, w.nu + epsn) - J(u0, w.nu - epsn)) / (2 * epsn)
+    ad_u = float((u0bar * du).sum())
+    assert abs(ad_u - fd_u) < 1e-6 * abs(ad_u), (ad_u, fd_u)
+    assert abs(nubar - fd_nu) < 1e-6 * abs(nubar), (nubar, fd_nu)
+
+
+def test_adjoint_of_the_mixed_form_matches_the_fp64_form(g):
+    # the mixed form runs the forward and the projections Q in double-float; the transposed
+    # residual Jacobian is FP64 in both forms: the two gradients agree to the mixed tolerance
+    vid, X = synth.split_square_mesh(16, L=1.0)
+    k, nu = 2, 1e-3
+    v0 = synth.sample_lattice(synth.random_spectrum_velocity(3, kmax=4, L=1.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((v0 ** 2).sum(-1)).max()), nu)
+    out = []
+    for prec in (0, 1):
+        mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+        mesh.set_velocity(v0)
+        mesh.project_divfree()
+        ubar = np.random.default_rng(4).standard_normal(mesh.get_coefficients().shape)
+        out.append(mesh.rk3_vjp(dt, 10, ubar, checkpoint_every=5))
+    (a, na), (b, nb) = out
+    assert np.linalg.norm(b - a) < 1e-9 * np.linalg.norm(a)
+    assert abs(nb - na) < 1e-9 * abs(na)
