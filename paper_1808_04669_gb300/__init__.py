@@ -173,6 +173,10 @@ class DGMesh:
         d["preconditioner"] = {0.0: "block Jacobi", 1.0: "lattice FFT", 2.0: "multilevel"}[d["precond_kind"]]
         return d
 
+    def set_tensor_cores(self, enable):
+        """Tensor-core (tcgen05) recovery on or off (dg_set_tensor_cores)."""
+        check(lib().dg_set_tensor_cores(self._h, int(bool(enable))), "dg_set_tensor_cores")
+
     def set_energy_watchdog(self, rel_tol):
         """Flag growth of ||u||^2 by more than rel_tol in a step (dg_set_energy_watchdog); 0 turns it off."""
         check(lib().dg_set_energy_watchdog(self._h, float(rel_tol)), "dg_set_energy_watchdog")

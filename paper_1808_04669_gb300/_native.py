@@ -16,7 +16,7 @@ STATUS = {0: "DG_OK", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_U
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
            "dg_project_divfree", "dg_rk3_step", "dg_step", "dg_batch_create", "dg_batch_destroy", "dg_batch_rk3_step", "dg_get_pressure", "dg_eval_residual", "dg_set_coefficients", "dg_get_coefficients",
            "dg_set_viscosity", "dg_rk3_vjp", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
-           "dg_set_energy_watchdog", "dg_solver_history", "dg_test_multilevel_apply", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
+           "dg_set_energy_watchdog", "dg_set_tensor_cores", "dg_solver_history", "dg_test_multilevel_apply", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
            "dg_host_facet_operator", "dg_host_lattice", "dg_host_multilevel"]
 
 
@@ -62,6 +62,7 @@ def lib():
         "dg_test_barrier_fault": (ctypes.c_int, [P, I64, ctypes.c_int]),
         "dg_test_multilevel_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "dg_solver_history": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P]),
+        "dg_set_tensor_cores": (ctypes.c_int, [P, ctypes.c_int]),
         "dg_profile": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
         "dg_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "dg_last_error": (ctypes.c_char_p, []),

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgdf.so")
 
-CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu", "k_multilevel.cu"]
+CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu", "k_multilevel.cu", "k_recover_tc.cu"]
 # (source, object name, extra flags): the lattice solver is compiled once per (k, form)
 CUDA_VARIANTS = [("k_lattice_inst.cu", "k_lattice_k%d_%d.o" % (k, m), ["-DDG_LAT_K=%d" % k, "-DDG_LAT_MIXED=%d" % m])
                  for k in (1, 2, 3) for m in (0, 1)]

@@ -63,6 +63,7 @@ struct dg_mesh {
   int solver_blocks[2] = {1, 1};
   bool use_lattice = false;
   int lattice_blocks = 0;
+  bool tc_available = false;      // the tensor-core recovery is set up (mixed form, <= 2 classes)
   bool use_ml = false;            // multilevel-preconditioned PCG (k_multilevel.cu)
   int ml_blocks = 0;
   std::string lattice_why;
@@ -484,6 +485,60 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
     std::vector<float> p2 = pairs(P, nd), g2 = pairs(G, L3);
     if ((rc = upload_f4(M, &d.ptab, pt)) || (rc = upload_f4(M, &d.P2, p2)) || (rc = upload_f4(M, &d.G2, g2)))
       return cleanup(rc);
+  }
+  if (d.elem_df && d.ptab && d.n_class <= 2) {
+    // tensor-core recovery: per class, tiles of 128 triangles, and the class operator
+    // B = [P, -G^T] (B[n][k], n < n_u output, k < n_u + 3(k+1) input) split into kTcSlices
+    // signed 8-bit digits per column scale, stored in the kernel's K-major tile layout
+    constexpr int S = 7;
+    int KP = 0, NP = 0;
+    dgdf::tc_dims(hm.k, &KP, &NP);
+    std::vector<int32_t> rows, tcls;
+    for (int c = 0; c < d.n_class; ++c) {
+      std::vector<int32_t> mine;
+      for (int t = 0; t < d.n_tri; ++t)
+        if (hm.tri_class[t] == c) mine.push_back(t);
+      for (size_t i = 0; i < mine.size(); i += 128) {
+        for (size_t j = 0; j < 128; ++j) rows.push_back(i + j < mine.size() ? mine[i + j] : -1);
+        tcls.push_back(c);
+      }
+    }
+    auto core_off = [&](int row, int k) {
+      return size_t((row >> 3) * (KP / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2) / 2;
+    };
+    std::vector<uint16_t> bb(size_t(d.n_class) * S * NP * KP, 0);
+    std::vector<int32_t> ec(size_t(d.n_class) * NP, 0);
+    for (int c = 0; c < d.n_class; ++c) {
+      const dgdf::ClassOps& co = hm.classes[c];
+      for (int n = 0; n < NP; ++n) {
+        std::vector<double> col(KP, 0.0);
+        if (n < nd)
+          for (int k = 0; k < nd + L3; ++k)
+            col[k] = k < nd ? co.P[size_t(n) * nd + k] : -co.G[size_t(k - nd) * nd + n];
+        double mx = 0.0;
+        for (double v : col) mx = std::max(mx, std::fabs(v));
+        int e = 0;
+        if (mx > 0.0) std::frexp(mx, &e);
+        ec[size_t(c) * NP + n] = e;
+        for (int k = 0; k < KP; ++k) {
+          double t = std::ldexp(col[k], -e);
+          for (int sl = 0; sl < S; ++sl) {
+            const double x = t * 256.0, dg = std::nearbyint(x);
+            t = x - dg;
+            const float df = float(dg);
+            uint32_t bits;
+            std::memcpy(&bits, &df, 4);
+            bb[(size_t(c) * S + sl) * NP * KP + core_off(n, k)] = uint16_t(bits >> 16);
+          }
+        }
+      }
+    }
+    if ((rc = upload(M, &d.tc_rows, rows)) || (rc = upload(M, &d.tc_tile_cls, tcls)) ||
+        (rc = upload(M, &d.tc_b, bb)) || (rc = upload(M, &d.tc_ec, ec)))
+      return cleanup(rc);
+    d.tc_tiles = int(tcls.size());
+    d.tc_rec = 1;
+    M->tc_available = true;
   }
   if (d.elem_df) {
     // reference tables in the field order of the kernels' shared-memory image
@@ -1363,6 +1418,16 @@ int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, con
   if (st.flags & dgdf::kFlagBarrierTimeout) return fail(DG_ERR_CUDA, "solver grid barrier timed out");
   if (st.flags & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
   if (st.flags & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached maxit");
+  return DG_OK;
+}
+
+int dg_set_tensor_cores(dg_mesh* M, int enable) {
+  if (int rc = check_mesh(M)) return rc;
+  if (enable != 0 && enable != 1) return fail(DG_ERR_INVALID_ARG, "enable must be 0 or 1");
+  if (enable && !M->tc_available)
+    return fail(DG_ERR_UNSUPPORTED, "the tensor-core recovery needs the mixed form and at most two geometry classes");
+  M->dm.tc_rec = enable;
+  ++M->gen;
   return DG_OK;
 }
 

@@ -117,6 +117,14 @@ struct DevMesh {
   void* lat_x2;                       // the same size: inverse halves of the split column pass
   int lat_split;                      // column pass split into even / odd wavenumbers
   int lat_tw2_off;                    // complex elements before the N/2 twiddles in shared memory
+  // tensor-core recovery (k_recover_tc.cu; mixed form, at most two geometry classes): tiles
+  // of 128 triangles of one class, the class operators [P, -G^T] as bf16 digit slices
+  int tc_rec;                         // 1: the stage kernel writes f into h_df, the recovery is k_recover_tc
+  int tc_tiles;
+  const int32_t* tc_rows;             // [tc_tiles][128] triangle ids, -1 padding
+  const int32_t* tc_tile_cls;         // [tc_tiles]
+  const uint16_t* tc_b;               // [n_class][kTcSlices][NP][KP] bf16 bits, tile layout
+  const int32_t* tc_ec;               // [n_class][NP] column exponents
   // multilevel preconditioner (NULL ml_lv: none)
   const MLLevelDev* ml_lv;            // [ml_nlev] in device memory
   int ml_nlev, ml_nc;                 // smoothing levels, rows of the coarsest level
@@ -176,6 +184,9 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
 // out may be NULL in the mixed form (only the double-float twin is written)
 cudaError_t launch_recover(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+// tensor-core recovery (tc_rec): u = [P, -G^T] [f; lam] per class tile
+cudaError_t launch_recover_tc(const DevMesh& m, double* out, float2* out_df, cudaStream_t s);
+int tc_dims(int k, int* kp, int* np);   // padded K and N of the tensor-core recovery for degree k
 // z = alpha x + beta y over n entries: double-float (mixed form) or FP64; z may alias x
 cudaError_t launch_axpby_df(const float2* x, const float2* y, float2* z, double alpha, double beta, long long n,
                             cudaStream_t s);

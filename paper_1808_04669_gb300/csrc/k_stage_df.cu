@@ -385,7 +385,12 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df2(DevMesh m, Sta
     }
   }
   const int cls = __ldg(&m.tri_class[t]);
-  if (a.mode != MODE_PRESSURE) {
+  if (a.mode != MODE_PRESSURE && m.tc_rec) {
+    // the tensor-core recovery applies P itself: keep f
+    if (live)
+#pragma unroll
+      for (int j = 0; j < NS; ++j) m.h_df[size_t(t) * ND + c * NS + j] = to_float2(f[j]);
+  } else if (a.mode != MODE_PRESSURE) {
     const float4* P = m.P2 + size_t(cls) * ND * NDP;
     for (int r = 0; r < NS; ++r) {
       const int i = c * NS + r;
@@ -512,6 +517,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 }
 
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
+  if (m.tc_rec) return launch_recover_tc(m, out, out_df, s);
   DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverThreads), kRecoverThreads, 0, s>>>(m, out, out_df)));
   return cudaGetLastError();
 }

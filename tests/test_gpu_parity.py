@@ -284,6 +284,56 @@ def test_wall_rk4_and_pressure_parity(g):
     assert rel(pe, pe_ref) < 1e-11 and rel(pf, pf_ref) < 1e-11
 
 
+# --------------------------------------------------------- tensor-core (tcgen05) recovery
+@pytest.mark.parametrize("N,k,walls", [(8, 1, False), (12, 2, False), (16, 3, False), (6, 3, True), (130, 3, False)])
+def test_tensor_core_recovery_matches_double_float_recovery(g, N, k, walls):
+    # the mixed form on a mesh with two geometry classes recovers u = [P, -G^T] [f; lam] on the
+    # tensor cores (8-bit digit splits, exact FP32 accumulation); the same steps with the
+    # double-float recovery on the FP32 units agree to the splits' 4e-15 (N = 130: 33800
+    # triangles, tiles with a ragged tail)
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=not walls)
+    vals = synth.sample_lattice(synth.random_spectrum_velocity(2, kmax=3, L=1.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), 1e-3)
+    out = []
+    for tc in (1, 0):
+        mesh = g.DGMesh(vid, X, k, 1e-3, precision=1)
+        mesh.set_tensor_cores(tc)
+        mesh.set_velocity(vals)
+        mesh.project_divfree()
+        mesh.rk3_step(dt, 3)
+        out.append(mesh.get_velocity())
+        dg = mesh.diagnostics()
+        assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-10
+    assert rel(out[0], out[1]) < 1e-12
+
+
+def test_tensor_core_recovery_against_oracle(g):
+    # shear layer, N = 16, BDM_3, five steps: the mixed form with the tensor-core recovery
+    # against the FP64 oracle at the mixed tolerance
+    k, nu, N = 3, 1e-4, 16
+    vid, X = synth.split_square_mesh(N)
+    vals = synth.sample_lattice(synth.double_shear_layer(), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    ref = d.to_lattice(d.rk3_step(d.project(d.from_lattice(vals)), dt, 5))
+    mesh = g.DGMesh(vid, X, k, nu, precision=1)
+    mesh.set_tensor_cores(1)
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    mesh.rk3_step(dt, 5)
+    assert rel(mesh.get_velocity(), ref) < TOLMIX
+
+
+def test_tensor_core_switch_rejected_where_not_set_up(g):
+    from paper_1808_04669_gb300 import DGError
+    vid, X = synth.split_square_mesh(4)
+    mesh = g.DGMesh(vid, X, 2, 0.0, precision=0)      # FP64 form: no tensor-core recovery
+    with pytest.raises(DGError) as e:
+        mesh.set_tensor_cores(1)
+    assert e.value.code == -3
+    mesh.set_tensor_cores(0)
+
+
 # ------------------------------------------------- multilevel preconditioner (non-lattice meshes)
 @pytest.mark.parametrize("N,k,walls,perturb", [(12, 2, True, 0.0), (12, 3, True, 0.0), (20, 1, True, 0.0),
                                                (10, 3, False, 0.12), (17, 2, False, 0.1)])
