@@ -291,6 +291,24 @@ def run_ours(args):
     t_ms = t_s * 1e3
     u_mixed = mixed.get_velocity()
 
+    # the same steps with the tensor-core (tcgen05) recovery, a secondary measurement
+    tc_line = None
+    try:
+        tcm = g.DGMesh(vid, X, k, w.nu, precision=g.MIXED, stream=stream.cuda_stream)
+        tcm.set_tensor_cores(1)
+        tcm.set_velocity(u0)
+        t_tc, prof_tc, _, _ = timed_steps(tcm, args.steps, args.warmup, profile=True)
+        rel_tc = float(np.linalg.norm(tcm.get_velocity() - u_mixed) / np.linalg.norm(u_mixed))
+        rec = prof_tc.get("recover", (0.0, 1))
+        tc_line = {"ms_per_step": t_tc / args.steps, "recover_ms_per_launch": rec[0] / max(rec[1], 1),
+                   "kernel_ms": {k_: v[0] for k_, v in prof_tc.items() if v[1]},
+                   "vs_double_float_recovery_rel_l2": rel_tc,
+                   "kernel": "k_recover_tc<%d>: u = [P, -G^T][f; lam] per 128-triangle class tile on tcgen05, "
+                             "7 bf16 digit slices per operand, exact FP32 accumulation in TMEM" % k}
+        tcm.close()
+    except g.DGError as e:
+        tc_line = {"unavailable": str(e)}
+
     # FP64 form on the same initial state and step count
     fp64 = g.DGMesh(vid, X, k, w.nu, precision=g.FP64, stream=stream.cuda_stream)
     fp64.set_velocity(u0)
@@ -399,6 +417,7 @@ def run_ours(args):
                  (s641["total_iters"] - s640["total_iters"]) / max(s641["solves"] - s640["solves"], 1),
                  "roofline": roof64},
         "mixed_vs_fp64_rel_l2": rel,
+        "tensor_core_recovery": tc_line,
         "solver": {"iters_per_solve": iters / max(solves, 1), "sweeps_per_solve": sweeps / max(solves, 1),
                    "preconditioner": mixed.solver_stats()["preconditioner"],
                    "dominant_kernel_ms_per_launch": per_launch_s * 1e3,

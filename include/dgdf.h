@@ -254,13 +254,14 @@ int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, con
                            const double* blocks, const double* binv, const double* g, double* lam, double rtol,
                            int maxit, void* cuda_stream, int* iterations, double* relres);
 
-/* Tensor-core recovery (mixed form, meshes with at most two geometry classes; on by
- * default where available). The recovery u_T = P_T f_T - G_T^T lam_T of eq. (12) runs
+/* Tensor-core recovery (mixed form, meshes with at most two geometry classes; off by
+ * default: on GB300 it measured slower than the double-float recovery, whose work is
+ * bound by memory latency, not by arithmetic). The recovery u_T = P_T f_T - G_T^T lam_T of eq. (12) runs
  * as one product [P_T, -G_T^T] [f_T; lam_T] per tile of 128 triangles of one class on
  * the tcgen05 tensor cores: bf16 operands split into seven signed 8-bit digits with
  * power-of-two scales, so that every FP32 accumulation is exact, and the digit levels
- * combined in double-float (relative error about 4e-15). enable = 0 uses the
- * double-float recovery on the FP32 units instead. Errors: DG_ERR_INVALID_ARG,
+ * combined in double-float (relative error about 4e-15). enable = 0 (the default)
+ * uses the double-float recovery on the FP32 units. Errors: DG_ERR_INVALID_ARG,
  * DG_ERR_UNSUPPORTED (enable = 1 where it is not set up). */
 int dg_set_tensor_cores(dg_mesh* mesh, int enable);
 

@@ -537,7 +537,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
         (rc = upload(M, &d.tc_b, bb)) || (rc = upload(M, &d.tc_ec, ec)))
       return cleanup(rc);
     d.tc_tiles = int(tcls.size());
-    d.tc_rec = 1;
+    d.tc_rec = 0;   // off by default: the double-float recovery is faster (dg_set_tensor_cores)
     M->tc_available = true;
   }
   if (d.elem_df) {

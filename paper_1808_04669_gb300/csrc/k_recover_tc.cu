@@ -4,6 +4,10 @@
 // triangles of a geometry class with the class operator as the shared operand
 // (M = 128 triangles per tile, K = n_u + 3(k+1) padded to 16 or 32, N = n_u padded).
 //
+// The MMAs: one per A digit slice and K-chunk (14), N = S n_u columns: the B operand is a
+// stack of S-1 zero blocks and the S digit slices of B, read from block S-1-s for A slice s,
+// so that output column block j receives the digit pairs (s, j-s) of level j.
+//
 // Precision. bf16 products with FP32 accumulation carry 8 bits; the mixed form needs
 // about 44. Each operand is therefore split into S = 7 signed 8-bit digits with one
 // power-of-two scale per row (A: the triangle's f and lam) or per column (B: the class
@@ -11,14 +15,15 @@
 // bf16). The product of two digits is an integer below 2^16, so the sums over K = 32 and
 // over the digit pairs (s, t) of one level L = s + t stay below 2^24 and the FP32
 // accumulation in TMEM is exact. Levels L < S are accumulated (sum_L (L+1) = 28
-// digit-pair products, 56 MMAs of K = 16), each in its own TMEM columns, and combined in
+// digit-pair products), each in its own TMEM columns, and combined in
 // double-float with the scales: the dropped levels L >= S bound the relative error by
 // about (S+1) K 2^(-8S) = 4e-15 of max|row| max|column|.
 //
-// One CTA of 128 threads per tile: every thread slices its triangle's row into shared
-// memory (canonical K-major core-matrix layout, no swizzle), one thread issues the MMAs
-// and commits them to an mbarrier, and every warp reads its 32 TMEM lanes (its 32
-// triangles) back. The mbarrier wait is bounded; TMEM is always released.
+// One CTA of 512 threads per tile (two CTAs per SM: 32 warps hide the gathers' latency):
+// four threads slice each triangle's row into shared memory (canonical K-major
+// core-matrix layout, no swizzle), one thread issues the MMAs and commits them to an
+// mbarrier, and warp w reads TMEM lanes 32 (w % 4) .. + 31 (its triangles) for column group
+// w / 4 back. The mbarrier wait is bounded; TMEM is always released.
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -31,7 +36,8 @@ namespace dgdf {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;          // triangles per tile (MMA M)
+constexpr int kTcBlock = 512;         // threads per CTA: four per row while slicing
 constexpr int kTcSlices = 7;          // digits per operand
 constexpr uint32_t kTcTmemCols = 256;
 constexpr unsigned long long kTcSpinLimit = 1ull << 20;
@@ -43,9 +49,12 @@ struct TcShape {
   static constexpr int KP = KR <= 16 ? 16 : 32;         // padded K
   static constexpr int NP = ND <= 16 ? 16 : 32;         // padded N
   static constexpr int S = kTcSlices;
-  static constexpr int A_BYTES = kTcThreads * KP * 2;   // one digit slice of the A tile
+  static constexpr int A_BYTES = kTcRows * KP * 2;      // one digit slice of the A tile
   static constexpr int B_BYTES = NP * KP * 2;           // one digit slice of B
-  static constexpr int SMEM = S * (A_BYTES + B_BYTES) + 256;
+  static constexpr int RS = ND + 1;                     // padded row of the staging tile (float2)
+  static_assert(kTcRows * RS * 8 <= S * A_BYTES, "the output tile reuses the A slices");
+  // A slices (later the output tile) | S-1 zero blocks and the S digit slices of B | mbarrier, rows
+  static constexpr int SMEM = S * A_BYTES + (2 * S - 1) * B_BYTES + 2048;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -96,6 +105,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "memory");
 }
 
+// 2^e as a float for -126 <= e <= 127 (built from its exponent field: exact)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// v 2^e, exact while the result is a normal float (two factors keep each in range)
+__device__ __forceinline__ float scale2(float v, int e) {
+  const int e1 = e / 2;
+  return v * pow2f(e1) * pow2f(e - e1);
+}
+
 // Byte offset of element (row, k) in a K-major no-swizzle tile with KP columns: core matrix
 // (row / 8, k / 8) holds 8 rows of 16 bytes; core matrices along K are 128 bytes apart, 8-row
 // groups KP / 8 * 128 bytes apart.
@@ -105,19 +122,24 @@ __device__ __forceinline__ uint32_t core_off(int row, int k) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kTcThreads) k_recover_tc(DevMesh m, double* out, float2* out_df) {
+__global__ void __launch_bounds__(kTcBlock, 2) k_recover_tc(DevMesh m, double* out, float2* out_df) {
   using T = TcShape<K>;
-  constexpr int ND = T::ND, NL = Dims<K>::NL, KP = T::KP, NP = T::NP, S = T::S;
+  constexpr int ND = T::ND, NL = Dims<K>::NL, L3 = T::L3, KP = T::KP, NP = T::NP, S = T::S, RS = T::RS;
+  constexpr int KQ = KP / 4;        // A values sliced per thread (4 threads per row)
+  constexpr int NG = NP / 8;        // column groups of 8 read back per level
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t* sA = smem;                                 // S slices of [128][KP] bf16
-  uint8_t* sB = smem + S * T::A_BYTES;                // S slices of [NP][KP] bf16
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + S * T::B_BYTES);
+  uint8_t* sA = smem;                                      // S slices of [128][KP] bf16
+  uint8_t* sB = smem + S * T::A_BYTES;                     // 2S-1 blocks of [NP][KP] bf16
+  float2* sIO = reinterpret_cast<float2*>(sA);             // [128][RS] u, once the MMAs are done
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (2 * S - 1) * T::B_BYTES);
   uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 1);
   int* ok_s = reinterpret_cast<int*>(taddr_s + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  int* rows_s = ok_s + 1;                                  // [128]
+  int* er_s = rows_s + kTcRows;                            // [128] row exponents
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x;
   const int cls = __ldg(&m.tc_tile_cls[tile]);
-  const int t = __ldg(&m.tc_rows[size_t(tile) * kTcThreads + tid]);   // -1: padding row
+  if (tid < kTcRows) rows_s[tid] = __ldg(&m.tc_rows[size_t(tile) * kTcRows + tid]);   // -1: padding
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
@@ -130,63 +152,115 @@ __global__ void __launch_bounds__(kTcThreads) k_recover_tc(DevMesh m, double* ou
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *ok_s = 1;
   }
-  // B: the class operator's digit slices, laid out on the host in this tile format
+  // B: S-1 zero blocks, then the class operator's S digit slices (laid out on the host). The
+  // MMA of A slice s reads the N = S NP rows starting at block S-1-s, so that its column block
+  // j meets B slice j - s (zero for j < s): column block j accumulates digit level j.
+  __syncthreads();   // rows_s
   {
     const uint4* src = reinterpret_cast<const uint4*>(m.tc_b) + size_t(cls) * (S * T::B_BYTES / 16);
     uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < S * T::B_BYTES / 16; i += kTcThreads) dst[i] = __ldg(&src[i]);
+    constexpr int nz = (S - 1) * T::B_BYTES / 16, nb = S * T::B_BYTES / 16;
+    for (int i = tid; i < nz; i += kTcBlock) dst[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < nb; i += kTcBlock) dst[nz + i] = __ldg(&src[i]);
   }
-  // A: this thread's row [f_T; lam_T] as double-float, its scale and its digit slices
-  int er = 0;
+  __syncthreads();
+  // A: row r = tid / 4, values k = KQ q .. KQ q + KQ - 1 (q = tid % 4) of [f_T; lam_T] (the four
+  // lanes of a row read its f contiguously); the row scale is the maximum over the four lanes;
+  // each digit slice is one 16-byte store
   {
-    dfl a[KP];
+    const int r = tid >> 2, q = tid & 3;
+    const int tr = rows_s[r];
+    // addresses first, then every load at once (no load behind a branch, so that they overlap):
+    // f from the recovery input, the multipliers of the row's facets with the sign of the
+    // facet's traversal for odd modes
+    int fac[3];
+    bool flp[3];
+    const int trv = tr >= 0 ? tr : 0;
 #pragma unroll
-    for (int k = 0; k < KP; ++k) a[k] = dfl(0);
-    if (t >= 0) {
+    for (int e = 0; e < 3; ++e) {
+      fac[e] = __ldg(&m.tri_facet[size_t(trv) * 3 + e]);
+      flp[e] = __ldg(&m.tri_orient[size_t(trv) * 3 + e]) < 0;
+    }
+    dfl a[KQ];
+    bool neg[KQ], use[KQ];
+    size_t idx[KQ];
+    bool is_f[KQ];
 #pragma unroll
-      for (int i = 0; i < ND; ++i) a[i] = to_dfl(m.h_df[size_t(t) * ND + i]);
+    for (int j = 0; j < KQ; ++j) {
+      const int k = KQ * q + j;
+      // k < ND: f; ND <= k < ND + L3: multiplier mode mm of local facet fe; beyond: padding, which
+      // reads a valid f entry of the row and is zeroed
+      const bool lam_k = k >= ND && k < ND + L3;
+      const int kl = lam_k ? k - ND : 0, fe = kl / NL, mm = kl - fe * NL;
+      is_f[j] = !lam_k;
+      use[j] = tr >= 0 && k < ND + L3;
+      neg[j] = lam_k && (mm & 1) && flp[fe];
+      const int f = fe == 0 ? fac[0] : (fe == 1 ? fac[1] : fac[2]);
+      idx[j] = lam_k ? size_t(f) * (m.lam_is_df ? m.lat_vs : NL) + mm : size_t(trv) * ND + min(k, ND - 1);
+    }
+    if (m.lam_is_df) {
+      float2 raw[KQ];
 #pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const int f = __ldg(&m.tri_facet[size_t(t) * 3 + e]);
-        const bool flip = __ldg(&m.tri_orient[size_t(t) * 3 + e]) < 0;
+      for (int j = 0; j < KQ; ++j) raw[j] = __ldcg(is_f[j] ? &m.h_df[idx[j]] : &m.lam_df[idx[j]]);
 #pragma unroll
-        for (int mm = 0; mm < NL; ++mm) {
-          const dfl v = m.lam_is_df ? to_dfl(__ldcg(&m.lam_df[size_t(f) * m.lat_vs + mm]))
-                                    : dfl(__ldcg(&m.lam[size_t(f) * NL + mm]));
-          a[ND + e * NL + mm] = (flip && (mm & 1)) ? -v : v;
-        }
+      for (int j = 0; j < KQ; ++j) {
+        const dfl v = to_dfl(raw[j]);
+        a[j] = use[j] ? (neg[j] ? -v : v) : dfl(0);
+      }
+    } else {
+      float2 rf[KQ];
+      double rl[KQ];
+#pragma unroll
+      for (int j = 0; j < KQ; ++j) {
+        rf[j] = __ldcg(&m.h_df[is_f[j] ? idx[j] : 0]);
+        rl[j] = __ldcg(&m.lam[is_f[j] ? 0 : idx[j]]);
+      }
+#pragma unroll
+      for (int j = 0; j < KQ; ++j) {
+        const dfl v = is_f[j] ? to_dfl(rf[j]) : dfl(rl[j]);
+        a[j] = use[j] ? (neg[j] ? -v : v) : dfl(0);
       }
     }
     float amax = 0.f;
 #pragma unroll
-    for (int k = 0; k < KP; ++k) amax = fmaxf(amax, fabsf(a[k].hi));
-    if (amax > 0.f) frexpf(amax, &er);
+    for (int j = 0; j < KQ; ++j) amax = fmaxf(amax, fabsf(a[j].hi));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 2));
+    // er: amax < 2^er <= 2 amax, from the exponent field (clamped: values near the top of the
+    // float range have overflowed anyway)
+    int er = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;
+    er = min(er, 126);
+    if (q == 0) er_s[r] = er;
     // digits: t_0 = a 2^-er in [-1, 1]; d_s = rint(256 t_s), t_(s+1) = 256 t_s - d_s
+    const float sc = pow2f(-er);   // |er| <= 127 for any finite row maximum that is a normal float
 #pragma unroll
-    for (int k = 0; k < KP; ++k) a[k] = dfl(ldexpf(a[k].hi, -er), ldexpf(a[k].lo, -er));
+    for (int j = 0; j < KQ; ++j) a[j] = dfl(a[j].hi * sc, a[j].lo * sc);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      uint32_t packed[KP / 2];
+    for (int sl = 0; sl < S; ++sl) {
+      uint32_t packed[KQ / 2];
 #pragma unroll
-      for (int k = 0; k < KP; k += 2) {
+      for (int j = 0; j < KQ; j += 2) {
         float d2[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const float x = a[k + q].hi * 256.f, y = a[k + q].lo * 256.f;
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const float x = a[j + h2].hi * 256.f, y = a[j + h2].lo * 256.f;
           const float d = rintf(x);
-          float h, l;
-          two_sum(x - d, y, h, l);   // exact: x - d is exact, the pair keeps the rest
-          a[k + q] = dfl(h, l);
-          d2[q] = d;
+          float hh, ll;
+          two_sum(x - d, y, hh, ll);   // exact: x - d is exact, the pair keeps the rest
+          a[j + h2] = dfl(hh, ll);
+          d2[h2] = d;
         }
         const __nv_bfloat16 b0 = __float2bfloat16_rn(d2[0]), b1 = __float2bfloat16_rn(d2[1]);
-        packed[k / 2] = uint32_t(__bfloat16_as_ushort(b0)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
+        packed[j / 2] = uint32_t(__bfloat16_as_ushort(b0)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
       }
-      uint8_t* base = sA + s * T::A_BYTES;
+      uint8_t* base = sA + sl * T::A_BYTES;
 #pragma unroll
-      for (int c = 0; c < KP / 8; ++c)
-        *reinterpret_cast<uint4*>(base + core_off<KP>(tid, 8 * c)) =
+      for (int c = 0; c < KQ / 8; ++c)
+        *reinterpret_cast<uint4*>(base + core_off<KP>(r, KQ * q + 8 * c)) =
             make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
+      if constexpr (KQ == 4) {   // K = 16: half a core-matrix row per thread
+        *reinterpret_cast<uint2*>(base + core_off<KP>(r, KQ * q)) = make_uint2(packed[0], packed[1]);
+      }
     }
   }
   // operands visible to the tensor cores, TMEM address visible to every thread
@@ -196,22 +270,19 @@ __global__ void __launch_bounds__(kTcThreads) k_recover_tc(DevMesh m, double* ou
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *taddr_s;
   if (tid == 0) {
-    constexpr uint32_t idesc = idesc_bf16(kTcThreads, NP);
+    constexpr uint32_t idesc = idesc_bf16(kTcRows, S * NP);
     constexpr uint32_t LBO = 128, SBO = (KP / 8) * 128;
     const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-    for (int L = 0; L < S; ++L) {
-      uint32_t acc = 0;
-      for (int s = 0; s <= L; ++s) {
-        const int tt = L - s;
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int sl = 0; sl < S; ++sl)
 #pragma unroll
-        for (int kk = 0; kk < KP / 16; ++kk) {
-          const uint64_t ad = smem_desc(a0 + s * T::A_BYTES + kk * 256, LBO, SBO);
-          const uint64_t bd = smem_desc(b0 + tt * T::B_BYTES + kk * 256, LBO, SBO);
-          tc_mma(tmem + uint32_t(L * NP), ad, bd, idesc, acc);
-          acc = 1;
-        }
+      for (int kk = 0; kk < KP / 16; ++kk) {
+        const uint64_t ad = smem_desc(a0 + sl * T::A_BYTES + kk * 256, LBO, SBO);
+        const uint64_t bd = smem_desc(b0 + (S - 1 - sl) * T::B_BYTES + kk * 256, LBO, SBO);
+        tc_mma(tmem, ad, bd, idesc, acc);
+        acc = 1;
       }
-    }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                  : "memory");
   }
@@ -228,40 +299,51 @@ __global__ void __launch_bounds__(kTcThreads) k_recover_tc(DevMesh m, double* ou
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   const bool ok = *ok_s != 0;
-  if (ok) {
-    // u[n] = sum_L 2^(er + ec[n] - 8 (L + 2)) D_L[n], smallest levels first
-    dfl u[ND];
+  // read-back: warp w owns TMEM lanes 32 (w % 4) .. + 31 (rows) and column group w / 4 of
+  // every level; u[n] = sum_L 2^(er + ec[n] - 8 (L + 2)) D_L[n], smallest levels first
+  if (ok && warp / 4 < NG) {
+    const int r = 32 * (warp & 3) + lane, g = warp >> 2;
+    const int er = er_s[r];
+    const int* ec = m.tc_ec + cls * NP + 8 * g;
+    dfl u[8];
+    int ecj[8];
 #pragma unroll
-    for (int n = 0; n < ND; ++n) u[n] = dfl(0);
-    const int* ec = m.tc_ec + cls * NP;
-    const uint32_t lane_base = uint32_t(warp * 32) << 16;
+    for (int j = 0; j < 8; ++j) {
+      u[j] = dfl(0);
+      ecj[j] = __ldg(&ec[j]);
+    }
+    const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
+#pragma unroll 1
     for (int L = S - 1; L >= 0; --L) {
+      uint32_t v[8];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(tmem + lane_base + uint32_t(L * NP + 8 * g))
+                   : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < NP; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + lane_base + uint32_t(L * NP + c0), r);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
-          if (n < ND) u[n] = u[n] + dfl(ldexpf(__uint_as_float(r[j]), er + __ldg(&ec[n]) - 8 * (L + 2)), 0.f);
-        }
-      }
+      for (int j = 0; j < 8; ++j) u[j] = u[j] + dfl(scale2(__uint_as_float(v[j]), er + ecj[j] - 8 * (L + 2)), 0.f);
     }
-    if (t >= 0) {
 #pragma unroll
-      for (int n = 0; n < ND; ++n) {
-        if (out_df) out_df[size_t(t) * ND + n] = to_float2(u[n]);
-        if (out) out[size_t(t) * ND + n] = to_double(u[n]);
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(&m.stats->flags, kFlagBarrierTimeout);
+    for (int j = 0; j < 8; ++j)
+      if (8 * g + j < ND) sIO[r * RS + 8 * g + j] = to_float2(u[j]);
   }
+  if (!ok && tid == 0) atomicOr(&m.stats->flags, kFlagBarrierTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+  if (ok) {
+    // coalesced writes of the tile's rows
+    for (int e = tid; e < kTcRows * ND; e += kTcBlock) {
+      const int r = e / ND, c = e - r * ND;
+      const int tr = rows_s[r];
+      if (tr < 0) continue;
+      const float2 v = sIO[r * RS + c];
+      if (out_df) out_df[size_t(tr) * ND + c] = v;
+      if (out) out[size_t(tr) * ND + c] = to_double(v);
+    }
+  }
 }
 
 template <int K>
@@ -269,14 +351,14 @@ cudaError_t launch_tc(const DevMesh& m, double* out, float2* out_df, cudaStream_
   using T = TcShape<K>;
   // at most two CTAs per SM, so that their TMEM (2 x 256 columns) always fits
   static bool attr = false;
-  const int smem = 100 * 1024;
+  const int smem = 110 * 1024;
   static_assert(T::SMEM <= smem, "tile does not fit the requested shared memory");
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_recover_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_recover_tc<K><<<m.tc_tiles, kTcThreads, smem, s>>>(m, out, out_df);
+  k_recover_tc<K><<<m.tc_tiles, kTcBlock, smem, s>>>(m, out, out_df);
   return cudaGetLastError();
 }
 
