@@ -471,8 +471,11 @@ def run_ensemble(args):
         meshes.append(m)
         units_per_step += dof_stage_units(m.n_tri, k, 1)
     batch = g.DGBatch(meshes)
+    batch.set_lanes(args.lanes)
     dts = np.array(dts)
-    batch.rk3_step(dts, args.warmup)
+    # warm-up: the eager steps that fill every member's multiplier history, then the lane
+    # tuner's replays (two per candidate), before the timed region
+    batch.rk3_step(dts, max(args.warmup, 12))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     batch.rk3_step(dts, args.steps)
@@ -480,6 +483,7 @@ def run_ensemble(args):
     value, _, t = job_rate(units_per_step * args.steps, time.perf_counter() - t0, dist, "cuda")
     lat, tris = reduce_over_ranks([sum(int(m.solver_stats()["lattice"]) for m in meshes),
                                    sum(m.n_tri for m in meshes)], "sum", dist, "cuda")
+    lanes, tune = batch.tuning()
     batch.close()
     if dist is not None:
         dist.barrier()
@@ -493,7 +497,9 @@ def run_ensemble(args):
                       "dtype": "f32x2 (double-float) element kernels and PCG vectors, f32 Fourier preconditioner, f64 state",
                       "config": {"workload": "ensemble of %d periodic unit-square meshes, N~U{32..256}, "
                                              "k~U{1,2,3}, log10 nu~U[-5,-2], seed 1" % n_inst,
-                                 "graph": "one captured CUDA graph per step (dg_batch_rk3_step)"}}), flush=True)
+                                 "graph": "one captured CUDA graph per step (dg_batch_rk3_step), members on "
+                                          "%d parallel branches" % lanes},
+                      "lanes": lanes, "lane_tuning_ms_per_step": {str(k_): v for k_, v in tune.items()}}), flush=True)
 
 
 def run_schemes(args):
@@ -684,6 +690,7 @@ def main():
                     help="step: the bench line; ensemble / adjoint / schemes: the batching, gradient, "
                          "time-scheme and wall workloads")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--lanes", type=int, default=0, help="ensemble: parallel graph branches (0: autotune)")
     ap.add_argument("--steps-adjoint", type=int, default=200)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--summarize-launches", metavar="CSV", help="print a per-kernel summary of an ncu launch list")

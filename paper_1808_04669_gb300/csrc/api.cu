@@ -65,6 +65,7 @@ struct dg_mesh {
   int lattice_blocks = 0;
   bool tc_available = false;      // the tensor-core recovery is set up (mixed form, <= 2 classes)
   bool use_ml = false;            // multilevel-preconditioned PCG (k_multilevel.cu)
+  int grid_div = 1;               // solver grid divided by this while a batch runs lanes
   int ml_blocks = 0;
   std::string lattice_why;
   double last_c = 0.0;            // coefficient of L(u') in the last stage solved
@@ -250,6 +251,14 @@ void forget_history(dg_mesh* M) {
   for (int s = 0; s < dg_mesh::kMaxStages; ++s) M->hist_n[s] = 0;
 }
 
+// Persistent solver blocks: the mesh's maximum, divided by the ensemble's lanes while a batch
+// runs members on parallel graph branches (so that every solver grid that can run at the
+// same time fits on the device together, and no grid barrier waits for another grid's blocks).
+int capped(const dg_mesh* M, int nb) {
+  if (M->grid_div > 1) nb = std::max(1, nb / M->grid_div);
+  return nb;
+}
+
 int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
@@ -277,15 +286,15 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
   a.inner_maxit = M->p.cg_maxit;
   a.floor_rtol = 1e-9;
   if (M->use_lattice) {
-    const int nb = M->lattice_blocks;
+    const int nb = capped(M, M->lattice_blocks);
     return launch(M, a.mixed ? KC_SOLVE_LAT32 : KC_SOLVE_LAT64,
                   [&] { return dgdf::launch_solve_lattice(M->dm, a, nb, a.mixed, M->stream); });
   }
   if (M->use_ml) {
-    const int nb = M->ml_blocks;
+    const int nb = capped(M, M->ml_blocks);
     return launch(M, KC_SOLVE_ML, [&] { return dgdf::launch_solve_ml(M->dm, a, nb, M->stream); });
   }
-  const int nb = M->solver_blocks[a.mixed];
+  const int nb = capped(M, M->solver_blocks[a.mixed]);
   return launch(M, a.mixed ? KC_SOLVE_MIXED : KC_SOLVE64, [&] { return dgdf::launch_solve(M->dm, a, nb, M->stream); });
 }
 
@@ -969,6 +978,13 @@ struct dg_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<double> graph_dt;
   std::vector<long long> graph_gen;   // each member's gen when the graph was captured
+  // lanes: members are dealt out to this many parallel branches of the captured step (0: the
+  // autotuner picks it on the next call); the branch streams, their join events
+  int lanes = 0;
+  int graph_lanes = 0;                 // lanes of the captured graph
+  std::vector<cudaStream_t> lane_streams;
+  std::vector<cudaEvent_t> lane_events;
+  double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};   // measured step time for 1, 2, 4, 8 lanes
 };
 
 extern "C" {
@@ -1016,10 +1032,110 @@ int dg_batch_destroy(dg_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->ev) cudaEventDestroy(B->ev);
+  for (cudaEvent_t e : B->lane_events) cudaEventDestroy(e);
+  for (cudaStream_t st : B->lane_streams) cudaStreamDestroy(st);
   if (B->stream) cudaStreamDestroy(B->stream);
   delete B;
   return DG_OK;
 }
+
+int dg_batch_set_lanes(dg_batch* B, int lanes) {
+  if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
+  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+    return fail(DG_ERR_INVALID_ARG, "lanes must be 0 (autotune), 1, 2, 4 or 8");
+  B->lanes = lanes;
+  if (lanes == 0)
+    for (double& t : B->tune_ms) t = -1.0;
+  return DG_OK;
+}
+
+int dg_batch_get_tuning(dg_batch* B, int* lanes, double ms[4]) {
+  if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
+  if (lanes) *lanes = B->lanes;
+  if (ms)
+    for (int i = 0; i < 4; ++i) ms[i] = B->tune_ms[i];
+  return DG_OK;
+}
+
+namespace {
+
+// Capture one SSP-RK3 step of every member as B's graph: members dealt out (largest first, to
+// the least loaded) to `lanes` parallel branches forked from and joined into the batch stream;
+// each member's solver grid is divided by the lanes for the capture.
+int capture_batch_step(dg_batch* B, const double* dt, int lanes) {
+  const size_t n = B->members.size();
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+  B->graph_lanes = 0;
+  lanes = std::max(1, std::min(lanes, int(n)));
+  while (int(B->lane_streams.size()) < lanes) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(DG_ERR_CUDA, "dg_batch_rk3_step: lane stream");
+    B->lane_streams.push_back(st);
+    B->lane_events.push_back(ev);
+  }
+  // largest members first, each to the lane with the least work so far
+  std::vector<size_t> order(n);
+  for (size_t i = 0; i < n; ++i) order[i] = i;
+  auto work = [&](size_t i) { return double(B->members[i]->dm.n_tri) * B->members[i]->dm.nd; };
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work(a) > work(b); });
+  std::vector<double> load(lanes, 0.0);
+  std::vector<int> lane_of(n, 0);
+  for (size_t i : order) {
+    const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
+    lane_of[i] = l;
+    load[l] += work(i);
+  }
+  for (dg_mesh* M : B->members) M->prof = false;   // no timing events inside the graph
+  cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  int rc = DG_OK;
+  if (lanes > 1) {
+    e = cudaEventRecord(B->ev, B->stream);
+    for (int l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(B->lane_streams[l], B->ev, 0);
+    if (e != cudaSuccess) rc = fail(DG_ERR_CUDA, std::string("fork: ") + cudaGetErrorString(e));
+  }
+  for (size_t i = 0; i < n && rc == DG_OK; ++i) {
+    dg_mesh* M = B->members[i];
+    M->stream = lanes > 1 ? B->lane_streams[lane_of[i]] : B->stream;
+    M->grid_div = lanes;
+    rc = enqueue_step(M, dt[i]);
+    M->grid_div = 1;
+    M->stream = B->stream;
+  }
+  if (lanes > 1 && rc == DG_OK) {
+    for (int l = 0; l < lanes && e == cudaSuccess; ++l) {
+      e = cudaEventRecord(B->lane_events[l], B->lane_streams[l]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->lane_events[l], 0);
+    }
+    if (e != cudaSuccess) rc = fail(DG_ERR_CUDA, std::string("join: ") + cudaGetErrorString(e));
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(B->stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(DG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  B->graph = g;
+  B->graph_lanes = lanes;
+  B->graph_dt.assign(dt, dt + n);
+  B->graph_gen.resize(n);
+  for (size_t i = 0; i < n; ++i) B->graph_gen[i] = B->members[i]->gen;
+  return DG_OK;
+}
+
+}  // namespace
 
 int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
   if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
@@ -1080,31 +1196,51 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     ++done;
     same_dt = false;              // the graph (if any) predates these eager steps
   }
-  if (done < nsteps && !same_dt) {
-    if (B->exec) cudaGraphExecDestroy(B->exec);
-    if (B->graph) cudaGraphDestroy(B->graph);
-    B->exec = nullptr;
-    B->graph = nullptr;
-    for (dg_mesh* M : B->members) M->prof = false;   // no timing events inside the graph
-    cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e)));
-    for (size_t i = 0; i < n && rc == DG_OK; ++i) rc = enqueue_step(B->members[i], dt[i]);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(B->stream, &g);
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return restore(rc);
+  // The autotuner: with lanes = 0, capture the step for 1, 2, 4 and 8 lanes in turn, time one
+  // replay of each (each a real step of the run) and keep the fastest. Member results do not
+  // depend on the lanes beyond the rounding of the solver's block-wise reductions.
+  if (done < nsteps && B->lanes == 0) {
+    const int cands[4] = {1, 2, 4, 8};
+    int best = 1;
+    double best_ms = -1.0;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    for (int ci = 0; ci < 4 && done < nsteps; ++ci) {
+      const int L = cands[ci];
+      if (L > 1 && L > int(n)) break;
+      if ((rc = capture_batch_step(B, dt, L))) break;
+      // one untimed replay uploads the graph, one timed replay measures it (when steps remain)
+      cudaError_t e = cudaGraphLaunch(B->exec, B->stream);
+      ++done;
+      if (e == cudaSuccess && done < nsteps) {
+        cudaEventRecord(t0, B->stream);
+        e = cudaGraphLaunch(B->exec, B->stream);
+        cudaEventRecord(t1, B->stream);
+        ++done;
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess) {
+          B->tune_ms[ci] = ms;
+          if (best_ms < 0.0 || ms < best_ms) {
+            best_ms = ms;
+            best = L;
+          }
+        }
+      }
+      if (e != cudaSuccess) {
+        rc = fail(DG_ERR_CUDA, std::string("dg_batch_rk3_step (tuning): ") + cudaGetErrorString(e));
+        break;
+      }
     }
-    if (e != cudaSuccess) return restore(fail(DG_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e)));
-    e = cudaGraphInstantiate(&B->exec, g, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return restore(fail(DG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)));
-    }
-    B->graph = g;
-    B->graph_dt.assign(dt, dt + n);
-    B->graph_gen.resize(n);
-    for (size_t i = 0; i < n; ++i) B->graph_gen[i] = B->members[i]->gen;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc) return restore(rc);
+    B->lanes = best;
+    same_dt = B->exec && B->graph_lanes == best;
+  }
+  if (done < nsteps && (!same_dt || B->graph_lanes != B->lanes)) {
+    if ((rc = capture_batch_step(B, dt, B->lanes))) return restore(rc);
   }
   for (int64_t s = done; s < nsteps; ++s) {
     cudaError_t e = cudaGraphLaunch(B->exec, B->stream);

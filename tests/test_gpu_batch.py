@@ -52,6 +52,7 @@ def test_batch_equals_members_stepped_alone(g):
     solo = [p[0][1] for p in pairs]
     dts = np.array([p[1] for p in pairs])
     batch = g.DGBatch(batch_members)
+    batch.set_lanes(1)
     batch.rk3_step(dts, 4)          # eager first step, graph capture, 3 replays
     batch.rk3_step(dts, 2)          # replays of the cached graph
     for m, dt in zip(solo, dts):
@@ -80,6 +81,7 @@ def test_batch_sees_a_viscosity_changed_between_calls(g):
     solo = [p[0][1] for p in pairs]
     dts = np.array([p[1] for p in pairs])
     batch = g.DGBatch(batch_members)
+    batch.set_lanes(1)
     batch.rk3_step(dts, 4)          # eager step, capture, replays
     for m, dt in zip(solo, dts):
         m.rk3_step(dt, 4)
@@ -94,6 +96,33 @@ def test_batch_sees_a_viscosity_changed_between_calls(g):
     batch.close()
 
 
+@pytest.mark.parametrize("lanes", [4, 0])
+def test_batch_on_parallel_lanes_equals_members_stepped_alone(g, lanes):
+    # members dealt out to parallel branches of the graph, solver grids divided by the lanes
+    # (fixed 4 lanes, or chosen by the tuner); results equal the solo runs up to the rounding of
+    # the solvers' block-wise reductions
+    pairs = [make(g, spec, 70 + i) for i, spec in enumerate(MEMBERS)]
+    batch_members = [p[0][0] for p in pairs]
+    solo = [p[0][1] for p in pairs]
+    dts = np.array([p[1] for p in pairs])
+    batch = g.DGBatch(batch_members)
+    batch.set_lanes(lanes)
+    batch.rk3_step(dts, 12)         # eager step, tuning replays (lanes = 0), captured replays
+    chosen, times = batch.tuning()
+    assert chosen in (1, 2, 4, 8)
+    if lanes == 0:
+        assert 1 in times and len(times) >= 2, times
+    else:
+        assert chosen == lanes
+    for m, dt in zip(solo, dts):
+        m.rk3_step(dt, 12)
+    for mb, ms in zip(batch_members, solo):
+        a, b = mb.get_velocity(), ms.get_velocity()
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(b).max())
+        assert mb.diagnostics()["max_jump"] < 1e-10
+    batch.close()
+
+
 def test_batch_rejects_bad_arguments(g):
     from paper_1808_04669_gb300 import DGError
     (m, _), dt = make(g, MEMBERS[0], 1)
@@ -102,4 +131,6 @@ def test_batch_rejects_bad_arguments(g):
     b = g.DGBatch([m])
     with pytest.raises(DGError):
         b.rk3_step([-1.0], 1)
+    with pytest.raises(DGError):
+        b.set_lanes(3)
     b.close()
