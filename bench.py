@@ -475,7 +475,7 @@ def run_ensemble(args):
     dts = np.array(dts)
     # warm-up: the eager steps that fill every member's multiplier history, then the lane
     # tuner's replays (two per candidate), before the timed region
-    batch.rk3_step(dts, max(args.warmup, 12))
+    batch.rk3_step(dts, max(args.warmup, 14))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     batch.rk3_step(dts, args.steps)

@@ -203,14 +203,14 @@ int dg_batch_rk3_step(dg_batch* batch, const double* dt, int64_t nsteps);
  * divided by the lanes, so that every solver grid that can run at the same time fits
  * on the device together (no grid barrier can wait for another grid's blocks).
  * lanes = 0 (the default) makes the next dg_batch_rk3_step tune it: it captures the
- * step for 1, 2, 4 and 8 lanes, times one replay of each (these are real steps of the
- * run, two per candidate) and keeps the fastest. lanes 1, 2, 4 or 8 fixes it.
+ * step for 1, 2, 4, 8 and 16 lanes, times one replay of each (these are real steps of
+ * the run, two per candidate) and keeps the fastest. lanes 1, 2, 4, 8 or 16 fixes it.
  * Member results do not depend on the lanes beyond the rounding of the solvers'
  * block-wise reductions. Errors: DG_ERR_INVALID_ARG. */
 int dg_batch_set_lanes(dg_batch* batch, int lanes);
 /* The lanes in use (0 before tuning) and the step times measured by the tuner for
- * 1, 2, 4, 8 lanes in ms (-1 where not measured); either pointer may be NULL. */
-int dg_batch_get_tuning(dg_batch* batch, int* lanes, double ms[4]);
+ * 1, 2, 4, 8, 16 lanes in ms (-1 where not measured); either pointer may be NULL. */
+int dg_batch_get_tuning(dg_batch* batch, int* lanes, double ms[5]);
 
 /* Pressure of the current state: the (w, lam) of eq. (12) with the functional
  * L(u) alone, so w ~ p in the elements and lam ~ p on the skeleton (Theorem 2,

@@ -237,15 +237,15 @@ class DGBatch:
         check(lib().dg_batch_rk3_step(self._h, d.ctypes.data_as(ctypes.c_void_p), int(nsteps)), "dg_batch_rk3_step")
 
     def set_lanes(self, lanes):
-        """Parallel branches of the captured step: 0 = autotune on the next call, or 1, 2, 4, 8."""
+        """Parallel branches of the captured step: 0 = autotune on the next call, or 1, 2, 4, 8, 16."""
         check(lib().dg_batch_set_lanes(self._h, int(lanes)), "dg_batch_set_lanes")
 
     def tuning(self):
         """(lanes in use, {lanes: measured ms per step}) (dg_batch_get_tuning)."""
         ln = ctypes.c_int(0)
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 5)()
         check(lib().dg_batch_get_tuning(self._h, ctypes.byref(ln), ms), "dg_batch_get_tuning")
-        return ln.value, {c: ms[i] for i, c in enumerate((1, 2, 4, 8)) if ms[i] >= 0}
+        return ln.value, {c: ms[i] for i, c in enumerate((1, 2, 4, 8, 16)) if ms[i] >= 0}
 
     def close(self):
         if getattr(self, "_h", None):

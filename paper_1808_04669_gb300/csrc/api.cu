@@ -984,7 +984,7 @@ struct dg_batch {
   int graph_lanes = 0;                 // lanes of the captured graph
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_events;
-  double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};   // measured step time for 1, 2, 4, 8 lanes
+  double tune_ms[5] = {-1.0, -1.0, -1.0, -1.0, -1.0};   // measured step time for 1, 2, 4, 8, 16 lanes
 };
 
 extern "C" {
@@ -1041,19 +1041,19 @@ int dg_batch_destroy(dg_batch* B) {
 
 int dg_batch_set_lanes(dg_batch* B, int lanes) {
   if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
-  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
-    return fail(DG_ERR_INVALID_ARG, "lanes must be 0 (autotune), 1, 2, 4 or 8");
+  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16)
+    return fail(DG_ERR_INVALID_ARG, "lanes must be 0 (autotune), 1, 2, 4, 8 or 16");
   B->lanes = lanes;
   if (lanes == 0)
     for (double& t : B->tune_ms) t = -1.0;
   return DG_OK;
 }
 
-int dg_batch_get_tuning(dg_batch* B, int* lanes, double ms[4]) {
+int dg_batch_get_tuning(dg_batch* B, int* lanes, double ms[5]) {
   if (!B) return fail(DG_ERR_INVALID_ARG, "NULL batch");
   if (lanes) *lanes = B->lanes;
   if (ms)
-    for (int i = 0; i < 4; ++i) ms[i] = B->tune_ms[i];
+    for (int i = 0; i < 5; ++i) ms[i] = B->tune_ms[i];
   return DG_OK;
 }
 
@@ -1196,17 +1196,17 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
     ++done;
     same_dt = false;              // the graph (if any) predates these eager steps
   }
-  // The autotuner: with lanes = 0, capture the step for 1, 2, 4 and 8 lanes in turn, time one
+  // The autotuner: with lanes = 0, capture the step for 1, 2, 4, 8 and 16 lanes in turn, time one
   // replay of each (each a real step of the run) and keep the fastest. Member results do not
   // depend on the lanes beyond the rounding of the solver's block-wise reductions.
   if (done < nsteps && B->lanes == 0) {
-    const int cands[4] = {1, 2, 4, 8};
+    const int cands[5] = {1, 2, 4, 8, 16};
     int best = 1;
     double best_ms = -1.0;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    for (int ci = 0; ci < 4 && done < nsteps; ++ci) {
+    for (int ci = 0; ci < 5 && done < nsteps; ++ci) {
       const int L = cands[ci];
       if (L > 1 && L > int(n)) break;
       if ((rc = capture_batch_step(B, dt, L))) break;
