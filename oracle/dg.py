@@ -13,7 +13,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .mesh import Topology
+from .mesh import Topology, INFLOW, OUTFLOW
 from .quadrature import triangle_rule, facet_rule
 
 RK3_STAGES = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))  # Sec. 2.3, eq. (8)
@@ -33,10 +33,14 @@ def _binom(n, m):
 class Discretization:
     """Spaces of Sec. 2.1 (eq. (4)) and the operators of Secs. 2.2-2.4 and 3 on one mesh."""
 
-    def __init__(self, tri_vertex_ids, tri_coords, k, nu, alpha=2.0, chunk=4096):
+    def __init__(self, tri_vertex_ids, tri_coords, k, nu, alpha=2.0, chunk=4096, boundary=None, inflow=None):
+        """boundary: kind per triangle edge [n_tri, 3] (0 wall, 1 inflow, 2 outflow; used on boundary
+        edges only), the boundary parts of Sec. 2.5, eq. (be); inflow: the inflow velocity u_in at the
+        k+1 equispaced points of every edge in the triangle's counter-clockwise direction
+        [n_tri, 3, k+1, 2] (read on inflow edges only)."""
         if k < 1:
             raise ValueError("k >= 1")
-        self.topo = Topology(tri_vertex_ids, tri_coords)
+        self.topo = Topology(tri_vertex_ids, tri_coords, boundary)
         self.k = int(k)
         self.nu = float(nu)
         self.alpha = float(alpha)
@@ -52,6 +56,7 @@ class Discretization:
         self.n_tri = self.topo.n_tri
         self.n_facet = self.topo.n_facet
         self._ops = None
+        self._set_inflow(inflow)
 
     # ------------------------------------------------------------------ basis
     def _basis(self, exps, tri, P):
@@ -116,6 +121,57 @@ class Discretization:
         V, G = self._basis(self.exps, tri, P)
         return tri, V, G
 
+    # ------------------------------------------------- inflow / outflow (Sec. 2.5)
+    def _set_inflow(self, inflow):
+        """u_in at the facet Gauss points of every inflow facet (canonical parameter) and the
+        moments d_F[m] = <mu_m, u_in.n>_F of its normal component (n outward from the domain):
+        the inhomogeneous constraint u.n = u_in.n on Gamma_in of eq. (be), tested against the
+        multiplier space P^k(F) as the normal-continuity rows of eq. (12)."""
+        T = self.topo
+        nq = len(self.ft)
+        self.inflow_q = np.zeros((self.n_facet, nq, 2))
+        self.inflow_d = np.zeros(self.n_facet * self.nl)
+        f = T.inflow
+        if len(f) == 0:
+            return
+        if inflow is None:
+            raise ValueError("inflow facets need inflow data")
+        vals = np.asarray(inflow, dtype=np.float64).reshape(self.n_tri, 3, self.k + 1, 2)
+        t0, e0, o0 = T.facet_tri[f, 0], T.facet_loc[f, 0], T.facet_orient[f, 0]
+        v = vals[t0, e0]                                         # element direction
+        v = np.where((o0 > 0)[:, None, None], v, v[:, ::-1, :])   # canonical direction
+        nodes = np.arange(self.k + 1) / self.k
+        Lq = np.stack([np.prod([(self.ft - nodes[j]) / (nodes[i] - nodes[j])
+                                for j in range(self.k + 1) if j != i], axis=0) for i in range(self.k + 1)], 0)
+        uq = np.einsum("iq,fic->fqc", Lq, v)
+        self.inflow_q[f] = uq
+        n0 = T.normal[t0, e0]
+        wq = self.fw[None, :] * T.facet_len[f][:, None]
+        mu = self._facet_basis(self.ft)
+        d = np.einsum("fq,mq,fq->fm", wq, mu, np.einsum("fqc,fc->fq", uq, n0))
+        self.inflow_d.reshape(self.n_facet, self.nl)[f] = d
+
+    def _boundary_flux(self, U, R):
+        """Convective terms of eq. (7) on inflow and outflow facets (Sec. 2.5): the flux
+        (u.n) u^up with u.n the average of the interior trace and the exterior state, and the
+        upwind value taken from the side u.n leaves. The exterior state is u_in on an inflow
+        facet and the interior trace on an outflow facet. Walls add nothing (u.n = 0), and the
+        viscous form has no boundary terms: natural conditions on every boundary facet."""
+        T = self.topo
+        f = np.concatenate([T.inflow, T.outflow])
+        if len(f) == 0:
+            return
+        t0, V0, _ = self._facet_side(f, 0)
+        e0 = T.facet_loc[f, 0]
+        n0 = T.normal[t0, e0]
+        u0 = np.einsum("fqj,fcj->fqc", V0, U[t0])
+        uext = np.where((T.facet_kind[f] == INFLOW)[:, None, None], self.inflow_q[f], u0)
+        un = 0.5 * np.einsum("fqc,fc->fq", u0 + uext, n0)
+        uup = np.where((un >= 0)[..., None], u0, uext)
+        wq = self.fw[None, :] * T.facet_len[f][:, None]
+        c0 = np.einsum("fq,fqc,fqj->fcj", wq, -un[..., None] * uup, V0)
+        np.add.at(R, t0, c0)
+
     # --------------------------------------------------------------- residual
     def residual(self, U, nu=None):
         """R[t, i] = L(u)(phi_i) = -C_h(u; u, phi_i) - B_h(u, phi_i) for every broken test phi_i.
@@ -164,6 +220,7 @@ class Discretization:
             Rf[t0, T.facet_loc[f, 0]] = c0                       # each (triangle, local facet) once
             Rf[t1, T.facet_loc[f, 1]] = c1
         R += Rf.sum(axis=1)
+        self._boundary_flux(U, R)
         return R.reshape(self.n_tri, self.nd)
 
     # ---------------------------------------------------------------- tangent
@@ -175,6 +232,8 @@ class Discretization:
         its equivalent form 1/2 (u.n)(u0 + u1) + 1/2 |u.n| (u0 - u1) with d|s|/ds = sign(s),
         sign(0) = 0.
         """
+        if len(self.topo.inflow) or len(self.topo.outflow):
+            raise NotImplementedError("the tangent covers walls and periodic meshes only")
         nu = self.nu
         ns = self.ns
         U = np.asarray(U, dtype=np.float64).reshape(self.n_tri, 2, ns)
@@ -325,35 +384,52 @@ class Discretization:
         rows = np.repeat(dof, 3 * nl, axis=1).ravel()
         cols = np.tile(dof, (1, 3 * nl)).ravel()
         S = sp.csc_matrix((Sloc.ravel(), (rows, cols)), shape=(nlam, nlam))
-        lu = spla.splu(S[1:, 1:].tocsc())
+        # p = 0 on Gamma_out (eq. (be)): the multipliers of outflow facets are zero, and the rest
+        # of S is nonsingular; without outflow facets the constant multiplier is pinned instead
+        act = np.ones(nlam, dtype=bool)
+        out = self.topo.outflow
+        if len(out):
+            act[(out[:, None] * nl + np.arange(nl)[None, :]).ravel()] = False
+        else:
+            act[0] = False
+        act = np.flatnonzero(act)
+        lu = spla.splu(S[act][:, act].tocsc())
         Zint = None
         if nw:
             Pp, Wq = self._vol(np.arange(n))
             Zv, _ = self._basis(self.wexps, np.arange(n), Pp)
             Zint = np.einsum("tq,tqm->tm", Wq, Zv)
-        self._ops = dict(P=Pm, W=Wm, C=Cm, M=Mm, D=Dm, CP=CP, dof=dof, S=S, lu=lu, Zint=Zint)
+        self._ops = dict(P=Pm, W=Wm, C=Cm, M=Mm, D=Dm, CP=CP, dof=dof, S=S, lu=lu, Zint=Zint, act=act)
         return self._ops
 
     # ------------------------------------------------------------------ solve
-    def solve_condensed(self, F):
+    def solve_condensed(self, F, homogeneous=False):
         """Hybrid-mixed solve of eq. (12) for the functional F[t, i] (Theorem 2).
 
         Returns (u, w, lam): u in the globally divergence-free space, w and lam
-        before the constant shift (see normalize_pressure).
+        before the constant shift (see normalize_pressure). With inflow facets u.n = u_in.n
+        holds there (Sec. 2.5): the facet system is S lam = g - d with the data moments d;
+        homogeneous = True solves with u.n = 0 instead (the time derivative of a state that
+        keeps the inflow data, as for the pressure functional L(u)).
         """
         o = self.prepare()
         F = np.asarray(F).reshape(self.n_tri, self.nd)
         gloc = np.einsum("tij,tj->ti", o["CP"], F)
         g = np.bincount(o["dof"].ravel(), weights=gloc.ravel(), minlength=self.n_facet * self.nl)
+        if not homogeneous:
+            g = g - self.inflow_d
         lam = np.zeros_like(g)
-        lam[1:] = o["lu"].solve(g[1:])
+        lam[o["act"]] = o["lu"].solve(g[o["act"]])
         r = F - np.einsum("tij,ti->tj", o["C"], lam[o["dof"]])
         u = np.einsum("tij,tj->ti", o["P"], r)
         w = np.einsum("tij,tj->ti", o["W"], r)
         return u, w, lam
 
     def normalize_pressure(self, w, lam):
-        """Shift w and lam by one constant so that the integral of w over the domain is zero (L^2_0, eq. (4e))."""
+        """Shift w and lam by one constant so that the integral of w over the domain is zero (L^2_0, eq. (4e)).
+        With outflow facets p = 0 there fixes the constant (eq. (be)): no shift."""
+        if len(self.topo.outflow):
+            return w, lam
         o = self.prepare()
         c = (o["Zint"] * w).sum() / self.topo.area.sum()
         w = w.copy()
@@ -386,9 +462,10 @@ class Discretization:
         K = sp.csr_matrix((np.concatenate(blocks_v), (np.concatenate(blocks_r), np.concatenate(blocks_c))),
                           shape=(N, N))
         keep = np.ones(N, dtype=bool)
-        keep[nu_ + nwt] = False
+        keep[nu_ + nwt + np.setdiff1d(np.arange(nlam), o["act"])] = False   # outflow (or the pinned dof)
         rhs = np.zeros(N)
         rhs[:nu_] = np.asarray(F).ravel()
+        rhs[nu_ + nwt:] = self.inflow_d       # C u = d on inflow facets, 0 elsewhere
         x = np.zeros(N)
         x[keep] = spla.spsolve(K[keep][:, keep].tocsc(), rhs[keep])
         return x[:nu_].reshape(n, nd), x[nu_:nu_ + nwt].reshape(n, nw), x[nu_ + nwt:]
@@ -407,18 +484,34 @@ class Discretization:
         Cg = sp.csr_matrix((o["C"].ravel(), (rows, cols)), shape=(self.n_facet * self.nl, n * nd))
         return sp.vstack([Dg, Cg]).tocsr()
 
+    def _active_constraints(self):
+        """Constraint rows and right-hand side: the outflow facets' normal-trace rows are
+        dropped (u.n is free there), inflow rows carry the data moments (Sec. 2.5)."""
+        B = self.constraint_matrix()
+        nw_all = self.n_tri * self.nw
+        keep = np.ones(B.shape[0], dtype=bool)
+        out = self.topo.outflow
+        if len(out):
+            keep[nw_all + (out[:, None] * self.nl + np.arange(self.nl)[None, :]).ravel()] = False
+        c = np.concatenate([np.zeros(nw_all), self.inflow_d])
+        return B[keep], c[keep]
+
     def divfree_basis(self):
-        """Explicit orthonormal basis Z of V_h^{k,-1} by SVD (tiny meshes only)."""
-        B = self.constraint_matrix().toarray()
-        return sla.null_space(B, rcond=1e-11)
+        """Explicit orthonormal basis Z of V_h^{k,-1} (with the boundary conditions: the space
+        with u.n = 0 on inflow facets) by SVD (tiny meshes only)."""
+        B, _ = self._active_constraints()
+        return sla.null_space(B.toarray(), rcond=1e-11)
 
     def project_nullspace(self, F):
-        """L2 projection through the explicit basis: u = Z (Z^T M Z)^-1 Z^T F."""
+        """L2 projection through the explicit basis onto the affine space {B u = c}:
+        u = u_p + Z (Z^T M Z)^-1 Z^T (F - M u_p), u_p any solution of B u = c."""
         o = self.prepare()
         Z = self.divfree_basis()
+        B, c = self._active_constraints()
+        up = np.linalg.lstsq(B.toarray(), c, rcond=None)[0]
         Mg = sp.block_diag([o["M"][t] for t in range(self.n_tri)]).toarray()
-        a = np.linalg.solve(Z.T @ Mg @ Z, Z.T @ np.asarray(F).ravel())
-        return (Z @ a).reshape(self.n_tri, self.nd)
+        a = np.linalg.solve(Z.T @ Mg @ Z, Z.T @ (np.asarray(F).ravel() - Mg @ up))
+        return (up + Z @ a).reshape(self.n_tri, self.nd)
 
     def solve_fe4(self, F):
         """Locally divergence-free hybrid variant eq. (13): broken div-free velocity and lam only.
@@ -477,7 +570,7 @@ class Discretization:
     def slope(self, U):
         """Time derivative of the semi-discrete system eq. (6) on V_h^{k,-1}: the hybrid-mixed
         solve of eq. (12) with the functional L(u) alone (the mass inversion of Sec. 3.1)."""
-        du, _, _ = self.solve_condensed(self.residual(U))
+        du, _, _ = self.solve_condensed(self.residual(U), homogeneous=True)
         return du
 
     def euler_step(self, U, dt, nsteps=1):
@@ -500,7 +593,7 @@ class Discretization:
 
     def pressure(self, U):
         """(w, lam) of eq. (12) with the functional L(u) alone: w ~ p, lam ~ p on the skeleton (Theorem 2, Remark 2)."""
-        _, w, lam = self.solve_condensed(self.residual(U))
+        _, w, lam = self.solve_condensed(self.residual(U), homogeneous=True)
         return self.normalize_pressure(w, lam)
 
     # --------------------------------------------------------------- lattice
@@ -567,7 +660,10 @@ class Discretization:
         fi = T.interior
         _, V1, _ = self._facet_side(fi, 1)
         u1[fi] = np.einsum("fqj,fcj->fqc", V1, U[T.facet_tri[fi, 1]])
-        jmax = float(np.abs(np.einsum("fqc,fc->fq", u0 - u1, n0)).max())
+        u1[T.inflow] = self.inflow_q[T.inflow]      # inflow: against the data; outflow: u.n is free
+        jmp = np.abs(np.einsum("fqc,fc->fq", u0 - u1, n0))
+        jmp[T.outflow] = 0.0
+        jmax = float(jmp.max())
         return dict(energy=self.energy(U.reshape(self.n_tri, -1)), enstrophy=ens, max_div=divmax, max_jump=jmax)
 
     def upwind_dissipation(self, U):

@@ -10,14 +10,18 @@ Definitions (shared with the C-ABI as conventions, implemented independently):
   identified vertices in the same canonical order and have the same edge
   vector (this separates the periodic images on meshes as coarse as 1 x 1);
 * facets are numbered in order of first appearance over (triangle, local facet);
-* an edge that no other triangle shares is a boundary facet (a wall of the domain): it has
-  one side, and facet_tri / facet_loc / facet_orient hold -1 for the missing second side.
+* an edge that no other triangle shares is a boundary facet: it has one side, and
+  facet_tri / facet_loc / facet_orient hold -1 for the missing second side. Its kind comes
+  from the caller's per-edge array (edge e of a triangle is opposite its vertex e): WALL
+  (default), INFLOW or OUTFLOW, the boundary parts of Sec. 2.5, eq. (be).
 """
 import numpy as np
 
+WALL, INFLOW, OUTFLOW = 0, 1, 2
+
 
 class Topology:
-    def __init__(self, tri_vertex_ids, tri_coords):
+    def __init__(self, tri_vertex_ids, tri_coords, edge_kind=None):
         vid = np.asarray(tri_vertex_ids, dtype=np.int64)
         X = np.asarray(tri_coords, dtype=np.float64)
         n = vid.shape[0]
@@ -77,6 +81,16 @@ class Topology:
             for s in range(2 if not self.boundary[f] else 1):
                 self.tri_facet[self.facet_tri[f, s], self.facet_loc[f, s]] = f
         self.facet_len = self.edge_len[self.facet_tri[:, 0], self.facet_loc[:, 0]]
+        self.facet_kind = np.full(self.n_facet, WALL, dtype=np.int64)
+        if edge_kind is not None:
+            ek = np.asarray(edge_kind).reshape(n, 3)
+            b = np.flatnonzero(self.boundary)
+            self.facet_kind[b] = ek[self.facet_tri[b, 0], self.facet_loc[b, 0]]
+            if np.any((self.facet_kind < 0) | (self.facet_kind > 2)):
+                raise ValueError("edge kinds are 0 (wall), 1 (inflow) or 2 (outflow)")
+        self.facet_kind[~self.boundary] = WALL   # the kind of an interior edge is not used
+        self.inflow = np.flatnonzero(self.boundary & (self.facet_kind == INFLOW))
+        self.outflow = np.flatnonzero(self.boundary & (self.facet_kind == OUTFLOW))
 
     def facet_points(self, f, side, t):
         """Physical points (in the side's own unwrapped coordinates) at canonical parameters t.

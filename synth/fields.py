@@ -7,7 +7,7 @@ grid, by an inverse FFT of the same coefficients.
 """
 import numpy as np
 
-from .mesh import lattice_points
+from .mesh import lattice_points, edge_points
 
 
 def taylor_green(L=2.0 * np.pi):
@@ -132,3 +132,11 @@ def sample_lattice(field, tri_coords, k, grid=None):
             return vals
     u1, u2 = field(P[..., 0], P[..., 1])
     return np.stack([u1, u2], axis=-1)
+
+
+def sample_edges(field, tri_coords, k):
+    """field at the k+1 equispaced points of every triangle edge (counter-clockwise direction):
+    [n_tri, 3, k+1, 2], the boundary-data format of the inflow condition."""
+    P = edge_points(tri_coords, k)
+    a, b = field(P[..., 0], P[..., 1])
+    return np.stack([np.broadcast_to(a, P.shape[:-1]), np.broadcast_to(b, P.shape[:-1])], -1).astype(np.float64)

@@ -515,3 +515,69 @@ def test_oracle_tangent_matches_finite_differences():
         dm = Discretization(vid, X, 2, 1e-2 - eps * dnu)
         fd = (dp.rk3_step(U + eps * dU, 0.01, 3) - dm.rk3_step(U - eps * dU, 0.01, 3)) / (2 * eps)
         assert np.linalg.norm(fd - dUk) / np.linalg.norm(dUk) < 1e-7
+
+
+# ----------------------------------------------------- inflow / outflow (Sec. 2.5, eq. (be))
+def _channel(Nx, Ny, k, periodic_y, inflow_field, Lx=1.5, Ly=1.0, nu=0.0):
+    vid, X = synth.channel_mesh(Nx, Ny, Lx, Ly, periodic_y=periodic_y)
+    bk = synth.boundary_kinds_by_x(X, 0.0, Lx)
+    uin = synth.sample_edges(inflow_field, X, k)
+    return Discretization(vid, X, k, nu, boundary=bk, inflow=uin), X
+
+
+@pytest.mark.parametrize("k,periodic_y", [(1, True), (2, True), (3, True), (2, False)])
+def test_inflow_outflow_solve_routes_agree(k, periodic_y):
+    # the condensed solve with the data moments on inflow facets and lam = 0 on outflow facets,
+    # the uncondensed saddle system and the SVD null-space projection onto the affine space agree,
+    # and the result keeps u.n = u_in.n on the inflow (to the multiplier space) and div u = 0
+    def f_in(x, y):
+        return 1.0 + 0.3 * np.sin(2 * np.pi * y) + 0 * x, 0.2 * np.cos(2 * np.pi * y) + 0 * x
+    d, X = _channel(3, 2, k, periodic_y, f_in)
+    F = np.random.default_rng(k).standard_normal((d.n_tri, d.nd))
+    u1, _, _ = d.solve_condensed(F)
+    u2, _, _ = d.solve_full(F)
+    u3 = d.project_nullspace(F)
+    sc = np.abs(u1).max()
+    assert np.abs(u1 - u2).max() < 1e-12 * sc and np.abs(u1 - u3).max() < 1e-12 * sc
+    dg = d.diagnostics(u1)
+    assert dg["max_div"] < 1e-10 * sc and dg["max_jump"] < 1e-10 * sc
+    # a random functional of the homogeneous problem: u.n = 0 on the inflow instead
+    u0, _, _ = d.solve_condensed(F, homogeneous=True)
+    assert np.abs(u1 - u0).max() > 0.1          # the O(1) inflow data moves the solution
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_shear_flow_through_a_channel_is_steady(k):
+    # Euler (nu = 0): u = (U(y), 0) is steady between free-slip walls, with u_in = u on the inflow and
+    # the outflow open: for a polynomial U of degree <= k the discrete residual vanishes for every
+    # broken test function (the boundary fluxes cancel the integration by parts), so the state is
+    # kept to rounding over the steps
+    U = (lambda y: 1.0 + 0.5 * y) if k == 1 else (lambda y: 1.0 + y * (1.0 - y))
+
+    def f(x, y):
+        return U(y) + 0 * x, 0 * y
+    d, X = _channel(4, 3, k, False, f)
+    U0 = d.project(d.from_lattice(synth.sample_lattice(f, X, k)))
+    ref = d.from_lattice(synth.sample_lattice(f, X, k))
+    assert np.abs(U0 - ref).max() < 1e-12
+    assert np.abs(d.residual(U0)).max() < 1e-12
+    U1 = d.rk3_step(U0, 0.01, 5)
+    assert np.abs(U1 - U0).max() < 1e-12
+
+
+def test_inflow_carries_its_momentum_in_and_outflow_lets_it_out():
+    # test function (0, 1) (divergence-free, zero normal component on the inflow, periodic in y):
+    # one forward Euler step from u = (1, 0) with inflow data (1, eps) changes int v by exactly
+    # dt * eps * Ly (the inflow flux of eq. (7) with the exterior state u_in); from u = (1, eps)
+    # with the same data nothing changes (the outflow takes the interior trace)
+    eps, Ly, dt, k = 0.07, 1.0, 0.02, 2
+    d, X = _channel(4, 3, k, True, lambda x, y: (1.0 + 0 * x, eps + 0 * y), Ly=Ly)
+    E = d.from_lattice(synth.sample_lattice(lambda x, y: (0 * x, 1.0 + 0 * y), X, k))
+
+    def int_v(U):
+        return float((d.apply_mass(U) * E).sum())
+    U0 = d.from_lattice(synth.sample_lattice(lambda x, y: (1.0 + 0 * x, 0 * y), X, k))
+    U1 = d.euler_step(U0, dt)
+    assert abs(int_v(U1) - dt * eps * Ly) < 1e-13
+    Ue = d.from_lattice(synth.sample_lattice(lambda x, y: (1.0 + 0 * x, eps + 0 * y), X, k))
+    assert np.abs(d.euler_step(Ue, dt) - Ue).max() < 1e-13
