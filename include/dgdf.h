@@ -112,6 +112,30 @@ typedef struct {
 int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords,
                    const dg_params* params, dg_mesh** out);
 
+/* dg_mesh_create with the kinds of the boundary facets of Sec. 2.5, eq. (be).
+ * edge_kind int8 [n_tri][3] (host memory; edge e of a triangle is the one opposite its
+ * vertex e), read on boundary edges only: 0 wall (u.n = 0, the default of dg_mesh_create),
+ * 1 inflow (u.n = u_in.n with the data of dg_set_inflow, zero until it is called), 2 outflow
+ * (p = 0: the facet's multipliers are zero and u.n is free). On inflow and outflow facets the
+ * convective flux of eq. (7) takes u.n as the average of the interior trace and the exterior
+ * state (u_in on inflow, the interior trace on outflow) and the upwind value from the side
+ * u.n leaves; the viscous form has no boundary terms (natural conditions on every boundary
+ * facet). With an outflow facet the facet system is definite and the pressure is not shifted
+ * to mean zero. NULL edge_kind: every boundary facet is a wall.
+ * Errors: those of dg_mesh_create; DG_ERR_INVALID_ARG for a kind outside 0..2. */
+int dg_mesh_create_ex(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords,
+                      const int8_t* edge_kind, const dg_params* params, dg_mesh** out);
+
+/* Inflow data u_in of Sec. 2.5 (eq. (be)) for a mesh with inflow facets: vals double
+ * [n_tri][3][k+1][2] (host memory), the velocity at the k+1 equispaced points of every
+ * triangle edge, from vertex (e+1) mod 3 to vertex (e+2) mod 3 of the triangle (its
+ * counter-clockwise direction); read on inflow edges only, interpolated to the facet
+ * quadrature points. Steps, projections and stage solves then impose u.n = u_in.n (as the
+ * moments against the multiplier basis) and take u_in as the exterior state of the
+ * convective flux. Synchronises the mesh's stream. Errors: DG_ERR_INVALID_ARG (NULL, no
+ * inflow facets, non-finite values), DG_ERR_CUDA. */
+int dg_set_inflow(dg_mesh* mesh, const double* vals);
+
 /* Release every device buffer of the mesh. NULL is allowed. */
 int dg_mesh_destroy(dg_mesh* mesh);
 
@@ -179,7 +203,8 @@ int dg_set_viscosity(dg_mesh* mesh, double nu);
  * broken space; pair it with divergence-free directions (or project it) for the
  * gradient on V_h^{k,-1}. States are kept every checkpoint_every steps and each segment
  * is recomputed during the reverse sweep (device memory: (K/checkpoint_every +
- * 3 checkpoint_every + 5) states, allocated for the call). */
+ * 3 checkpoint_every + 5) states, allocated for the call). Meshes with inflow or outflow
+ * facets (dg_mesh_create_ex) give DG_ERR_UNSUPPORTED. */
 int dg_rk3_vjp(dg_mesh* mesh, double dt, int64_t nsteps, int64_t checkpoint_every, const double* ubar,
                double* u0bar, double* nubar, int on_device);
 
@@ -215,7 +240,10 @@ int dg_batch_get_tuning(dg_batch* batch, int* lanes, double ms[5]);
 /* Pressure of the current state: the (w, lam) of eq. (12) with the functional
  * L(u) alone, so w ~ p in the elements and lam ~ p on the skeleton (Theorem 2,
  * Remark 2), shifted by one constant so that the integral of w is zero
- * (L^2_0, eq. (4e)). p_elem [n_tri][n_lat(k-1)]; p_facet [n_facet][k+1] or NULL. */
+ * (L^2_0, eq. (4e)); with outflow facets p = 0 there fixes the constant and no shift is
+ * applied (eq. (be)), and u.n = 0 is imposed on inflow facets (the functional L(u) is the
+ * time derivative of a state that keeps its inflow data).
+ * p_elem [n_tri][n_lat(k-1)]; p_facet [n_facet][k+1] or NULL. */
 int dg_get_pressure(dg_mesh* mesh, double* p_elem, double* p_facet, int on_device);
 
 /* Riesz representer of L(u) for the current state u (no projection): the

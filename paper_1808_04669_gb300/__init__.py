@@ -41,12 +41,20 @@ class DGMesh:
     """One mesh and its state, owned by libdgdf (dg_mesh_create ... dg_mesh_destroy)."""
 
     def __init__(self, tri_vertex_ids, tri_coords, k, nu, alpha=2.0, precision=FP64, cg_rtol=1e-13,
-                 cg_maxit=20000, stream=None, precond=PRECOND_AUTO):
+                 cg_maxit=20000, stream=None, precond=PRECOND_AUTO, boundary=None, inflow=None):
+        """boundary: kind of every triangle edge [n_tri, 3] (0 wall, 1 inflow, 2 outflow; edge e
+        is opposite vertex e; read on boundary edges), or None for walls (dg_mesh_create_ex);
+        inflow: u_in at the k+1 equispaced points of every edge [n_tri, 3, k+1, 2] (set_inflow)."""
         L = lib()
         vid = np.ascontiguousarray(tri_vertex_ids, dtype=np.int64)
         X = np.ascontiguousarray(tri_coords, dtype=np.float64)
         if vid.ndim != 2 or vid.shape[1] != 3 or X.shape != (vid.shape[0], 3, 2):
             raise ValueError("tri_vertex_ids [n,3] and tri_coords [n,3,2] expected")
+        kinds = None
+        if boundary is not None:
+            kinds = np.ascontiguousarray(boundary, dtype=np.int8)
+            if kinds.shape != (vid.shape[0], 3):
+                raise ValueError("boundary [n_tri, 3] expected")
         if stream is None:
             try:
                 import torch
@@ -56,14 +64,26 @@ class DGMesh:
         self.params = DGParams(int(k), float(nu), float(alpha), int(precision), float(cg_rtol), int(cg_maxit),
                                ctypes.c_void_p(int(stream)), int(precond))
         h = ctypes.c_void_p()
-        check(L.dg_mesh_create(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
-                               ctypes.byref(self.params), ctypes.byref(h)), "dg_mesh_create")
+        check(L.dg_mesh_create_ex(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p),
+                                  X.ctypes.data_as(ctypes.c_void_p),
+                                  None if kinds is None else kinds.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.byref(self.params), ctypes.byref(h)), "dg_mesh_create_ex")
         self._h = h
         info = self.info()
         self.n_tri, self.n_facet, self.k, self.n_lat = (int(v) for v in info[:4])
         self.n_class, self.n_stencil = int(info[4]), int(info[5])
         self.n_vel_dofs, self.n_lam_dofs = int(info[6]), int(info[7])
         self.nw = self.k * (self.k + 1) // 2
+        if inflow is not None:
+            self.set_inflow(inflow)
+
+    def set_inflow(self, vals):
+        """Inflow velocity at the k+1 equispaced points of every triangle edge, in the triangle's
+        counter-clockwise direction [n_tri, 3, k+1, 2] (dg_set_inflow; read on inflow edges)."""
+        v = np.ascontiguousarray(vals, dtype=np.float64)
+        if v.shape != (self.n_tri, 3, self.k + 1, 2):
+            raise ValueError("inflow values [n_tri, 3, k+1, 2] expected")
+        check(lib().dg_set_inflow(self._h, v.ctypes.data_as(ctypes.c_void_p)), "dg_set_inflow")
 
     def close(self):
         if getattr(self, "_h", None):

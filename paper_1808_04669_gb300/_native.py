@@ -13,7 +13,7 @@ DG_OK = 0
 STATUS = {0: "DG_OK", -1: "DG_ERR_INVALID_ARG", -2: "DG_ERR_MESH", -3: "DG_ERR_UNSUPPORTED", -4: "DG_ERR_CUDA",
           -5: "DG_ERR_NOT_CONVERGED", -6: "DG_ERR_NONFINITE", -7: "DG_ERR_OOM", -8: "DG_ERR_UNSTABLE"}
 
-EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
+EXPORTS = ["dg_mesh_create", "dg_mesh_create_ex", "dg_set_inflow", "dg_mesh_destroy", "dg_mesh_info", "dg_set_velocity", "dg_get_velocity",
            "dg_project_divfree", "dg_rk3_step", "dg_step", "dg_batch_create", "dg_batch_destroy", "dg_batch_rk3_step", "dg_batch_set_lanes", "dg_batch_get_tuning", "dg_get_pressure", "dg_eval_residual", "dg_set_coefficients", "dg_get_coefficients",
            "dg_set_viscosity", "dg_rk3_vjp", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
            "dg_set_energy_watchdog", "dg_set_tensor_cores", "dg_solver_history", "dg_test_multilevel_apply", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
@@ -39,6 +39,8 @@ def lib():
     P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
     sig = {
         "dg_mesh_create": (ctypes.c_int, [I64, P, P, ctypes.POINTER(DGParams), ctypes.POINTER(ctypes.c_void_p)]),
+        "dg_mesh_create_ex": (ctypes.c_int, [I64, P, P, P, ctypes.POINTER(DGParams), ctypes.POINTER(ctypes.c_void_p)]),
+        "dg_set_inflow": (ctypes.c_int, [P, P]),
         "dg_mesh_destroy": (ctypes.c_int, [P]),
         "dg_mesh_info": (ctypes.c_int, [P, P]),
         "dg_set_velocity": (ctypes.c_int, [P, P, ctypes.c_int]),

@@ -259,9 +259,10 @@ int capped(const dg_mesh* M, int nb) {
   return nb;
 }
 
-int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0) {
+int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0, bool homog = false) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
+  a.homog = homog ? 1 : 0;
   // lattice solver inside a step: warm start from the same stage of the last two steps.
   // lam_s is c_s dt times a smooth function of time, so with equal step sizes the linear
   // extrapolation 2 lam(n-1) - lam(n-2) is second-order accurate; one entry, or a changed
@@ -325,6 +326,11 @@ const char* dg_kernel_name(int i) { return (i >= 0 && i < KC_COUNT) ? kKernelNam
 
 int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, const dg_params* params,
                    dg_mesh** out) {
+  return dg_mesh_create_ex(n_tri, tri_vertex_ids, tri_coords, nullptr, params, out);
+}
+
+int dg_mesh_create_ex(int64_t n_tri, const int64_t* tri_vertex_ids, const double* tri_coords, const int8_t* edge_kind,
+                      const dg_params* params, dg_mesh** out) {
   g_err.clear();
   if (!out || !params || !tri_vertex_ids || !tri_coords) return fail(DG_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
@@ -343,7 +349,7 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
   M->p = p;
   M->stream = static_cast<cudaStream_t>(p.cuda_stream);
   std::string err;
-  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, p.k, p.alpha, M->hm, err);
+  int rc = dgdf::build_host_mesh(n_tri, tri_vertex_ids, tri_coords, p.k, p.alpha, M->hm, err, edge_kind);
   if (rc) {
     delete M;
     return fail(rc, err);
@@ -419,6 +425,16 @@ int dg_mesh_create(int64_t n_tri, const int64_t* tri_vertex_ids, const double* t
       (rc = upload(M, &d.st_binv, hm.stencil_binv)) || (rc = upload(M, &d.st_blk_f, to_float(hm.stencil_blocks))) ||
       (rc = upload(M, &d.st_binv_f, to_float(hm.stencil_binv))))
     return cleanup(rc);
+  // inflow / outflow boundaries (Sec. 2.5): facet kinds, and zero inflow data until
+  // dg_set_inflow; with outflow facets S has no kernel
+  d.has_kernel = hm.has_outflow ? 0 : 1;
+  if (hm.has_inflow || hm.has_outflow) {
+    if ((rc = upload(M, &d.facet_kind, hm.facet_kind))) return cleanup(rc);
+    if (hm.has_inflow) {
+      std::vector<double> uq(size_t(d.n_facet) * ref.nqf * 2, 0.0), dm(size_t(d.n_facet) * nl, 0.0);
+      if ((rc = upload(M, &d.inflow_q, uq)) || (rc = upload(M, &d.inflow_d, dm))) return cleanup(rc);
+    }
+  }
   if (d.elem_df && d.n_class <= dgdf::kDnClasses) {
     // normal derivatives of the basis at the facet points, per class
     const int nqf = ref.nqf, ns = hm.ns;
@@ -1365,6 +1381,8 @@ extern "C" {
 int dg_rk3_vjp(dg_mesh* M, double dt, int64_t nsteps, int64_t checkpoint_every, const double* ubar, double* u0bar,
                double* nubar, int on_device) {
   if (int rc = check_mesh(M)) return rc;
+  if (M->dm.facet_kind)
+    return fail(DG_ERR_UNSUPPORTED, "dg_rk3_vjp: meshes with inflow or outflow facets are not supported");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (nsteps < 1) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 1");
   if (!ubar || !u0bar) return fail(DG_ERR_INVALID_ARG, "NULL ubar or u0bar");
@@ -1456,7 +1474,7 @@ int dg_get_pressure(dg_mesh* M, double* p_elem, double* p_facet, int on_device) 
   a.up_df = M->dm.u_df;
   a.un_df = M->dm.u_df;
   if ((rc = launch(M, KC_PRESSURE, [&] { return dgdf::launch_stage(M->dm, a, M->stream); }))) return rc;
-  if ((rc = solve(M, 0.0))) return rc;
+  if ((rc = solve(M, 0.0, -1, 0.0, true))) return rc;   // L(u) alone: u.n = 0 on inflow facets
   if (M->dm.lam_is_df) {   // the pressure kernels read the multipliers in FP64
     if ((rc = launch(M, KC_PRESSURE, [&] {
            return dgdf::launch_to_double(M->dm.lam_df, M->dm.lat_vs, M->dm.lam, M->dm.nl, M->dm.n_facet, M->stream);
@@ -1554,6 +1572,23 @@ int dg_facet_solve_noalloc(int k, int64_t n_facet, const int32_t* facet_nbr, con
   if (st.flags & dgdf::kFlagBarrierTimeout) return fail(DG_ERR_CUDA, "solver grid barrier timed out");
   if (st.flags & dgdf::kFlagNonFinite) return fail(DG_ERR_NONFINITE, "non-finite residual in the facet solve");
   if (st.flags & dgdf::kFlagNotConverged) return fail(DG_ERR_NOT_CONVERGED, "facet solve reached maxit");
+  return DG_OK;
+}
+
+int dg_set_inflow(dg_mesh* M, const double* vals) {
+  if (int rc = check_mesh(M)) return rc;
+  if (!vals) return fail(DG_ERR_INVALID_ARG, "NULL vals");
+  if (!M->hm.has_inflow) return fail(DG_ERR_INVALID_ARG, "dg_set_inflow: the mesh has no inflow facets");
+  const size_t nv = size_t(M->dm.n_tri) * 3 * (M->hm.k + 1) * 2;
+  for (size_t i = 0; i < nv; ++i)
+    if (!std::isfinite(vals[i])) return fail(DG_ERR_INVALID_ARG, "dg_set_inflow: values must be finite");
+  std::vector<double> uq, dm;
+  dgdf::inflow_data(M->hm, vals, uq, dm);
+  CK(cudaMemcpyAsync(const_cast<double*>(M->dm.inflow_q), uq.data(), uq.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, M->stream));
+  CK(cudaMemcpyAsync(const_cast<double*>(M->dm.inflow_d), dm.data(), dm.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
   return DG_OK;
 }
 

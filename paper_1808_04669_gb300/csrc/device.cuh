@@ -14,6 +14,9 @@ enum : int {
   kFlagEnergyGrowth = 8,
 };
 
+// Kinds of boundary facets (Sec. 2.5, eq. (be)); interior facets read as walls.
+enum : int { kFacetWall = 0, kFacetInflow = 1, kFacetOutflow = 2 };
+
 // Per-class geometry record (doubles): Jinv[4] row-major (d xi_r / d x_d),
 // det = 2|T|, s = 1/sqrt(det), normal[3][2], flen[3], zint0 = integral of the
 // constant basis function, cinv0 = coefficient of the constant 1 in the first
@@ -132,6 +135,14 @@ struct DevMesh {
   double *ml_xc, *ml_bc;              // coarsest vectors
   double* ml_hist;                    // NULL, or [kMLHist][4] per-iteration history of the last
                                       // multilevel solve: relres, r.z, p.S p, alpha
+  // inflow / outflow boundaries (Sec. 2.5, eq. (be)); facet_kind NULL: every boundary facet
+  // is a wall
+  const int8_t* facet_kind;           // [n_facet] kFacetWall / kFacetInflow / kFacetOutflow
+  const double* inflow_q;             // [n_facet][nqf][2] u_in at the facet points, canonical order
+  const double* inflow_d;             // [n_facet][nl] moments of u_in.n (outward) against the
+                                      // multiplier basis, canonical orientation
+  int has_kernel;                     // 1: S is singular by the constant multiplier (no outflow
+                                      // facet); 0: outflow rows are identities and S is definite
   GridBar *bar;
   DevStats *stats;
   double *diag;                       // [8] diagnostics output
@@ -168,6 +179,7 @@ struct SolveArgs {
   int max_sweeps;
   int inner_maxit;     // iteration cap of each inner FP32 solve
   double floor_rtol;   // accepted relative residual once refinement stagnates at its rounding floor
+  int homog;           // 1: u.n = 0 on inflow facets (no data moments subtracted from g)
   // lattice solver, warm start from the same stage of earlier steps (overrides warm_scale):
   // lam0 = c1 hist1 + c2 hist2 (hist2 read only if c2 != 0); the kernel then moves hist1
   // into hist2, and the caller stores the new lam in hist1. Layout of lam.

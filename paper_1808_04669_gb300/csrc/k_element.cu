@@ -8,6 +8,54 @@
 
 namespace dgdf {
 
+// Convective term of eq. (7) on boundary facet e of triangle t when it is an inflow or
+// outflow facet (Sec. 2.5): the flux (u.n) u^up with u.n the average of the interior trace and
+// the exterior state, which is u_in on an inflow facet (stored at the facet points in the
+// canonical direction: our point q is point q there when the triangle runs the facet the
+// canonical way, else point NQF-1-q) and the interior trace on an outflow facet. The viscous
+// form has no boundary terms (natural conditions on every boundary facet).
+template <int K, typename R>
+__device__ void boundary_flux(const DevMesh& m, const SmemTables<K, R>& T, int t, int e, const R (&Ji)[4], R s,
+                              const R (&up)[Dims<K>::ND], R (&acc)[Dims<K>::ND]) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS;
+  const int f = m.tri_facet[size_t(t) * 3 + e];
+  const int kd = m.facet_kind[f];
+  if (kd == kFacetWall) return;
+  const bool canon = m.tri_orient[size_t(t) * 3 + e] > 0;
+  const double* geo = m.geo + size_t(m.tri_class[t]) * kGeo;
+  const R n0 = R(geo[G_NRM + 2 * e]), n1 = R(geo[G_NRM + 2 * e + 1]);
+  const R len = R(geo[G_FLEN + e]);
+#pragma unroll 1
+  for (int q = 0; q < D::NQF; ++q) {
+    R ui0 = 0, ui1 = 0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const R ph = T.fphi[e][q][j];
+      ui0 += ph * up[j];
+      ui1 += ph * up[NS + j];
+    }
+    ui0 *= s;
+    ui1 *= s;
+    R uo0 = ui0, uo1 = ui1;
+    if (kd == kFacetInflow) {
+      const double* uq = m.inflow_q + (size_t(f) * D::NQF + (canon ? q : D::NQF - 1 - q)) * 2;
+      uo0 = R(uq[0]);
+      uo1 = R(uq[1]);
+    }
+    const R vn = R(0.5) * ((ui0 + uo0) * n0 + (ui1 + uo1) * n1);
+    const R w0 = vn >= R(0) ? ui0 : uo0, w1 = vn >= R(0) ? ui1 : uo1;
+    const R w = T.fw[q] * len * s;
+    const R A0 = -w * vn * w0, A1 = -w * vn * w1;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const R ph = T.fphi[e][q][j];
+      acc[j] += A0 * ph;
+      acc[NS + j] += A1 * ph;
+    }
+  }
+}
+
 // acc[i] = L(u)(phi_i) on triangle t: -C_h(u;u,phi_i) - B_h(u,phi_i) (eq. (7), eq. (18)).
 // Volume: int (u x u - nu grad u) : grad phi. Facets: the upwind flux with u.n the
 // average of both traces, and the SIPG consistency, symmetry and penalty terms,
@@ -60,7 +108,12 @@ __device__ void element_residual(const DevMesh& m, const SmemTables<K, R>& T, in
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
     const int tn = m.tri_nbr[size_t(t) * 3 + e];
-    if (tn < 0) continue;   // a wall adds no term (u.n = 0 there; SIPG on interior facets only)
+    if (tn < 0) {
+      // a wall adds no term (u.n = 0 there; SIPG on interior facets only); inflow and outflow
+      // facets add the convective flux against the exterior state (Sec. 2.5)
+      if (m.facet_kind) boundary_flux<K, R>(m, T, t, e, Ji, s, up, acc);
+      continue;
+    }
     const int en = m.tri_nbr_loc[size_t(t) * 3 + e];
     const double* geon = m.geo + size_t(m.tri_class[tn]) * kGeo;
     const R sn = R(geon[G_S]);
@@ -423,7 +476,8 @@ __global__ void __launch_bounds__(128) k_pressure_lattice(DevMesh m, const doubl
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += 32) v += m.red[i];
     v = warp_sum(v);
-    if (threadIdx.x == 0) cshift = v / m.area_total;
+    // with outflow facets p = 0 there fixes the constant (eq. (be)): no shift
+    if (threadIdx.x == 0) cshift = m.has_kernel ? v / m.area_total : 0.0;
   }
   __syncthreads();
   const double c = cshift;
@@ -543,8 +597,13 @@ __global__ void __launch_bounds__(128) k_diagnostics(DevMesh m, const double* co
       dmax = fmax(dmax, fabs(g00 + g11));
     }
     for (int e = 0; e < 3; ++e) {
-      // on a wall the jump is u.n itself: the missing side counts as zero
+      // on a wall the jump is u.n itself: the missing side counts as zero; on an inflow facet
+      // it is (u - u_in).n; on an outflow facet u.n is free (Sec. 2.5)
       const int tnr = m.tri_nbr[size_t(t) * 3 + e];
+      const int fid = m.tri_facet[size_t(t) * 3 + e];
+      const int kd = (tnr < 0 && m.facet_kind) ? int(m.facet_kind[fid]) : int(kFacetWall);
+      if (kd == kFacetOutflow) continue;
+      const bool canon = m.tri_orient[size_t(t) * 3 + e] > 0;
       const int tn = tnr < 0 ? t : tnr;
       const int el = tnr < 0 ? e : m.tri_nbr_loc[size_t(t) * 3 + e];
       const double sn = tnr < 0 ? 0.0 : m.geo[size_t(m.tri_class[tn]) * kGeo + G_S];
@@ -561,7 +620,13 @@ __global__ void __launch_bounds__(128) k_diagnostics(DevMesh m, const double* co
           b0 += T.fphi[el][qn][j] * cn[j];
           b1 += T.fphi[el][qn][j] * cn[NS + j];
         }
-        jmax = fmax(jmax, fabs((s * a0 - sn * b0) * n0 + (s * a1 - sn * b1) * n1));
+        double x0 = sn * b0, x1 = sn * b1;
+        if (kd == kFacetInflow) {
+          const double* uq = m.inflow_q + (size_t(fid) * D::NQF + (canon ? q : qn)) * 2;
+          x0 = uq[0];
+          x1 = uq[1];
+        }
+        jmax = fmax(jmax, fabs((s * a0 - x0) * n0 + (s * a1 - x1) * n1));
       }
     }
   }

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
   for (int f = gtid; f < nF; f += gsz) {
     double gv[NL];
     assemble_g<NL>(m, f, gv);
+    boundary_g<NL>(m, f, a.homog, gv);
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;
@@ -255,8 +256,9 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
     gg[1] += gv[0];
   }
   if (!grid_reduce<2>(m, 4, gg, bar)) return;
-  const double c0 = gg[1] / double(nF);
-  const double inv_nf = 1.0 / double(nF);
+  // with outflow facets S is definite: no constant component to remove (inv_nf = 0)
+  const double inv_nf = m.has_kernel ? 1.0 / double(nF) : 0.0;
+  const double c0 = gg[1] * inv_nf;
   const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] * inv_nf, 0.0));
   const double stop = a.rtol * gnorm;
   int it = 0;

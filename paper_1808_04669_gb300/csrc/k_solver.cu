@@ -35,8 +35,9 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   // z = B r, rho = r.z, rr = r.r ; x = 0 if requested. The residual norm used for
   // stopping leaves out the component along the kernel of S (mode 0 = 1 on every
-  // facet), which CG cannot reduce and which rounding puts into r.
-  const double inv_nf = 1.0 / double(nF);
+  // facet), which CG cannot reduce and which rounding puts into r (none with outflow
+  // facets: S is then definite).
+  const double inv_nf = m.has_kernel ? 1.0 / double(nF) : 0.0;
   double red[3] = {0.0, 0.0, 0.0};
   for (int f = gtid; f < nF; f += gsz) {
     R r[NL], z[NL];
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
   for (int f = gtid; f < nF; f += gsz) {
     double gv[NL];
     assemble_g<NL>(m, f, gv);
+    boundary_g<NL>(m, f, a.homog, gv);
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;
@@ -154,9 +156,11 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
   }
   if (!grid_reduce<2>(m, 4, gg, bar)) return;
   // project g onto the range of S: remove its component along the constant multiplier
-  const double c0 = gg[1] / double(nF);
-  for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
-  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] / double(nF), 0.0));
+  const double inv_nf = m.has_kernel ? 1.0 / double(nF) : 0.0;
+  const double c0 = gg[1] * inv_nf;
+  if (c0 != 0.0)
+    for (int f = gtid; f < nF; f += gsz) m.g[size_t(f) * NL] -= c0;
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] * inv_nf, 0.0));
   const double stop = a.rtol * gnorm;
   int iters = 0, sweeps = 0;
   bool conv = false;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
         break;
       }
       if (!grid_reduce<2>(m, 6, rr, bar)) return;
-      rr[0] = fmax(rr[0] - rr[1] * rr[1] / double(nF), 0.0);
+      rr[0] = fmax(rr[0] - rr[1] * rr[1] * inv_nf, 0.0);
       const double prev = relres;
       relres = sqrt(rr[0]) / gnorm;
       if (!isfinite(rr[0])) {
@@ -397,6 +401,7 @@ cudaError_t solve_noalloc(int k, int n_facet, const int32_t* facet_nbr, const in
   DevMesh m{};
   m.k = k;
   m.nl = k + 1;
+  m.has_kernel = 1;   // the operator is taken singular by the constant multiplier
   m.n_facet = n_facet;
   m.facet_nbr = facet_nbr;
   m.facet_stencil = stencil;

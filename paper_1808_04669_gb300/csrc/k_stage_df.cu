@@ -35,6 +35,41 @@ __device__ __forceinline__ void load_df(const float2* __restrict__ p, dfl (&c)[N
   for (int i = 0; i < N; ++i) c[i] = to_dfl(p[i]);
 }
 
+// Inflow and outflow facets of triangle t (Sec. 2.5, eq. (be)), component c: the convective
+// flux of eq. (7) with u.n the average of the interior trace and the exterior state, which is
+// u_in on an inflow facet (stored at the facet points in the canonical direction: our point q
+// is its point q, or NQF-1-q when the triangle runs the facet the other way) and the interior
+// trace on an outflow facet, and the upwind value from the side u.n leaves. The viscous form
+// has no boundary terms. Whether a facet is taken depends on t alone, so both threads of a
+// pair take it together, and they exchange u.n through a shuffle over the pair only. ui(e, q)
+// returns the interior trace of component c; add(e, q, F) adds -w_q F phi_j(e, q) to acc.
+template <int NQF, typename Trace, typename Add>
+__device__ __forceinline__ void boundary_terms(const DevMesh& m, const float2* geo, int t, int c, dfl s, Trace ui,
+                                               Add add) {
+  const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1u);
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    if (__ldg(&m.tri_nbr[size_t(t) * 3 + e]) >= 0) continue;
+    const int fid = __ldg(&m.tri_facet[size_t(t) * 3 + e]);
+    const int kd = __ldg(&m.facet_kind[fid]);
+    if (kd == kFacetWall) continue;
+    const bool canon = __ldg(&m.tri_orient[size_t(t) * 3 + e]) > 0;
+    const dfl nc = to_dfl(geo[G_NRM + 2 * e + c]);
+    const dfl lens = to_dfl(geo[G_FLEN + e]) * s;
+#pragma unroll 1
+    for (int q = 0; q < NQF; ++q) {
+      const dfl u = ui(e, q);
+      const dfl uo =
+          kd == kFacetInflow ? dfl(__ldg(&m.inflow_q[(size_t(fid) * NQF + (canon ? q : NQF - 1 - q)) * 2 + c])) : u;
+      const dfl pc = (u + uo) * nc;
+      const dfl po(__shfl_xor_sync(pair_mask, pc.hi, 1), __shfl_xor_sync(pair_mask, pc.lo, 1));
+      const dfl vn = half(c ? po + pc : pc + po);
+      const dfl wup = vn >= dfl(0) ? u : uo;
+      add(e, q, lens * vn * wup);
+    }
+  }
+}
+
 // acc[j] += the component-c part of L(u')(phi_j): -C_h(u;u,phi) - B_h(u,phi) of
 // eq. (7) and eq. (18). Volume: int (u_c u - nu grad u_c) . grad phi_j. Facets: the
 // upwind flux (u.n) u_c^up with u.n the average of both traces, and the SIPG
@@ -81,8 +116,9 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
   // ---- facet terms
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
-    // A wall (no neighbour) adds no term. It is evaluated against its own trace with weight
-    // zero, so that both threads of every pair still reach each shuffle.
+    // A boundary facet (no neighbour) adds no term here. It is evaluated against its own trace
+    // with weight zero, so that both threads of every pair still reach each shuffle; inflow and
+    // outflow facets add their convective flux in boundary_component.
     const int tnr = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
     const bool wall = tnr < 0;
     const int tn = wall ? t : tnr;
@@ -134,6 +170,20 @@ __device__ __forceinline__ void residual_component(const DevMesh& m, const SmemT
       }
     }
   }
+  if (m.facet_kind)
+    boundary_terms<D::NQF>(
+        m, geo, t, c, s,
+        [&](int e, int q) {
+          dacc V = dacc_zero();
+#pragma unroll
+          for (int j = 0; j < NS; ++j) mad(V, T.fphi[e][q][j], up[j]);
+          return s * val(V);
+        },
+        [&](int e, int q, dfl F) {
+          const dfl A = -(T.fw[q] * F);
+#pragma unroll
+          for (int j = 0; j < NS; ++j) mad(acc[j], A, T.fphi[e][q][j]);
+        });
 }
 
 // Stage kernel, mixed form (all modes, see StageMode): reads the double-float
@@ -278,7 +328,7 @@ __device__ __forceinline__ void residual_pairs(const DevMesh& m, const PairTable
   // ---- facet terms
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
-    // a wall: own trace, weight zero (see residual_component)
+    // a boundary facet: own trace, weight zero (see residual_component)
     const int tnr = __ldg(&m.tri_nbr[size_t(t) * 3 + e]);
     const bool wall = tnr < 0;
     const int tn = wall ? t : tnr;
@@ -320,6 +370,20 @@ __device__ __forceinline__ void residual_pairs(const DevMesh& m, const PairTable
       }
     }
   }
+  if (m.facet_kind)
+    boundary_terms<D::NQF>(
+        m, geo, t, c, s,
+        [&](int e, int q) {
+          dacc2 V = dacc2_zero();
+#pragma unroll
+          for (int jp = 0; jp < NS2; ++jp) mad2(V, pair(T.fphi[e][q][jp]), up[jp]);
+          return s * val_sum(V);
+        },
+        [&](int e, int q, dfl F) {
+          const dfl2 A = splat(-(to_dfl(T.fw[q]) * F));
+#pragma unroll
+          for (int jp = 0; jp < NS2; ++jp) mad2(acc[jp], A, pair(T.fphi[e][q][jp]));
+        });
 }
 
 // Stage kernel, paired form: the modes, inputs and outputs of k_stage_df; the class

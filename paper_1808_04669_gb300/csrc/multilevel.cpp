@@ -223,12 +223,18 @@ CsrHost sa_prolongator(const CsrHost& A, const Vec& nn, Vec& nn_next) {
     }
     srp[i + 1] = int32_t(sci.size());
   }
+  // isolated rows (no nonzero off the diagonal: the identity rows of outflow facets) join no
+  // aggregate; their rows of P are empty, the smoother solves them exactly
+  std::vector<char> isolated(n, 1);
+  for (int i = 0; i < n; ++i)
+    for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (A.ci[p] != i && A.v[p] != 0.0) isolated[i] = 0;
   // aggregation: a node whose strong neighbours are all free starts an aggregate with them;
   // then every free node joins the aggregate of a strong neighbour, or starts its own
   std::vector<int32_t> agg(n, -1);
   int na = 0;
   for (int i = 0; i < n; ++i) {
-    if (agg[i] >= 0) continue;
+    if (agg[i] >= 0 || isolated[i]) continue;
     bool free = true;
     for (int p = srp[i]; p < srp[i + 1] && free; ++p) free = agg[sci[p]] < 0;
     if (!free) continue;
@@ -237,7 +243,7 @@ CsrHost sa_prolongator(const CsrHost& A, const Vec& nn, Vec& nn_next) {
     ++na;
   }
   for (int i = 0; i < n; ++i) {
-    if (agg[i] >= 0) continue;
+    if (agg[i] >= 0 || isolated[i]) continue;
     for (int p = srp[i]; p < srp[i + 1]; ++p)
       if (agg[sci[p]] >= 0) {
         agg[i] = agg[sci[p]];
@@ -247,20 +253,20 @@ CsrHost sa_prolongator(const CsrHost& A, const Vec& nn, Vec& nn_next) {
   }
   // tentative prolongator: the near-null vector restricted to each aggregate, normalised
   nn_next.assign(na, 0.0);
-  for (int i = 0; i < n; ++i) nn_next[agg[i]] += nn[i] * nn[i];
+  for (int i = 0; i < n; ++i)
+    if (agg[i] >= 0) nn_next[agg[i]] += nn[i] * nn[i];
   for (double& v : nn_next) v = std::sqrt(v);
   CsrHost P0;
   P0.n_rows = n;
   P0.n_cols = na;
-  P0.rp.resize(n + 1);
-  P0.ci.resize(n);
-  P0.v.resize(n);
+  P0.rp.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    P0.rp[i] = i;
-    P0.ci[i] = agg[i];
-    P0.v[i] = nn_next[agg[i]] > 0.0 ? nn[i] / nn_next[agg[i]] : 0.0;
+    if (agg[i] >= 0) {
+      P0.ci.push_back(agg[i]);
+      P0.v.push_back(nn_next[agg[i]] > 0.0 ? nn[i] / nn_next[agg[i]] : 0.0);
+    }
+    P0.rp[i + 1] = int32_t(P0.ci.size());
   }
-  P0.rp[n] = n;
   // smoothed prolongator P = (I - omega D^-1 A) P0, omega = 4 / (3 rho(D^-1 A))
   auto aA = [&](const double* x, double* y) { csr_apply(A, x, y); };
   auto aD = [&](const double* x, double* y) {
@@ -274,10 +280,12 @@ CsrHost sa_prolongator(const CsrHost& A, const Vec& nn, Vec& nn_next) {
   P.n_cols = na;
   P.rp.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    // row i of P0 (one entry) minus omega / d_i times row i of A P0
+    // row i of P0 (one entry, none for an isolated row) minus omega / d_i times row i of A P0
     const size_t start = P.ci.size();
-    P.ci.push_back(P0.ci[i]);
-    P.v.push_back(P0.v[i]);
+    for (int p = P0.rp[i]; p < P0.rp[i + 1]; ++p) {
+      P.ci.push_back(P0.ci[p]);
+      P.v.push_back(P0.v[p]);
+    }
     for (int p = AP.rp[i]; p < AP.rp[i + 1]; ++p) {
       const double v = -omega / d[i] * AP.v[p];
       size_t q = start;

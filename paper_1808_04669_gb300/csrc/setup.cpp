@@ -707,11 +707,29 @@ void class_ops(const RefTables& ref, const double* x, ClassOps& co) {
 }  // namespace
 
 int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha, HostMesh& hm,
-                    std::string& err) {
+                    std::string& err, const int8_t* edge_kind) {
   int rc = build_reference(k, hm.ref, err);
   if (rc) return rc;
   rc = build_topology(n_tri, vid, X, hm.topo, err);
   if (rc) return rc;
+  // kinds of the boundary facets (Sec. 2.5, eq. (be)): wall, inflow or outflow, from the kind of
+  // the single triangle edge of each boundary facet; interior facets are kWall (not used)
+  hm.facet_kind.assign(hm.topo.n_facet, kWall);
+  hm.has_outflow = false;
+  hm.has_inflow = false;
+  if (edge_kind) {
+    for (int64_t f = 0; f < hm.topo.n_facet; ++f) {
+      if (hm.topo.facet_tri[f * 2 + 1] >= 0) continue;
+      const int8_t kd = edge_kind[size_t(hm.topo.facet_tri[f * 2]) * 3 + hm.topo.facet_loc[f * 2]];
+      if (kd < kWall || kd > kOutflow) {
+        err = "edge kinds are 0 (wall), 1 (inflow) or 2 (outflow)";
+        return DG_ERR_INVALID_ARG;
+      }
+      hm.facet_kind[f] = kd;
+      hm.has_outflow = hm.has_outflow || kd == kOutflow;
+      hm.has_inflow = hm.has_inflow || kd == kInflow;
+    }
+  }
   const RefTables& ref = hm.ref;
   hm.k = k;
   hm.ns = ref.ns;
@@ -805,6 +823,15 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
       hm.facet_nbr[f * 4 + si * 2 + 0] = T.tri_facet[size_t(t) * 3 + (e + 1) % 3];
       hm.facet_nbr[f * 4 + si * 2 + 1] = T.tri_facet[size_t(t) * 3 + (e + 2) % 3];
     }
+    // outflow (p = 0, eq. (be)): the facet's multipliers are zero, so its row is the identity
+    // and the other rows do not couple to it
+    const bool own_out = hm.facet_kind[f] == kOutflow;
+    key.push_back(own_out ? 1 : 0);
+    bool slot_out[4];
+    for (int b = 0; b < 4; ++b) {
+      slot_out[b] = hm.facet_kind[hm.facet_nbr[f * 4 + b]] == kOutflow && hm.facet_nbr[f * 4 + b] != f;
+      key.push_back(slot_out[b] ? 1 : 0);
+    }
     auto it = st.find(key);
     if (it == st.end()) {
       int32_t id = int32_t(st.size());
@@ -826,6 +853,12 @@ int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, d
                   sgn(e, m) * co.S[size_t(e * nl + m) * L3 + ee * nl + mm] * sgn(ee, mm);
         }
       }
+      if (own_out) {
+        std::fill(blk.begin(), blk.end(), 0.0);
+        for (int m = 0; m < nl; ++m) blk[size_t(m) * nl + m] = 1.0;
+      }
+      for (int b = 0; b < 4; ++b)
+        if (slot_out[b]) std::fill(blk.begin() + size_t(b + 1) * nl * nl, blk.begin() + size_t(b + 2) * nl * nl, 0.0);
       std::vector<double> inv(blk.begin(), blk.begin() + nl * nl);
       if (!invert(inv, nl)) {
         err = "singular facet block";
@@ -1145,6 +1178,7 @@ void renumber_facets_lattice(HostMesh& hm, Lattice& L) {
   for (auto& x : hm.facet_nbr) x = nw[x];
   permute(hm.facet_stencil, 1);
   permute(hm.facet_side0, 1);
+  permute(hm.facet_kind, 1);
   for (auto& x : T.tri_facet) x = nw[x];
   for (int64_t n = 0; n < nF; ++n) L.facet_of[n] = int32_t(n);
   hm.facet_ext = old_of_new;
@@ -1153,6 +1187,49 @@ void renumber_facets_lattice(HostMesh& hm, Lattice& L) {
 }  // namespace dgdf
 
 namespace dgdf {
+void inflow_data(const HostMesh& hm, const double* vals, std::vector<double>& uq, std::vector<double>& dmom) {
+  const Topology& T = hm.topo;
+  const RefTables& ref = hm.ref;
+  const int k = hm.k, nl = hm.nl, nqf = ref.nqf;
+  uq.assign(size_t(T.n_facet) * nqf * 2, 0.0);
+  dmom.assign(size_t(T.n_facet) * nl, 0.0);
+  // Lagrange basis of the k+1 equispaced edge points at the facet rule's points
+  std::vector<double> Lq(size_t(k + 1) * nqf);
+  for (int i = 0; i <= k; ++i)
+    for (int q = 0; q < nqf; ++q) {
+      double v = 1.0;
+      for (int j = 0; j <= k; ++j)
+        if (j != i) v *= (ref.ft[q] - double(j) / k) / (double(i - j) / k);
+      Lq[size_t(i) * nqf + q] = v;
+    }
+  std::vector<double> ue(size_t(nqf) * 2);
+  for (int64_t f = 0; f < T.n_facet; ++f) {
+    if (hm.facet_kind[f] != kInflow) continue;
+    const int64_t t = T.facet_tri[f * 2];
+    const int e = T.facet_loc[f * 2];
+    const bool canon = T.tri_orient[size_t(t) * 3 + e] > 0;
+    const double* v = vals + (size_t(t) * 3 + e) * (k + 1) * 2;
+    for (int q = 0; q < nqf; ++q)
+      for (int c = 0; c < 2; ++c) {
+        double a = 0.0;
+        for (int i = 0; i <= k; ++i) a += Lq[size_t(i) * nqf + q] * v[i * 2 + c];
+        ue[q * 2 + c] = a;
+      }
+    const ClassOps& co = hm.classes[hm.tri_class[t]];
+    for (int q = 0; q < nqf; ++q) {
+      // canonical point q is the triangle's point q, or nqf-1-q when it runs the facet backwards
+      const int qe = canon ? q : nqf - 1 - q;
+      double* o = &uq[(size_t(f) * nqf + q) * 2];
+      o[0] = ue[qe * 2];
+      o[1] = ue[qe * 2 + 1];
+      const double un = o[0] * co.normal[e][0] + o[1] * co.normal[e][1];
+      const double w = ref.fw[q] * co.flen[e];
+      for (int m = 0; m < nl; ++m)
+        dmom[size_t(f) * nl + m] += w * std::sqrt(2.0 * m + 1.0) * legendre(m, 2.0 * ref.ft[q] - 1.0) * un;
+    }
+  }
+}
+
 void symmetric_eigen(const std::vector<double>& A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
   sym_eig(A, n, evals, evecs);
 }

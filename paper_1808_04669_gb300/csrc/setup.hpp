@@ -71,8 +71,13 @@ struct Lattice {
   std::vector<double> twiddle;     // [N][2] exp(-2 pi i t / N)
 };
 
+// kinds of boundary facets (Sec. 2.5, eq. (be)); interior facets are kWall
+enum : int8_t { kWall = 0, kInflow = 1, kOutflow = 2 };
+
 struct HostMesh {
   int k = 0, ns = 0, nd = 0, nw = 0, nl = 0;
+  std::vector<int8_t> facet_kind;   // [n_facet]
+  bool has_inflow = false, has_outflow = false;
   double alpha = 2.0;
   Topology topo;
   RefTables ref;
@@ -99,8 +104,15 @@ int build_topology(int64_t n_tri, const int64_t* vid, const double* X, Topology&
 constexpr int kVolumePoints(int k) { return k == 1 ? 3 : (k == 2 ? 7 : 16); }
 
 int build_reference(int k, RefTables& ref, std::string& err);
+// Inflow data of Sec. 2.5 from u_in at the k+1 equispaced points of every triangle edge
+// (vals [n_tri][3][k+1][2], the triangle's counter-clockwise direction; read on inflow edges):
+// uq [n_facet][nqf][2] = u_in at the facet rule's points in canonical order, dmom [n_facet][nl]
+// = int_F mu_m (u_in.n) ds with the multiplier basis mu_m in the canonical parameter and n the
+// outward normal. Zero on every other facet.
+void inflow_data(const HostMesh& hm, const double* vals, std::vector<double>& uq, std::vector<double>& dmom);
+// edge_kind: kind of every triangle edge [n_tri][3] (read on boundary edges) or NULL (walls)
 int build_host_mesh(int64_t n_tri, const int64_t* vid, const double* X, int k, double alpha,
-                    HostMesh& hm, std::string& err);
+                    HostMesh& hm, std::string& err, const int8_t* edge_kind = nullptr);
 // Detects the split-square lattice structure and computes the inverse Fourier symbol.
 // eig_half: the eigen form of the half spectrum (seig) instead of the full inverse (sinv).
 void build_lattice(const HostMesh& hm, const double* X, Lattice& lat, bool eig_half = false);

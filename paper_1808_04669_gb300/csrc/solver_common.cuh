@@ -154,6 +154,22 @@ __device__ __forceinline__ void assemble_g_df(const DevMesh& m, int f, dfl (&gv)
   }
 }
 
+// g on the boundary facets of Sec. 2.5, eq. (be): zero on outflow facets (their multipliers
+// are zero: identity rows of S), and minus the data moments <mu_m, u_in.n> on inflow facets,
+// so that the solution takes u.n = u_in.n there (homog: u.n = 0 instead).
+template <int NL>
+__device__ __forceinline__ void boundary_g(const DevMesh& m, int f, int homog, double (&gv)[NL]) {
+  if (!m.facet_kind) return;
+  const int kd = __ldg(&m.facet_kind[f]);
+  if (kd == kFacetOutflow) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) gv[j] = 0.0;
+  } else if (kd == kFacetInflow && !homog) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) gv[j] -= __ldg(&m.inflow_d[size_t(f) * NL + j]);
+  }
+}
+
 template <int NL>
 __device__ __forceinline__ void facet_nbrs(const DevMesh& m, int f, int (&nb)[5]) {
   nb[0] = f;
