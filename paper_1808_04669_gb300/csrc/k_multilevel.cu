@@ -27,6 +27,36 @@ namespace {
 
 constexpr int kMLThreads = 256;
 
+// Rows of a level in groups of G lanes of one warp, G = the largest power of two <= 32 with
+// G n <= the grid's threads (one round of the grid covers every row whenever n allows): the
+// lanes of a group split a row's sum (dot(i, lane, G), a strided partial sum) and add their
+// partials by shuffles, then lane 0 of the group calls f(i, sum). Short coarse levels thus keep
+// the grid busy instead of one thread walking a long row load by load. The loop bound and the
+// shuffles are the same in every lane of a warp.
+template <typename Dot, typename F>
+__device__ __forceinline__ void rows_grouped(int n, Dot&& dot, F&& f) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  int G = 1;
+  while (G < 32 && 2 * G * n <= gsz) G *= 2;
+  const int lane = threadIdx.x & (G - 1), grp = gtid / G, ngrp = gsz / G;
+  for (int i0 = 0; i0 < n; i0 += ngrp) {
+    const int i = i0 + grp;
+    double s = i < n ? dot(i, lane, G) : 0.0;
+    for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (i < n && lane == 0) f(i, s);
+  }
+}
+
+// Strided partial sum of a CSR row: sum over p = rp[i] + lane, + G, ... of v[p] x[ci[p]]
+__device__ __forceinline__ double csr_part(const int32_t* rp, const int32_t* ci, const double* v, const double* x,
+                                           int i, int lane, int G) {
+  double s = 0.0;
+  const int p1 = __ldg(&rp[i + 1]);
+#pragma unroll 4
+  for (int p = __ldg(&rp[i]) + lane; p < p1; p += G) s += __ldg(&v[p]) * __ldcg(&x[__ldg(&ci[p])]);
+  return s;
+}
+
 // y = (A x)_i for row i of level L (bs <= NL values; y[0] only on CSR levels)
 template <int NL>
 __device__ __forceinline__ void ml_row_apply(const DevMesh& m, const MLLevelDev& L, int i, const double* x,
@@ -112,51 +142,67 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
     const MLLevelDev& L = lv[l];
     const int bs = L.bs;
     // [A] second Chebyshev step from zero
-    for (int i = gtid; i < L.n; i += gsz) {
-      double y[NL], res[NL], t[NL];
-      ml_row_apply<NL>(m, L, i, L.d, y);
+    if (L.stencil) {
+      for (int i = gtid; i < L.n; i += gsz) {
+        double y[NL], res[NL], t[NL];
+        ml_row_apply<NL>(m, L, i, L.d, y);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
-      ml_row_binv<NL>(m, L, i, res, t);
+        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
+        ml_row_binv<NL>(m, L, i, res, t);
 #pragma unroll
-      for (int j = 0; j < NL; ++j)
-        if (j < bs) {
-          const double d = __ldcg(&L.d[size_t(i) * bs + j]);
-          L.x[size_t(i) * bs + j] = d + L.c1 * d + L.c2 * t[j];
-        }
+        for (int j = 0; j < NL; ++j)
+          if (j < bs) {
+            const double d = __ldcg(&L.d[size_t(i) * bs + j]);
+            L.x[size_t(i) * bs + j] = d + L.c1 * d + L.c2 * t[j];
+          }
+      }
+    } else {
+      rows_grouped(
+          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
+          [&](int i, double y) {
+            const double t = __ldg(&L.binv[i]) * (__ldcg(&L.b[i]) - y);
+            const double d = __ldcg(&L.d[i]);
+            L.x[i] = d + L.c1 * d + L.c2 * t;
+          });
     }
     if (!grid_sync(bar, m.stats)) return false;
     // [B] residual, injected restriction
     const bool last = l + 1 == nlev;
-    for (int i = gtid; i < L.n; i += gsz) {
-      double y[NL];
-      ml_row_apply<NL>(m, L, i, L.x, y);
+    if (L.stencil) {
+      for (int i = gtid; i < L.n; i += gsz) {
+        double y[NL];
+        ml_row_apply<NL>(m, L, i, L.x, y);
 #pragma unroll
-      for (int j = 0; j < NL; ++j)
-        if (j < bs) {
-          const double r = __ldcg(&L.b[size_t(i) * bs + j]) - y[j];
-          L.r[size_t(i) * bs + j] = r;
-          if (L.inject && j < L.bs_next) {
-            if (last) m.ml_bc[i] = r;   // bs_next = 1 into the coarsest level
-            else lv[l + 1].b[size_t(i) * L.bs_next + j] = r;
+        for (int j = 0; j < NL; ++j)
+          if (j < bs) {
+            const double r = __ldcg(&L.b[size_t(i) * bs + j]) - y[j];
+            L.r[size_t(i) * bs + j] = r;
+            if (L.inject && j < L.bs_next) {
+              if (last) m.ml_bc[i] = r;   // bs_next = 1 into the coarsest level
+              else lv[l + 1].b[size_t(i) * L.bs_next + j] = r;
+            }
           }
-        }
-      if (L.inject && !last) ml_row_first_step<NL>(m, lv[l + 1], i);
+        if (L.inject && !last) ml_row_first_step<NL>(m, lv[l + 1], i);
+      }
+    } else {
+      // CSR levels hold one value per row and transfer through R (phase [C])
+      rows_grouped(
+          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
+          [&](int i, double y) { L.r[i] = __ldcg(&L.b[i]) - y; });
     }
     if (!grid_sync(bar, m.stats)) return false;
     if (!L.inject) {
       // [C] CSR restriction b_next = R r
-      for (int j = gtid; j < L.n_next; j += gsz) {
-        double v = 0.0;
-        const int p1 = __ldg(&L.r_rp[j + 1]);
-        for (int p = __ldg(&L.r_rp[j]); p < p1; ++p) v += __ldg(&L.r_v[p]) * __ldcg(&L.r[__ldg(&L.r_ci[p])]);
-        if (last) {
-          m.ml_bc[j] = v;
-        } else {
-          lv[l + 1].b[j] = v;
-          ml_row_first_step<NL>(m, lv[l + 1], j);
-        }
-      }
+      rows_grouped(
+          L.n_next, [&](int j, int lane, int G) { return csr_part(L.r_rp, L.r_ci, L.r_v, L.r, j, lane, G); },
+          [&](int j, double v) {
+            if (last) {
+              m.ml_bc[j] = v;
+            } else {
+              lv[l + 1].b[j] = v;
+              ml_row_first_step<NL>(m, lv[l + 1], j);
+            }
+          });
       if (!grid_sync(bar, m.stats)) return false;
     }
   }
@@ -164,13 +210,18 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
   {
     const int nc = m.ml_nc;
     const MLLevelDev& Lz = lv[nlev - 1];
-    for (int i = gtid; i < nc; i += gsz) {
-      double v = 0.0;
-      const double* row = m.ml_cpinv + size_t(i) * nc;
-      for (int j = 0; j < nc; ++j) v += __ldg(&row[j]) * __ldcg(&m.ml_bc[j]);
-      m.ml_xc[i] = v;
-      if (Lz.inject) Lz.x[size_t(i) * Lz.bs] += v;
-    }
+    rows_grouped(
+        nc,
+        [&](int i, int lane, int G) {
+          double v = 0.0;
+          const double* row = m.ml_cpinv + size_t(i) * nc;
+          for (int j = lane; j < nc; j += G) v += __ldg(&row[j]) * __ldcg(&m.ml_bc[j]);
+          return v;
+        },
+        [&](int i, double v) {
+          m.ml_xc[i] = v;
+          if (Lz.inject) Lz.x[size_t(i) * Lz.bs] += v;
+        });
     if (!grid_sync(bar, m.stats)) return false;
   }
   for (int l = nlev - 1; l >= 0; --l) {
@@ -179,31 +230,50 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
     if (!L.inject) {
       // [U] CSR prolongation x += P x_next
       const double* xn = (l + 1 == nlev) ? m.ml_xc : lv[l + 1].x;
-      for (int i = gtid; i < L.n; i += gsz) {
-        double v = 0.0;
-        const int p1 = __ldg(&L.p_rp[i + 1]);
-        for (int p = __ldg(&L.p_rp[i]); p < p1; ++p) v += __ldg(&L.p_v[p]) * __ldcg(&xn[__ldg(&L.p_ci[p])]);
-        L.x[i] += v;
-      }
+      rows_grouped(
+          L.n, [&](int i, int lane, int G) { return csr_part(L.p_rp, L.p_ci, L.p_v, xn, i, lane, G); },
+          [&](int i, double v) { L.x[i] += v; });
       if (!grid_sync(bar, m.stats)) return false;
     }
     // [Q] r = b - A x, d = c0 B r
-    for (int i = gtid; i < L.n; i += gsz) {
-      double y[NL], res[NL], t[NL];
-      ml_row_apply<NL>(m, L, i, L.x, y);
+    if (L.stencil) {
+      for (int i = gtid; i < L.n; i += gsz) {
+        double y[NL], res[NL], t[NL];
+        ml_row_apply<NL>(m, L, i, L.x, y);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
-      ml_row_binv<NL>(m, L, i, res, t);
+        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
+        ml_row_binv<NL>(m, L, i, res, t);
 #pragma unroll
-      for (int j = 0; j < NL; ++j)
-        if (j < bs) {
-          L.r[size_t(i) * bs + j] = res[j];
-          L.d[size_t(i) * bs + j] = L.c0 * t[j];
-        }
+        for (int j = 0; j < NL; ++j)
+          if (j < bs) {
+            L.r[size_t(i) * bs + j] = res[j];
+            L.d[size_t(i) * bs + j] = L.c0 * t[j];
+          }
+      }
+    } else {
+      rows_grouped(
+          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
+          [&](int i, double y) {
+            const double res = __ldcg(&L.b[i]) - y;
+            L.r[i] = res;
+            L.d[i] = L.c0 * (__ldg(&L.binv[i]) * res);
+          });
     }
     if (!grid_sync(bar, m.stats)) return false;
     // [R] x += d + c1 d + c2 B (r - A d); inject into the finer level (same facet rows)
     const MLLevelDev* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
+    if (!L.stencil) {
+      // a CSR level (never level 0, never below an injecting level)
+      rows_grouped(
+          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
+          [&](int i, double y) {
+            const double t = __ldg(&L.binv[i]) * (__ldcg(&L.r[i]) - y);
+            const double d = __ldcg(&L.d[i]);
+            L.x[i] = __ldcg(&L.x[i]) + d + L.c1 * d + L.c2 * t;
+          });
+      if (!grid_sync(bar, m.stats)) return false;
+      continue;
+    }
     for (int i = gtid; i < L.n; i += gsz) {
       double y[NL], res[NL], t[NL];
       ml_row_apply<NL>(m, L, i, L.d, y);
