@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dgdf.h"
@@ -604,42 +605,64 @@ int dg_mesh_create_ex(int64_t n_tri, const int64_t* tri_vertex_ids, const double
     dgdf::MLHost mlh;
     std::string merr;
     if ((rc = dgdf::build_multilevel(M->hm, mlh, merr))) return cleanup(fail(rc, merr));
-    std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
-    for (size_t l = 0; l < mlh.lv.size(); ++l) {
-      const dgdf::MLHostLevel& H = mlh.lv[l];
-      dgdf::MLLevelDev& L = lv[l];
-      L.stencil = H.stencil ? 1 : 0;
-      L.bs = H.bs;
-      L.n = H.n;
-      L.inject = H.inject ? 1 : 0;
-      L.n_next = H.n_next;
-      L.bs_next = H.bs_next;
-      L.c0 = H.cheb[0];
-      L.c1 = H.cheb[1];
-      L.c2 = H.cheb[2];
-      if ((rc = upload(M, &L.binv, H.binv))) return cleanup(rc);
-      if (!H.stencil && ((rc = upload(M, &L.a_rp, H.A.rp)) || (rc = upload(M, &L.a_ci, H.A.ci)) ||
-                         (rc = upload(M, &L.a_v, H.A.v))))
-        return cleanup(rc);
-      if (!H.inject && ((rc = upload(M, &L.p_rp, H.P.rp)) || (rc = upload(M, &L.p_ci, H.P.ci)) ||
-                        (rc = upload(M, &L.p_v, H.P.v)) || (rc = upload(M, &L.r_rp, H.R.rp)) ||
-                        (rc = upload(M, &L.r_ci, H.R.ci)) || (rc = upload(M, &L.r_v, H.R.v))))
-        return cleanup(rc);
-      const size_t nv = size_t(H.n) * H.bs;
-      if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
-        L.b = d.r;
-        L.x = d.z;
-      } else if ((rc = dalloc(M, &L.b, nv)) || (rc = dalloc(M, &L.x, nv))) {
-        return cleanup(rc);
+    // the V-cycle's precision: FP32 in the mixed form (a preconditioner needs no more; the PCG
+    // vectors and S stay FP64), FP64 in the FP64 form
+    const bool ml32 = p.precision == DG_PRECISION_MIXED;
+    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    auto fill = [&](auto& lv, auto conv, auto* cpinv_out, auto** xc, auto** bc) -> int {
+      for (size_t l = 0; l < mlh.lv.size(); ++l) {
+        const dgdf::MLHostLevel& H = mlh.lv[l];
+        auto& L = lv[l];
+        using T = std::remove_pointer_t<decltype(L.x)>;
+        L.stencil = H.stencil ? 1 : 0;
+        L.bs = H.bs;
+        L.n = H.n;
+        L.inject = H.inject ? 1 : 0;
+        L.n_next = H.n_next;
+        L.bs_next = H.bs_next;
+        L.c0 = T(H.cheb[0]);
+        L.c1 = T(H.cheb[1]);
+        L.c2 = T(H.cheb[2]);
+        int rc2 = 0;
+        if ((rc2 = upload(M, &L.binv, conv(H.binv)))) return rc2;
+        if (!H.stencil && ((rc2 = upload(M, &L.a_rp, H.A.rp)) || (rc2 = upload(M, &L.a_ci, H.A.ci)) ||
+                           (rc2 = upload(M, &L.a_v, conv(H.A.v)))))
+          return rc2;
+        if (!H.inject && ((rc2 = upload(M, &L.p_rp, H.P.rp)) || (rc2 = upload(M, &L.p_ci, H.P.ci)) ||
+                          (rc2 = upload(M, &L.p_v, conv(H.P.v))) || (rc2 = upload(M, &L.r_rp, H.R.rp)) ||
+                          (rc2 = upload(M, &L.r_ci, H.R.ci)) || (rc2 = upload(M, &L.r_v, conv(H.R.v)))))
+          return rc2;
+        const size_t nv = size_t(H.n) * H.bs;
+        if constexpr (std::is_same<T, double>::value) {
+          if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
+            L.b = d.r;
+            L.x = d.z;
+          }
+        }
+        if (!L.b && ((rc2 = dalloc(M, &L.b, nv)) || (rc2 = dalloc(M, &L.x, nv)))) return rc2;
+        if ((rc2 = dalloc(M, &L.r, nv)) || (rc2 = dalloc(M, &L.d, nv))) return rc2;
       }
-      if ((rc = dalloc(M, &L.r, nv)) || (rc = dalloc(M, &L.d, nv))) return cleanup(rc);
+      int rc2 = 0;
+      if ((rc2 = upload(M, cpinv_out, conv(mlh.cpinv))) || (rc2 = dalloc(M, xc, size_t(mlh.nc))) ||
+          (rc2 = dalloc(M, bc, size_t(mlh.nc))))
+        return rc2;
+      return 0;
+    };
+    if (ml32) {
+      std::vector<dgdf::MLLevelT<float>> lv(mlh.lv.size());
+      if ((rc = fill(lv, f32, &d.ml_cpinv_f, &d.ml_xc_f, &d.ml_bc_f))) return cleanup(rc);
+      const dgdf::MLLevelT<float>* lvd = nullptr;
+      if ((rc = upload(M, &lvd, lv))) return cleanup(rc);
+      d.ml_lv_f = lvd;
+    } else {
+      std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
+      if ((rc = fill(lv, [](const std::vector<double>& v) { return v; }, &d.ml_cpinv, &d.ml_xc, &d.ml_bc)))
+        return cleanup(rc);
+      const dgdf::MLLevelDev* lvd = nullptr;
+      if ((rc = upload(M, &lvd, lv))) return cleanup(rc);
+      d.ml_lv = lvd;
     }
-    const dgdf::MLLevelDev* lvd = nullptr;
-    if ((rc = upload(M, &lvd, lv)) || (rc = upload(M, &d.ml_cpinv, mlh.cpinv)) ||
-        (rc = dalloc(M, &d.ml_xc, size_t(mlh.nc))) || (rc = dalloc(M, &d.ml_bc, size_t(mlh.nc))))
-      return cleanup(rc);
-    d.ml_lv = lvd;
-    d.ml_nlev = int(lv.size());
+    d.ml_nlev = int(mlh.lv.size());
     d.ml_nc = mlh.nc;
     M->use_ml = d.ml_nlev >= 1;
     M->ml_blocks = dgdf::solver_ml_blocks(d);

@@ -45,22 +45,25 @@ struct GridBar {
   unsigned int gen;
 };
 
-// One smoothing level of the multilevel preconditioner (multilevel.hpp), in device memory.
-struct MLLevelDev {
+// One smoothing level of the multilevel preconditioner (multilevel.hpp), in device memory, with
+// its operators and vectors in the precision R of the V-cycle (FP64, or FP32 in the mixed form).
+template <typename R>
+struct MLLevelT {
   int stencil;        // 1: the facet stencil of S on the first bs modes; 0: the CSR matrix a_*
   int bs, n;          // values per row, rows
   int inject;         // 1: transfer to the next level keeps the leading bs_next modes (same facet rows)
   int n_next, bs_next;
-  const double* binv; // stencil: [n_stencil][bs][bs]; CSR: [n] 1 / a_ii
+  const R* binv;      // stencil: [n_stencil][bs][bs]; CSR: [n] 1 / a_ii
   const int32_t *a_rp, *a_ci;
-  const double* a_v;
+  const R* a_v;
   const int32_t *p_rp, *p_ci;   // prolongation [n x n_next] (CSR transfer)
-  const double* p_v;
+  const R* p_v;
   const int32_t *r_rp, *r_ci;   // restriction [n_next x n]
-  const double* r_v;
-  double c0, c1, c2;  // Chebyshev(2) coefficients
-  double *x, *b, *r, *d;   // work vectors [n * bs]
+  const R* r_v;
+  R c0, c1, c2;       // Chebyshev(2) coefficients
+  R *x, *b, *r, *d;   // work vectors [n * bs]
 };
+using MLLevelDev = MLLevelT<double>;
 
 struct DevMesh {
   int k, ns, nd, nw, nl, nq, nqf;
@@ -128,11 +131,16 @@ struct DevMesh {
   const int32_t* tc_tile_cls;         // [tc_tiles]
   const uint16_t* tc_b;               // [n_class][kTcSlices][NP][KP] bf16 bits, tile layout
   const int32_t* tc_ec;               // [n_class][NP] column exponents
-  // multilevel preconditioner (NULL ml_lv: none)
+  // multilevel preconditioner (NULL ml_lv and ml_lv_f: none). The V-cycle runs in FP64 (ml_lv,
+  // ml_cpinv, ml_xc, ml_bc) or, in the mixed form, in FP32 (the _f twins; level 0 then has
+  // vectors of its own, filled from and written back to the PCG vectors r and z)
   const MLLevelDev* ml_lv;            // [ml_nlev] in device memory
+  const MLLevelT<float>* ml_lv_f;
   int ml_nlev, ml_nc;                 // smoothing levels, rows of the coarsest level
   const double* ml_cpinv;             // [ml_nc][ml_nc] pseudo-inverse of the coarsest operator
   double *ml_xc, *ml_bc;              // coarsest vectors
+  const float* ml_cpinv_f;
+  float *ml_xc_f, *ml_bc_f;
   double* ml_hist;                    // NULL, or [kMLHist][4] per-iteration history of the last
                                       // multilevel solve: relres, r.z, p.S p, alpha
   // inflow / outflow boundaries (Sec. 2.5, eq. (be)); facet_kind NULL: every boundary facet

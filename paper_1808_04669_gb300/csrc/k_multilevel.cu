@@ -16,6 +16,8 @@
 //                  into the finer level's leading modes in the same phase
 // so a level costs four or five barriers and the V-cycle is symmetric (the same
 // Chebyshev polynomial before and after). The level records live in shared memory.
+#include <type_traits>
+
 #include "device.cuh"
 #include "kcommon.cuh"
 #include "multilevel.hpp"
@@ -27,13 +29,34 @@ namespace {
 
 constexpr int kMLThreads = 256;
 
+// Operators of the V-cycle in its precision R: the facet stencil blocks and the coarsest
+// pseudo-inverse and vectors.
+template <typename R>
+struct MLOps;
+template <>
+struct MLOps<double> {
+  __device__ static const double* blocks(const DevMesh& m) { return m.st_blk; }
+  __device__ static const MLLevelDev* levels(const DevMesh& m) { return m.ml_lv; }
+  __device__ static const double* cpinv(const DevMesh& m) { return m.ml_cpinv; }
+  __device__ static double* xc(const DevMesh& m) { return m.ml_xc; }
+  __device__ static double* bc(const DevMesh& m) { return m.ml_bc; }
+};
+template <>
+struct MLOps<float> {
+  __device__ static const float* blocks(const DevMesh& m) { return m.st_blk_f; }
+  __device__ static const MLLevelT<float>* levels(const DevMesh& m) { return m.ml_lv_f; }
+  __device__ static const float* cpinv(const DevMesh& m) { return m.ml_cpinv_f; }
+  __device__ static float* xc(const DevMesh& m) { return m.ml_xc_f; }
+  __device__ static float* bc(const DevMesh& m) { return m.ml_bc_f; }
+};
+
 // Rows of a level in groups of G lanes of one warp, G = the largest power of two <= 32 with
 // G n <= the grid's threads (one round of the grid covers every row whenever n allows): the
 // lanes of a group split a row's sum (dot(i, lane, G), a strided partial sum) and add their
 // partials by shuffles, then lane 0 of the group calls f(i, sum). Short coarse levels thus keep
 // the grid busy instead of one thread walking a long row load by load. The loop bound and the
 // shuffles are the same in every lane of a warp.
-template <typename Dot, typename F>
+template <typename R, typename Dot, typename F>
 __device__ __forceinline__ void rows_grouped(int n, Dot&& dot, F&& f) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   int G = 1;
@@ -41,63 +64,57 @@ __device__ __forceinline__ void rows_grouped(int n, Dot&& dot, F&& f) {
   const int lane = threadIdx.x & (G - 1), grp = gtid / G, ngrp = gsz / G;
   for (int i0 = 0; i0 < n; i0 += ngrp) {
     const int i = i0 + grp;
-    double s = i < n ? dot(i, lane, G) : 0.0;
+    R s = i < n ? dot(i, lane, G) : R(0);
     for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (i < n && lane == 0) f(i, s);
   }
 }
 
 // Strided partial sum of a CSR row: sum over p = rp[i] + lane, + G, ... of v[p] x[ci[p]]
-__device__ __forceinline__ double csr_part(const int32_t* rp, const int32_t* ci, const double* v, const double* x,
-                                           int i, int lane, int G) {
-  double s = 0.0;
+template <typename R>
+__device__ __forceinline__ R csr_part(const int32_t* rp, const int32_t* ci, const R* v, const R* x, int i, int lane,
+                                      int G) {
+  R s = R(0);
   const int p1 = __ldg(&rp[i + 1]);
 #pragma unroll 4
   for (int p = __ldg(&rp[i]) + lane; p < p1; p += G) s += __ldg(&v[p]) * __ldcg(&x[__ldg(&ci[p])]);
   return s;
 }
 
-// y = (A x)_i for row i of level L (bs <= NL values; y[0] only on CSR levels)
-template <int NL>
-__device__ __forceinline__ void ml_row_apply(const DevMesh& m, const MLLevelDev& L, int i, const double* x,
-                                             double (&y)[NL]) {
-  if (L.stencil) {
-    const int bs = L.bs;
-    const double* blk = m.st_blk + size_t(__ldg(&m.facet_stencil[i])) * 5 * NL * NL;
-    int nb[5];
-    nb[0] = i;
+// y = (A x)_i for row i of a stencil level L (bs <= NL values)
+template <int NL, typename R>
+__device__ __forceinline__ void ml_row_apply(const DevMesh& m, const MLLevelT<R>& L, int i, const R* x,
+                                             R (&y)[NL]) {
+  const int bs = L.bs;
+  const R* blk = MLOps<R>::blocks(m) + size_t(__ldg(&m.facet_stencil[i])) * 5 * NL * NL;
+  int nb[5];
+  nb[0] = i;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) nb[b + 1] = __ldg(&m.facet_nbr[size_t(i) * 4 + b]);
+  for (int b = 0; b < 4; ++b) nb[b + 1] = __ldg(&m.facet_nbr[size_t(i) * 4 + b]);
 #pragma unroll
-    for (int ii = 0; ii < NL; ++ii) {
-      double v = 0.0;
-      if (ii < bs) {
+  for (int ii = 0; ii < NL; ++ii) {
+    R v = R(0);
+    if (ii < bs) {
 #pragma unroll
-        for (int b = 0; b < 5; ++b)
+      for (int b = 0; b < 5; ++b)
 #pragma unroll
-          for (int jj = 0; jj < NL; ++jj)
-            if (jj < bs) v += __ldg(&blk[(b * NL + ii) * NL + jj]) * __ldcg(&x[size_t(nb[b]) * bs + jj]);
-      }
-      y[ii] = v;
+        for (int jj = 0; jj < NL; ++jj)
+          if (jj < bs) v += __ldg(&blk[(b * NL + ii) * NL + jj]) * __ldcg(&x[size_t(nb[b]) * bs + jj]);
     }
-  } else {
-    double v = 0.0;
-    const int p1 = __ldg(&L.a_rp[i + 1]);
-    for (int p = __ldg(&L.a_rp[i]); p < p1; ++p) v += __ldg(&L.a_v[p]) * __ldcg(&x[__ldg(&L.a_ci[p])]);
-    y[0] = v;
+    y[ii] = v;
   }
 }
 
 // out = B v for row i of level L
-template <int NL>
-__device__ __forceinline__ void ml_row_binv(const DevMesh& m, const MLLevelDev& L, int i, const double (&v)[NL],
-                                            double (&out)[NL]) {
+template <int NL, typename R>
+__device__ __forceinline__ void ml_row_binv(const DevMesh& m, const MLLevelT<R>& L, int i, const R (&v)[NL],
+                                            R (&out)[NL]) {
   if (L.stencil) {
     const int bs = L.bs;
-    const double* B = L.binv + size_t(__ldg(&m.facet_stencil[i])) * bs * bs;
+    const R* B = L.binv + size_t(__ldg(&m.facet_stencil[i])) * bs * bs;
 #pragma unroll
     for (int ii = 0; ii < NL; ++ii) {
-      double s = 0.0;
+      R s = R(0);
       if (ii < bs) {
 #pragma unroll
         for (int jj = 0; jj < NL; ++jj)
@@ -108,60 +125,72 @@ __device__ __forceinline__ void ml_row_binv(const DevMesh& m, const MLLevelDev& 
   } else {
     out[0] = __ldg(&L.binv[i]) * v[0];
 #pragma unroll
-    for (int ii = 1; ii < NL; ++ii) out[ii] = 0.0;
+    for (int ii = 1; ii < NL; ++ii) out[ii] = R(0);
   }
 }
 
 // First Chebyshev step from zero on row i of level L: d = c0 B b, x = d.
-template <int NL>
-__device__ __forceinline__ void ml_row_first_step(const DevMesh& m, const MLLevelDev& L, int i) {
+template <int NL, typename R>
+__device__ __forceinline__ void ml_row_first_step(const DevMesh& m, const MLLevelT<R>& L, int i) {
   const int bs = L.bs;
-  double bv[NL], t[NL];
+  R bv[NL], t[NL];
 #pragma unroll
-  for (int j = 0; j < NL; ++j) bv[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) : 0.0;
-  ml_row_binv<NL>(m, L, i, bv, t);
+  for (int j = 0; j < NL; ++j) bv[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) : R(0);
+  ml_row_binv<NL, R>(m, L, i, bv, t);
 #pragma unroll
   for (int j = 0; j < NL; ++j)
     if (j < bs) {
-      const double d = L.c0 * t[j];
+      const R d = L.c0 * t[j];
       L.d[size_t(i) * bs + j] = d;
       L.x[size_t(i) * bs + j] = d;
     }
 }
 
+// Level 0's input from the PCG residual r (facet f), then its first Chebyshev step. In FP64 the
+// level's b is r itself; in FP32 it is r rounded.
+template <int NL, typename R>
+__device__ __forceinline__ void ml_start_row(const DevMesh& m, const MLLevelT<R>& L0, int f) {
+  if constexpr (!std::is_same<R, double>::value) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) L0.b[size_t(f) * NL + j] = R(m.r[size_t(f) * NL + j]);
+  }
+  ml_row_first_step<NL, R>(m, L0, f);
+}
+
 // One V-cycle: on entry lv[0].b holds the input and lv[0].d = lv[0].x = c0 B b (set by the
-// caller before a barrier); on return every thread has written its rows of lv[0].x (the
-// output z) and accumulated, over its level-0 rows, b.z, b.b and the sum of b's mode 0 into
-// red[0..2]. The caller's reduction is the closing barrier.
-template <int NL>
-__device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[3]) {
+// caller before a barrier, ml_start_row); on return every thread has written its rows of the
+// output z (m.z: lv[0].x itself in FP64, its FP64 image in FP32) and accumulated, over its
+// level-0 rows, r.z, r.r and the sum of r's mode 0 into red[0..2], with r the PCG residual
+// m.r. The caller's reduction is the closing barrier.
+template <int NL, typename R>
+__device__ bool ml_vcycle(const DevMesh& m, const MLLevelT<R>* lv, double (&red)[3]) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   const int nlev = m.ml_nlev;
   GridBar* bar = m.bar;
   for (int l = 0; l < nlev; ++l) {
-    const MLLevelDev& L = lv[l];
+    const MLLevelT<R>& L = lv[l];
     const int bs = L.bs;
     // [A] second Chebyshev step from zero
     if (L.stencil) {
       for (int i = gtid; i < L.n; i += gsz) {
-        double y[NL], res[NL], t[NL];
-        ml_row_apply<NL>(m, L, i, L.d, y);
+        R y[NL], res[NL], t[NL];
+        ml_row_apply<NL, R>(m, L, i, L.d, y);
 #pragma unroll
-        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
-        ml_row_binv<NL>(m, L, i, res, t);
+        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : R(0);
+        ml_row_binv<NL, R>(m, L, i, res, t);
 #pragma unroll
         for (int j = 0; j < NL; ++j)
           if (j < bs) {
-            const double d = __ldcg(&L.d[size_t(i) * bs + j]);
+            const R d = __ldcg(&L.d[size_t(i) * bs + j]);
             L.x[size_t(i) * bs + j] = d + L.c1 * d + L.c2 * t[j];
           }
       }
     } else {
-      rows_grouped(
-          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
-          [&](int i, double y) {
-            const double t = __ldg(&L.binv[i]) * (__ldcg(&L.b[i]) - y);
-            const double d = __ldcg(&L.d[i]);
+      rows_grouped<R>(
+          L.n, [&](int i, int lane, int G) { return csr_part<R>(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
+          [&](int i, R y) {
+            const R t = __ldg(&L.binv[i]) * (__ldcg(&L.b[i]) - y);
+            const R d = __ldcg(&L.d[i]);
             L.x[i] = d + L.c1 * d + L.c2 * t;
           });
     }
@@ -170,37 +199,37 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
     const bool last = l + 1 == nlev;
     if (L.stencil) {
       for (int i = gtid; i < L.n; i += gsz) {
-        double y[NL];
-        ml_row_apply<NL>(m, L, i, L.x, y);
+        R y[NL];
+        ml_row_apply<NL, R>(m, L, i, L.x, y);
 #pragma unroll
         for (int j = 0; j < NL; ++j)
           if (j < bs) {
-            const double r = __ldcg(&L.b[size_t(i) * bs + j]) - y[j];
+            const R r = __ldcg(&L.b[size_t(i) * bs + j]) - y[j];
             L.r[size_t(i) * bs + j] = r;
             if (L.inject && j < L.bs_next) {
-              if (last) m.ml_bc[i] = r;   // bs_next = 1 into the coarsest level
+              if (last) MLOps<R>::bc(m)[i] = r;   // bs_next = 1 into the coarsest level
               else lv[l + 1].b[size_t(i) * L.bs_next + j] = r;
             }
           }
-        if (L.inject && !last) ml_row_first_step<NL>(m, lv[l + 1], i);
+        if (L.inject && !last) ml_row_first_step<NL, R>(m, lv[l + 1], i);
       }
     } else {
       // CSR levels hold one value per row and transfer through R (phase [C])
-      rows_grouped(
-          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
-          [&](int i, double y) { L.r[i] = __ldcg(&L.b[i]) - y; });
+      rows_grouped<R>(
+          L.n, [&](int i, int lane, int G) { return csr_part<R>(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
+          [&](int i, R y) { L.r[i] = __ldcg(&L.b[i]) - y; });
     }
     if (!grid_sync(bar, m.stats)) return false;
     if (!L.inject) {
       // [C] CSR restriction b_next = R r
-      rows_grouped(
-          L.n_next, [&](int j, int lane, int G) { return csr_part(L.r_rp, L.r_ci, L.r_v, L.r, j, lane, G); },
-          [&](int j, double v) {
+      rows_grouped<R>(
+          L.n_next, [&](int j, int lane, int G) { return csr_part<R>(L.r_rp, L.r_ci, L.r_v, L.r, j, lane, G); },
+          [&](int j, R v) {
             if (last) {
-              m.ml_bc[j] = v;
+              MLOps<R>::bc(m)[j] = v;
             } else {
               lv[l + 1].b[j] = v;
-              ml_row_first_step<NL>(m, lv[l + 1], j);
+              ml_row_first_step<NL, R>(m, lv[l + 1], j);
             }
           });
       if (!grid_sync(bar, m.stats)) return false;
@@ -209,40 +238,42 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
   // coarsest level: x_c = pinv b_c
   {
     const int nc = m.ml_nc;
-    const MLLevelDev& Lz = lv[nlev - 1];
-    rows_grouped(
+    const MLLevelT<R>& Lz = lv[nlev - 1];
+    const R* bc = MLOps<R>::bc(m);
+    R* xc = MLOps<R>::xc(m);
+    rows_grouped<R>(
         nc,
         [&](int i, int lane, int G) {
-          double v = 0.0;
-          const double* row = m.ml_cpinv + size_t(i) * nc;
-          for (int j = lane; j < nc; j += G) v += __ldg(&row[j]) * __ldcg(&m.ml_bc[j]);
+          R v = R(0);
+          const R* row = MLOps<R>::cpinv(m) + size_t(i) * nc;
+          for (int j = lane; j < nc; j += G) v += __ldg(&row[j]) * __ldcg(&bc[j]);
           return v;
         },
-        [&](int i, double v) {
-          m.ml_xc[i] = v;
+        [&](int i, R v) {
+          xc[i] = v;
           if (Lz.inject) Lz.x[size_t(i) * Lz.bs] += v;
         });
     if (!grid_sync(bar, m.stats)) return false;
   }
   for (int l = nlev - 1; l >= 0; --l) {
-    const MLLevelDev& L = lv[l];
+    const MLLevelT<R>& L = lv[l];
     const int bs = L.bs;
     if (!L.inject) {
       // [U] CSR prolongation x += P x_next
-      const double* xn = (l + 1 == nlev) ? m.ml_xc : lv[l + 1].x;
-      rows_grouped(
-          L.n, [&](int i, int lane, int G) { return csr_part(L.p_rp, L.p_ci, L.p_v, xn, i, lane, G); },
-          [&](int i, double v) { L.x[i] += v; });
+      const R* xn = (l + 1 == nlev) ? MLOps<R>::xc(m) : lv[l + 1].x;
+      rows_grouped<R>(
+          L.n, [&](int i, int lane, int G) { return csr_part<R>(L.p_rp, L.p_ci, L.p_v, xn, i, lane, G); },
+          [&](int i, R v) { L.x[i] += v; });
       if (!grid_sync(bar, m.stats)) return false;
     }
     // [Q] r = b - A x, d = c0 B r
     if (L.stencil) {
       for (int i = gtid; i < L.n; i += gsz) {
-        double y[NL], res[NL], t[NL];
-        ml_row_apply<NL>(m, L, i, L.x, y);
+        R y[NL], res[NL], t[NL];
+        ml_row_apply<NL, R>(m, L, i, L.x, y);
 #pragma unroll
-        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : 0.0;
-        ml_row_binv<NL>(m, L, i, res, t);
+        for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.b[size_t(i) * bs + j]) - y[j] : R(0);
+        ml_row_binv<NL, R>(m, L, i, res, t);
 #pragma unroll
         for (int j = 0; j < NL; ++j)
           if (j < bs) {
@@ -251,45 +282,48 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
           }
       }
     } else {
-      rows_grouped(
-          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
-          [&](int i, double y) {
-            const double res = __ldcg(&L.b[i]) - y;
+      rows_grouped<R>(
+          L.n, [&](int i, int lane, int G) { return csr_part<R>(L.a_rp, L.a_ci, L.a_v, L.x, i, lane, G); },
+          [&](int i, R y) {
+            const R res = __ldcg(&L.b[i]) - y;
             L.r[i] = res;
             L.d[i] = L.c0 * (__ldg(&L.binv[i]) * res);
           });
     }
     if (!grid_sync(bar, m.stats)) return false;
     // [R] x += d + c1 d + c2 B (r - A d); inject into the finer level (same facet rows)
-    const MLLevelDev* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
+    const MLLevelT<R>* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
     if (!L.stencil) {
       // a CSR level (never level 0, never below an injecting level)
-      rows_grouped(
-          L.n, [&](int i, int lane, int G) { return csr_part(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
-          [&](int i, double y) {
-            const double t = __ldg(&L.binv[i]) * (__ldcg(&L.r[i]) - y);
-            const double d = __ldcg(&L.d[i]);
+      rows_grouped<R>(
+          L.n, [&](int i, int lane, int G) { return csr_part<R>(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
+          [&](int i, R y) {
+            const R t = __ldg(&L.binv[i]) * (__ldcg(&L.r[i]) - y);
+            const R d = __ldcg(&L.d[i]);
             L.x[i] = __ldcg(&L.x[i]) + d + L.c1 * d + L.c2 * t;
           });
       if (!grid_sync(bar, m.stats)) return false;
       continue;
     }
     for (int i = gtid; i < L.n; i += gsz) {
-      double y[NL], res[NL], t[NL];
-      ml_row_apply<NL>(m, L, i, L.d, y);
+      R y[NL], res[NL], t[NL];
+      ml_row_apply<NL, R>(m, L, i, L.d, y);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.r[size_t(i) * bs + j]) - y[j] : 0.0;
-      ml_row_binv<NL>(m, L, i, res, t);
+      for (int j = 0; j < NL; ++j) res[j] = j < bs ? __ldcg(&L.r[size_t(i) * bs + j]) - y[j] : R(0);
+      ml_row_binv<NL, R>(m, L, i, res, t);
 #pragma unroll
       for (int j = 0; j < NL; ++j)
         if (j < bs) {
-          const double d = __ldcg(&L.d[size_t(i) * bs + j]);
-          const double x = __ldcg(&L.x[size_t(i) * bs + j]) + d + L.c1 * d + L.c2 * t[j];
+          const R d = __ldcg(&L.d[size_t(i) * bs + j]);
+          const R x = __ldcg(&L.x[size_t(i) * bs + j]) + d + L.c1 * d + L.c2 * t[j];
           L.x[size_t(i) * bs + j] = x;
           if (F) F->x[size_t(i) * F->bs + j] += x;
           if (l == 0) {
-            const double b = __ldcg(&L.b[size_t(i) * bs + j]);
-            red[0] += b * x;
+            // the output z and the PCG scalars, against the FP64 residual
+            const double z = double(x);
+            if constexpr (!std::is_same<R, double>::value) m.z[size_t(i) * bs + j] = z;
+            const double b = __ldcg(&m.r[size_t(i) * bs + j]);
+            red[0] += b * z;
             red[1] += b * b;
             if (j == 0) red[2] += b;
           }
@@ -302,11 +336,11 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelDev* lv, double (&red)[
 
 // One solve: g assembled from the element sides, lam0 = warm_scale * lam, constant multiplier
 // removed from g, then PCG with the V-cycle. Level 0's b and x are the PCG vectors r and z.
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a) {
   constexpr int NL = K + 1;
-  __shared__ MLLevelDev lv[kMLMaxLevels];
-  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = m.ml_lv[l];
+  __shared__ MLLevelT<R> lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = MLOps<R>::levels(m)[l];
   __syncthreads();
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
@@ -360,11 +394,11 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
     // remove the constant component; first Chebyshev step of the V-cycle on r
     for (int f = gtid; f < nF; f += gsz) {
       m.r[size_t(f) * NL] -= r0s[0] * inv_nf;
-      ml_row_first_step<NL>(m, lv[0], f);
+      ml_start_row<NL, R>(m, lv[0], f);
     }
     if (!grid_sync(bar, m.stats)) return;
     double red[3] = {0.0, 0.0, 0.0};
-    if (!ml_vcycle<NL>(m, lv, red)) return;
+    if (!ml_vcycle<NL, R>(m, lv, red)) return;
     if (!grid_reduce<3>(m, 1, red, bar)) return;
     double rho = red[0];
     rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
@@ -443,11 +477,11 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
           m.lam[o] += alpha * pnew[o];
           m.r[o] -= alpha * m.q[o] + (j == 0 ? cmean : 0.0);
         }
-        ml_row_first_step<NL>(m, lv[0], f);
+        ml_start_row<NL, R>(m, lv[0], f);
       }
       if (!grid_sync(bar, m.stats)) return;
       double red2[3] = {0.0, 0.0, 0.0};
-      if (!ml_vcycle<NL>(m, lv, red2)) return;
+      if (!ml_vcycle<NL, R>(m, lv, red2)) return;
       if (!grid_reduce<3>(m, 1, red2, bar)) return;
       beta = red2[0] / rho;
       rho = red2[0];
@@ -472,31 +506,34 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
 
 // One V-cycle z = M r on its own (test hook dg_test_multilevel_apply): r and z are facet-major
 // [n_facet][k+1] in device memory. Uses the solver's level-0 vectors m.r and m.z.
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(kMLThreads) k_ml_apply(DevMesh m, const double* rin, double* zout) {
   constexpr int NL = K + 1;
-  __shared__ MLLevelDev lv[kMLMaxLevels];
-  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = m.ml_lv[l];
+  __shared__ MLLevelT<R> lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < m.ml_nlev; l += blockDim.x) lv[l] = MLOps<R>::levels(m)[l];
   __syncthreads();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   for (int f = gtid; f < m.n_facet; f += gsz) {
 #pragma unroll
     for (int j = 0; j < NL; ++j) m.r[size_t(f) * NL + j] = rin[size_t(f) * NL + j];
-    ml_row_first_step<NL>(m, lv[0], f);
+    ml_start_row<NL, R>(m, lv[0], f);
   }
   if (!grid_sync(m.bar, m.stats)) return;
   double red[3] = {0.0, 0.0, 0.0};
-  if (!ml_vcycle<NL>(m, lv, red)) return;
+  if (!ml_vcycle<NL, R>(m, lv, red)) return;
   for (int f = gtid; f < m.n_facet; f += gsz)
 #pragma unroll
     for (int j = 0; j < NL; ++j) zout[size_t(f) * NL + j] = m.z[size_t(f) * NL + j];
 }
 
-const void* ml_kernel(int k) {
-  switch (k) {
-    case 1: return (const void*)k_solve_ml<1>;
-    case 2: return (const void*)k_solve_ml<2>;
-    case 3: return (const void*)k_solve_ml<3>;
+const void* ml_kernel(int k, bool fp32) {
+  switch (k * 2 + (fp32 ? 1 : 0)) {
+    case 2: return (const void*)k_solve_ml<1, double>;
+    case 3: return (const void*)k_solve_ml<1, float>;
+    case 4: return (const void*)k_solve_ml<2, double>;
+    case 5: return (const void*)k_solve_ml<2, float>;
+    case 6: return (const void*)k_solve_ml<3, double>;
+    case 7: return (const void*)k_solve_ml<3, float>;
     default: return nullptr;
   }
 }
@@ -504,14 +541,18 @@ const void* ml_kernel(int k) {
 }  // namespace
 
 cudaError_t launch_ml_apply(const DevMesh& m, const double* r, double* z, int nblocks, cudaStream_t s) {
-  if (!m.ml_lv || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
+  const bool fp32 = m.ml_lv_f != nullptr;
+  if ((!m.ml_lv && !fp32) || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   const void* fn = nullptr;
-  switch (m.k) {
-    case 1: fn = (const void*)k_ml_apply<1>; break;
-    case 2: fn = (const void*)k_ml_apply<2>; break;
-    case 3: fn = (const void*)k_ml_apply<3>; break;
+  switch (m.k * 2 + (fp32 ? 1 : 0)) {
+    case 2: fn = (const void*)k_ml_apply<1, double>; break;
+    case 3: fn = (const void*)k_ml_apply<1, float>; break;
+    case 4: fn = (const void*)k_ml_apply<2, double>; break;
+    case 5: fn = (const void*)k_ml_apply<2, float>; break;
+    case 6: fn = (const void*)k_ml_apply<3, double>; break;
+    case 7: fn = (const void*)k_ml_apply<3, float>; break;
     default: return cudaErrorInvalidValue;
   }
   DevMesh mm = m;
@@ -520,7 +561,7 @@ cudaError_t launch_ml_apply(const DevMesh& m, const double* r, double* z, int nb
 }
 
 int solver_ml_blocks(const DevMesh& m) {
-  const void* fn = ml_kernel(m.k);
+  const void* fn = ml_kernel(m.k, m.ml_lv_f != nullptr);
   if (!fn) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -538,10 +579,11 @@ int solver_ml_blocks(const DevMesh& m) {
 }
 
 cudaError_t launch_solve_ml(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s) {
-  if (!m.ml_lv || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
+  const bool fp32 = m.ml_lv_f != nullptr;
+  if ((!m.ml_lv && !fp32) || m.ml_nlev < 1 || m.ml_nlev > kMLMaxLevels) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(m.bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
-  const void* fn = ml_kernel(m.k);
+  const void* fn = ml_kernel(m.k, fp32);
   if (!fn) return cudaErrorInvalidValue;
   DevMesh mm = m;
   SolveArgs aa = a;

@@ -418,6 +418,24 @@ def test_multilevel_device_v_cycle_matches_host_reference(g, N, k, walls):
         assert rel(mesh.test_multilevel_apply(r[i]), host[i]) < 1e-13
 
 
+@pytest.mark.parametrize("N,k,walls", [(8, 3, True), (64, 3, True), (64, 2, False)])
+def test_multilevel_fp32_v_cycle_matches_host_reference(g, N, k, walls):
+    # the mixed form runs the V-cycle in FP32 (the PCG vectors and S stay FP64): one V-cycle
+    # against the host's FP64 reference, for inputs in the range of S (the constant multiplier,
+    # the kernel of S on closed meshes, removed), to FP32 rounding amplified by the cycle
+    vid, X = synth.split_square_mesh(N, L=1.0, periodic=not walls)
+    if not walls:
+        rng = np.random.default_rng(1)
+        X = X + (0.1 / N * rng.uniform(-1, 1, size=(N * N, 2)))[vid]
+    mesh = g.DGMesh(vid, X, k, 1e-4, precision=1, precond=g.PRECOND_MULTILEVEL)
+    r = np.random.default_rng(2).standard_normal((2, mesh.n_facet, k + 1))
+    r[:, :, 0] -= r[:, :, 0].mean(axis=1, keepdims=True)
+    r = r.reshape(2, -1)
+    host = g.host_multilevel(vid, X, k, r=r)["z"]
+    for i in range(2):
+        assert rel(mesh.test_multilevel_apply(r[i]), host[i]) < 1e-5
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_split_column_pass_parity_n64(g, k):
     # N = 64: the lattice solver splits each column into even and odd wavenumbers (N/2+1 <= SMs);
