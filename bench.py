@@ -503,10 +503,10 @@ def run_ensemble(args):
 
 
 def run_schemes(args):
-    """The other explicit schemes and walls (mixed form, device-timed, L2 flushed between steps):
-    SSP-RK3, forward Euler and RK4 on the bench workload, and SSP-RK3 on the Taylor-Green cell
-    in a box with free-slip walls (block-Jacobi facet solves). Units: broken velocity DOFs times
-    the stages of each step."""
+    """The other explicit schemes and boundaries (mixed form, device-timed, L2 flushed between
+    steps): SSP-RK3, forward Euler and RK4 on the bench workload; SSP-RK3 on the Taylor-Green
+    cell in a box with free-slip walls and on a channel with inflow and outflow (multilevel facet
+    solves). Units: broken velocity DOFs times the stages of each step."""
     import numpy as np
     import torch
     torch.cuda.set_device(env_rank()[2])
@@ -559,6 +559,28 @@ def run_schemes(args):
     out["results"].append({"workload": "Taylor-Green cell, unit square with free-slip walls, %dx%d split squares "
                                        "(%d triangles), BDM_%d, nu=%g, %s PCG" % (N, N, m.n_tri, k, nu,
                                                                                  m.solver_stats()["preconditioner"]),
+                           "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
+                           "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
+    m.close()
+    # inflow/outflow (Sec. 2.5): a channel [0, 2] x [0, 1] periodic in y, inflow on x = 0 with
+    # u_in = (1 + 0.3 sin 2 pi y, 0.2 cos 2 pi y), open outflow on x = 2
+    Ny = (args.n or 128) // 2 or 1
+    Nx = 2 * Ny
+    vid, X = synth.channel_mesh(Nx, Ny, 2.0, 1.0, periodic_y=True)
+    kinds = synth.boundary_kinds_by_x(X, 0.0, 2.0)
+
+    def profile(x, y):
+        return 1.0 + 0.3 * np.sin(2 * np.pi * y) + 0 * x, 0.2 * np.cos(2 * np.pi * y) + 0 * x
+    vals = synth.sample_lattice(profile, X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu)
+    m = g.DGMesh(vid, X, k, nu, precision=g.MIXED, stream=stream.cuda_stream, boundary=kinds,
+                 inflow=synth.sample_edges(profile, X, k))
+    m.set_velocity(vals)
+    m.project_divfree()
+    ms, its = timed(m, dt, g.SSPRK3, args.steps, args.warmup)
+    out["results"].append({"workload": "channel [0,2]x[0,1] periodic in y, inflow x=0, outflow x=2, %dx%d split "
+                                       "squares (%d triangles), BDM_%d, nu=%g, %s PCG" % (Nx, Ny, m.n_tri, k, nu,
+                                                                                     m.solver_stats()["preconditioner"]),
                            "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
                            "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
     m.close()
