@@ -26,8 +26,12 @@ convergence orders, the energy identity of Sec. 2.2, symmetry of the SIPG form
 eq. (18), zero divergence and normal jump, agreement of the four solve routes,
 dimension counts of the divergence-free space and of Table 3, and the third
 order of the SSP-RK3 scheme eq. (8).
+
+``dg3`` is the same method on closed tetrahedral meshes (d = 3), pinned in
+tests/test_oracle3_pins.py.
 """
 from .mesh import Topology
 from .dg import Discretization
+from .dg3 import Discretization3, Topology3
 
-__all__ = ["Topology", "Discretization"]
+__all__ = ["Topology", "Discretization", "Topology3", "Discretization3"]
