@@ -237,6 +237,82 @@ class DGMesh:
         return res
 
 
+class DGMesh3:
+    """One closed tetrahedral mesh and its state (include/dgdf3.h: dg3_mesh_create ... dg3_mesh_destroy),
+    FP64, k = 1 or 2."""
+
+    def __init__(self, tet_vertex_ids, tet_coords, k, nu, alpha=2.0, cg_rtol=1e-13, cg_maxit=20000, stream=None):
+        L = lib()
+        vid = np.ascontiguousarray(tet_vertex_ids, dtype=np.int64)
+        X = np.ascontiguousarray(tet_coords, dtype=np.float64)
+        if vid.ndim != 2 or vid.shape[1] != 4 or X.shape != (vid.shape[0], 4, 3):
+            raise ValueError("tet_vertex_ids [n,4] and tet_coords [n,4,3] expected")
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        self.params = DGParams(int(k), float(nu), float(alpha), FP64, float(cg_rtol), int(cg_maxit),
+                               ctypes.c_void_p(int(stream)), PRECOND_BLOCK_JACOBI)
+        h = ctypes.c_void_p()
+        check(L.dg3_mesh_create(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(self.params), ctypes.byref(h)), "dg3_mesh_create")
+        self._h = h
+        info = self.info()
+        self.n_tet, self.n_face, self.k, self.n_lat = (int(v) for v in info[:4])
+        self.n_class, self.n_stencil = int(info[4]), int(info[5])
+        self.n_vel_dofs, self.n_lam_dofs = int(info[6]), int(info[7])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg3_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        out = (ctypes.c_int64 * 8)()
+        check(lib().dg3_mesh_info(self._h, out), "dg3_mesh_info")
+        return list(out)
+
+    def set_velocity(self, vals):
+        if isinstance(vals, np.ndarray):
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        p, dev = _ptr(vals)
+        check(lib().dg3_set_velocity(self._h, p, dev), "dg3_set_velocity")
+
+    def get_velocity(self, out=None):
+        if out is None:
+            out = np.empty((self.n_tet, self.n_lat, 3))
+        p, dev = _ptr(out)
+        check(lib().dg3_get_velocity(self._h, p, dev), "dg3_get_velocity")
+        return out
+
+    def project_divfree(self):
+        check(lib().dg3_project_divfree(self._h), "dg3_project_divfree")
+
+    def rk3_step(self, dt, nsteps=1):
+        check(lib().dg3_rk3_step(self._h, float(dt), int(nsteps)), "dg3_rk3_step")
+
+    def eval_residual(self, out=None):
+        if out is None:
+            out = np.empty((self.n_tet, self.n_lat, 3))
+        p, dev = _ptr(out)
+        check(lib().dg3_eval_residual(self._h, p, dev), "dg3_eval_residual")
+        return out
+
+    def diagnostics(self):
+        out = (ctypes.c_double * 8)()
+        check(lib().dg3_get_diagnostics(self._h, out), "dg3_get_diagnostics")
+        keys = ("energy", "enstrophy", "max_div", "max_jump", "last_iters", "last_relres", "total_iters", "solves")
+        return dict(zip(keys, list(out)))
+
+
 class DGBatch:
     """An ensemble of DGMesh members advanced together (dg_batch_create / dg_batch_rk3_step)."""
 
@@ -415,5 +491,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGMesh3", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "facet_solve_noalloc",
            "lib"]

@@ -1,4 +1,4 @@
-"""ctypes binding of libdgdf (include/dgdf.h, include/dgdf_host.h): argument marshalling only.
+"""ctypes binding of libdgdf (include/dgdf.h, include/dgdf_host.h, include/dgdf3.h): argument marshalling only.
 
 The library must have been built in-tree (``paper_1808_04669_gb300.build``);
 there is no fallback: a missing library raises ImportError.
@@ -17,7 +17,9 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_create_ex", "dg_set_inflow", "dg_mesh_dest
            "dg_project_divfree", "dg_rk3_step", "dg_step", "dg_batch_create", "dg_batch_destroy", "dg_batch_rk3_step", "dg_batch_set_lanes", "dg_batch_get_tuning", "dg_get_pressure", "dg_eval_residual", "dg_set_coefficients", "dg_get_coefficients",
            "dg_set_viscosity", "dg_rk3_vjp", "dg_get_diagnostics", "dg_get_solver_stats", "dg_facet_solve_noalloc",
            "dg_set_energy_watchdog", "dg_set_tensor_cores", "dg_solver_history", "dg_test_multilevel_apply", "dg_test_barrier_fault", "dg_profile", "dg_kernel_name", "dg_last_error", "dg_host_topology", "dg_host_reference",
-           "dg_host_facet_operator", "dg_host_lattice", "dg_host_multilevel"]
+           "dg_host_facet_operator", "dg_host_lattice", "dg_host_multilevel",
+           "dg3_mesh_create", "dg3_mesh_destroy", "dg3_mesh_info", "dg3_set_velocity", "dg3_get_velocity",
+           "dg3_project_divfree", "dg3_rk3_step", "dg3_eval_residual", "dg3_get_diagnostics"]
 
 
 class DGParams(ctypes.Structure):
@@ -42,6 +44,15 @@ def lib():
         "dg_mesh_create_ex": (ctypes.c_int, [I64, P, P, P, ctypes.POINTER(DGParams), ctypes.POINTER(ctypes.c_void_p)]),
         "dg_set_inflow": (ctypes.c_int, [P, P]),
         "dg_mesh_destroy": (ctypes.c_int, [P]),
+        "dg3_mesh_create": (ctypes.c_int, [I64, P, P, ctypes.POINTER(DGParams), ctypes.POINTER(ctypes.c_void_p)]),
+        "dg3_mesh_destroy": (ctypes.c_int, [P]),
+        "dg3_mesh_info": (ctypes.c_int, [P, P]),
+        "dg3_set_velocity": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "dg3_get_velocity": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "dg3_project_divfree": (ctypes.c_int, [P]),
+        "dg3_rk3_step": (ctypes.c_int, [P, D, I64]),
+        "dg3_eval_residual": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "dg3_get_diagnostics": (ctypes.c_int, [P, P]),
         "dg_mesh_info": (ctypes.c_int, [P, P]),
         "dg_set_velocity": (ctypes.c_int, [P, P, ctypes.c_int]),
         "dg_get_velocity": (ctypes.c_int, [P, P, ctypes.c_int]),

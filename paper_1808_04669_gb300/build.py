@@ -10,11 +10,12 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgdf.so")
 
-CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu", "k_multilevel.cu", "k_recover_tc.cu"]
+CUDA_SOURCES = ["api.cu", "k_element.cu", "k_stage_df.cu", "k_solver.cu", "k_lattice.cu", "k_multilevel.cu", "k_recover_tc.cu",
+                "api3.cu", "k_tet.cu"]
 # (source, object name, extra flags): the lattice solver is compiled once per (k, form)
 CUDA_VARIANTS = [("k_lattice_inst.cu", "k_lattice_k%d_%d.o" % (k, m), ["-DDG_LAT_K=%d" % k, "-DDG_LAT_MIXED=%d" % m])
                  for k in (1, 2, 3) for m in (0, 1)]
-CXX_SOURCES = ["setup.cpp", "host_api.cpp", "multilevel.cpp"]
+CXX_SOURCES = ["setup.cpp", "host_api.cpp", "multilevel.cpp", "setup3.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +38,7 @@ def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in CUDA_SOURCES + CXX_SOURCES + [v[0] for v in CUDA_VARIANTS]]
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".hpp"))]
-    hdrs += [os.path.join(HERE, "..", "include", f) for f in ("dgdf.h", "dgdf_host.h")]
+    hdrs += [os.path.join(HERE, "..", "include", f) for f in ("dgdf.h", "dgdf_host.h", "dgdf3.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(f) < t for f in srcs + hdrs + [__file__]):

@@ -55,6 +55,12 @@ const char* kKernelNames[KC_COUNT] = {"stage_residual", "facet_pcg_fp64",
 
 }  // namespace
 
+namespace dgdf {
+// error reporting of the other C-ABI translation units (api3.cu): the same thread-local message
+int api_fail(int code, const std::string& msg) { return fail(code, msg); }
+void api_clear_error() { g_err.clear(); }
+}  // namespace dgdf
+
 struct dg_mesh {
   dgdf::HostMesh hm;
   dgdf::DevMesh dm{};

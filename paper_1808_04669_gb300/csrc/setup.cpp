@@ -1233,4 +1233,10 @@ void inflow_data(const HostMesh& hm, const double* vals, std::vector<double>& uq
 void symmetric_eigen(const std::vector<double>& A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
   sym_eig(A, n, evals, evecs);
 }
+
+void host_gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+  gauss_jacobi(n, a, b, x, w);
+}
+
+bool host_invert(std::vector<double>& A, int n) { return invert(A, n); }
 }  // namespace dgdf

@@ -119,6 +119,10 @@ void build_lattice(const HostMesh& hm, const double* X, Lattice& lat, bool eig_h
 // Eigen-decomposition of a small dense symmetric matrix (row-major [n][n]) by cyclic Jacobi
 // rotations: evals[i] and column i of evecs ([n][n], row-major).
 void symmetric_eigen(const std::vector<double>& A, int n, std::vector<double>& evals, std::vector<double>& evecs);
+// Gauss-Jacobi rule for the weight (1-x)^a (1+x)^b on [-1,1] (n points, Golub-Welsch).
+void host_gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+// In-place inverse of an n x n row-major matrix (partial pivoting); false if singular.
+bool host_invert(std::vector<double>& A, int n);
 // Renumbers the facets of a lattice mesh internally in (type, j, i) order, so that the
 // facet-major vectors are the Fourier passes' row order; records the external ids.
 void renumber_facets_lattice(HostMesh& hm, Lattice& lat);

@@ -1,0 +1,113 @@
+"""The three-dimensional path (include/dgdf3.h: closed tetrahedral meshes, FP64) against the 3-D
+oracle (oracle/dg3.py) on the same seeded inputs: periodic Kuhn cube meshes, the ABC flow plus
+seeded noise. Tolerance: 1e-12 relative L2 over lattice values."""
+import numpy as np
+import pytest
+
+from oracle.dg3 import Discretization3
+from synth.mesh3 import abc_flow, kuhn_cube_mesh, sample_lattice3
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1808_04669_gb300 import build
+    build.build()
+    import paper_1808_04669_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def field(X, k, seed, noise=0.3):
+    v = sample_lattice3(abc_flow(), X, k)
+    return v + noise * np.random.default_rng(seed).standard_normal(v.shape)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_lattice_roundtrip_and_info(g, k):
+    vid, X = kuhn_cube_mesh(2)
+    m = g.DGMesh3(vid, X, k, 0.0)
+    assert m.n_tet == 48 and m.n_face == 96
+    v = field(X, k, 1)
+    m.set_velocity(v)
+    assert np.abs(m.get_velocity() - v).max() < 1e-13
+
+
+@pytest.mark.parametrize("N,k,nu", [(2, 1, 0.0), (2, 2, 0.05), (3, 1, 0.02), (3, 2, 0.0)])
+def test_residual_parity(g, N, k, nu):
+    vid, X = kuhn_cube_mesh(N)
+    d = Discretization3(vid, X, k, nu)
+    v = field(X, k, 10 + N)
+    m = g.DGMesh3(vid, X, k, nu)
+    m.set_velocity(v)
+    ref = d.to_lattice(d.riesz(d.residual(d.from_lattice(v))))
+    assert rel(m.eval_residual(), ref) < TOL
+
+
+@pytest.mark.parametrize("N,k", [(2, 1), (2, 2), (3, 2)])
+def test_projection_parity(g, N, k):
+    vid, X = kuhn_cube_mesh(N)
+    d = Discretization3(vid, X, k, 0.0)
+    v = field(X, k, 20 + N)
+    m = g.DGMesh3(vid, X, k, 0.0)
+    m.set_velocity(v)
+    m.project_divfree()
+    ref = d.to_lattice(d.project(d.from_lattice(v)))
+    assert rel(m.get_velocity(), ref) < TOL
+    dg = m.diagnostics()
+    assert dg["max_div"] < 1e-11 and dg["max_jump"] < 1e-11
+
+
+@pytest.mark.parametrize("N,k,nu", [(2, 1, 0.01), (2, 2, 0.01), (3, 2, 1e-3)])
+def test_rk3_parity(g, N, k, nu):
+    vid, X = kuhn_cube_mesh(N)
+    d = Discretization3(vid, X, k, nu)
+    v = field(X, k, 30 + N, noise=0.1)
+    dt = 0.3 * (2 * np.pi / N) / (k * k * np.abs(v).max())
+    U = d.rk3_step(d.project(d.from_lattice(v)), dt, 3)
+    m = g.DGMesh3(vid, X, k, nu)
+    m.set_velocity(v)
+    m.project_divfree()
+    m.rk3_step(dt, 3)
+    assert rel(m.get_velocity(), d.to_lattice(U)) < TOL
+    dg = m.diagnostics()
+    od = d.diagnostics(U)
+    assert abs(dg["energy"] - od["energy"]) < 1e-11 * od["energy"]
+    assert dg["max_jump"] < 1e-11
+
+
+def test_abc_flow_decays_as_exp_minus_nu_t(g):
+    # the ABC field decays as exp(-nu t); the discrete energy of its projection follows on 4^3 cells
+    k, nu, N = 2, 0.05, 4
+    vid, X = kuhn_cube_mesh(N)
+    m = g.DGMesh3(vid, X, k, nu)
+    m.set_velocity(sample_lattice3(abc_flow(), X, k))
+    m.project_divfree()
+    e0 = m.diagnostics()["energy"]
+    T, steps = 0.5, 20
+    m.rk3_step(T / steps, steps)
+    e1 = m.diagnostics()["energy"]
+    assert abs(e1 / e0 - np.exp(-2 * nu * T)) < 0.02
+
+
+def test_arguments_rejected(g):
+    vid, X = kuhn_cube_mesh(2)
+    with pytest.raises(g.DGError) as e:
+        g.DGMesh3(vid, X, 3, 0.0)
+    assert e.value.code == -3
+    # an open mesh (one cube's six tetrahedra without periodic identification): faces with one side
+    vid1, X1 = kuhn_cube_mesh(2)
+    sel = np.arange(6)
+    ids = np.arange(24).reshape(6, 4)
+    with pytest.raises(g.DGError) as e:
+        g.DGMesh3(ids, X1[sel], 1, 0.0)
+    assert e.value.code in (-2, -3)

@@ -22,16 +22,17 @@ def g():
 
 def declared_functions():
     names = []
-    for h in ("dgdf.h", "dgdf_host.h"):
+    for h in ("dgdf.h", "dgdf_host.h", "dgdf3.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dg_[a-z_0-9]+)\s*\(", src, flags=re.M)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dg3?_[a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
 def test_library_exports_every_declared_symbol(g):
     names = declared_functions()
     assert "dg_mesh_create" in names and "dg_rk3_step" in names and "dg_host_topology" in names
+    assert "dg3_mesh_create" in names and "dg3_rk3_step" in names
     L = g.lib()
     for n in names:
         assert hasattr(L, n), n
