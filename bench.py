@@ -584,7 +584,74 @@ def run_schemes(args):
                            "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
                            "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
     m.close()
+    # three dimensions (closed tetrahedral meshes, FP64): the ABC flow on the periodic cube
+    # [0, 2 pi]^3 cut into Kuhn tetrahedra, BDM_2, block-Jacobi PCG
+    from synth.mesh3 import abc_flow, kuhn_cube_mesh, sample_lattice3
+    N3, k3, nu3 = max(2, (args.n or 128) // 8), 2, 1e-3
+    vid, X = kuhn_cube_mesh(N3)
+    vals = sample_lattice3(abc_flow(), X, k3)
+    h3 = 2 * np.pi / N3
+    vmax = float(np.sqrt((vals ** 2).sum(-1)).max())
+    dt = min(0.1 * h3 / (k3 * k3 * vmax), 0.05 * h3 * h3 / (k3 ** 4 * nu3))
+    m3 = g.DGMesh3(vid, X, k3, nu3, stream=stream.cuda_stream)
+    m3.set_velocity(vals)
+    m3.project_divfree()
+    m3.rk3_step(dt, args.warmup)
+    torch.cuda.synchronize()
+    d0 = m3.diagnostics()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m3.rk3_step(dt, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    ms = total / args.steps
+    d1 = m3.diagnostics()
+    its = (d1["total_iters"] - d0["total_iters"]) / max(d1["solves"] - d0["solves"], 1)
+    # the stage kernel alone (MODE_RESIDUAL through dg3_eval_residual, lattice output included)
+    res = torch.empty((m3.n_tet, m3.n_lat, 3), dtype=torch.float64, device="cuda")
+    m3.eval_residual(res)
+    torch.cuda.synchronize()
+    rt = []
+    for _ in range(5):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m3.eval_residual(res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rt.append(e0.elapsed_time(e1))
+    rms = float(np.median(rt))
+    flops = stage3_flops_per_tet(k3) * m3.n_tet
+    nd3 = 3 * (k3 + 1) * (k3 + 2) * (k3 + 3) // 6
+    sm_mhz, sms = 2070.0, sm_count()
+    peak64 = 2 * sms * sm_mhz * 1e6 * 2 / 1e12
+    out["results"].append({"workload": "ABC flow, periodic cube [0,2pi]^3, %d^3 cubes x 6 Kuhn tetrahedra (%d), BDM_%d, "
+                                       "nu=%g, FP64, block-Jacobi PCG" % (N3, m3.n_tet, k3, nu3),
+                           "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
+                           "value": m3.n_tet * nd3 * 3 / (ms * 1e-3),
+                           "residual_kernel_ms": rms,
+                           "residual_kernel_fp64_tflops": flops / (rms * 1e-3) / 1e12,
+                           "fp64_peak_tflops": peak64,
+                           "peak_source": "derived: 2 FP64 FMA/clock/SM x %d SMs x 2070 MHz x 2 flops" % sms})
+    m3.close()
     print(json.dumps(out), flush=True)
+
+
+def stage3_flops_per_tet(k):
+    """Flops of the 3-D residual per tetrahedron (FMA = 2), counted from its loops: volume points
+    (3k+1)//2 cubed, each evaluating u and grad u (12 ns) and testing (9 ns) plus the flux (~40);
+    four faces of ((3k+2)//2)^2 points, each evaluating both traces and normal derivatives (18 ns)
+    and testing (9 ns) plus ~30."""
+    ns = (k + 1) * (k + 2) * (k + 3) // 6
+    nq = ((3 * k + 1) // 2) ** 3
+    nqf = ((3 * k + 2) // 2) ** 2
+    fma = nq * (21 * ns + 40) + 4 * nqf * (27 * ns + 30)
+    return 2 * fma
 
 
 def run_adjoint(args):
