@@ -585,7 +585,7 @@ def run_schemes(args):
                            "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
     m.close()
     # three dimensions (closed tetrahedral meshes, FP64): the ABC flow on the periodic cube
-    # [0, 2 pi]^3 cut into Kuhn tetrahedra, BDM_2, block-Jacobi PCG
+    # [0, 2 pi]^3 cut into Kuhn tetrahedra, BDM_2, multilevel PCG
     from synth.mesh3 import abc_flow, kuhn_cube_mesh, sample_lattice3
     N3, k3, nu3 = max(2, (args.n or 128) // 8), 2, 1e-3
     vid, X = kuhn_cube_mesh(N3)
@@ -631,7 +631,7 @@ def run_schemes(args):
     sm_mhz, sms = 2070.0, sm_count()
     peak64 = 2 * sms * sm_mhz * 1e6 * 2 / 1e12
     out["results"].append({"workload": "ABC flow, periodic cube [0,2pi]^3, %d^3 cubes x 6 Kuhn tetrahedra (%d), BDM_%d, "
-                                       "nu=%g, FP64, block-Jacobi PCG" % (N3, m3.n_tet, k3, nu3),
+                                       "nu=%g, FP64, multilevel PCG" % (N3, m3.n_tet, k3, nu3),
                            "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
                            "value": m3.n_tet * nd3 * 3 / (ms * 1e-3),
                            "residual_kernel_ms": rms,

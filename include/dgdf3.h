@@ -2,7 +2,7 @@
  * meshes (Sec. 2.1 with d = 3: BDM_k velocities, broken P^{k-1} pressures, P^k multipliers on the
  * triangular faces; the hybrid-mixed solve of eq. (12) after static condensation; the upwind
  * convection form eq. (7) and the SIPG viscous form eq. (18); SSP-RK3, eq. (8)). FP64 form,
- * block-Jacobi PCG on the face system, k = 1 or 2.
+ * multilevel (or block-Jacobi) PCG on the face system, k = 1 or 2.
  *
  * Conventions:
  * - local face e of a tetrahedron is the one opposite its vertex e; every face must be shared by
@@ -32,7 +32,11 @@ typedef struct dg_mesh3 dg_mesh3;
 /* Build a mesh: n_tet >= 1; tet_vertex_ids int64 [n_tet][4] (ids of the identified periodic
  * vertices), tet_coords double [n_tet][4][3] (unwrapped corners, positively oriented); host memory.
  * params as for dg_mesh_create: k in 1..2, nu >= 0, alpha > 0 (eq. (18)), precision must be
- * DG_PRECISION_FP64, cg_rtol / cg_maxit / cuda_stream as there; precond is ignored (block Jacobi).
+ * DG_PRECISION_FP64, cg_rtol / cg_maxit / cuda_stream as there. precond: DG_PRECOND_BLOCK_JACOBI
+ * gives block-Jacobi PCG; otherwise (the default) PCG with one V-cycle of a multilevel
+ * preconditioner per iteration: the assembled face operator with point-Jacobi Chebyshev(2)
+ * smoothing, injection to the face-constant multipliers, smoothed aggregation, a
+ * pseudo-inverse on the coarsest level (FP64, set up on the host at creation).
  * State starts at zero. Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED (k, precision,
  * a face with one side), DG_ERR_CUDA, DG_ERR_OOM. */
 int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords,

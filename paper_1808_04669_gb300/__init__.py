@@ -239,9 +239,10 @@ class DGMesh:
 
 class DGMesh3:
     """One closed tetrahedral mesh and its state (include/dgdf3.h: dg3_mesh_create ... dg3_mesh_destroy),
-    FP64, k = 1 or 2."""
+    FP64, k = 1 or 2; multilevel PCG by default, block Jacobi with precond=PRECOND_BLOCK_JACOBI."""
 
-    def __init__(self, tet_vertex_ids, tet_coords, k, nu, alpha=2.0, cg_rtol=1e-13, cg_maxit=20000, stream=None):
+    def __init__(self, tet_vertex_ids, tet_coords, k, nu, alpha=2.0, cg_rtol=1e-13, cg_maxit=20000, stream=None,
+                 precond=PRECOND_AUTO):
         L = lib()
         vid = np.ascontiguousarray(tet_vertex_ids, dtype=np.int64)
         X = np.ascontiguousarray(tet_coords, dtype=np.float64)
@@ -254,7 +255,7 @@ class DGMesh3:
             except Exception:
                 stream = 0
         self.params = DGParams(int(k), float(nu), float(alpha), FP64, float(cg_rtol), int(cg_maxit),
-                               ctypes.c_void_p(int(stream)), PRECOND_BLOCK_JACOBI)
+                               ctypes.c_void_p(int(stream)), int(precond))
         h = ctypes.c_void_p()
         check(L.dg3_mesh_create(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
                                 ctypes.byref(self.params), ctypes.byref(h)), "dg3_mesh_create")

@@ -8,6 +8,7 @@
 #include "../../include/dgdf.h"
 #include "../../include/dgdf3.h"
 #include "device3.cuh"
+#include "multilevel.hpp"
 #include "setup3.hpp"
 
 namespace dgdf {
@@ -22,6 +23,9 @@ struct dg_mesh3 {
   cudaStream_t stream = nullptr;
   std::vector<void*> allocs;
   int solver_blocks = 1;
+  bool use_ml = false;            // multilevel PCG (k_solve3_ml), else block Jacobi (k_solve3)
+  int ml_blocks = 1;
+  dgdf::DevMesh mv{};             // the hierarchy and the PCG vectors for the multilevel kernel
   bool has_lam = false;
   double last_c = 0.0;
   double* lattice = nullptr;          // [n_tet][ns][3] staging
@@ -84,7 +88,9 @@ int solve3(dg_mesh3* M, double warm_scale) {
   a.warm_scale = warm_scale;
   a.rtol = M->p.cg_rtol;
   a.maxit = M->p.cg_maxit;
-  CK3(dgdf::launch_solve3(M->dm, a, M->solver_blocks, M->stream));
+  a.floor_rtol = 1e-9;
+  if (M->use_ml) CK3(dgdf::launch_solve3_ml(M->dm, M->mv, a, M->ml_blocks, M->stream));
+  else CK3(dgdf::launch_solve3(M->dm, a, M->solver_blocks, M->stream));
   return DG_OK;
 }
 
@@ -179,6 +185,61 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
   if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
   if (e != cudaSuccess) return cleanup(api_fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
   M->solver_blocks = dgdf::solver3_blocks(d);
+  // multilevel preconditioner (default; DG_PRECOND_BLOCK_JACOBI keeps block Jacobi): the face
+  // operator assembled as CSR, point-Jacobi Chebyshev smoothing, injection to the face-constant
+  // multipliers, smoothed aggregation (multilevel.hpp, build_multilevel_csr); FP64
+  if (p.precond != DG_PRECOND_BLOCK_JACOBI) {
+    dgdf::CsrHost A0 = dgdf::stencil_csr(d.n_face, hm.nl, 6, hm.face_stencil.data(), hm.face_nbr.data(),
+                                         hm.stencil_blocks.data());
+    dgdf::MLHost mlh;
+    std::string merr;
+    if ((rc = dgdf::build_multilevel_csr(A0, hm.nl, mlh, merr))) return cleanup(api_fail(rc, merr));
+    std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
+    for (size_t l = 0; l < mlh.lv.size(); ++l) {
+      const dgdf::MLHostLevel& H = mlh.lv[l];
+      dgdf::MLLevelDev& L = lv[l];
+      L.stencil = 0;
+      L.bs = 1;
+      L.n = H.n;
+      L.inject = 0;
+      L.n_next = H.n_next;
+      L.bs_next = 1;
+      L.modes = l == 0 ? hm.nl : 1;
+      L.c0 = H.cheb[0];
+      L.c1 = H.cheb[1];
+      L.c2 = H.cheb[2];
+      if ((rc = upload3(M, &L.binv, H.binv)) || (rc = upload3(M, &L.a_rp, H.A.rp)) ||
+          (rc = upload3(M, &L.a_ci, H.A.ci)) || (rc = upload3(M, &L.a_v, H.A.v)) ||
+          (rc = upload3(M, &L.p_rp, H.P.rp)) || (rc = upload3(M, &L.p_ci, H.P.ci)) ||
+          (rc = upload3(M, &L.p_v, H.P.v)) || (rc = upload3(M, &L.r_rp, H.R.rp)) ||
+          (rc = upload3(M, &L.r_ci, H.R.ci)) || (rc = upload3(M, &L.r_v, H.R.v)))
+        return cleanup(rc);
+      if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
+        L.b = d.r;
+        L.x = d.z;
+      } else if ((rc = dalloc3(M, &L.b, size_t(H.n))) || (rc = dalloc3(M, &L.x, size_t(H.n)))) {
+        return cleanup(rc);
+      }
+      if ((rc = dalloc3(M, &L.r, size_t(H.n))) || (rc = dalloc3(M, &L.d, size_t(H.n)))) return cleanup(rc);
+    }
+    dgdf::DevMesh& v = M->mv;
+    const dgdf::MLLevelDev* lvd = nullptr;
+    if ((rc = upload3(M, &lvd, lv)) || (rc = upload3(M, &v.ml_cpinv, mlh.cpinv)) ||
+        (rc = dalloc3(M, &v.ml_xc, size_t(mlh.nc))) || (rc = dalloc3(M, &v.ml_bc, size_t(mlh.nc))))
+      return cleanup(rc);
+    v.ml_lv = lvd;
+    v.ml_nlev = int(lv.size());
+    v.ml_nc = mlh.nc;
+    v.k = d.k;
+    v.n_facet = d.n_face;
+    v.r = d.r;
+    v.z = d.z;
+    v.red = d.red;
+    v.bar = d.bar;
+    v.stats = d.stats;
+    M->use_ml = true;
+    M->ml_blocks = dgdf::solver3_ml_blocks(d);
+  }
   *out = M;
   return DG_OK;
 }

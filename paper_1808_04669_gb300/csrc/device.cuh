@@ -53,6 +53,8 @@ struct MLLevelT {
   int bs, n;          // values per row, rows
   int inject;         // 1: transfer to the next level keeps the leading bs_next modes (same facet rows)
   int n_next, bs_next;
+  int modes;          // CSR level 0 of an assembled hierarchy: values per face (row i is mode i % modes);
+                      // 0 or 1 otherwise
   const R* binv;      // stencil: [n_stencil][bs][bs]; CSR: [n] 1 / a_ii
   const int32_t *a_rp, *a_ci;
   const R* a_v;

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "device3.cuh"
 #include "kcommon.cuh"
 #include "multilevel.hpp"
 #include "solver_common.cuh"
@@ -294,14 +295,31 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelT<R>* lv, double (&red)
     // [R] x += d + c1 d + c2 B (r - A d); inject into the finer level (same facet rows)
     const MLLevelT<R>* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
     if (!L.stencil) {
-      // a CSR level (never level 0, never below an injecting level)
+      // a CSR level (never below an injecting level); level 0 of an assembled hierarchy is one
+      // too, with one row per face mode: it writes the output z and accumulates the PCG scalars
+      const int modes = L.modes > 1 ? L.modes : 1;
+      double part[3] = {0.0, 0.0, 0.0};
       rows_grouped<R>(
           L.n, [&](int i, int lane, int G) { return csr_part<R>(L.a_rp, L.a_ci, L.a_v, L.d, i, lane, G); },
           [&](int i, R y) {
             const R t = __ldg(&L.binv[i]) * (__ldcg(&L.r[i]) - y);
             const R d = __ldcg(&L.d[i]);
-            L.x[i] = __ldcg(&L.x[i]) + d + L.c1 * d + L.c2 * t;
+            const R x = __ldcg(&L.x[i]) + d + L.c1 * d + L.c2 * t;
+            L.x[i] = x;
+            if (l == 0) {
+              const double z = double(x);
+              if constexpr (!std::is_same<R, double>::value) m.z[i] = z;
+              const double b = __ldcg(&m.r[i]);
+              part[0] += b * z;
+              part[1] += b * b;
+              if (i % modes == 0) part[2] += b;
+            }
           });
+      if (l == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) red[j] += part[j];
+        continue;   // the caller's reduction is the closing barrier
+      }
       if (!grid_sync(bar, m.stats)) return false;
       continue;
     }
@@ -504,6 +522,175 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
   }
 }
 
+// y = (S x)_f on the face stencil of the three-dimensional path (seven blocks), with
+// x = a + beta b (b NULL: x = a)
+template <int NL>
+__device__ __forceinline__ void spmv3_ml(const DevMesh3& m3, int f, const double* a, const double* b, double beta,
+                                         double (&y)[NL]) {
+  const double* blk = m3.st_blk + size_t(__ldg(&m3.face_stencil[f])) * 7 * NL * NL;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) y[i] = 0.0;
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const int g = s == 0 ? f : __ldg(&m3.face_nbr[size_t(f) * 6 + s - 1]);
+    double xs[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const size_t o = size_t(g) * NL + j;
+      xs[j] = b ? __ldcg(&a[o]) + beta * __ldcg(&b[o]) : __ldcg(&a[o]);
+    }
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) y[i] += __ldg(&blk[(s * NL + i) * NL + j]) * xs[j];
+  }
+}
+
+// Face-system solve of the three-dimensional path with the multilevel preconditioner of an
+// assembled hierarchy (multilevel.hpp, build_multilevel_csr): FP64 PCG as in k_solve_ml, with
+// the face stencil of m3 (seven blocks) for S and g assembled from both sides' G f (canonical
+// face basis: no orientation signs). mv carries the hierarchy and the PCG vectors r and z, the
+// reduction slots, the barrier and the counters (the same buffers as m3's).
+template <int K>
+__global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh mv, SolveArgs a) {
+  constexpr int NL = (K + 1) * (K + 2) / 2, L4 = 4 * NL;
+  __shared__ MLLevelDev lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < mv.ml_nlev; l += blockDim.x) lv[l] = mv.ml_lv[l];
+  __syncthreads();
+  const int nF = m3.n_face;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  GridBar* bar = mv.bar;
+  double gg[2] = {0.0, 0.0};
+  for (int f = gtid; f < nF; f += gsz) {
+    const int t0 = m3.face_tet[size_t(f) * 2], t1 = m3.face_tet[size_t(f) * 2 + 1];
+    const int e0 = m3.face_loc[size_t(f) * 2], e1 = m3.face_loc[size_t(f) * 2 + 1];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const double v = m3.gl[size_t(t0) * L4 + e0 * NL + j] + m3.gl[size_t(t1) * L4 + e1 * NL + j];
+      const size_t o = size_t(f) * NL + j;
+      m3.g[o] = v;
+      m3.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m3.lam[o];
+      gg[0] += v * v;
+      if (j == 0) gg[1] += v;
+    }
+  }
+  if (!grid_reduce<2>(mv, 4, gg, bar)) return;
+  const double inv_nf = 1.0 / double(nF);   // closed mesh: the constant multiplier is the kernel of S
+  const double c0 = gg[1] * inv_nf;
+  const double gnorm = sqrt(fmax(gg[0] - gg[1] * gg[1] * inv_nf, 0.0));
+  const double stop = a.rtol * gnorm;
+  int it = 0;
+  bool conv = false;
+  double rr = 0.0;
+  if (gnorm == 0.0) {
+    for (int f = gtid; f < nF; f += gsz)
+#pragma unroll
+      for (int j = 0; j < NL; ++j) m3.lam[size_t(f) * NL + j] = 0.0;
+    conv = true;
+  } else {
+    // r = g - c0 1 - S lam, kept in the range of S (its mode-0 mean removed before every
+    // V-cycle, as in k_solve_ml), then the first Chebyshev step on every row of level 0
+    for (int f = gtid; f < nF; f += gsz) m3.g[size_t(f) * NL] -= c0;
+    if (!grid_sync(bar, mv.stats)) return;
+    double r0s[1] = {0.0};
+    for (int f = gtid; f < nF; f += gsz) {
+      double y[NL];
+      spmv3_ml<NL>(m3, f, m3.lam, nullptr, 0.0, y);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) mv.r[size_t(f) * NL + j] = m3.g[size_t(f) * NL + j] - y[j];
+      r0s[0] += mv.r[size_t(f) * NL];
+    }
+    if (!grid_reduce<1>(mv, 0, r0s, bar)) return;
+    for (int f = gtid; f < nF; f += gsz) {
+      mv.r[size_t(f) * NL] -= r0s[0] * inv_nf;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) ml_row_first_step<1, double>(mv, lv[0], f * NL + j);
+    }
+    if (!grid_sync(bar, mv.stats)) return;
+    double red[3] = {0.0, 0.0, 0.0};
+    if (!ml_vcycle<1, double>(mv, lv, red)) return;
+    if (!grid_reduce<3>(mv, 1, red, bar)) return;
+    double rho = red[0];
+    rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
+    double rsum = red[2];
+    double beta = 0.0;
+    double* pold = m3.pa;
+    double* pnew = m3.pb;
+    double best = rr;
+    int stall = 0;
+    for (;; ++it) {
+      if (!isfinite(rr) || !isfinite(rho)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&mv.stats->flags, kFlagNonFinite);
+        break;
+      }
+      if (sqrt(rr) <= stop) {
+        conv = true;
+        break;
+      }
+      if (rr < 0.25 * best) {
+        best = rr;
+        stall = 0;
+      } else if (++stall >= 10) {
+        conv = sqrt(best) <= a.floor_rtol * gnorm;
+        break;
+      }
+      if (it >= a.maxit) break;
+      // p_new = z + beta p_old, q = S p_new; reduce p.q and the mode-0 sum of q
+      double pq[2] = {0.0, 0.0};
+      for (int f = gtid; f < nF; f += gsz) {
+        double y[NL];
+        spmv3_ml<NL>(m3, f, mv.z, it == 0 ? nullptr : pold, beta, y);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(f) * NL + j;
+          const double p = it == 0 ? __ldcg(&mv.z[o]) : __ldcg(&mv.z[o]) + beta * __ldcg(&pold[o]);
+          pnew[o] = p;
+          m3.q[o] = y[j];
+          pq[0] += p * y[j];
+        }
+        pq[1] += y[0];
+      }
+      if (!grid_reduce<2>(mv, 6, pq, bar)) return;
+      if (!(pq[0] > 0.0)) {
+        if (!isfinite(pq[0]) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&mv.stats->flags, kFlagNonFinite);
+        break;
+      }
+      const double alpha = rho / pq[0];
+      const double cmean = (rsum - alpha * pq[1]) * inv_nf;
+      for (int f = gtid; f < nF; f += gsz) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const size_t o = size_t(f) * NL + j;
+          m3.lam[o] += alpha * pnew[o];
+          mv.r[o] -= alpha * m3.q[o] + (j == 0 ? cmean : 0.0);
+          ml_row_first_step<1, double>(mv, lv[0], f * NL + j);
+        }
+      }
+      if (!grid_sync(bar, mv.stats)) return;
+      double red2[3] = {0.0, 0.0, 0.0};
+      if (!ml_vcycle<1, double>(mv, lv, red2)) return;
+      if (!grid_reduce<3>(mv, 1, red2, bar)) return;
+      beta = red2[0] / rho;
+      rho = red2[0];
+      rr = fmax(red2[1] - red2[2] * red2[2] * inv_nf, 0.0);
+      rsum = red2[2];
+      double* t = pold;
+      pold = pnew;
+      pnew = t;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats* st = mv.stats;
+    st->last_iters = it;
+    st->total_iters += it;
+    st->solves += 1;
+    st->last_relres = gnorm > 0.0 ? sqrt(rr) / gnorm : 0.0;
+    st->last_sweeps = 1;
+    st->total_sweeps += 1;
+    if (!conv) atomicOr(&st->flags, kFlagNotConverged);
+  }
+}
+
 // One V-cycle z = M r on its own (test hook dg_test_multilevel_apply): r and z are facet-major
 // [n_facet][k+1] in device memory. Uses the solver's level-0 vectors m.r and m.z.
 template <int K, typename R>
@@ -576,6 +763,35 @@ int solver_ml_blocks(const DevMesh& m) {
   if (nb > need) nb = need;
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
   return nb < 1 ? 1 : nb;
+}
+
+int solver3_ml_blocks(const DevMesh3& m) {
+  const void* fn = m.k == 1 ? (const void*)k_solve3_ml<1> : (const void*)k_solve3_ml<2>;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMLThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = per_sm * sms;
+  if (nb > 2 * sms) nb = 2 * sms;
+  const int need = (m.n_face * ((m.k + 1) * (m.k + 2) / 2) + kMLThreads - 1) / kMLThreads;
+  if (nb > need) nb = need;
+  if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
+  return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_solve3_ml(const DevMesh3& m, const DevMesh& mv, const SolveArgs& a, int nblocks, cudaStream_t s) {
+  if (!mv.ml_lv || mv.ml_nlev < 1 || mv.ml_nlev > kMLMaxLevels || (m.k != 1 && m.k != 2)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(mv.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  DevMesh3 mm = m;
+  DevMesh vv = mv;
+  SolveArgs aa = a;
+  void* args[] = {&mm, &vv, &aa};
+  const void* fn = m.k == 1 ? (const void*)k_solve3_ml<1> : (const void*)k_solve3_ml<2>;
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kMLThreads), args, 0, s);
 }
 
 cudaError_t launch_solve_ml(const DevMesh& m, const SolveArgs& a, int nblocks, cudaStream_t s) {

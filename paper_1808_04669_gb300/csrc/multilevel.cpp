@@ -503,6 +503,130 @@ int build_multilevel(const HostMesh& hm, MLHost& ml, std::string& err) {
   return DG_OK;
 }
 
+CsrHost stencil_csr(int n, int nl, int nb, const int32_t* cls, const int32_t* nbr, const double* blocks) {
+  CsrHost A;
+  A.n_rows = A.n_cols = n * nl;
+  A.rp.assign(size_t(n) * nl + 1, 0);
+  std::vector<int32_t> cols;
+  std::vector<double> vals;
+  for (int f = 0; f < n; ++f) {
+    const double* blk = blocks + size_t(cls[f]) * (1 + nb) * nl * nl;
+    for (int i = 0; i < nl; ++i) {
+      cols.clear();
+      vals.clear();
+      for (int b = 0; b <= nb; ++b) {
+        const int g = b == 0 ? f : nbr[size_t(f) * nb + b - 1];
+        for (int j = 0; j < nl; ++j) {
+          const int c = g * nl + j;
+          const double v = blk[(size_t(b) * nl + i) * nl + j];
+          size_t q = 0;
+          while (q < cols.size() && cols[q] != c) ++q;
+          if (q == cols.size()) {
+            cols.push_back(c);
+            vals.push_back(v);
+          } else {
+            vals[q] += v;
+          }
+        }
+      }
+      A.ci.insert(A.ci.end(), cols.begin(), cols.end());
+      A.v.insert(A.v.end(), vals.begin(), vals.end());
+      A.rp[size_t(f) * nl + i + 1] = int32_t(A.ci.size());
+    }
+  }
+  return A;
+}
+
+int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err) {
+  ml = MLHost();
+  if (A0.n_rows % nl) {
+    err = "multilevel: operator size is not a multiple of the modes per face";
+    return DG_ERR_INVALID_ARG;
+  }
+  const int nf = A0.n_rows / nl;
+  auto diag_inv = [](const CsrHost& A) {
+    std::vector<double> d(A.n_rows, 0.0);
+    for (int r = 0; r < A.n_rows; ++r)
+      for (int p = A.rp[r]; p < A.rp[r + 1]; ++p)
+        if (A.ci[p] == r) d[r] += A.v[p];
+    for (double& v : d) v = 1.0 / v;
+    return d;
+  };
+  // level 0: all modes, transferred to the face-constant multipliers (mode 0) by injection
+  MLHostLevel L0;
+  L0.stencil = false;
+  L0.bs = 1;
+  L0.n = A0.n_rows;
+  L0.A = A0;
+  L0.binv = diag_inv(A0);
+  L0.P.n_rows = A0.n_rows;
+  L0.P.n_cols = nf;
+  L0.P.rp.assign(A0.n_rows + 1, 0);
+  for (int i = 0; i < A0.n_rows; ++i) {
+    if (i % nl == 0) {
+      L0.P.ci.push_back(i / nl);
+      L0.P.v.push_back(1.0);
+    }
+    L0.P.rp[i + 1] = int32_t(L0.P.ci.size());
+  }
+  L0.R = transpose(L0.P);
+  L0.n_next = nf;
+  CsrHost A = spgemm(L0.R, spgemm(A0, L0.P));
+  ml.lv.push_back(std::move(L0));
+  // h-levels: smoothed aggregation on the mode-0 operator
+  Vec nn(nf, 1.0), nn_next;
+  while (A.n_rows > kMLCoarseMax && int(ml.lv.size()) < kMLMaxLevels) {
+    CsrHost P = sa_prolongator(A, nn, nn_next);
+    if (P.n_cols >= A.n_rows) break;
+    MLHostLevel L;
+    L.stencil = false;
+    L.bs = 1;
+    L.n = A.n_rows;
+    L.binv = diag_inv(A);
+    L.R = transpose(P);
+    L.n_next = P.n_cols;
+    CsrHost Ac = spgemm(L.R, spgemm(A, P));
+    L.A = std::move(A);
+    L.P = std::move(P);
+    ml.lv.push_back(std::move(L));
+    A = std::move(Ac);
+    nn.swap(nn_next);
+  }
+  const int nc = A.n_rows;
+  if (nc > 4 * kMLCoarseMax) {
+    err = "multilevel: coarsening stalled";
+    return DG_ERR_UNSUPPORTED;
+  }
+  std::vector<double> D(size_t(nc) * nc, 0.0), ev, V;
+  for (int r = 0; r < nc; ++r)
+    for (int p = A.rp[r]; p < A.rp[r + 1]; ++p) D[size_t(r) * nc + A.ci[p]] += A.v[p];
+  for (int r = 0; r < nc; ++r)
+    for (int c = r + 1; c < nc; ++c) {
+      const double s = 0.5 * (D[size_t(r) * nc + c] + D[size_t(c) * nc + r]);
+      D[size_t(r) * nc + c] = D[size_t(c) * nc + r] = s;
+    }
+  symmetric_eigen(D, nc, ev, V);
+  double emax = 0.0;
+  for (double e : ev) emax = std::max(emax, std::fabs(e));
+  ml.nc = nc;
+  ml.cpinv.assign(size_t(nc) * nc, 0.0);
+  for (int i = 0; i < nc; ++i) {
+    if (!(ev[i] > 1e-10 * emax)) continue;
+    const double inv = 1.0 / ev[i];
+    for (int r = 0; r < nc; ++r)
+      for (int c = 0; c < nc; ++c) ml.cpinv[size_t(r) * nc + c] += V[size_t(r) * nc + i] * inv * V[size_t(c) * nc + i];
+  }
+  ml.lv.back().n_next = nc;
+  const HostMesh none;
+  for (MLHostLevel& L : ml.lv) {
+    auto aA = [&](const double* x, double* y) { level_apply(none, L, x, y); };
+    auto aB = [&](const double* x, double* y) { level_binv(none, L, x, y); };
+    L.lmax = lanczos_lmax(L.n, aA, aB, 30);
+    set_chebyshev(L);
+  }
+  return DG_OK;
+}
+
 void multilevel_apply_host(const HostMesh& hm, const MLHost& ml, const double* r, double* z) {
   vcycle(hm, ml, 0, r, z);
 }

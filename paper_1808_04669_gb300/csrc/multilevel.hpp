@@ -61,6 +61,16 @@ struct MLHost {
 // Builds the hierarchy from hm's facet stencil. Returns 0 or a dg_status code.
 int build_multilevel(const HostMesh& hm, MLHost& ml, std::string& err);
 
+// The same hierarchy from an assembled operator A0 (CSR, nl values per face, face-major) with
+// point-Jacobi smoothing on every level: level 0 keeps all modes and transfers to the
+// face-constant multipliers (mode 0) by injection, then smoothed aggregation as above. Used for
+// the face system of the three-dimensional path.
+int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err);
+
+// A block stencil operator as CSR: row block f couples to itself and to nbr[f][0..nb) through
+// blocks[cls[f]][1 + nb][nl][nl] (slot 0 its own block); duplicate columns are merged.
+CsrHost stencil_csr(int n, int nl, int nb, const int32_t* cls, const int32_t* nbr, const double* blocks);
+
 // z = M r for one V-cycle, on the host (the reference of the device kernel);
 // r and z hold n_facet (k+1) values.
 void multilevel_apply_host(const HostMesh& hm, const MLHost& ml, const double* r, double* z);

@@ -53,12 +53,13 @@ def test_residual_parity(g, N, k, nu):
     assert rel(m.eval_residual(), ref) < TOL
 
 
-@pytest.mark.parametrize("N,k", [(2, 1), (2, 2), (3, 2)])
-def test_projection_parity(g, N, k):
+@pytest.mark.parametrize("N,k,precond", [(2, 1, 0), (2, 2, 0), (3, 2, 0), (2, 1, 1), (3, 2, 1)])
+def test_projection_parity(g, N, k, precond):
+    # multilevel (default) and block-Jacobi PCG
     vid, X = kuhn_cube_mesh(N)
     d = Discretization3(vid, X, k, 0.0)
     v = field(X, k, 20 + N)
-    m = g.DGMesh3(vid, X, k, 0.0)
+    m = g.DGMesh3(vid, X, k, 0.0, precond=precond)
     m.set_velocity(v)
     m.project_divfree()
     ref = d.to_lattice(d.project(d.from_lattice(v)))
@@ -67,14 +68,14 @@ def test_projection_parity(g, N, k):
     assert dg["max_div"] < 1e-11 and dg["max_jump"] < 1e-11
 
 
-@pytest.mark.parametrize("N,k,nu", [(2, 1, 0.01), (2, 2, 0.01), (3, 2, 1e-3)])
-def test_rk3_parity(g, N, k, nu):
+@pytest.mark.parametrize("N,k,nu,precond", [(2, 1, 0.01, 0), (2, 2, 0.01, 0), (3, 2, 1e-3, 0), (3, 2, 1e-3, 1)])
+def test_rk3_parity(g, N, k, nu, precond):
     vid, X = kuhn_cube_mesh(N)
     d = Discretization3(vid, X, k, nu)
     v = field(X, k, 30 + N, noise=0.1)
     dt = 0.3 * (2 * np.pi / N) / (k * k * np.abs(v).max())
     U = d.rk3_step(d.project(d.from_lattice(v)), dt, 3)
-    m = g.DGMesh3(vid, X, k, nu)
+    m = g.DGMesh3(vid, X, k, nu, precond=precond)
     m.set_velocity(v)
     m.project_divfree()
     m.rk3_step(dt, 3)
@@ -111,3 +112,21 @@ def test_arguments_rejected(g):
     with pytest.raises(g.DGError) as e:
         g.DGMesh3(ids, X1[sel], 1, 0.0)
     assert e.value.code in (-2, -3)
+
+
+def test_multilevel_iterations_stay_flat_on_16_cubes(g):
+    # 16^3 Kuhn cubes, BDM_2: the multilevel PCG needs a few dozen iterations per projection, block
+    # Jacobi several hundred, and both give the same projection
+    k = 2
+    vid, X = kuhn_cube_mesh(16)
+    v = field(X, k, 3)
+    out = {}
+    for pc in (g.PRECOND_AUTO, g.PRECOND_BLOCK_JACOBI):
+        m = g.DGMesh3(vid, X, k, 0.0, precond=pc)
+        m.set_velocity(v)
+        m.project_divfree()
+        out[pc] = (m.get_velocity(), m.diagnostics())
+    (a, da), (b, db) = out[g.PRECOND_AUTO], out[g.PRECOND_BLOCK_JACOBI]
+    assert da["last_iters"] <= 60 and db["last_iters"] > 4 * da["last_iters"], (da, db)
+    assert rel(a, b) < 1e-11
+    assert da["max_div"] < 1e-10 and da["max_jump"] < 1e-10
