@@ -34,9 +34,9 @@ typedef struct dg_mesh3 dg_mesh3;
  * params as for dg_mesh_create: k in 1..2, nu >= 0, alpha > 0 (eq. (18)), precision must be
  * DG_PRECISION_FP64, cg_rtol / cg_maxit / cuda_stream as there. precond: DG_PRECOND_BLOCK_JACOBI
  * gives block-Jacobi PCG; otherwise (the default) PCG with one V-cycle of a multilevel
- * preconditioner per iteration: the assembled face operator with point-Jacobi Chebyshev(2)
- * smoothing, injection to the face-constant multipliers, smoothed aggregation, a
- * pseudo-inverse on the coarsest level (FP64, set up on the host at creation).
+ * preconditioner per iteration: block-Jacobi Chebyshev(2) smoothing on the face system, injection
+ * to the face-constant multipliers, smoothed aggregation on their operator with point-Jacobi
+ * smoothing, a pseudo-inverse on the coarsest level (FP64, set up on the host at creation).
  * State starts at zero. Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED (k, precision,
  * a face with one side), DG_ERR_CUDA, DG_ERR_OOM. */
 int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords,

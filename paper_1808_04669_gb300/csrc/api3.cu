@@ -185,42 +185,53 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
   if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
   if (e != cudaSuccess) return cleanup(api_fail(DG_ERR_CUDA, std::string("initialise: ") + cudaGetErrorString(e)));
   M->solver_blocks = dgdf::solver3_blocks(d);
-  // multilevel preconditioner (default; DG_PRECOND_BLOCK_JACOBI keeps block Jacobi): the face
-  // operator assembled as CSR, point-Jacobi Chebyshev smoothing, injection to the face-constant
-  // multipliers, smoothed aggregation (multilevel.hpp, build_multilevel_csr); FP64
+  // multilevel preconditioner (default; DG_PRECOND_BLOCK_JACOBI keeps block Jacobi): block-Jacobi
+  // Chebyshev smoothing on the face stencil, injection to the face-constant multipliers, smoothed
+  // aggregation with point-Jacobi smoothing on their assembled operator (multilevel.hpp,
+  // build_multilevel_csr); FP64
   if (p.precond != DG_PRECOND_BLOCK_JACOBI) {
     dgdf::CsrHost A0 = dgdf::stencil_csr(d.n_face, hm.nl, 6, hm.face_stencil.data(), hm.face_nbr.data(),
                                          hm.stencil_blocks.data());
     dgdf::MLHost mlh;
     std::string merr;
-    if ((rc = dgdf::build_multilevel_csr(A0, hm.nl, mlh, merr))) return cleanup(api_fail(rc, merr));
+    if ((rc = dgdf::build_multilevel_csr(A0, hm.nl, hm.face_stencil.data(), &hm.stencil_binv, mlh, merr)))
+      return cleanup(api_fail(rc, merr));
     std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
     for (size_t l = 0; l < mlh.lv.size(); ++l) {
       const dgdf::MLHostLevel& H = mlh.lv[l];
       dgdf::MLLevelDev& L = lv[l];
-      L.stencil = 0;
-      L.bs = 1;
+      L.stencil = H.stencil ? 1 : 0;
+      L.bs = H.bs;
       L.n = H.n;
-      L.inject = 0;
+      L.inject = H.inject ? 1 : 0;
       L.n_next = H.n_next;
-      L.bs_next = 1;
-      L.modes = l == 0 ? hm.nl : 1;
+      L.bs_next = H.bs_next;
+      L.modes = 1;
       L.c0 = H.cheb[0];
       L.c1 = H.cheb[1];
       L.c2 = H.cheb[2];
-      if ((rc = upload3(M, &L.binv, H.binv)) || (rc = upload3(M, &L.a_rp, H.A.rp)) ||
-          (rc = upload3(M, &L.a_ci, H.A.ci)) || (rc = upload3(M, &L.a_v, H.A.v)) ||
-          (rc = upload3(M, &L.p_rp, H.P.rp)) || (rc = upload3(M, &L.p_ci, H.P.ci)) ||
-          (rc = upload3(M, &L.p_v, H.P.v)) || (rc = upload3(M, &L.r_rp, H.R.rp)) ||
-          (rc = upload3(M, &L.r_ci, H.R.ci)) || (rc = upload3(M, &L.r_v, H.R.v)))
+      if ((rc = upload3(M, &L.binv, H.binv))) return cleanup(rc);
+      if (H.stencil) {   // level 0: block Jacobi on the seven-block face stencil
+        L.st_cls = d.face_stencil;
+        L.st_nbr = d.face_nbr;
+        L.st_nnb = 6;
+        L.st_blk = d.st_blk;
+      } else if ((rc = upload3(M, &L.a_rp, H.A.rp)) || (rc = upload3(M, &L.a_ci, H.A.ci)) ||
+                 (rc = upload3(M, &L.a_v, H.A.v))) {
         return cleanup(rc);
+      }
+      if (!H.inject && ((rc = upload3(M, &L.p_rp, H.P.rp)) || (rc = upload3(M, &L.p_ci, H.P.ci)) ||
+                        (rc = upload3(M, &L.p_v, H.P.v)) || (rc = upload3(M, &L.r_rp, H.R.rp)) ||
+                        (rc = upload3(M, &L.r_ci, H.R.ci)) || (rc = upload3(M, &L.r_v, H.R.v))))
+        return cleanup(rc);
+      const size_t nv = size_t(H.n) * H.bs;
       if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
         L.b = d.r;
         L.x = d.z;
-      } else if ((rc = dalloc3(M, &L.b, size_t(H.n))) || (rc = dalloc3(M, &L.x, size_t(H.n)))) {
+      } else if ((rc = dalloc3(M, &L.b, nv)) || (rc = dalloc3(M, &L.x, nv))) {
         return cleanup(rc);
       }
-      if ((rc = dalloc3(M, &L.r, size_t(H.n))) || (rc = dalloc3(M, &L.d, size_t(H.n)))) return cleanup(rc);
+      if ((rc = dalloc3(M, &L.r, nv)) || (rc = dalloc3(M, &L.d, nv))) return cleanup(rc);
     }
     dgdf::DevMesh& v = M->mv;
     const dgdf::MLLevelDev* lvd = nullptr;

@@ -64,6 +64,11 @@ struct MLLevelT {
   const R* r_v;
   R c0, c1, c2;       // Chebyshev(2) coefficients
   R *x, *b, *r, *d;   // work vectors [n * bs]
+  // a stencil level with a stencil of its own (NULL st_nbr: the facet stencil of the mesh):
+  // row i couples to itself and to st_nbr[i][0..st_nnb) through st_blk[st_cls[i]][1 + st_nnb][bs][bs]
+  const int32_t *st_cls, *st_nbr;
+  int st_nnb;
+  const R* st_blk;
 };
 using MLLevelDev = MLLevelT<double>;
 

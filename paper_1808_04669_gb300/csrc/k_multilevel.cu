@@ -86,6 +86,24 @@ __device__ __forceinline__ R csr_part(const int32_t* rp, const int32_t* ci, cons
 template <int NL, typename R>
 __device__ __forceinline__ void ml_row_apply(const DevMesh& m, const MLLevelT<R>& L, int i, const R* x,
                                              R (&y)[NL]) {
+  if (L.st_nbr) {
+    // the level's own stencil (all NL modes): slot 0 the row itself, then st_nnb neighbours
+    const int nnb = L.st_nnb;
+    const R* blk = L.st_blk + size_t(__ldg(&L.st_cls[i])) * (1 + nnb) * NL * NL;
+#pragma unroll
+    for (int ii = 0; ii < NL; ++ii) y[ii] = R(0);
+    for (int b = 0; b <= nnb; ++b) {
+      const int g = b == 0 ? i : __ldg(&L.st_nbr[size_t(i) * nnb + b - 1]);
+      R xs[NL];
+#pragma unroll
+      for (int jj = 0; jj < NL; ++jj) xs[jj] = __ldcg(&x[size_t(g) * NL + jj]);
+#pragma unroll
+      for (int ii = 0; ii < NL; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < NL; ++jj) y[ii] += __ldg(&blk[(b * NL + ii) * NL + jj]) * xs[jj];
+    }
+    return;
+  }
   const int bs = L.bs;
   const R* blk = MLOps<R>::blocks(m) + size_t(__ldg(&m.facet_stencil[i])) * 5 * NL * NL;
   int nb[5];
@@ -112,7 +130,7 @@ __device__ __forceinline__ void ml_row_binv(const DevMesh& m, const MLLevelT<R>&
                                             R (&out)[NL]) {
   if (L.stencil) {
     const int bs = L.bs;
-    const R* B = L.binv + size_t(__ldg(&m.facet_stencil[i])) * bs * bs;
+    const R* B = L.binv + size_t(__ldg(L.st_cls ? &L.st_cls[i] : &m.facet_stencil[i])) * bs * bs;
 #pragma unroll
     for (int ii = 0; ii < NL; ++ii) {
       R s = R(0);
@@ -295,8 +313,9 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelT<R>* lv, double (&red)
     // [R] x += d + c1 d + c2 B (r - A d); inject into the finer level (same facet rows)
     const MLLevelT<R>* F = l > 0 && lv[l - 1].inject ? &lv[l - 1] : nullptr;
     if (!L.stencil) {
-      // a CSR level (never below an injecting level); level 0 of an assembled hierarchy is one
-      // too, with one row per face mode: it writes the output z and accumulates the PCG scalars
+      // a CSR level; below an injecting level its rows are the finer level's rows (faces) and its
+      // result goes into their mode 0. Level 0 of an assembled hierarchy is CSR too, with one
+      // row per face mode: it writes the output z and accumulates the PCG scalars
       const int modes = L.modes > 1 ? L.modes : 1;
       double part[3] = {0.0, 0.0, 0.0};
       rows_grouped<R>(
@@ -306,6 +325,7 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelT<R>* lv, double (&red)
             const R d = __ldcg(&L.d[i]);
             const R x = __ldcg(&L.x[i]) + d + L.c1 * d + L.c2 * t;
             L.x[i] = x;
+            if (F) F->x[size_t(i) * F->bs] += x;   // injected into the finer level's mode 0
             if (l == 0) {
               const double z = double(x);
               if constexpr (!std::is_same<R, double>::value) m.z[i] = z;
@@ -603,12 +623,11 @@ __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh m
     if (!grid_reduce<1>(mv, 0, r0s, bar)) return;
     for (int f = gtid; f < nF; f += gsz) {
       mv.r[size_t(f) * NL] -= r0s[0] * inv_nf;
-#pragma unroll
-      for (int j = 0; j < NL; ++j) ml_row_first_step<1, double>(mv, lv[0], f * NL + j);
+      ml_row_first_step<NL, double>(mv, lv[0], f);
     }
     if (!grid_sync(bar, mv.stats)) return;
     double red[3] = {0.0, 0.0, 0.0};
-    if (!ml_vcycle<1, double>(mv, lv, red)) return;
+    if (!ml_vcycle<NL, double>(mv, lv, red)) return;
     if (!grid_reduce<3>(mv, 1, red, bar)) return;
     double rho = red[0];
     rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
@@ -663,12 +682,12 @@ __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh m
           const size_t o = size_t(f) * NL + j;
           m3.lam[o] += alpha * pnew[o];
           mv.r[o] -= alpha * m3.q[o] + (j == 0 ? cmean : 0.0);
-          ml_row_first_step<1, double>(mv, lv[0], f * NL + j);
         }
+        ml_row_first_step<NL, double>(mv, lv[0], f);
       }
       if (!grid_sync(bar, mv.stats)) return;
       double red2[3] = {0.0, 0.0, 0.0};
-      if (!ml_vcycle<1, double>(mv, lv, red2)) return;
+      if (!ml_vcycle<NL, double>(mv, lv, red2)) return;
       if (!grid_reduce<3>(mv, 1, red2, bar)) return;
       beta = red2[0] / rho;
       rho = red2[0];

@@ -537,7 +537,8 @@ CsrHost stencil_csr(int n, int nl, int nb, const int32_t* cls, const int32_t* nb
   return A;
 }
 
-int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err) {
+int build_multilevel_csr(const CsrHost& A0, int nl, const int32_t* cls, const std::vector<double>* cls_binv,
+                         MLHost& ml, std::string& err) {
   ml = MLHost();
   if (A0.n_rows % nl) {
     err = "multilevel: operator size is not a multiple of the modes per face";
@@ -552,27 +553,59 @@ int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err
     for (double& v : d) v = 1.0 / v;
     return d;
   };
-  // level 0: all modes, transferred to the face-constant multipliers (mode 0) by injection
-  MLHostLevel L0;
-  L0.stencil = false;
-  L0.bs = 1;
-  L0.n = A0.n_rows;
-  L0.A = A0;
-  L0.binv = diag_inv(A0);
-  L0.P.n_rows = A0.n_rows;
-  L0.P.n_cols = nf;
-  L0.P.rp.assign(A0.n_rows + 1, 0);
+  // injection of the face-constant multipliers (mode 0 of every face)
+  CsrHost Pm;
+  Pm.n_rows = A0.n_rows;
+  Pm.n_cols = nf;
+  Pm.rp.assign(A0.n_rows + 1, 0);
   for (int i = 0; i < A0.n_rows; ++i) {
     if (i % nl == 0) {
-      L0.P.ci.push_back(i / nl);
-      L0.P.v.push_back(1.0);
+      Pm.ci.push_back(i / nl);
+      Pm.v.push_back(1.0);
     }
-    L0.P.rp[i + 1] = int32_t(L0.P.ci.size());
+    Pm.rp[i + 1] = int32_t(Pm.ci.size());
   }
-  L0.R = transpose(L0.P);
-  L0.n_next = nf;
-  CsrHost A = spgemm(L0.R, spgemm(A0, L0.P));
-  ml.lv.push_back(std::move(L0));
+  const CsrHost Rm = transpose(Pm);
+  CsrHost A = spgemm(Rm, spgemm(A0, Pm));   // the mode-0 operator
+  // level 0: all modes; block Jacobi on the face stencil (cls given) or point Jacobi on the CSR rows
+  {
+    MLHostLevel L0;
+    L0.n_next = nf;
+    if (cls) {
+      L0.stencil = true;
+      L0.bs = nl;
+      L0.n = nf;
+      L0.binv = *cls_binv;
+      L0.inject = true;
+      L0.bs_next = 1;
+    } else {
+      L0.stencil = false;
+      L0.bs = 1;
+      L0.n = A0.n_rows;
+      L0.A = A0;
+      L0.binv = diag_inv(A0);
+      L0.P = Pm;
+      L0.R = Rm;
+    }
+    auto aA = [&](const double* x, double* y) { csr_apply(A0, x, y); };
+    auto aB = [&](const double* x, double* y) {
+      if (!cls) {
+        for (int i = 0; i < A0.n_rows; ++i) y[i] = L0.binv[i] * x[i];
+        return;
+      }
+      for (int f = 0; f < nf; ++f) {
+        const double* B = &(*cls_binv)[size_t(cls[f]) * nl * nl];
+        for (int a = 0; a < nl; ++a) {
+          double v = 0.0;
+          for (int c = 0; c < nl; ++c) v += B[a * nl + c] * x[size_t(f) * nl + c];
+          y[size_t(f) * nl + a] = v;
+        }
+      }
+    };
+    L0.lmax = lanczos_lmax(A0.n_rows, aA, aB, 30);
+    set_chebyshev(L0);
+    ml.lv.push_back(std::move(L0));
+  }
   // h-levels: smoothed aggregation on the mode-0 operator
   Vec nn(nf, 1.0), nn_next;
   while (A.n_rows > kMLCoarseMax && int(ml.lv.size()) < kMLMaxLevels) {
@@ -588,6 +621,11 @@ int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err
     CsrHost Ac = spgemm(L.R, spgemm(A, P));
     L.A = std::move(A);
     L.P = std::move(P);
+    const HostMesh none;
+    auto aA = [&](const double* x, double* y) { level_apply(none, L, x, y); };
+    auto aB = [&](const double* x, double* y) { level_binv(none, L, x, y); };
+    L.lmax = lanczos_lmax(L.n, aA, aB, 30);
+    set_chebyshev(L);
     ml.lv.push_back(std::move(L));
     A = std::move(Ac);
     nn.swap(nn_next);
@@ -617,13 +655,6 @@ int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err
       for (int c = 0; c < nc; ++c) ml.cpinv[size_t(r) * nc + c] += V[size_t(r) * nc + i] * inv * V[size_t(c) * nc + i];
   }
   ml.lv.back().n_next = nc;
-  const HostMesh none;
-  for (MLHostLevel& L : ml.lv) {
-    auto aA = [&](const double* x, double* y) { level_apply(none, L, x, y); };
-    auto aB = [&](const double* x, double* y) { level_binv(none, L, x, y); };
-    L.lmax = lanczos_lmax(L.n, aA, aB, 30);
-    set_chebyshev(L);
-  }
   return DG_OK;
 }
 

@@ -61,11 +61,15 @@ struct MLHost {
 // Builds the hierarchy from hm's facet stencil. Returns 0 or a dg_status code.
 int build_multilevel(const HostMesh& hm, MLHost& ml, std::string& err);
 
-// The same hierarchy from an assembled operator A0 (CSR, nl values per face, face-major) with
-// point-Jacobi smoothing on every level: level 0 keeps all modes and transfers to the
-// face-constant multipliers (mode 0) by injection, then smoothed aggregation as above. Used for
-// the face system of the three-dimensional path.
-int build_multilevel_csr(const CsrHost& A0, int nl, MLHost& ml, std::string& err);
+// The same hierarchy from an assembled operator A0 (CSR, nl values per face, face-major): level 0
+// keeps all modes and transfers to the face-constant multipliers (mode 0) by injection, then
+// smoothed aggregation as above with point-Jacobi smoothing. Level 0 smooths with block Jacobi
+// on its face stencil when cls (stencil class per face) and cls_binv ([class][nl][nl] inverses of
+// the own blocks) are given (a stencil level, applied by the device through the level's own
+// stencil pointers; the host V-cycle does not take it), else with point Jacobi on the CSR rows.
+// Used for the face system of the three-dimensional path.
+int build_multilevel_csr(const CsrHost& A0, int nl, const int32_t* cls, const std::vector<double>* cls_binv,
+                         MLHost& ml, std::string& err);
 
 // A block stencil operator as CSR: row block f couples to itself and to nbr[f][0..nb) through
 // blocks[cls[f]][1 + nb][nl][nl] (slot 0 its own block); duplicate columns are merged.
