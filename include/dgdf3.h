@@ -36,7 +36,8 @@ typedef struct dg_mesh3 dg_mesh3;
  * gives block-Jacobi PCG; otherwise (the default) PCG with one V-cycle of a multilevel
  * preconditioner per iteration: block-Jacobi Chebyshev(2) smoothing on the face system, injection
  * to the face-constant multipliers, smoothed aggregation on their operator with point-Jacobi
- * smoothing, a pseudo-inverse on the coarsest level (FP64, set up on the host at creation).
+ * smoothing, a pseudo-inverse on the coarsest level (set up on the host at creation; the V-cycle
+ * runs in FP32, the PCG vectors, S and the stopping test in FP64).
  * State starts at zero. Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED (k, precision,
  * a face with one side), DG_ERR_CUDA, DG_ERR_OOM. */
 int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords,

@@ -188,7 +188,7 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
   // multilevel preconditioner (default; DG_PRECOND_BLOCK_JACOBI keeps block Jacobi): block-Jacobi
   // Chebyshev smoothing on the face stencil, injection to the face-constant multipliers, smoothed
   // aggregation with point-Jacobi smoothing on their assembled operator (multilevel.hpp,
-  // build_multilevel_csr); FP64
+  // build_multilevel_csr)
   if (p.precond != DG_PRECOND_BLOCK_JACOBI) {
     dgdf::CsrHost A0 = dgdf::stencil_csr(d.n_face, hm.nl, 6, hm.face_stencil.data(), hm.face_nbr.data(),
                                          hm.stencil_blocks.data());
@@ -196,10 +196,16 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
     std::string merr;
     if ((rc = dgdf::build_multilevel_csr(A0, hm.nl, hm.face_stencil.data(), &hm.stencil_binv, mlh, merr)))
       return cleanup(api_fail(rc, merr));
-    std::vector<dgdf::MLLevelDev> lv(mlh.lv.size());
+    // the V-cycle runs in FP32 (a preconditioner needs no more; the PCG vectors and S stay FP64):
+    // level operators, transfers, Chebyshev coefficients and the coarsest pseudo-inverse rounded
+    // once; level 0 has vectors of its own, filled from r and written back to z
+    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    std::vector<dgdf::MLLevelT<float>> lv(mlh.lv.size());
+    const float* blk32 = nullptr;
+    if ((rc = upload3(M, &blk32, f32(hm.stencil_blocks)))) return cleanup(rc);
     for (size_t l = 0; l < mlh.lv.size(); ++l) {
       const dgdf::MLHostLevel& H = mlh.lv[l];
-      dgdf::MLLevelDev& L = lv[l];
+      dgdf::MLLevelT<float>& L = lv[l];
       L.stencil = H.stencil ? 1 : 0;
       L.bs = H.bs;
       L.n = H.n;
@@ -207,38 +213,34 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
       L.n_next = H.n_next;
       L.bs_next = H.bs_next;
       L.modes = 1;
-      L.c0 = H.cheb[0];
-      L.c1 = H.cheb[1];
-      L.c2 = H.cheb[2];
-      if ((rc = upload3(M, &L.binv, H.binv))) return cleanup(rc);
+      L.c0 = float(H.cheb[0]);
+      L.c1 = float(H.cheb[1]);
+      L.c2 = float(H.cheb[2]);
+      if ((rc = upload3(M, &L.binv, f32(H.binv)))) return cleanup(rc);
       if (H.stencil) {   // level 0: block Jacobi on the seven-block face stencil
         L.st_cls = d.face_stencil;
         L.st_nbr = d.face_nbr;
         L.st_nnb = 6;
-        L.st_blk = d.st_blk;
+        L.st_blk = blk32;
       } else if ((rc = upload3(M, &L.a_rp, H.A.rp)) || (rc = upload3(M, &L.a_ci, H.A.ci)) ||
-                 (rc = upload3(M, &L.a_v, H.A.v))) {
+                 (rc = upload3(M, &L.a_v, f32(H.A.v)))) {
         return cleanup(rc);
       }
       if (!H.inject && ((rc = upload3(M, &L.p_rp, H.P.rp)) || (rc = upload3(M, &L.p_ci, H.P.ci)) ||
-                        (rc = upload3(M, &L.p_v, H.P.v)) || (rc = upload3(M, &L.r_rp, H.R.rp)) ||
-                        (rc = upload3(M, &L.r_ci, H.R.ci)) || (rc = upload3(M, &L.r_v, H.R.v))))
+                        (rc = upload3(M, &L.p_v, f32(H.P.v))) || (rc = upload3(M, &L.r_rp, H.R.rp)) ||
+                        (rc = upload3(M, &L.r_ci, H.R.ci)) || (rc = upload3(M, &L.r_v, f32(H.R.v)))))
         return cleanup(rc);
       const size_t nv = size_t(H.n) * H.bs;
-      if (l == 0) {   // level 0 works on the PCG vectors: b = r, x = z
-        L.b = d.r;
-        L.x = d.z;
-      } else if ((rc = dalloc3(M, &L.b, nv)) || (rc = dalloc3(M, &L.x, nv))) {
+      if ((rc = dalloc3(M, &L.b, nv)) || (rc = dalloc3(M, &L.x, nv)) || (rc = dalloc3(M, &L.r, nv)) ||
+          (rc = dalloc3(M, &L.d, nv)))
         return cleanup(rc);
-      }
-      if ((rc = dalloc3(M, &L.r, nv)) || (rc = dalloc3(M, &L.d, nv))) return cleanup(rc);
     }
     dgdf::DevMesh& v = M->mv;
-    const dgdf::MLLevelDev* lvd = nullptr;
-    if ((rc = upload3(M, &lvd, lv)) || (rc = upload3(M, &v.ml_cpinv, mlh.cpinv)) ||
-        (rc = dalloc3(M, &v.ml_xc, size_t(mlh.nc))) || (rc = dalloc3(M, &v.ml_bc, size_t(mlh.nc))))
+    const dgdf::MLLevelT<float>* lvd = nullptr;
+    if ((rc = upload3(M, &lvd, lv)) || (rc = upload3(M, &v.ml_cpinv_f, f32(mlh.cpinv))) ||
+        (rc = dalloc3(M, &v.ml_xc_f, size_t(mlh.nc))) || (rc = dalloc3(M, &v.ml_bc_f, size_t(mlh.nc))))
       return cleanup(rc);
-    v.ml_lv = lvd;
+    v.ml_lv_f = lvd;
     v.ml_nlev = int(lv.size());
     v.ml_nc = mlh.nc;
     v.k = d.k;
@@ -249,7 +251,7 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
     v.bar = d.bar;
     v.stats = d.stats;
     M->use_ml = true;
-    M->ml_blocks = dgdf::solver3_ml_blocks(d);
+    M->ml_blocks = dgdf::solver3_ml_blocks(d, true);
   }
   *out = M;
   return DG_OK;

@@ -48,7 +48,7 @@ cudaError_t launch_coef_to_lattice3(const DevMesh3& m, const double* coef, doubl
 cudaError_t launch_diagnostics3(const DevMesh3& m, const double* coef, cudaStream_t s);
 // FP64 PCG with the multilevel preconditioner of an assembled hierarchy (k_multilevel.cu): mv
 // holds the hierarchy (ml_*), the PCG vectors r and z, red, bar and stats
-int solver3_ml_blocks(const DevMesh3& m);
+int solver3_ml_blocks(const DevMesh3& m, bool fp32);   // fp32: the V-cycle in FP32 (mv.ml_lv_f)
 cudaError_t launch_solve3_ml(const DevMesh3& m, const DevMesh& mv, const SolveArgs& a, int nblocks, cudaStream_t s);
 
 }  // namespace dgdf

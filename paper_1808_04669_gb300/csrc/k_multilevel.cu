@@ -571,11 +571,11 @@ __device__ __forceinline__ void spmv3_ml(const DevMesh3& m3, int f, const double
 // the face stencil of m3 (seven blocks) for S and g assembled from both sides' G f (canonical
 // face basis: no orientation signs). mv carries the hierarchy and the PCG vectors r and z, the
 // reduction slots, the barrier and the counters (the same buffers as m3's).
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh mv, SolveArgs a) {
   constexpr int NL = (K + 1) * (K + 2) / 2, L4 = 4 * NL;
-  __shared__ MLLevelDev lv[kMLMaxLevels];
-  for (int l = threadIdx.x; l < mv.ml_nlev; l += blockDim.x) lv[l] = mv.ml_lv[l];
+  __shared__ MLLevelT<R> lv[kMLMaxLevels];
+  for (int l = threadIdx.x; l < mv.ml_nlev; l += blockDim.x) lv[l] = MLOps<R>::levels(mv)[l];
   __syncthreads();
   const int nF = m3.n_face;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
@@ -623,11 +623,11 @@ __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh m
     if (!grid_reduce<1>(mv, 0, r0s, bar)) return;
     for (int f = gtid; f < nF; f += gsz) {
       mv.r[size_t(f) * NL] -= r0s[0] * inv_nf;
-      ml_row_first_step<NL, double>(mv, lv[0], f);
+      ml_start_row<NL, R>(mv, lv[0], f);
     }
     if (!grid_sync(bar, mv.stats)) return;
     double red[3] = {0.0, 0.0, 0.0};
-    if (!ml_vcycle<NL, double>(mv, lv, red)) return;
+    if (!ml_vcycle<NL, R>(mv, lv, red)) return;
     if (!grid_reduce<3>(mv, 1, red, bar)) return;
     double rho = red[0];
     rr = fmax(red[1] - red[2] * red[2] * inv_nf, 0.0);
@@ -683,11 +683,11 @@ __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh m
           m3.lam[o] += alpha * pnew[o];
           mv.r[o] -= alpha * m3.q[o] + (j == 0 ? cmean : 0.0);
         }
-        ml_row_first_step<NL, double>(mv, lv[0], f);
+        ml_start_row<NL, R>(mv, lv[0], f);
       }
       if (!grid_sync(bar, mv.stats)) return;
       double red2[3] = {0.0, 0.0, 0.0};
-      if (!ml_vcycle<NL, double>(mv, lv, red2)) return;
+      if (!ml_vcycle<NL, R>(mv, lv, red2)) return;
       if (!grid_reduce<3>(mv, 1, red2, bar)) return;
       beta = red2[0] / rho;
       rho = red2[0];
@@ -784,8 +784,19 @@ int solver_ml_blocks(const DevMesh& m) {
   return nb < 1 ? 1 : nb;
 }
 
-int solver3_ml_blocks(const DevMesh3& m) {
-  const void* fn = m.k == 1 ? (const void*)k_solve3_ml<1> : (const void*)k_solve3_ml<2>;
+const void* ml3_kernel(int k, bool fp32) {
+  switch (k * 2 + (fp32 ? 1 : 0)) {
+    case 2: return (const void*)k_solve3_ml<1, double>;
+    case 3: return (const void*)k_solve3_ml<1, float>;
+    case 4: return (const void*)k_solve3_ml<2, double>;
+    case 5: return (const void*)k_solve3_ml<2, float>;
+    default: return nullptr;
+  }
+}
+
+int solver3_ml_blocks(const DevMesh3& m, bool fp32) {
+  const void* fn = ml3_kernel(m.k, fp32);
+  if (!fn) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -802,14 +813,15 @@ int solver3_ml_blocks(const DevMesh3& m) {
 }
 
 cudaError_t launch_solve3_ml(const DevMesh3& m, const DevMesh& mv, const SolveArgs& a, int nblocks, cudaStream_t s) {
-  if (!mv.ml_lv || mv.ml_nlev < 1 || mv.ml_nlev > kMLMaxLevels || (m.k != 1 && m.k != 2)) return cudaErrorInvalidValue;
+  const bool fp32 = mv.ml_lv_f != nullptr;
+  const void* fn = ml3_kernel(m.k, fp32);
+  if ((!mv.ml_lv && !fp32) || mv.ml_nlev < 1 || mv.ml_nlev > kMLMaxLevels || !fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(mv.bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   DevMesh3 mm = m;
   DevMesh vv = mv;
   SolveArgs aa = a;
   void* args[] = {&mm, &vv, &aa};
-  const void* fn = m.k == 1 ? (const void*)k_solve3_ml<1> : (const void*)k_solve3_ml<2>;
   return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(kMLThreads), args, 0, s);
 }
 
