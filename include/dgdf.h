@@ -146,7 +146,10 @@ int dg_mesh_info(const dg_mesh* mesh, int64_t out[8]);
 
 /* Set the state from lattice values vals [n_tri][n_lat(k)][2] (the broken P^k
  * field interpolating them). No projection is applied: call
- * dg_project_divfree to move it into V_h^{k,-1}.
+ * dg_project_divfree to move it into V_h^{k,-1}. The facet solver keeps its multipliers of
+ * the last stages and steps: they set only the initial guess of the next solves, whose results
+ * meet cg_rtol from any guess, and a state that continues the trajectory (a host round trip per
+ * step) keeps the short warm-started solves; dg_project_divfree drops them.
  * Errors: DG_ERR_INVALID_ARG (NULL), DG_ERR_NONFINITE (NaN/Inf in vals). */
 int dg_set_velocity(dg_mesh* mesh, const double* vals, int on_device);
 
@@ -185,7 +188,7 @@ int dg_step(dg_mesh* mesh, int scheme, double dt, int64_t nsteps);
  * scalar Dubiner polynomials scaled to unit L2 norm on the triangle; component-major,
  * double [n_tri][2 n_lat(k)]). The Euclidean inner product of coefficient arrays is
  * the L2 inner product of the fields, so gradients in this representation are L2
- * Riesz representers. */
+ * Riesz representers. Setting keeps the solver's warm-start multipliers, as dg_set_velocity. */
 int dg_set_coefficients(dg_mesh* mesh, const double* coef, int on_device);
 int dg_get_coefficients(dg_mesh* mesh, double* coef, int on_device);
 

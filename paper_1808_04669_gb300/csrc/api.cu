@@ -867,9 +867,9 @@ int dg_set_velocity(dg_mesh* M, const double* vals, int on_device) {
   if (flag) return fail(DG_ERR_NONFINITE, "non-finite velocity value");
   rc = launch(M, KC_LATTICE, [&] { return dgdf::launch_lattice_to_coef(M->dm, M->lattice, M->dm.u, M->stream); });
   if (rc) return rc;
-  M->has_lam = false;
+  // the solver's multipliers of the last stages and steps stay: they only set the initial guess
+  // of the next solves (a state that continues the trajectory keeps its short solves)
   M->udf_valid = false;
-  forget_history(M);
   if ((rc = reset_watch(M))) return rc;
   return finish(M, false);
 }
@@ -1308,9 +1308,7 @@ int dg_set_coefficients(dg_mesh* M, const double* coef, int on_device) {
   const size_t n = size_t(M->dm.n_tri) * M->hm.nd;
   CK(cudaMemcpyAsync(M->dm.u, coef, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      M->stream));
-  M->has_lam = false;
-  M->udf_valid = false;
-  forget_history(M);
+  M->udf_valid = false;   // the solver's warm-start multipliers stay (as in dg_set_velocity)
   if (int rc = reset_watch(M)) return rc;
   return finish(M, false);
 }
