@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 # over the three stages of a step (the first stage reads one state, the others two), from the
 # ncu capture summarised in profiles/; used only while the stage-kernel sources still hash to
 # the captured `sha`, else the line reports null.
-NCU_TRAFFIC = {"stage_residual": {"sha": "211300c86dcfe281", "n_tri": 131072, "bytes": 41049344,
+NCU_TRAFFIC = {"stage_residual": {"sha": "d424d998ab124977", "n_tri": 131072, "bytes": 40971435,
                                   "source": "profiles/k_stage_df2_shear_n256_k3.md"}}
 
 
@@ -584,6 +584,15 @@ def run_schemes(args):
                            "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
                            "value": dof_stage_units(m.n_tri, k, 1) / (ms * 1e-3)})
     m.close()
+    out["results"].append(run_three_d(args, g, stream, flush))
+    print(json.dumps(out), flush=True)
+
+
+def run_three_d(args, g, stream, flush):
+    """The three-dimensional line (row f2): SSP-RK3 steps of the ABC flow on the periodic cube,
+    device-timed with L2 flushed between steps, and the residual kernel alone."""
+    import numpy as np
+    import torch
     # three dimensions (closed tetrahedral meshes, FP64): the ABC flow on the periodic cube
     # [0, 2 pi]^3 cut into Kuhn tetrahedra, BDM_2, multilevel PCG
     from synth.mesh3 import abc_flow, kuhn_cube_mesh, sample_lattice3
@@ -613,15 +622,15 @@ def run_schemes(args):
     d1 = m3.diagnostics()
     its = (d1["total_iters"] - d0["total_iters"]) / max(d1["solves"] - d0["solves"], 1)
     # the stage kernel alone (MODE_RESIDUAL through dg3_eval_residual, lattice output included)
-    res = torch.empty((m3.n_tet, m3.n_lat, 3), dtype=torch.float64, device="cuda")
-    m3.eval_residual(res)
+    rbuf = torch.empty((m3.n_tet, m3.n_lat, 3), dtype=torch.float64, device="cuda")
+    m3.eval_residual(rbuf)
     torch.cuda.synchronize()
     rt = []
     for _ in range(5):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         e0.record(stream)
-        m3.eval_residual(res)
+        m3.eval_residual(rbuf)
         e1.record(stream)
         torch.cuda.synchronize()
         rt.append(e0.elapsed_time(e1))
@@ -630,16 +639,16 @@ def run_schemes(args):
     nd3 = 3 * (k3 + 1) * (k3 + 2) * (k3 + 3) // 6
     sm_mhz, sms = 2070.0, sm_count()
     peak64 = 2 * sms * sm_mhz * 1e6 * 2 / 1e12
-    out["results"].append({"workload": "ABC flow, periodic cube [0,2pi]^3, %d^3 cubes x 6 Kuhn tetrahedra (%d), BDM_%d, "
-                                       "nu=%g, FP64, multilevel PCG" % (N3, m3.n_tet, k3, nu3),
-                           "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
-                           "value": m3.n_tet * nd3 * 3 / (ms * 1e-3),
-                           "residual_kernel_ms": rms,
-                           "residual_kernel_fp64_tflops": flops / (rms * 1e-3) / 1e12,
-                           "fp64_peak_tflops": peak64,
-                           "peak_source": "derived: 2 FP64 FMA/clock/SM x %d SMs x 2070 MHz x 2 flops" % sms})
+    res = {"workload": "ABC flow, periodic cube [0,2pi]^3, %d^3 cubes x 6 Kuhn tetrahedra (%d), BDM_%d, "
+                       "nu=%g, FP64, multilevel PCG" % (N3, m3.n_tet, k3, nu3),
+           "scheme": "ssprk3", "ms_per_step": ms, "iters_per_solve": its,
+           "value": m3.n_tet * nd3 * 3 / (ms * 1e-3),
+           "residual_kernel_ms": rms,
+           "residual_kernel_fp64_tflops": flops / (rms * 1e-3) / 1e12,
+           "fp64_peak_tflops": peak64,
+           "peak_source": "derived: 2 FP64 FMA/clock/SM x %d SMs x 2070 MHz x 2 flops" % sms}
     m3.close()
-    print(json.dumps(out), flush=True)
+    return res
 
 
 def stage3_flops_per_tet(k):
@@ -775,9 +784,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=("step", "ensemble", "adjoint", "schemes"), default="step",
+    ap.add_argument("--mode", choices=("step", "ensemble", "adjoint", "schemes", "threed"), default="step",
                     help="step: the bench line; ensemble / adjoint / schemes: the batching, gradient, "
-                         "time-scheme and wall workloads")
+                         "time-scheme, boundary and 3-D workloads; threed: the 3-D line alone")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--lanes", type=int, default=0, help="ensemble: parallel graph branches (0: autotune)")
     ap.add_argument("--steps-adjoint", type=int, default=200)
@@ -798,6 +807,16 @@ def main():
         run_ensemble(args)
     elif args.mode == "adjoint":
         run_adjoint(args)
+    elif args.mode == "threed":
+        import torch
+        torch.cuda.set_device(env_rank()[2])
+        from paper_1808_04669_gb300 import build as _b
+        _b.build()
+        import paper_1808_04669_gb300 as g
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"mode": "threed", "unit": UNIT, "data": "synthetic", "steps": args.steps,
+                          "warmup": args.warmup,
+                          "results": [run_three_d(args, g, torch.cuda.current_stream(), flush)]}), flush=True)
     elif args.mode == "schemes":
         run_schemes(args)
     else:
