@@ -74,6 +74,15 @@ int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const doubl
                        int64_t info[34], int nr, const double* r, double* z, const double* g, double* lam,
                        double rtol, int64_t* iters);
 
+/* Three-dimensional host check (include/dgdf3.h conventions): the L2 projection of the field
+ * given by lattice values vals [n_tet][n_lat3(k)][3] onto the divergence-free space, computed on
+ * the host from the set-up dg3_mesh_create uploads (class operators, face stencil) with a host
+ * PCG preconditioned by one V-cycle of the assembled multilevel hierarchy (point-Jacobi smoothing),
+ * to 1e-13 relative. out: lattice values, as vals; *iters: PCG iterations (may be NULL).
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_MESH, DG_ERR_UNSUPPORTED. */
+int dg3_host_project(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords, int k, double alpha,
+                     const double* vals, double* out, int64_t* iters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -456,6 +456,20 @@ def host_multilevel(tri_vertex_ids, tri_coords, k, alpha=2.0, r=None, g=None, rt
             "z": z, "lam": lam, "iters": int(it.value) if g is not None else None}
 
 
+def host_project3(tet_vertex_ids, tet_coords, k, vals, alpha=2.0):
+    """Host-side L2 projection of a 3-D field onto the divergence-free space from the library's own
+    set-up (include/dgdf_host.h, dg3_host_project): (lattice values, PCG iterations)."""
+    vid = np.ascontiguousarray(tet_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tet_coords, dtype=np.float64)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    out = np.empty_like(v)
+    it = ctypes.c_int64()
+    check(lib().dg3_host_project(vid.shape[0], vid.ctypes.data_as(ctypes.c_void_p), X.ctypes.data_as(ctypes.c_void_p),
+                                 int(k), float(alpha), v.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it)), "dg3_host_project")
+    return out, int(it.value)
+
+
 def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13, maxit=20000, stream=None):
     """dg_facet_solve_noalloc on caller-owned CUDA tensors (torch); lam is updated in place.
 
@@ -492,5 +506,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGMesh3", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGMesh3", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "host_project3", "facet_solve_noalloc",
            "lib"]

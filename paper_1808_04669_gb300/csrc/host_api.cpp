@@ -9,6 +9,7 @@
 #include "../../include/dgdf_host.h"
 #include "multilevel.hpp"
 #include "setup.hpp"
+#include "setup3.hpp"
 
 extern "C" {
 
@@ -168,6 +169,106 @@ int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const doubl
       rz = rz2;
     }
     if (iters) *iters = it;
+  }
+  return DG_OK;
+}
+
+int dg3_host_project(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords, int k, double alpha,
+                     const double* vals, double* out, int64_t* iters) {
+  if (!vals || !out || !(alpha > 0.0)) return DG_ERR_INVALID_ARG;
+  dgdf::HostMesh3 hm;
+  std::string err;
+  int rc = dgdf::build_host_mesh3(n_tet, tet_vertex_ids, tet_coords, k, alpha, hm, err);
+  if (rc) return rc;
+  const int ns = hm.ns, nd = hm.nd, nl = hm.nl, L4 = 4 * nl;
+  const size_t nT = size_t(hm.n_tet), nF = size_t(hm.n_face), n = nF * nl;
+  // coefficients of the interpolant (M = I in the orthonormal basis), then g = sum of G f
+  std::vector<double> f(nT * nd), g(n, 0.0);
+  for (size_t t = 0; t < nT; ++t) {
+    const dgdf::Class3& co = hm.classes[hm.tet_class[t]];
+    const double sq = std::sqrt(co.det);
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < ns; ++j) {
+        double v = 0.0;
+        for (int p = 0; p < ns; ++p) v += hm.ref.lat_inv[size_t(j) * ns + p] * vals[(t * ns + p) * 3 + c];
+        f[t * nd + c * ns + j] = sq * v;
+      }
+    for (int e = 0; e < 4; ++e) {
+      const size_t fc = size_t(hm.tet_face[t * 4 + e]);
+      for (int m = 0; m < nl; ++m) {
+        double v = 0.0;
+        for (int j = 0; j < nd; ++j) v += co.G[size_t(e * nl + m) * nd + j] * f[t * nd + j];
+        g[fc * nl + m] += v;
+      }
+    }
+  }
+  // S lam = g by PCG with one host V-cycle of the assembled hierarchy (point-Jacobi smoothing on
+  // every level), the constant multiplier left out of g and of the residual
+  dgdf::CsrHost A = dgdf::stencil_csr(int(nF), nl, 6, hm.face_stencil.data(), hm.face_nbr.data(),
+                                      hm.stencil_blocks.data());
+  dgdf::MLHost ml;
+  if ((rc = dgdf::build_multilevel_csr(A, nl, nullptr, nullptr, ml, err))) return rc;
+  auto centre = [&](std::vector<double>& v) {
+    double c0 = 0.0;
+    for (size_t fc = 0; fc < nF; ++fc) c0 += v[fc * nl];
+    c0 /= double(nF);
+    for (size_t fc = 0; fc < nF; ++fc) v[fc * nl] -= c0;
+  };
+  auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
+    for (size_t i = 0; i < n; ++i) {
+      double v = 0.0;
+      for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) v += A.v[p] * x[A.ci[p]];
+      y[i] = v;
+    }
+  };
+  auto dot = [&](const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+  };
+  const dgdf::HostMesh none;
+  centre(g);
+  std::vector<double> lam(n, 0.0), r(g), z(n), p(n), q(n);
+  const double gn = std::sqrt(dot(g, g));
+  int64_t it = 0;
+  if (gn > 0.0) {
+    dgdf::multilevel_apply_host(none, ml, r.data(), z.data());
+    p = z;
+    double rho = dot(r, z);
+    for (; it < 2000 && std::sqrt(dot(r, r)) > 1e-13 * gn; ++it) {
+      apply(p, q);
+      const double al = rho / dot(p, q);
+      for (size_t i = 0; i < n; ++i) {
+        lam[i] += al * p[i];
+        r[i] -= al * q[i];
+      }
+      centre(r);
+      dgdf::multilevel_apply_host(none, ml, r.data(), z.data());
+      const double rn = dot(r, z), be = rn / rho;
+      rho = rn;
+      for (size_t i = 0; i < n; ++i) p[i] = z[i] + be * p[i];
+    }
+  }
+  if (iters) *iters = it;
+  // u = P f - G^T lam, as lattice values
+  for (size_t t = 0; t < nT; ++t) {
+    const dgdf::Class3& co = hm.classes[hm.tet_class[t]];
+    std::vector<double> u(nd), lt(L4);
+    for (int e = 0; e < 4; ++e)
+      for (int m = 0; m < nl; ++m) lt[e * nl + m] = lam[size_t(hm.tet_face[t * 4 + e]) * nl + m];
+    for (int i = 0; i < nd; ++i) {
+      double v = 0.0;
+      for (int j = 0; j < nd; ++j) v += co.P[size_t(i) * nd + j] * f[t * nd + j];
+      for (int l = 0; l < L4; ++l) v -= co.G[size_t(l) * nd + i] * lt[l];
+      u[i] = v;
+    }
+    const double s = 1.0 / std::sqrt(co.det);
+    for (int pt = 0; pt < ns; ++pt)
+      for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        for (int j = 0; j < ns; ++j) v += hm.ref.lat_phi[size_t(pt) * ns + j] * u[c * ns + j];
+        out[(t * ns + pt) * 3 + c] = s * v;
+      }
   }
   return DG_OK;
 }

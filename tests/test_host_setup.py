@@ -290,3 +290,19 @@ def test_multilevel_v_cycle_is_symmetric_positive_on_the_range(g):
     G = r @ z.T
     assert np.abs(G - G.T).max() <= 1e-12 * np.abs(G).max()
     assert np.linalg.eigvalsh(0.5 * (G + G.T)).min() > 0
+
+
+@pytest.mark.parametrize("N,k", [(2, 1), (2, 2), (3, 2)])
+def test_three_dimensional_setup_projects_like_the_oracle(g, N, k):
+    # the library's 3-D host set-up (topology, canonical faces, class operators, face stencil and
+    # the assembled multilevel hierarchy) gives the oracle's L2 projection onto the
+    # divergence-free space, computed on the host
+    from oracle.dg3 import Discretization3
+    from synth.mesh3 import abc_flow, kuhn_cube_mesh, sample_lattice3
+    vid, X = kuhn_cube_mesh(N)
+    v = sample_lattice3(abc_flow(), X, k) + 0.3 * np.random.default_rng(N).standard_normal((6 * N ** 3, (k + 1) * (k + 2) * (k + 3) // 6, 3))
+    out, its = g.host_project3(vid, X, k, v)
+    d = Discretization3(vid, X, k, 0.0)
+    ref = d.to_lattice(d.project(d.from_lattice(v)))
+    assert np.linalg.norm(out - ref) < 1e-11 * np.linalg.norm(ref)
+    assert 0 < its < 60
