@@ -130,3 +130,45 @@ def test_multilevel_iterations_stay_flat_on_16_cubes(g):
     assert da["last_iters"] <= 60 and db["last_iters"] > 4 * da["last_iters"], (da, db)
     assert rel(a, b) < 1e-11
     assert da["max_div"] < 1e-10 and da["max_jump"] < 1e-10
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_errors_and_edge_cases(g, precond):
+    vid, X = kuhn_cube_mesh(2)
+    k = 2
+    v = field(X, k, 7)
+    # an iteration cap that cannot be met is reported, not hidden
+    m = g.DGMesh3(vid, X, k, 0.0, cg_maxit=1, precond=precond)
+    m.set_velocity(v)
+    with pytest.raises(g.DGError) as e:
+        m.project_divfree()
+    assert e.value.code == -5
+    # non-finite input is refused before it reaches the device state
+    m = g.DGMesh3(vid, X, k, 0.0, precond=precond)
+    bad = v.copy()
+    bad[3, 1, 2] = np.inf
+    with pytest.raises(g.DGError) as e:
+        m.set_velocity(bad)
+    assert e.value.code == -6
+    # zero steps leave the state; the projection is idempotent
+    m.set_velocity(v)
+    m.project_divfree()
+    u1 = m.get_velocity()
+    m.rk3_step(0.01, 0)
+    assert np.array_equal(m.get_velocity(), u1)
+    m.project_divfree()
+    assert rel(m.get_velocity(), u1) < 1e-12
+
+
+def test_rk3_parity_k1_multilevel_n3(g):
+    vid, X = kuhn_cube_mesh(3)
+    k, nu = 1, 0.02
+    d = Discretization3(vid, X, k, nu)
+    v = field(X, k, 41, noise=0.2)
+    dt = 0.2 * (2 * np.pi / 3) / np.abs(v).max()
+    U = d.rk3_step(d.project(d.from_lattice(v)), dt, 4)
+    m = g.DGMesh3(vid, X, k, nu)
+    m.set_velocity(v)
+    m.project_divfree()
+    m.rk3_step(dt, 4)
+    assert rel(m.get_velocity(), d.to_lattice(U)) < TOL
