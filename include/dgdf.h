@@ -168,6 +168,9 @@ int dg_project_divfree(dg_mesh* mesh);
  * preconditioner (lattice meshes), to the same cg_rtol; the element residual,
  * condensation and recovery run in double-float arithmetic (FP32 pairs, about
  * 48 significant bits) in the mixed form and in FP64 in the FP64 form.
+ * Each stage's solve starts from an extrapolation of the same stage's multipliers in
+ * the last steps (linear on lattice meshes, quadratic otherwise, once the steps had the
+ * same dt; an initial guess only: every solve meets cg_rtol).
  * Returns DG_ERR_NOT_CONVERGED if any solve hit cg_maxit, DG_ERR_NONFINITE if
  * a residual norm became NaN/Inf (the state is then undefined).
  * Same as dg_step(mesh, DG_SCHEME_SSPRK3, dt, nsteps). */

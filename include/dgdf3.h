@@ -58,7 +58,10 @@ int dg3_get_velocity(dg_mesh3* mesh, double* vals, int on_device);
 int dg3_project_divfree(dg_mesh3* mesh);
 
 /* nsteps >= 0 SSP-RK3 steps of size dt > 0, each stage M u_s = a M u^n + b [M u' + dt L(u')]
- * solved by the hybrid-mixed system (eq. (8), eq. (12)). Errors as dg3_project_divfree. */
+ * solved by the hybrid-mixed system (eq. (8), eq. (12)). Each stage's face solve starts from
+ * the quadratic extrapolation of the same stage's multipliers in the last three steps (once
+ * they had this dt; fewer entries: linear, or the last one rescaled); dg3_set_velocity keeps
+ * that history, dg3_project_divfree drops it. Errors as dg3_project_divfree. */
 int dg3_rk3_step(dg_mesh3* mesh, double dt, int64_t nsteps);
 
 /* The Riesz representer of L(u) (eq. (6)) of the current state, as lattice values. */

@@ -79,11 +79,13 @@ struct dg_mesh {
   long long gen = 0;              // bumped by every setter that changes a kernel argument
                                   // (dg_set_viscosity): batch graphs captured earlier are stale
   bool has_lam = false;
-  // lattice solver: multipliers of each stage of the current scheme in the last two steps
-  // (device, the layout of the solver's lam), their step sizes, and how many are valid
+  // multipliers of each stage of the current scheme in the last hist_len steps (device, the
+  // layout of the solver's lam), their step sizes, and how many are valid
   static constexpr int kMaxStages = 4;
-  void* hist[kMaxStages][2] = {};
-  double hist_dt[kMaxStages][2] = {};
+  static constexpr int kHist = 3;
+  int hist_len = 0;
+  void* hist[kMaxStages][kHist] = {};
+  double hist_dt[kMaxStages][kHist] = {};
   int hist_n[kMaxStages] = {};
   int hist_scheme = -1;           // the scheme the history belongs to
   size_t hist_bytes = 0;
@@ -270,20 +272,25 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0, bool h
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
   a.homog = homog ? 1 : 0;
-  // lattice solver inside a step: warm start from the same stage of the last two steps.
-  // lam_s is c_s dt times a smooth function of time, so with equal step sizes the linear
-  // extrapolation 2 lam(n-1) - lam(n-2) is second-order accurate; one entry, or a changed
-  // step size, gives lam(n-1) rescaled by dt / dt(n-1).
-  if (M->use_lattice && stage >= 0 && M->hist_n[stage] >= 1) {
+  // inside a step: warm start from the same stage of the last steps. lam_s is c_s dt times a
+  // smooth function of time, so with equal step sizes the quadratic extrapolation
+  // 3 lam(n-1) - 3 lam(n-2) + lam(n-3) is third-order accurate and the linear
+  // 2 lam(n-1) - lam(n-2) second-order; one entry, or a changed step size, gives lam(n-1)
+  // rescaled by dt / dt(n-1).
+  if (stage >= 0 && M->hist_n[stage] >= 1) {
     const double* hd = M->hist_dt[stage];
+    const int n = M->hist_n[stage];
     a.hist1 = M->hist[stage][0];
     a.hist2 = M->hist[stage][1];
-    if (M->hist_n[stage] >= 2 && hd[0] == dt && hd[1] == dt) {
+    a.hist3 = M->hist[stage][2];
+    a.c1 = dt / hd[0];
+    if (n >= 3 && hd[0] == dt && hd[1] == dt && hd[2] == dt) {
+      a.c1 = 3.0;
+      a.c2 = -3.0;
+      a.c3 = 1.0;
+    } else if (n >= 2 && hd[0] == dt && hd[1] == dt) {
       a.c1 = 2.0;
       a.c2 = -1.0;
-    } else {
-      a.c1 = dt / hd[0];
-      a.c2 = 0.0;
     }
   }
   a.rtol = M->p.cg_rtol;
@@ -307,14 +314,14 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0, bool h
 }
 
 // After the solve of RK stage s with step size dt: the new multipliers become the newest
-// history entry (the solver already moved the previous one into the second slot).
+// history entry (the solver already moved the older ones down one slot).
 int push_history(dg_mesh* M, int s, double dt) {
-  if (!M->use_lattice) return DG_OK;
+  if (M->hist_len == 0) return DG_OK;
   const void* lam = M->dm.lam_is_df ? static_cast<const void*>(M->dm.lam_df) : static_cast<const void*>(M->dm.lam);
   CK(cudaMemcpyAsync(M->hist[s][0], lam, M->hist_bytes, cudaMemcpyDeviceToDevice, M->stream));
-  M->hist_dt[s][1] = M->hist_dt[s][0];
+  for (int h = M->hist_len - 1; h > 0; --h) M->hist_dt[s][h] = M->hist_dt[s][h - 1];
   M->hist_dt[s][0] = dt;
-  M->hist_n[s] = M->hist_n[s] < 2 ? M->hist_n[s] + 1 : 2;
+  M->hist_n[s] = std::min(M->hist_n[s] + 1, M->hist_len);
   return DG_OK;
 }
 
@@ -811,15 +818,18 @@ int dg_mesh_create_ex(int64_t n_tri, const int64_t* tri_vertex_ids, const double
     d.lat_logn = logn;
     M->use_lattice = true;
     M->lattice_blocks = lat_blocks;
-    // multiplier history of the stages (warm starts), in the layout of the solver's lam
-    M->hist_bytes = nF * size_t(fp32 ? d.lat_vs : nl) * 8;
-    for (int s = 0; s < dg_mesh::kMaxStages; ++s)
-      for (int h = 0; h < 2; ++h) {
-        double* p = nullptr;
-        if ((rc = dalloc(M, &p, M->hist_bytes / 8))) return cleanup(rc);
-        M->hist[s][h] = p;
-      }
   }
+  // multiplier history of the stages (warm starts), in the layout of the solver's lam: two
+  // entries on the lattice path (its solves take two PCG iterations from the linear
+  // extrapolation already; a third entry did not lower that count), three for the others
+  M->hist_len = M->use_lattice ? 2 : 3;
+  M->hist_bytes = size_t(M->dm.n_facet) * size_t(M->use_lattice && lat_fp32 ? M->dm.lat_vs : M->hm.k + 1) * 8;
+  for (int s = 0; s < dg_mesh::kMaxStages; ++s)
+    for (int h = 0; h < M->hist_len; ++h) {
+      double* p = nullptr;
+      if ((rc = dalloc(M, &p, M->hist_bytes / 8))) return cleanup(rc);
+      M->hist[s][h] = p;
+    }
   *out = M;
   return DG_OK;
 }
@@ -1219,15 +1229,17 @@ int dg_batch_rk3_step(dg_batch* B, const double* dt, int64_t nsteps) {
   bool same_dt = B->exec && B->graph_dt.size() == n && B->graph_gen.size() == n;
   for (size_t i = 0; same_dt && i < n; ++i)
     same_dt = B->graph_dt[i] == dt[i] && B->graph_gen[i] == B->members[i]->gen;
-  // A member is in steady mode when its solves are warm and, on the lattice path, every
-  // stage has two history entries taken with the current step size; the captured step
+  // A member is in steady mode when its solves are warm and every stage has a full
+  // multiplier history taken with the current step size; the captured step
   // replays that mode, so steps run eagerly until all members reach it.
   auto steady = [&](size_t i) {
     const dg_mesh* M = B->members[i];
     if (!M->has_lam) return false;
-    if (!M->use_lattice) return true;
-    for (int s = 0; s < 3; ++s)
-      if (M->hist_n[s] < 2 || M->hist_dt[s][0] != dt[i] || M->hist_dt[s][1] != dt[i]) return false;
+    for (int s = 0; s < 3; ++s) {
+      if (M->hist_n[s] < M->hist_len) return false;
+      for (int h = 0; h < M->hist_len; ++h)
+        if (M->hist_dt[s][h] != dt[i]) return false;
+    }
     return true;
   };
   int64_t done = 0;

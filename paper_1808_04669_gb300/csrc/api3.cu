@@ -1,6 +1,7 @@
 // C-ABI of the three-dimensional path (include/dgdf3.h): closed tetrahedral meshes, FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -28,6 +29,12 @@ struct dg_mesh3 {
   dgdf::DevMesh mv{};             // the hierarchy and the PCG vectors for the multilevel kernel
   bool has_lam = false;
   double last_c = 0.0;
+  // multipliers of each SSP-RK3 stage in the last kHist steps (warm starts; the layout of lam),
+  // their step sizes, and how many are valid
+  static constexpr int kHist = 3;
+  double* hist[3][kHist] = {};
+  double hist_dt[3][kHist] = {};
+  int hist_n[3] = {};
   double* lattice = nullptr;          // [n_tet][ns][3] staging
   dgdf::DevStats* host_stats = nullptr;
 };
@@ -83,14 +90,45 @@ int reset3(dg_mesh3* M) {
   return DG_OK;
 }
 
-int solve3(dg_mesh3* M, double warm_scale) {
+// stage >= 0: a solve of SSP-RK3 stage `stage` with step size dt. The multipliers of the
+// stage are c dt times a smooth function of time: with three earlier entries taken with this
+// step size, the warm start is the quadratic extrapolation 3 lam(n-1) - 3 lam(n-2) + lam(n-3),
+// with two the linear one, else lam(n-1) rescaled by dt / dt(n-1); with none, warm_scale lam.
+int solve3(dg_mesh3* M, double warm_scale, int stage = -1, double dt = 0.0) {
   dgdf::SolveArgs a{};
   a.warm_scale = warm_scale;
+  if (stage >= 0 && M->hist_n[stage] >= 1) {
+    const double* hd = M->hist_dt[stage];
+    const int n = M->hist_n[stage];
+    a.hist1 = M->hist[stage][0];
+    a.hist2 = M->hist[stage][1];
+    a.hist3 = M->hist[stage][2];
+    a.c1 = dt / hd[0];
+    if (n >= 3 && hd[0] == dt && hd[1] == dt && hd[2] == dt) {
+      a.c1 = 3.0;
+      a.c2 = -3.0;
+      a.c3 = 1.0;
+    } else if (n >= 2 && hd[0] == dt && hd[1] == dt) {
+      a.c1 = 2.0;
+      a.c2 = -1.0;
+    }
+  }
   a.rtol = M->p.cg_rtol;
   a.maxit = M->p.cg_maxit;
   a.floor_rtol = 1e-9;
   if (M->use_ml) CK3(dgdf::launch_solve3_ml(M->dm, M->mv, a, M->ml_blocks, M->stream));
   else CK3(dgdf::launch_solve3(M->dm, a, M->solver_blocks, M->stream));
+  return DG_OK;
+}
+
+// After the solve of stage s with step size dt: the new multipliers become the newest history
+// entry (the solver already moved the older ones down one slot).
+int push_history3(dg_mesh3* M, int s, double dt) {
+  const size_t bytes = size_t(M->dm.n_face) * M->hm.nl * sizeof(double);
+  CK3(cudaMemcpyAsync(M->hist[s][0], M->dm.lam, bytes, cudaMemcpyDeviceToDevice, M->stream));
+  for (int h = dg_mesh3::kHist - 1; h > 0; --h) M->hist_dt[s][h] = M->hist_dt[s][h - 1];
+  M->hist_dt[s][0] = dt;
+  M->hist_n[s] = std::min(M->hist_n[s] + 1, dg_mesh3::kHist);
   return DG_OK;
 }
 
@@ -177,6 +215,9 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
       (rc = dalloc3(M, &d.stats, 1)) || (rc = dalloc3(M, &d.diag, 8)) ||
       (rc = dalloc3(M, &M->lattice, nT * hm.ns * 3)))
     return cleanup(rc);
+  for (int s = 0; s < 3; ++s)
+    for (int h = 0; h < dg_mesh3::kHist; ++h)
+      if ((rc = dalloc3(M, &M->hist[s][h], nF * nl))) return cleanup(rc);
   cudaError_t e = cudaMallocHost(&M->host_stats, sizeof(dgdf::DevStats));
   if (e != cudaSuccess) return cleanup(api_fail(DG_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e)));
   e = cudaMemsetAsync(d.u, 0, nT * nd * sizeof(double), M->stream);
@@ -316,6 +357,7 @@ int dg3_project_divfree(dg_mesh3* M) {
   if ((rc = solve3(M, 0.0))) return rc;
   CK3(dgdf::launch_recover3(M->dm, M->dm.u, M->stream));
   M->has_lam = false;
+  for (int s = 0; s < 3; ++s) M->hist_n[s] = 0;
   return finish3(M, true);
 }
 
@@ -338,8 +380,9 @@ int dg3_rk3_step(dg_mesh3* M, double dt, int64_t nsteps) {
       a.un = d.u;
       a.up = s == 0 ? d.u : d.ustage;
       CK3(dgdf::launch_stage3(d, a, M->stream));
-      // warm start from the previous stage's multipliers, rescaled by the ratio of the L coefficients
-      if ((rc = solve3(M, M->has_lam ? a.c / M->last_c : 0.0))) return rc;
+      // warm start from the stage's history, else from the previous stage's multipliers
+      // rescaled by the ratio of the L coefficients
+      if ((rc = solve3(M, M->has_lam ? a.c / M->last_c : 0.0, s, dt)) || (rc = push_history3(M, s, dt))) return rc;
       CK3(dgdf::launch_recover3(d, s == 2 ? d.u : d.ustage, M->stream));
       M->last_c = a.c;
       M->has_lam = true;

@@ -196,11 +196,13 @@ struct SolveArgs {
   double floor_rtol;   // accepted relative residual once refinement stagnates at its rounding floor
   int homog;           // 1: u.n = 0 on inflow facets (no data moments subtracted from g)
   // lattice solver, warm start from the same stage of earlier steps (overrides warm_scale):
-  // lam0 = c1 hist1 + c2 hist2 (hist2 read only if c2 != 0); the kernel then moves hist1
-  // into hist2, and the caller stores the new lam in hist1. Layout of lam.
+  // lam0 = c1 hist1 + c2 hist2 + c3 hist3 (hist2 read only if c2 != 0, hist3 only if
+  // c3 != 0); the kernel then moves hist2 into hist3 (if hist3 is set) and hist1 into
+  // hist2, and the caller stores the new lam in hist1. Layout of lam.
   void* hist1;
   void* hist2;
-  double c1, c2;
+  void* hist3;
+  double c1, c2, c3;
 };
 
 // Launchers (k dispatched at run time). Return the launch error.

@@ -842,9 +842,11 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   GridBar* bar = m.bar;
   // g from both sides of every facet; warm-started lam
-  const A warm = A(a.warm_scale), hc1 = A(a.c1), hc2 = A(a.c2);
+  const A warm = A(a.warm_scale), hc1 = A(a.c1), hc2 = A(a.c2), hc3 = A(a.c3);
   V* hist1 = static_cast<V*>(a.hist1);
   V* hist2 = static_cast<V*>(a.hist2);
+  V* hist3 = static_cast<V*>(a.hist3);
+  const bool use2 = a.c2 != 0.0, use3 = a.c3 != 0.0;
   double ga = 0.0;
   Acc g0 = acc_zero(Acc{});
 #pragma unroll 4
@@ -854,11 +856,18 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     facet_g<NL>(m, f, gv);
     if (hist1) {
       // extrapolation from the same stage of earlier steps; the history shifts by one
-      A h1[NL];
+      A h1[NL], h2[NL];
       ldf<NL, VS>(hist1 + o, h1);
-      if (a.c2 != 0.0) ldf<NL, VS>(hist2 + o, lv);
+      if (use2 || hist3) ldf<NL, VS>(hist2 + o, h2);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) lv[j] = a.c2 != 0.0 ? hc1 * h1[j] + hc2 * lv[j] : hc1 * h1[j];
+      for (int j = 0; j < NL; ++j) lv[j] = use2 ? hc1 * h1[j] + hc2 * h2[j] : hc1 * h1[j];
+      if (use3) {
+        A h3[NL];
+        ldf<NL, VS>(hist3 + o, h3);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) lv[j] = lv[j] + hc3 * h3[j];
+      }
+      if (hist3) stf<NL, VS>(hist3 + o, h2);
       stf<NL, VS>(hist2 + o, h1);
     } else if (a.warm_scale != 0.0) {
       ldf<NL, VS>(L.lam + o, lv);

@@ -372,8 +372,8 @@ __device__ bool ml_vcycle(const DevMesh& m, const MLLevelT<R>* lv, double (&red)
   return true;
 }
 
-// One solve: g assembled from the element sides, lam0 = warm_scale * lam, constant multiplier
-// removed from g, then PCG with the V-cycle. Level 0's b and x are the PCG vectors r and z.
+// One solve: g assembled from the element sides, lam0 from the history or warm_scale * lam
+// (warm_start_row), constant multiplier removed from g, then PCG with the V-cycle. Level 0's b and x are the PCG vectors r and z.
 template <int K, typename R>
 __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a) {
   constexpr int NL = K + 1;
@@ -392,9 +392,9 @@ __global__ void __launch_bounds__(kMLThreads) k_solve_ml(DevMesh m, SolveArgs a)
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;
       m.g[o] = gv[j];
-      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
       gg[0] += gv[j] * gv[j];
     }
+    warm_start_row<NL>(m.lam, a, size_t(f) * NL);
     gg[1] += gv[0];
   }
   if (!grid_reduce<2>(m, 4, gg, bar)) return;
@@ -589,10 +589,10 @@ __global__ void __launch_bounds__(kMLThreads) k_solve3_ml(DevMesh3 m3, DevMesh m
       const double v = m3.gl[size_t(t0) * L4 + e0 * NL + j] + m3.gl[size_t(t1) * L4 + e1 * NL + j];
       const size_t o = size_t(f) * NL + j;
       m3.g[o] = v;
-      m3.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m3.lam[o];
       gg[0] += v * v;
       if (j == 0) gg[1] += v;
     }
+    warm_start_row<NL>(m3.lam, a, size_t(f) * NL);
   }
   if (!grid_reduce<2>(mv, 4, gg, bar)) return;
   const double inv_nf = 1.0 / double(nF);   // closed mesh: the constant multiplier is the kernel of S

@@ -131,8 +131,8 @@ __device__ int pcg(const DevMesh& m, R* x, R* rv, R* zv, R* pa, R* pb, R* qv, co
   return it;
 }
 
-// One solve: g = assembled element contributions, lam0 = warm_scale * lam, then
-// FP64 PCG (mixed = 0) or FP64 refinement around FP32 PCG (mixed = 1).
+// One solve: g = assembled element contributions, lam0 from the history or warm_scale * lam
+// (warm_start_row), then FP64 PCG (mixed = 0) or FP64 refinement around FP32 PCG (mixed = 1).
 template <int K, int MIXED>
 __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a) {
   constexpr int NL = K + 1;
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve(DevMesh m, SolveArgs a
     for (int j = 0; j < NL; ++j) {
       const size_t o = size_t(f) * NL + j;
       m.g[o] = gv[j];
-      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
       gg[0] += gv[j] * gv[j];
     }
+    warm_start_row<NL>(m.lam, a, size_t(f) * NL);
     gg[1] += gv[0];
   }
   if (!grid_reduce<2>(m, 4, gg, bar)) return;

@@ -295,9 +295,10 @@ __device__ __forceinline__ void binv3(const DevMesh3& m, int f, const double (&r
 }
 
 // Face-system solve, one persistent cooperative kernel: g = both sides' G f (no orientation
-// signs: both sides use the canonical face basis), lam0 = warm_scale lam, the constant
-// multiplier (mode 0 on every face, the kernel of S on a closed mesh) removed from g, then FP64
-// PCG with the block-Jacobi preconditioner. Residual norms leave out the mode-0 mean.
+// signs: both sides use the canonical face basis), lam0 from the history or warm_scale lam
+// (warm_start_row), the constant multiplier (mode 0 on every face, the kernel of S on a closed
+// mesh) removed from g, then FP64 PCG with the block-Jacobi preconditioner. Residual norms
+// leave out the mode-0 mean.
 template <int K>
 __global__ void __launch_bounds__(kSolverThreads) k_solve3(DevMesh3 m, SolveArgs a) {
   constexpr int NL = Dims3<K>::NL, L4 = 4 * NL;
@@ -313,10 +314,10 @@ __global__ void __launch_bounds__(kSolverThreads) k_solve3(DevMesh3 m, SolveArgs
       const double v = m.gl[size_t(t0) * L4 + e0 * NL + j] + m.gl[size_t(t1) * L4 + e1 * NL + j];
       const size_t o = size_t(f) * NL + j;
       m.g[o] = v;
-      m.lam[o] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * m.lam[o];
       gg[0] += v * v;
       if (j == 0) gg[1] += v;
     }
+    warm_start_row<NL>(m.lam, a, size_t(f) * NL);
   }
   if (!reduce3<2>(m, 4, gg)) return;
   const double c0 = gg[1] * inv_nf;

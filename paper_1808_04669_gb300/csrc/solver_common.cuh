@@ -170,6 +170,34 @@ __device__ __forceinline__ void boundary_g(const DevMesh& m, int f, int homog, d
   }
 }
 
+// lam0 of one facet row (NL FP64 values at lam + o; the history vectors share its layout):
+// with a history (SolveArgs::hist1, the same stage of earlier steps), the extrapolation
+// c1 hist1 + c2 hist2 + c3 hist3, and the history moves down one slot (hist2 -> hist3 if
+// hist3 is set, hist1 -> hist2; the caller then stores the new lam in hist1); without one,
+// warm_scale lam (zero for a cold start).
+template <int NL>
+__device__ __forceinline__ void warm_start_row(double* lam, const SolveArgs& a, size_t o) {
+  if (!a.hist1) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) lam[o + j] = a.warm_scale == 0.0 ? 0.0 : a.warm_scale * lam[o + j];
+    return;
+  }
+  double* h1 = static_cast<double*>(a.hist1) + o;
+  double* h2 = static_cast<double*>(a.hist2) + o;
+  double* h3 = a.hist3 ? static_cast<double*>(a.hist3) + o : nullptr;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    const double v1 = h1[j];
+    const double v2 = (a.c2 != 0.0 || h3) ? h2[j] : 0.0;
+    double v = a.c1 * v1;
+    if (a.c2 != 0.0) v += a.c2 * v2;
+    if (a.c3 != 0.0) v += a.c3 * h3[j];
+    if (h3) h3[j] = v2;
+    h2[j] = v1;
+    lam[o + j] = v;
+  }
+}
+
 template <int NL>
 __device__ __forceinline__ void facet_nbrs(const DevMesh& m, int f, int (&nb)[5]) {
   nb[0] = f;
