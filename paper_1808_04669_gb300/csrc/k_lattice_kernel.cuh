@@ -408,15 +408,18 @@ __device__ __forceinline__ void stf(double* p, const double (&v)[NL]) {
 // facet type with all k+1 modes is one contiguous range of the facet-major vectors:
 // DOF index ((type N + j) N + i) VS + m.
 
-// Row pass, forward: per tile read r (first updating r -= alpha q + c_prev 1,
-// lam += alpha_lam p when `update`; 1 is the constant multiplier, mode 0 on every facet),
-// accumulate r.r and the sum of the mode-0 entries of r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per
-// mode, FFT along i, split into the two rows' half spectra and store them in X.
+// Row pass, forward: per tile read r and update it: with `update`, r -= alpha q + c_prev 1 and
+// lam += alpha_lam p (1 is the constant multiplier, mode 0 on every facet); without (the first
+// pass of a solve, r holding g - S lam0), r = scale (r - c_prev 1), and the multiplier history
+// moves down one slot (hdst <- hsrc, when hsrc is set). Accumulate r.r and the sum of the
+// mode-0 entries of r, pack rows j0+2p (real part) and j0+2p+1 (imaginary part) per mode, FFT
+// along i, split into the two rows' half spectra and store them in X.
 template <int K, bool MIXED>
 __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename LatT<MIXED>::A alpha,
                              typename LatT<MIXED>::A alpha_lam, typename LatT<MIXED>::A c_prev,
                              const typename LatT<MIXED>::V* p, typename LatT<MIXED>::Acc& rr,
-                             typename LatT<MIXED>::Acc& r0sum) {
+                             typename LatT<MIXED>::Acc& r0sum, typename LatT<MIXED>::A scale,
+                             const typename LatT<MIXED>::V* hsrc, typename LatT<MIXED>::V* hdst) {
   using T = LatT<MIXED>;
   using C2 = typename T::C2;
   using R = typename T::R;
@@ -447,6 +450,16 @@ __device__ void rows_forward(const LatCtx<K, MIXED>& L, bool update, typename La
         rv[0] = rv[0] - c_prev;   // the constant-multiplier component measured last pass
         stf<NL, VS>(L.r + o, rv);
         stf<NL, VS>(L.lam + o, lv);
+      } else {
+        rv[0] = rv[0] - c_prev;
+#pragma unroll
+        for (int mm = 0; mm < NL; ++mm) rv[mm] = scale * rv[mm];
+        stf<NL, VS>(L.r + o, rv);
+        if (hsrc) {
+          A hv[NL];
+          ldf<NL, VS>(hsrc + o, hv);
+          stf<NL, VS>(hdst + o, hv);
+        }
       }
       acc_add(r0sum, rv[0]);
 #pragma unroll
@@ -699,6 +712,53 @@ __device__ __forceinline__ void spmv_lat(const DevMesh& m, int f, const X* x, XV
   for (int i = 0; i < NL; ++i) y[i] = fin(acc[i]);
 }
 
+// The warm start of a solve from the multiplier history and its image under S in one pass:
+// lam0 = c1 h1 + c2 h2 (h2 read only if use2) at facet f and at its four stencil neighbours,
+// y = (S lam0)_f. Every facet forms its own and its neighbours' lam0 with the same operations,
+// so lam0 (returned for f) is the same bits wherever it is formed.
+template <int NL, int VS, bool MIXED>
+__device__ __forceinline__ void spmv_lat_hist(const DevMesh& m, int f, const typename LatT<MIXED>::V* h1,
+                                              const typename LatT<MIXED>::V* h2, typename LatT<MIXED>::A c1,
+                                              typename LatT<MIXED>::A c2, bool use2,
+                                              typename LatT<MIXED>::A (&lam0)[NL], typename LatT<MIXED>::A (&y)[NL]) {
+  using A = typename LatT<MIXED>::A;
+  using Acc = typename LatT<MIXED>::Acc;
+  int nb[5];
+  facet_nbrs<NL>(m, f, nb);
+  const size_t sb = size_t(__ldg(&m.facet_stencil[f])) * 5 * NL * NL;
+  A xs[5][NL];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const size_t o = size_t(nb[b]) * VS;
+    ldf<NL, VS>(h1 + o, xs[b]);
+    if (use2) {
+      A t[NL];
+      ldf<NL, VS>(h2 + o, t);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) xs[b][j] = c1 * xs[b][j] + c2 * t[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) xs[b][j] = c1 * xs[b][j];
+    }
+  }
+  Acc acc[NL];
+#pragma unroll
+  for (int i = 0; i < NL; ++i) acc[i] = acc_zero(Acc{});
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const A xv = xs[b][j];
+#pragma unroll
+      for (int i = 0; i < NL; ++i) mad(acc[i], stencil_entry(m, sb + (b * NL + i) * NL + j, A{}), xv);
+    }
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    y[i] = fin(acc[i]);
+    lam0[i] = xs[0][i];
+  }
+}
+
 // g of facet f in the arithmetic type of the form
 template <int NL>
 __device__ __forceinline__ void facet_g(const DevMesh& m, int f, double (&gv)[NL]) {
@@ -841,12 +901,15 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   const int nF = m.n_facet;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   GridBar* bar = m.bar;
-  // g from both sides of every facet; warm-started lam
-  const A warm = A(a.warm_scale), hc1 = A(a.c1), hc2 = A(a.c2), hc3 = A(a.c3);
+  // g from both sides of every facet and the warm start lam0. With a history (the same stage
+  // of earlier steps), lam0 = c1 hist1 + c2 hist2 and r = g - S lam0 in the same pass (every
+  // facet forms its neighbours' lam0 from the history, which this launch only reads until
+  // the first row pass moves it down one slot); otherwise lam0 = warm_scale lam (or zero),
+  // and r = g - S lam0 takes a pass of its own after a grid barrier.
+  const A warm = A(a.warm_scale), hc1 = A(a.c1), hc2 = A(a.c2);
   V* hist1 = static_cast<V*>(a.hist1);
   V* hist2 = static_cast<V*>(a.hist2);
-  V* hist3 = static_cast<V*>(a.hist3);
-  const bool use2 = a.c2 != 0.0, use3 = a.c3 != 0.0;
+  const bool use2 = a.c2 != 0.0;
   double ga = 0.0;
   Acc g0 = acc_zero(Acc{});
 #pragma unroll 4
@@ -855,34 +918,27 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
     A gv[NL], lv[NL];
     facet_g<NL>(m, f, gv);
     if (hist1) {
-      // extrapolation from the same stage of earlier steps; the history shifts by one
-      A h1[NL], h2[NL];
-      ldf<NL, VS>(hist1 + o, h1);
-      if (use2 || hist3) ldf<NL, VS>(hist2 + o, h2);
+      A y[NL];
+      spmv_lat_hist<NL, VS, MIXED>(m, f, hist1, hist2, hc1, hc2, use2, lv, y);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) lv[j] = use2 ? hc1 * h1[j] + hc2 * h2[j] : hc1 * h1[j];
-      if (use3) {
-        A h3[NL];
-        ldf<NL, VS>(hist3 + o, h3);
-#pragma unroll
-        for (int j = 0; j < NL; ++j) lv[j] = lv[j] + hc3 * h3[j];
-      }
-      if (hist3) stf<NL, VS>(hist3 + o, h2);
-      stf<NL, VS>(hist2 + o, h1);
-    } else if (a.warm_scale != 0.0) {
-      ldf<NL, VS>(L.lam + o, lv);
-#pragma unroll
-      for (int j = 0; j < NL; ++j) lv[j] = warm * lv[j];
+      for (int j = 0; j < NL; ++j) y[j] = gv[j] - y[j];
+      stf<NL, VS>(L.r + o, y);
     } else {
+      if (a.warm_scale != 0.0) {
+        ldf<NL, VS>(L.lam + o, lv);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) lv[j] = A(0);
+        for (int j = 0; j < NL; ++j) lv[j] = warm * lv[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) lv[j] = A(0);
+      }
+      stf<NL, VS>(L.g + o, gv);
     }
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const double lead = lead_d(gv[j]);
       ga = fma(lead, lead, ga);
     }
-    stf<NL, VS>(L.g + o, gv);
     stf<NL, VS>(L.lam + o, lv);
     acc_add(g0, gv[0]);
   }
@@ -910,35 +966,42 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
   double relres = 0.0;
   if (gnorm == 0.0) {
     for (int f = gtid; f < nF; f += gsz) {
+      const size_t o = size_t(f) * VS;
       A zero[NL];
 #pragma unroll
       for (int j = 0; j < NL; ++j) zero[j] = A(0);
-      stf<NL, VS>(L.lam + size_t(f) * VS, zero);
+      stf<NL, VS>(L.lam + o, zero);
+      if (hist1) {
+        A hv[NL];
+        ldf<NL, VS>(hist1 + o, hv);
+        stf<NL, VS>(hist2 + o, hv);
+      }
     }
     conv = true;
   } else {
-    // r = sigma (g - S lam) with the constant component of g removed
-    const A c0a = A(c0), sg = A(sigma);
+    if (!hist1) {
+      // r = g - S lam0
 #pragma unroll 4
-    for (int f = gtid; f < nF; f += gsz) {
-      const size_t o = size_t(f) * VS;
-      A y[NL], gv[NL], rv[NL];
-      spmv_lat<NL, VS, MIXED>(m, f, L.lam, A{}, y);
-      ldf<NL, VS>(L.g + o, gv);
-      gv[0] = gv[0] - c0a;
+      for (int f = gtid; f < nF; f += gsz) {
+        const size_t o = size_t(f) * VS;
+        A y[NL], gv[NL];
+        spmv_lat<NL, VS, MIXED>(m, f, L.lam, A{}, y);
+        ldf<NL, VS>(L.g + o, gv);
 #pragma unroll
-      for (int j = 0; j < NL; ++j) rv[j] = sg * (gv[j] - y[j]);
-      stf<NL, VS>(L.g + o, gv);
-      stf<NL, VS>(L.r + o, rv);
+        for (int j = 0; j < NL; ++j) y[j] = gv[j] - y[j];
+        stf<NL, VS>(L.r + o, y);
+      }
+      if (!grid_sync(bar, m.stats)) return;
     }
-    if (!grid_sync(bar, m.stats)) return;
     // z = M r
     // The constant multiplier is in the kernel of S and of the preconditioner, so PCG cannot
     // reduce r's component along it; rounding in every update adds to it (relative size
     // eps times the cancellation in S q). It is measured with r.r (the sum of the mode-0
     // entries), left out of the convergence test, and subtracted from r in the next update.
+    // The first row pass scales r by sigma and removes the constant component of g from it:
+    // r = sigma (g - c0 1 - S lam0).
     Acc rra[2] = {acc_zero(Acc{}), acc_zero(Acc{})};
-    rows_forward<K, MIXED>(L, false, A(0), A(0), A(0), p, rra[0], rra[1]);
+    rows_forward<K, MIXED>(L, false, A(0), A(0), A(c0), p, rra[0], rra[1], A(sigma), hist1, hist2);
     double rr[2];
     if (!lat_reduce<2>(m, 6, rra, bar, rr)) return;
     double cmode = rr[1] / double(nF);
@@ -1020,7 +1083,7 @@ __global__ void __launch_bounds__(kLatThreads, 2) k_solve_lat(DevMesh m, SolveAr
       // r -= alpha q, lam += alpha p, and the forward row pass of z = M r
       rra[0] = acc_zero(Acc{});
       rra[1] = acc_zero(Acc{});
-      rows_forward<K, MIXED>(L, true, sc.alpha, sc.alpha_lam, A(cmode), p, rra[0], rra[1]);
+      rows_forward<K, MIXED>(L, true, sc.alpha, sc.alpha_lam, A(cmode), p, rra[0], rra[1], A(1), nullptr, nullptr);
       if (!lat_reduce<2>(m, 6, rra, bar, rr)) return;
       cmode = rr[1] / double(nF);
       const double rr_prev = rrv;
