@@ -354,9 +354,11 @@ int dg_test_multilevel_apply(dg_mesh* mesh, const double* r, double* z, int on_d
  * The state after such a solve is undefined; (0, -1) restores normal operation. */
 int dg_test_barrier_fault(dg_mesh* mesh, int64_t spin_limit, int skip_block);
 
-/* Per-kernel-class device timing. enable = 1 makes the library record a CUDA
- * event pair on its stream around every kernel launch from then on and add the
- * elapsed times up at the end of each call; enable = 0 stops recording,
+/* Per-kernel-class device timing. enable = 1 makes the library record CUDA events
+ * on its stream around every kernel launch from then on and add the elapsed times
+ * up at the end of each call; inside a time step, a launch that directly follows
+ * another starts at that launch's end event (one event per kernel boundary; the
+ * launch gap counts in the following kernel). enable = 0 stops recording,
  * enable = 2 resets the totals. out_ms / out_launches (each n entries, or NULL)
  * receive the totals per class in the order of dg_kernel_name(0..). */
 int dg_profile(dg_mesh* mesh, int enable, double* out_ms, int64_t* out_launches, int n);

@@ -109,7 +109,12 @@ struct dg_mesh {
   struct Rec {
     int kc;
     cudaEvent_t a, b;
+    bool owns_a;   // false: a is the previous record's b (chained launches)
   };
+  // inside a step, consecutive launches share one event: the end of a launch is the start of
+  // the next (a non-kernel operation between them clears prof_prev)
+  bool prof_chain = false;
+  cudaEvent_t prof_prev = nullptr;
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
   double prof_ms[KC_COUNT] = {};
@@ -180,20 +185,37 @@ cudaEvent_t get_event(dg_mesh* M) {
   return e;
 }
 
-// Launch wrapper: records an event pair around the launch when profiling.
+// Launch wrapper: records an event pair around the launch when profiling. Inside a step
+// (prof_chain) a launch that directly follows another starts at that launch's end event, so
+// that a step records one event per kernel boundary; the launch gap is then counted in the
+// following kernel's time.
 template <typename F>
 int launch(dg_mesh* M, int kc, F&& f) {
   cudaEvent_t a = nullptr, b = nullptr;
+  bool owns_a = true;
   if (M->prof) {
-    a = get_event(M);
+    if (M->prof_chain && M->prof_prev) {
+      a = M->prof_prev;
+      owns_a = false;
+    } else {
+      a = get_event(M);
+      cudaEventRecord(a, M->stream);
+    }
     b = get_event(M);
-    cudaEventRecord(a, M->stream);
   }
+  M->prof_prev = nullptr;
   cudaError_t e = f();
-  if (e != cudaSuccess) return fail(DG_ERR_CUDA, std::string("kernel launch (") + kKernelNames[kc] + "): " + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    if (M->prof) {   // give back the events of the failed launch
+      if (owns_a) M->pool.push_back(a);
+      M->pool.push_back(b);
+    }
+    return fail(DG_ERR_CUDA, std::string("kernel launch (") + kKernelNames[kc] + "): " + cudaGetErrorString(e));
+  }
   if (M->prof) {
     cudaEventRecord(b, M->stream);
-    M->pending.push_back({kc, a, b});
+    M->pending.push_back({kc, a, b, owns_a});
+    if (M->prof_chain) M->prof_prev = b;
   }
   return DG_OK;
 }
@@ -205,10 +227,11 @@ void collect_profile(dg_mesh* M) {
       M->prof_ms[r.kc] += ms;
       M->prof_n[r.kc] += 1;
     }
-    M->pool.push_back(r.a);
+    if (r.owns_a) M->pool.push_back(r.a);
     M->pool.push_back(r.b);
   }
   M->pending.clear();
+  M->prof_prev = nullptr;
 }
 
 // Synchronise the stream, gather profiling, translate device flags to a status.
@@ -318,6 +341,7 @@ int solve(dg_mesh* M, double warm_scale, int stage = -1, double dt = 0.0, bool h
 int push_history(dg_mesh* M, int s, double dt) {
   if (M->hist_len == 0) return DG_OK;
   const void* lam = M->dm.lam_is_df ? static_cast<const void*>(M->dm.lam_df) : static_cast<const void*>(M->dm.lam);
+  M->prof_prev = nullptr;   // a copy between two launches: no chained profiling event across it
   CK(cudaMemcpyAsync(M->hist[s][0], lam, M->hist_bytes, cudaMemcpyDeviceToDevice, M->stream));
   for (int h = M->hist_len - 1; h > 0; --h) M->hist_dt[s][h] = M->hist_dt[s][h - 1];
   M->hist_dt[s][0] = dt;
@@ -971,7 +995,17 @@ int ensure_rk_w(dg_mesh* M) {
 // condensation kernel, the facet solve (warm-started from the previous stage's
 // multipliers rescaled by the ratio of the L coefficients, or from the same stage of the
 // last steps) and the recovery. No synchronisation.
+struct ProfChain {   // chained profiling events for the launches of one step
+  dg_mesh* M;
+  explicit ProfChain(dg_mesh* m) : M(m) { M->prof_chain = true; }
+  ~ProfChain() {
+    M->prof_chain = false;
+    M->prof_prev = nullptr;
+  }
+};
+
 int enqueue_step(dg_mesh* M, double dt, int scheme = DG_SCHEME_SSPRK3) {
+  ProfChain chain(M);
   dgdf::DevMesh& d = M->dm;
   const Scheme& sc = kSchemes[scheme];
   int rc = ensure_udf(M);
@@ -999,8 +1033,9 @@ int enqueue_step(dg_mesh* M, double dt, int scheme = DG_SCHEME_SSPRK3) {
     sa.up_df = (s == 0) ? d.u_df : d.ustage_df;
     if ((rc = launch(M, KC_STAGE, [&] { return dgdf::launch_stage(d, sa, M->stream); }))) return rc;
     const double warm = M->has_lam ? sa.c / M->last_c : 0.0;
-    if ((rc = solve(M, warm, s, dt)) || (rc = push_history(M, s, dt))) return rc;
+    if ((rc = solve(M, warm, s, dt))) return rc;
     if ((rc = launch(M, KC_RECOVER, [&] { return dgdf::launch_recover(d, out, out_df, M->stream); }))) return rc;
+    if ((rc = push_history(M, s, dt))) return rc;
     M->last_c = sa.c;
     M->has_lam = true;
     if (k.wop) {
