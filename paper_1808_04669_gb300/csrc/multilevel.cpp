@@ -389,6 +389,61 @@ void vcycle(const HostMesh& hm, const MLHost& ml, size_t l, const double* b, dou
   smooth(hm, L, b, x1.data(), x);
 }
 
+// Pseudo-inverse of the coarsest operator A (symmetric positive semi-definite, nc rows), dense,
+// symmetrised. Up to 256 rows: from its eigen-decomposition, the eigenvalues below 1e-10 of the
+// largest dropped. Larger (the Jacobi eigensolver's cost grows as nc^3 per sweep): when the
+// near-null vector v is in the kernel (|A v| <= 1e-9 |A|_F |v|, a closed mesh), through the
+// definite matrix B = A + s u u^T (u = v / |v|, s the mean diagonal entry), whose inverse is
+// A^+ + u u^T / s, so that A^+ = B^-1 - u u^T / s; otherwise (A definite) A^-1. Both by
+// Gauss-Jordan elimination with partial pivoting. Returns false if the matrix is singular.
+bool coarse_pinv(const CsrHost& A, const Vec& v, Vec& out) {
+  const int nc = A.n_rows;
+  Vec D(size_t(nc) * nc, 0.0);
+  for (int r = 0; r < nc; ++r)
+    for (int p = A.rp[r]; p < A.rp[r + 1]; ++p) D[size_t(r) * nc + A.ci[p]] += A.v[p];
+  for (int r = 0; r < nc; ++r)
+    for (int c = r + 1; c < nc; ++c) {
+      const double h = 0.5 * (D[size_t(r) * nc + c] + D[size_t(c) * nc + r]);
+      D[size_t(r) * nc + c] = D[size_t(c) * nc + r] = h;
+    }
+  out.assign(size_t(nc) * nc, 0.0);
+  if (nc <= 256) {
+    Vec ev, V;
+    symmetric_eigen(D, nc, ev, V);
+    double emax = 0.0;
+    for (double e : ev) emax = std::max(emax, std::fabs(e));
+    for (int i = 0; i < nc; ++i) {
+      if (!(ev[i] > 1e-10 * emax)) continue;
+      const double inv = 1.0 / ev[i];
+      for (int r = 0; r < nc; ++r)
+        for (int c = 0; c < nc; ++c) out[size_t(r) * nc + c] += V[size_t(r) * nc + i] * inv * V[size_t(c) * nc + i];
+    }
+    return true;
+  }
+  double fro = 0.0, vv = 0.0, avv = 0.0, tr = 0.0;
+  for (double x : D) fro += x * x;
+  for (int r = 0; r < nc; ++r) {
+    double y = 0.0;
+    for (int c = 0; c < nc; ++c) y += D[size_t(r) * nc + c] * v[c];
+    avv += y * y;
+    vv += v[r] * v[r];
+    tr += D[size_t(r) * nc + r];
+  }
+  const bool kernel = vv > 0.0 && std::sqrt(avv) <= 1e-9 * std::sqrt(fro) * std::sqrt(vv);
+  const double s = tr / nc;
+  if (kernel)
+    for (int r = 0; r < nc; ++r)
+      for (int c = 0; c < nc; ++c) D[size_t(r) * nc + c] += s * v[r] * v[c] / vv;
+  if (!host_invert(D, nc)) return false;
+  for (int r = 0; r < nc; ++r)
+    for (int c = 0; c < nc; ++c) {
+      double x = 0.5 * (D[size_t(r) * nc + c] + D[size_t(c) * nc + r]);
+      if (kernel) x -= v[r] * v[c] / (vv * s);
+      out[size_t(r) * nc + c] = x;
+    }
+  return true;
+}
+
 }  // namespace
 
 int build_multilevel(const HostMesh& hm, MLHost& ml, std::string& err) {
@@ -462,31 +517,16 @@ int build_multilevel(const HostMesh& hm, MLHost& ml, std::string& err) {
   }
   // aggregation made no progress on the mode-0 operator: it is the coarsest level itself
   if (!ml.lv.empty() && ml.lv.back().stencil && ml.lv.back().bs == 1 && ml.lv.back().P.n_rows == 0) ml.lv.pop_back();
-  // coarsest: pseudo-inverse of the remaining operator (its kernel, the near-null vector,
-  // is dropped with the eigenvalues below 1e-10 of the largest)
+  // coarsest: pseudo-inverse of the remaining operator (coarse_pinv)
   const int nc = A.n_rows;
   if (nc > 4 * kMLCoarseMax) {
     err = "multilevel: coarsening stalled";
     return DG_ERR_UNSUPPORTED;
   }
-  std::vector<double> D(size_t(nc) * nc, 0.0), ev, V;
-  for (int r = 0; r < nc; ++r)
-    for (int p = A.rp[r]; p < A.rp[r + 1]; ++p) D[size_t(r) * nc + A.ci[p]] += A.v[p];
-  for (int r = 0; r < nc; ++r)
-    for (int c = r + 1; c < nc; ++c) {
-      const double s = 0.5 * (D[size_t(r) * nc + c] + D[size_t(c) * nc + r]);
-      D[size_t(r) * nc + c] = D[size_t(c) * nc + r] = s;
-    }
-  symmetric_eigen(D, nc, ev, V);
-  double emax = 0.0;
-  for (double e : ev) emax = std::max(emax, std::fabs(e));
   ml.nc = nc;
-  ml.cpinv.assign(size_t(nc) * nc, 0.0);
-  for (int i = 0; i < nc; ++i) {
-    if (!(ev[i] > 1e-10 * emax)) continue;
-    const double inv = 1.0 / ev[i];
-    for (int r = 0; r < nc; ++r)
-      for (int c = 0; c < nc; ++c) ml.cpinv[size_t(r) * nc + c] += V[size_t(r) * nc + i] * inv * V[size_t(c) * nc + i];
+  if (!coarse_pinv(A, nn, ml.cpinv)) {
+    err = "multilevel: singular coarsest operator";
+    return DG_ERR_MESH;
   }
   if (!ml.lv.empty()) {
     ml.lv.back().n_next = nc;
@@ -635,24 +675,10 @@ int build_multilevel_csr(const CsrHost& A0, int nl, const int32_t* cls, const st
     err = "multilevel: coarsening stalled";
     return DG_ERR_UNSUPPORTED;
   }
-  std::vector<double> D(size_t(nc) * nc, 0.0), ev, V;
-  for (int r = 0; r < nc; ++r)
-    for (int p = A.rp[r]; p < A.rp[r + 1]; ++p) D[size_t(r) * nc + A.ci[p]] += A.v[p];
-  for (int r = 0; r < nc; ++r)
-    for (int c = r + 1; c < nc; ++c) {
-      const double s = 0.5 * (D[size_t(r) * nc + c] + D[size_t(c) * nc + r]);
-      D[size_t(r) * nc + c] = D[size_t(c) * nc + r] = s;
-    }
-  symmetric_eigen(D, nc, ev, V);
-  double emax = 0.0;
-  for (double e : ev) emax = std::max(emax, std::fabs(e));
   ml.nc = nc;
-  ml.cpinv.assign(size_t(nc) * nc, 0.0);
-  for (int i = 0; i < nc; ++i) {
-    if (!(ev[i] > 1e-10 * emax)) continue;
-    const double inv = 1.0 / ev[i];
-    for (int r = 0; r < nc; ++r)
-      for (int c = 0; c < nc; ++c) ml.cpinv[size_t(r) * nc + c] += V[size_t(r) * nc + i] * inv * V[size_t(c) * nc + i];
+  if (!coarse_pinv(A, nn, ml.cpinv)) {
+    err = "multilevel: singular coarsest operator";
+    return DG_ERR_MESH;
   }
   ml.lv.back().n_next = nc;
   return DG_OK;

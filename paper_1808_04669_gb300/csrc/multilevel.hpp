@@ -14,8 +14,9 @@
 //   tentative prolongator from the near-null vector carried down the levels (so
 //   the kernel stays exact on every level), one Jacobi smoothing step of the
 //   prolongator, Galerkin coarse operators R A P with R = P^T.
-//   The coarsest operator (<= kMLCoarseMax rows) is applied through its
-//   pseudo-inverse.
+//   The coarsest operator (<= kMLCoarseMax rows) is applied through its dense
+//   pseudo-inverse (one grid-wide phase, where every further level would take
+//   four or five).
 // Smoothing: Chebyshev polynomials of degree 2 in B A with B the block-Jacobi
 // inverse, on [lmax / 4, 1.1 lmax], lmax estimated by Lanczos (from CG
 // coefficients). Pre- and post-smoothing use the same polynomial, so one V-cycle
@@ -31,7 +32,7 @@
 namespace dgdf {
 
 constexpr int kMLMaxLevels = 16;
-constexpr int kMLCoarseMax = 256;
+constexpr int kMLCoarseMax = 768;
 
 struct CsrHost {
   int n_rows = 0, n_cols = 0;
