@@ -11,7 +11,8 @@ oracle and sharing no code with the CUDA path:
 * the hybrid-mixed system eq. (12), condensed per element and solved by a sparse LU with one
   multiplier pinned (the constant multiplier is the kernel on a closed mesh), and the
   uncondensed saddle system as an independent route;
-* SSP-RK3 (eq. (8)) in the paper's stage form.
+* SSP-RK3 (eq. (8)) in the paper's stage form;
+* the pressure: (w, lam) of eq. (12) with the functional L(u) alone, mean-free (eq. (4e)).
 
 Faces. A face is parametrised in canonical coordinates (s, t): x = p0 + s (p1 - p0) + t (p2 - p0)
 with p0, p1, p2 its vertices in increasing periodic vertex id. Both sides of a face evaluate at
@@ -405,6 +406,32 @@ class Discretization3:
             U2 = self.stage(U, U1, *RK3_STAGES[1], dt)
             U = self.stage(U, U2, *RK3_STAGES[2], dt)
         return U
+
+    def pressure(self, U):
+        """(w, lam) of eq. (12) with the functional L(u) alone (Theorem 2, Remark 2): w ~ p in the
+        elements and lam ~ p on the faces, both shifted by one constant so that the integral of w
+        is zero (L^2_0, eq. (4e)). The Bernstein bases are partitions of unity, so the constant
+        is the same shift of every coefficient."""
+        _, w, lam = self.solve_condensed(self.residual(U))
+        tet = np.arange(self.n_tet)
+        P, W = self._vol(tet)
+        Z, _ = self._basis(self.wexps, tet, P)
+        c = np.einsum("tq,tqm,tm->", W, Z, w) / W.sum()
+        return w - c, lam - c
+
+    def pressure_lattice(self, w, lam):
+        """Element pressure at the degree-(k-1) lattice points of each tetrahedron [n_tet, n_lat(k-1)]
+        (the centroid for k = 1), face pressure at the degree-k lattice points of each face in
+        canonical coordinates, (s, t) = (i/k, j/k), j = 0..k, i = 0..k-j (i fastest) [n_face, nl]."""
+        T = self.topo
+        xi = self._lattice_xi(self.k - 1)
+        P = T.X[:, 0][:, None, :] + np.einsum("tij,qj->tqi", T.J, xi)
+        Z, _ = self._basis(self.wexps, np.arange(self.n_tet), P)
+        pe = np.einsum("tqm,tm->tq", Z, np.asarray(w).reshape(self.n_tet, self.nw))
+        k = self.k
+        st = np.array([(i / k, j / k) for j in range(k + 1) for i in range(k + 1 - j)])
+        pf = np.asarray(lam).reshape(self.n_face, self.nl) @ self._face_basis(st)
+        return pe, pf
 
     # ------------------------------------------------------------- lattice
     def _lattice_xi(self, m):
