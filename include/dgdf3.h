@@ -64,6 +64,18 @@ int dg3_project_divfree(dg_mesh3* mesh);
  * that history, dg3_project_divfree drops it. Errors as dg3_project_divfree. */
 int dg3_rk3_step(dg_mesh3* mesh, double dt, int64_t nsteps);
 
+/* Pressure of the current state: the (w, lam) of eq. (12) with the functional L(u) alone, so
+ * w ~ p in the tetrahedra and lam ~ p on the faces (Theorem 2, Remark 2), shifted by one constant
+ * so that the integral of w over the domain is zero (L^2_0, eq. (4e)).
+ * p_elem [n_tet][n_lat3(k-1)]: w at the degree-(k-1) lattice points of each tetrahedron (the
+ * order of the velocity lattice with k - 1 for k; the centroid for k = 1).
+ * p_face [n_face][(k+1)(k+2)/2] or NULL: lam at the points p0 + (i/k)(p1 - p0) + (j/k)(p2 - p0),
+ * j = 0..k, i = 0..k-j (i fastest), p0, p1, p2 the face's vertices in increasing periodic vertex
+ * id; faces are numbered in order of first appearance over the tetrahedra t = 0, 1, ... and
+ * their local faces e = 0..3.
+ * Host or device memory. Errors as dg3_project_divfree. */
+int dg3_get_pressure(dg_mesh3* mesh, double* p_elem, double* p_face, int on_device);
+
 /* The Riesz representer of L(u) (eq. (6)) of the current state, as lattice values. */
 int dg3_eval_residual(dg_mesh3* mesh, double* vals, int on_device);
 

@@ -307,6 +307,17 @@ class DGMesh3:
         check(lib().dg3_eval_residual(self._h, p, dev), "dg3_eval_residual")
         return out
 
+    def get_pressure(self, with_face=True):
+        """(p_elem [n_tet, n_lat3(k-1)], p_face [n_face, (k+1)(k+2)/2] or None) of the current
+        state, mean-free (dg3_get_pressure)."""
+        k = self.k
+        pe = np.empty((self.n_tet, k * (k + 1) * (k + 2) // 6))
+        pf = np.empty((self.n_face, (k + 1) * (k + 2) // 2)) if with_face else None
+        p, dev = _ptr(pe)
+        q = _ptr(pf)[0] if pf is not None else None
+        check(lib().dg3_get_pressure(self._h, p, q, dev), "dg3_get_pressure")
+        return pe, pf
+
     def diagnostics(self):
         out = (ctypes.c_double * 8)()
         check(lib().dg3_get_diagnostics(self._h, out), "dg3_get_diagnostics")

@@ -37,6 +37,8 @@ struct dg_mesh3 {
   int hist_n[3] = {};
   double* lattice = nullptr;          // [n_tet][ns][3] staging
   dgdf::DevStats* host_stats = nullptr;
+  double *pe = nullptr, *pf = nullptr, *ppart = nullptr;   // pressure outputs and scratch (first use)
+  double volume = 0.0;                // of the domain
 };
 
 namespace {
@@ -179,7 +181,7 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
   d.n_stencil = hm.n_stencil;
   d.nu = p.nu;
   const int nd = hm.nd, L4 = 4 * hm.nl;
-  std::vector<double> geo(size_t(d.n_class) * dgdf::kGeo3, 0.0), P, G;
+  std::vector<double> geo(size_t(d.n_class) * dgdf::kGeo3, 0.0), P, G, W, WC;
   for (int c = 0; c < d.n_class; ++c) {
     const dgdf::Class3& co = hm.classes[c];
     double* g = &geo[size_t(c) * dgdf::kGeo3];
@@ -193,12 +195,17 @@ int dg3_mesh_create(int64_t n_tet, const int64_t* tet_vertex_ids, const double* 
     }
     P.insert(P.end(), co.P.begin(), co.P.end());
     G.insert(G.end(), co.G.begin(), co.G.end());
+    W.insert(W.end(), co.W.begin(), co.W.end());
+    WC.insert(WC.end(), co.WC.begin(), co.WC.end());
   }
+  for (int64_t t = 0; t < hm.n_tet; ++t) M->volume += hm.classes[hm.tet_class[t]].det / 6.0;
   if ((rc = upload3(M, &d.vw, ref.vw)) || (rc = upload3(M, &d.vphi, ref.vphi)) ||
       (rc = upload3(M, &d.vdphi, ref.vdphi)) || (rc = upload3(M, &d.fw, ref.fw)) ||
       (rc = upload3(M, &d.fphi, ref.fphi)) || (rc = upload3(M, &d.fdphi, ref.fdphi)) ||
       (rc = upload3(M, &d.lat_phi, ref.lat_phi)) || (rc = upload3(M, &d.lat_inv, ref.lat_inv)) ||
       (rc = upload3(M, &d.geo, geo)) || (rc = upload3(M, &d.P, P)) || (rc = upload3(M, &d.G, G)) ||
+      (rc = upload3(M, &d.W, W)) || (rc = upload3(M, &d.WC, WC)) || (rc = upload3(M, &d.plat_phi, ref.plat_phi)) ||
+      (rc = upload3(M, &d.mu_lat, ref.mu_lat)) ||
       (rc = upload3(M, &d.tet_class, hm.tet_class)) || (rc = upload3(M, &d.tet_nbr, hm.tet_nbr)) ||
       (rc = upload3(M, &d.tet_face, hm.tet_face)) || (rc = upload3(M, &d.tet_nbr_loc, hm.tet_nbr_loc)) ||
       (rc = upload3(M, &d.face_sigma, hm.face_sigma)) || (rc = upload3(M, &d.face_tet, hm.face_tet)) ||
@@ -387,6 +394,31 @@ int dg3_rk3_step(dg_mesh3* M, double dt, int64_t nsteps) {
       M->last_c = a.c;
       M->has_lam = true;
     }
+  return finish3(M, true);
+}
+
+int dg3_get_pressure(dg_mesh3* M, double* p_elem, double* p_face, int on_device) {
+  if (int rc = check3(M)) return rc;
+  if (!p_elem) return api_fail(DG_ERR_INVALID_ARG, "NULL p_elem");
+  int rc = reset3(M);
+  if (rc) return rc;
+  dgdf::DevMesh3& d = M->dm;
+  const size_t npe = size_t(d.n_tet) * d.nw, npf = size_t(d.n_face) * d.nl;
+  if (!M->pe && ((rc = dalloc3(M, &M->pe, npe)) || (rc = dalloc3(M, &M->pf, npf)) ||
+                 (rc = dalloc3(M, &M->ppart, size_t(dgdf::pressure3_parts(d))))))
+    return rc;
+  // the functional L(u) alone (eq. (12) with F = L(u), Theorem 2, Remark 2)
+  dgdf::StageArgs a{};
+  a.mode = dgdf::MODE_PRESSURE;
+  a.up = d.u;
+  a.un = d.u;
+  CK3(dgdf::launch_stage3(d, a, M->stream));
+  if ((rc = solve3(M, 0.0))) return rc;
+  CK3(dgdf::launch_pressure3(d, M->pe, p_face ? M->pf : nullptr, M->ppart, M->volume, M->stream));
+  M->has_lam = false;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK3(cudaMemcpyAsync(p_elem, M->pe, npe * sizeof(double), kind, M->stream));
+  if (p_face) CK3(cudaMemcpyAsync(p_face, M->pf, npf * sizeof(double), kind, M->stream));
   return finish3(M, true);
 }
 

@@ -24,6 +24,9 @@ struct DevMesh3 {
   const double *vw, *vphi, *vdphi, *fw, *fphi, *fdphi, *lat_phi, *lat_inv;
   const double* geo;                  // [n_class][kGeo3]
   const double *P, *G;                // [n_class][nd][nd], [n_class][4 nl][nd]
+  const double *W, *WC;               // pressure rows [n_class][nw][nd], [n_class][nw][4 nl]
+  const double *plat_phi, *mu_lat;    // P^(k-1) basis at the (k-1)-lattice [nw][nw]; face basis
+                                      // at the face's k-lattice [nl][nl]
   const int32_t *tet_class, *tet_nbr, *tet_face;
   const int8_t* tet_nbr_loc;
   const double* face_sigma;           // [n_face]
@@ -46,6 +49,11 @@ int solver3_blocks(const DevMesh3& m);
 cudaError_t launch_lattice_to_coef3(const DevMesh3& m, const double* vals, double* coef, cudaStream_t s);
 cudaError_t launch_coef_to_lattice3(const DevMesh3& m, const double* coef, double* vals, cudaStream_t s);
 cudaError_t launch_diagnostics3(const DevMesh3& m, const double* coef, cudaStream_t s);
+// Pressure from h = f (MODE_PRESSURE) and lam: pe [n_tet][nw] lattice values and pf [n_face][nl]
+// (NULL: not written), shifted to a zero mean over the domain of volume vol; part holds
+// pressure3_parts(m) doubles of scratch.
+int pressure3_parts(const DevMesh3& m);
+cudaError_t launch_pressure3(const DevMesh3& m, double* pe, double* pf, double* part, double vol, cudaStream_t s);
 // FP64 PCG with the multilevel preconditioner of an assembled hierarchy (k_multilevel.cu): mv
 // holds the hierarchy (ml_*), the PCG vectors r and z, red, bar and stats
 int solver3_ml_blocks(const DevMesh3& m, bool fp32);   // fp32: the V-cycle in FP32 (mv.ml_lv_f)

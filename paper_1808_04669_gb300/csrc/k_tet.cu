@@ -3,6 +3,8 @@
 // One thread per tetrahedron in the element kernels; the volume tables sit in shared memory,
 // the face tables (four local faces x six vertex orderings) are read through the L1 cache.
 // Conventions (canonical face coordinates, perm index, face rule): setup3.hpp.
+#include <algorithm>
+
 #include "device3.cuh"
 #include "kcommon.cuh"
 #include "solver_common.cuh"
@@ -175,8 +177,8 @@ __device__ void tet_residual(const DevMesh3& m, const VolTables3<K>& T, int t, c
 }
 
 // Stage kernel (modes as StageMode): f = a u^n + b u' + c L(u') (MODE_STAGE), L(u') alone
-// (MODE_RESIDUAL: h = f, the Riesz representer since M = I), or f = u' (MODE_PROJECT); then
-// h = P f and gl = G f per class.
+// (MODE_RESIDUAL: h = f, the Riesz representer since M = I; MODE_PRESSURE: h = f and gl = G f),
+// or f = u' (MODE_PROJECT); then h = P f and gl = G f per class.
 template <int K>
 __global__ void __launch_bounds__(kTetThreads) k_stage3(DevMesh3 m, StageArgs a) {
   using D = Dims3<K>;
@@ -199,20 +201,21 @@ __global__ void __launch_bounds__(kTetThreads) k_stage3(DevMesh3 m, StageArgs a)
       for (int i = 0; i < ND; ++i) f[i] = a.a * a.un[size_t(t) * ND + i] + a.b * up[i] + a.c * f[i];
     }
   }
-  if (a.mode == MODE_RESIDUAL) {
+  if (a.mode == MODE_RESIDUAL || a.mode == MODE_PRESSURE) {
 #pragma unroll
     for (int i = 0; i < ND; ++i) m.h[size_t(t) * ND + i] = f[i];
-    return;
+    if (a.mode == MODE_RESIDUAL) return;
   }
   const int cls = m.tet_class[t];
   const double* P = m.P + size_t(cls) * ND * ND;
   const double* G = m.G + size_t(cls) * L4 * ND;
-  for (int i = 0; i < ND; ++i) {
-    double v = 0.0;
+  if (a.mode != MODE_PRESSURE)
+    for (int i = 0; i < ND; ++i) {
+      double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < ND; ++j) v += __ldg(&P[i * ND + j]) * f[j];
-    m.h[size_t(t) * ND + i] = v;
-  }
+      for (int j = 0; j < ND; ++j) v += __ldg(&P[i * ND + j]) * f[j];
+      m.h[size_t(t) * ND + i] = v;
+    }
   for (int i = 0; i < L4; ++i) {
     double v = 0.0;
 #pragma unroll
@@ -241,6 +244,78 @@ __global__ void __launch_bounds__(kTetThreads) k_recover3(DevMesh3 m, double* ou
 #pragma unroll
     for (int l = 0; l < L4; ++l) v -= __ldg(&G[l * ND + i]) * lam[l];
     out[size_t(t) * ND + i] = v;
+  }
+}
+
+// Element pressure of eq. (12) (h = f of MODE_PRESSURE, lam the solve's multipliers):
+// w = W (f - C^T lam) = W f - WC lam, in the basis s phi_m (m < nw) of P^(k-1); its values at the
+// (k-1)-lattice points go to pe, and each block's sum of the integrals of w to part.
+template <int K>
+__global__ void __launch_bounds__(kTetThreads) k_pressure3(DevMesh3 m, double* pe, double* part) {
+  using D = Dims3<K>;
+  constexpr int ND = D::ND, NS = D::NS, NL = D::NL, L4 = 4 * NL, NW = K * (K + 1) * (K + 2) / 6;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double integral = 0.0;
+  if (t < m.n_tet) {
+    double f[ND], lam[L4], w[NW];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) f[i] = m.h[size_t(t) * ND + i];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int fc = m.tet_face[size_t(t) * 4 + e];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) lam[e * NL + j] = m.lam[size_t(fc) * NL + j];
+    }
+    const int cls = m.tet_class[t];
+    const double* W = m.W + size_t(cls) * NW * ND;
+    const double* WC = m.WC + size_t(cls) * NW * L4;
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) v += __ldg(&W[a * ND + j]) * f[j];
+#pragma unroll
+      for (int l = 0; l < L4; ++l) v -= __ldg(&WC[a * L4 + l]) * lam[l];
+      w[a] = v;
+    }
+    const double sc = m.geo[size_t(cls) * kGeo3 + G3_S], det = m.geo[size_t(cls) * kGeo3 + G3_DET];
+#pragma unroll
+    for (int p = 0; p < NW; ++p) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < NW; ++a) v += __ldg(&m.plat_phi[p * NW + a]) * w[a];
+      pe[size_t(t) * NW + p] = sc * v;
+    }
+    for (int q = 0; q < D::NQ; ++q) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < NW; ++a) v += __ldg(&m.vphi[q * NS + a]) * w[a];
+      integral += __ldg(&m.vw[q]) * v;
+    }
+    integral *= det * sc;
+  }
+  integral = block_sum(integral);
+  if (threadIdx.x == 0) part[blockIdx.x] = integral;
+}
+
+// The mean c = (sum of the block integrals) / vol, the same in every block (fixed order); pe -= c,
+// and the face pressure pf = (the multiplier basis at the face's k-lattice) lam - c.
+__global__ void k_pressure3_finish(DevMesh3 m, double* pe, double* pf, const double* part, int nparts, double vol) {
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) a += part[b];
+  const double c = block_sum(a) / vol;
+  const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x, gsz = size_t(gridDim.x) * blockDim.x;
+  const size_t npe = size_t(m.n_tet) * m.nw;
+  for (size_t i = gtid; i < npe; i += gsz) pe[i] -= c;
+  if (!pf) return;
+  const int nl = m.nl;
+  const size_t npf = size_t(m.n_face) * nl;
+  for (size_t i = gtid; i < npf; i += gsz) {
+    const size_t fc = i / nl;
+    const int p = int(i - fc * nl);
+    double v = 0.0;
+    for (int j = 0; j < nl; ++j) v += __ldg(&m.mu_lat[p * nl + j]) * m.lam[fc * nl + j];
+    pf[i] = v - c;
   }
 }
 
@@ -611,6 +686,17 @@ cudaError_t launch_diagnostics3(const DevMesh3& m, const double* coef, cudaStrea
   if (nb > kMaxSolverBlocks) nb = kMaxSolverBlocks;
   DGDF_DISPATCH_K3(m.k, (k_diagnostics3<K><<<nb, kTetThreads, 0, s>>>(m, coef)));
   k_diag_finish3<<<1, 32, 0, s>>>(m, nb);
+  return cudaGetLastError();
+}
+
+int pressure3_parts(const DevMesh3& m) { return blocks3(m.n_tet); }
+
+cudaError_t launch_pressure3(const DevMesh3& m, double* pe, double* pf, double* part, double vol, cudaStream_t s) {
+  const int nb = blocks3(m.n_tet);
+  DGDF_DISPATCH_K3(m.k, (k_pressure3<K><<<nb, kTetThreads, 0, s>>>(m, pe, part)));
+  const size_t n = std::max(size_t(m.n_tet) * m.nw, size_t(m.n_face) * m.nl);
+  const int fb = int(std::min<size_t>((n + 255) / 256, 1024));
+  k_pressure3_finish<<<fb, 256, 0, s>>>(m, pe, pf, part, nb, vol);
   return cudaGetLastError();
 }
 

@@ -203,6 +203,22 @@ int build_ref3(int k, Ref3& r, std::string& err) {
         for (int m = 0; m < nl; ++m) s += C[size_t(j) * nl + m] * V[size_t(q) * nl + m];
         r.mu[size_t(q) * nl + j] = s;
       }
+    // the same basis at the face's k-lattice points
+    r.mu_lat.assign(size_t(nl) * nl, 0.0);
+    int p = 0;
+    for (int jj = 0; jj <= k; ++jj)
+      for (int ii = 0; ii <= k - jj; ++ii, ++p) {
+        const double sp = double(ii) / k, tp = double(jj) / k;
+        std::vector<double> mono(nl);
+        int m = 0;
+        for (int d = 0; d <= k; ++d)
+          for (int bb = 0; bb <= d; ++bb, ++m) mono[m] = std::pow(sp, d - bb) * std::pow(tp, bb);
+        for (int j = 0; j < nl; ++j) {
+          double s = 0;
+          for (int mm = 0; mm < nl; ++mm) s += C[size_t(j) * nl + mm] * mono[mm];
+          r.mu_lat[size_t(p) * nl + j] = s;
+        }
+      }
   }
   // lattice (l outer, j, i inner; i/k, j/k, l/k)
   r.lat_phi.resize(size_t(ns) * ns);
@@ -213,6 +229,20 @@ int build_ref3(int k, Ref3& r, std::string& err) {
         for (int i = 0; i <= k - l - j; ++i, ++p) {
           const double x[3] = {double(i) / k, double(j) / k, double(l) / k};
           B.eval(x, &r.lat_phi[size_t(p) * ns], nullptr);
+        }
+  }
+  // the first nw functions (a basis of P^(k-1)) at the (k-1)-lattice, or at the centroid
+  {
+    const int km = k - 1, nw = r.nw;
+    r.plat_phi.assign(size_t(nw) * nw, 0.0);
+    std::vector<double> all(ns);
+    int p = 0;
+    for (int l = 0; l <= km; ++l)
+      for (int j = 0; j <= km - l; ++j)
+        for (int i = 0; i <= km - l - j; ++i, ++p) {
+          const double x[3] = {km ? double(i) / km : 0.25, km ? double(j) / km : 0.25, km ? double(l) / km : 0.25};
+          B.eval(x, all.data(), nullptr);
+          for (int m = 0; m < nw; ++m) r.plat_phi[size_t(p) * nw + m] = all[m];
         }
   }
   r.lat_inv = r.lat_phi;
@@ -283,6 +313,16 @@ void class_ops3(const Ref3& r, Class3& co) {
       double v = (i == j) ? 1.0 : 0.0;
       for (int a = 0; a < nw; ++a) v -= D[size_t(a) * nd + i] * Wm[size_t(a) * nd + j];
       co.P[size_t(i) * nd + j] = v;
+    }
+  // pressure rows: u - D^T w = r and D u = 0 give w = -(D D^T)^-1 D r, r = f - C^T lam
+  co.W.assign(size_t(nw) * nd, 0.0);
+  for (size_t i = 0; i < co.W.size(); ++i) co.W[i] = -Wm[i];
+  co.WC.assign(size_t(nw) * 4 * nl, 0.0);
+  for (int a = 0; a < nw; ++a)
+    for (int l = 0; l < 4 * nl; ++l) {
+      double v = 0;
+      for (int j = 0; j < nd; ++j) v += co.W[size_t(a) * nd + j] * C[size_t(l) * nd + j];
+      co.WC[size_t(a) * 4 * nl + l] = v;
     }
   for (int i = 0; i < nd; ++i)
     for (int j = i + 1; j < nd; ++j) {

@@ -35,6 +35,10 @@ struct Ref3 {
   std::vector<double> fphi, fdphi;    // [4 faces][6 perms][nqf][ns], [4][6][nqf][ns][3]
   std::vector<double> mu;             // multiplier basis at the face points [nqf][nl]
   std::vector<double> lat_phi, lat_inv;   // basis at the k-lattice [ns][ns] and its inverse
+  std::vector<double> plat_phi;       // the first nw functions (P^(k-1)) at the (k-1)-lattice
+                                      // [nw][nw] (the centroid for k = 1)
+  std::vector<double> mu_lat;         // multiplier basis at the face's k-lattice points [nl][nl]:
+                                      // (s, t) = (i/k, j/k), j = 0..k, i = 0..k-j (i fastest)
 };
 
 struct Class3 {
@@ -46,6 +50,8 @@ struct Class3 {
   std::vector<double> P;    // [nd][nd]
   std::vector<double> G;    // [4nl][nd]  C P
   std::vector<double> S;    // [4nl][4nl] C P C^T
+  std::vector<double> W;    // [nw][nd]   pressure rows of the local solve: w = W (f - C^T lam)
+  std::vector<double> WC;   // [nw][4nl]  W C^T
 };
 
 struct HostMesh3 {

@@ -172,3 +172,31 @@ def test_rk3_parity_k1_multilevel_n3(g):
     m.project_divfree()
     m.rk3_step(dt, 4)
     assert rel(m.get_velocity(), d.to_lattice(U)) < TOL
+
+
+@pytest.mark.parametrize("N,k,nu,precond", [(2, 1, 0.01, 0), (2, 2, 0.0, 0), (3, 2, 0.01, 0), (3, 1, 0.0, 1)])
+def test_pressure_parity(g, N, k, nu, precond):
+    # the pressure of L(u) (eq. (12) with that functional alone), mean-free, at the element's
+    # degree-(k-1) lattice points and the face's degree-k lattice points
+    vid, X = kuhn_cube_mesh(N)
+    d = Discretization3(vid, X, k, nu)
+    v = field(X, k, 40 + N, noise=0.2)
+    m = g.DGMesh3(vid, X, k, nu, precond=precond)
+    m.set_velocity(v)
+    m.project_divfree()
+    m.rk3_step(0.01, 1)                    # a solve history, which the pressure solve must not use
+    pe, pf = m.get_pressure()
+    U = d.from_lattice(m.get_velocity())
+    w, lam = d.pressure(U)
+    pe_ref, pf_ref = d.pressure_lattice(w, lam)
+    assert pe.shape == pe_ref.shape and pf.shape == pf_ref.shape
+    assert rel(pe, pe_ref) < 1e-11
+    assert rel(pf, pf_ref) < 1e-11
+    # element pressure alone; the state is unchanged and steps still match
+    pe2, none = m.get_pressure(with_face=False)
+    assert none is None and rel(pe2, pe) < 1e-13
+    u0 = m.get_velocity()
+    m.rk3_step(0.01, 1)
+    ref = d.to_lattice(d.rk3_step(d.from_lattice(u0), 0.01, 1))
+    assert rel(m.get_velocity(), ref) < TOL
+
