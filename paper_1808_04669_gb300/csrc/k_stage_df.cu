@@ -477,7 +477,10 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df2(DevMesh m, Sta
 // double-float, with lam from the double-float solver (lam_is_df) or the FP64 one.
 // Writes the double-float twin out_df and, if out is given, u in FP64. A block's rows of
 // h and u pass through shared memory (padded rows), so that global reads and writes are
-// coalesced; each thread computes one triangle.
+// coalesced; each thread computes one triangle. A full block's thread issues all ND of its
+// coalesced tile loads before it stores any of them to shared memory, so that enough
+// bytes are in flight per SM to stream h at HBM speed (the loads of the grid-stride loop
+// each waited for the last).
 constexpr int kRecoverThreads = 128;
 
 template <int K>
@@ -488,7 +491,18 @@ __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, doubl
   const int t0 = blockIdx.x * kRecoverThreads;
   const int nt = min(kRecoverThreads, m.n_tri - t0);
   const float2* hb = m.h_df + size_t(t0) * ND;
-  for (int e = threadIdx.x; e < nt * ND; e += kRecoverThreads) tile[(e / ND) * RS + e % ND] = hb[e];
+  if (nt == kRecoverThreads) {
+    float2 v[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = __ldg(&hb[q * kRecoverThreads + threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const int e = q * kRecoverThreads + threadIdx.x;
+      tile[(e / ND) * RS + e % ND] = v[q];
+    }
+  } else {
+    for (int e = threadIdx.x; e < nt * ND; e += kRecoverThreads) tile[(e / ND) * RS + e % ND] = hb[e];
+  }
   __syncthreads();
   if (int(threadIdx.x) < nt) {
     const int t = t0 + threadIdx.x;
