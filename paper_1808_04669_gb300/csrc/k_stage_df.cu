@@ -477,26 +477,28 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df2(DevMesh m, Sta
 // double-float, with lam from the double-float solver (lam_is_df) or the FP64 one.
 // Writes the double-float twin out_df and, if out is given, u in FP64. A block's rows of
 // h and u pass through shared memory (padded rows), so that global reads and writes are
-// coalesced; each thread computes one triangle. A full block's thread issues all ND of its
-// coalesced tile loads before it stores any of them to shared memory, so that enough
-// bytes are in flight per SM to stream h at HBM speed (the loads of the grid-stride loop
-// each waited for the last).
-constexpr int kRecoverThreads = 128;
+// coalesced; a thread issues all its tile loads before its shared-memory stores. Two threads
+// per triangle, one per velocity component (warp-uniform): the whole grid is resident at
+// once, and twice the threads with half the compensated sums each hide more of the gathers'
+// latency.
+constexpr int kRecoverTris = 128;
+constexpr int kRecoverThreads = 2 * kRecoverTris;
 
 template <int K>
 __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, double* out, float2* out_df) {
   using D = Dims<K>;
-  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL, RS = ND + 1;
-  __shared__ float2 tile[kRecoverThreads * RS];
-  const int t0 = blockIdx.x * kRecoverThreads;
-  const int nt = min(kRecoverThreads, m.n_tri - t0);
+  constexpr int ND = D::ND, NS = D::NS, NL = D::NL, L3 = 3 * NL, RS = ND + 1;
+  constexpr int PER = kRecoverTris * ND / kRecoverThreads;   // tile values per thread (= NS)
+  __shared__ float2 tile[kRecoverTris * RS];
+  const int t0 = blockIdx.x * kRecoverTris;
+  const int nt = min(kRecoverTris, m.n_tri - t0);
   const float2* hb = m.h_df + size_t(t0) * ND;
-  if (nt == kRecoverThreads) {
-    float2 v[ND];
+  if (nt == kRecoverTris) {
+    float2 v[PER];
 #pragma unroll
-    for (int q = 0; q < ND; ++q) v[q] = __ldg(&hb[q * kRecoverThreads + threadIdx.x]);
+    for (int q = 0; q < PER; ++q) v[q] = __ldg(&hb[q * kRecoverThreads + threadIdx.x]);
 #pragma unroll
-    for (int q = 0; q < ND; ++q) {
+    for (int q = 0; q < PER; ++q) {
       const int e = q * kRecoverThreads + threadIdx.x;
       tile[(e / ND) * RS + e % ND] = v[q];
     }
@@ -504,8 +506,9 @@ __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, doubl
     for (int e = threadIdx.x; e < nt * ND; e += kRecoverThreads) tile[(e / ND) * RS + e % ND] = hb[e];
   }
   __syncthreads();
-  if (int(threadIdx.x) < nt) {
-    const int t = t0 + threadIdx.x;
+  const int r = threadIdx.x % kRecoverTris, c = threadIdx.x / kRecoverTris;
+  if (r < nt) {
+    const int t = t0 + r;
     dfl lam[L3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -518,9 +521,10 @@ __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, doubl
       }
     }
     const float2* G = m.Gdf + size_t(__ldg(&m.tri_class[t])) * L3 * ND;
-    float2* row = tile + threadIdx.x * RS;
-#pragma unroll 4
-    for (int i = 0; i < ND; ++i) {
+    float2* row = tile + r * RS;
+#pragma unroll 5
+    for (int j = 0; j < NS; ++j) {
+      const int i = c * NS + j;
       dacc v = dacc_of(to_dfl(row[i]));
 #pragma unroll
       for (int l = 0; l < L3; ++l) mad(v, to_dfl(__ldg(&G[l * ND + i])), lam[l]);
@@ -596,7 +600,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
   if (m.tc_rec) return launch_recover_tc(m, out, out_df, s);
-  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverThreads), kRecoverThreads, 0, s>>>(m, out, out_df)));
+  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverTris), kRecoverThreads, 0, s>>>(m, out, out_df)));
   return cudaGetLastError();
 }
 
