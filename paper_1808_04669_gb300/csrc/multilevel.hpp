@@ -32,7 +32,7 @@
 namespace dgdf {
 
 constexpr int kMLMaxLevels = 16;
-constexpr int kMLCoarseMax = 768;
+constexpr int kMLCoarseMax = 1024;
 
 struct CsrHost {
   int n_rows = 0, n_cols = 0;
