@@ -563,6 +563,86 @@ __global__ void k_coef_to_lattice(DevMesh m, const double* coef, double* vals) {
   }
 }
 
+// The same conversions for the mixed form, in double-float arithmetic on the FP32 pipes (the
+// FP64 pipe, 1/64 of the FP32 rate here, only splits the inputs and rounds the outputs). The
+// tables are split into double-float pairs once per block; a block's 128 triangles pass through
+// shared memory, so that global reads and writes are coalesced.
+constexpr int kConvTris = 128;
+
+template <int K>
+__global__ void __launch_bounds__(kConvTris) k_lattice_to_coef_df(DevMesh m, const double* vals, double* coef) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, NV = 2 * NS, RS = NV + 1;
+  __shared__ float2 tab[NS * NS];
+  __shared__ double tile[kConvTris * RS];
+  for (int i = threadIdx.x; i < NS * NS; i += kConvTris) tab[i] = to_float2(dfl(m.lat_inv[i]));
+  const int t0 = blockIdx.x * kConvTris;
+  const int nt = min(kConvTris, m.n_tri - t0);
+  const double* vb = vals + size_t(t0) * NV;
+  for (int e = threadIdx.x; e < nt * NV; e += kConvTris) tile[(e / NV) * RS + e % NV] = vb[e];
+  __syncthreads();
+  if (int(threadIdx.x) < nt) {
+    const int t = t0 + threadIdx.x;
+    const dfl sq(1.0 / m.geo[size_t(m.tri_class[t]) * kGeo + G_S]);
+    double* row = tile + threadIdx.x * RS;
+    dfl v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = dfl(row[i]);   // [p][c]
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      dacc c0 = dacc_zero(), c1 = dacc_zero();
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        const dfl a = to_dfl(tab[j * NS + p]);
+        mad(c0, a, v[2 * p]);
+        mad(c1, a, v[2 * p + 1]);
+      }
+      row[j] = to_double(sq * val(c0));
+      row[NS + j] = to_double(sq * val(c1));
+    }
+  }
+  __syncthreads();
+  double* cb = coef + size_t(t0) * NV;
+  for (int e = threadIdx.x; e < nt * NV; e += kConvTris) cb[e] = tile[(e / NV) * RS + e % NV];
+}
+
+template <int K>
+__global__ void __launch_bounds__(kConvTris) k_coef_to_lattice_df(DevMesh m, const double* coef, double* vals) {
+  using D = Dims<K>;
+  constexpr int NS = D::NS, NV = 2 * NS, RS = NV + 1;
+  __shared__ float2 tab[NS * NS];
+  __shared__ double tile[kConvTris * RS];
+  for (int i = threadIdx.x; i < NS * NS; i += kConvTris) tab[i] = to_float2(dfl(m.lat_phi[i]));
+  const int t0 = blockIdx.x * kConvTris;
+  const int nt = min(kConvTris, m.n_tri - t0);
+  const double* cb = coef + size_t(t0) * NV;
+  for (int e = threadIdx.x; e < nt * NV; e += kConvTris) tile[(e / NV) * RS + e % NV] = cb[e];
+  __syncthreads();
+  if (int(threadIdx.x) < nt) {
+    const int t = t0 + threadIdx.x;
+    const dfl sc(m.geo[size_t(m.tri_class[t]) * kGeo + G_S]);
+    double* row = tile + threadIdx.x * RS;
+    dfl c[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c[i] = dfl(row[i]);   // [c][j]
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      dacc v0 = dacc_zero(), v1 = dacc_zero();
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const dfl a = to_dfl(tab[p * NS + j]);
+        mad(v0, a, c[j]);
+        mad(v1, a, c[NS + j]);
+      }
+      row[2 * p] = to_double(sc * val(v0));
+      row[2 * p + 1] = to_double(sc * val(v1));
+    }
+  }
+  __syncthreads();
+  double* vb = vals + size_t(t0) * NV;
+  for (int e = threadIdx.x; e < nt * NV; e += kConvTris) vb[e] = tile[(e / NV) * RS + e % NV];
+}
+
 // Diagnostics partials per block: red[0] energy, red[1] enstrophy, red[2] max |div|,
 // red[3] max |[u.n]| (each facet is seen from both sides).
 template <int K>
@@ -708,13 +788,20 @@ inline int blocks_for(long long n, int bs) { return int((n + bs - 1) / bs); }
     default: return cudaErrorInvalidValue;        \
   }
 
+// Lattice conversions: FP64 arithmetic in the FP64 form, double-float in the mixed form.
 cudaError_t launch_lattice_to_coef(const DevMesh& m, const double* vals, double* coef, cudaStream_t s) {
-  DGDF_DISPATCH_K(m.k, (k_lattice_to_coef<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, vals, coef)));
+  if (m.elem_df)
+    DGDF_DISPATCH_K(m.k, (k_lattice_to_coef_df<K><<<blocks_for(m.n_tri, kConvTris), kConvTris, 0, s>>>(m, vals, coef)))
+  else
+    DGDF_DISPATCH_K(m.k, (k_lattice_to_coef<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, vals, coef)))
   return cudaGetLastError();
 }
 
 cudaError_t launch_coef_to_lattice(const DevMesh& m, const double* coef, double* vals, cudaStream_t s) {
-  DGDF_DISPATCH_K(m.k, (k_coef_to_lattice<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, coef, vals)));
+  if (m.elem_df)
+    DGDF_DISPATCH_K(m.k, (k_coef_to_lattice_df<K><<<blocks_for(m.n_tri, kConvTris), kConvTris, 0, s>>>(m, coef, vals)))
+  else
+    DGDF_DISPATCH_K(m.k, (k_coef_to_lattice<K><<<blocks_for(m.n_tri, 128), 128, 0, s>>>(m, coef, vals)))
   return cudaGetLastError();
 }
 
