@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 # over the three stages of a step (the first stage reads one state, the others two), from the
 # ncu capture summarised in profiles/; used only while the stage-kernel sources still hash to
 # the captured `sha`, else the line reports null.
-NCU_TRAFFIC = {"stage_residual": {"sha": "bbe447730577cfd4", "n_tri": 131072, "bytes": 40973397,
+NCU_TRAFFIC = {"stage_residual": {"sha": "62f71c3ca9c15082", "n_tri": 131072, "bytes": 40963755,
                                   "source": "profiles/k_stage_df2_shear_n256_k3.md"}}
 
 

@@ -477,18 +477,23 @@ __global__ void __launch_bounds__(kStageDfThreads, 2) k_stage_df2(DevMesh m, Sta
 // double-float, with lam from the double-float solver (lam_is_df) or the FP64 one.
 // Writes the double-float twin out_df and, if out is given, u in FP64. A block's rows of
 // h and u pass through shared memory (padded rows), so that global reads and writes are
-// coalesced; a thread issues all its tile loads before its shared-memory stores. Two threads
-// per triangle, one per velocity component (warp-uniform): the whole grid is resident at
-// once, and twice the threads with half the compensated sums each hide more of the gathers'
-// latency.
+// coalesced; a thread issues all its tile loads before its shared-memory stores. For k = 3,
+// two threads per triangle, one per velocity component (warp-uniform): twice the threads
+// with half the compensated sums each hide more of the gathers' latency (33.1 -> 30.8 us per
+// launch at 256^2); for k <= 2 the second thread's repeated gathers cost more than that.
 constexpr int kRecoverTris = 128;
-constexpr int kRecoverThreads = 2 * kRecoverTris;
+template <int K>
+struct RecoverShape {
+  static constexpr int TPT = K == 3 ? 2 : 1;           // threads per triangle
+  static constexpr int THREADS = TPT * kRecoverTris;
+};
 
 template <int K>
-__global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, double* out, float2* out_df) {
+__global__ void __launch_bounds__(RecoverShape<K>::THREADS) k_recover_df(DevMesh m, double* out, float2* out_df) {
   using D = Dims<K>;
-  constexpr int ND = D::ND, NS = D::NS, NL = D::NL, L3 = 3 * NL, RS = ND + 1;
-  constexpr int PER = kRecoverTris * ND / kRecoverThreads;   // tile values per thread (= NS)
+  constexpr int ND = D::ND, NL = D::NL, L3 = 3 * NL, RS = ND + 1;
+  constexpr int TPT = RecoverShape<K>::TPT, kRecoverThreads = RecoverShape<K>::THREADS;
+  constexpr int PER = kRecoverTris * ND / kRecoverThreads;   // tile values per thread
   __shared__ float2 tile[kRecoverTris * RS];
   const int t0 = blockIdx.x * kRecoverTris;
   const int nt = min(kRecoverTris, m.n_tri - t0);
@@ -507,6 +512,7 @@ __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, doubl
   }
   __syncthreads();
   const int r = threadIdx.x % kRecoverTris, c = threadIdx.x / kRecoverTris;
+  constexpr int NOUT = ND / TPT;   // outputs per thread: one component (TPT = 2) or both
   if (r < nt) {
     const int t = t0 + r;
     dfl lam[L3];
@@ -523,8 +529,8 @@ __global__ void __launch_bounds__(kRecoverThreads) k_recover_df(DevMesh m, doubl
     const float2* G = m.Gdf + size_t(__ldg(&m.tri_class[t])) * L3 * ND;
     float2* row = tile + r * RS;
 #pragma unroll 5
-    for (int j = 0; j < NS; ++j) {
-      const int i = c * NS + j;
+    for (int j = 0; j < NOUT; ++j) {
+      const int i = c * NOUT + j;
       dacc v = dacc_of(to_dfl(row[i]));
 #pragma unroll
       for (int l = 0; l < L3; ++l) mad(v, to_dfl(__ldg(&G[l * ND + i])), lam[l]);
@@ -600,7 +606,7 @@ cudaError_t launch_stage_df(const DevMesh& m, const StageArgs& a, cudaStream_t s
 
 cudaError_t launch_recover_df(const DevMesh& m, double* out, float2* out_df, cudaStream_t s) {
   if (m.tc_rec) return launch_recover_tc(m, out, out_df, s);
-  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverTris), kRecoverThreads, 0, s>>>(m, out, out_df)));
+  DGDF_DISPATCH_K(m.k, (k_recover_df<K><<<blocks_for(m.n_tri, kRecoverTris), RecoverShape<K>::THREADS, 0, s>>>(m, out, out_df)));
   return cudaGetLastError();
 }
 
