@@ -84,15 +84,71 @@ def measured_peaks():
 
 
 class ClockSampler:
+    """SM clock and clock-event reasons of one GPU during a region. Read-only NVML queries
+    (libnvidia-ml through ctypes) polled every 2 ms by a thread, so that a region of a few tens
+    of milliseconds still gets samples; `nvidia-smi -lms 200` where NVML cannot be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h): SW power cap, HW slowdown, SW / HW thermal slowdown
+    REASON_BITS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+                   ("hw_thermal_slowdown", 0x40))
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.thread = None
+        self.samples = []
+        self.source = None
+
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        dev = ctypes.c_void_p()
+        ok = False
+        try:   # the CUDA device by its UUID (NVML may number the GPUs differently from CUDA)
+            import torch
+            u = str(torch.cuda.get_device_properties(self.index).uuid)
+            u = u if u.startswith("GPU-") else "GPU-" + u
+            ok = lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(u.encode()), ctypes.byref(dev)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(dev)) != 0:
+            lib.nvmlShutdown()
+            return None
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, dev, reasons_fn
 
     def __enter__(self):
+        import ctypes
+        import threading
+        self.samples = []
+        try:
+            handles = self._nvml()
+        except (OSError, AttributeError):
+            handles = None
+        if handles is not None:
+            lib, dev, reasons_fn = handles
+            self.source = "nvml"
+            self.stop = threading.Event()
+
+            def poll():
+                clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+                while not self.stop.is_set():
+                    if (lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0 and       # NVML_CLOCK_SM
+                            lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0 and
+                            reasons_fn(dev, ctypes.byref(rs)) == 0):
+                        self.samples.append((float(clk.value), float(mx.value), int(rs.value)))
+                    self.stop.wait(0.002)
+                lib.nvmlShutdown()
+
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.thread.start()
+            return self
+        self.source = "nvidia-smi"
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -103,6 +159,9 @@ class ClockSampler:
 
     def __exit__(self, *a):
         self.lines = []
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -114,6 +173,13 @@ class ClockSampler:
 
     def summary(self):
         sm, smax, reasons = [], [], set()
+        if self.source == "nvml":
+            for c, m, r in self.samples:
+                sm.append(c)
+                smax.append(m)
+                for n, bit in self.REASON_BITS:
+                    if r & bit:
+                        reasons.add(n)
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for l in getattr(self, "lines", []):
             p = [x.strip() for x in l.split(",")]
@@ -128,9 +194,10 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "min_sm_mhz": min(sm), "source": self.source}
 
 
 def element_kernel_sha():
