@@ -364,6 +364,41 @@ def test_multilevel_rk3_parity(g, N, k, walls, perturb):
         assert dg["max_jump"] < 1e-11 and dg["max_div"] < 1e-10
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multilevel_warm_start_history_across_step_sizes_and_schemes(g, prec):
+    # the multilevel solves start from the same stage's multipliers in the last steps (quadratic
+    # extrapolation once three steps had the same dt, linear with two, the last one rescaled after
+    # a change of dt, none after a change of scheme); whatever the start, every solve meets
+    # cg_rtol, so the states follow the oracle's direct solves through the whole sequence, and
+    # with a full history the solves take fewer iterations than without one
+    k, nu = 2, 1e-3
+    vid, X = synth.split_square_mesh(12, L=1.0, periodic=False)
+    vals = synth.sample_lattice(synth.random_spectrum_velocity(7, kmax=3, L=1.0), X, k)
+    dt = synth.cfl_dt(X, k, float(np.sqrt((vals ** 2).sum(-1)).max()), nu)
+    d = Discretization(vid, X, k, nu)
+    U = d.project(d.from_lattice(vals))
+    mesh = g.DGMesh(vid, X, k, nu, precision=prec)
+    assert mesh.solver_stats()["preconditioner"] == "multilevel"
+    mesh.set_velocity(vals)
+    mesh.project_divfree()
+    tol = TOL64 if prec == 0 else TOLMIX
+    its = []
+    for n, h, scheme in ((1, dt, g.SSPRK3), (5, dt, g.SSPRK3), (2, 0.5 * dt, g.SSPRK3), (4, dt, g.SSPRK3),
+                         (2, dt, g.RK4), (3, dt, g.SSPRK3)):
+        st0 = mesh.solver_stats()
+        mesh.step(h, n, scheme=scheme)
+        st1 = mesh.solver_stats()
+        its.append((st1["total_iters"] - st0["total_iters"]) / (st1["solves"] - st0["solves"]))
+        if scheme == g.RK4:
+            U = d.rk4_step(U, h, n)
+        else:
+            U = d.rk3_step(U, h, n)
+        assert rel(mesh.get_velocity(), d.to_lattice(U)) < tol, (prec, n, h, scheme)
+    # the first step starts cold (then from the previous stage rescaled); five more steps at the
+    # same dt bring the full history
+    assert its[1] < its[0], its
+
+
 def test_multilevel_iterations_on_a_128_box_with_walls(g):
     # the case block Jacobi handles worst: 128 x 128 box, BDM_3 (1934 iterations per solve);
     # the multilevel PCG stays at a few dozen and gives the same projection
