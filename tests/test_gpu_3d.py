@@ -200,3 +200,28 @@ def test_pressure_parity(g, N, k, nu, precond):
     ref = d.to_lattice(d.rk3_step(d.from_lattice(u0), 0.01, 1))
     assert rel(m.get_velocity(), ref) < TOL
 
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_rk3_warm_start_history_across_step_sizes(g, precond):
+    # each stage's face solve starts from the same stage's multipliers in the last steps:
+    # quadratic extrapolation once three steps had the same dt, linear with two, the last one
+    # rescaled after a change of dt; every solve meets cg_rtol whatever the start
+    N, k, nu = 2, 2, 1e-2
+    vid, X = kuhn_cube_mesh(N)
+    d = Discretization3(vid, X, k, nu)
+    v = field(X, k, 60, noise=0.1)
+    dt = 0.2 * (2 * np.pi / N) / (k * k * np.abs(v).max())
+    m = g.DGMesh3(vid, X, k, nu, precond=precond)
+    m.set_velocity(v)
+    m.project_divfree()
+    U = d.project(d.from_lattice(v))
+    its = []
+    for n, h in ((1, dt), (5, dt), (2, 0.5 * dt), (3, dt)):
+        before = m.diagnostics()
+        m.rk3_step(h, n)
+        after = m.diagnostics()
+        its.append((after["total_iters"] - before["total_iters"]) / (after["solves"] - before["solves"]))
+        U = d.rk3_step(U, h, n)
+        assert rel(m.get_velocity(), d.to_lattice(U)) < TOL, (n, h)
+    assert its[1] < its[0], its
