@@ -72,7 +72,7 @@ int dg3_rk3_step(dg_mesh3* mesh, double dt, int64_t nsteps);
  * p_face [n_face][(k+1)(k+2)/2] or NULL: lam at the points p0 + (i/k)(p1 - p0) + (j/k)(p2 - p0),
  * j = 0..k, i = 0..k-j (i fastest), p0, p1, p2 the face's vertices in increasing periodic vertex
  * id; faces are numbered in order of first appearance over the tetrahedra t = 0, 1, ... and
- * their local faces e = 0..3.
+ * their local faces e = 0..3 (dg3_host_faces in dgdf_host.h lists them).
  * Host or device memory. Errors as dg3_project_divfree. */
 int dg3_get_pressure(dg_mesh3* mesh, double* p_elem, double* p_face, int on_device);
 

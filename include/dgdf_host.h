@@ -74,6 +74,16 @@ int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const doubl
                        int64_t info[34], int nr, const double* r, double* z, const double* g, double* lam,
                        double rtol, int64_t* iters);
 
+/* Face numbering of the three-dimensional set-up (dg3_mesh_create's, include/dgdf3.h), on the host.
+ * *n_face_out (may be NULL) receives the number of faces; face_tet [n_face][2] and face_loc
+ * [n_face][2] (each may be NULL) the two tetrahedra of every face and its local index in each (the
+ * face opposite that local vertex); face_vid [n_face][3] (may be NULL) its periodic vertex ids in
+ * increasing order (p0, p1, p2 of the canonical parametrisation that dg3_get_pressure's face
+ * values use). Call with NULL arrays first for the count; caller-owned host arrays.
+ * Errors: DG_ERR_INVALID_ARG (NULL mesh arrays), DG_ERR_MESH, DG_ERR_UNSUPPORTED. */
+int dg3_host_faces(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords, int64_t* n_face_out,
+                   int64_t* face_tet, int8_t* face_loc, int64_t* face_vid);
+
 /* Three-dimensional host check (include/dgdf3.h conventions): the L2 projection of the field
  * given by lattice values vals [n_tet][n_lat3(k)][3] onto the divergence-free space, computed on
  * the host from the set-up dg3_mesh_create uploads (class operators, face stencil) with a host

@@ -467,6 +467,23 @@ def host_multilevel(tri_vertex_ids, tri_coords, k, alpha=2.0, r=None, g=None, rt
             "z": z, "lam": lam, "iters": int(it.value) if g is not None else None}
 
 
+def host_faces3(tet_vertex_ids, tet_coords):
+    """Face numbering of the 3-D set-up (include/dgdf_host.h, dg3_host_faces): (face_tet [n_face, 2],
+    face_loc [n_face, 2], face_vid [n_face, 3] sorted periodic vertex ids)."""
+    vid = np.ascontiguousarray(tet_vertex_ids, dtype=np.int64)
+    X = np.ascontiguousarray(tet_coords, dtype=np.float64)
+    V = ctypes.c_void_p
+    nf = ctypes.c_int64(0)
+    check(lib().dg3_host_faces(vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), ctypes.byref(nf),
+                               None, None, None), "dg3_host_faces")
+    ft = np.empty((nf.value, 2), dtype=np.int64)
+    fl = np.empty((nf.value, 2), dtype=np.int8)
+    fv = np.empty((nf.value, 3), dtype=np.int64)
+    check(lib().dg3_host_faces(vid.shape[0], vid.ctypes.data_as(V), X.ctypes.data_as(V), None,
+                               ft.ctypes.data_as(V), fl.ctypes.data_as(V), fv.ctypes.data_as(V)), "dg3_host_faces")
+    return ft, fl, fv
+
+
 def host_project3(tet_vertex_ids, tet_coords, k, vals, alpha=2.0):
     """Host-side L2 projection of a 3-D field onto the divergence-free space from the library's own
     set-up (include/dgdf_host.h, dg3_host_project): (lattice values, PCG iterations)."""
@@ -517,5 +534,5 @@ def facet_solve_noalloc(k, facet_nbr, stencil, blocks, binv, g, lam, rtol=1e-13,
     return it.value, rr.value
 
 
-__all__ = ["DGMesh", "DGMesh3", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "host_project3", "facet_solve_noalloc",
+__all__ = ["DGMesh", "DGMesh3", "DGBatch", "DGError", "FP64", "MIXED", "PRECOND_AUTO", "PRECOND_BLOCK_JACOBI", "PRECOND_MULTILEVEL", "host_topology", "host_reference", "host_facet_operator", "host_lattice", "host_multilevel", "host_project3", "host_faces3", "facet_solve_noalloc",
            "lib"]

@@ -20,7 +20,7 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_create_ex", "dg_set_inflow", "dg_mesh_dest
            "dg_host_facet_operator", "dg_host_lattice", "dg_host_multilevel",
            "dg3_mesh_create", "dg3_mesh_destroy", "dg3_mesh_info", "dg3_set_velocity", "dg3_get_velocity",
            "dg3_project_divfree", "dg3_rk3_step", "dg3_eval_residual", "dg3_get_pressure", "dg3_get_diagnostics",
-           "dg3_host_project"]
+           "dg3_host_project", "dg3_host_faces"]
 
 
 class DGParams(ctypes.Structure):
@@ -54,6 +54,7 @@ def lib():
         "dg3_rk3_step": (ctypes.c_int, [P, D, I64]),
         "dg3_eval_residual": (ctypes.c_int, [P, P, ctypes.c_int]),
         "dg3_get_pressure": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "dg3_host_faces": (ctypes.c_int, [ctypes.c_int64, P, P, P, P, P, P]),
         "dg3_get_diagnostics": (ctypes.c_int, [P, P]),
         "dg3_host_project": (ctypes.c_int, [I64, P, P, ctypes.c_int, D, P, P, P]),
         "dg_mesh_info": (ctypes.c_int, [P, P]),

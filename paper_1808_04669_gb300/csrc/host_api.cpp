@@ -173,6 +173,34 @@ int dg_host_multilevel(int64_t n_tri, const int64_t* tri_vertex_ids, const doubl
   return DG_OK;
 }
 
+int dg3_host_faces(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords, int64_t* n_face_out,
+                   int64_t* face_tet, int8_t* face_loc, int64_t* face_vid) {
+  if (!tet_vertex_ids || !tet_coords) return DG_ERR_INVALID_ARG;
+  dgdf::HostMesh3 hm;
+  std::string err;
+  int rc = dgdf::build_host_mesh3(n_tet, tet_vertex_ids, tet_coords, 1, 2.0, hm, err);
+  if (rc) return rc;
+  if (n_face_out) *n_face_out = hm.n_face;
+  for (int64_t f = 0; f < hm.n_face; ++f) {
+    for (int s = 0; s < 2; ++s) {
+      if (face_tet) face_tet[f * 2 + s] = hm.face_tet[size_t(f) * 2 + s];
+      if (face_loc) face_loc[f * 2 + s] = hm.face_loc[size_t(f) * 2 + s];
+    }
+    if (face_vid) {
+      // the three vertices of the first side's local face (all but its vertex e), sorted by id
+      const int64_t t = hm.face_tet[size_t(f) * 2];
+      const int e = hm.face_loc[size_t(f) * 2];
+      int64_t id[3];
+      int n = 0;
+      for (int v = 0; v < 4; ++v)
+        if (v != e) id[n++] = tet_vertex_ids[t * 4 + v];
+      std::sort(id, id + 3);
+      for (int c = 0; c < 3; ++c) face_vid[f * 3 + c] = id[c];
+    }
+  }
+  return DG_OK;
+}
+
 int dg3_host_project(int64_t n_tet, const int64_t* tet_vertex_ids, const double* tet_coords, int k, double alpha,
                      const double* vals, double* out, int64_t* iters) {
   if (!vals || !out || !(alpha > 0.0)) return DG_ERR_INVALID_ARG;

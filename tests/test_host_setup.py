@@ -312,3 +312,22 @@ def test_three_dimensional_setup_projects_like_the_oracle(g, N, k):
     ref = d.to_lattice(d.project(d.from_lattice(v)))
     assert np.linalg.norm(out - ref) < 1e-11 * np.linalg.norm(ref)
     assert 0 < its < 60
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_three_dimensional_face_numbering_matches_the_oracle(g, N):
+    # dg3_host_faces: faces in order of first appearance over (tetrahedron, local face), the two
+    # sides and local indices as the oracle's topology finds them, vertex ids sorted
+    from oracle.dg3 import Topology3
+    from synth.mesh3 import kuhn_cube_mesh
+    vid, X = kuhn_cube_mesh(N)
+    ft, fl, fv = g.host_faces3(vid, X)
+    T = Topology3(vid, X)
+    assert ft.shape == (T.n_face, 2) and fv.shape == (T.n_face, 3)
+    assert np.array_equal(ft, T.face_tet) and np.array_equal(fl.astype(np.int64), T.face_loc)
+    for f in range(T.n_face):
+        loc = [v for v in range(4) if v != fl[f, 0]]
+        assert list(fv[f]) == sorted(int(vid[ft[f, 0], v]) for v in loc)
+        # the other side sees the same three periodic vertex ids
+        loc1 = [v for v in range(4) if v != fl[f, 1]]
+        assert sorted(int(vid[ft[f, 1], v]) for v in loc1) == list(fv[f])
